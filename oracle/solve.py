@@ -1,0 +1,73 @@
+"""The DevelSet-Optimizer loop, FP64 (test infrastructure only).
+
+Sec. III-A / III-C: starting from phi_0 (the TSDF of the target, or a given
+level set), each iteration i
+  1. extracts the mask M = [phi <= 0]                        Eq. (phi2mask)
+  2. images it, I = sum_j w_j |M (*) h_j|^2                    Sec. II-B
+  3. evaluates L_DSO and R = dL/dI at the three dose corners  Sec. III-A
+  4. back-propagates V = dL/dM                                 Eqs. (ilt_gradient), (pvb_gradient), (vel)
+  5. updates phi by upwind transport + curvature               Eq. (dso_evolution)
+  6. re-initialises phi to the TSDF of its mask when (i + 1) is a multiple
+     of ``reinit_every`` (global iteration index, so a split run resumes
+     exactly).
+History entry i holds (L_DSO, L2, PVB) of the mask that iteration i imaged;
+entry ``iters`` holds the final mask's.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import litho, resist as _resist, levelset, sdf
+
+
+@dataclass
+class SolveParams:
+    resist: _resist.ResistParams = field(default_factory=_resist.ResistParams)
+    dt: float = 0.5
+    lam: float = 0.1
+    iters: int = 20
+    reinit_every: int = 5
+    start_iter: int = 0
+    d_lo: float = sdf.D_LO
+    d_hi: float = sdf.D_HI
+
+
+@dataclass
+class SolveResult:
+    phi: np.ndarray
+    mask: np.ndarray
+    loss: list
+    l2: list
+    pvb: list
+
+
+def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None):
+    """One DSO iteration at global index i. Returns (phi_next, ResistResult)."""
+    M = levelset.mask_from_phi(phi)
+    I = litho.aerial(M, H, w)
+    res = _resist.resist(I, Zt, p.resist)
+    V = litho.aerial_gradient(M, res.R, H, w)
+    vmax = float(np.abs(V).max())
+    phi, M = levelset.step(phi, V, vmax, m, p.dt, p.lam)
+    if p.reinit_every > 0 and (i + 1) % p.reinit_every == 0:
+        phi = sdf.tsdf(M, p.d_lo, p.d_hi)
+    return phi, res
+
+
+def ilt_solve(Zt, H, w, p: SolveParams, phi0=None, m=None) -> SolveResult:
+    Zt = (np.asarray(Zt) != 0).astype(np.uint8)
+    phi = sdf.tsdf(Zt, p.d_lo, p.d_hi) if phi0 is None else np.asarray(phi0, dtype=np.float64).copy()
+    loss, l2, pvb = [], [], []
+    for t in range(p.iters):
+        phi, res = iterate(phi, Zt, H, w, p, p.start_iter + t, m)
+        loss.append(res.loss)
+        l2.append(res.l2)
+        pvb.append(res.pvb)
+    M = levelset.mask_from_phi(phi)
+    res = _resist.resist(litho.aerial(M, H, w), Zt, p.resist)
+    loss.append(res.loss)
+    l2.append(res.l2)
+    pvb.append(res.pvb)
+    return SolveResult(phi=phi, mask=M, loss=loss, l2=l2, pvb=pvb)
