@@ -1,0 +1,355 @@
+"""Benchmark of the level-set ILT loop on one node (one process per GPU).
+
+A step is one full DSO solve (TSDF init, `iters` iterations of image / loss /
+adjoint / level-set update with re-initialisation every 5, final imaging) of
+one synthetic clip per GPU. The default workload is the full-size one:
+a 2048^2 Manhattan metal-layer clip at 1 nm/px, K = 24 SOCS kernels of
+35 x 35, dose corners +/-2% (alpha = 1, beta = 7.5), dt = 0.5, lambda = 0.1,
+100 iterations. The metric is clips/s (whole job); clips are independent, so
+N GPUs solve N different clips with no collective ("scaling": "weak").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3]
+    python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, K, k, iters, beta, seed)
+    "manhattan2048": dict(n=2048, K=24, k=35, iters=100, beta=7.5, seed=1000),
+    "rect256": dict(n=256, K=8, k=15, iters=20, beta=0.0, seed=0),
+}
+METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def algorithmic_flops_per_iter(n, K, k):
+    """Real flops of the truncated-DFT method per clip per iteration, SOCS form
+    (forward A_j per kernel, adjoint projection per kernel, mask spectrum and
+    back-projection, small k x k stages)."""
+    return 16 * K * k * n * n + 8 * k * n * n + 16 * K * n * k * k + 16 * n * k * k
+
+
+def window_flops_per_iter(n, K, k):
+    """Real multiply-add flops this library issues per iteration through the
+    difference window (the four n^2-sized contractions dominate)."""
+    k2 = 2 * k - 1
+    big = 2 * n * n * (2 * k) + 2 * n * n * (2 * k2) + 2 * n * n * (2 * k2) + 2 * n * n * (2 * k)
+    small = 8 * n * k2 * k2 + 8 * n * k * k + 8 * K * k ** 4 * 2
+    return big + small
+
+
+# per-launch algorithmic cost of each kernel class: (kind, bytes_per_px or flops fn)
+def kernel_cost(name, n, K, k, launches_per_iter_shape=None):
+    px = n * n
+    k2 = 2 * k - 1
+    if name == "levelset_step":
+        return "hbm", 13 * px
+    if name == "resist":
+        return "hbm", 9 * px
+    if name == "edt_cols":
+        return "hbm", 5 * px
+    if name == "edt_rows":
+        return "hbm", 13 * px
+    if name in ("expand_gemm", "tc_expand"):
+        # half the launches expand W2 (forward), half W (adjoint)
+        return "flops", 2 * px * (2 * k2 + 2 * k) / 2
+    if name in ("spectrum_partial", "tc_spectrum"):
+        return "flops", 2 * px * (2 * k + 2 * k2) / 2
+    return None, None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def simt_fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak of the CUDA cores: 152 SMs x 128 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------
+# the reference arm: the FP64 CPU oracle on a bounded sample
+# --------------------------------------------------------------------------
+def oracle_sample(wl, budget_s=30.0):
+    """Time the oracle on a bounded sample of one clip's solve and scale it to
+    clips/s: one full-size DSO iteration (image, loss, gradient, step) plus a
+    re-initialisation measured on a row sample and amortised over 5 iterations."""
+    from oracle import levelset, litho, resist, sdf
+    n, K, k, iters, beta = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"]
+    o = synth.optics(n, K, k)
+    Zt = synth.manhattan_clip(wl["seed"]) if n == 2048 else synth.rect_clip(wl["seed"], n=n)
+    t0 = time.perf_counter()
+    rows = np.arange(0, n, max(1, n // 64))
+    sdf.tsdf(Zt, rows=rows)
+    t_reinit = (time.perf_counter() - t0) * n / len(rows)
+    phi = np.where(Zt > 0, -0.5, 0.5)
+    t0 = time.perf_counter()
+    M = levelset.mask_from_phi(phi)
+    I = litho.aerial(M, o.H, o.w)
+    res = resist.resist(I, Zt, resist.ResistParams(beta=beta))
+    V = litho.aerial_gradient(M, res.R, o.H, o.w)
+    levelset.step(phi, V, float(np.abs(V).max()), None, 0.5, 0.1)
+    t_iter = time.perf_counter() - t0
+    per_clip = iters * t_iter + (iters / 5 + 1) * t_reinit + t_iter * 0.1
+    sample = (f"one {n}^2 DSO iteration (K={K}, k={k}) timed in full ({t_iter:.1f} s) plus a TSDF on "
+              f"{len(rows)} of {n} rows ({t_reinit * len(rows) / n:.1f} s, scaled to {t_reinit:.1f} s); "
+              f"clip = {iters} iterations + {iters // 5 + 1} re-initialisations")
+    return 1.0 / per_clip, per_clip, sample
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    vals = []
+    sample = ""
+    for _ in range(max(1, args.steps)):
+        v, per_clip, sample = oracle_sample(wl)
+        vals.append(v)
+        if time.perf_counter() - t0 > 150:
+            break
+    value = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "clips/s", "n_gpus": args.gpus,
+           "steps": len(vals), "warmup": 0, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, **{k: wl[k] for k in ("n", "K", "k", "iters", "beta")}},
+           "cpu_baseline": {"value": value, "unit": "clips/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "clips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, wl):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    n, K, k, iters, beta = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"]
+    prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3}[args.precision]
+    o = synth.optics(n, K, k)
+    seed = wl["seed"] + rank
+    Zt = synth.manhattan_clip(seed) if n == 2048 else synth.rect_clip(seed, n=n)
+    opt = dv.devel_optics_create(n, o.H, o.w, prec)
+    target = torch.from_numpy(Zt.ravel().copy()).to(dev)
+    phi = torch.empty(n * n, dtype=torch.float32, device=dev)
+    M = torch.empty(n * n, dtype=torch.uint8, device=dev)
+    L = torch.zeros(iters + 1, dtype=torch.float64, device=dev)
+    l2 = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
+    pvb = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
+    clip = dv.Clip(opt, target, phi, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        dv.devel_ilt_solve(params, [clip], st, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(st.item()) != 0:
+        raise RuntimeError(f"solver status {int(st.item())}")
+
+    # timed region: K solves, L2 flushed between them, per-kernel events on
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    dv.devel_profile_start(1 << 20)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = dv.devel_profile_stop()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms  # clips/s, one clip per GPU per step
+
+    # end to end through the public API with host buffers
+    tgt_host = torch.from_numpy(Zt.ravel().copy()).pin_memory()
+    mask_host = torch.empty(n * n, dtype=torch.uint8).pin_memory()
+    hist_host = torch.empty(iters + 1, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        target.copy_(tgt_host, non_blocking=True)
+        step()
+        mask_host.copy_(M, non_blocking=True)
+        hist_host.copy_(L, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+    e2e_t = torch.tensor([float(np.median(e2e_ms))], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * 1000.0 / float(e2e_t.item())
+
+    if rank == 0:
+        hbm, bf16, src = measured_peaks()
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        # dominant kernel class by summed device time
+        tot = sum(v[1] for v in prof.values())
+        dom = max(prof.items(), key=lambda kv: kv[1][1])
+        name, (cnt, kms) = dom
+        kind, cost = kernel_cost(name, n, K, k)
+        avg_s = kms / cnt / 1000.0
+        if kind == "hbm":
+            ach = cost / avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": src}
+        elif kind == "flops":
+            ach = cost / avg_s / 1e12
+            if name.startswith("tc_"):
+                roof = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                        "frac": ach / bf16, "peak_source": src}
+            else:
+                pk = simt_fp32_peak_tflops(sm_mhz)
+                roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                        "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+        else:
+            roof = {"bound": None}
+        roof.update({"kernel": name, "launches_per_step": cnt / args.steps, "avg_launch_us": avg_s * 1e6,
+                     "share": kms / tot, "traffic": None})
+        kernels = {kn: {"launches": c, "ms": round(t, 3), "share": round(t / tot, 4)} for kn, (c, t) in
+                   sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        if args.no_cpu_baseline:
+            cpu = None
+        else:
+            v, per_clip, sample = oracle_sample(wl)
+            cpu = {"value": v, "unit": "clips/s", "cores": 1, "kind": "oracle", "sample": sample}
+        out = {
+            "metric": METRIC, "value": value, "unit": "clips/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "K": K, "k": k, "iters": iters, "beta": beta,
+                       "dt": 0.5, "lambda": 0.1, "reinit_every": 5, "clips_per_gpu_per_step": 1,
+                       "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "litho_tflops": {"window_method": window_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12,
+                             "socs_equivalent": algorithmic_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12},
+            "e2e": {"value": e2e_value, "unit": "clips/s", "h2d_bytes_per_step": n * n,
+                    "d2h_bytes_per_step": n * n + 8 * (iters + 1)},
+            "gpu_launches": int(sum(c for c, _ in prof.values())),
+            "roofline": roof,
+            "kernels": kernels,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "final_l2": int(l2[-1].item()), "final_pvb": int(pvb[-1].item()),
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="manhattan2048")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * develset.h -- C ABI of the GB300 level-set inverse-lithography (ILT) library.
+ *
+ * The library runs the per-iteration hot path of the DevelSet-Optimizer
+ * (DSO) loop of "DevelSet: Deep Neural Level Set for Instant Mask
+ * Optimization" (Chen et al., arXiv 2303.12529) as CUDA kernels for sm_103a:
+ *
+ *   devel_reinit_sdf      Eqs. (sdf), (tsdf), Alg. 1 CUDA_TSDF     TSDF of a mask
+ *   devel_litho_forward   Sec. II-B SOCS imaging                   I = sum_j w_j |M (*) h_j|^2
+ *   devel_resist_loss     Sec. III-A sigmoid resist, L_ilt, L_pvb; Sec. II-C L2, PVBand
+ *   devel_litho_adjoint   Eqs. (ilt_gradient), (pvb_gradient), (vel)  dL/dM from dL/dI
+ *   devel_levelset_step   Eqs. (dso_evolution), (numerical-settings), (curva_numer), (phi2mask)
+ *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Images are n x n, row-major, index p = y * n + x (y = row, x = column).
+ *   Lithography is periodic (circular convolution on the n x n torus).
+ * - Optical kernel j is given by its spectrum on a k x k window centred on
+ *   DC (k odd, r = (k-1)/2): H[j][a][b] is the value at frequency
+ *   (u, v) = (a - r, b - r) cycles per n pixels, u along rows (y), v along
+ *   columns (x). The spatial kernel is h_j = IDFT_n(zero-padded H_j), with
+ *   the 1/n^2 on the inverse. Complex values are interleaved (re, im) float.
+ * - Pointers are DEVICE pointers owned by the caller unless marked "host".
+ *   Device arrays must be 16-byte aligned (any cudaMalloc / PyTorch
+ *   allocation is). Nothing is allocated after devel_optics_create.
+ * - Every call enqueues work on `stream` and returns without waiting, so
+ *   CUDA errors from the kernels themselves surface at the caller's next
+ *   synchronisation. Calls that share one devel_optics handle must not run
+ *   concurrently (the handle holds the per-iteration workspace).
+ * - Return value: DEVEL_OK, or a negative code; devel_last_error() then
+ *   returns a thread-local message naming the argument or the CUDA error.
+ *   Argument checks happen before any work is enqueued.
+ */
+#ifndef DEVELSET_H
+#define DEVELSET_H
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DEVEL_OK 0
+#define DEVEL_EINVAL (-1)   /* bad size, null or misaligned pointer, bad option */
+#define DEVEL_ECUDA (-2)    /* a CUDA runtime call or kernel launch failed       */
+#define DEVEL_ENOMEM (-3)   /* devel_optics_create could not allocate            */
+#define DEVEL_ETIMEOUT (-4) /* a bounded device-side wait gave up                */
+#define DEVEL_ENAN (-5)     /* a non-finite loss or velocity maximum was found   */
+
+/* Arithmetic of the truncated-DFT contractions (forward and adjoint). */
+#define DEVEL_PREC_FP32 0   /* FP32 FMA on the CUDA cores                         */
+#define DEVEL_PREC_BF16X3 1 /* tcgen05 BF16 hi+lo split, 3 products, FP32 accumulate */
+
+/* Thread-local text of the last error returned on this thread ("" if none). */
+const char* devel_last_error(void);
+
+/* ABI version: (major << 16) | minor. */
+int devel_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Optics handle                                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct devel_optics devel_optics;
+
+/*
+ * Create the imaging model for n x n clips: K SOCS kernels (Sec. II-B; the
+ * paper uses N_k = 24) on a k x k window.
+ *   H_host  host, float[K][k][k][2]: kernel spectra (see conventions)
+ *   w_host  host, float[K]: SOCS weights sigma_j >= 0
+ *   precision DEVEL_PREC_FP32 or DEVEL_PREC_BF16X3
+ * Requires 16 <= n <= 8192, k odd, 3 <= k, 2k - 1 <= n, 1 <= K <= k*k.
+ * Copies everything it needs to the device ("loaded and pinned in GPU memory
+ * throughout the optimization", Sec. III-A) and allocates the workspace of
+ * devel_litho_* and devel_ilt_solve for this n (about 21 bytes per pixel plus
+ * O(n k) tables). *out receives the handle; on error *out is left NULL.
+ * Returns DEVEL_EINVAL, DEVEL_ENOMEM or DEVEL_ECUDA on failure.
+ */
+int devel_optics_create(int n, int K, int k, const float* H_host, const float* w_host,
+                        int precision, devel_optics** out);
+
+/* Wait for the device, then free the handle and its device memory. NULL is a no-op. */
+int devel_optics_destroy(devel_optics* optics);
+
+/* n of the handle (or -1 for NULL). */
+int devel_optics_n(const devel_optics* optics);
+
+/* ------------------------------------------------------------------------ */
+/* Lithography                                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Aerial image of a real mask (Sec. II-B):
+ *   I(p) = sum_j w_j |A_j(p)|^2,  A_j = mask (*) h_j  (circular).
+ *   mask       device float[n*n], any real values (the solver passes 0/1)
+ *   intensity  device float[n*n], written
+ * The mask may not alias intensity.
+ */
+int devel_litho_forward(const devel_optics* optics, const float* mask, float* intensity,
+                        cudaStream_t stream);
+
+/* Resist and loss parameters, Sec. III-A and IV (sigma_z = 50, alpha = 1, beta = 7.5). */
+typedef struct {
+    float sigma_z;   /* sigmoid steepness                                    */
+    float I_th;      /* print threshold                                      */
+    float alpha;     /* weight of L_ilt (nominal condition)                  */
+    float beta;      /* weight of L_pvb (inner + outer corners)              */
+    float dose_in;   /* inner-corner dose, image scales by dose_in^2 (0.98)  */
+    float dose_out;  /* outer-corner dose, image scales by dose_out^2 (1.02) */
+} devel_resist_params;
+
+/*
+ * Sigmoid resist Z_c = 1/(1+exp(-sigma_z (d_c^2 I - I_th))) at the three
+ * conditions c = nominal (d=1), inner, outer, and
+ *   L    = alpha sum (Z_nom - Z_t)^2 + beta [sum (Z_in - Z_t)^2 + sum (Z_out - Z_t)^2]
+ *   dLdI = sum_c coef_c 2 (Z_c - Z_t) sigma_z Z_c (1 - Z_c) d_c^2
+ *   L2   = #{[I >= I_th] != Z_t},  PVB = #{[d_in^2 I >= I_th] xor [d_out^2 I >= I_th]}
+ *   intensity  device float[n*n]
+ *   target     device uint8[n*n], 0/1
+ *   params     host
+ *   dLdI       device float[n*n], written (may alias intensity)
+ *   loss_out   device double[4]: {L, sum (Z_nom-Z_t)^2, sum (Z_in-Z_t)^2, sum (Z_out-Z_t)^2}
+ *   counts_out device long long[2]: {L2, PVB}
+ * n is the handle's; its workspace holds the reduction partials. The sums
+ * are FP64 and reproducible (fixed reduction order).
+ */
+int devel_resist_loss(const devel_optics* optics, const float* intensity, const unsigned char* target,
+                      const devel_resist_params* params, float* dLdI, double* loss_out,
+                      long long* counts_out, cudaStream_t stream);
+
+/*
+ * Gradient of a loss L(I) with respect to the mask, given R = dL/dI
+ * (Eq. ilt_gradient with the weights and the sum over kernels written out):
+ *   dLdM(q) = sum_j 2 w_j Re sum_p R(p) conj(A_j(p)) h_j(p - q)
+ *   mask   device float[n*n] (the mask the forward image was taken of)
+ *   dLdI   device float[n*n]
+ *   dLdM   device float[n*n], written
+ *   vmax   device double[1], written with max_q |dLdM(q)|
+ */
+int devel_litho_adjoint(const devel_optics* optics, const float* mask, const float* dLdI,
+                        float* dLdM, double* vmax, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Level set                                                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One explicit level-set update, Eq. (dso_evolution) with the descent sign
+ * (the velocity is V = +dL/dM), central differences of Eq.
+ * (numerical-settings), curvature term of Eq. (curva_numer):
+ *   F        = -dt V / vmax                 (transport skipped if vmax == 0)
+ *   phi_out  = phi - [max(F,0) |grad phi|^+ + min(F,0) |grad phi|^-]
+ *                  + dt lambda m Kc
+ *   Kc       = (phi_xx phi_y^2 - 2 phi_x phi_y phi_xy + phi_yy phi_x^2)/(phi_x^2 + phi_y^2)
+ *              (0 where phi_x^2 + phi_y^2 < 1e-12)
+ *   mask_out = [phi_out <= 0]                                   Eq. (phi2mask)
+ * |grad phi|^+- are Godunov's first-order upwind magnitudes; borders
+ * replicate the edge pixel.
+ *   phi      device float[n*n]         V      device float[n*n]
+ *   vmax     device double[1]          m      device float[n*n] or NULL (m = 1)
+ *   phi_out  device float[n*n], must not alias phi
+ *   mask_out device uint8[n*n] or NULL
+ */
+int devel_levelset_step(int n, const float* phi, const float* V, const double* vmax,
+                        const float* m, float dt, float lambda, float* phi_out,
+                        unsigned char* mask_out, cudaStream_t stream);
+
+/*
+ * Truncated signed distance of a mask, Eqs. (sdf), (tsdf) (Alg. 1 CUDA_TSDF):
+ *   phi = +(sqrt(d2) - 1/2)  outside (mask == 0),
+ *   phi = -(sqrt(d2) - 1/2)  inside  (mask != 0),
+ * clamped to [d_lo, d_hi] (the paper: D_l = -100, D_u = 900), where d2 is
+ * the exact squared Euclidean distance between pixel centres to the nearest
+ * pixel of the other class. [phi <= 0] reproduces the mask.
+ *   mask   device uint8[n*n] (0 = outside, nonzero = inside)
+ *   phi    device float[n*n], written
+ *   d2     device int[n*n], scratch; on return d2[p] is the exact integer
+ *          squared distance of p to the other class, or -1 if that class is empty
+ * Requires 1 <= n <= 16384 and d_lo <= d_hi.
+ */
+int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo,
+                     float d_hi, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Whole loop                                                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    devel_resist_params resist;
+    float dt;            /* CFL number eta: the front moves at most dt px per iteration */
+    float lambda;        /* curvature weight                                              */
+    float d_lo, d_hi;    /* TSDF clamp, Eq. (tsdf)                                        */
+    int iters;           /* iterations T                                                  */
+    int reinit_every;    /* re-initialise after iteration i when (i+1) % reinit_every == 0 (0 = never) */
+    int start_iter;      /* global index of the first iteration (resume)                  */
+} devel_ilt_params;
+
+typedef struct {
+    const devel_optics* optics;    /* imaging model; fixes n                              */
+    const unsigned char* target;   /* device uint8[n*n], Z_t                              */
+    float* phi;                    /* device float[n*n]: in = phi_0 if phi_given, out = phi_T */
+    int phi_given;                 /* 0: phi_0 = TSDF(target) (the paper's start, Sec. III-A) */
+    const float* m;                /* device float[n*n] curvature modulation m_theta, or NULL */
+    unsigned char* mask_out;       /* device uint8[n*n] or NULL: [phi_T <= 0]            */
+    double* loss_hist;             /* device double[iters+1] or NULL: L of the mask imaged
+                                      by iteration i; entry iters is the final mask's    */
+    long long* l2_hist;            /* device long long[iters+1] or NULL                  */
+    long long* pvb_hist;           /* device long long[iters+1] or NULL                  */
+} devel_clip;
+
+/*
+ * Run `params->iters` DSO iterations on each clip (host array of nclips):
+ * image, resist loss, adjoint velocity, level-set step, periodic TSDF
+ * re-initialisation, all on `stream`, nothing copied to the host.
+ *   status_dev  device int[1]: set to 0, then to DEVEL_ENAN by the device if a
+ *               loss or max|V| is not finite (read it after synchronising).
+ * Clips may have different n; each clip's handle must not be used by any
+ * other concurrent call.
+ */
+int devel_ilt_solve(const devel_ilt_params* params, int nclips, const devel_clip* clips,
+                    int* status_dev, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Optional kernel timing (tracing)                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Open a profile: until devel_profile_stop, every kernel launch of the
+ * library is bracketed by two CUDA events on its stream (at most `capacity`
+ * launches; events are created here, on the host, not on the hot path).
+ * Not for use during stream capture. One profile at a time per process.
+ */
+int devel_profile_start(int capacity);
+/* Close the profile, wait for its events and accumulate per-kernel times. */
+int devel_profile_stop(void);
+/* Number of kernel classes. */
+int devel_profile_kinds(void);
+/* Name, launch count and summed device time (ms) of kernel class `kind`
+ * in the last closed profile. */
+int devel_profile_query(int kind, const char** name, int* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEVELSET_H */

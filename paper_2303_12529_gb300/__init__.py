@@ -1,0 +1,272 @@
+"""Python binding of libdevelset, the GB300 level-set ILT library.
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name in ``libdevelset.so`` (declared in ``include/develset.h``);
+PyTorch supplies device memory and the current CUDA stream. There is no
+fallback: if the library is not built, importing this package fails.
+
+Build it with ``python paper_2303_12529_gb300/build.py`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdevelset.so")
+
+DEVEL_OK = 0
+DEVEL_EINVAL = -1
+DEVEL_ECUDA = -2
+DEVEL_ENOMEM = -3
+DEVEL_ETIMEOUT = -4
+DEVEL_ENAN = -5
+DEVEL_PREC_FP32 = 0
+DEVEL_PREC_BF16X3 = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is not built; run `python paper_2303_12529_gb300/build.py` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+
+
+class DevelError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class devel_resist_params(ctypes.Structure):
+    _fields_ = [("sigma_z", _F), ("I_th", _F), ("alpha", _F), ("beta", _F),
+                ("dose_in", _F), ("dose_out", _F)]
+
+
+class devel_ilt_params(ctypes.Structure):
+    _fields_ = [("resist", devel_resist_params), ("dt", _F), ("lambda_", _F), ("d_lo", _F),
+                ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I)]
+
+
+class devel_clip(ctypes.Structure):
+    _fields_ = [("optics", _P), ("target", _P), ("phi", _P), ("phi_given", _I), ("m", _P),
+                ("mask_out", _P), ("loss_hist", _P), ("l2_hist", _P), ("pvb_hist", _P)]
+
+
+def _sig(name, argtypes, restype=_I):
+    f = getattr(_lib, name)
+    f.argtypes = argtypes
+    f.restype = restype
+    return f
+
+
+_lib.devel_last_error.restype = ctypes.c_char_p
+_lib.devel_last_error.argtypes = []
+_sig("devel_version", [])
+_sig("devel_optics_create", [_I, _I, _I, _P, _P, _I, ctypes.POINTER(_P)])
+_sig("devel_optics_destroy", [_P])
+_sig("devel_optics_n", [_P])
+_sig("devel_litho_forward", [_P, _P, _P, _P])
+_sig("devel_resist_loss", [_P, _P, _P, ctypes.POINTER(devel_resist_params), _P, _P, _P, _P])
+_sig("devel_litho_adjoint", [_P, _P, _P, _P, _P, _P])
+_sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
+_sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
+_sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
+
+_sig("devel_profile_start", [_I])
+_sig("devel_profile_stop", [])
+_sig("devel_profile_kinds", [])
+_sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
+                             ctypes.POINTER(ctypes.c_double)])
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_optics_destroy",
+            "devel_optics_n", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
+            "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
+            "devel_profile_stop", "devel_profile_kinds", "devel_profile_query")
+
+
+def _check(rc: int):
+    if rc != DEVEL_OK:
+        raise DevelError(rc, _lib.devel_last_error().decode(errors="replace"))
+
+
+def devel_last_error() -> str:
+    return _lib.devel_last_error().decode(errors="replace")
+
+
+def devel_version() -> int:
+    return _lib.devel_version()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Optics:
+    """Owner of a ``devel_optics*`` handle (destroyed with the object)."""
+
+    def __init__(self, handle: int, n: int, K: int, k: int, precision: int):
+        self.handle = handle
+        self.n, self.K, self.k, self.precision = n, K, k, precision
+
+    def close(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(_lib.devel_optics_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def devel_optics_create(n: int, H: np.ndarray, w: np.ndarray, precision: int = DEVEL_PREC_FP32) -> Optics:
+    """H: complex [K, k, k] kernel spectra on the centred window; w: [K] weights."""
+    H = np.asarray(H)
+    K, k, k2 = H.shape
+    if k != k2:
+        raise ValueError("H must be [K, k, k]")
+    Hf = np.ascontiguousarray(np.stack([H.real, H.imag], axis=-1), dtype=np.float32)
+    wf = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    if wf.shape != (K,):
+        raise ValueError("w must be [K]")
+    out = _P()
+    _check(_lib.devel_optics_create(n, K, k, Hf.ctypes.data, wf.ctypes.data, precision, ctypes.byref(out)))
+    return Optics(out.value, n, K, k, precision)
+
+
+def devel_optics_destroy(optics: Optics):
+    optics.close()
+
+
+def devel_litho_forward(optics: Optics, mask, intensity, stream=None):
+    import torch
+    N = optics.n * optics.n
+    _check(_lib.devel_litho_forward(optics.handle, _ptr(mask, torch.float32, N, "mask"),
+                                    _ptr(intensity, torch.float32, N, "intensity"), _stream(stream)))
+
+
+def resist_params(sigma_z=50.0, I_th=0.225, alpha=1.0, beta=0.0, dose_in=0.98, dose_out=1.02):
+    return devel_resist_params(sigma_z, I_th, alpha, beta, dose_in, dose_out)
+
+
+def devel_resist_loss(optics: Optics, intensity, target, params: devel_resist_params, dLdI,
+                      loss_out, counts_out, stream=None):
+    import torch
+    N = optics.n * optics.n
+    _check(_lib.devel_resist_loss(optics.handle, _ptr(intensity, torch.float32, N, "intensity"),
+                                  _ptr(target, torch.uint8, N, "target"), ctypes.byref(params),
+                                  _ptr(dLdI, torch.float32, N, "dLdI"),
+                                  _ptr(loss_out, torch.float64, 4, "loss_out"),
+                                  _ptr(counts_out, torch.int64, 2, "counts_out"), _stream(stream)))
+
+
+def devel_litho_adjoint(optics: Optics, mask, dLdI, dLdM, vmax, stream=None):
+    import torch
+    N = optics.n * optics.n
+    _check(_lib.devel_litho_adjoint(optics.handle, _ptr(mask, torch.float32, N, "mask"),
+                                    _ptr(dLdI, torch.float32, N, "dLdI"),
+                                    _ptr(dLdM, torch.float32, N, "dLdM"),
+                                    _ptr(vmax, torch.float64, 1, "vmax"), _stream(stream)))
+
+
+def devel_levelset_step(n: int, phi, V, vmax, m, dt: float, lam: float, phi_out, mask_out,
+                        stream=None):
+    import torch
+    N = n * n
+    _check(_lib.devel_levelset_step(n, _ptr(phi, torch.float32, N, "phi"),
+                                    _ptr(V, torch.float32, N, "V"),
+                                    _ptr(vmax, torch.float64, 1, "vmax"),
+                                    _ptr(m, torch.float32, N, "m"), dt, lam,
+                                    _ptr(phi_out, torch.float32, N, "phi_out"),
+                                    _ptr(mask_out, torch.uint8, N, "mask_out"), _stream(stream)))
+
+
+def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):
+    import torch
+    N = n * n
+    _check(_lib.devel_reinit_sdf(n, _ptr(mask, torch.uint8, N, "mask"), _ptr(phi, torch.float32, N, "phi"),
+                                 _ptr(d2, torch.int32, N, "d2"), d_lo, d_hi, _stream(stream)))
+
+
+def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,
+               reinit_every=5, start_iter=0) -> devel_ilt_params:
+    return devel_ilt_params(resist if resist is not None else resist_params(), dt, lam, d_lo, d_hi,
+                            iters, reinit_every, start_iter)
+
+
+@dataclass
+class Clip:
+    """One clip of a devel_ilt_solve call (tensors stay owned by the caller)."""
+    optics: Optics
+    target: object           # uint8 [n*n]
+    phi: object              # float32 [n*n], in/out
+    phi_given: bool = False
+    m: object = None         # float32 [n*n] or None
+    mask_out: object = None  # uint8 [n*n] or None
+    loss_hist: object = None  # float64 [iters+1] or None
+    l2_hist: object = None   # int64 [iters+1] or None
+    pvb_hist: object = None  # int64 [iters+1] or None
+
+
+def devel_ilt_solve(params: devel_ilt_params, clips, status, stream=None):
+    import torch
+    arr = (devel_clip * len(clips))()
+    H = params.iters + 1
+    for i, c in enumerate(clips):
+        N = c.optics.n * c.optics.n
+        arr[i] = devel_clip(c.optics.handle, _ptr(c.target, torch.uint8, N, "target"),
+                            _ptr(c.phi, torch.float32, N, "phi"), int(bool(c.phi_given)),
+                            _ptr(c.m, torch.float32, N, "m"), _ptr(c.mask_out, torch.uint8, N, "mask_out"),
+                            _ptr(c.loss_hist, torch.float64, H, "loss_hist"),
+                            _ptr(c.l2_hist, torch.int64, H, "l2_hist"),
+                            _ptr(c.pvb_hist, torch.int64, H, "pvb_hist"))
+    _check(_lib.devel_ilt_solve(ctypes.byref(params), len(clips), arr, _ptr(status, torch.int32, 1, "status"),
+                                _stream(stream)))
+
+
+def devel_profile_start(capacity: int = 1 << 16):
+    _check(_lib.devel_profile_start(capacity))
+
+
+def devel_profile_stop() -> dict:
+    """Close the profile; returns {kernel: (launches, total_ms)} for kernels that ran."""
+    _check(_lib.devel_profile_stop())
+    out = {}
+    for k in range(_lib.devel_profile_kinds()):
+        name = ctypes.c_char_p()
+        cnt = _I()
+        ms = ctypes.c_double()
+        _check(_lib.devel_profile_query(k, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)))
+        if cnt.value:
+            out[name.value.decode()] = (cnt.value, ms.value)
+    return out

@@ -1,0 +1,336 @@
+// C ABI of libdevelset: argument checks, the optics handle, and the
+// forward / adjoint / solve sequences built from the kernels of the other
+// translation units.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace devel {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+    return set_error(DEVEL_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int expand_parts(int n);
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+#define CHECK_PTR(p, name)                                                             \
+    do {                                                                               \
+        if (!(p)) return set_error(DEVEL_EINVAL, "%s: %s is NULL", __func__, name);    \
+        if (!aligned16(p))                                                             \
+            return set_error(DEVEL_EINVAL, "%s: %s is not 16-byte aligned", __func__, name); \
+    } while (0)
+
+#define CHECK_OPT_PTR(p, name)                                                         \
+    do {                                                                               \
+        if ((p) && !aligned16(p))                                                      \
+            return set_error(DEVEL_EINVAL, "%s: %s is not 16-byte aligned", __func__, name); \
+    } while (0)
+
+// forward image from ws.mhat: Ihat on W2, then the expansion
+int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s) {
+    int rc = launch_socs_y(o, s);
+    if (rc) return rc;
+    rc = launch_hopkins(o, s);
+    if (rc) return rc;
+    return launch_expand(o, o->ws.Ihat, o->basisW2, o->k2, I, 1.0f, false, s);
+}
+
+// adjoint from ws.Y (filled by the forward pass of the same mask) and R
+int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
+                      cudaStream_t s) {
+    const float inv = 1.0f / ((float)o->n * (float)o->n);
+    int rc = launch_spectrum_f32(o, R, o->basisW2, o->k2, o->ws.rhat, inv, s);
+    if (rc) return rc;
+    rc = launch_adjoint_window(o, s);
+    if (rc) return rc;
+    rc = launch_expand(o, o->ws.Shat, o->basisW, o->k, V, 2.0f, true, s);
+    if (rc) return rc;
+    return launch_vmax_final(o, vmax, status, s);
+}
+
+static void free_optics(devel_optics* o) {
+    if (!o) return;
+    void* ptrs[] = {o->basisW, o->basisW2, o->Hp, o->ws.part, o->ws.mhat, o->ws.Y, o->ws.Ihat,
+                    o->ws.rhat, o->ws.Shat, o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart,
+                    o->ws.bufI, o->ws.bufV, o->ws.phi2, o->ws.M, o->ws.d2, o->ws.vmax,
+                    o->ws.loss4, o->ws.cnt2};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete o;
+}
+
+// cos / sin table of a centred window of side kw: rows 0..kw-1 cos, kw..2kw-1 sin,
+// angle 2 pi ((a - r) x mod n) / n reduced exactly in integers, evaluated in double.
+static std::vector<float> make_basis(int n, int kw) {
+    const int r = (kw - 1) / 2;
+    std::vector<float> t((size_t)2 * kw * n);
+    for (int a = 0; a < kw; ++a) {
+        const long long u = a - r;
+        for (int x = 0; x < n; ++x) {
+            long long m = (u * x) % n;
+            if (m < 0) m += n;
+            const double ang = 2.0 * M_PI * (double)m / (double)n;
+            t[(size_t)a * n + x] = (float)std::cos(ang);
+            t[(size_t)(kw + a) * n + x] = (float)std::sin(ang);
+        }
+    }
+    return t;
+}
+
+}  // namespace devel
+
+using namespace devel;
+
+extern "C" {
+
+const char* devel_last_error(void) { return g_err; }
+
+int devel_version(void) { return (1 << 16) | 0; }
+
+int devel_optics_n(const devel_optics* o) { return o ? o->n : -1; }
+
+int devel_optics_create(int n, int K, int k, const float* H_host, const float* w_host,
+                        int precision, devel_optics** out) {
+    if (!out) return set_error(DEVEL_EINVAL, "devel_optics_create: out is NULL");
+    *out = nullptr;
+    if (!H_host || !w_host) return set_error(DEVEL_EINVAL, "devel_optics_create: H_host/w_host is NULL");
+    if (n < 16 || n > 8192) return set_error(DEVEL_EINVAL, "devel_optics_create: n=%d outside [16, 8192]", n);
+    if (k < 3 || (k % 2) == 0 || k > kMaxWindow)
+        return set_error(DEVEL_EINVAL, "devel_optics_create: k=%d must be odd in [3, %d]", k, kMaxWindow);
+    if (2 * k - 1 > n) return set_error(DEVEL_EINVAL, "devel_optics_create: 2k-1=%d exceeds n=%d", 2 * k - 1, n);
+    if (K < 1 || K > k * k) return set_error(DEVEL_EINVAL, "devel_optics_create: K=%d outside [1, k*k]", K);
+    if (precision != DEVEL_PREC_FP32)
+        return set_error(DEVEL_EINVAL, "devel_optics_create: precision %d not available in this build", precision);
+    for (int j = 0; j < K; ++j)
+        if (!(w_host[j] >= 0.f) || !std::isfinite(w_host[j]))
+            return set_error(DEVEL_EINVAL, "devel_optics_create: w[%d] must be finite and >= 0", j);
+
+    devel_optics* o = new devel_optics();
+    o->n = n;
+    o->K = K;
+    o->k = k;
+    o->r = (k - 1) / 2;
+    o->k2 = 2 * k - 1;
+    o->r2 = k - 1;
+    o->precision = precision;
+    o->nblk_spec = (n + 15) / 16;
+    const size_t npix = (size_t)n * n;
+    const int kk = k * k, kk2 = o->k2 * o->k2;
+    const int nred = resist_parts(n);
+    o->npart_red = nred;
+
+#define ALLOC(ptr, bytes)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                              \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            free_optics(o);                                                                \
+            return set_error(DEVEL_ENOMEM, "devel_optics_create: cudaMalloc(%zu): %s",     \
+                             (size_t)(bytes), cudaGetErrorString(e_));                     \
+        }                                                                                  \
+    } while (0)
+
+    ALLOC(o->basisW, sizeof(float) * 2 * k * n);
+    ALLOC(o->basisW2, sizeof(float) * 2 * o->k2 * n);
+    ALLOC(o->Hp, sizeof(float2) * K * kk);
+    ALLOC(o->ws.part, sizeof(float2) * o->nblk_spec * kk2);
+    ALLOC(o->ws.mhat, sizeof(float2) * kk);
+    ALLOC(o->ws.Y, sizeof(float2) * K * kk);
+    ALLOC(o->ws.Ihat, sizeof(float2) * kk2);
+    ALLOC(o->ws.rhat, sizeof(float2) * kk2);
+    ALLOC(o->ws.Shat, sizeof(float2) * kk);
+    ALLOC(o->ws.Acat, sizeof(float) * n * 2 * o->k2);
+    ALLOC(o->ws.dpart, sizeof(double) * 3 * nred);
+    ALLOC(o->ws.lpart, sizeof(long long) * 2 * nred);
+    ALLOC(o->ws.vpart, sizeof(float) * expand_parts(n));
+    ALLOC(o->ws.bufI, sizeof(float) * npix);
+    ALLOC(o->ws.bufV, sizeof(float) * npix);
+    ALLOC(o->ws.phi2, sizeof(float) * npix);
+    ALLOC(o->ws.M, npix);
+    ALLOC(o->ws.d2, sizeof(int) * npix);
+    ALLOC(o->ws.vmax, sizeof(double));
+    ALLOC(o->ws.loss4, sizeof(double) * 4);
+    ALLOC(o->ws.cnt2, sizeof(long long) * 2);
+#undef ALLOC
+
+    std::vector<float> bw = make_basis(n, k), bw2 = make_basis(n, o->k2);
+    std::vector<float2> hp((size_t)K * kk);
+    for (int j = 0; j < K; ++j) {
+        const double sw = std::sqrt((double)w_host[j]);
+        for (int i = 0; i < kk; ++i) {
+            hp[(size_t)j * kk + i] = make_float2((float)(sw * H_host[((size_t)j * kk + i) * 2]),
+                                                 (float)(sw * H_host[((size_t)j * kk + i) * 2 + 1]));
+        }
+    }
+    cudaError_t e = cudaMemcpy(o->basisW, bw.data(), bw.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(o->basisW2, bw2.data(), bw2.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(o->Hp, hp.data(), hp.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_optics(o);
+        return cuda_error(e, "devel_optics_create: cudaMemcpy");
+    }
+    *out = o;
+    return DEVEL_OK;
+}
+
+int devel_optics_destroy(devel_optics* o) {
+    if (!o) return DEVEL_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_optics(o);
+    if (e != cudaSuccess) return cuda_error(e, "devel_optics_destroy: cudaDeviceSynchronize");
+    return DEVEL_OK;
+}
+
+int devel_litho_forward(const devel_optics* o, const float* mask, float* intensity, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_litho_forward: optics is NULL");
+    CHECK_PTR(mask, "mask");
+    CHECK_PTR(intensity, "intensity");
+    if ((const void*)mask == (const void*)intensity)
+        return set_error(DEVEL_EINVAL, "devel_litho_forward: mask aliases intensity");
+    const float inv = 1.0f / ((float)o->n * (float)o->n);
+    int rc = launch_spectrum_f32(o, mask, o->basisW, o->k, o->ws.mhat, inv, s);
+    if (rc) return rc;
+    return forward_from_mhat(o, intensity, s);
+}
+
+int devel_resist_loss(const devel_optics* o, const float* intensity, const unsigned char* target,
+                      const devel_resist_params* p, float* dLdI, double* loss_out,
+                      long long* counts_out, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_resist_loss: optics is NULL");
+    if (!p) return set_error(DEVEL_EINVAL, "devel_resist_loss: params is NULL");
+    CHECK_PTR(intensity, "intensity");
+    CHECK_PTR(target, "target");
+    CHECK_PTR(dLdI, "dLdI");
+    CHECK_PTR(loss_out, "loss_out");
+    CHECK_PTR(counts_out, "counts_out");
+    return launch_resist(o->n, intensity, target, *p, dLdI, o->ws.dpart, o->ws.lpart, o->npart_red,
+                         loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, s);
+}
+
+int devel_litho_adjoint(const devel_optics* o, const float* mask, const float* dLdI, float* dLdM,
+                        double* vmax, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_litho_adjoint: optics is NULL");
+    CHECK_PTR(mask, "mask");
+    CHECK_PTR(dLdI, "dLdI");
+    CHECK_PTR(dLdM, "dLdM");
+    CHECK_PTR(vmax, "vmax");
+    const float inv = 1.0f / ((float)o->n * (float)o->n);
+    int rc = launch_spectrum_f32(o, mask, o->basisW, o->k, o->ws.mhat, inv, s);
+    if (rc) return rc;
+    rc = launch_socs_y(o, s);  // Y_j = sqrt(w_j) H_j mhat
+    if (rc) return rc;
+    return adjoint_from_mhat(o, dLdI, dLdM, vmax, nullptr, s);
+}
+
+int devel_levelset_step(int n, const float* phi, const float* V, const double* vmax, const float* m,
+                        float dt, float lambda, float* phi_out, unsigned char* mask_out, cudaStream_t s) {
+    if (n < 1 || n > 16384) return set_error(DEVEL_EINVAL, "devel_levelset_step: n=%d outside [1, 16384]", n);
+    CHECK_PTR(phi, "phi");
+    CHECK_PTR(V, "V");
+    CHECK_PTR(vmax, "vmax");
+    CHECK_PTR(phi_out, "phi_out");
+    CHECK_OPT_PTR(m, "m");
+    CHECK_OPT_PTR(mask_out, "mask_out");
+    if (phi == phi_out) return set_error(DEVEL_EINVAL, "devel_levelset_step: phi_out aliases phi");
+    if (!std::isfinite(dt) || !std::isfinite(lambda))
+        return set_error(DEVEL_EINVAL, "devel_levelset_step: dt/lambda not finite");
+    return launch_levelset_step(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, s);
+}
+
+int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
+                     cudaStream_t s) {
+    if (n < 1 || n > 16384) return set_error(DEVEL_EINVAL, "devel_reinit_sdf: n=%d outside [1, 16384]", n);
+    CHECK_PTR(mask, "mask");
+    CHECK_PTR(phi, "phi");
+    CHECK_PTR(d2, "d2");
+    if (!(d_lo <= d_hi)) return set_error(DEVEL_EINVAL, "devel_reinit_sdf: d_lo > d_hi");
+    return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s);
+}
+
+int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
+                    cudaStream_t s) {
+    if (!p) return set_error(DEVEL_EINVAL, "devel_ilt_solve: params is NULL");
+    if (nclips < 0 || (nclips > 0 && !clips)) return set_error(DEVEL_EINVAL, "devel_ilt_solve: bad clip list");
+    CHECK_PTR(status, "status_dev");
+    if (p->iters < 0 || p->reinit_every < 0 || p->start_iter < 0)
+        return set_error(DEVEL_EINVAL, "devel_ilt_solve: negative iters/reinit_every/start_iter");
+    if (!(p->d_lo <= p->d_hi)) return set_error(DEVEL_EINVAL, "devel_ilt_solve: d_lo > d_hi");
+    for (int c = 0; c < nclips; ++c) {
+        const devel_clip& cl = clips[c];
+        if (!cl.optics) return set_error(DEVEL_EINVAL, "devel_ilt_solve: clip %d has no optics", c);
+        CHECK_PTR(cl.target, "clip.target");
+        CHECK_PTR(cl.phi, "clip.phi");
+        CHECK_OPT_PTR(cl.m, "clip.m");
+        CHECK_OPT_PTR(cl.mask_out, "clip.mask_out");
+        CHECK_OPT_PTR(cl.loss_hist, "clip.loss_hist");
+        CHECK_OPT_PTR(cl.l2_hist, "clip.l2_hist");
+        CHECK_OPT_PTR(cl.pvb_hist, "clip.pvb_hist");
+    }
+    DEVEL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    for (int c = 0; c < nclips; ++c) {
+        const devel_clip& cl = clips[c];
+        const devel_optics* o = cl.optics;
+        const int n = o->n;
+        const Workspace& w = o->ws;
+        const float inv = 1.0f / ((float)n * (float)n);
+        float* phi = cl.phi;
+        float* phi_alt = w.phi2;
+        int rc;
+        if (!cl.phi_given) {
+            rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
+            if (rc) return rc;
+        }
+        rc = launch_mask_from_phi(n, phi, w.M, s);
+        if (rc) return rc;
+        for (int t = 0; t <= p->iters; ++t) {
+            // image the current mask, resist loss and dL/dI (in place in bufI)
+            rc = launch_spectrum_u8(o, w.M, o->basisW, o->k, w.mhat, inv, s);
+            if (rc) return rc;
+            rc = forward_from_mhat(o, w.bufI, s);
+            if (rc) return rc;
+            rc = launch_resist(n, w.bufI, cl.target, p->resist, w.bufI, w.dpart, w.lpart, o->npart_red,
+                               nullptr, nullptr, cl.loss_hist ? cl.loss_hist + t : nullptr,
+                               cl.l2_hist ? cl.l2_hist + t : nullptr,
+                               cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
+            if (rc) return rc;
+            if (t == p->iters) break;  // the final mask is imaged for its metrics only
+            rc = adjoint_from_mhat(o, w.bufI, w.bufV, w.vmax, status, s);
+            if (rc) return rc;
+            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M, s);
+            if (rc) return rc;
+            float* tmp = phi;
+            phi = phi_alt;
+            phi_alt = tmp;
+            const int gi = p->start_iter + t;
+            if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
+                rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
+                if (rc) return rc;
+            }
+        }
+        if (phi != cl.phi)
+            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.phi, phi, sizeof(float) * n * n, cudaMemcpyDeviceToDevice, s));
+        if (cl.mask_out)
+            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.mask_out, w.M, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return DEVEL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA sources of libdevelset.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/develset.h"
+
+namespace devel {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message, see devel_last_error)
+// ---------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* where);
+
+#define DEVEL_CUDA_TRY(call)                                       \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::devel::cuda_error(_e, #call); \
+    } while (0)
+
+#define DEVEL_LAUNCH_CHECK(where)                                  \
+    do {                                                           \
+        cudaError_t _e = cudaGetLastError();                       \
+        if (_e != cudaSuccess) return ::devel::cuda_error(_e, where); \
+    } while (0)
+
+// kernel classes of the optional event profiler (prof.cu)
+enum ProfKind {
+    PK_SPECTRUM = 0, PK_SPECTRUM_REDUCE, PK_SOCS_Y, PK_HOPKINS, PK_ADJ_WINDOW,
+    PK_EXPAND_T, PK_EXPAND_GEMM, PK_VMAX, PK_RESIST, PK_RESIST_FINAL,
+    PK_STEP, PK_MASK, PK_EDT_COLS, PK_EDT_ROWS, PK_U8F32,
+    PK_TC_EXPAND, PK_TC_SPECTRUM, PROF_NKINDS
+};
+void prof_begin(int kind, cudaStream_t s);
+void prof_end(int kind, cudaStream_t s);
+
+// Device-side limit of the window side handled by the FP32 kernels.
+constexpr int kMaxWindow = 63;
+
+// ---------------------------------------------------------------------------
+// the imaging model and its workspace
+// ---------------------------------------------------------------------------
+struct Workspace {
+    float2* part = nullptr;    // [nblk_spec][k2*k2] spectrum partials
+    float2* mhat = nullptr;    // [k*k]   mask spectrum on W, scaled 1/n^2
+    float2* Y = nullptr;       // [K][k*k] sqrt(w_j) H_j * mhat
+    float2* Ihat = nullptr;    // [k2*k2] aerial-image spectrum on W2
+    float2* rhat = nullptr;    // [k2*k2] dL/dI spectrum on W2, scaled 1/n^2
+    float2* Shat = nullptr;    // [k*k]   adjoint spectrum on W
+    float* Acat = nullptr;     // [n][2*k2] expansion operand [Re T | -Im T]
+    double* dpart = nullptr;   // reduction partials, doubles
+    long long* lpart = nullptr;// reduction partials, counts
+    float* vpart = nullptr;    // per-block max |V|
+    // solver buffers
+    float* bufI = nullptr;     // [n*n] intensity, then dL/dI (in place)
+    float* bufV = nullptr;     // [n*n] dL/dM
+    float* phi2 = nullptr;     // [n*n] ping-pong level set
+    unsigned char* M = nullptr;// [n*n] mask
+    int* d2 = nullptr;         // [n*n] EDT scratch
+    double* vmax = nullptr;    // [1]
+    double* loss4 = nullptr;   // [4]
+    long long* cnt2 = nullptr; // [2]
+};
+
+}  // namespace devel
+
+struct devel_optics {
+    int n, K, k, r, k2, r2, precision;
+    int nblk_spec;            // row blocks of the spectrum reduction
+    int npart_red;            // size of the generic reduction partial arrays
+    float* basisW = nullptr;  // [2k][n]:  cos(2 pi (a-r) x / n) rows, then sin rows
+    float* basisW2 = nullptr; // [2k2][n]: same on the difference window W2 = W - W
+    float2* Hp = nullptr;     // [K][k*k]: sqrt(w_j) H_j
+    devel::Workspace ws;
+};
+
+namespace devel {
+
+// ---------------------------------------------------------------------------
+// launchers (litho.cu)
+// ---------------------------------------------------------------------------
+// spectrum on a window of side kw (basis [2kw][n]) of an n x n real image:
+// out[a][b] = scale * sum_p X(p) e^{-2 pi i ((a-r)y + (b-r)x)/n}
+int launch_spectrum_f32(const devel_optics* o, const float* X, const float* basis, int kw,
+                        float2* out, float scale, cudaStream_t s);
+int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const float* basis, int kw,
+                       float2* out, float scale, cudaStream_t s);
+// Y_j = sqrt(w_j) H_j mhat
+int launch_socs_y(const devel_optics* o, cudaStream_t s);
+// Ihat from Y (SOCS sum of autocorrelations on W2)
+int launch_hopkins(const devel_optics* o, cudaStream_t s);
+// Shat from mhat (via Y) and rhat
+int launch_adjoint_window(const devel_optics* o, cudaStream_t s);
+// out = Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} (times `mult`), optional max|out|
+int launch_expand(const devel_optics* o, const float2* Z, const float* basis, int kw, float* out,
+                  float mult, bool want_max, cudaStream_t s);
+int expand_parts(int n);
+int launch_vmax_final(const devel_optics* o, double* vmax, int* status, cudaStream_t s);
+
+// resist.cu
+int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
+                  float* R, double* dpart, long long* lpart, int nparts, double* loss4,
+                  long long* cnt2, double* loss_hist, long long* l2_hist, long long* pvb_hist,
+                  int* status, cudaStream_t s);
+int resist_parts(int n);
+
+// levelset.cu
+int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
+                         const float* m, float dt, float lambda, float* phi_out,
+                         unsigned char* mask_out, cudaStream_t s);
+int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s);
+int launch_u8_to_f32(int n, const unsigned char* M, float* out, cudaStream_t s);
+
+// reinit.cu
+int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
+                  cudaStream_t s);
+
+// forward / adjoint bodies shared by the ABI and the solver (api.cu)
+int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s);
+int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
+                      cudaStream_t s);
+
+}  // namespace devel

@@ -1,0 +1,106 @@
+// Optional per-kernel timing with CUDA events.
+//
+// When a profile is open (devel_profile_start), every kernel launch of the
+// library is bracketed by two events recorded on the launching stream; after
+// devel_profile_stop the host reads per-kernel launch counts and summed
+// device time. Off by default; when off the cost is one branch per launch.
+// Not for use inside stream capture.
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace devel {
+
+static const char* kNames[PROF_NKINDS] = {
+    "spectrum_partial", "spectrum_reduce", "socs_y",     "hopkins",   "adjoint_window",
+    "expand_T",         "expand_gemm",     "vmax_final", "resist",    "resist_final",
+    "levelset_step",    "mask_from_phi",   "edt_cols",   "edt_rows",  "u8_to_f32",
+    "tc_expand",        "tc_spectrum",
+};
+
+struct Slot {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+static bool g_on = false;
+static std::vector<Slot> g_pool;
+static size_t g_used = 0;
+static int g_open_kind = -1;
+static int g_launches[PROF_NKINDS];
+static double g_ms[PROF_NKINDS];
+static bool g_overflow = false;
+
+bool prof_on() { return g_on; }
+
+void prof_begin(int kind, cudaStream_t s) {
+    if (!g_on) return;
+    if (g_used >= g_pool.size()) {
+        g_overflow = true;
+        g_open_kind = -1;
+        return;
+    }
+    g_pool[g_used].kind = kind;
+    cudaEventRecord(g_pool[g_used].a, s);
+    g_open_kind = kind;
+}
+
+void prof_end(int kind, cudaStream_t s) {
+    if (!g_on || g_open_kind != kind) return;
+    cudaEventRecord(g_pool[g_used].b, s);
+    ++g_used;
+    g_open_kind = -1;
+}
+
+}  // namespace devel
+
+using namespace devel;
+
+extern "C" {
+
+int devel_profile_start(int capacity) {
+    if (capacity < 1 || capacity > (1 << 22))
+        return set_error(DEVEL_EINVAL, "devel_profile_start: capacity %d outside [1, 4194304]", capacity);
+    if (g_on) return set_error(DEVEL_EINVAL, "devel_profile_start: a profile is already open");
+    if ((int)g_pool.size() < capacity) {
+        for (size_t i = g_pool.size(); i < (size_t)capacity; ++i) {
+            Slot sl{0, nullptr, nullptr};
+            DEVEL_CUDA_TRY(cudaEventCreate(&sl.a));
+            DEVEL_CUDA_TRY(cudaEventCreate(&sl.b));
+            g_pool.push_back(sl);
+        }
+    }
+    g_used = 0;
+    g_overflow = false;
+    std::memset(g_launches, 0, sizeof(g_launches));
+    for (int i = 0; i < PROF_NKINDS; ++i) g_ms[i] = 0.0;
+    g_on = true;
+    return DEVEL_OK;
+}
+
+int devel_profile_stop(void) {
+    if (!g_on) return set_error(DEVEL_EINVAL, "devel_profile_stop: no profile open");
+    g_on = false;
+    for (size_t i = 0; i < g_used; ++i) {
+        DEVEL_CUDA_TRY(cudaEventSynchronize(g_pool[i].b));
+        float ms = 0.f;
+        DEVEL_CUDA_TRY(cudaEventElapsedTime(&ms, g_pool[i].a, g_pool[i].b));
+        g_launches[g_pool[i].kind] += 1;
+        g_ms[g_pool[i].kind] += ms;
+    }
+    if (g_overflow) return set_error(DEVEL_EINVAL, "devel_profile_stop: capacity exceeded, profile truncated");
+    return DEVEL_OK;
+}
+
+int devel_profile_kinds(void) { return PROF_NKINDS; }
+
+int devel_profile_query(int kind, const char** name, int* launches, double* total_ms) {
+    if (kind < 0 || kind >= PROF_NKINDS) return set_error(DEVEL_EINVAL, "devel_profile_query: bad kind %d", kind);
+    if (name) *name = kNames[kind];
+    if (launches) *launches = g_launches[kind];
+    if (total_ms) *total_ms = g_ms[kind];
+    return DEVEL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Re-initialisation of the level set to a truncated signed distance.
+//
+// Eqs. (sdf), (tsdf) and Alg. 1 (CUDA_TSDF). Instead of the paper's search
+// over all boundary pixels, the exact squared Euclidean distance is computed
+// separably (d2(y,x) = min_x' [(x - x')^2 + g(y,x')^2], g the distance along
+// the column):
+//
+//   k_edt_cols  one pass per column strip: g to the nearest pixel of each
+//               class along the column, both packed in one 32-bit word
+//               (two 16-bit distances, 0xFFFF = none);
+//   k_edt_rows  one block per row: the row of packed g in shared memory; each
+//               pixel searches outwards |dx| = 1, 2, ... while dx^2 is below
+//               its best candidate, so the work per pixel is its distance.
+//               Writes the exact d2 (or -1) over the packed words, and phi.
+//
+// Integer arithmetic throughout; sqrtf is IEEE round-to-nearest (no fast
+// math), so phi is the correctly rounded sqrt(d2) minus one half.
+#include <climits>
+
+#include "common.cuh"
+
+namespace devel {
+namespace {
+
+constexpr int kCW = 32;   // columns per block
+constexpr int kSeg = 32;  // segments per column
+constexpr unsigned kNone = 0xFFFFu;
+
+__global__ void __launch_bounds__(kCW * kSeg)
+k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g) {
+    __shared__ int lastv[2][kSeg][kCW];
+    __shared__ int firstv[2][kSeg][kCW];
+    const int cx = threadIdx.x, sg = threadIdx.y;
+    const int x = blockIdx.x * kCW + cx;
+    const int L = (n + kSeg - 1) / kSeg;
+    const int ys = min(n, sg * L), ye = min(n, ys + L);
+    int f0 = -1, f1 = -1, l0 = -1, l1 = -1;
+    if (x < n) {
+        for (int y = ys; y < ye; ++y) {
+            if (mask[(size_t)y * n + x]) {
+                if (f1 < 0) f1 = y;
+                l1 = y;
+            } else {
+                if (f0 < 0) f0 = y;
+                l0 = y;
+            }
+        }
+    }
+    firstv[0][sg][cx] = f0;
+    firstv[1][sg][cx] = f1;
+    lastv[0][sg][cx] = l0;
+    lastv[1][sg][cx] = l1;
+    __syncthreads();
+    if (x >= n) return;
+    int up0 = -1, up1 = -1, dn0 = -1, dn1 = -1;
+    for (int s = sg - 1; s >= 0 && (up0 < 0 || up1 < 0); --s) {
+        if (up0 < 0) up0 = lastv[0][s][cx];
+        if (up1 < 0) up1 = lastv[1][s][cx];
+    }
+    for (int s = sg + 1; s < kSeg && (dn0 < 0 || dn1 < 0); ++s) {
+        if (dn0 < 0) dn0 = firstv[0][s][cx];
+        if (dn1 < 0) dn1 = firstv[1][s][cx];
+    }
+    // downward sweep: distance to the nearest pixel of each class at or above
+    int p0 = up0, p1 = up1;
+    for (int y = ys; y < ye; ++y) {
+        if (mask[(size_t)y * n + x]) p1 = y; else p0 = y;
+        const unsigned d0 = p0 < 0 ? kNone : (unsigned)(y - p0);
+        const unsigned d1 = p1 < 0 ? kNone : (unsigned)(y - p1);
+        g[(size_t)y * n + x] = d0 | (d1 << 16);
+    }
+    // upward sweep: combine with the nearest at or below
+    int q0 = dn0, q1 = dn1;
+    for (int y = ye - 1; y >= ys; --y) {
+        if (mask[(size_t)y * n + x]) q1 = y; else q0 = y;
+        const unsigned w = g[(size_t)y * n + x];
+        unsigned d0 = w & 0xFFFFu, d1 = w >> 16;
+        if (q0 >= 0) d0 = min(d0, (unsigned)(q0 - y));
+        if (q1 >= 0) d1 = min(d1, (unsigned)(q1 - y));
+        g[(size_t)y * n + x] = d0 | (d1 << 16);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g,
+           float* __restrict__ phi, float d_lo, float d_hi) {
+    extern __shared__ unsigned row[];
+    const int y = blockIdx.x;
+    const size_t base = (size_t)y * n;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) row[x] = g[base + x];
+    __syncthreads();
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const bool inside = mask[base + x] != 0;
+        // an inside pixel looks for class 0 (low half), an outside one for class 1 (high half)
+        const int sh = inside ? 0 : 16;
+        int best = INT_MAX;
+        {
+            const unsigned gx = (row[x] >> sh) & 0xFFFFu;
+            if (gx != kNone) best = (int)(gx * gx);
+        }
+        for (int dx = 1; dx < n; ++dx) {
+            const int dx2 = dx * dx;
+            if (dx2 >= best) break;
+            const bool lo = x - dx >= 0, hi = x + dx < n;
+            if (!lo && !hi) break;
+            if (lo) {
+                const unsigned gv = (row[x - dx] >> sh) & 0xFFFFu;
+                if (gv != kNone) best = min(best, dx2 + (int)(gv * gv));
+            }
+            if (hi) {
+                const unsigned gv = (row[x + dx] >> sh) & 0xFFFFu;
+                if (gv != kNone) best = min(best, dx2 + (int)(gv * gv));
+            }
+        }
+        float v;
+        int d2;
+        if (best == INT_MAX) {
+            d2 = -1;
+            v = inside ? d_lo : d_hi;
+        } else {
+            d2 = best;
+            const float dist = sqrtf((float)best) - 0.5f;
+            v = inside ? -dist : dist;
+            v = fminf(fmaxf(v, d_lo), d_hi);
+        }
+        g[base + x] = (unsigned)d2;
+        phi[base + x] = v;
+    }
+}
+
+}  // namespace
+
+int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
+                  cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            16384 * 4));
+        attr = true;
+    }
+    prof_begin(PK_EDT_COLS, s);
+    k_edt_cols<<<(n + kCW - 1) / kCW, dim3(kCW, kSeg), 0, s>>>(mask, n, reinterpret_cast<unsigned*>(d2));
+    prof_end(PK_EDT_COLS, s);
+    DEVEL_LAUNCH_CHECK("k_edt_cols");
+    prof_begin(PK_EDT_ROWS, s);
+    k_edt_rows<<<n, 256, sizeof(unsigned) * n, s>>>(mask, n, reinterpret_cast<unsigned*>(d2), phi, d_lo, d_hi);
+    prof_end(PK_EDT_ROWS, s);
+    DEVEL_LAUNCH_CHECK("k_edt_rows");
+    return DEVEL_OK;
+}
+
+}  // namespace devel

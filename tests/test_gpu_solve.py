@@ -1,0 +1,55 @@
+"""GPU parity of devel_ilt_solve against the oracle's DSO loop (Sec. III-A,
+III-C): ILT results within 0.1% thresholded-pixel mismatch, L2 and PVB within
+1%, on the 256^2 rectangle workload (K = 8, k = 15, 20 iterations)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import solve
+from gpu_util import need_gpu, dev, host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(dv, Zt, o, iters, beta=0.0, phi0=None, start=0, reinit_every=5):
+    n = Zt.shape[0]
+    opt = dv.devel_optics_create(n, o.H, o.w)
+    phi = torch.zeros(n * n, dtype=torch.float32, device="cuda") if phi0 is None else dev(phi0.astype(np.float32))
+    M = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    L = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    l2 = torch.zeros(iters + 1, dtype=torch.int64, device="cuda")
+    pvb = torch.zeros(iters + 1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    p = dv.ilt_params(dv.resist_params(beta=beta), iters=iters, start_iter=start, reinit_every=reinit_every)
+    clip = dv.Clip(opt, dev(Zt), phi, phi_given=phi0 is not None, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb)
+    dv.devel_ilt_solve(p, [clip], st)
+    torch.cuda.synchronize()
+    assert int(host(st)[0]) == 0
+    return host(phi, n), host(M, n), host(L), host(l2), host(pvb)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_solve_matches_oracle_rect_workload(seed):
+    dv = need_gpu()
+    o = synth.optics(256, 8, 15)
+    Zt = synth.rect_clip(seed)
+    phi, M, L, l2, pvb = run_gpu(dv, Zt, o, 20)
+    ref = solve.ilt_solve(Zt, o.H, o.w, solve.SolveParams(iters=20))
+    mismatch = np.count_nonzero(M != ref.mask) / M.size
+    assert mismatch <= 1e-3, mismatch
+    assert abs(l2[-1] - ref.l2[-1]) <= 0.01 * max(ref.l2[-1], 1)
+    assert abs(pvb[-1] - ref.pvb[-1]) <= 0.01 * max(ref.pvb[-1], 100)
+    assert np.allclose(L[0], ref.loss[0], rtol=1e-5)
+
+
+def test_solve_resume_is_exact():
+    """A 4 + 3 split run is bit-identical to a 7-iteration run (reinit keyed on
+    the global iteration index)."""
+    dv = need_gpu()
+    o = synth.optics(128, 6, 11)
+    Zt = synth.rect_clip(7, n=128, border=8)
+    phiA, MA, LA, _, _ = run_gpu(dv, Zt, o, 7, reinit_every=3)
+    phi4, _, L4, _, _ = run_gpu(dv, Zt, o, 4, reinit_every=3)
+    phiB, MB, LB, _, _ = run_gpu(dv, Zt, o, 3, phi0=phi4, start=4, reinit_every=3)
+    assert np.array_equal(phiA, phiB) and np.array_equal(MA, MB)
+    assert np.array_equal(LA[:4], L4[:4]) and np.array_equal(LA[4:], LB)
