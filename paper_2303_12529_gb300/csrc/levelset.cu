@@ -38,7 +38,8 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
     float out = c;
     const double vm = *vmax;
     if (vm > 0.0) {
-        const float F = -dt * (float)((double)V[p] / vm);
+        // FP32 reciprocal: an FP64 division per pixel is slow on GB300
+        const float F = -dt * (V[p] * (1.0f / (float)vm));
         const float dmx = c - xm, dpx = xp - c, dmy = c - ym, dpy = yp - c;
         if (F > 0.f) {
             const float a = fmaxf(dmx, 0.f), b = fminf(dpx, 0.f), cc = fmaxf(dmy, 0.f), d = fminf(dpy, 0.f);

@@ -28,8 +28,10 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, size
          float* __restrict__ R, double* __restrict__ dpart, long long* __restrict__ lpart) {
     __shared__ double sd[4][kThreads / 32];
     __shared__ long long sl[2][kThreads / 32];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    long long l2 = 0, pvb = 0;
+    // per-thread partials in FP32 (a thread sums a handful of pixels), FP64 from
+    // the warp level up: GB300 issues few FP64 operations per clock
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    int l2 = 0, pvb = 0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
         const float Iv = I[i];
@@ -39,9 +41,9 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, size
         const float zi = sigmoidf(p.sigma_z * (Ii - p.I_th));
         const float zo = sigmoidf(p.sigma_z * (Io - p.I_th));
         const float en = zn - zt, ei = zi - zt, eo = zo - zt;
-        s0 += (double)en * en;
-        s1 += (double)ei * ei;
-        s2 += (double)eo * eo;
+        f0 = fmaf(en, en, f0);
+        f1 = fmaf(ei, ei, f1);
+        f2 = fmaf(eo, eo, f2);
         const float gn = p.alpha * 2.f * en * p.sigma_z * zn * (1.f - zn);
         const float gi = p.beta * 2.f * ei * p.sigma_z * zi * (1.f - zi) * p.d2in;
         const float go = p.beta * 2.f * eo * p.sigma_z * zo * (1.f - zo) * p.d2out;
@@ -50,6 +52,7 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, size
         l2 += (pn != (Zt[i] != 0));
         pvb += ((Ii >= p.I_th) != (Io >= p.I_th));
     }
+    double s0 = f0, s1 = f1, s2 = f2;
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_down_sync(0xffffffffu, s0, o);
         s1 += __shfl_down_sync(0xffffffffu, s1, o);
@@ -84,19 +87,49 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, size
     }
 }
 
-__global__ void k_resist_final(const double* __restrict__ dpart, const long long* __restrict__ lpart,
-                               int nparts, double alpha, double beta, double* loss4,
-                               long long* cnt2, double* loss_hist, long long* l2_hist,
-                               long long* pvb_hist, int* status) {
-    if (threadIdx.x != 0) return;
+// One block of 256 threads: thread t sums partials t, t+256, ... in order, then a
+// fixed shuffle tree; the result does not depend on timing.
+__global__ void __launch_bounds__(256)
+k_resist_final(const double* __restrict__ dpart, const long long* __restrict__ lpart,
+               int nparts, double alpha, double beta, double* loss4,
+               long long* cnt2, double* loss_hist, long long* l2_hist,
+               long long* pvb_hist, int* status) {
+    __shared__ double sd[3][8];
+    __shared__ long long sl[2][8];
     double a = 0, b = 0, c = 0;
     long long x = 0, y = 0;
-    for (int i = 0; i < nparts; ++i) {
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
         a += dpart[i * 3 + 0];
         b += dpart[i * 3 + 1];
         c += dpart[i * 3 + 2];
         x += lpart[i * 2 + 0];
         y += lpart[i * 2 + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sd[0][w] = a;
+        sd[1][w] = b;
+        sd[2][w] = c;
+        sl[0][w] = x;
+        sl[1][w] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = b = c = 0;
+    x = y = 0;
+    for (int i = 0; i < 8; ++i) {
+        a += sd[0][i];
+        b += sd[1][i];
+        c += sd[2][i];
+        x += sl[0][i];
+        y += sl[1][i];
     }
     const double L = alpha * a + beta * (b + c);
     if (loss4) {
@@ -141,7 +174,7 @@ int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_re
     prof_end(PK_RESIST, s);
     DEVEL_LAUNCH_CHECK("k_resist");
     prof_begin(PK_RESIST_FINAL, s);
-    k_resist_final<<<1, 32, 0, s>>>(dpart, lpart, nparts, (double)p.alpha, (double)p.beta, loss4,
+    k_resist_final<<<1, 256, 0, s>>>(dpart, lpart, nparts, (double)p.alpha, (double)p.beta, loss4,
                                     cnt2, loss_hist, l2_hist, pvb_hist, status);
     prof_end(PK_RESIST_FINAL, s);
     DEVEL_LAUNCH_CHECK("k_resist_final");
