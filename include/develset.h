@@ -181,6 +181,32 @@ int devel_levelset_step(int n, const float* phi, const float* V, const double* v
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo,
                      float d_hi, cudaStream_t stream);
 
+/*
+ * Allocation-free re-initialisation (the paper has no counterpart).
+ *
+ * Same result as devel_reinit_sdf (same kernels, bit-identical phi), for
+ * callers that cannot allocate device memory and so cannot supply the d2
+ * scratch: for example an embedder whose device memory is all owned by its
+ * own pool allocator, or a latency-critical loop that must not pay the
+ * device-wide synchronisation a cudaMalloc/cudaFree can cause. The n*n
+ * distance scratch lives instead in a static device array inside the library:
+ *   - n <= DEVEL_REINIT_STATIC_MAX_N (2048); larger n returns DEVEL_EINVAL.
+ *     The array (2048*2048 32-bit words, 16 MiB) is reserved on every GPU
+ *     that loads the library, until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls share the one array: calls whose kernels overlap on the GPU
+ *     (other streams, other threads) race on it; serialise them.
+ *   - The array keeps the last call's contents; a call writes every word it
+ *     reads before reading it, so nothing needs clearing.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   mask  device uint8[n*n]      phi  device float[n*n], written
+ */
+#define DEVEL_REINIT_STATIC_MAX_N 2048
+int devel_reinit_sdf_static(int n, const unsigned char* mask, float* phi, float d_lo, float d_hi,
+                            cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Whole loop                                                               */
 /* ------------------------------------------------------------------------ */

@@ -80,6 +80,7 @@ _sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
+_sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
 _sig("devel_profile_start", [_I])
 _sig("devel_profile_stop", [])
 _sig("devel_profile_kinds", [])
@@ -90,7 +91,9 @@ _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER
 EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_optics_destroy",
             "devel_optics_n", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
-            "devel_profile_stop", "devel_profile_kinds", "devel_profile_query")
+            "devel_profile_stop", "devel_profile_kinds", "devel_profile_query",
+            "devel_reinit_sdf_static")
+REINIT_STATIC_MAX_N = 2048
 
 
 def _check(rc: int):
@@ -216,6 +219,15 @@ def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 
     N = n * n
     _check(_lib.devel_reinit_sdf(n, _ptr(mask, torch.uint8, N, "mask"), _ptr(phi, torch.float32, N, "phi"),
                                  _ptr(d2, torch.int32, N, "d2"), d_lo, d_hi, _stream(stream)))
+
+
+def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):
+    """devel_reinit_sdf without the scratch argument: the library's static
+    device array (n <= 2048) serves as scratch; nothing is allocated."""
+    import torch
+    N = n * n
+    _check(_lib.devel_reinit_sdf_static(n, _ptr(mask, torch.uint8, N, "mask"),
+                                        _ptr(phi, torch.float32, N, "phi"), d_lo, d_hi, _stream(stream)))
 
 
 def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,

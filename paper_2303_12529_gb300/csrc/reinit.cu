@@ -16,6 +16,7 @@
 // Integer arithmetic throughout; sqrtf is IEEE round-to-nearest (no fast
 // math), so phi is the correctly rounded sqrt(d2) minus one half.
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -150,3 +151,53 @@ int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d
 }
 
 }  // namespace devel
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the distance scratch lives in a static device array.
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory (their memory is owned by another
+// allocator, or they must not pay cudaMalloc's implicit synchronisation), so
+// devel_reinit_sdf_static needs no scratch argument. The array below is
+// reserved on every GPU that loads this library, for the life of the process.
+static __device__ __align__(256) unsigned g_reinit_scratch[(size_t)DEVEL_REINIT_STATIC_MAX_N *
+                                                           DEVEL_REINIT_STATIC_MAX_N];
+
+namespace devel {
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+}  // namespace devel
+
+extern "C" int devel_reinit_sdf_static(int n, const unsigned char* mask, float* phi, float d_lo,
+                                       float d_hi, cudaStream_t s) {
+    using namespace devel;
+    if (n < 1 || n > DEVEL_REINIT_STATIC_MAX_N)
+        return set_error(DEVEL_EINVAL,
+                         "devel_reinit_sdf_static: n=%d outside [1, %d] (size of the static scratch)", n,
+                         DEVEL_REINIT_STATIC_MAX_N);
+    if (!mask || !phi) return set_error(DEVEL_EINVAL, "devel_reinit_sdf_static: mask/phi is NULL");
+    if ((reinterpret_cast<uintptr_t>(mask) | reinterpret_cast<uintptr_t>(phi)) & 15u)
+        return set_error(DEVEL_EINVAL, "devel_reinit_sdf_static: mask/phi not 16-byte aligned");
+    if (!(d_lo <= d_hi)) return set_error(DEVEL_EINVAL, "devel_reinit_sdf_static: d_lo > d_hi");
+    int dev = 0;
+    DEVEL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(DEVEL_EINVAL, "devel_reinit_sdf_static: device %d beyond %d", dev, kMaxDevices);
+    void* scratch = nullptr;
+    {
+        // set-up on the first call per device, with that device current: the host
+        // symbol is only a stand-in, the kernels need the array's device address
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        scratch = g_scratch_addr[dev];
+        if (!scratch) {
+            cudaError_t e = cudaGetSymbolAddress(&scratch, g_reinit_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "devel_reinit_sdf_static: cudaGetSymbolAddress");
+            g_scratch_addr[dev] = scratch;
+        }
+    }
+    // every scratch word the kernels read is written earlier in the same call,
+    // so the previous call's contents need no clearing
+    return launch_reinit(n, mask, phi, static_cast<int*>(scratch), d_lo, d_hi, s);
+}
