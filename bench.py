@@ -67,7 +67,7 @@ def kernel_cost(name, n, K, k, launches_per_iter_shape=None):
     if name in ("expand_gemm", "tc_expand"):
         # half the launches expand W2 (forward), half W (adjoint)
         return "flops", 2 * px * (2 * k2 + 2 * k) / 2
-    if name in ("spectrum_partial", "tc_spectrum"):
+    if name in ("spectrum_gemm", "tc_spectrum"):
         return "flops", 2 * px * (2 * k + 2 * k2) / 2
     return None, None
 

@@ -1,6 +1,7 @@
 // C ABI of libdevelset: argument checks, the optics handle, and the
 // forward / adjoint / solve sequences built from the kernels of the other
 // translation units.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,53 +45,56 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 // forward image from ws.mhat: Ihat on W2, then the expansion
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s) {
-    int rc = launch_socs_y(o, s);
+    int rc = launch_ihat(o, s);
     if (rc) return rc;
-    rc = launch_hopkins(o, s);
-    if (rc) return rc;
-    return launch_expand(o, o->ws.Ihat, o->basisW2, o->k2, I, 1.0f, false, s);
+    return launch_expand(o, o->ws.Ihat, o->W2, I, 1.0f, false, s);
 }
 
-// adjoint from ws.Y (filled by the forward pass of the same mask) and R
+// adjoint from ws.mhat (the spectrum of the imaged mask) and R = dL/dI
 int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
                       cudaStream_t s) {
-    const float inv = 1.0f / ((float)o->n * (float)o->n);
-    int rc = launch_spectrum_f32(o, R, o->basisW2, o->k2, o->ws.rhat, inv, s);
+    int rc = launch_spectrum_f32(o, R, o->W2, o->ws.rhat, s);
     if (rc) return rc;
-    rc = launch_adjoint_window(o, s);
+    rc = launch_shat(o, s);
     if (rc) return rc;
-    rc = launch_expand(o, o->ws.Shat, o->basisW, o->k, V, 2.0f, true, s);
+    rc = launch_expand(o, o->ws.Shat, o->W, V, 2.0f, true, s);
     if (rc) return rc;
     return launch_vmax_final(o, vmax, status, s);
 }
 
 static void free_optics(devel_optics* o) {
     if (!o) return;
-    void* ptrs[] = {o->basisW, o->basisW2, o->Hp, o->ws.part, o->ws.mhat, o->ws.Y, o->ws.Ihat,
-                    o->ws.rhat, o->ws.Shat, o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart,
-                    o->ws.bufI, o->ws.bufV, o->ws.phi2, o->ws.M, o->ws.d2, o->ws.vmax,
-                    o->ws.loss4, o->ws.cnt2};
+    void* ptrs[] = {o->W.basis, o->W.basisT, o->W2.basis, o->W2.basisT, o->TCC, o->Tdiff, o->goff,
+                    o->ws.Ppart, o->ws.part, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat, o->ws.Bmat,
+                    o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
+                    o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete o;
 }
 
-// cos / sin table of a centred window of side kw: rows 0..kw-1 cos, kw..2kw-1 sin,
-// angle 2 pi ((a - r) x mod n) / n reduced exactly in integers, evaluated in double.
-static std::vector<float> make_basis(int n, int kw) {
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// cos / sin table of a centred window of side kw, padded to ldk rows:
+// rows 0..kw-1 cos, kw..2kw-1 sin, rest 0; angle 2 pi ((a - r) x mod n) / n
+// reduced exactly in integers and evaluated in double. Also its transpose.
+static void make_basis(int n, int kw, int ldk, std::vector<float>& t, std::vector<float>& tT) {
     const int r = (kw - 1) / 2;
-    std::vector<float> t((size_t)2 * kw * n);
+    t.assign((size_t)ldk * n, 0.f);
+    tT.assign((size_t)n * ldk, 0.f);
     for (int a = 0; a < kw; ++a) {
         const long long u = a - r;
         for (int x = 0; x < n; ++x) {
             long long m = (u * x) % n;
             if (m < 0) m += n;
             const double ang = 2.0 * M_PI * (double)m / (double)n;
-            t[(size_t)a * n + x] = (float)std::cos(ang);
-            t[(size_t)(kw + a) * n + x] = (float)std::sin(ang);
+            const float c = (float)std::cos(ang), sn = (float)std::sin(ang);
+            t[(size_t)a * n + x] = c;
+            t[(size_t)(kw + a) * n + x] = sn;
+            tT[(size_t)x * ldk + a] = c;
+            tT[(size_t)x * ldk + kw + a] = sn;
         }
     }
-    return t;
 }
 
 }  // namespace devel
@@ -129,11 +133,19 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     o->k2 = 2 * k - 1;
     o->r2 = k - 1;
     o->precision = precision;
-    o->nblk_spec = (n + 15) / 16;
+    o->W.kw = k;
+    o->W.ldk = round_up(2 * k, 16);
+    o->W2.kw = o->k2;
+    o->W2.ldk = round_up(2 * o->k2, 16);
+    {
+        int ns = (n + 255) / 256;
+        o->nsplit = ns < 1 ? 1 : (ns > 16 ? 16 : ns);
+    }
     const size_t npix = (size_t)n * n;
     const int kk = k * k, kk2 = o->k2 * o->k2;
     const int nred = resist_parts(n);
     o->npart_red = nred;
+    const int ld2 = o->W2.ldk;
 
 #define ALLOC(ptr, bytes)                                                                  \
     do {                                                                                   \
@@ -146,16 +158,21 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         }                                                                                  \
     } while (0)
 
-    ALLOC(o->basisW, sizeof(float) * 2 * k * n);
-    ALLOC(o->basisW2, sizeof(float) * 2 * o->k2 * n);
-    ALLOC(o->Hp, sizeof(float2) * K * kk);
-    ALLOC(o->ws.part, sizeof(float2) * o->nblk_spec * kk2);
+    ALLOC(o->W.basis, sizeof(float) * o->W.ldk * n);
+    ALLOC(o->W.basisT, sizeof(float) * o->W.ldk * n);
+    ALLOC(o->W2.basis, sizeof(float) * ld2 * n);
+    ALLOC(o->W2.basisT, sizeof(float) * ld2 * n);
+    ALLOC(o->TCC, sizeof(float2) * (size_t)kk * kk);
+    ALLOC(o->Tdiff, sizeof(float2) * (size_t)kk * kk);
+    ALLOC(o->goff, sizeof(int) * kk2);
+    ALLOC(o->ws.Ppart, sizeof(float) * (size_t)o->nsplit * n * ld2);
+    ALLOC(o->ws.part, sizeof(float2) * (size_t)spectrum_blocks(n) * kk2);
     ALLOC(o->ws.mhat, sizeof(float2) * kk);
-    ALLOC(o->ws.Y, sizeof(float2) * K * kk);
     ALLOC(o->ws.Ihat, sizeof(float2) * kk2);
     ALLOC(o->ws.rhat, sizeof(float2) * kk2);
     ALLOC(o->ws.Shat, sizeof(float2) * kk);
-    ALLOC(o->ws.Acat, sizeof(float) * n * 2 * o->k2);
+    ALLOC(o->ws.Bmat, sizeof(float) * ld2 * ld2);
+    ALLOC(o->ws.Acat, sizeof(float) * (size_t)n * ld2);
     ALLOC(o->ws.dpart, sizeof(double) * 3 * nred);
     ALLOC(o->ws.lpart, sizeof(long long) * 2 * nred);
     ALLOC(o->ws.vpart, sizeof(float) * expand_parts(n));
@@ -169,20 +186,63 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.cnt2, sizeof(long long) * 2);
 #undef ALLOC
 
-    std::vector<float> bw = make_basis(n, k), bw2 = make_basis(n, o->k2);
-    std::vector<float2> hp((size_t)K * kk);
+    // DFT tables of both windows
+    std::vector<float> b1, b1T, b2, b2T;
+    make_basis(n, k, o->W.ldk, b1, b1T);
+    make_basis(n, o->k2, ld2, b2, b2T);
+    // rank-K TCC in double: TCC(a, b) = sum_j w_j H_j(a) conj(H_j(b))  (Sec. II-B)
+    std::vector<double> Hr((size_t)K * kk), Hi((size_t)K * kk);
     for (int j = 0; j < K; ++j) {
         const double sw = std::sqrt((double)w_host[j]);
         for (int i = 0; i < kk; ++i) {
-            hp[(size_t)j * kk + i] = make_float2((float)(sw * H_host[((size_t)j * kk + i) * 2]),
-                                                 (float)(sw * H_host[((size_t)j * kk + i) * 2 + 1]));
+            Hr[(size_t)j * kk + i] = sw * H_host[((size_t)j * kk + i) * 2];
+            Hi[(size_t)j * kk + i] = sw * H_host[((size_t)j * kk + i) * 2 + 1];
         }
     }
-    cudaError_t e = cudaMemcpy(o->basisW, bw.data(), bw.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(o->basisW2, bw2.data(), bw2.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(o->Hp, hp.data(), hp.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    std::vector<float2> tcc((size_t)kk * kk);
+    for (int a = 0; a < kk; ++a) {
+        for (int b = 0; b < kk; ++b) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < K; ++j) {
+                const double ar = Hr[(size_t)j * kk + a], ai = Hi[(size_t)j * kk + a];
+                const double br = Hr[(size_t)j * kk + b], bi = Hi[(size_t)j * kk + b];
+                re += ar * br + ai * bi;
+                im += ai * br - ar * bi;
+            }
+            tcc[(size_t)a * kk + b] = make_float2((float)re, (float)im);
+        }
+    }
+    // grouped by difference g = a - b in W2: rect(g) = {a : a - g in W}, row-major
+    std::vector<float2> tdiff((size_t)kk * kk);
+    std::vector<int> goff(kk2);
+    {
+        size_t off = 0;
+        const int r2 = o->r2;
+        for (int c1 = 0; c1 < o->k2; ++c1) {
+            for (int c2 = 0; c2 < o->k2; ++c2) {
+                goff[c1 * o->k2 + c2] = (int)off;
+                const int a1lo = std::max(0, c1 - r2), a1hi = std::min(k, c1 - r2 + k);
+                const int a2lo = std::max(0, c2 - r2), a2hi = std::min(k, c2 - r2 + k);
+                for (int a1 = a1lo; a1 < a1hi; ++a1)
+                    for (int a2 = a2lo; a2 < a2hi; ++a2) {
+                        const int b1 = a1 - c1 + r2, b2 = a2 - c2 + r2;
+                        tdiff[off++] = tcc[(size_t)(a1 * k + a2) * kk + (b1 * k + b2)];
+                    }
+            }
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    struct Cp { void* d; const void* h; size_t bytes; } cps[] = {
+        {o->W.basis, b1.data(), b1.size() * sizeof(float)},
+        {o->W.basisT, b1T.data(), b1T.size() * sizeof(float)},
+        {o->W2.basis, b2.data(), b2.size() * sizeof(float)},
+        {o->W2.basisT, b2T.data(), b2T.size() * sizeof(float)},
+        {o->TCC, tcc.data(), tcc.size() * sizeof(float2)},
+        {o->Tdiff, tdiff.data(), tdiff.size() * sizeof(float2)},
+        {o->goff, goff.data(), goff.size() * sizeof(int)},
+    };
+    for (const Cp& c : cps)
+        if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h, c.bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_optics(o);
         return cuda_error(e, "devel_optics_create: cudaMemcpy");
@@ -205,8 +265,7 @@ int devel_litho_forward(const devel_optics* o, const float* mask, float* intensi
     CHECK_PTR(intensity, "intensity");
     if ((const void*)mask == (const void*)intensity)
         return set_error(DEVEL_EINVAL, "devel_litho_forward: mask aliases intensity");
-    const float inv = 1.0f / ((float)o->n * (float)o->n);
-    int rc = launch_spectrum_f32(o, mask, o->basisW, o->k, o->ws.mhat, inv, s);
+    int rc = launch_spectrum_f32(o, mask, o->W, o->ws.mhat, s);
     if (rc) return rc;
     return forward_from_mhat(o, intensity, s);
 }
@@ -232,10 +291,7 @@ int devel_litho_adjoint(const devel_optics* o, const float* mask, const float* d
     CHECK_PTR(dLdI, "dLdI");
     CHECK_PTR(dLdM, "dLdM");
     CHECK_PTR(vmax, "vmax");
-    const float inv = 1.0f / ((float)o->n * (float)o->n);
-    int rc = launch_spectrum_f32(o, mask, o->basisW, o->k, o->ws.mhat, inv, s);
-    if (rc) return rc;
-    rc = launch_socs_y(o, s);  // Y_j = sqrt(w_j) H_j mhat
+    int rc = launch_spectrum_f32(o, mask, o->W, o->ws.mhat, s);
     if (rc) return rc;
     return adjoint_from_mhat(o, dLdI, dLdM, vmax, nullptr, s);
 }
@@ -290,7 +346,6 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         const devel_optics* o = cl.optics;
         const int n = o->n;
         const Workspace& w = o->ws;
-        const float inv = 1.0f / ((float)n * (float)n);
         float* phi = cl.phi;
         float* phi_alt = w.phi2;
         int rc;
@@ -302,7 +357,7 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         if (rc) return rc;
         for (int t = 0; t <= p->iters; ++t) {
             // image the current mask, resist loss and dL/dI (in place in bufI)
-            rc = launch_spectrum_u8(o, w.M, o->basisW, o->k, w.mhat, inv, s);
+            rc = launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
             if (rc) return rc;
             rc = forward_from_mhat(o, w.bufI, s);
             if (rc) return rc;

@@ -31,7 +31,7 @@ enum ProfKind {
     PK_SPECTRUM = 0, PK_SPECTRUM_REDUCE, PK_SOCS_Y, PK_HOPKINS, PK_ADJ_WINDOW,
     PK_EXPAND_T, PK_EXPAND_GEMM, PK_VMAX, PK_RESIST, PK_RESIST_FINAL,
     PK_STEP, PK_MASK, PK_EDT_COLS, PK_EDT_ROWS, PK_U8F32,
-    PK_TC_EXPAND, PK_TC_SPECTRUM, PROF_NKINDS
+    PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PROF_NKINDS
 };
 void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
@@ -42,14 +42,23 @@ constexpr int kMaxWindow = 63;
 // ---------------------------------------------------------------------------
 // the imaging model and its workspace
 // ---------------------------------------------------------------------------
+// A centred frequency window of side kw and its DFT tables.
+struct Window {
+    int kw = 0;              // window side (odd)
+    int ldk = 0;             // round_up(2 kw, 16): padded contraction length
+    float* basis = nullptr;  // [ldk][n]: rows a: cos(2 pi (a-r) x/n), rows kw+a: sin(...), rest 0
+    float* basisT = nullptr; // [n][ldk]: the transpose
+};
+
 struct Workspace {
-    float2* part = nullptr;    // [nblk_spec][k2*k2] spectrum partials
+    float* Ppart = nullptr;    // [nsplit][n][ldk2] split-K slices of the reduction
+    float2* part = nullptr;    // [nblk][k2*k2] row-block partial spectra
     float2* mhat = nullptr;    // [k*k]   mask spectrum on W, scaled 1/n^2
-    float2* Y = nullptr;       // [K][k*k] sqrt(w_j) H_j * mhat
     float2* Ihat = nullptr;    // [k2*k2] aerial-image spectrum on W2
     float2* rhat = nullptr;    // [k2*k2] dL/dI spectrum on W2, scaled 1/n^2
     float2* Shat = nullptr;    // [k*k]   adjoint spectrum on W
-    float* Acat = nullptr;     // [n][2*k2] expansion operand [Re T | -Im T]
+    float* Bmat = nullptr;     // [ldk2][ldk2] expansion coefficients
+    float* Acat = nullptr;     // [n][ldk2] expansion operand [Re T | -Im T]
     double* dpart = nullptr;   // reduction partials, doubles
     long long* lpart = nullptr;// reduction partials, counts
     float* vpart = nullptr;    // per-block max |V|
@@ -68,11 +77,12 @@ struct Workspace {
 
 struct devel_optics {
     int n, K, k, r, k2, r2, precision;
-    int nblk_spec;            // row blocks of the spectrum reduction
+    int nsplit;               // split-K slices of the reduction GEMM
     int npart_red;            // size of the generic reduction partial arrays
-    float* basisW = nullptr;  // [2k][n]:  cos(2 pi (a-r) x / n) rows, then sin rows
-    float* basisW2 = nullptr; // [2k2][n]: same on the difference window W2 = W - W
-    float2* Hp = nullptr;     // [K][k*k]: sqrt(w_j) H_j
+    devel::Window W, W2;      // the kernel window and the difference window
+    float2* TCC = nullptr;    // [k*k][k*k] TCC_K(a, b) = sum_j w_j H_j(a) conj(H_j(b))
+    float2* Tdiff = nullptr;  // k^4 entries: TCC_K(a, a - g) grouped by g in W2
+    int* goff = nullptr;      // [k2*k2] offset of each g's group in Tdiff
     devel::Workspace ws;
 };
 
@@ -81,21 +91,19 @@ namespace devel {
 // ---------------------------------------------------------------------------
 // launchers (litho.cu)
 // ---------------------------------------------------------------------------
-// spectrum on a window of side kw (basis [2kw][n]) of an n x n real image:
-// out[a][b] = scale * sum_p X(p) e^{-2 pi i ((a-r)y + (b-r)x)/n}
-int launch_spectrum_f32(const devel_optics* o, const float* X, const float* basis, int kw,
-                        float2* out, float scale, cudaStream_t s);
-int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const float* basis, int kw,
-                       float2* out, float scale, cudaStream_t s);
-// Y_j = sqrt(w_j) H_j mhat
-int launch_socs_y(const devel_optics* o, cudaStream_t s);
-// Ihat from Y (SOCS sum of autocorrelations on W2)
-int launch_hopkins(const devel_optics* o, cudaStream_t s);
-// Shat from mhat (via Y) and rhat
-int launch_adjoint_window(const devel_optics* o, cudaStream_t s);
-// out = Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} (times `mult`), optional max|out|
-int launch_expand(const devel_optics* o, const float2* Z, const float* basis, int kw, float* out,
-                  float mult, bool want_max, cudaStream_t s);
+// spectrum of an n x n real image on window w (output scaled 1/n^2):
+// out[a][b] = n^-2 sum_p X(p) e^{-2 pi i ((a-r)y + (b-r)x)/n}
+int launch_spectrum_f32(const devel_optics* o, const float* X, const Window& w, float2* out, cudaStream_t s);
+int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const Window& w, float2* out,
+                       cudaStream_t s);
+int spectrum_blocks(int n);
+// Ihat (on W2) from mhat with the rank-K TCC
+int launch_ihat(const devel_optics* o, cudaStream_t s);
+// Shat (on W) from mhat and rhat with the rank-K TCC
+int launch_shat(const devel_optics* o, cudaStream_t s);
+// out = mult * Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} on window w; optional max|out|
+int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float* out, float mult,
+                  bool want_max, cudaStream_t s);
 int expand_parts(int n);
 int launch_vmax_final(const devel_optics* o, double* vmax, int* status, cudaStream_t s);
 

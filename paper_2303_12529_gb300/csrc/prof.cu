@@ -13,10 +13,10 @@
 namespace devel {
 
 static const char* kNames[PROF_NKINDS] = {
-    "spectrum_partial", "spectrum_reduce", "socs_y",     "hopkins",   "adjoint_window",
-    "expand_T",         "expand_gemm",     "vmax_final", "resist",    "resist_final",
-    "levelset_step",    "mask_from_phi",   "edt_cols",   "edt_rows",  "u8_to_f32",
-    "tc_expand",        "tc_spectrum",
+    "spectrum_gemm", "spectrum_reduce", "unused",     "ihat_tcc",  "shat_tcc",
+    "expand_T",      "expand_gemm",     "vmax_final", "resist",    "resist_final",
+    "levelset_step", "mask_from_phi",   "edt_cols",   "edt_rows",  "u8_to_f32",
+    "tc_expand",     "tc_spectrum",     "spectrum_stage2", "tc_split",
 };
 
 struct Slot {
