@@ -85,6 +85,13 @@ int devel_optics_destroy(devel_optics* optics);
 /* n of the handle (or -1 for NULL). */
 int devel_optics_n(const devel_optics* optics);
 
+/*
+ * Synchronise `stream`, then report (and clear) the handle's device error
+ * flag: DEVEL_ETIMEOUT if a tensor-core kernel's bounded wait gave up during
+ * an earlier devel_litho_* call on this handle, else DEVEL_OK.
+ */
+int devel_optics_check(const devel_optics* optics, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Lithography                                                              */
 /* ------------------------------------------------------------------------ */

@@ -73,6 +73,7 @@ _sig("devel_version", [])
 _sig("devel_optics_create", [_I, _I, _I, _P, _P, _I, ctypes.POINTER(_P)])
 _sig("devel_optics_destroy", [_P])
 _sig("devel_optics_n", [_P])
+_sig("devel_optics_check", [_P, _P])
 _sig("devel_litho_forward", [_P, _P, _P, _P])
 _sig("devel_resist_loss", [_P, _P, _P, ctypes.POINTER(devel_resist_params), _P, _P, _P, _P])
 _sig("devel_litho_adjoint", [_P, _P, _P, _P, _P, _P])
@@ -89,7 +90,7 @@ _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER
 
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_optics_destroy",
-            "devel_optics_n", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
+            "devel_optics_n", "devel_optics_check", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query",
             "devel_reinit_sdf_static")
@@ -165,6 +166,11 @@ def devel_optics_create(n: int, H: np.ndarray, w: np.ndarray, precision: int = D
     out = _P()
     _check(_lib.devel_optics_create(n, K, k, Hf.ctypes.data, wf.ctypes.data, precision, ctypes.byref(out)))
     return Optics(out.value, n, K, k, precision)
+
+
+def devel_optics_check(optics: Optics, stream=None):
+    """Synchronise and raise DevelError if a bounded device wait of this handle gave up."""
+    _check(_lib.devel_optics_check(optics.handle, _stream(stream)))
 
 
 def devel_optics_destroy(optics: Optics):

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace devel {
 
@@ -47,7 +48,7 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s) {
     int rc = launch_ihat(o, s);
     if (rc) return rc;
-    return launch_expand(o, o->ws.Ihat, o->W2, I, 1.0f, false, s);
+    return launch_expand(o, o->ws.Ihat, o->W2, I, 1.0f, false, nullptr, s);
 }
 
 // adjoint from ws.mhat (the spectrum of the imaged mask) and R = dL/dI
@@ -57,9 +58,10 @@ int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* v
     if (rc) return rc;
     rc = launch_shat(o, s);
     if (rc) return rc;
-    rc = launch_expand(o, o->ws.Shat, o->W, V, 2.0f, true, s);
+    int nparts = 0;
+    rc = launch_expand(o, o->ws.Shat, o->W, V, 2.0f, true, &nparts, s);
     if (rc) return rc;
-    return launch_vmax_final(o, vmax, status, s);
+    return launch_vmax_final(o, nparts, vmax, status, s);
 }
 
 static void free_optics(devel_optics* o) {
@@ -67,7 +69,10 @@ static void free_optics(devel_optics* o) {
     void* ptrs[] = {o->W.basis, o->W.basisT, o->W2.basis, o->W2.basisT, o->TCC, o->Tdiff, o->goff,
                     o->ws.Ppart, o->ws.part, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat, o->ws.Bmat,
                     o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
-                    o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2};
+                    o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
+                    o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
+                    o->tcW2.basis_hi, o->tcW2.basis_lo, o->tcW2.basisT_hi, o->tcW2.basisT_lo,
+                    o->Xhi, o->Xlo, o->Acat_hi, o->Acat_lo, o->tc_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete o;
@@ -119,8 +124,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         return set_error(DEVEL_EINVAL, "devel_optics_create: k=%d must be odd in [3, %d]", k, kMaxWindow);
     if (2 * k - 1 > n) return set_error(DEVEL_EINVAL, "devel_optics_create: 2k-1=%d exceeds n=%d", 2 * k - 1, n);
     if (K < 1 || K > k * k) return set_error(DEVEL_EINVAL, "devel_optics_create: K=%d outside [1, k*k]", K);
-    if (precision != DEVEL_PREC_FP32)
-        return set_error(DEVEL_EINVAL, "devel_optics_create: precision %d not available in this build", precision);
+    if (precision != DEVEL_PREC_FP32 && precision != DEVEL_PREC_BF16X3)
+        return set_error(DEVEL_EINVAL, "devel_optics_create: unknown precision %d", precision);
     for (int j = 0; j < K; ++j)
         if (!(w_host[j] >= 0.f) || !std::isfinite(w_host[j]))
             return set_error(DEVEL_EINVAL, "devel_optics_create: w[%d] must be finite and >= 0", j);
@@ -137,7 +142,10 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     o->W.ldk = round_up(2 * k, 16);
     o->W2.kw = o->k2;
     o->W2.ldk = round_up(2 * o->k2, 16);
-    {
+    o->ldn = round_up(n, 64);
+    if (precision == DEVEL_PREC_BF16X3) {
+        o->nsplit = o->ldn / 256 + (o->ldn % 256 ? 1 : 0);  // 256-wide K slices of the tc reduction
+    } else {
         int ns = (n + 255) / 256;
         o->nsplit = ns < 1 ? 1 : (ns > 16 ? 16 : ns);
     }
@@ -184,6 +192,21 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.vmax, sizeof(double));
     ALLOC(o->ws.loss4, sizeof(double) * 4);
     ALLOC(o->ws.cnt2, sizeof(long long) * 2);
+    ALLOC(o->tc_err, sizeof(int));
+    if (precision == DEVEL_PREC_BF16X3) {
+        const size_t bf = sizeof(__nv_bfloat16);
+        for (TcWindow* tw : {&o->tcW, &o->tcW2}) {
+            const int ldk = (tw == &o->tcW) ? o->W.ldk : ld2;
+            ALLOC(tw->basis_hi, bf * ldk * o->ldn);
+            ALLOC(tw->basis_lo, bf * ldk * o->ldn);
+            ALLOC(tw->basisT_hi, bf * (size_t)n * ldk);
+            ALLOC(tw->basisT_lo, bf * (size_t)n * ldk);
+        }
+        ALLOC(o->Xhi, bf * (size_t)n * o->ldn);
+        ALLOC(o->Xlo, bf * (size_t)n * o->ldn);
+        ALLOC(o->Acat_hi, bf * (size_t)n * ld2);
+        ALLOC(o->Acat_lo, bf * (size_t)n * ld2);
+    }
 #undef ALLOC
 
     // DFT tables of both windows
@@ -243,9 +266,36 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     };
     for (const Cp& c : cps)
         if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h, c.bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(o->tc_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         free_optics(o);
         return cuda_error(e, "devel_optics_create: cudaMemcpy");
+    }
+    if (precision == DEVEL_PREC_BF16X3) {
+        // bf16 hi/lo DFT tables (split on the device from the FP32 tables) and tensor maps
+        int rc = DEVEL_OK;
+        for (int wi = 0; wi < 2 && rc == DEVEL_OK; ++wi) {
+            const Window& w = wi ? o->W2 : o->W;
+            TcWindow& tw = wi ? o->tcW2 : o->tcW;
+            rc = tc::launch_split(w.basis, w.ldk, n, n, o->ldn, tw.basis_hi, tw.basis_lo, 0);
+            if (!rc) rc = tc::launch_split(w.basisT, n, w.ldk, w.ldk, w.ldk, tw.basisT_hi, tw.basisT_lo, 0);
+            if (!rc) rc = tc::make_map(&tw.m_basis_hi, tw.basis_hi, w.ldk, o->ldn, o->ldn, w.ldk);
+            if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, w.ldk, o->ldn, o->ldn, w.ldk);
+            if (!rc) rc = tc::make_map(&tw.m_basisT_hi, tw.basisT_hi, n, w.ldk, w.ldk, 128);
+            if (!rc) rc = tc::make_map(&tw.m_basisT_lo, tw.basisT_lo, n, w.ldk, w.ldk, 128);
+            if (!rc) rc = tc::make_map(&tw.m_acat_hi, o->Acat_hi, n, w.ldk, w.ldk, 128);
+            if (!rc) rc = tc::make_map(&tw.m_acat_lo, o->Acat_lo, n, w.ldk, w.ldk, 128);
+        }
+        if (!rc) rc = tc::make_map(&o->m_X_hi, o->Xhi, n, o->ldn, o->ldn, 128);
+        if (!rc) rc = tc::make_map(&o->m_X_lo, o->Xlo, n, o->ldn, o->ldn, 128);
+        if (!rc) {
+            cudaError_t e2 = cudaDeviceSynchronize();
+            if (e2 != cudaSuccess) rc = cuda_error(e2, "devel_optics_create: table split");
+        }
+        if (rc) {
+            free_optics(o);
+            return rc;
+        }
     }
     *out = o;
     return DEVEL_OK;
@@ -256,6 +306,18 @@ int devel_optics_destroy(devel_optics* o) {
     cudaError_t e = cudaDeviceSynchronize();
     free_optics(o);
     if (e != cudaSuccess) return cuda_error(e, "devel_optics_destroy: cudaDeviceSynchronize");
+    return DEVEL_OK;
+}
+
+int devel_optics_check(const devel_optics* o, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_optics_check: optics is NULL");
+    DEVEL_CUDA_TRY(cudaStreamSynchronize(s));
+    int flag = 0;
+    DEVEL_CUDA_TRY(cudaMemcpy(&flag, o->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        DEVEL_CUDA_TRY(cudaMemset(o->tc_err, 0, sizeof(int)));
+        return set_error(flag, "devel_optics_check: a bounded device wait gave up (code %d)", flag);
+    }
     return DEVEL_OK;
 }
 

@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA sources of libdevelset.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,10 +75,27 @@ struct Workspace {
     long long* cnt2 = nullptr; // [2]
 };
 
+// bf16 hi/lo tables and tensor maps of one window for the tensor-core path
+struct TcWindow {
+    __nv_bfloat16* basis_hi = nullptr;   // [ldk][ldn]
+    __nv_bfloat16* basis_lo = nullptr;
+    __nv_bfloat16* basisT_hi = nullptr;  // [n][ldk]
+    __nv_bfloat16* basisT_lo = nullptr;
+    CUtensorMap m_basis_hi, m_basis_lo, m_basisT_hi, m_basisT_lo, m_acat_hi, m_acat_lo;
+};
+
 }  // namespace devel
 
 struct devel_optics {
     int n, K, k, r, k2, r2, precision;
+    int ldn = 0;                  // tensor-core path: round_up(n, 64)
+    devel::TcWindow tcW, tcW2;
+    __nv_bfloat16* Xhi = nullptr;     // [n][ldn] operand of the reductions
+    __nv_bfloat16* Xlo = nullptr;
+    __nv_bfloat16* Acat_hi = nullptr; // [n][ldk2] operand of the expansions
+    __nv_bfloat16* Acat_lo = nullptr;
+    CUtensorMap m_X_hi, m_X_lo;
+    int* tc_err = nullptr;            // device flag: DEVEL_ETIMEOUT from a bounded wait
     int nsplit;               // split-K slices of the reduction GEMM
     int npart_red;            // size of the generic reduction partial arrays
     devel::Window W, W2;      // the kernel window and the difference window
@@ -102,10 +121,11 @@ int launch_ihat(const devel_optics* o, cudaStream_t s);
 // Shat (on W) from mhat and rhat with the rank-K TCC
 int launch_shat(const devel_optics* o, cudaStream_t s);
 // out = mult * Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} on window w; optional max|out|
+// (returns the number of max|out| partials written when want_max)
 int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float* out, float mult,
-                  bool want_max, cudaStream_t s);
+                  bool want_max, int* nparts, cudaStream_t s);
 int expand_parts(int n);
-int launch_vmax_final(const devel_optics* o, double* vmax, int* status, cudaStream_t s);
+int launch_vmax_final(const devel_optics* o, int nparts, double* vmax, int* status, cudaStream_t s);
 
 // resist.cu
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,

@@ -25,6 +25,7 @@
 // with basis[c][x] = cos / sin(2 pi (a - r) x / n) (c = a, kw + a) and
 // basisT its transpose, zero-padded to ldk = round_up(2kw, 16) columns.
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace devel {
 namespace {
@@ -306,19 +307,38 @@ __global__ void k_vmax_final(const float* __restrict__ vpart, int nparts, double
     }
 }
 
+constexpr int kTcSplitK = 256;  // K slice of one split of the tensor-core reduction
+
+int tc_operand_f32(const devel_optics* o, const float* X, cudaStream_t s) {
+    return tc::launch_split(X, o->n, o->n, o->n, o->ldn, o->Xhi, o->Xlo, s);
+}
+int tc_operand_f32(const devel_optics* o, const unsigned char* M, cudaStream_t s) {
+    return tc::launch_mask_bf16(M, o->n, o->ldn, o->Xhi, s);
+}
+
 template <typename TA>
 int spectrum_impl(const devel_optics* o, const TA* X, const Window& w, float2* out, cudaStream_t s) {
     const int n = o->n;
     const Workspace& ws = o->ws;
     const int nsplit = o->nsplit;
-    const int kchunk = ((n + nsplit - 1) / nsplit + gBK - 1) / gBK * gBK;
     const size_t sstride = (size_t)n * w.ldk;
-    dim3 grid((w.ldk + gBN - 1) / gBN, (n + gBM - 1) / gBM, nsplit);
-    prof_begin(PK_SPECTRUM, s);
-    k_gemm_nt<TA, EPI_STORE><<<grid, kThreads, 0, s>>>(X, n, w.basis, n, n, w.ldk, n, kchunk, 1.0f,
-                                                        ws.Ppart, w.ldk, sstride, nullptr);
-    prof_end(PK_SPECTRUM, s);
-    DEVEL_LAUNCH_CHECK("k_gemm_nt(spectrum)");
+    if (o->precision == DEVEL_PREC_BF16X3) {
+        int rc = tc_operand_f32(o, X, s);
+        if (rc) return rc;
+        const TcWindow& tw = (&w == &o->W) ? o->tcW : o->tcW2;
+        tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, sizeof(TA) == 4 ? 1 : 0};
+        rc = tc::launch_gemm(op, w.ldk, false, PK_TC_SPECTRUM, n, w.ldk, o->ldn, kTcSplitK, 1.0f, ws.Ppart,
+                             w.ldk, sstride, nullptr, o->tc_err, s);
+        if (rc) return rc;
+    } else {
+        const int kchunk = ((n + nsplit - 1) / nsplit + gBK - 1) / gBK * gBK;
+        dim3 grid((w.ldk + gBN - 1) / gBN, (n + gBM - 1) / gBM, nsplit);
+        prof_begin(PK_SPECTRUM, s);
+        k_gemm_nt<TA, EPI_STORE><<<grid, kThreads, 0, s>>>(X, n, w.basis, n, n, w.ldk, n, kchunk, 1.0f,
+                                                            ws.Ppart, w.ldk, sstride, nullptr);
+        prof_end(PK_SPECTRUM, s);
+        DEVEL_LAUNCH_CHECK("k_gemm_nt(spectrum)");
+    }
     const int nblk = (n + kTY - 1) / kTY;
     const size_t smem = sizeof(float) * 4 * kTY * w.kw;
     prof_begin(PK_SPECTRUM_STAGE2, s);
@@ -365,7 +385,7 @@ int launch_shat(const devel_optics* o, cudaStream_t s) {
 }
 
 int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float* out, float mult,
-                  bool want_max, cudaStream_t s) {
+                  bool want_max, int* nparts, cudaStream_t s) {
     const int n = o->n;
     const Workspace& ws = o->ws;
     prof_begin(PK_EXPAND_T, s);
@@ -376,6 +396,17 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float
                                                          w.ldk, 1.0f, ws.Acat, w.ldk, 0, nullptr);
     prof_end(PK_EXPAND_T, s);
     DEVEL_LAUNCH_CHECK("k_gemm_nt(T)");
+    if (o->precision == DEVEL_PREC_BF16X3) {
+        int rc = tc::launch_split(ws.Acat, n, w.ldk, w.ldk, w.ldk, o->Acat_hi, o->Acat_lo, s);
+        if (rc) return rc;
+        const TcWindow& tw = (&w == &o->W) ? o->tcW : o->tcW2;
+        tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, &tw.m_basisT_hi, &tw.m_basisT_lo, 1};
+        const int kps = (w.ldk + 63) / 64 * 64;
+        if (nparts) *nparts = ((n + 127) / 128) * ((n + 127) / 128);
+        return tc::launch_gemm(op, 128, want_max, PK_TC_EXPAND, n, n, w.ldk, kps, mult, out, n, 0,
+                               want_max ? ws.vpart : nullptr, o->tc_err, s);
+    }
+    if (nparts) *nparts = expand_parts(n);
     dim3 g((n + gBN - 1) / gBN, (n + gBM - 1) / gBM, 1);
     prof_begin(PK_EXPAND_GEMM, s);
     if (want_max)
@@ -391,9 +422,9 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float
 
 int expand_parts(int n) { return ((n + gBN - 1) / gBN) * ((n + gBM - 1) / gBM); }
 
-int launch_vmax_final(const devel_optics* o, double* vmax, int* status, cudaStream_t s) {
+int launch_vmax_final(const devel_optics* o, int nparts, double* vmax, int* status, cudaStream_t s) {
     prof_begin(PK_VMAX, s);
-    k_vmax_final<<<1, 1024, 0, s>>>(o->ws.vpart, expand_parts(o->n), vmax, status);
+    k_vmax_final<<<1, 1024, 0, s>>>(o->ws.vpart, nparts, vmax, status);
     prof_end(PK_VMAX, s);
     DEVEL_LAUNCH_CHECK("k_vmax_final");
     return DEVEL_OK;

@@ -1,0 +1,38 @@
+// Host interface of the tcgen05 contraction kernels (tc.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+namespace devel {
+namespace tc {
+
+// The four operand tensor maps of one GEMM (see make_map). use_alo = 0 skips
+// the A_lo term (A exact in bf16).
+struct Operands {
+    const CUtensorMap* Ahi;
+    const CUtensorMap* Alo;
+    const CUtensorMap* Bhi;
+    const CUtensorMap* Blo;
+    int use_alo;
+};
+
+// bf16 tensor map over a row-major [rows][cols] array with row pitch ld
+// elements; boxes of 64 columns x box_rows rows, 128-byte swizzle, zero fill.
+int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int box_rows);
+
+// D = scale * A B^T (M x N, contraction length K, a multiple of 16), BN in
+// {80, 128, 144}; split-K slices of k_per_split (a multiple of 64) go to
+// C + z * split_stride. vel: also write the per-CTA max |D| to vpart.
+int launch_gemm(const Operands& op, int BN, bool vel, int prof_kind, int M, int N, int K, int k_per_split,
+                float scale, float* C, int ldc, size_t split_stride, float* vpart, int* err, cudaStream_t s);
+
+// hi/lo split of a row-major float array [rows][cols] (pitch ldx) into
+// [rows][ldo] bf16 arrays, zero beyond cols; lo may be NULL.
+int launch_split(const float* X, int rows, int cols, int ldx, int ldo, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                 cudaStream_t s);
+// 0/1 mask (uint8 [n][n]) to bf16 [n][ldo], zero beyond n.
+int launch_mask_bf16(const unsigned char* M, int n, int ldo, __nv_bfloat16* hi, cudaStream_t s);
+
+}  // namespace tc
+}  // namespace devel

@@ -15,6 +15,8 @@ from gpu_util import need_gpu, dev, host, rel_err, torch
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
+TOL_BF16X3 = 2e-4
+PRECISIONS = [(0, TOL_FP32), (1, TOL_BF16X3)]  # DEVEL_PREC_FP32, DEVEL_PREC_BF16X3
 
 CASES = [
     # (n, K, k, kind)
@@ -38,11 +40,12 @@ def _masks(n):
     yield "real", synth.random_field(3, n, -0.5, 1.5)
 
 
+@pytest.mark.parametrize("prec,tol", PRECISIONS)
 @pytest.mark.parametrize("n,K,k,kind", CASES)
-def test_forward_matches_oracle(n, K, k, kind):
+def test_forward_matches_oracle(n, K, k, kind, prec, tol):
     dv = need_gpu()
     H, w = _model(n, K, k, kind)
-    opt = dv.devel_optics_create(n, H, w)
+    opt = dv.devel_optics_create(n, H, w, prec)
     out = torch.empty(n * n, dtype=torch.float32, device="cuda")
     for name, M in _masks(n):
         Mf = M.astype(np.float32)
@@ -51,7 +54,8 @@ def test_forward_matches_oracle(n, K, k, kind):
         ref = litho.aerial(Mf.astype(np.float64), H.astype(np.complex64).astype(np.complex128),
                            w.astype(np.float32).astype(np.float64))
         e = rel_err(host(out, n), ref)
-        assert e <= TOL_FP32, (name, e)
+        assert e <= tol, (name, e)
+    dv.devel_optics_check(opt)
 
 
 def test_forward_clear_field_and_empty_mask():
@@ -98,11 +102,12 @@ def test_resist_loss_matches_oracle(beta):
     assert host(cnt).tolist() == [l2, pvb]
 
 
+@pytest.mark.parametrize("prec,tol", PRECISIONS)
 @pytest.mark.parametrize("n,K,k,kind", CASES)
-def test_adjoint_matches_oracle(n, K, k, kind):
+def test_adjoint_matches_oracle(n, K, k, kind, prec, tol):
     dv = need_gpu()
     H, w = _model(n, K, k, kind, seed=1)
-    opt = dv.devel_optics_create(n, H, w)
+    opt = dv.devel_optics_create(n, H, w, prec)
     rng = np.random.default_rng(n)
     V = torch.empty(n * n, dtype=torch.float32, device="cuda")
     vmax = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -115,19 +120,21 @@ def test_adjoint_matches_oracle(n, K, k, kind):
         torch.cuda.synchronize()
         ref = litho.aerial_gradient(Mf.astype(np.float64), R.astype(np.float64), Hc, wc)
         e = rel_err(host(V, n), ref)
-        assert e <= TOL_FP32, (name, e)
+        assert e <= tol, (name, e)
         vm = float(host(vmax)[0])
-        assert abs(vm - np.abs(ref).max()) <= TOL_FP32 * np.abs(ref).max()
+        assert abs(vm - np.abs(ref).max()) <= tol * np.abs(ref).max()
         assert vm == float(np.abs(host(V)).max())
+    dv.devel_optics_check(opt)
 
 
-def test_forward_full_size_sampled():
+@pytest.mark.parametrize("prec,tol", PRECISIONS)
+def test_forward_full_size(prec, tol):
     """2048^2, K = 24, k = 35 (the full-size workload's model), Manhattan
-    clip: compare sampled rows against the oracle's full-size FFT image."""
+    clip, against the oracle's full-size FFT image."""
     dv = need_gpu()
     n = 2048
     o = synth.optics(n, 24, 35)
-    opt = dv.devel_optics_create(n, o.H, o.w)
+    opt = dv.devel_optics_create(n, o.H, o.w, prec)
     Zt = synth.manhattan_clip(1000)
     out = torch.empty(n * n, dtype=torch.float32, device="cuda")
     dv.devel_litho_forward(opt, dev(Zt.astype(np.float32)), out)
@@ -135,4 +142,24 @@ def test_forward_full_size_sampled():
     ref = litho.aerial(Zt.astype(np.float64), o.H.astype(np.complex64).astype(np.complex128),
                        o.w.astype(np.float32).astype(np.float64))
     got = host(out, n)
-    assert rel_err(got, ref) <= TOL_FP32
+    assert rel_err(got, ref) <= tol
+    dv.devel_optics_check(opt)
+
+
+@pytest.mark.parametrize("prec,tol", PRECISIONS)
+def test_adjoint_full_size(prec, tol):
+    dv = need_gpu()
+    n = 2048
+    o = synth.optics(n, 24, 35)
+    opt = dv.devel_optics_create(n, o.H, o.w, prec)
+    Zt = synth.manhattan_clip(1001).astype(np.float32)
+    R = synth.random_field(9, n, -1.0, 1.0).astype(np.float32)
+    V = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    vmax = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dv.devel_litho_adjoint(opt, dev(Zt), dev(R), V, vmax)
+    torch.cuda.synchronize()
+    ref = litho.aerial_gradient(Zt.astype(np.float64), R.astype(np.float64),
+                                o.H.astype(np.complex64).astype(np.complex128),
+                                o.w.astype(np.float32).astype(np.float64))
+    assert rel_err(host(V, n), ref) <= tol
+    dv.devel_optics_check(opt)
