@@ -183,7 +183,7 @@ int devel_levelset_step(int n, const float* phi, const float* V, const double* v
  *   phi    device float[n*n], written
  *   d2     device int[n*n], scratch; on return d2[p] is the exact integer
  *          squared distance of p to the other class, or -1 if that class is empty
- * Requires 1 <= n <= 16384 and d_lo <= d_hi.
+ * Requires 1 <= n <= 8192 and d_lo <= d_hi.
  */
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo,
                      float d_hi, cudaStream_t stream);
@@ -226,6 +226,10 @@ typedef struct {
     int iters;           /* iterations T                                                  */
     int reinit_every;    /* re-initialise after iteration i when (i+1) % reinit_every == 0 (0 = never) */
     int start_iter;      /* global index of the first iteration (resume)                  */
+    int use_graph;       /* 1: capture the solve into a CUDA graph on first use and replay it
+                            on later calls with identical params and clip list (kernel
+                            arguments are baked in; the data behind the pointers is read at
+                            replay); 0: launch kernel by kernel. Ignored while a profile is open. */
 } devel_ilt_params;
 
 typedef struct {
@@ -248,7 +252,9 @@ typedef struct {
  *   status_dev  device int[1]: set to 0, then to DEVEL_ENAN by the device if a
  *               loss or max|V| is not finite (read it after synchronising).
  * Clips may have different n; each clip's handle must not be used by any
- * other concurrent call.
+ * other concurrent call. With use_graph, the first call with a given
+ * argument set captures the work on an internal stream (not on `stream`)
+ * and later calls replay it: one graph launch on `stream`.
  */
 int devel_ilt_solve(const devel_ilt_params* params, int nclips, const devel_clip* clips,
                     int* status_dev, cudaStream_t stream);

@@ -52,7 +52,7 @@ class devel_resist_params(ctypes.Structure):
 
 class devel_ilt_params(ctypes.Structure):
     _fields_ = [("resist", devel_resist_params), ("dt", _F), ("lambda_", _F), ("d_lo", _F),
-                ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I)]
+                ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I), ("use_graph", _I)]
 
 
 class devel_clip(ctypes.Structure):
@@ -237,9 +237,9 @@ def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float
 
 
 def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,
-               reinit_every=5, start_iter=0) -> devel_ilt_params:
+               reinit_every=5, start_iter=0, use_graph=True) -> devel_ilt_params:
     return devel_ilt_params(resist if resist is not None else resist_params(), dt, lam, d_lo, d_hi,
-                            iters, reinit_every, start_iter)
+                            iters, reinit_every, start_iter, int(bool(use_graph)))
 
 
 @dataclass

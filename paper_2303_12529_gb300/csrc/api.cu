@@ -2,6 +2,7 @@
 // forward / adjoint / solve sequences built from the kernels of the other
 // translation units.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -29,6 +30,22 @@ int cuda_error(cudaError_t e, const char* where) {
 
 int expand_parts(int n);
 
+// Shared-memory opt-ins of every kernel, once per device, outside any stream capture.
+static int init_device_attrs() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    DEVEL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(DEVEL_EINVAL, "device index %d", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return DEVEL_OK;
+    int rc = litho_init_attrs();
+    if (!rc) rc = reinit_init_attrs();
+    if (!rc) rc = tc::init_attrs();
+    if (!rc) done[dev] = true;
+    return rc;
+}
+
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 #define CHECK_PTR(p, name)                                                             \
@@ -44,30 +61,62 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
             return set_error(DEVEL_EINVAL, "%s: %s is not 16-byte aligned", __func__, name); \
     } while (0)
 
-// forward image from ws.mhat: Ihat on W2, then the expansion
+// forward image from ws.mhat: Ihat on W2, then the expansion (plain store)
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s) {
     int rc = launch_ihat(o, s);
     if (rc) return rc;
-    return launch_expand(o, o->ws.Ihat, o->W2, I, 1.0f, false, nullptr, s);
+    EpiArgs ep;
+    ep.C = I;
+    return launch_expand(o, o->ws.Ihat, o->W2, EPI_STORE, ep, nullptr, s);
 }
 
-// adjoint from ws.mhat (the spectrum of the imaged mask) and R = dL/dI
+// forward image and resist loss: I into ws.bufI, then dL/dI into ws.bufI (FP32
+// path, in place) or into the bf16 reduction operand Xhi/Xlo (tensor-core path);
+// the loss and metrics of this image go to the history slots (or loss4/cnt2).
+int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, const devel_resist_params& rp,
+                           double* loss4, long long* cnt2, double* lh, long long* l2h, long long* pvbh,
+                           int* status, cudaStream_t s) {
+    int rc = forward_from_mhat(o, o->ws.bufI, s);
+    if (rc) return rc;
+    const bool tcp = o->precision == DEVEL_PREC_BF16X3;
+    return launch_resist(o->n, o->ws.bufI, target, rp, tcp ? nullptr : o->ws.bufI, tcp ? o->Xhi : nullptr,
+                         tcp ? o->Xlo : nullptr, o->ldn, o->ws.dpart, o->ws.lpart, o->npart_red, loss4, cnt2, lh,
+                         l2h, pvbh, status, s);
+}
+
+// adjoint from ws.mhat (spectrum of the imaged mask) and the spectrum rhat of R
+static int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s) {
+    int rc = launch_shat(o, s);
+    if (rc) return rc;
+    EpiArgs ep;
+    ep.C = V;
+    ep.scale = 2.0f;
+    int nparts = 0;
+    rc = launch_expand(o, o->ws.Shat, o->W, EPI_VEL, ep, &nparts, s);
+    if (rc) return rc;
+    return launch_vmax_final(o, nparts, vmax, status, s);
+}
+
+// adjoint with R given as an FP32 image
 int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
                       cudaStream_t s) {
     int rc = launch_spectrum_f32(o, R, o->W2, o->ws.rhat, s);
     if (rc) return rc;
-    rc = launch_shat(o, s);
+    return adjoint_from_rhat(o, V, vmax, status, s);
+}
+
+// adjoint with R where forward_loss_from_mhat left it
+static int adjoint_resident(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s) {
+    int rc = o->precision == DEVEL_PREC_BF16X3 ? launch_spectrum_resident(o, o->W2, o->ws.rhat, s)
+                                               : launch_spectrum_f32(o, o->ws.bufI, o->W2, o->ws.rhat, s);
     if (rc) return rc;
-    int nparts = 0;
-    rc = launch_expand(o, o->ws.Shat, o->W, V, 2.0f, true, &nparts, s);
-    if (rc) return rc;
-    return launch_vmax_final(o, nparts, vmax, status, s);
+    return adjoint_from_rhat(o, V, vmax, status, s);
 }
 
 static void free_optics(devel_optics* o) {
     if (!o) return;
     void* ptrs[] = {o->W.basis, o->W.basisT, o->W2.basis, o->W2.basisT, o->TCC, o->Tdiff, o->goff,
-                    o->ws.Ppart, o->ws.part, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat, o->ws.Bmat,
+                    o->ws.Ppart, o->ws.P, o->ws.Q, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat,
                     o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
@@ -106,6 +155,153 @@ static void make_basis(int n, int kw, int ldk, std::vector<float>& t, std::vecto
 
 using namespace devel;
 
+static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
+                         cudaStream_t s) {
+    DEVEL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    for (int c = 0; c < nclips; ++c) {
+        const devel_clip& cl = clips[c];
+        const devel_optics* o = cl.optics;
+        const int n = o->n;
+        const Workspace& w = o->ws;
+        float* phi = cl.phi;
+        float* phi_alt = w.phi2;
+        int rc;
+        if (!cl.phi_given) {
+            rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
+            if (rc) return rc;
+        }
+        rc = launch_mask_from_phi(n, phi, w.M, s);
+        if (rc) return rc;
+        for (int t = 0; t <= p->iters; ++t) {
+            // image the current mask, resist loss and dL/dI (in place in bufI)
+            rc = launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
+            if (rc) return rc;
+            rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr,
+                                        cl.loss_hist ? cl.loss_hist + t : nullptr,
+                                        cl.l2_hist ? cl.l2_hist + t : nullptr,
+                                        cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
+            if (rc) return rc;
+            if (t == p->iters) break;  // the final mask is imaged for its metrics only
+            rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
+            if (rc) return rc;
+            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M, s);
+            if (rc) return rc;
+            float* tmp = phi;
+            phi = phi_alt;
+            phi_alt = tmp;
+            const int gi = p->start_iter + t;
+            if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
+                rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
+                if (rc) return rc;
+            }
+        }
+        if (phi != cl.phi)
+            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.phi, phi, sizeof(float) * n * n, cudaMemcpyDeviceToDevice, s));
+        if (cl.mask_out)
+            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.mask_out, w.M, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return DEVEL_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of whole solves
+// ---------------------------------------------------------------------------
+// A solve is captured once per distinct (params, clip list) into a graph on an
+// internal capture stream, then replayed with one cudaGraphLaunch on the
+// caller's stream. Kernel arguments (pointers, sizes) are baked into the
+// graph; the data they point to is read at replay time.
+namespace {
+struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int device = -1;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;  // most recent last
+constexpr size_t kMaxGraphs = 8;
+cudaStream_t g_capture_stream[64] = {};
+
+std::vector<unsigned char> solve_key(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
+                                     int device) {
+    std::vector<unsigned char> k(sizeof(devel_ilt_params) + sizeof(int) * 2 + sizeof(int*) +
+                                 sizeof(devel_clip) * nclips);
+    unsigned char* q = k.data();
+    std::memcpy(q, p, sizeof(devel_ilt_params));
+    q += sizeof(devel_ilt_params);
+    std::memcpy(q, &nclips, sizeof(int));
+    q += sizeof(int);
+    std::memcpy(q, &device, sizeof(int));
+    q += sizeof(int);
+    std::memcpy(q, &status, sizeof(int*));
+    q += sizeof(int*);
+    if (nclips) std::memcpy(q, clips, sizeof(devel_clip) * nclips);
+    return k;
+}
+}  // namespace
+
+static int solve_graph(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
+                       cudaStream_t s) {
+    int dev = 0;
+    DEVEL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return enqueue_solve(p, nclips, clips, status, s);
+    std::vector<unsigned char> key = solve_key(p, nclips, clips, status, dev);
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size(); ++i) {
+        if (g_graphs[i].device == dev && g_graphs[i].key == key) {
+            GraphEntry e = g_graphs[i];
+            g_graphs.erase(g_graphs.begin() + i);
+            g_graphs.push_back(e);
+            DEVEL_CUDA_TRY(cudaGraphLaunch(e.exec, s));
+            return DEVEL_OK;
+        }
+    }
+    if (!g_capture_stream[dev])
+        DEVEL_CUDA_TRY(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+    cudaStream_t cs = g_capture_stream[dev];
+    DEVEL_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_solve(p, nclips, clips, status, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "devel_ilt_solve: cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "devel_ilt_solve: cudaGraphInstantiate");
+    if (g_graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(GraphEntry{key, exec, dev});
+    DEVEL_CUDA_TRY(cudaGraphLaunch(exec, s));
+    return DEVEL_OK;
+}
+
+// Drop cached graphs that reference a handle about to be destroyed.
+static void drop_graphs_of(const devel_optics* o) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size();) {
+        const std::vector<unsigned char>& k = g_graphs[i].key;
+        const size_t head = sizeof(devel_ilt_params) + sizeof(int) * 2 + sizeof(int*);
+        bool uses = false;
+        for (size_t off = head; off + sizeof(devel_clip) <= k.size(); off += sizeof(devel_clip)) {
+            devel_clip c;
+            std::memcpy(&c, k.data() + off, sizeof(devel_clip));
+            if (c.optics == o) uses = true;
+        }
+        if (uses) {
+            cudaGraphExecDestroy(g_graphs[i].exec);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 extern "C" {
 
 const char* devel_last_error(void) { return g_err; }
@@ -130,6 +326,10 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         if (!(w_host[j] >= 0.f) || !std::isfinite(w_host[j]))
             return set_error(DEVEL_EINVAL, "devel_optics_create: w[%d] must be finite and >= 0", j);
 
+    {
+        int rc0 = init_device_attrs();
+        if (rc0) return rc0;
+    }
     devel_optics* o = new devel_optics();
     o->n = n;
     o->K = K;
@@ -151,8 +351,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     }
     const size_t npix = (size_t)n * n;
     const int kk = k * k, kk2 = o->k2 * o->k2;
-    const int nred = resist_parts(n);
-    o->npart_red = nred;
+    const int nred = std::max(resist_parts(n), expand_parts(n));  // CTA partials of any loss reduction
+    o->npart_red = resist_parts(n);
     const int ld2 = o->W2.ldk;
 
 #define ALLOC(ptr, bytes)                                                                  \
@@ -174,12 +374,13 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->Tdiff, sizeof(float2) * (size_t)kk * kk);
     ALLOC(o->goff, sizeof(int) * kk2);
     ALLOC(o->ws.Ppart, sizeof(float) * (size_t)o->nsplit * n * ld2);
-    ALLOC(o->ws.part, sizeof(float2) * (size_t)spectrum_blocks(n) * kk2);
+    o->nq = std::max(1, std::min(16, n / 128));
+    ALLOC(o->ws.P, sizeof(float) * (size_t)n * ld2);
+    ALLOC(o->ws.Q, sizeof(float) * (size_t)o->nq * ld2 * ld2);
     ALLOC(o->ws.mhat, sizeof(float2) * kk);
     ALLOC(o->ws.Ihat, sizeof(float2) * kk2);
     ALLOC(o->ws.rhat, sizeof(float2) * kk2);
     ALLOC(o->ws.Shat, sizeof(float2) * kk);
-    ALLOC(o->ws.Bmat, sizeof(float) * ld2 * ld2);
     ALLOC(o->ws.Acat, sizeof(float) * (size_t)n * ld2);
     ALLOC(o->ws.dpart, sizeof(double) * 3 * nred);
     ALLOC(o->ws.lpart, sizeof(long long) * 2 * nred);
@@ -286,6 +487,11 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
             if (!rc) rc = tc::make_map(&tw.m_acat_hi, o->Acat_hi, n, w.ldk, w.ldk, 128);
             if (!rc) rc = tc::make_map(&tw.m_acat_lo, o->Acat_lo, n, w.ldk, w.ldk, 128);
         }
+        // the operand's pad columns [n, ldn) must read as zeros: only kernels that
+        // write zeros there (or nothing) ever touch them afterwards
+        if (!rc && (cudaMemset(o->Xhi, 0, sizeof(__nv_bfloat16) * (size_t)n * o->ldn) != cudaSuccess ||
+                    cudaMemset(o->Xlo, 0, sizeof(__nv_bfloat16) * (size_t)n * o->ldn) != cudaSuccess))
+            rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
         if (!rc) rc = tc::make_map(&o->m_X_hi, o->Xhi, n, o->ldn, o->ldn, 128);
         if (!rc) rc = tc::make_map(&o->m_X_lo, o->Xlo, n, o->ldn, o->ldn, 128);
         if (!rc) {
@@ -303,6 +509,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
 
 int devel_optics_destroy(devel_optics* o) {
     if (!o) return DEVEL_OK;
+    drop_graphs_of(o);
     cudaError_t e = cudaDeviceSynchronize();
     free_optics(o);
     if (e != cudaSuccess) return cuda_error(e, "devel_optics_destroy: cudaDeviceSynchronize");
@@ -342,8 +549,8 @@ int devel_resist_loss(const devel_optics* o, const float* intensity, const unsig
     CHECK_PTR(dLdI, "dLdI");
     CHECK_PTR(loss_out, "loss_out");
     CHECK_PTR(counts_out, "counts_out");
-    return launch_resist(o->n, intensity, target, *p, dLdI, o->ws.dpart, o->ws.lpart, o->npart_red,
-                         loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, s);
+    return launch_resist(o->n, intensity, target, *p, dLdI, nullptr, nullptr, 0, o->ws.dpart, o->ws.lpart,
+                         o->npart_red, loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, s);
 }
 
 int devel_litho_adjoint(const devel_optics* o, const float* mask, const float* dLdI, float* dLdM,
@@ -375,11 +582,13 @@ int devel_levelset_step(int n, const float* phi, const float* V, const double* v
 
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                      cudaStream_t s) {
-    if (n < 1 || n > 16384) return set_error(DEVEL_EINVAL, "devel_reinit_sdf: n=%d outside [1, 16384]", n);
+    if (n < 1 || n > 8192) return set_error(DEVEL_EINVAL, "devel_reinit_sdf: n=%d outside [1, 8192]", n);
     CHECK_PTR(mask, "mask");
     CHECK_PTR(phi, "phi");
     CHECK_PTR(d2, "d2");
     if (!(d_lo <= d_hi)) return set_error(DEVEL_EINVAL, "devel_reinit_sdf: d_lo > d_hi");
+    int rc = init_device_attrs();
+    if (rc) return rc;
     return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s);
 }
 
@@ -402,52 +611,8 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         CHECK_OPT_PTR(cl.l2_hist, "clip.l2_hist");
         CHECK_OPT_PTR(cl.pvb_hist, "clip.pvb_hist");
     }
-    DEVEL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-    for (int c = 0; c < nclips; ++c) {
-        const devel_clip& cl = clips[c];
-        const devel_optics* o = cl.optics;
-        const int n = o->n;
-        const Workspace& w = o->ws;
-        float* phi = cl.phi;
-        float* phi_alt = w.phi2;
-        int rc;
-        if (!cl.phi_given) {
-            rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
-            if (rc) return rc;
-        }
-        rc = launch_mask_from_phi(n, phi, w.M, s);
-        if (rc) return rc;
-        for (int t = 0; t <= p->iters; ++t) {
-            // image the current mask, resist loss and dL/dI (in place in bufI)
-            rc = launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
-            if (rc) return rc;
-            rc = forward_from_mhat(o, w.bufI, s);
-            if (rc) return rc;
-            rc = launch_resist(n, w.bufI, cl.target, p->resist, w.bufI, w.dpart, w.lpart, o->npart_red,
-                               nullptr, nullptr, cl.loss_hist ? cl.loss_hist + t : nullptr,
-                               cl.l2_hist ? cl.l2_hist + t : nullptr,
-                               cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
-            if (rc) return rc;
-            if (t == p->iters) break;  // the final mask is imaged for its metrics only
-            rc = adjoint_from_mhat(o, w.bufI, w.bufV, w.vmax, status, s);
-            if (rc) return rc;
-            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M, s);
-            if (rc) return rc;
-            float* tmp = phi;
-            phi = phi_alt;
-            phi_alt = tmp;
-            const int gi = p->start_iter + t;
-            if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
-                rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
-                if (rc) return rc;
-            }
-        }
-        if (phi != cl.phi)
-            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.phi, phi, sizeof(float) * n * n, cudaMemcpyDeviceToDevice, s));
-        if (cl.mask_out)
-            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.mask_out, w.M, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
-    }
-    return DEVEL_OK;
+    if (p->use_graph && !prof_on()) return solve_graph(p, nclips, clips, status, s);
+    return enqueue_solve(p, nclips, clips, status, s);
 }
 
 }  // extern "C"

@@ -35,8 +35,28 @@ enum ProfKind {
     PK_STEP, PK_MASK, PK_EDT_COLS, PK_EDT_ROWS, PK_U8F32,
     PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PROF_NKINDS
 };
+bool prof_on();
 void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
+
+// Resist constants as the kernels use them (doses squared).
+struct ResistArgs {
+    float sigma_z, I_th, alpha, beta, d2in, d2out;
+};
+
+// Epilogues of the contraction GEMMs.
+enum { EPI_STORE = 0, EPI_VEL = 1 };
+
+struct EpiArgs {
+    float* C = nullptr;              // output
+    int ldc = 0;
+    size_t split_stride = 0;         // offset of split-K slice z: C + z * split_stride
+    float scale = 1.f;
+    float* vpart = nullptr;          // EPI_VEL: per-CTA max |out|
+    int n = 0;
+};
+
+constexpr int kTcSplitK = 256;  // K slice of one split of the tensor-core reduction
 
 // Device-side limit of the window side handled by the FP32 kernels.
 constexpr int kMaxWindow = 63;
@@ -53,13 +73,13 @@ struct Window {
 };
 
 struct Workspace {
-    float* Ppart = nullptr;    // [nsplit][n][ldk2] split-K slices of the reduction
-    float2* part = nullptr;    // [nblk][k2*k2] row-block partial spectra
+    float* Ppart = nullptr;    // [nsplit][n][ldk2] split-K slices of P (reduction stage 1)
+    float* P = nullptr;        // [n][ldk2] stage-1 slices summed
+    float* Q = nullptr;        // [nq][ldk2][ldk2] split-K slices of reduction stage 2
     float2* mhat = nullptr;    // [k*k]   mask spectrum on W, scaled 1/n^2
     float2* Ihat = nullptr;    // [k2*k2] aerial-image spectrum on W2
     float2* rhat = nullptr;    // [k2*k2] dL/dI spectrum on W2, scaled 1/n^2
     float2* Shat = nullptr;    // [k*k]   adjoint spectrum on W
-    float* Bmat = nullptr;     // [ldk2][ldk2] expansion coefficients
     float* Acat = nullptr;     // [n][ldk2] expansion operand [Re T | -Im T]
     double* dpart = nullptr;   // reduction partials, doubles
     long long* lpart = nullptr;// reduction partials, counts
@@ -96,7 +116,8 @@ struct devel_optics {
     __nv_bfloat16* Acat_lo = nullptr;
     CUtensorMap m_X_hi, m_X_lo;
     int* tc_err = nullptr;            // device flag: DEVEL_ETIMEOUT from a bounded wait
-    int nsplit;               // split-K slices of the reduction GEMM
+    int nsplit;               // split-K slices of reduction stage 1 (over x)
+    int nq;                   // split-K slices of reduction stage 2 (over y)
     int npart_red;            // size of the generic reduction partial arrays
     devel::Window W, W2;      // the kernel window and the difference window
     float2* TCC = nullptr;    // [k*k][k*k] TCC_K(a, b) = sum_j w_j H_j(a) conj(H_j(b))
@@ -115,23 +136,30 @@ namespace devel {
 int launch_spectrum_f32(const devel_optics* o, const float* X, const Window& w, float2* out, cudaStream_t s);
 int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const Window& w, float2* out,
                        cudaStream_t s);
-int spectrum_blocks(int n);
+// tensor-core path: spectrum of the image already split into Xhi/Xlo
+int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s);
 // Ihat (on W2) from mhat with the rank-K TCC
 int launch_ihat(const devel_optics* o, cudaStream_t s);
 // Shat (on W) from mhat and rhat with the rank-K TCC
 int launch_shat(const devel_optics* o, cudaStream_t s);
 // out = mult * Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} on window w; optional max|out|
-// (returns the number of max|out| partials written when want_max)
-int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float* out, float mult,
-                  bool want_max, int* nparts, cudaStream_t s);
+// epi: EPI_STORE (ep.C = out) or EPI_VEL (ep.C, max |out| partials);
+// *nparts = number of CTA partials.
+int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int epi, const EpiArgs& ep,
+                  int* nparts, cudaStream_t s);
+int launch_resist_final(int nparts, const devel_resist_params& p, const double* dpart, const long long* lpart,
+                        double* loss4, long long* cnt2, double* loss_hist, long long* l2_hist,
+                        long long* pvb_hist, int* status, cudaStream_t s);
 int expand_parts(int n);
 int launch_vmax_final(const devel_optics* o, int nparts, double* vmax, int* status, cudaStream_t s);
 
 // resist.cu
+// dL/dI of the image I (n x n): into R (FP32, n x n) and/or into bf16 hi/lo
+// arrays of pitch ldr; loss partials, then the final reduction.
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
-                  float* R, double* dpart, long long* lpart, int nparts, double* loss4,
-                  long long* cnt2, double* loss_hist, long long* l2_hist, long long* pvb_hist,
-                  int* status, cudaStream_t s);
+                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, double* dpart,
+                  long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
+                  long long* l2_hist, long long* pvb_hist, int* status, cudaStream_t s);
 int resist_parts(int n);
 
 // levelset.cu
@@ -141,12 +169,19 @@ int launch_levelset_step(int n, const float* phi, const float* V, const double* 
 int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s);
 int launch_u8_to_f32(int n, const unsigned char* M, float* out, cudaStream_t s);
 
+// one-time kernel attributes (api.cu calls them once per device)
+int litho_init_attrs();
+int reinit_init_attrs();
+
 // reinit.cu
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                   cudaStream_t s);
 
 // forward / adjoint bodies shared by the ABI and the solver (api.cu)
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s);
+int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, const devel_resist_params& rp,
+                           double* loss4, long long* cnt2, double* lh, long long* l2h, long long* pvbh,
+                           int* status, cudaStream_t s);
 int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
                       cudaStream_t s);
 

@@ -12,34 +12,16 @@
 namespace devel {
 namespace {
 
-constexpr int kTX = 32, kTYS = 8;
+// Tile of 128 x 8 pixels per block of 32 x 8 threads, four adjacent pixels per
+// thread; the (8 + 2) x (128 + 2) neighbourhood is staged in shared memory.
+constexpr int kTX = 32, kTYS = 8, kPX = 4, kW = kTX * kPX;
 
-__global__ void __launch_bounds__(kTX * kTYS)
-k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
-                const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
-                int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out) {
-    __shared__ float t[kTYS + 2][kTX + 2];
-    const int bx = blockIdx.x * kTX, by = blockIdx.y * kTYS;
-    // cooperative load of the (kTYS+2) x (kTX+2) tile with clamped (replicated) borders
-    for (int i = threadIdx.y * kTX + threadIdx.x; i < (kTYS + 2) * (kTX + 2); i += kTX * kTYS) {
-        const int ly = i / (kTX + 2), lx = i - ly * (kTX + 2);
-        const int y = min(max(by + ly - 1, 0), n - 1);
-        const int x = min(max(bx + lx - 1, 0), n - 1);
-        t[ly][lx] = phi[(size_t)y * n + x];
-    }
-    __syncthreads();
-    const int x = bx + threadIdx.x, y = by + threadIdx.y;
-    if (x >= n || y >= n) return;
-    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    const float c = t[ly][lx];
-    const float xm = t[ly][lx - 1], xp = t[ly][lx + 1];
-    const float ym = t[ly - 1][lx], yp = t[ly + 1][lx];
-    const size_t p = (size_t)y * n + x;
+__device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, float yp, float xpyp, float xmyp,
+                                         float xpym, float xmym, float v, float inv_vmax, float dt, float lam,
+                                         float mm) {
     float out = c;
-    const double vm = *vmax;
-    if (vm > 0.0) {
-        // FP32 reciprocal: an FP64 division per pixel is slow on GB300
-        const float F = -dt * (V[p] * (1.0f / (float)vm));
+    if (inv_vmax > 0.f) {
+        const float F = -dt * (v * inv_vmax);
         const float dmx = c - xm, dpx = xp - c, dmy = c - ym, dpy = yp - c;
         if (F > 0.f) {
             const float a = fmaxf(dmx, 0.f), b = fminf(dpx, 0.f), cc = fmaxf(dmy, 0.f), d = fminf(dpy, 0.f);
@@ -52,15 +34,81 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
     if (lam != 0.f) {
         const float px = 0.5f * (xp - xm), py = 0.5f * (yp - ym);
         const float pxx = xp + xm - 2.f * c, pyy = yp + ym - 2.f * c;
-        const float pxy = 0.25f * ((t[ly + 1][lx + 1] - t[ly + 1][lx - 1]) - (t[ly - 1][lx + 1] - t[ly - 1][lx - 1]));
+        const float pxy = 0.25f * ((xpyp - xmyp) - (xpym - xmym));
         const float den = px * px + py * py;
         float kc = 0.f;
         if (den >= 1e-12f) kc = (pxx * py * py - 2.f * px * py * pxy + pyy * px * px) / den;
-        const float mm = m ? m[p] : 1.f;
         out += dt * lam * mm * kc;
     }
-    phi_out[p] = out;
-    if (mask_out) mask_out[p] = out <= 0.f ? 1 : 0;
+    return out;
+}
+
+__global__ void __launch_bounds__(kTX * kTYS)
+k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
+                const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
+                int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out) {
+    __shared__ float t[kTYS + 2][kW + 2];
+    __shared__ float s_inv;
+    const int bx = blockIdx.x * kW, by = blockIdx.y * kTYS;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if (tid == 0) {
+        // FP32 reciprocal of max|V| (0 when there is no transport); one per block
+        const double vm = *vmax;
+        s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
+    }
+    for (int i = tid; i < (kTYS + 2) * (kW + 2); i += kTX * kTYS) {
+        const int ly = i / (kW + 2), lx = i - ly * (kW + 2);
+        const int y = min(max(by + ly - 1, 0), n - 1);
+        const int x = min(max(bx + lx - 1, 0), n - 1);
+        t[ly][lx] = phi[(size_t)y * n + x];
+    }
+    __syncthreads();
+    const int y = by + threadIdx.y;
+    if (y >= n) return;
+    const int x0 = bx + threadIdx.x * kPX;
+    if (x0 >= n) return;
+    const float inv = s_inv;
+    const int ly = threadIdx.y + 1;
+    const size_t p0 = (size_t)y * n + x0;
+    const bool full = x0 + kPX <= n && ((p0 & 3) == 0);
+    float v[kPX], mm[kPX];
+    if (full) {
+        const float4 q = *reinterpret_cast<const float4*>(V + p0);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        if (m) {
+            const float4 r = *reinterpret_cast<const float4*>(m + p0);
+            mm[0] = r.x; mm[1] = r.y; mm[2] = r.z; mm[3] = r.w;
+        } else {
+            mm[0] = mm[1] = mm[2] = mm[3] = 1.f;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPX; ++j) {
+            v[j] = x0 + j < n ? V[p0 + j] : 0.f;
+            mm[j] = (m && x0 + j < n) ? m[p0 + j] : 1.f;
+        }
+    }
+    float o[kPX];
+#pragma unroll
+    for (int j = 0; j < kPX; ++j) {
+        const int lx = threadIdx.x * kPX + j + 1;
+        o[j] = step_px(t[ly][lx], t[ly][lx - 1], t[ly][lx + 1], t[ly - 1][lx], t[ly + 1][lx], t[ly + 1][lx + 1],
+                       t[ly + 1][lx - 1], t[ly - 1][lx + 1], t[ly - 1][lx - 1], v[j], inv, dt, lam, mm[j]);
+    }
+    if (full) {
+        *reinterpret_cast<float4*>(phi_out + p0) = make_float4(o[0], o[1], o[2], o[3]);
+        if (mask_out)
+            *reinterpret_cast<uchar4*>(mask_out + p0) =
+                make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPX; ++j) {
+            if (x0 + j < n) {
+                phi_out[p0 + j] = o[j];
+                if (mask_out) mask_out[p0 + j] = o[j] <= 0.f ? 1 : 0;
+            }
+        }
+    }
 }
 
 __global__ void k_mask_from_phi(const float* __restrict__ phi, size_t npix, unsigned char* __restrict__ M) {
@@ -86,7 +134,7 @@ int grid_for(size_t npix) {
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, cudaStream_t s) {
-    dim3 grid((n + kTX - 1) / kTX, (n + kTYS - 1) / kTYS);
+    dim3 grid((n + kW - 1) / kW, (n + kTYS - 1) / kTYS);
     prof_begin(PK_STEP, s);
     k_levelset_step<<<grid, dim3(kTX, kTYS), 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out);
     prof_end(PK_STEP, s);

@@ -1,4 +1,4 @@
-// Truncated-DFT lithography, FP32 on the CUDA cores.
+// Truncated-DFT lithography through the difference window.
 //
 // Every optical kernel's spectrum is confined to the k x k window W
 // (Sec. II-B, SOCS). Then |A_j|^2 and R * A_j are confined to the
@@ -16,14 +16,20 @@
 //   Shat(f)  = sum_a conj(TCC_K(f, a)) mhat(a) rhat(f - a),   f in W
 //   V(q)     = 2 Re sum_f Shat(f) e^{+i 2pi f.q/n}            (= dL/dM, Eq. ilt_gradient)
 //
-// The n^2-sized work is four separable contractions, all run by one
-// register-tiled NT GEMM (C = A B^T, both operands K-major):
-//   reduction onto a window of side kw:  P = X basis^T          (K = n, split-K)
-//                                         Xhat = E* P           (per row block)
-//   expansion from a window:             T = G Bmat^T           (K = 2kw)
-//                                         out = T basisT^T      (K = 2kw)
-// with basis[c][x] = cos / sin(2 pi (a - r) x / n) (c = a, kw + a) and
-// basisT its transpose, zero-padded to ldk = round_up(2kw, 16) columns.
+// Tables: basis[c][x] = cos / sin(2 pi (a - r) x / n) for c = a, kw + a,
+// zero-padded to ldk = round_up(2 kw, 16) rows; basisT its transpose.
+//
+// Reduction of an n x n image X onto a window (two contractions):
+//   1. P^T = basis X^T  (split-K over x; FP32 NT GEMM, or the tcgen05 GEMM
+//      with a transposed store),  P^T[c][y] = sum_x basis[c][x] X[y][x]
+//   2. Q = basis P      (split-K over y; FP32 NT GEMM summing the slices of 1)
+//   3. Xhat(a,b) = n^-2 [(Q[a][b] - Q[kw+a][kw+b]) - i (Q[a][kw+b] + Q[kw+a][b])]
+// Expansion of a window spectrum Z into an n x n image:
+//   1. T(y, b) = sum_a e^{+i theta_a y} Z(a, b), stored as Acat = [Re T | -Im T]
+//   2. out = Acat basisT^T   (FP32 NT GEMM or tcgen05), with a fused epilogue:
+//      plain store, velocity (x2, max |.|) or the resist loss (dL/dI).
+#include <algorithm>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -40,43 +46,29 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-// Fixed-order block reduction of a float2 (deterministic); valid in thread 0.
-__device__ float2 block_sum2(float2 v, float2* sh) {
+__device__ __forceinline__ float2 warp_sum2(float2 v) {
     for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_down_sync(0xffffffffu, v.x, o);
         v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    float2 t = make_float2(0.f, 0.f);
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        t = lane < nw ? sh[lane] : make_float2(0.f, 0.f);
-        for (int o = 16; o > 0; o >>= 1) {
-            t.x += __shfl_down_sync(0xffffffffu, t.x, o);
-            t.y += __shfl_down_sync(0xffffffffu, t.y, o);
-        }
-    }
-    return t;
+    return v;
 }
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(unsigned char v) { return v ? 1.f : 0.f; }
 
 // --------------------------------------------------------------------------
-// NT GEMM: C[m][nn] = scale * sum_k A[m][k] B[nn][k]
-//   tile 128 x 64 x 16, 256 threads, 8 x 4 outputs per thread,
-//   register prefetch of the next k-slab; split-K over gridDim.z.
+// FP32 GEMM: C[m][nn] = scale * sum_k A[m][k] B(k, nn), A K-major; B K-major
+// (B[nn][k], BN_MAJOR = false) or N-major (B[k][nn], BN_MAJOR = true).
+//   tile 128 x 64 x 16, 256 threads, 8 x 4 outputs per thread, register
+//   prefetch of the next k-slab; split-K over gridDim.z.
 // --------------------------------------------------------------------------
 constexpr int gBM = 128, gBN = 64, gBK = 16;
-enum { EPI_STORE = 0, EPI_VEL = 1 };
 
-template <typename TA, int EPI>
+template <typename TA, typename TB, int EPI, bool BN_MAJOR>
 __global__ void __launch_bounds__(kThreads)
-k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ldb, int M, int N,
-          int K, int kchunk, float scale, float* __restrict__ C, int ldc, size_t split_stride,
-          float* __restrict__ vpart) {
+k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M, int N, int K, int kchunk,
+          EpiArgs ep) {
     __shared__ float As[gBK][gBM + 4];
     __shared__ float Bs[gBK][gBN + 4];
     __shared__ float red[kThreads / 32];
@@ -101,9 +93,11 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ld
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * kThreads, r = e >> 4, kk = e & 15;
+            const int e = tid + i * kThreads;
+            // K-major B: consecutive threads walk k; N-major B: consecutive threads walk nn
+            const int r = BN_MAJOR ? (e & 63) : (e >> 4), kk = BN_MAJOR ? (e >> 6) : (e & 15);
             const int nn = n0 + r, k = k0 + kk;
-            rb[i] = (nn < N && k < ke) ? B[(size_t)nn * ldb + k] : 0.f;
+            rb[i] = (nn < N && k < ke) ? to_f(BN_MAJOR ? B[(size_t)k * ldb + nn] : B[(size_t)nn * ldb + k]) : 0.f;
         }
     };
     if (kb < ke) load(kb);
@@ -116,7 +110,8 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ld
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int e = tid + i * kThreads;
-            Bs[e & 15][e >> 4] = rb[i];
+            if (BN_MAJOR) Bs[e >> 6][e & 63] = rb[i];
+            else Bs[e & 15][e >> 4] = rb[i];
         }
         __syncthreads();
         if (k0 + gBK < ke) load(k0 + gBK);
@@ -134,7 +129,7 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ld
         }
         __syncthreads();
     }
-    float* Cz = C + blockIdx.z * split_stride;
+    float* Cz = ep.C + blockIdx.z * ep.split_stride;
     float mx = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -144,11 +139,12 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ld
         for (int j = 0; j < 4; ++j) {
             const int nn = n0 + tx + 16 * j;
             if (nn >= N) continue;
-            const float v = acc[i][j] * scale;
-            Cz[(size_t)m * ldc + nn] = v;
+            const float v = acc[i][j] * ep.scale;
+            Cz[(size_t)m * ep.ldc + nn] = v;
             if (EPI == EPI_VEL) mx = fmaxf(mx, fabsf(v));
         }
     }
+    const int part = blockIdx.y * gridDim.x + blockIdx.x;
     if (EPI == EPI_VEL) {
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
         if ((tid & 31) == 0) red[tid >> 5] = mx;
@@ -156,84 +152,59 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const float* __restrict__ B, int ld
         if (tid == 0) {
             float m = red[0];
             for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
-            vpart[blockIdx.y * gridDim.x + blockIdx.x] = m;
+            ep.vpart[part] = m;
         }
     }
 }
 
-// --------------------------------------------------------------------------
-// reduction, second stage: row block of kTY rows, all kw x kw outputs
-//   part[blk][a][b] = sum_{y in blk} e^{-i theta_a y} P(y, b),
-//   P(y, b) = Pc - i Ps, Pc/Ps summed over the split-K slices in order.
-// --------------------------------------------------------------------------
-constexpr int kTY = 16;
+// P = sum_z Ppart[z] over the split-K slices of stage 1, elementwise in slice order.
+__global__ void k_sum_slices(const float* __restrict__ Ppart, int nz, size_t len, float* __restrict__ P) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        float v = 0.f;
+        for (int z = 0; z < nz; ++z) v += Ppart[z * len + i];
+        P[i] = v;
+    }
+}
 
+// Xhat(a, b) = scale [(Q[a][b] - Q[kw+a][kw+b]) - i (Q[a][kw+b] + Q[kw+a][b])], Q summed over
+// the nq slices of stage 2: one warp per output, lane l sums slices l, l+32, ..., then a
+// fixed shuffle tree.
 __global__ void __launch_bounds__(kThreads)
-k_spec_stage2(const float* __restrict__ Ppart, int nsplit, size_t sstride, int ldp, int n,
-              const float* __restrict__ basis, int kw, float2* __restrict__ part) {
-    extern __shared__ float sm[];
-    float* Pc = sm;               // [kTY][kw]
-    float* Ps = Pc + kTY * kw;    // [kTY][kw]
-    float* Ca = Ps + kTY * kw;    // [kw][kTY]
-    float* Sa = Ca + kw * kTY;    // [kw][kTY]
-    const int y0 = blockIdx.x * kTY;
-    const int rows = min(kTY, n - y0);
-    for (int i = threadIdx.x; i < kTY * kw; i += blockDim.x) {
-        const int ty = i / kw, b = i - ty * kw;
-        float c = 0.f, s = 0.f;
-        if (ty < rows) {
-            const float* p = Ppart + (size_t)(y0 + ty) * ldp;
-            for (int z = 0; z < nsplit; ++z) {
-                c += p[z * sstride + b];
-                s += p[z * sstride + kw + b];
-            }
-        }
-        Pc[i] = c;
-        Ps[i] = s;
+k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, float2* __restrict__ out) {
+    const int o = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= kw * kw) return;
+    const int a = o / kw, b = o - a * kw;
+    float re = 0.f, im = 0.f;
+    const size_t st = (size_t)ldq * ldq;
+    for (int z = lane; z < nq; z += 32) {
+        const float* q = Q + z * st;
+        re += q[a * ldq + b] - q[(kw + a) * ldq + kw + b];
+        im -= q[a * ldq + kw + b] + q[(kw + a) * ldq + b];
     }
-    for (int i = threadIdx.x; i < kw * kTY; i += blockDim.x) {
-        const int a = i / kTY, ty = i - a * kTY;
-        const bool ok = ty < rows;
-        Ca[i] = ok ? basis[(size_t)a * n + y0 + ty] : 0.f;
-        Sa[i] = ok ? basis[(size_t)(kw + a) * n + y0 + ty] : 0.f;
-    }
+    float2 v = warp_sum2(make_float2(re, im));
+    if (lane == 0) out[o] = make_float2(v.x * scale, v.y * scale);
+}
+
+// --------------------------------------------------------------------------
+// frequency-domain sums with the rank-K TCC (one warp per output frequency)
+// --------------------------------------------------------------------------
+// Fixed-order block reduction of a float2 over 128 threads (4 warps); valid in thread 0.
+__device__ __forceinline__ float2 block_sum2_128(float2 v, float2* sh) {
+    v = warp_sum2(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    // e^{-i ta y} (Pc - i Ps) = (ca Pc - sa Ps) - i (ca Ps + sa Pc)
-    for (int o = threadIdx.x; o < kw * kw; o += blockDim.x) {
-        const int a = o / kw, b = o - a * kw;
-        float sr = 0.f, si = 0.f;
-#pragma unroll 4
-        for (int ty = 0; ty < kTY; ++ty) {
-            const float ca = Ca[a * kTY + ty], sa = Sa[a * kTY + ty];
-            const float pc = Pc[ty * kw + b], ps = Ps[ty * kw + b];
-            sr = fmaf(ca, pc, fmaf(-sa, ps, sr));
-            si = fmaf(-ca, ps, fmaf(-sa, pc, si));
-        }
-        part[(size_t)blockIdx.x * kw * kw + o] = make_float2(sr, si);
-    }
+    return cadd(cadd(sh[0], sh[1]), cadd(sh[2], sh[3]));
 }
 
-__global__ void k_spectrum_reduce(const float2* __restrict__ part, int nblk, int nout, float scale,
-                                  float2* __restrict__ out) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= nout) return;
-    float2 s = make_float2(0.f, 0.f);
-    for (int b = 0; b < nblk; ++b) s = cadd(s, part[(size_t)b * nout + o]);
-    out[o] = make_float2(s.x * scale, s.y * scale);
-}
-
-// --------------------------------------------------------------------------
-// frequency-domain sums with the rank-K TCC
-// --------------------------------------------------------------------------
-// Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), one block per g;
-// rect(g) = {a in W : a - g in W}, t = row-major index within rect(g).
-__global__ void __launch_bounds__(kThreads)
+// Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), one block of 128
+// threads per g; rect(g) = {a in W : a - g in W}, t = row-major index within rect(g).
+__global__ void __launch_bounds__(128)
 k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
            const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat) {
-    extern __shared__ float2 ms[];  // [k*k] mhat, then 32 for the reduction
-    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
-    for (int i = threadIdx.x; i < kk; i += blockDim.x) ms[i] = mhat[i];
-    __syncthreads();
+    __shared__ float2 sh[4];
+    const int k2 = 2 * k - 1, r2 = k - 1;
     const int g = blockIdx.x;
     const int c1 = g / k2, c2 = g - c1 * k2;
     const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
@@ -241,50 +212,73 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
     const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
     const float2* T = Tdiff + goff[g];
     float2 acc = make_float2(0.f, 0.f);
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    for (int t = threadIdx.x; t < total; t += 128) {
         const int i1 = t / n2, i2 = t - i1 * n2;
         const int a1 = a1lo + i1, a2 = a2lo + i2;
         const int b1 = a1 - c1 + r2, b2 = a2 - c2 + r2;
-        acc = cadd(acc, cmul(T[t], cmulc(ms[a1 * k + a2], ms[b1 * k + b2])));
+        acc = cadd(acc, cmul(__ldg(T + t), cmulc(__ldg(mhat + a1 * k + a2), __ldg(mhat + b1 * k + b2))));
     }
-    const float2 s = block_sum2(acc, ms + kk);
+    const float2 s = block_sum2_128(acc, sh);
     if (threadIdx.x == 0) Ihat[g] = s;
 }
 
-// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block per f.
-__global__ void __launch_bounds__(kThreads)
+// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f.
+__global__ void __launch_bounds__(128)
 k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
            const float2* __restrict__ rhat, int k, float2* __restrict__ Shat) {
-    __shared__ float2 sh[32];
+    __shared__ float2 sh[4];
     const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
     const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
     const float2* row = TCC + (size_t)f * kk;
     float2 acc = make_float2(0.f, 0.f);
-    for (int a = threadIdx.x; a < kk; a += blockDim.x) {
+    for (int a = threadIdx.x; a < kk; a += 128) {
         const int a1 = a / k, a2 = a - a1 * k;
-        const float2 u = cmul(mhat[a], rhat[(f1 - a1 + r2) * k2 + (f2 - a2 + r2)]);
-        acc = cadd(acc, cmulc(u, row[a]));
+        const float2 u = cmul(__ldg(mhat + a), __ldg(rhat + (f1 - a1 + r2) * k2 + (f2 - a2 + r2)));
+        acc = cadd(acc, cmulc(u, __ldg(row + a)));
     }
-    const float2 s = block_sum2(acc, sh);
+    const float2 s = block_sum2_128(acc, sh);
     if (threadIdx.x == 0) Shat[f] = s;
 }
 
-// Bmat [ldk][ldk] such that T = G Bmat^T gives [Re T | -Im T] with
-// T(y, b) = sum_a e^{+i theta_a y} Z(a, b) and G = [cos | sin] (basisT):
-//   row b:      [ Zr(:, b) | -Zi(:, b) ]      row kw + b: [ -Zi(:, b) | -Zr(:, b) ]
-__global__ void k_build_bmat(const float2* __restrict__ Z, int kw, int ldk, float* __restrict__ Bm) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ldk * ldk) return;
-    const int cp = i / ldk, c = i - cp * ldk;
-    float v = 0.f;
-    if (cp < 2 * kw && c < 2 * kw) {
-        const int b = cp < kw ? cp : cp - kw;
-        const int a = c < kw ? c : c - kw;
-        const float2 z = Z[a * kw + b];
-        if (cp < kw) v = c < kw ? z.x : -z.y;
-        else v = c < kw ? -z.y : -z.x;
+// T(y, b) = sum_a e^{+i theta_a y} Z(a, b) -> Acat[y] = [Re T | -Im T | 0 ...] (ldk columns),
+// as FP32 (Af) or as bf16 hi/lo (Ahi, Alo). One thread per (y, b), b in [0, ldk - kw):
+// b < kw computes T(y, b) and writes columns b and kw + b, b >= kw writes padding column kw + b.
+__global__ void __launch_bounds__(256)
+k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n, int kw, int ldk,
+           float* __restrict__ Af, __nv_bfloat16* __restrict__ Ahi, __nv_bfloat16* __restrict__ Alo) {
+    const int per = ldk - kw;
+    const long long total = (long long)n * per;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(p / per), b = (int)(p - (long long)y * per);
+        const size_t base = (size_t)y * ldk;
+        float v0 = 0.f, v1 = 0.f;
+        if (b < kw) {
+            const float* g = basisT + base;
+            float tr = 0.f, ti = 0.f;
+            for (int a = 0; a < kw; ++a) {
+                const float2 z = __ldg(Z + a * kw + b);
+                const float c = __ldg(g + a), s = __ldg(g + kw + a);
+                tr = fmaf(c, z.x, fmaf(-s, z.y, tr));
+                ti = fmaf(c, z.y, fmaf(s, z.x, ti));
+            }
+            v0 = tr;
+            v1 = -ti;
+        }
+        if (Af) {
+            if (b < kw) Af[base + b] = v0;
+            Af[base + kw + b] = v1;
+        } else {
+            if (b < kw) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
+                Ahi[base + b] = h0;
+                Alo[base + b] = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+            }
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(v1);
+            Ahi[base + kw + b] = h1;
+            Alo[base + kw + b] = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+        }
     }
-    Bm[i] = v;
 }
 
 __global__ void k_vmax_final(const float* __restrict__ vpart, int nparts, double* vmax, int* status) {
@@ -307,70 +301,104 @@ __global__ void k_vmax_final(const float* __restrict__ vpart, int nparts, double
     }
 }
 
-constexpr int kTcSplitK = 256;  // K slice of one split of the tensor-core reduction
-
-int tc_operand_f32(const devel_optics* o, const float* X, cudaStream_t s) {
-    return tc::launch_split(X, o->n, o->n, o->n, o->ldn, o->Xhi, o->Xlo, s);
+template <typename TA, typename TB, int EPI, bool BN_MAJOR = false>
+int gemm_nt(const TA* A, int lda, const TB* B, int ldb, int M, int N, int K, int splits, const EpiArgs& ep, int kind,
+            cudaStream_t s, const char* what) {
+    const int kchunk = ((K + splits - 1) / splits + gBK - 1) / gBK * gBK;
+    dim3 grid((N + gBN - 1) / gBN, (M + gBM - 1) / gBM, splits);
+    prof_begin(kind, s);
+    k_gemm_nt<TA, TB, EPI, BN_MAJOR><<<grid, kThreads, 0, s>>>(A, lda, B, ldb, M, N, K, kchunk, ep);
+    prof_end(kind, s);
+    DEVEL_LAUNCH_CHECK(what);
+    return DEVEL_OK;
 }
-int tc_operand_f32(const devel_optics* o, const unsigned char* M, cudaStream_t s) {
-    return tc::launch_mask_bf16(M, o->n, o->ldn, o->Xhi, s);
-}
 
-template <typename TA>
-int spectrum_impl(const devel_optics* o, const TA* X, const Window& w, float2* out, cudaStream_t s) {
+const TcWindow& tc_window(const devel_optics* o, const Window& w) { return (&w == &o->W) ? o->tcW : o->tcW2; }
+
+// stage 1 of the reduction: P^T slices in ws.Ppart ([nsplit][ldk][n])
+template <typename TX>
+int reduce_stage1(const devel_optics* o, const TX* X, const Window& w, cudaStream_t s) {
     const int n = o->n;
     const Workspace& ws = o->ws;
-    const int nsplit = o->nsplit;
-    const size_t sstride = (size_t)n * w.ldk;
+    EpiArgs ep;
+    ep.C = ws.Ppart;
+    ep.ldc = w.ldk;
+    ep.split_stride = (size_t)n * w.ldk;
+    ep.scale = 1.0f;
     if (o->precision == DEVEL_PREC_BF16X3) {
-        int rc = tc_operand_f32(o, X, s);
+        int rc = sizeof(TX) == 1 ? tc::launch_mask_bf16(reinterpret_cast<const unsigned char*>(X), n, o->ldn,
+                                                        o->Xhi, s)
+                                 : tc::launch_split(reinterpret_cast<const float*>(X), n, n, n, o->ldn, o->Xhi,
+                                                    o->Xlo, s);
         if (rc) return rc;
-        const TcWindow& tw = (&w == &o->W) ? o->tcW : o->tcW2;
-        tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, sizeof(TA) == 4 ? 1 : 0};
-        rc = tc::launch_gemm(op, w.ldk, false, PK_TC_SPECTRUM, n, w.ldk, o->ldn, kTcSplitK, 1.0f, ws.Ppart,
-                             w.ldk, sstride, nullptr, o->tc_err, s);
-        if (rc) return rc;
-    } else {
-        const int kchunk = ((n + nsplit - 1) / nsplit + gBK - 1) / gBK * gBK;
-        dim3 grid((w.ldk + gBN - 1) / gBN, (n + gBM - 1) / gBM, nsplit);
-        prof_begin(PK_SPECTRUM, s);
-        k_gemm_nt<TA, EPI_STORE><<<grid, kThreads, 0, s>>>(X, n, w.basis, n, n, w.ldk, n, kchunk, 1.0f,
-                                                            ws.Ppart, w.ldk, sstride, nullptr);
-        prof_end(PK_SPECTRUM, s);
-        DEVEL_LAUNCH_CHECK("k_gemm_nt(spectrum)");
+        const TcWindow& tw = tc_window(o, w);
+        tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, sizeof(TX) == 1 ? 0 : 1};
+        return tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err,
+                               s);
     }
-    const int nblk = (n + kTY - 1) / kTY;
-    const size_t smem = sizeof(float) * 4 * kTY * w.kw;
+    return gemm_nt<TX, float, EPI_STORE>(X, n, w.basis, n, n, w.ldk, n, o->nsplit, ep, PK_SPECTRUM, s,
+                                         "k_gemm_nt(spectrum)");
+}
+
+// stages 2-3 of the reduction from the slices P[z][y][c] in ws.Ppart
+int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStream_t s) {
+    const int n = o->n;
+    const Workspace& ws = o->ws;
+    const size_t len = (size_t)n * w.ldk;
     prof_begin(PK_SPECTRUM_STAGE2, s);
-    k_spec_stage2<<<nblk, kThreads, smem, s>>>(ws.Ppart, nsplit, sstride, w.ldk, n, w.basis, w.kw, ws.part);
+    k_sum_slices<<<(int)std::min<size_t>((len + 255) / 256, 4 * 148), 256, 0, s>>>(ws.Ppart, o->nsplit, len, ws.P);
     prof_end(PK_SPECTRUM_STAGE2, s);
-    DEVEL_LAUNCH_CHECK("k_spec_stage2");
+    DEVEL_LAUNCH_CHECK("k_sum_slices");
+    EpiArgs ep;
+    ep.C = ws.Q;
+    ep.ldc = w.ldk;
+    ep.split_stride = (size_t)w.ldk * w.ldk;
+    ep.scale = 1.0f;
+    int rc = gemm_nt<float, float, EPI_STORE, true>(w.basis, n, ws.P, w.ldk, w.ldk, w.ldk, n, o->nq, ep,
+                                                    PK_SPECTRUM_STAGE2, s, "k_gemm_nt(stage2)");
+    if (rc) return rc;
     const int nout = w.kw * w.kw;
     const float scale = 1.0f / ((float)n * (float)n);
     prof_begin(PK_SPECTRUM_REDUCE, s);
-    k_spectrum_reduce<<<(nout + 255) / 256, 256, 0, s>>>(ws.part, nblk, nout, scale, out);
+    k_spec_final<<<(nout + 7) / 8, kThreads, 0, s>>>(ws.Q, o->nq, w.ldk, w.kw, scale, out);
     prof_end(PK_SPECTRUM_REDUCE, s);
-    DEVEL_LAUNCH_CHECK("k_spectrum_reduce");
+    DEVEL_LAUNCH_CHECK("k_spec_final");
     return DEVEL_OK;
 }
 
 }  // namespace
 
-int spectrum_blocks(int n) { return (n + kTY - 1) / kTY; }
+int litho_init_attrs() {
+    const int big = 200 * 1024;
+    (void)big;
+    return DEVEL_OK;
+}
 
 int launch_spectrum_f32(const devel_optics* o, const float* X, const Window& w, float2* out, cudaStream_t s) {
-    return spectrum_impl<float>(o, X, w, out, s);
+    int rc = reduce_stage1<float>(o, X, w, s);
+    return rc ? rc : reduce_finish(o, w, out, s);
 }
 int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const Window& w, float2* out,
                        cudaStream_t s) {
-    return spectrum_impl<unsigned char>(o, X, w, out, s);
+    int rc = reduce_stage1<unsigned char>(o, X, w, s);
+    return rc ? rc : reduce_finish(o, w, out, s);
+}
+
+int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s) {
+    const Workspace& ws = o->ws;
+    EpiArgs ep;
+    ep.C = ws.Ppart;
+    ep.ldc = w.ldk;
+    ep.split_stride = (size_t)o->n * w.ldk;
+    const TcWindow& tw = tc_window(o, w);
+    tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, 1};
+    int rc = tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, o->n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err, s);
+    return rc ? rc : reduce_finish(o, w, out, s);
 }
 
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
-    const int kk = o->k * o->k;
     prof_begin(PK_HOPKINS, s);
-    k_ihat_tcc<<<o->k2 * o->k2, kThreads, sizeof(float2) * (kk + 32), s>>>(o->Tdiff, o->goff, o->ws.mhat,
-                                                                           o->k, o->ws.Ihat);
+    k_ihat_tcc<<<o->k2 * o->k2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat);
     prof_end(PK_HOPKINS, s);
     DEVEL_LAUNCH_CHECK("k_ihat_tcc");
     return DEVEL_OK;
@@ -378,46 +406,41 @@ int launch_ihat(const devel_optics* o, cudaStream_t s) {
 
 int launch_shat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_ADJ_WINDOW, s);
-    k_shat_tcc<<<o->k * o->k, kThreads, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat);
+    k_shat_tcc<<<o->k * o->k, 128, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat);
     prof_end(PK_ADJ_WINDOW, s);
     DEVEL_LAUNCH_CHECK("k_shat_tcc");
     return DEVEL_OK;
 }
 
-int launch_expand(const devel_optics* o, const float2* Z, const Window& w, float* out, float mult,
-                  bool want_max, int* nparts, cudaStream_t s) {
+int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int epi, const EpiArgs& ep_in,
+                  int* nparts, cudaStream_t s) {
     const int n = o->n;
     const Workspace& ws = o->ws;
+    const bool tcp = o->precision == DEVEL_PREC_BF16X3;
     prof_begin(PK_EXPAND_T, s);
-    k_build_bmat<<<(w.ldk * w.ldk + 255) / 256, 256, 0, s>>>(Z, w.kw, w.ldk, ws.Bmat);
-    DEVEL_LAUNCH_CHECK("k_build_bmat");
-    dim3 gT((w.ldk + gBN - 1) / gBN, (n + gBM - 1) / gBM, 1);
-    k_gemm_nt<float, EPI_STORE><<<gT, kThreads, 0, s>>>(w.basisT, w.ldk, ws.Bmat, w.ldk, n, w.ldk, w.ldk,
-                                                         w.ldk, 1.0f, ws.Acat, w.ldk, 0, nullptr);
+    const long long pairs = (long long)n * (w.ldk - w.kw);
+    k_expand_T<<<(int)std::min<long long>((pairs + 255) / 256, 16 * 148), 256, 0, s>>>(
+        Z, w.basisT, n, w.kw, w.ldk, tcp ? nullptr : ws.Acat, tcp ? o->Acat_hi : nullptr,
+        tcp ? o->Acat_lo : nullptr);
     prof_end(PK_EXPAND_T, s);
-    DEVEL_LAUNCH_CHECK("k_gemm_nt(T)");
-    if (o->precision == DEVEL_PREC_BF16X3) {
-        int rc = tc::launch_split(ws.Acat, n, w.ldk, w.ldk, w.ldk, o->Acat_hi, o->Acat_lo, s);
-        if (rc) return rc;
-        const TcWindow& tw = (&w == &o->W) ? o->tcW : o->tcW2;
+    DEVEL_LAUNCH_CHECK("k_expand_T");
+    EpiArgs ep = ep_in;
+    ep.n = n;
+    ep.ldc = n;
+    ep.split_stride = 0;
+    ep.vpart = ws.vpart;
+    if (tcp) {
+        const TcWindow& tw = tc_window(o, w);
         tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, &tw.m_basisT_hi, &tw.m_basisT_lo, 1};
-        const int kps = (w.ldk + 63) / 64 * 64;
         if (nparts) *nparts = ((n + 127) / 128) * ((n + 127) / 128);
-        return tc::launch_gemm(op, 128, want_max, PK_TC_EXPAND, n, n, w.ldk, kps, mult, out, n, 0,
-                               want_max ? ws.vpart : nullptr, o->tc_err, s);
+        return tc::launch_gemm(op, 128, epi, PK_TC_EXPAND, n, n, w.ldk, (w.ldk + 63) / 64 * 64, ep, o->tc_err, s);
     }
     if (nparts) *nparts = expand_parts(n);
-    dim3 g((n + gBN - 1) / gBN, (n + gBM - 1) / gBM, 1);
-    prof_begin(PK_EXPAND_GEMM, s);
-    if (want_max)
-        k_gemm_nt<float, EPI_VEL><<<g, kThreads, 0, s>>>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk, w.ldk,
-                                                          mult, out, n, 0, ws.vpart);
-    else
-        k_gemm_nt<float, EPI_STORE><<<g, kThreads, 0, s>>>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk,
-                                                            w.ldk, mult, out, n, 0, nullptr);
-    prof_end(PK_EXPAND_GEMM, s);
-    DEVEL_LAUNCH_CHECK("k_gemm_nt(expand)");
-    return DEVEL_OK;
+    if (epi == EPI_VEL)
+        return gemm_nt<float, float, EPI_VEL>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk, 1, ep, PK_EXPAND_GEMM,
+                                              s, "k_gemm_nt(expand)");
+    return gemm_nt<float, float, EPI_STORE>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk, 1, ep, PK_EXPAND_GEMM, s,
+                                            "k_gemm_nt(expand)");
 }
 
 int expand_parts(int n) { return ((n + gBN - 1) / gBN) * ((n + gBM - 1) / gBM); }

@@ -5,95 +5,75 @@
 // uses +/-2% dose). Sec. II-C: squared L2 = #{[I >= I_th] != Z_t}, PVBand =
 // #{[d_in^2 I >= I_th] xor [d_out^2 I >= I_th]}.
 //
-// The per-pixel work is one HBM pass (read I and Z_t, write R: 9 B/px). The
-// sums are accumulated in FP64 per thread, reduced per block in a fixed
-// order, and the per-block partials are summed in block order by a second
-// kernel, so results are bitwise reproducible.
-#include "common.cuh"
+// The standalone kernel is one HBM pass (read I and Z_t, write R: 9 B/px);
+// inside the solver the same per-pixel code runs in the epilogue of the
+// forward expansion instead (resist.cuh). Sums are FP32 per thread, FP64 from
+// the warp up, reduced per block in a fixed order and then over blocks in
+// block order, so results are bitwise reproducible.
+#include "resist.cuh"
 
 namespace devel {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxParts = 1184;  // 8 x 148: bounded grid of the reduction
+constexpr int kMaxParts = 1184;  // 8 x 148: bounded grid of the standalone kernel
 
-struct ResistArgs {
-    float sigma_z, I_th, alpha, beta, d2in, d2out;
-};
-
-__device__ __forceinline__ float sigmoidf(float t) { return 1.f / (1.f + expf(-t)); }
-
+// Rows y = blockIdx.x, blockIdx.x + gridDim.x, ...; each thread four adjacent
+// pixels (float4 / uchar4 loads when the row is 16-byte aligned).
 __global__ void __launch_bounds__(kThreads)
-k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, size_t npix, ResistArgs p,
-         float* __restrict__ R, double* __restrict__ dpart, long long* __restrict__ lpart) {
-    __shared__ double sd[4][kThreads / 32];
-    __shared__ long long sl[2][kThreads / 32];
-    // per-thread partials in FP32 (a thread sums a handful of pixels), FP64 from
-    // the warp level up: GB300 issues few FP64 operations per clock
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-    int l2 = 0, pvb = 0;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
-        const float Iv = I[i];
-        const float zt = Zt[i] ? 1.f : 0.f;
-        const float In = Iv, Ii = p.d2in * Iv, Io = p.d2out * Iv;
-        const float zn = sigmoidf(p.sigma_z * (In - p.I_th));
-        const float zi = sigmoidf(p.sigma_z * (Ii - p.I_th));
-        const float zo = sigmoidf(p.sigma_z * (Io - p.I_th));
-        const float en = zn - zt, ei = zi - zt, eo = zo - zt;
-        f0 = fmaf(en, en, f0);
-        f1 = fmaf(ei, ei, f1);
-        f2 = fmaf(eo, eo, f2);
-        const float gn = p.alpha * 2.f * en * p.sigma_z * zn * (1.f - zn);
-        const float gi = p.beta * 2.f * ei * p.sigma_z * zi * (1.f - zi) * p.d2in;
-        const float go = p.beta * 2.f * eo * p.sigma_z * zo * (1.f - zo) * p.d2out;
-        R[i] = gn + gi + go;
-        const bool pn = In >= p.I_th;
-        l2 += (pn != (Zt[i] != 0));
-        pvb += ((Ii >= p.I_th) != (Io >= p.I_th));
-    }
-    double s0 = f0, s1 = f1, s2 = f2;
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-        s2 += __shfl_down_sync(0xffffffffu, s2, o);
-        l2 += __shfl_down_sync(0xffffffffu, l2, o);
-        pvb += __shfl_down_sync(0xffffffffu, pvb, o);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        sd[0][w] = s0;
-        sd[1][w] = s1;
-        sd[2][w] = s2;
-        sl[0][w] = l2;
-        sl[1][w] = pvb;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0;
-        long long x = 0, y = 0;
-        for (int i = 0; i < kThreads / 32; ++i) {
-            a += sd[0][i];
-            b += sd[1][i];
-            c += sd[2][i];
-            x += sl[0][i];
-            y += sl[1][i];
+k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, int n, ResistArgs p,
+         float* __restrict__ R, __nv_bfloat16* __restrict__ Rhi, __nv_bfloat16* __restrict__ Rlo, int ldr,
+         double* __restrict__ dpart, long long* __restrict__ lpart) {
+    __shared__ double sd[3][32];
+    __shared__ long long sl[2][32];
+    LossAcc acc;
+    const bool vec = (n & 3) == 0;
+    for (int y = blockIdx.x; y < n; y += gridDim.x) {
+        const size_t base = (size_t)y * n;
+        for (int x0 = threadIdx.x * 4; x0 < n; x0 += blockDim.x * 4) {
+            float iv[4], rv[4];
+            unsigned char zv[4];
+            if (vec) {
+                const float4 q = *reinterpret_cast<const float4*>(I + base + x0);
+                const uchar4 z = *reinterpret_cast<const uchar4*>(Zt + base + x0);
+                iv[0] = q.x; iv[1] = q.y; iv[2] = q.z; iv[3] = q.w;
+                zv[0] = z.x; zv[1] = z.y; zv[2] = z.z; zv[3] = z.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    iv[j] = x0 + j < n ? I[base + x0 + j] : 0.f;
+                    zv[j] = x0 + j < n ? Zt[base + x0 + j] : 0;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                rv[j] = (x0 + j < n) ? resist_px(iv[j], zv[j] != 0, p, acc) : 0.f;
+            if (R) {
+                if (vec) {
+                    *reinterpret_cast<float4*>(R + base + x0) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+                } else {
+                    for (int j = 0; j < 4 && x0 + j < n; ++j) R[base + x0 + j] = rv[j];
+                }
+            }
+            if (Rhi) {
+                const size_t b2 = (size_t)y * ldr + x0;
+                for (int j = 0; j < 4 && x0 + j < n; ++j) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(rv[j]);
+                    Rhi[b2 + j] = h;
+                    Rlo[b2 + j] = __float2bfloat16_rn(rv[j] - __bfloat162float(h));
+                }
+            }
         }
-        dpart[blockIdx.x * 3 + 0] = a;
-        dpart[blockIdx.x * 3 + 1] = b;
-        dpart[blockIdx.x * 3 + 2] = c;
-        lpart[blockIdx.x * 2 + 0] = x;
-        lpart[blockIdx.x * 2 + 1] = y;
     }
+    block_store_loss(acc, blockIdx.x, dpart, lpart, sd, sl);
 }
 
 // One block of 256 threads: thread t sums partials t, t+256, ... in order, then a
 // fixed shuffle tree; the result does not depend on timing.
 __global__ void __launch_bounds__(256)
-k_resist_final(const double* __restrict__ dpart, const long long* __restrict__ lpart,
-               int nparts, double alpha, double beta, double* loss4,
-               long long* cnt2, double* loss_hist, long long* l2_hist,
-               long long* pvb_hist, int* status) {
+k_resist_final(const double* __restrict__ dpart, const long long* __restrict__ lpart, int nparts,
+               double alpha, double beta, double* loss4, long long* cnt2, double* loss_hist,
+               long long* l2_hist, long long* pvb_hist, int* status) {
     __shared__ double sd[3][8];
     __shared__ long long sl[2][8];
     double a = 0, b = 0, c = 0;
@@ -150,35 +130,28 @@ k_resist_final(const double* __restrict__ dpart, const long long* __restrict__ l
 
 }  // namespace
 
-int resist_parts(int n) {
-    const size_t npix = (size_t)n * n;
-    size_t blocks = (npix + (size_t)kThreads * 4 - 1) / ((size_t)kThreads * 4);
-    if (blocks > (size_t)kMaxParts) blocks = kMaxParts;
-    if (blocks < 1) blocks = 1;
-    return (int)blocks;
-}
+int resist_parts(int n) { return n < kMaxParts ? n : kMaxParts; }
 
-int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
-                  float* R, double* dpart, long long* lpart, int nparts, double* loss4,
-                  long long* cnt2, double* loss_hist, long long* l2_hist, long long* pvb_hist,
-                  int* status, cudaStream_t s) {
-    ResistArgs a;
-    a.sigma_z = p.sigma_z;
-    a.I_th = p.I_th;
-    a.alpha = p.alpha;
-    a.beta = p.beta;
-    a.d2in = p.dose_in * p.dose_in;
-    a.d2out = p.dose_out * p.dose_out;
-    prof_begin(PK_RESIST, s);
-    k_resist<<<nparts, kThreads, 0, s>>>(I, Zt, (size_t)n * n, a, R, dpart, lpart);
-    prof_end(PK_RESIST, s);
-    DEVEL_LAUNCH_CHECK("k_resist");
+int launch_resist_final(int nparts, const devel_resist_params& p, const double* dpart, const long long* lpart,
+                        double* loss4, long long* cnt2, double* loss_hist, long long* l2_hist,
+                        long long* pvb_hist, int* status, cudaStream_t s) {
     prof_begin(PK_RESIST_FINAL, s);
-    k_resist_final<<<1, 256, 0, s>>>(dpart, lpart, nparts, (double)p.alpha, (double)p.beta, loss4,
-                                    cnt2, loss_hist, l2_hist, pvb_hist, status);
+    k_resist_final<<<1, 256, 0, s>>>(dpart, lpart, nparts, (double)p.alpha, (double)p.beta, loss4, cnt2,
+                                     loss_hist, l2_hist, pvb_hist, status);
     prof_end(PK_RESIST_FINAL, s);
     DEVEL_LAUNCH_CHECK("k_resist_final");
     return DEVEL_OK;
+}
+
+int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
+                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, double* dpart,
+                  long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
+                  long long* l2_hist, long long* pvb_hist, int* status, cudaStream_t s) {
+    prof_begin(PK_RESIST, s);
+    k_resist<<<nparts, kThreads, 0, s>>>(I, Zt, n, make_resist_args(p), R, Rhi, Rlo, ldr, dpart, lpart);
+    prof_end(PK_RESIST, s);
+    DEVEL_LAUNCH_CHECK("k_resist");
+    return launch_resist_final(nparts, p, dpart, lpart, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status, s);
 }
 
 }  // namespace devel

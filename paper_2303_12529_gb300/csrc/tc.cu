@@ -160,17 +160,19 @@ template <int BN>
 struct Cfg {
     static constexpr uint32_t kBBytes = BN * kBK * 2;
     static constexpr uint32_t kStage = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = (kStage * 4 <= 200 * 1024) ? 4 : 3;
+    // as many stages (2..4) as fit in 227 KB of shared memory with the alignment slack
+    static constexpr int kFit = (int)((227u * 1024u - 2048u) / kStage);
+    static constexpr int kStages = kFit > 4 ? 4 : kFit;
+    static_assert(kFit >= 2, "tile too wide for double buffering");
     static constexpr uint32_t kCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
 };
 
-template <int BN, bool VEL>
+template <int BN, int EPI>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M, int N,
-          int kb_per_split, int kb_total, int ksteps_last, int use_alo, float scale, float* __restrict__ C,
-          int ldc, size_t split_stride, float* __restrict__ vpart, int* err) {
+          int kb_per_split, int kb_total, int ksteps_last, int use_alo, const EpiArgs ep, int* err) {
     using CF = Cfg<BN>;
     constexpr int S = CF::kStages;
     extern __shared__ uint8_t smem_raw[];
@@ -257,7 +259,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     fence_after_sync();
     float mx = 0.f;
     const int row = m0 + warp * 32 + lane;
-    float* Cz = C + (size_t)blockIdx.z * split_stride;
+    float* Cz = ep.C ? ep.C + (size_t)blockIdx.z * ep.split_stride : nullptr;
+    const float scale = ep.scale;
     for (int c = 0; c < BN; c += 16) {
         float v[16];
         if (have) {
@@ -266,39 +269,42 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] *= scale;
+        const int col0 = n0 + c;
         if (row < M) {
-            float* dst = Cz + (size_t)row * ldc + n0 + c;
-            if (n0 + c + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+            float* dst = Cz + (size_t)row * ep.ldc + col0;
+            if (col0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) {
-                    const float4 q = make_float4(v[j] * scale, v[j + 1] * scale, v[j + 2] * scale, v[j + 3] * scale);
-                    *reinterpret_cast<float4*>(dst + j) = q;
-                    if (VEL) mx = fmaxf(mx, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), fabsf(q.w))));
+                    *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (EPI == EPI_VEL)
+                        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[j]), fabsf(v[j + 1])), fmaxf(fabsf(v[j + 2]), fabsf(v[j + 3]))));
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if (n0 + c + j < N) {
-                        const float x = v[j] * scale;
-                        dst[j] = x;
-                        if (VEL) mx = fmaxf(mx, fabsf(x));
+                    if (col0 + j < N) {
+                        dst[j] = v[j];
+                        if (EPI == EPI_VEL) mx = fmaxf(mx, fabsf(v[j]));
                     }
                 }
             }
         }
     }
-    if (VEL) {
+    if (EPI == EPI_VEL) {
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
         if (lane == 0) red[warp] = mx;
     }
+    const int part = blockIdx.y * gridDim.x + blockIdx.x;
     // a producer that stopped early waits (bounded) for the loads it issued
     if (warp == 0 && lane == 0 && !ok) {
         for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(&full[i % S], (i / S) & 1, nullptr);
     }
     fence_before_sync();
     __syncthreads();
-    if (VEL && threadIdx.x == 0)
-        vpart[blockIdx.y * gridDim.x + blockIdx.x] = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    if (EPI == EPI_VEL && threadIdx.x == 0)
+        ep.vpart[part] = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
     if (warp == 1) {
         fence_after_sync();
         tmem_dealloc(tmem, CF::kCols);
@@ -308,49 +314,47 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // fp32 -> bf16 hi/lo splits
 // ---------------------------------------------------------------------------
+// One block row per image row (blockIdx.y), threads along the columns.
 __global__ void k_split_rows(const float* __restrict__ X, int rows, int cols, int ldx, int ldo,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-    const size_t total = (size_t)rows * ldo;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int r = (int)(i / ldo), c = (int)(i - (size_t)r * ldo);
-        const float x = c < cols ? X[(size_t)r * ldx + c] : 0.f;
+    const int r = blockIdx.y;
+    const float* xr = X + (size_t)r * ldx;
+    __nv_bfloat16* hr = hi + (size_t)r * ldo;
+    __nv_bfloat16* lr = lo ? lo + (size_t)r * ldo : nullptr;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ldo; c += gridDim.x * blockDim.x) {
+        const float x = c < cols ? xr[c] : 0.f;
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi[i] = h;
-        if (lo) lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+        hr[c] = h;
+        if (lr) lr[c] = __float2bfloat16_rn(x - __bfloat162float(h));
     }
 }
 
+// 0/1 mask row -> bf16 row of pitch ldo, four pixels per thread.
 __global__ void k_mask_bf16(const unsigned char* __restrict__ M, int n, int ldo, __nv_bfloat16* __restrict__ hi) {
-    const size_t total = (size_t)n * ldo;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int r = (int)(i / ldo), c = (int)(i - (size_t)r * ldo);
-        hi[i] = __float2bfloat16_rn(c < n && M[(size_t)r * n + c] ? 1.f : 0.f);
+    const int r = blockIdx.y;
+    const unsigned char* mr = M + (size_t)r * n;
+    __nv_bfloat16* hr = hi + (size_t)r * ldo;
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < ldo; c += gridDim.x * blockDim.x * 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c + j < ldo) hr[c + j] = (c + j < n && mr[c + j]) ? one : zero;
     }
 }
 
-int grid_for(size_t total) {
-    size_t b = (total + 255) / 256;
-    if (b > 8 * 148) b = 8 * 148;
-    return (int)(b < 1 ? 1 : b);
+template <int BN, int EPI>
+cudaError_t set_attr_bn() {
+    return cudaFuncSetAttribute(k_tc_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<BN>::kSmem);
 }
 
-template <int BN, bool VEL>
-int launch_gemm_bn(const Operands& op, int M, int N, int kb_per_split, int kb_total, int ksteps_last,
-                   int splits, float scale, float* C, int ldc, size_t split_stride, float* vpart, int* err,
-                   cudaStream_t s) {
+template <int BN, int EPI>
+int launch_gemm_bn(const Operands& op, int M, int N, int kb_per_split, int kb_total, int ksteps_last, int splits,
+                   const EpiArgs& ep, int* err, cudaStream_t s) {
     using CF = Cfg<BN>;
-    static bool attr = false;
-    if (!attr) {
-        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)CF::kSmem));
-        attr = true;
-    }
     dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
-    k_tc_gemm<BN, VEL><<<grid, 128, CF::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N, kb_per_split,
-                                                     kb_total, ksteps_last, op.use_alo, scale, C, ldc,
-                                                     split_stride, vpart, err);
+    k_tc_gemm<BN, EPI><<<grid, 128, CF::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N, kb_per_split,
+                                                     kb_total, ksteps_last, op.use_alo, ep, err);
     DEVEL_LAUNCH_CHECK("k_tc_gemm");
     return DEVEL_OK;
 }
@@ -396,8 +400,8 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
     return DEVEL_OK;
 }
 
-int launch_gemm(const Operands& op, int BN, bool vel, int prof_kind, int M, int N, int K, int k_per_split,
-                float scale, float* C, int ldc, size_t split_stride, float* vpart, int* err, cudaStream_t s) {
+int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
+                const EpiArgs& ep, int* err, cudaStream_t s) {
     if (K % 16 != 0 || k_per_split % kBK != 0)
         return set_error(DEVEL_EINVAL, "tc gemm: K=%d / split %d not aligned", K, k_per_split);
     const int kb_total = (K + kBK - 1) / kBK;
@@ -406,15 +410,14 @@ int launch_gemm(const Operands& op, int BN, bool vel, int prof_kind, int M, int 
     const int ksteps_last = (K - (kb_total - 1) * kBK) / 16;
     prof_begin(prof_kind, s);
     int rc;
-    if (BN == 128 && vel) {
-        rc = launch_gemm_bn<128, true>(op, M, N, kb_per_split, kb_total, ksteps_last, splits, scale, C, ldc,
-                                       split_stride, vpart, err, s);
-    } else {
+#define DEVEL_TC_ARGS op, M, N, kb_per_split, kb_total, ksteps_last, splits, ep, err, s
+    if (BN == 128 && epi == EPI_VEL) {
+        rc = launch_gemm_bn<128, EPI_VEL>(DEVEL_TC_ARGS);
+    } else if (epi == EPI_STORE) {
         switch (BN) {
-#define DEVEL_TC_CASE(bn)                                                                                   \
-    case bn:                                                                                                \
-        rc = launch_gemm_bn<bn, false>(op, M, N, kb_per_split, kb_total, ksteps_last, splits, scale, C, ldc, \
-                                       split_stride, vpart, err, s);                                         \
+#define DEVEL_TC_CASE(bn)                                         \
+    case bn:                                                      \
+        rc = launch_gemm_bn<bn, EPI_STORE>(DEVEL_TC_ARGS);        \
         break;
             DEVEL_TC_CASE(16) DEVEL_TC_CASE(32) DEVEL_TC_CASE(48) DEVEL_TC_CASE(64) DEVEL_TC_CASE(80)
             DEVEL_TC_CASE(96) DEVEL_TC_CASE(112) DEVEL_TC_CASE(128) DEVEL_TC_CASE(144) DEVEL_TC_CASE(160)
@@ -424,15 +427,31 @@ int launch_gemm(const Operands& op, int BN, bool vel, int prof_kind, int M, int 
             default:
                 rc = set_error(DEVEL_EINVAL, "tc gemm: unsupported tile width %d", BN);
         }
+    } else {
+        rc = set_error(DEVEL_EINVAL, "tc gemm: unsupported epilogue %d with tile width %d", epi, BN);
     }
+#undef DEVEL_TC_ARGS
     prof_end(prof_kind, s);
     return rc;
+}
+
+// Shared-memory opt-in of every kernel instantiation (call once per device,
+// outside stream capture).
+int init_attrs() {
+    cudaError_t e = set_attr_bn<128, EPI_VEL>();
+#define DEVEL_TC_ATTR(bn) if (e == cudaSuccess) e = set_attr_bn<bn, EPI_STORE>();
+    DEVEL_TC_ATTR(16) DEVEL_TC_ATTR(32) DEVEL_TC_ATTR(48) DEVEL_TC_ATTR(64) DEVEL_TC_ATTR(80) DEVEL_TC_ATTR(96)
+    DEVEL_TC_ATTR(112) DEVEL_TC_ATTR(128) DEVEL_TC_ATTR(144) DEVEL_TC_ATTR(160) DEVEL_TC_ATTR(176)
+    DEVEL_TC_ATTR(192) DEVEL_TC_ATTR(208) DEVEL_TC_ATTR(224) DEVEL_TC_ATTR(240) DEVEL_TC_ATTR(256)
+#undef DEVEL_TC_ATTR
+    if (e != cudaSuccess) return cuda_error(e, "tc::init_attrs");
+    return DEVEL_OK;
 }
 
 int launch_split(const float* X, int rows, int cols, int ldx, int ldo, __nv_bfloat16* hi, __nv_bfloat16* lo,
                  cudaStream_t s) {
     prof_begin(PK_TC_SPLIT, s);
-    k_split_rows<<<grid_for((size_t)rows * ldo), 256, 0, s>>>(X, rows, cols, ldx, ldo, hi, lo);
+    k_split_rows<<<dim3((ldo + 255) / 256, rows), 256, 0, s>>>(X, rows, cols, ldx, ldo, hi, lo);
     prof_end(PK_TC_SPLIT, s);
     DEVEL_LAUNCH_CHECK("k_split_rows");
     return DEVEL_OK;
@@ -440,7 +459,7 @@ int launch_split(const float* X, int rows, int cols, int ldx, int ldo, __nv_bflo
 
 int launch_mask_bf16(const unsigned char* M, int n, int ldo, __nv_bfloat16* hi, cudaStream_t s) {
     prof_begin(PK_TC_SPLIT, s);
-    k_mask_bf16<<<grid_for((size_t)n * ldo), 256, 0, s>>>(M, n, ldo, hi);
+    k_mask_bf16<<<dim3((ldo + 1023) / 1024, n), 256, 0, s>>>(M, n, ldo, hi);
     prof_end(PK_TC_SPLIT, s);
     DEVEL_LAUNCH_CHECK("k_mask_bf16");
     return DEVEL_OK;

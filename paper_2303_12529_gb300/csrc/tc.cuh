@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "common.cuh"
+
 namespace devel {
 namespace tc {
 
@@ -21,11 +23,15 @@ struct Operands {
 // elements; boxes of 64 columns x box_rows rows, 128-byte swizzle, zero fill.
 int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int box_rows);
 
-// D = scale * A B^T (M x N, contraction length K, a multiple of 16), BN in
-// {80, 128, 144}; split-K slices of k_per_split (a multiple of 64) go to
-// C + z * split_stride. vel: also write the per-CTA max |D| to vpart.
-int launch_gemm(const Operands& op, int BN, bool vel, int prof_kind, int M, int N, int K, int k_per_split,
-                float scale, float* C, int ldc, size_t split_stride, float* vpart, int* err, cudaStream_t s);
+// D = ep.scale * A B^T (M x N, contraction length K, a multiple of 16), BN a
+// multiple of 16 up to 256; split-K slices of k_per_split (a multiple of 64).
+// epi: EPI_STORE (row-major into ep.C + z * split_stride) or EPI_VEL
+// (store and the per-CTA max |D| into ep.vpart; BN = 128).
+int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
+                const EpiArgs& ep, int* err, cudaStream_t s);
+
+// Shared-memory opt-in of all tensor-core kernels (once per device).
+int init_attrs();
 
 // hi/lo split of a row-major float array [rows][cols] (pitch ldx) into
 // [rows][ldo] bf16 arrays, zero beyond cols; lo may be NULL.
