@@ -267,15 +267,24 @@ int devel_ilt_solve(const devel_ilt_params* params, int nclips, const devel_clip
  * Open a profile: until devel_profile_stop, every kernel launch of the
  * library is bracketed by two CUDA events on its stream (at most `capacity`
  * launches; events are created here, on the host, not on the hot path).
- * Not for use during stream capture. One profile at a time per process.
+ * A solve captured into a graph meanwhile records the events inside the
+ * graph (such graphs are dropped when the profile closes). One profile at a
+ * time per process.
  */
 int devel_profile_start(int capacity);
-/* Close the profile, wait for its events and accumulate per-kernel times. */
+/*
+ * Wait for the events recorded so far and add their launch counts and times
+ * to the per-kernel totals. With kernel-by-kernel launches call it once before
+ * devel_profile_stop; a solve captured into a CUDA graph while the profile is
+ * open records its events on every replay, so call it after each replay.
+ */
+int devel_profile_collect(void);
+/* Close the profile (the totals stay readable). */
 int devel_profile_stop(void);
 /* Number of kernel classes. */
 int devel_profile_kinds(void);
 /* Name, launch count and summed device time (ms) of kernel class `kind`
- * in the last closed profile. */
+ * accumulated by devel_profile_collect. */
 int devel_profile_query(int kind, const char** name, int* launches, double* total_ms);
 
 #ifdef __cplusplus

@@ -84,6 +84,7 @@ _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(de
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
 _sig("devel_profile_start", [_I])
 _sig("devel_profile_stop", [])
+_sig("devel_profile_collect", [])
 _sig("devel_profile_kinds", [])
 _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                              ctypes.POINTER(ctypes.c_double)])
@@ -92,7 +93,7 @@ _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER
 EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_optics_destroy",
             "devel_optics_n", "devel_optics_check", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
-            "devel_profile_stop", "devel_profile_kinds", "devel_profile_query",
+            "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static")
 REINIT_STATIC_MAX_N = 2048
 
@@ -276,8 +277,16 @@ def devel_profile_start(capacity: int = 1 << 16):
     _check(_lib.devel_profile_start(capacity))
 
 
-def devel_profile_stop() -> dict:
-    """Close the profile; returns {kernel: (launches, total_ms)} for kernels that ran."""
+def devel_profile_collect():
+    """Accumulate the events recorded so far (after each graph replay, or once)."""
+    _check(_lib.devel_profile_collect())
+
+
+def devel_profile_stop(collect: bool = True) -> dict:
+    """Close the profile (collecting first unless collect=False); returns
+    {kernel: (launches, total_ms)} for kernels that ran."""
+    if collect:
+        _check(_lib.devel_profile_collect())
     _check(_lib.devel_profile_stop())
     out = {}
     for k in range(_lib.devel_profile_kinds()):

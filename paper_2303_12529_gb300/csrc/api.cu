@@ -81,7 +81,7 @@ int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, c
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
     return launch_resist(o->n, o->ws.bufI, target, rp, tcp ? nullptr : o->ws.bufI, tcp ? o->Xhi : nullptr,
                          tcp ? o->Xlo : nullptr, o->ldn, o->ws.dpart, o->ws.lpart, o->npart_red, loss4, cnt2, lh,
-                         l2h, pvbh, status, s);
+                         l2h, pvbh, status, o->ws.counters, s);
 }
 
 // adjoint from ws.mhat (spectrum of the imaged mask) and the spectrum rhat of R
@@ -91,10 +91,10 @@ static int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int*
     EpiArgs ep;
     ep.C = V;
     ep.scale = 2.0f;
-    int nparts = 0;
-    rc = launch_expand(o, o->ws.Shat, o->W, EPI_VEL, ep, &nparts, s);
-    if (rc) return rc;
-    return launch_vmax_final(o, nparts, vmax, status, s);
+    ep.counter = o->ws.counters + 1;
+    ep.vmax = vmax;
+    ep.status = status;
+    return launch_expand(o, o->ws.Shat, o->W, EPI_VEL, ep, nullptr, s);
 }
 
 // adjoint with R given as an FP32 image
@@ -121,7 +121,7 @@ static void free_optics(devel_optics* o) {
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
                     o->tcW2.basis_hi, o->tcW2.basis_lo, o->tcW2.basisT_hi, o->tcW2.basisT_lo,
-                    o->Xhi, o->Xlo, o->Acat_hi, o->Acat_lo, o->tc_err};
+                    o->Xhi, o->Xlo, o->Acat_hi, o->Acat_lo, o->tc_err, o->ws.counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete o;
@@ -170,11 +170,16 @@ static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip
             rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
             if (rc) return rc;
         }
+        const bool tcp = o->precision == DEVEL_PREC_BF16X3;
         rc = launch_mask_from_phi(n, phi, w.M, s);
         if (rc) return rc;
+        if (tcp) {  // later masks come out of the level-set step already in bf16
+            rc = tc::launch_mask_bf16(w.M, n, o->ldn, o->Xhi, s);
+            if (rc) return rc;
+        }
         for (int t = 0; t <= p->iters; ++t) {
             // image the current mask, resist loss and dL/dI (in place in bufI)
-            rc = launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
+            rc = tcp ? launch_spectrum_mask_resident(o, o->W, w.mhat, s) : launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
             if (rc) return rc;
             rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr,
                                         cl.loss_hist ? cl.loss_hist + t : nullptr,
@@ -184,7 +189,8 @@ static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip
             if (t == p->iters) break;  // the final mask is imaged for its metrics only
             rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
             if (rc) return rc;
-            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M, s);
+            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
+                                      tcp ? o->Xhi : nullptr, o->ldn, s);
             if (rc) return rc;
             float* tmp = phi;
             phi = phi_alt;
@@ -222,6 +228,9 @@ std::vector<GraphEntry> g_graphs;  // most recent last
 constexpr size_t kMaxGraphs = 8;
 cudaStream_t g_capture_stream[64] = {};
 
+// A graph captured while a profile is open records the profiler's events; it is
+// keyed by the profile generation (device slot replaced by ~generation) so it is
+// never replayed after that profile closes.
 std::vector<unsigned char> solve_key(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
                                      int device) {
     std::vector<unsigned char> k(sizeof(devel_ilt_params) + sizeof(int) * 2 + sizeof(int*) +
@@ -231,7 +240,8 @@ std::vector<unsigned char> solve_key(const devel_ilt_params* p, int nclips, cons
     q += sizeof(devel_ilt_params);
     std::memcpy(q, &nclips, sizeof(int));
     q += sizeof(int);
-    std::memcpy(q, &device, sizeof(int));
+    const int tag = prof_on() ? (int)(~prof_generation()) : device;
+    std::memcpy(q, &tag, sizeof(int));
     q += sizeof(int);
     std::memcpy(q, &status, sizeof(int*));
     q += sizeof(int*);
@@ -394,6 +404,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.loss4, sizeof(double) * 4);
     ALLOC(o->ws.cnt2, sizeof(long long) * 2);
     ALLOC(o->tc_err, sizeof(int));
+    ALLOC(o->ws.counters, sizeof(unsigned) * 4);
     if (precision == DEVEL_PREC_BF16X3) {
         const size_t bf = sizeof(__nv_bfloat16);
         for (TcWindow* tw : {&o->tcW, &o->tcW2}) {
@@ -468,6 +479,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     for (const Cp& c : cps)
         if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h, c.bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(o->tc_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(o->ws.counters, 0, sizeof(unsigned) * 4);
     if (e != cudaSuccess) {
         free_optics(o);
         return cuda_error(e, "devel_optics_create: cudaMemcpy");
@@ -550,7 +562,7 @@ int devel_resist_loss(const devel_optics* o, const float* intensity, const unsig
     CHECK_PTR(loss_out, "loss_out");
     CHECK_PTR(counts_out, "counts_out");
     return launch_resist(o->n, intensity, target, *p, dLdI, nullptr, nullptr, 0, o->ws.dpart, o->ws.lpart,
-                         o->npart_red, loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, s);
+                         o->npart_red, loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, o->ws.counters, s);
 }
 
 int devel_litho_adjoint(const devel_optics* o, const float* mask, const float* dLdI, float* dLdM,
@@ -577,7 +589,7 @@ int devel_levelset_step(int n, const float* phi, const float* V, const double* v
     if (phi == phi_out) return set_error(DEVEL_EINVAL, "devel_levelset_step: phi_out aliases phi");
     if (!std::isfinite(dt) || !std::isfinite(lambda))
         return set_error(DEVEL_EINVAL, "devel_levelset_step: dt/lambda not finite");
-    return launch_levelset_step(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, s);
+    return launch_levelset_step(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, nullptr, 0, s);
 }
 
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
@@ -611,7 +623,7 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         CHECK_OPT_PTR(cl.l2_hist, "clip.l2_hist");
         CHECK_OPT_PTR(cl.pvb_hist, "clip.pvb_hist");
     }
-    if (p->use_graph && !prof_on()) return solve_graph(p, nclips, clips, status, s);
+    if (p->use_graph) return solve_graph(p, nclips, clips, status, s);
     return enqueue_solve(p, nclips, clips, status, s);
 }
 

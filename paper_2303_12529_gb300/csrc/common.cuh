@@ -36,6 +36,7 @@ enum ProfKind {
     PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PROF_NKINDS
 };
 bool prof_on();
+unsigned prof_generation();
 void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
 
@@ -54,9 +55,47 @@ struct EpiArgs {
     float scale = 1.f;
     float* vpart = nullptr;          // EPI_VEL: per-CTA max |out|
     int n = 0;
+    // EPI_VEL: the last CTA reduces vpart into *vmax (FP64), flags non-finite in *status
+    unsigned* counter = nullptr;
+    double* vmax = nullptr;
+    int* status = nullptr;
 };
 
 constexpr int kTcSplitK = 256;  // K slice of one split of the tensor-core reduction
+
+// Called by every thread of every block of an EPI_VEL expansion after the block has
+// stored its max |V| in vpart[its index]: the last block to arrive reduces all nparts
+// values (max is exact, so order does not matter), writes *vmax in FP64, flags a
+// non-finite value in *status, and resets *counter to zero.
+__device__ __forceinline__ void vmax_last_block(const float* vpart, int nparts, unsigned* counter, double* vmax,
+                                                int* status) {
+    __shared__ bool s_last;
+    __shared__ float s_red[32];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == (unsigned)nparts - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    float m = 0.f;
+    bool bad = false;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const float v = __ldcg(vpart + i);
+        if (!(v == v) || isinf(v)) bad = true;
+        m = fmaxf(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        float r = s_red[0];
+        for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) r = fmaxf(r, s_red[w]);
+        *vmax = (double)r;
+        if (bad && status) *status = DEVEL_ENAN;
+        *counter = 0u;
+    }
+}
 
 // Device-side limit of the window side handled by the FP32 kernels.
 constexpr int kMaxWindow = 63;
@@ -93,6 +132,7 @@ struct Workspace {
     double* vmax = nullptr;    // [1]
     double* loss4 = nullptr;   // [4]
     long long* cnt2 = nullptr; // [2]
+    unsigned* counters = nullptr;  // [4] zeroed: last-block counters (0: resist, 1: max |V|)
 };
 
 // bf16 hi/lo tables and tensor maps of one window for the tensor-core path
@@ -147,25 +187,28 @@ int launch_shat(const devel_optics* o, cudaStream_t s);
 // *nparts = number of CTA partials.
 int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int epi, const EpiArgs& ep,
                   int* nparts, cudaStream_t s);
-int launch_resist_final(int nparts, const devel_resist_params& p, const double* dpart, const long long* lpart,
-                        double* loss4, long long* cnt2, double* loss_hist, long long* l2_hist,
-                        long long* pvb_hist, int* status, cudaStream_t s);
+
 int expand_parts(int n);
-int launch_vmax_final(const devel_optics* o, int nparts, double* vmax, int* status, cudaStream_t s);
+
 
 // resist.cu
 // dL/dI of the image I (n x n): into R (FP32, n x n) and/or into bf16 hi/lo
 // arrays of pitch ldr; loss partials, then the final reduction.
+// (one kernel: the last block to finish also does the final FP64 sums; `counter`
+// is a zeroed device word that the kernel leaves zeroed)
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
                   float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, double* dpart,
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
-                  long long* l2_hist, long long* pvb_hist, int* status, cudaStream_t s);
+                  long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s);
 int resist_parts(int n);
 
 // levelset.cu
+// mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
-                         unsigned char* mask_out, cudaStream_t s);
+                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s);
+// tensor-core path: spectrum of the mask already in Xhi (bf16, exact)
+int launch_spectrum_mask_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s);
 int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s);
 int launch_u8_to_f32(int n, const unsigned char* M, float* out, cudaStream_t s);
 

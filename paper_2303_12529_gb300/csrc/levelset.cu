@@ -37,7 +37,7 @@ __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, 
         const float pxy = 0.25f * ((xpyp - xmyp) - (xpym - xmym));
         const float den = px * px + py * py;
         float kc = 0.f;
-        if (den >= 1e-12f) kc = (pxx * py * py - 2.f * px * py * pxy + pyy * px * px) / den;
+        if (den >= 1e-12f) kc = __fdividef(pxx * py * py - 2.f * px * py * pxy + pyy * px * px, den);
         out += dt * lam * mm * kc;
     }
     return out;
@@ -46,7 +46,8 @@ __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, 
 __global__ void __launch_bounds__(kTX * kTYS)
 k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
                 const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
-                int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out) {
+                int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
+                __nv_bfloat16* __restrict__ mask_bf, int ldb) {
     __shared__ float t[kTYS + 2][kW + 2];
     __shared__ float s_inv;
     const int bx = blockIdx.x * kW, by = blockIdx.y * kTYS;
@@ -56,58 +57,51 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
         const double vm = *vmax;
         s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
     }
-    for (int i = tid; i < (kTYS + 2) * (kW + 2); i += kTX * kTYS) {
+    // stage the tile: all of a thread's loads are issued before its shared stores
+    constexpr int kTile = (kTYS + 2) * (kW + 2);
+    constexpr int kPer = (kTile + kTX * kTYS - 1) / (kTX * kTYS);
+    float tv[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = tid + u * kTX * kTYS;
         const int ly = i / (kW + 2), lx = i - ly * (kW + 2);
         const int y = min(max(by + ly - 1, 0), n - 1);
         const int x = min(max(bx + lx - 1, 0), n - 1);
-        t[ly][lx] = phi[(size_t)y * n + x];
+        tv[u] = i < kTile ? phi[(size_t)y * n + x] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = tid + u * kTX * kTYS;
+        if (i < kTile) (&t[0][0])[i] = tv[u];
     }
     __syncthreads();
     const int y = by + threadIdx.y;
     if (y >= n) return;
-    const int x0 = bx + threadIdx.x * kPX;
-    if (x0 >= n) return;
     const float inv = s_inv;
     const int ly = threadIdx.y + 1;
-    const size_t p0 = (size_t)y * n + x0;
-    const bool full = x0 + kPX <= n && ((p0 & 3) == 0);
-    float v[kPX], mm[kPX];
-    if (full) {
-        const float4 q = *reinterpret_cast<const float4*>(V + p0);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        if (m) {
-            const float4 r = *reinterpret_cast<const float4*>(m + p0);
-            mm[0] = r.x; mm[1] = r.y; mm[2] = r.z; mm[3] = r.w;
-        } else {
-            mm[0] = mm[1] = mm[2] = mm[3] = 1.f;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPX; ++j) {
-            v[j] = x0 + j < n ? V[p0 + j] : 0.f;
-            mm[j] = (m && x0 + j < n) ? m[p0 + j] : 1.f;
-        }
-    }
-    float o[kPX];
+    const size_t prow = (size_t)y * n;
+    // pixel j of this thread: x = bx + threadIdx.x + 32 j (consecutive lanes, consecutive
+    // pixels: coalesced global access, conflict-free shared-memory reads)
+    float vv[kPX], mv[kPX];
 #pragma unroll
     for (int j = 0; j < kPX; ++j) {
-        const int lx = threadIdx.x * kPX + j + 1;
-        o[j] = step_px(t[ly][lx], t[ly][lx - 1], t[ly][lx + 1], t[ly - 1][lx], t[ly + 1][lx], t[ly + 1][lx + 1],
-                       t[ly + 1][lx - 1], t[ly - 1][lx + 1], t[ly - 1][lx - 1], v[j], inv, dt, lam, mm[j]);
+        const int x = bx + threadIdx.x + kTX * j;
+        vv[j] = x < n ? V[prow + x] : 0.f;
+        mv[j] = (m && x < n) ? m[prow + x] : 1.f;
     }
-    if (full) {
-        *reinterpret_cast<float4*>(phi_out + p0) = make_float4(o[0], o[1], o[2], o[3]);
-        if (mask_out)
-            *reinterpret_cast<uchar4*>(mask_out + p0) =
-                make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
-    } else {
 #pragma unroll
-        for (int j = 0; j < kPX; ++j) {
-            if (x0 + j < n) {
-                phi_out[p0 + j] = o[j];
-                if (mask_out) mask_out[p0 + j] = o[j] <= 0.f ? 1 : 0;
-            }
-        }
+    for (int j = 0; j < kPX; ++j) {
+        const int lx0 = threadIdx.x + kTX * j;
+        const int x = bx + lx0;
+        if (x >= n) break;
+        const int lx = lx0 + 1;
+        const size_t p = prow + x;
+        const float o = step_px(t[ly][lx], t[ly][lx - 1], t[ly][lx + 1], t[ly - 1][lx], t[ly + 1][lx],
+                                t[ly + 1][lx + 1], t[ly + 1][lx - 1], t[ly - 1][lx + 1], t[ly - 1][lx - 1], vv[j], inv,
+                                dt, lam, mv[j]);
+        phi_out[p] = o;
+        if (mask_out) mask_out[p] = o <= 0.f ? 1 : 0;
+        if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(o <= 0.f ? 1.f : 0.f);
     }
 }
 
@@ -133,10 +127,11 @@ int grid_for(size_t npix) {
 
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
-                         unsigned char* mask_out, cudaStream_t s) {
+                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s) {
     dim3 grid((n + kW - 1) / kW, (n + kTYS - 1) / kTYS);
     prof_begin(PK_STEP, s);
-    k_levelset_step<<<grid, dim3(kTX, kTYS), 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out);
+    k_levelset_step<<<grid, dim3(kTX, kTYS), 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
+                                                    ldb);
     prof_end(PK_STEP, s);
     DEVEL_LAUNCH_CHECK("k_levelset_step");
     return DEVEL_OK;

@@ -154,6 +154,7 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, 
             for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
             ep.vpart[part] = m;
         }
+        vmax_last_block(ep.vpart, gridDim.x * gridDim.y, ep.counter, ep.vmax, ep.status);
     }
 }
 
@@ -212,6 +213,7 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
     const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
     const float2* T = Tdiff + goff[g];
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int t = threadIdx.x; t < total; t += 128) {
         const int i1 = t / n2, i2 = t - i1 * n2;
         const int a1 = a1lo + i1, a2 = a2lo + i2;
@@ -231,6 +233,7 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
     const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
     const float2* row = TCC + (size_t)f * kk;
     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int a = threadIdx.x; a < kk; a += 128) {
         const int a1 = a / k, a2 = a - a1 * k;
         const float2 u = cmul(__ldg(mhat + a), __ldg(rhat + (f1 - a1 + r2) * k2 + (f2 - a2 + r2)));
@@ -241,24 +244,62 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
 }
 
 // T(y, b) = sum_a e^{+i theta_a y} Z(a, b) -> Acat[y] = [Re T | -Im T | 0 ...] (ldk columns),
-// as FP32 (Af) or as bf16 hi/lo (Ahi, Alo). One thread per (y, b), b in [0, ldk - kw):
-// b < kw computes T(y, b) and writes columns b and kw + b, b >= kw writes padding column kw + b.
+// as FP32 (Af) or as bf16 hi/lo (Ahi, Alo). A block of 256 threads takes kTRows rows; Z and
+// the rows' cos / sin values are staged in shared memory; a warp per row, lane l computes
+// the columns b = l, l + 32, ... (and writes the zero padding beyond 2 kw).
+constexpr int kTRows = 8;
+
 __global__ void __launch_bounds__(256)
 k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n, int kw, int ldk,
            float* __restrict__ Af, __nv_bfloat16* __restrict__ Ahi, __nv_bfloat16* __restrict__ Alo) {
-    const int per = ldk - kw;
-    const long long total = (long long)n * per;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(p / per), b = (int)(p - (long long)y * per);
-        const size_t base = (size_t)y * ldk;
+    extern __shared__ float2 zs[];  // [kw * kw] Z, then [kTRows][ldk] floats of basisT
+    float* gs = reinterpret_cast<float*>(zs + kw * kw);
+    const int y0 = blockIdx.x * kTRows;
+    // stage Z with batches of independent loads in flight (latency, not bandwidth, bound)
+    {
+        const int nz = kw * kw;
+        for (int i0 = threadIdx.x; i0 < nz; i0 += 8 * blockDim.x) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < nz ? __ldg(Z + i) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < nz) zs[i] = v[u];
+            }
+        }
+        const int ng = kTRows * ldk;
+        for (int i0 = threadIdx.x; i0 < ng; i0 += 8 * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                const int r = i / ldk, c = i - r * ldk;
+                v[u] = i < ng ? __ldg(basisT + (size_t)min(y0 + r, n - 1) * ldk + c) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < ng) gs[i] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int y = y0 + r;
+    if (y >= n) return;
+    const float* g = gs + r * ldk;
+    const size_t base = (size_t)y * ldk;
+    for (int b = lane; b < ldk - kw; b += 32) {
         float v0 = 0.f, v1 = 0.f;
         if (b < kw) {
-            const float* g = basisT + base;
             float tr = 0.f, ti = 0.f;
             for (int a = 0; a < kw; ++a) {
-                const float2 z = __ldg(Z + a * kw + b);
-                const float c = __ldg(g + a), s = __ldg(g + kw + a);
+                const float2 z = zs[a * kw + b];
+                const float c = g[a], s = g[kw + a];
                 tr = fmaf(c, z.x, fmaf(-s, z.y, tr));
                 ti = fmaf(c, z.y, fmaf(s, z.x, ti));
             }
@@ -278,26 +319,6 @@ k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n
             Ahi[base + kw + b] = h1;
             Alo[base + kw + b] = __float2bfloat16_rn(v1 - __bfloat162float(h1));
         }
-    }
-}
-
-__global__ void k_vmax_final(const float* __restrict__ vpart, int nparts, double* vmax, int* status) {
-    __shared__ float red[32];
-    float m = 0.f;
-    bool bad = false;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        const float v = vpart[i];
-        if (!(v == v) || isinf(v)) bad = true;
-        m = fmaxf(m, v);
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    bad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-        float r = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
-        *vmax = (double)r;
-        if (bad && status) *status = DEVEL_ENAN;
     }
 }
 
@@ -370,7 +391,7 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
 
 int litho_init_attrs() {
     const int big = 200 * 1024;
-    (void)big;
+    DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_expand_T, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return DEVEL_OK;
 }
 
@@ -381,6 +402,18 @@ int launch_spectrum_f32(const devel_optics* o, const float* X, const Window& w, 
 int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const Window& w, float2* out,
                        cudaStream_t s) {
     int rc = reduce_stage1<unsigned char>(o, X, w, s);
+    return rc ? rc : reduce_finish(o, w, out, s);
+}
+
+int launch_spectrum_mask_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s) {
+    const Workspace& ws = o->ws;
+    EpiArgs ep;
+    ep.C = ws.Ppart;
+    ep.ldc = w.ldk;
+    ep.split_stride = (size_t)o->n * w.ldk;
+    const TcWindow& tw = tc_window(o, w);
+    tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, 0};
+    int rc = tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, o->n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err, s);
     return rc ? rc : reduce_finish(o, w, out, s);
 }
 
@@ -418,8 +451,7 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
     const Workspace& ws = o->ws;
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
     prof_begin(PK_EXPAND_T, s);
-    const long long pairs = (long long)n * (w.ldk - w.kw);
-    k_expand_T<<<(int)std::min<long long>((pairs + 255) / 256, 16 * 148), 256, 0, s>>>(
+    k_expand_T<<<(n + kTRows - 1) / kTRows, 256, sizeof(float2) * w.kw * w.kw + sizeof(float) * kTRows * w.ldk, s>>>(
         Z, w.basisT, n, w.kw, w.ldk, tcp ? nullptr : ws.Acat, tcp ? o->Acat_hi : nullptr,
         tcp ? o->Acat_lo : nullptr);
     prof_end(PK_EXPAND_T, s);
@@ -444,13 +476,5 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
 }
 
 int expand_parts(int n) { return ((n + gBN - 1) / gBN) * ((n + gBM - 1) / gBM); }
-
-int launch_vmax_final(const devel_optics* o, int nparts, double* vmax, int* status, cudaStream_t s) {
-    prof_begin(PK_VMAX, s);
-    k_vmax_final<<<1, 1024, 0, s>>>(o->ws.vpart, nparts, vmax, status);
-    prof_end(PK_VMAX, s);
-    DEVEL_LAUNCH_CHECK("k_vmax_final");
-    return DEVEL_OK;
-}
 
 }  // namespace devel

@@ -31,8 +31,10 @@ static int g_open_kind = -1;
 static int g_launches[PROF_NKINDS];
 static double g_ms[PROF_NKINDS];
 static bool g_overflow = false;
+static unsigned g_generation = 0;  // bumped by every devel_profile_start
 
 bool prof_on() { return g_on; }
+unsigned prof_generation() { return g_generation; }
 
 void prof_begin(int kind, cudaStream_t s) {
     if (!g_on) return;
@@ -42,13 +44,15 @@ void prof_begin(int kind, cudaStream_t s) {
         return;
     }
     g_pool[g_used].kind = kind;
-    cudaEventRecord(g_pool[g_used].a, s);
+    // external record: inside a stream capture this becomes an event-record node
+    // that timestamps the event on every replay (not a capture-internal dependency)
+    cudaEventRecordWithFlags(g_pool[g_used].a, s, cudaEventRecordExternal);
     g_open_kind = kind;
 }
 
 void prof_end(int kind, cudaStream_t s) {
     if (!g_on || g_open_kind != kind) return;
-    cudaEventRecord(g_pool[g_used].b, s);
+    cudaEventRecordWithFlags(g_pool[g_used].b, s, cudaEventRecordExternal);
     ++g_used;
     g_open_kind = -1;
 }
@@ -75,13 +79,12 @@ int devel_profile_start(int capacity) {
     g_overflow = false;
     std::memset(g_launches, 0, sizeof(g_launches));
     for (int i = 0; i < PROF_NKINDS; ++i) g_ms[i] = 0.0;
+    ++g_generation;
     g_on = true;
     return DEVEL_OK;
 }
 
-int devel_profile_stop(void) {
-    if (!g_on) return set_error(DEVEL_EINVAL, "devel_profile_stop: no profile open");
-    g_on = false;
+int devel_profile_collect(void) {
     for (size_t i = 0; i < g_used; ++i) {
         DEVEL_CUDA_TRY(cudaEventSynchronize(g_pool[i].b));
         float ms = 0.f;
@@ -89,7 +92,14 @@ int devel_profile_stop(void) {
         g_launches[g_pool[i].kind] += 1;
         g_ms[g_pool[i].kind] += ms;
     }
-    if (g_overflow) return set_error(DEVEL_EINVAL, "devel_profile_stop: capacity exceeded, profile truncated");
+    if (g_overflow) return set_error(DEVEL_EINVAL, "devel_profile_collect: capacity exceeded, profile truncated");
+    return DEVEL_OK;
+}
+
+int devel_profile_stop(void) {
+    if (!g_on) return set_error(DEVEL_EINVAL, "devel_profile_stop: no profile open");
+    g_on = false;
+    ++g_generation;
     return DEVEL_OK;
 }
 

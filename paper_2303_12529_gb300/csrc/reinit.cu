@@ -82,40 +82,87 @@ k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     }
 }
 
+// Row pass: d2(x) = min_x' [(x - x')^2 + g(x')^2] over the columns x' where the
+// wanted class occurs. One block per row, the row of packed g in shared memory;
+// each pixel searches outwards |x - x'| = 1, 2, ... while (x - x')^2 is below its
+// best candidate. Per 16-column block the smaller g of each class is kept, and
+// a pixel skips a whole block when even its best case (distance to the block's
+// near edge squared plus the block minimum squared) cannot beat the candidate.
+constexpr int kBlk = 16;
+constexpr int kEnvMaxN = 8192;
+
+// Squared column distance, or kFar when the column has no pixel of the class; kFar
+// plus any squared row distance (< 2^28 for n <= 8192) stays below INT_MAX.
+constexpr int kFar = 1 << 30;
+
 __global__ void __launch_bounds__(256)
 k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g,
            float* __restrict__ phi, float d_lo, float d_hi) {
-    extern __shared__ unsigned row[];
+    extern __shared__ int sfx[];  // f0[n], f1[n]: g^2 per class; b0[nb], b1[nb]: block minima
+    const int nb = (n + kBlk - 1) / kBlk;
+    int* f0 = sfx;
+    int* f1 = f0 + n;
+    int* b0 = f1 + n;
+    int* b1 = b0 + nb;
     const int y = blockIdx.x;
     const size_t base = (size_t)y * n;
-    for (int x = threadIdx.x; x < n; x += blockDim.x) row[x] = g[base + x];
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const unsigned w = g[base + x];
+        const unsigned a = w & 0xFFFFu, b = w >> 16;
+        f0[x] = a == kNone ? kFar : (int)(a * a);
+        f1[x] = b == kNone ? kFar : (int)(b * b);
+    }
     __syncthreads();
+    bool any0 = false, any1 = false;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        int m0 = kFar, m1 = kFar;
+        for (int x = b * kBlk; x < min(n, (b + 1) * kBlk); ++x) {
+            m0 = min(m0, f0[x]);
+            m1 = min(m1, f1[x]);
+        }
+        b0[b] = m0;
+        b1[b] = m1;
+        any0 |= m0 < kFar;
+        any1 |= m1 < kFar;
+    }
+    // rows in which a class never occurs (in any column) need no search for it
+    const bool has0 = __syncthreads_or(any0), has1 = __syncthreads_or(any1);
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
         const bool inside = mask[base + x] != 0;
-        // an inside pixel looks for class 0 (low half), an outside one for class 1 (high half)
-        const int sh = inside ? 0 : 16;
-        int best = INT_MAX;
-        {
-            const unsigned gx = (row[x] >> sh) & 0xFFFFu;
-            if (gx != kNone) best = (int)(gx * gx);
-        }
-        for (int dx = 1; dx < n; ++dx) {
-            const int dx2 = dx * dx;
-            if (dx2 >= best) break;
-            const bool lo = x - dx >= 0, hi = x + dx < n;
-            if (!lo && !hi) break;
-            if (lo) {
-                const unsigned gv = (row[x - dx] >> sh) & 0xFFFFu;
-                if (gv != kNone) best = min(best, dx2 + (int)(gv * gv));
-            }
-            if (hi) {
-                const unsigned gv = (row[x + dx] >> sh) & 0xFFFFu;
-                if (gv != kNone) best = min(best, dx2 + (int)(gv * gv));
+        // an inside pixel looks for class 0, an outside one for class 1
+        const int* f = inside ? f0 : f1;
+        const int* bm = inside ? b0 : b1;
+        int best = f[x];
+        if (inside ? has0 : has1) {
+            int L = x - 1, R = x + 1;
+            while (true) {
+                const int dl = x - L, dr = R - x;
+                const int dl2 = dl * dl, dr2 = dr * dr;
+                const bool lok = L >= 0 && dl2 < best;
+                const bool rok = R < n && dr2 < best;
+                if (!lok && !rok) break;
+                if (lok) {
+                    // at the right edge of a block, skip it if even its minimum cannot win
+                    if ((L & (kBlk - 1)) == kBlk - 1 && dl2 + bm[L >> 4] >= best) {
+                        L -= kBlk;
+                    } else {
+                        best = min(best, dl2 + f[L]);
+                        --L;
+                    }
+                }
+                if (rok) {
+                    if ((R & (kBlk - 1)) == 0 && dr2 + bm[R >> 4] >= best) {
+                        R += kBlk;
+                    } else {
+                        best = min(best, dr2 + f[R]);
+                        ++R;
+                    }
+                }
             }
         }
         float v;
         int d2;
-        if (best == INT_MAX) {
+        if (best >= kFar) {
             d2 = -1;
             v = inside ? d_lo : d_hi;
         } else {
@@ -131,20 +178,22 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
 
 }  // namespace
 
+static size_t edt_rows_smem(int n) { return sizeof(int) * 2 * (n + (n + kBlk - 1) / kBlk); }
+
+int reinit_init_attrs() {
+    DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)edt_rows_smem(kEnvMaxN)));
+    return DEVEL_OK;
+}
+
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                   cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            16384 * 4));
-        attr = true;
-    }
     prof_begin(PK_EDT_COLS, s);
     k_edt_cols<<<(n + kCW - 1) / kCW, dim3(kCW, kSeg), 0, s>>>(mask, n, reinterpret_cast<unsigned*>(d2));
     prof_end(PK_EDT_COLS, s);
     DEVEL_LAUNCH_CHECK("k_edt_cols");
     prof_begin(PK_EDT_ROWS, s);
-    k_edt_rows<<<n, 256, sizeof(unsigned) * n, s>>>(mask, n, reinterpret_cast<unsigned*>(d2), phi, d_lo, d_hi);
+    k_edt_rows<<<n, 256, edt_rows_smem(n), s>>>(mask, n, reinterpret_cast<unsigned*>(d2), phi, d_lo, d_hi);
     prof_end(PK_EDT_ROWS, s);
     DEVEL_LAUNCH_CHECK("k_edt_rows");
     return DEVEL_OK;
@@ -173,7 +222,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 extern "C" int devel_reinit_sdf_static(int n, const unsigned char* mask, float* phi, float d_lo,
                                        float d_hi, cudaStream_t s) {
     using namespace devel;
-    if (n < 1 || n > DEVEL_REINIT_STATIC_MAX_N)
+    if (n < 1 || n > DEVEL_REINIT_STATIC_MAX_N || n > kEnvMaxN)
         return set_error(DEVEL_EINVAL,
                          "devel_reinit_sdf_static: n=%d outside [1, %d] (size of the static scratch)", n,
                          DEVEL_REINIT_STATIC_MAX_N);

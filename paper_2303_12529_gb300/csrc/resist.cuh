@@ -30,7 +30,7 @@ struct LossAcc {
 // |t| of order 1, where dL/dI peaks; larger |t| only in saturated pixels.
 __device__ __forceinline__ void sigmoid_slope(float t, float& z, float& dz) {
     const float e = __expf(-t);
-    z = __frcp_rn(1.f + e);
+    z = __fdividef(1.f, 1.f + e);
     dz = e * z * z;
 }
 

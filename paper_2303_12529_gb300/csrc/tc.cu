@@ -309,6 +309,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         fence_after_sync();
         tmem_dealloc(tmem, CF::kCols);
     }
+    if (EPI == EPI_VEL) vmax_last_block(ep.vpart, gridDim.x * gridDim.y, ep.counter, ep.vmax, ep.status);
 }
 
 // ---------------------------------------------------------------------------
