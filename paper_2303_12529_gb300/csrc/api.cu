@@ -386,7 +386,9 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.Ppart, sizeof(float) * (size_t)o->nsplit * n * ld2);
     o->nq = std::max(1, std::min(16, n / 128));
     ALLOC(o->ws.P, sizeof(float) * (size_t)n * ld2);
-    ALLOC(o->ws.Q, sizeof(float) * (size_t)o->nq * ld2 * ld2);
+    const size_t nslices =
+        precision == DEVEL_PREC_BF16X3 ? (size_t)std::max(o->nq, tc::spectrum2_slices(n, o->ldn)) : (size_t)o->nq;
+    ALLOC(o->ws.Q, sizeof(float) * nslices * ld2 * ld2);
     ALLOC(o->ws.mhat, sizeof(float2) * kk);
     ALLOC(o->ws.Ihat, sizeof(float2) * kk2);
     ALLOC(o->ws.rhat, sizeof(float2) * kk2);
@@ -409,8 +411,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         const size_t bf = sizeof(__nv_bfloat16);
         for (TcWindow* tw : {&o->tcW, &o->tcW2}) {
             const int ldk = (tw == &o->tcW) ? o->W.ldk : ld2;
-            ALLOC(tw->basis_hi, bf * ldk * o->ldn);
-            ALLOC(tw->basis_lo, bf * ldk * o->ldn);
+            ALLOC(tw->basis_hi, bf * round_up(ldk, 128) * o->ldn);
+            ALLOC(tw->basis_lo, bf * round_up(ldk, 128) * o->ldn);
             ALLOC(tw->basisT_hi, bf * (size_t)n * ldk);
             ALLOC(tw->basisT_lo, bf * (size_t)n * ldk);
         }
@@ -490,7 +492,15 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         for (int wi = 0; wi < 2 && rc == DEVEL_OK; ++wi) {
             const Window& w = wi ? o->W2 : o->W;
             TcWindow& tw = wi ? o->tcW2 : o->tcW;
+            const int rows128 = round_up(w.ldk, 128);
+            if (cudaMemset(tw.basis_hi, 0, sizeof(__nv_bfloat16) * rows128 * o->ldn) != cudaSuccess ||
+                cudaMemset(tw.basis_lo, 0, sizeof(__nv_bfloat16) * rows128 * o->ldn) != cudaSuccess) {
+                rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
+                break;
+            }
             rc = tc::launch_split(w.basis, w.ldk, n, n, o->ldn, tw.basis_hi, tw.basis_lo, 0);
+            if (!rc) rc = tc::make_map(&tw.m_basis128_hi, tw.basis_hi, rows128, o->ldn, o->ldn, 128);
+            if (!rc) rc = tc::make_map(&tw.m_basis128_lo, tw.basis_lo, rows128, o->ldn, o->ldn, 128);
             if (!rc) rc = tc::launch_split(w.basisT, n, w.ldk, w.ldk, w.ldk, tw.basisT_hi, tw.basisT_lo, 0);
             if (!rc) rc = tc::make_map(&tw.m_basis_hi, tw.basis_hi, w.ldk, o->ldn, o->ldn, w.ldk);
             if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, w.ldk, o->ldn, o->ldn, w.ldk);

@@ -137,11 +137,12 @@ struct Workspace {
 
 // bf16 hi/lo tables and tensor maps of one window for the tensor-core path
 struct TcWindow {
-    __nv_bfloat16* basis_hi = nullptr;   // [ldk][ldn]
+    __nv_bfloat16* basis_hi = nullptr;   // [round_up(ldk, 128)][ldn], rows >= ldk zero
     __nv_bfloat16* basis_lo = nullptr;
     __nv_bfloat16* basisT_hi = nullptr;  // [n][ldk]
     __nv_bfloat16* basisT_lo = nullptr;
     CUtensorMap m_basis_hi, m_basis_lo, m_basisT_hi, m_basisT_lo, m_acat_hi, m_acat_lo;
+    CUtensorMap m_basis128_hi, m_basis128_lo;  // same tables, 128-row boxes (fused reduction, phase 2)
 };
 
 }  // namespace devel

@@ -12,25 +12,25 @@
 namespace devel {
 namespace {
 
-// Tile of 128 x 8 pixels per block of 32 x 8 threads, four adjacent pixels per
-// thread; the (8 + 2) x (128 + 2) neighbourhood is staged in shared memory.
-constexpr int kTX = 32, kTYS = 8, kPX = 4, kW = kTX * kPX;
+// One thread per four adjacent pixels of a row; its 3 x 6 neighbourhood comes
+// straight from global memory (rows y-1, y, y+1, columns x0-1 .. x0+4, borders
+// replicated), overlapping reads between threads being served by L1. Vector
+// loads and stores when the row is 16-byte aligned.
+constexpr int kPX = 4;
 
 __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, float yp, float xpyp, float xmyp,
                                          float xpym, float xmym, float v, float inv_vmax, float dt, float lam,
                                          float mm) {
     float out = c;
-    if (inv_vmax > 0.f) {
-        const float F = -dt * (v * inv_vmax);
-        const float dmx = c - xm, dpx = xp - c, dmy = c - ym, dpy = yp - c;
-        if (F > 0.f) {
-            const float a = fmaxf(dmx, 0.f), b = fminf(dpx, 0.f), cc = fmaxf(dmy, 0.f), d = fminf(dpy, 0.f);
-            out -= F * sqrtf(a * a + b * b + cc * cc + d * d);
-        } else if (F < 0.f) {
-            const float a = fminf(dmx, 0.f), b = fmaxf(dpx, 0.f), cc = fminf(dmy, 0.f), d = fmaxf(dpy, 0.f);
-            out -= F * sqrtf(a * a + b * b + cc * cc + d * d);
-        }
-    }
+    // Godunov upwind |grad phi| for the sign of F = -dt V / max|V| (one square root)
+    const float F = -dt * (v * inv_vmax);
+    const float dmx = c - xm, dpx = xp - c, dmy = c - ym, dpy = yp - c;
+    const bool pos = F > 0.f;
+    const float a = pos ? fmaxf(dmx, 0.f) : fminf(dmx, 0.f);
+    const float b = pos ? fminf(dpx, 0.f) : fmaxf(dpx, 0.f);
+    const float cc = pos ? fmaxf(dmy, 0.f) : fminf(dmy, 0.f);
+    const float d = pos ? fminf(dpy, 0.f) : fmaxf(dpy, 0.f);
+    out -= F * sqrtf(a * a + b * b + cc * cc + d * d);
     if (lam != 0.f) {
         const float px = 0.5f * (xp - xm), py = 0.5f * (yp - ym);
         const float pxx = xp + xm - 2.f * c, pyy = yp + ym - 2.f * c;
@@ -43,65 +43,79 @@ __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, 
     return out;
 }
 
-__global__ void __launch_bounds__(kTX * kTYS)
+__device__ __forceinline__ void load_row6(const float* __restrict__ r, int x0, int n, bool vec, float (&v)[kPX + 2]) {
+    v[0] = r[max(x0 - 1, 0)];
+    if (vec) {
+        const float4 q = *reinterpret_cast<const float4*>(r + x0);
+        v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPX; ++j) v[1 + j] = r[min(x0 + j, n - 1)];
+    }
+    v[kPX + 1] = r[min(x0 + kPX, n - 1)];
+}
+
+__global__ void __launch_bounds__(256)
 k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
                 const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
                 int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
                 __nv_bfloat16* __restrict__ mask_bf, int ldb) {
-    __shared__ float t[kTYS + 2][kW + 2];
-    __shared__ float s_inv;
-    const int bx = blockIdx.x * kW, by = blockIdx.y * kTYS;
-    const int tid = threadIdx.y * kTX + threadIdx.x;
-    if (tid == 0) {
-        // FP32 reciprocal of max|V| (0 when there is no transport); one per block
-        const double vm = *vmax;
-        s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
-    }
-    // stage the tile: all of a thread's loads are issued before its shared stores
-    constexpr int kTile = (kTYS + 2) * (kW + 2);
-    constexpr int kPer = (kTile + kTX * kTYS - 1) / (kTX * kTYS);
-    float tv[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int i = tid + u * kTX * kTYS;
-        const int ly = i / (kW + 2), lx = i - ly * (kW + 2);
-        const int y = min(max(by + ly - 1, 0), n - 1);
-        const int x = min(max(bx + lx - 1, 0), n - 1);
-        tv[u] = i < kTile ? phi[(size_t)y * n + x] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int i = tid + u * kTX * kTYS;
-        if (i < kTile) (&t[0][0])[i] = tv[u];
-    }
-    __syncthreads();
-    const int y = by + threadIdx.y;
-    if (y >= n) return;
-    const float inv = s_inv;
-    const int ly = threadIdx.y + 1;
+    const int y = blockIdx.y;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kPX;
+    if (x0 >= n) return;
+    const double vm = *vmax;
+    const float inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
+    const bool vec = ((n & 3) == 0) && (x0 + kPX <= n);
     const size_t prow = (size_t)y * n;
-    // pixel j of this thread: x = bx + threadIdx.x + 32 j (consecutive lanes, consecutive
-    // pixels: coalesced global access, conflict-free shared-memory reads)
+    float rm[kPX + 2], r0[kPX + 2], rp[kPX + 2];
+    load_row6(phi + (size_t)max(y - 1, 0) * n, x0, n, vec, rm);
+    load_row6(phi + prow, x0, n, vec, r0);
+    load_row6(phi + (size_t)min(y + 1, n - 1) * n, x0, n, vec, rp);
     float vv[kPX], mv[kPX];
+    if (vec) {
+        const float4 q = *reinterpret_cast<const float4*>(V + prow + x0);
+        vv[0] = q.x; vv[1] = q.y; vv[2] = q.z; vv[3] = q.w;
+        if (m) {
+            const float4 w = *reinterpret_cast<const float4*>(m + prow + x0);
+            mv[0] = w.x; mv[1] = w.y; mv[2] = w.z; mv[3] = w.w;
+        } else {
+            mv[0] = mv[1] = mv[2] = mv[3] = 1.f;
+        }
+    } else {
 #pragma unroll
-    for (int j = 0; j < kPX; ++j) {
-        const int x = bx + threadIdx.x + kTX * j;
-        vv[j] = x < n ? V[prow + x] : 0.f;
-        mv[j] = (m && x < n) ? m[prow + x] : 1.f;
+        for (int j = 0; j < kPX; ++j) {
+            const bool in = x0 + j < n;
+            vv[j] = in ? V[prow + x0 + j] : 0.f;
+            mv[j] = (m && in) ? m[prow + x0 + j] : 1.f;
+        }
     }
+    float o[kPX];
 #pragma unroll
     for (int j = 0; j < kPX; ++j) {
-        const int lx0 = threadIdx.x + kTX * j;
-        const int x = bx + lx0;
-        if (x >= n) break;
-        const int lx = lx0 + 1;
-        const size_t p = prow + x;
-        const float o = step_px(t[ly][lx], t[ly][lx - 1], t[ly][lx + 1], t[ly - 1][lx], t[ly + 1][lx],
-                                t[ly + 1][lx + 1], t[ly + 1][lx - 1], t[ly - 1][lx + 1], t[ly - 1][lx - 1], vv[j], inv,
-                                dt, lam, mv[j]);
-        phi_out[p] = o;
-        if (mask_out) mask_out[p] = o <= 0.f ? 1 : 0;
-        if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(o <= 0.f ? 1.f : 0.f);
+        const int i = j + 1;
+        o[j] = step_px(r0[i], r0[i - 1], r0[i + 1], rm[i], rp[i], rp[i + 1], rp[i - 1], rm[i + 1], rm[i - 1], vv[j],
+                       inv, dt, lam, mv[j]);
+    }
+    if (vec) {
+        *reinterpret_cast<float4*>(phi_out + prow + x0) = make_float4(o[0], o[1], o[2], o[3]);
+        if (mask_out)
+            *reinterpret_cast<uchar4*>(mask_out + prow + x0) =
+                make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
+        if (mask_bf) {
+            __nv_bfloat16 h[kPX];
+#pragma unroll
+            for (int j = 0; j < kPX; ++j) h[j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
+            *reinterpret_cast<uint2*>(mask_bf + (size_t)y * ldb + x0) = *reinterpret_cast<const uint2*>(h);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPX; ++j) {
+            if (x0 + j < n) {
+                phi_out[prow + x0 + j] = o[j];
+                if (mask_out) mask_out[prow + x0 + j] = o[j] <= 0.f ? 1 : 0;
+                if (mask_bf) mask_bf[(size_t)y * ldb + x0 + j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
+            }
+        }
     }
 }
 
@@ -128,9 +142,9 @@ int grid_for(size_t npix) {
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s) {
-    dim3 grid((n + kW - 1) / kW, (n + kTYS - 1) / kTYS);
+    dim3 grid((n + 256 * kPX - 1) / (256 * kPX), n);
     prof_begin(PK_STEP, s);
-    k_levelset_step<<<grid, dim3(kTX, kTYS), 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
+    k_levelset_step<<<grid, 256, 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
                                                     ldb);
     prof_end(PK_STEP, s);
     DEVEL_LAUNCH_CHECK("k_levelset_step");

@@ -169,23 +169,38 @@ __global__ void k_sum_slices(const float* __restrict__ Ppart, int nz, size_t len
 }
 
 // Xhat(a, b) = scale [(Q[a][b] - Q[kw+a][kw+b]) - i (Q[a][kw+b] + Q[kw+a][b])], Q summed over
-// the nq slices of stage 2: one warp per output, lane l sums slices l, l+32, ..., then a
-// fixed shuffle tree.
-__global__ void __launch_bounds__(kThreads)
+// nq partial slices. Block = (row a, 32 columns b); lane = column, warp w sums slices
+// w, w + 8, ... (coalesced row reads), then the 8 warp sums are added in warp order.
+constexpr int kFinWarps = 8;
+__global__ void __launch_bounds__(32 * kFinWarps)
 k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, float2* __restrict__ out) {
-    const int o = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (o >= kw * kw) return;
-    const int a = o / kw, b = o - a * kw;
+    __shared__ float2 part[kFinWarps][32];
+    const int a = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane;
     float re = 0.f, im = 0.f;
-    const size_t st = (size_t)ldq * ldq;
-    for (int z = lane; z < nq; z += 32) {
-        const float* q = Q + z * st;
-        re += q[a * ldq + b] - q[(kw + a) * ldq + kw + b];
-        im -= q[a * ldq + kw + b] + q[(kw + a) * ldq + b];
+    if (b < kw) {
+        const size_t st = (size_t)ldq * ldq;
+        const float* q = Q + (size_t)w * st;
+        const float* r0 = q + (size_t)a * ldq;
+        const float* r1 = q + (size_t)(kw + a) * ldq;
+        for (int z = w; z < nq; z += kFinWarps, r0 += kFinWarps * st, r1 += kFinWarps * st) {
+            re += __ldcg(r0 + b) - __ldcg(r1 + kw + b);
+            im -= __ldcg(r0 + kw + b) + __ldcg(r1 + b);
+        }
     }
-    float2 v = warp_sum2(make_float2(re, im));
-    if (lane == 0) out[o] = make_float2(v.x * scale, v.y * scale);
+    part[w][lane] = make_float2(re, im);
+    __syncthreads();
+    if (w != 0 || b >= kw) return;
+    float2 v = part[0][lane];
+    for (int i = 1; i < kFinWarps; ++i) v = cadd(v, part[i][lane]);
+    out[a * kw + b] = make_float2(v.x * scale, v.y * scale);
+}
+
+void launch_spec_final(const float* Q, int nq, int ldq, int kw, float2* out, int n, cudaStream_t s) {
+    const float scale = 1.0f / ((float)n * (float)n);
+    prof_begin(PK_SPECTRUM_REDUCE, s);
+    k_spec_final<<<dim3(kw, (kw + 31) / 32), 32 * kFinWarps, 0, s>>>(Q, nq, ldq, kw, scale, out);
+    prof_end(PK_SPECTRUM_REDUCE, s);
 }
 
 // --------------------------------------------------------------------------
@@ -201,6 +216,8 @@ __device__ __forceinline__ float2 block_sum2_128(float2 v, float2* sh) {
 
 // Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), one block of 128
 // threads per g; rect(g) = {a in W : a - g in W}, t = row-major index within rect(g).
+// The aerial image is real, so Ihat(-g) = conj(Ihat(g)): blocks cover the first half of
+// the k2 x k2 window (flat index g <= center) and write the mirrored entry as well.
 __global__ void __launch_bounds__(128)
 k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
            const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat) {
@@ -221,7 +238,10 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
         acc = cadd(acc, cmul(__ldg(T + t), cmulc(__ldg(mhat + a1 * k + a2), __ldg(mhat + b1 * k + b2))));
     }
     const float2 s = block_sum2_128(acc, sh);
-    if (threadIdx.x == 0) Ihat[g] = s;
+    if (threadIdx.x == 0) {
+        Ihat[g] = s;
+        Ihat[k2 * k2 - 1 - g] = make_float2(s.x, -s.y);
+    }
 }
 
 // Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f.
@@ -336,7 +356,7 @@ int gemm_nt(const TA* A, int lda, const TB* B, int ldb, int M, int N, int K, int
 
 const TcWindow& tc_window(const devel_optics* o, const Window& w) { return (&w == &o->W) ? o->tcW : o->tcW2; }
 
-// stage 1 of the reduction: P^T slices in ws.Ppart ([nsplit][ldk][n])
+// stage 1 of the FP32 reduction: P slices in ws.Ppart ([nsplit][n][ldk])
 template <typename TX>
 int reduce_stage1(const devel_optics* o, const TX* X, const Window& w, cudaStream_t s) {
     const int n = o->n;
@@ -346,17 +366,6 @@ int reduce_stage1(const devel_optics* o, const TX* X, const Window& w, cudaStrea
     ep.ldc = w.ldk;
     ep.split_stride = (size_t)n * w.ldk;
     ep.scale = 1.0f;
-    if (o->precision == DEVEL_PREC_BF16X3) {
-        int rc = sizeof(TX) == 1 ? tc::launch_mask_bf16(reinterpret_cast<const unsigned char*>(X), n, o->ldn,
-                                                        o->Xhi, s)
-                                 : tc::launch_split(reinterpret_cast<const float*>(X), n, n, n, o->ldn, o->Xhi,
-                                                    o->Xlo, s);
-        if (rc) return rc;
-        const TcWindow& tw = tc_window(o, w);
-        tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, sizeof(TX) == 1 ? 0 : 1};
-        return tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err,
-                               s);
-    }
     return gemm_nt<TX, float, EPI_STORE>(X, n, w.basis, n, n, w.ldk, n, o->nsplit, ep, PK_SPECTRUM, s,
                                          "k_gemm_nt(spectrum)");
 }
@@ -378,11 +387,20 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
     int rc = gemm_nt<float, float, EPI_STORE, true>(w.basis, n, ws.P, w.ldk, w.ldk, w.ldk, n, o->nq, ep,
                                                     PK_SPECTRUM_STAGE2, s, "k_gemm_nt(stage2)");
     if (rc) return rc;
-    const int nout = w.kw * w.kw;
-    const float scale = 1.0f / ((float)n * (float)n);
-    prof_begin(PK_SPECTRUM_REDUCE, s);
-    k_spec_final<<<(nout + 7) / 8, kThreads, 0, s>>>(ws.Q, o->nq, w.ldk, w.kw, scale, out);
-    prof_end(PK_SPECTRUM_REDUCE, s);
+    launch_spec_final(ws.Q, o->nq, w.ldk, w.kw, out, n, s);
+    DEVEL_LAUNCH_CHECK("k_spec_final");
+    return DEVEL_OK;
+}
+
+// tensor-core reduction: both contractions in one kernel (bf16 operand already in
+// Xhi/Xlo), then the slice sum and complex combination
+int reduce_tc(const devel_optics* o, const Window& w, int use_alo, float2* out, cudaStream_t s) {
+    const TcWindow& tw = tc_window(o, w);
+    tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, use_alo};
+    int rc = tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, o->n, o->ldn, o->ws.Q,
+                                  o->tc_err, s);
+    if (rc) return rc;
+    launch_spec_final(o->ws.Q, tc::spectrum2_slices(o->n, o->ldn), w.ldk, w.kw, out, o->n, s);
     DEVEL_LAUNCH_CHECK("k_spec_final");
     return DEVEL_OK;
 }
@@ -396,42 +414,34 @@ int litho_init_attrs() {
 }
 
 int launch_spectrum_f32(const devel_optics* o, const float* X, const Window& w, float2* out, cudaStream_t s) {
+    if (o->precision == DEVEL_PREC_BF16X3) {
+        int rc = tc::launch_split(X, o->n, o->n, o->n, o->ldn, o->Xhi, o->Xlo, s);
+        return rc ? rc : reduce_tc(o, w, 1, out, s);
+    }
     int rc = reduce_stage1<float>(o, X, w, s);
     return rc ? rc : reduce_finish(o, w, out, s);
 }
 int launch_spectrum_u8(const devel_optics* o, const unsigned char* X, const Window& w, float2* out,
                        cudaStream_t s) {
+    if (o->precision == DEVEL_PREC_BF16X3) {
+        int rc = tc::launch_mask_bf16(X, o->n, o->ldn, o->Xhi, s);
+        return rc ? rc : reduce_tc(o, w, 0, out, s);
+    }
     int rc = reduce_stage1<unsigned char>(o, X, w, s);
     return rc ? rc : reduce_finish(o, w, out, s);
 }
 
 int launch_spectrum_mask_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s) {
-    const Workspace& ws = o->ws;
-    EpiArgs ep;
-    ep.C = ws.Ppart;
-    ep.ldc = w.ldk;
-    ep.split_stride = (size_t)o->n * w.ldk;
-    const TcWindow& tw = tc_window(o, w);
-    tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, 0};
-    int rc = tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, o->n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err, s);
-    return rc ? rc : reduce_finish(o, w, out, s);
+    return reduce_tc(o, w, 0, out, s);
 }
 
 int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s) {
-    const Workspace& ws = o->ws;
-    EpiArgs ep;
-    ep.C = ws.Ppart;
-    ep.ldc = w.ldk;
-    ep.split_stride = (size_t)o->n * w.ldk;
-    const TcWindow& tw = tc_window(o, w);
-    tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, 1};
-    int rc = tc::launch_gemm(op, w.ldk, EPI_STORE, PK_TC_SPECTRUM, o->n, w.ldk, o->ldn, kTcSplitK, ep, o->tc_err, s);
-    return rc ? rc : reduce_finish(o, w, out, s);
+    return reduce_tc(o, w, 1, out, s);
 }
 
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_HOPKINS, s);
-    k_ihat_tcc<<<o->k2 * o->k2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat);
+    k_ihat_tcc<<<(o->k2 * o->k2 + 1) / 2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat);
     prof_end(PK_HOPKINS, s);
     DEVEL_LAUNCH_CHECK("k_ihat_tcc");
     return DEVEL_OK;

@@ -86,8 +86,9 @@ k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
 // wanted class occurs. One block per row, the row of packed g in shared memory;
 // each pixel searches outwards |x - x'| = 1, 2, ... while (x - x')^2 is below its
 // best candidate. Per 16-column block the smaller g of each class is kept, and
-// a pixel skips a whole block when even its best case (distance to the block's
-// near edge squared plus the block minimum squared) cannot beat the candidate.
+// the search skips the rest of a block when even its best case (distance to the
+// nearest unscanned column squared plus the block minimum squared) cannot beat
+// the candidate (about 6 steps per pixel on a Manhattan clip).
 constexpr int kBlk = 16;
 constexpr int kEnvMaxN = 8192;
 
@@ -141,18 +142,20 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
                 const bool lok = L >= 0 && dl2 < best;
                 const bool rok = R < n && dr2 < best;
                 if (!lok && !rok) break;
+                // skip the rest of the 16-column block holding L (or R) when even the block's
+                // minimum at the nearest unscanned column cannot win; valid at any position,
+                // since every unscanned column of the block is at least that far
                 if (lok) {
-                    // at the right edge of a block, skip it if even its minimum cannot win
-                    if ((L & (kBlk - 1)) == kBlk - 1 && dl2 + bm[L >> 4] >= best) {
-                        L -= kBlk;
+                    if (dl2 + bm[L >> 4] >= best) {
+                        L = (L & ~(kBlk - 1)) - 1;
                     } else {
                         best = min(best, dl2 + f[L]);
                         --L;
                     }
                 }
                 if (rok) {
-                    if ((R & (kBlk - 1)) == 0 && dr2 + bm[R >> 4] >= best) {
-                        R += kBlk;
+                    if (dr2 + bm[R >> 4] >= best) {
+                        R = (R | (kBlk - 1)) + 1;
                     } else {
                         best = min(best, dr2 + f[R]);
                         ++R;

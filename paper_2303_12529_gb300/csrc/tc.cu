@@ -313,6 +313,229 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 }
 
 // ---------------------------------------------------------------------------
+// Fused reduction onto a window: both contractions in one kernel
+// ---------------------------------------------------------------------------
+// CTA (row tile m0 of 128 image rows y, K slice z of 256 columns x):
+//   phase 1  D1[y][c] = sum_x X[y][x] basis[c][x]            (the mainloop above, M = 128, N = BN)
+//   phase 2  D1 is drained from TMEM, split to bf16 hi/lo and written transposed into shared
+//            memory as a K-major operand B2[c2][y] (128-byte swizzle, as TMA would lay it out);
+//            D2[c1][c2] = sum_y basis[c1][y] D1[y][c2] for c1 in 128-row blocks (A2 by TMA)
+//   out      D2 rows c1 < BN to Q + slice * BN^2, slice = m-tile * splits + z (BN = ldk)
+// The slices are then summed (in slice order) and combined into the complex window spectrum.
+template <int BN>
+struct Cfg2 {
+    static constexpr uint32_t kB2 = BN * 128;                 // one k-block of B2 (bf16, 64 y)
+    static constexpr uint32_t kPhase2 = 4 * kB2 + 4 * kABytes; // B2 hi/lo x 2 k-blocks, A2 hi/lo x 2 k-blocks
+    static constexpr uint32_t kRing = Cfg<BN>::kStages * Cfg<BN>::kStage;
+    static constexpr uint32_t kArena = kRing > kPhase2 ? kRing : kPhase2;
+    static constexpr int kMB = (BN + 127) / 128;               // 128-row blocks of c1
+    static constexpr uint32_t kCols = kMB > 1 ? 512 : Cfg<BN>::kCols;
+    static constexpr size_t kSmem = 1024 + (size_t)kArena + 512;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+           const __grid_constant__ CUtensorMap tmChi, const __grid_constant__ CUtensorMap tmClo,
+           int kb_per_split, int kb_total, int use_alo, float* __restrict__ Q, int* err) {
+    using CF = Cfg<BN>;
+    using C2 = Cfg2<BN>;
+    constexpr int S = CF::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C2::kArena);
+    uint64_t* empty = full + S;
+    uint64_t* accum = empty + S;
+    uint64_t* a2full = accum + 1;  // [2]
+    uint64_t* acc2 = a2full + 2;   // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc2 + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kBM;
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int nkb = max(0, min(kb_per_split, kb_total - kb0));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a2full[i], 1);
+            mbar_init(&acc2[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, C2::kCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_ptr = [&](int s, int which) -> uint8_t* {
+        uint8_t* base = smem + s * CF::kStage;
+        return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
+    };
+    // phase-2 buffers overlay the ring once phase 1 is complete
+    uint8_t* B2hi = smem;                 // [2 k-blocks][BN rows][128 B]
+    uint8_t* B2lo = smem + 2 * C2::kB2;
+    uint8_t* A2hi = smem + 4 * C2::kB2;   // [2 k-blocks][128 rows][128 B]
+    uint8_t* A2lo = A2hi + 2 * kABytes;
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+
+    // ---------------- phase 1 ----------------
+    int issued = 0;
+    bool ok = true;
+    if (warp == 0 && lane == 0 && nkb > 0) {
+        const uint32_t bytes = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % S;
+            if (i >= S && !mbar_wait(&empty[s], ((i / S) - 1) & 1, err)) {
+                ok = false;
+                break;
+            }
+            mbar_arrive_expect_tx(&full[s], bytes);
+            const int kc = (kb0 + i) * kBK;
+            tma_load_2d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0);
+            if (use_alo) tma_load_2d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0);
+            tma_load_2d(&tmBhi, &full[s], stage_ptr(s, 2), kc, 0);
+            tma_load_2d(&tmBlo, &full[s], stage_ptr(s, 3), kc, 0);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0 && nkb > 0) {
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % S;
+            if (!mbar_wait(&full[s], (i / S) & 1, err)) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            const uint64_t dAhi = smem_desc_sw128(smem_u32(stage_ptr(s, 0)));
+            const uint64_t dAlo = smem_desc_sw128(smem_u32(stage_ptr(s, 1)));
+            const uint64_t dBhi = smem_desc_sw128(smem_u32(stage_ptr(s, 2)));
+            const uint64_t dBlo = smem_desc_sw128(smem_u32(stage_ptr(s, 3)));
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
+                if (use_alo) mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accum);
+    }
+    __syncwarp();
+    bool have = nkb > 0 && ok;
+    if (nkb > 0) have = mbar_wait(accum, 0, err);
+    have = __syncthreads_and(have);  // phase 1 finished (or failed) for the whole CTA
+    fence_after_sync();
+
+    // ---------------- phase 2 ----------------
+    if (have) {
+        // A2 of the first c1 block: TMA into its buffers (the ring is idle now)
+        if (warp == 0 && lane == 0) {
+            mbar_arrive_expect_tx(&a2full[0], 4 * kABytes);
+            for (int kb = 0; kb < 2; ++kb) {
+                tma_load_2d(&tmChi, &a2full[0], A2hi + kb * kABytes, m0 + kb * kBK, 0);
+                tma_load_2d(&tmClo, &a2full[0], A2lo + kb * kABytes, m0 + kb * kBK, 0);
+            }
+        }
+        // drain D1: thread = row y of the tile, 16 columns at a time; write B2[c][y] (bf16 hi/lo)
+        const int yl = warp * 32 + lane;
+        const uint32_t kbo = (uint32_t)(yl >> 6) * C2::kB2;
+        const uint32_t chunk = (uint32_t)((yl & 63) >> 3), e2 = (uint32_t)(yl & 7) * 2;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t c2 = (uint32_t)(c + j);
+                const uint32_t off = kbo + c2 * 128u + (((chunk ^ (c2 & 7u)) << 4) | e2);
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+                *reinterpret_cast<__nv_bfloat16*>(B2hi + off) = h;
+                *reinterpret_cast<__nv_bfloat16*>(B2lo + off) = __float2bfloat16_rn(v[j] - __bfloat162float(h));
+            }
+        }
+        // generic-proxy stores -> visible to the tensor core (async proxy); TMEM reads done
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before_sync();
+    }
+    __syncthreads();
+    fence_after_sync();
+    bool ok2 = have;
+    if (have && warp == 1 && lane == 0) {
+        for (int mb = 0; mb < C2::kMB && ok2; ++mb) {
+            if (!mbar_wait(&a2full[mb], 0, err)) {
+                ok2 = false;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t d2 = tmem + (uint32_t)(mb * 256);
+            for (int kb = 0; kb < 2; ++kb) {
+                const uint64_t dAhi = smem_desc_sw128(smem_u32(A2hi + kb * kABytes));
+                const uint64_t dAlo = smem_desc_sw128(smem_u32(A2lo + kb * kABytes));
+                const uint64_t dBhi = smem_desc_sw128(smem_u32(B2hi + kb * C2::kB2));
+                const uint64_t dBlo = smem_desc_sw128(smem_u32(B2lo + kb * C2::kB2));
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                    mma_bf16(d2, dAhi + adv, dBhi + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(d2, dAhi + adv, dBlo + adv, idesc, 1u);
+                    mma_bf16(d2, dAlo + adv, dBhi + adv, idesc, 1u);
+                }
+            }
+            mma_commit(&acc2[mb]);
+        }
+    }
+    if (have && C2::kMB > 1 && warp == 0 && lane == 0) {
+        // A2 of the second c1 block reuses the buffers once the first block's MMAs are done
+        if (mbar_wait(&acc2[0], 0, err)) {
+            mbar_arrive_expect_tx(&a2full[1], 4 * kABytes);
+            for (int kb = 0; kb < 2; ++kb) {
+                tma_load_2d(&tmChi, &a2full[1], A2hi + kb * kABytes, m0 + kb * kBK, kBM);
+                tma_load_2d(&tmClo, &a2full[1], A2lo + kb * kABytes, m0 + kb * kBK, kBM);
+            }
+        }
+    }
+    __syncwarp();
+    // epilogue: D2 row c1 = mb * 128 + lane-row of this warp; write the slice of Q
+    const int slice = blockIdx.y * gridDim.z + blockIdx.z;
+    float* Qs = Q + (size_t)slice * BN * BN;
+    for (int mb = 0; mb < C2::kMB; ++mb) {
+        bool h2 = have;
+        if (h2) h2 = mbar_wait(&acc2[mb], 0, err);
+        h2 = __all_sync(0xffffffffu, h2);
+        fence_after_sync();
+        const int c1 = mb * kBM + warp * 32 + lane;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            if (h2) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mb * 256 + c), v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            }
+            if (c1 < BN) {  // BN == ldk: each row of the slice is 16-float aligned
+                float4* q4 = reinterpret_cast<float4*>(Qs + (size_t)c1 * BN + c);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) q4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+        }
+    }
+    // a producer that stopped early waits (bounded) for the loads it issued
+    if (warp == 0 && lane == 0 && !ok) {
+        for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(&full[i % S], (i / S) & 1, nullptr);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, C2::kCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // fp32 -> bf16 hi/lo splits
 // ---------------------------------------------------------------------------
 // One block row per image row (blockIdx.y), threads along the columns.
@@ -436,6 +659,47 @@ int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N
     return rc;
 }
 
+template <int BN>
+int launch_spec2_bn(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int M, int kb_per_split,
+                    int kb_total, int splits, float* Q, int* err, cudaStream_t s) {
+    dim3 grid(1, (M + kBM - 1) / kBM, splits);
+    k_tc_spec2<BN><<<grid, 128, Cfg2<BN>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, *Chi, *Clo, kb_per_split,
+                                                      kb_total, op.use_alo, Q, err);
+    DEVEL_LAUNCH_CHECK("k_tc_spec2");
+    return DEVEL_OK;
+}
+
+template <int BN>
+cudaError_t set_attr_spec2() {
+    return cudaFuncSetAttribute(k_tc_spec2<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg2<BN>::kSmem);
+}
+
+int spectrum2_slices(int M, int K) { return ((M + kBM - 1) / kBM) * ((K + kTcSplitK - 1) / kTcSplitK); }
+
+int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
+                     float* Q, int* err, cudaStream_t s) {
+    if (K % kBK != 0) return set_error(DEVEL_EINVAL, "tc spectrum: K=%d not a multiple of %d", K, kBK);
+    const int kb_total = K / kBK, kb_per_split = kTcSplitK / kBK;
+    const int splits = (kb_total + kb_per_split - 1) / kb_per_split;
+    prof_begin(PK_TC_SPECTRUM, s);
+    int rc;
+    switch (BN) {
+#define DEVEL_SPEC2_CASE(bn)                                                                               \
+    case bn:                                                                                               \
+        rc = launch_spec2_bn<bn>(op, Chi, Clo, M, kb_per_split, kb_total, splits, Q, err, s);              \
+        break;
+        DEVEL_SPEC2_CASE(16) DEVEL_SPEC2_CASE(32) DEVEL_SPEC2_CASE(48) DEVEL_SPEC2_CASE(64) DEVEL_SPEC2_CASE(80)
+        DEVEL_SPEC2_CASE(96) DEVEL_SPEC2_CASE(112) DEVEL_SPEC2_CASE(128) DEVEL_SPEC2_CASE(144)
+        DEVEL_SPEC2_CASE(160) DEVEL_SPEC2_CASE(176) DEVEL_SPEC2_CASE(192) DEVEL_SPEC2_CASE(208)
+        DEVEL_SPEC2_CASE(224) DEVEL_SPEC2_CASE(240) DEVEL_SPEC2_CASE(256)
+#undef DEVEL_SPEC2_CASE
+        default:
+            rc = set_error(DEVEL_EINVAL, "tc spectrum: unsupported window width %d", BN);
+    }
+    prof_end(PK_TC_SPECTRUM, s);
+    return rc;
+}
+
 // Shared-memory opt-in of every kernel instantiation (call once per device,
 // outside stream capture).
 int init_attrs() {
@@ -445,6 +709,12 @@ int init_attrs() {
     DEVEL_TC_ATTR(112) DEVEL_TC_ATTR(128) DEVEL_TC_ATTR(144) DEVEL_TC_ATTR(160) DEVEL_TC_ATTR(176)
     DEVEL_TC_ATTR(192) DEVEL_TC_ATTR(208) DEVEL_TC_ATTR(224) DEVEL_TC_ATTR(240) DEVEL_TC_ATTR(256)
 #undef DEVEL_TC_ATTR
+#define DEVEL_SPEC2_ATTR(bn) if (e == cudaSuccess) e = set_attr_spec2<bn>();
+    DEVEL_SPEC2_ATTR(16) DEVEL_SPEC2_ATTR(32) DEVEL_SPEC2_ATTR(48) DEVEL_SPEC2_ATTR(64) DEVEL_SPEC2_ATTR(80)
+    DEVEL_SPEC2_ATTR(96) DEVEL_SPEC2_ATTR(112) DEVEL_SPEC2_ATTR(128) DEVEL_SPEC2_ATTR(144) DEVEL_SPEC2_ATTR(160)
+    DEVEL_SPEC2_ATTR(176) DEVEL_SPEC2_ATTR(192) DEVEL_SPEC2_ATTR(208) DEVEL_SPEC2_ATTR(224) DEVEL_SPEC2_ATTR(240)
+    DEVEL_SPEC2_ATTR(256)
+#undef DEVEL_SPEC2_ATTR
     if (e != cudaSuccess) return cuda_error(e, "tc::init_attrs");
     return DEVEL_OK;
 }

@@ -30,6 +30,15 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
 int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
                 const EpiArgs& ep, int* err, cudaStream_t s);
 
+// Both contractions of a window reduction in one kernel (k_tc_spec2): the phase-1
+// operands as in launch_gemm (A = image [M rows][K], B = basis [BN rows][K]), and
+// Chi/Clo = the same basis tables with 128-row boxes (the phase-2 A operand).
+// Writes spectrum2_slices(M, K) partial [BN][BN] slices to Q; BN = the window's ldk,
+// K a multiple of 64.
+int spectrum2_slices(int M, int K);
+int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
+                     float* Q, int* err, cudaStream_t s);
+
 // Shared-memory opt-in of all tensor-core kernels (once per device).
 int init_attrs();
 
