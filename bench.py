@@ -6,9 +6,11 @@ one synthetic clip per GPU. The default workload is the full-size one:
 a 2048^2 Manhattan metal-layer clip at 1 nm/px, K = 24 SOCS kernels of
 35 x 35, dose corners +/-2% (alpha = 1, beta = 7.5), dt = 0.5, lambda = 0.1,
 100 iterations. The metric is clips/s (whole job); clips are independent, so
-N GPUs solve N different clips with no collective ("scaling": "weak").
+N GPUs solve N different clips with no collective ("scaling": "weak"). By
+default the compensated-BF16 solve is the headline and the plain FP32 solve of
+the same clip is measured beside it as the comparator (speed and final L2/PVB).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|fp32|bf16x3]
     python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
 """
 from __future__ import annotations
@@ -35,6 +37,11 @@ WORKLOADS = {
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernels, from the ncu captures summarised under profiles/; a kernel changed since its
+# capture has no entry.
+TRAFFIC = {}
+
 
 def algorithmic_flops_per_iter(n, K, k):
     """Real flops of the truncated-DFT method per clip per iteration, SOCS form
@@ -52,24 +59,41 @@ def window_flops_per_iter(n, K, k):
     return big + small
 
 
-# per-launch algorithmic cost of each kernel class: (kind, bytes_per_px or flops fn)
-def kernel_cost(name, n, K, k, launches_per_iter_shape=None):
+# Algorithmic HBM bytes of one launch of each kernel class (n x n clip, windows of
+# side k and k2 = 2k - 1, padded contraction lengths ldk / ldk2, bf16 hi/lo operands on
+# the tensor-core path). Every kernel of the loop is bounded by HBM (or by latency)
+# rather than by the tensor pipe: the contractions are only 2 ldk deep.
+def kernel_bytes(name, n, K, k, tc):
     px = n * n
     k2 = 2 * k - 1
+    ldk, ldk2 = -(-2 * k // 16) * 16, -(-2 * k2 // 16) * 16
+    ldn = -(-n // 64) * 64
+    slices = -(-n // 128) * -(-ldn // 256)
     if name == "levelset_step":
-        return "hbm", 13 * px
+        return (15 if tc else 13) * px            # phi, V in; phi, mask (+ bf16 mask) out
     if name == "resist":
-        return "hbm", 9 * px
+        return 9 * px                             # I, Z_t in; dL/dI (fp32, or bf16 hi + lo) out
     if name == "edt_cols":
-        return "hbm", 5 * px
+        return 5 * px                             # mask in, packed column distances out
     if name == "edt_rows":
-        return "hbm", 13 * px
-    if name in ("expand_gemm", "tc_expand"):
-        # half the launches expand W2 (forward), half W (adjoint)
-        return "flops", 2 * px * (2 * k2 + 2 * k) / 2
-    if name in ("spectrum_gemm", "tc_spectrum"):
-        return "flops", 2 * px * (2 * k + 2 * k2) / 2
-    return None, None
+        return 13 * px                            # distances and mask in, d^2 and phi out
+    if name in ("tc_expand", "expand_gemm"):
+        # output image + the two operands; launches alternate between W2 and W
+        ops = lambda l: 2 * n * l * (4 if tc else 4)
+        return 4 * px + (ops(ldk2) + ops(ldk)) / 2
+    if name in ("tc_spectrum", "spectrum_gemm"):
+        # image operand (mask: bf16 hi only; dL/dI: hi + lo) + partial spectra out
+        img = (2 * ldn * n + 4 * ldn * n) / 2 if tc else (1 * px + 4 * px) / 2
+        return img + slices * (ldk * ldk + ldk2 * ldk2) / 2 * 4
+    if name == "expand_T":
+        return n * (ldk + ldk2) / 2 * (4 if tc else 4)
+    if name == "spectrum_reduce":
+        return slices * (ldk * ldk + ldk2 * ldk2) / 2 * 4
+    if name == "ihat_tcc":
+        return k ** 4 / 2 * 8
+    if name == "shat_tcc":
+        return k ** 4 * 8
+    return None
 
 
 def clip_seeds(base_seed: int, rank: int, world: int, clips_per_rank: int = 1):
@@ -223,140 +247,173 @@ def run_ours(args, wl):
     stream = torch.cuda.current_stream()
 
     n, K, k, iters, beta = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"]
-    prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3}[args.precision]
     o = synth.optics(n, K, k)
     seed = clip_seeds(wl["seed"], rank, world)[0]
     Zt = synth.manhattan_clip(seed) if n == 2048 else synth.rect_clip(seed, n=n)
-    opt = dv.devel_optics_create(n, o.H, o.w, prec)
     target = torch.from_numpy(Zt.ravel().copy()).to(dev)
-    phi = torch.empty(n * n, dtype=torch.float32, device=dev)
-    M = torch.empty(n * n, dtype=torch.uint8, device=dev)
-    L = torch.zeros(iters + 1, dtype=torch.float64, device=dev)
-    l2 = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
-    pvb = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
-    st = torch.zeros(1, dtype=torch.int32, device=dev)
-    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
-    clip = dv.Clip(opt, target, phi, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
+    precs = ["bf16x3", "fp32"] if args.precision == "both" else [args.precision]
 
-    def step():
-        dv.devel_ilt_solve(params, [clip], st, stream)
+    def measure(prec_name):
+        prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3}[prec_name]
+        opt = dv.devel_optics_create(n, o.H, o.w, prec)
+        phi = torch.empty(n * n, dtype=torch.float32, device=dev)
+        M = torch.empty(n * n, dtype=torch.uint8, device=dev)
+        L = torch.zeros(iters + 1, dtype=torch.float64, device=dev)
+        l2 = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
+        pvb = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        clip = dv.Clip(opt, target, phi, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if int(st.item()) != 0:
-        raise RuntimeError(f"solver status {int(st.item())}")
+        def step():
+            dv.devel_ilt_solve(params, [clip], st, stream)
 
-    def timed(nsteps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
-        for i in range(nsteps):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if int(st.item()) != 0:
+            raise RuntimeError(f"solver status {int(st.item())}")
+
+        # timed region: K solves (each one CUDA-graph replay), L2 flushed between them
+        sampler = ClockSampler(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / nsteps
-
-    # timed region: K solves (each one CUDA-graph replay), L2 flushed between them
-    sampler = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ms = timed(args.steps)
-    clocks = sampler.stop()
-    # per-kernel device times: the same K solves again, each a replay of a graph
-    # captured with a CUDA-event pair around every kernel (the library's profiler)
-    dv.devel_profile_start(1 << 16)
-    step()  # capture the profiled graph
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        clocks = sampler.stop()
+        # per-kernel device times: the same K solves again, each a replay of a graph
+        # captured with a CUDA-event pair around every kernel (the library's profiler)
+        dv.devel_profile_start(1 << 16)
+        step()  # capture the profiled graph
         torch.cuda.synchronize()
         dv.devel_profile_collect()
-    ms_profiled = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    prof = dv.devel_profile_stop(collect=False)
-    ms = job_time_ms(ms, dist, dev)
-    value = world * 1000.0 / ms  # clips/s, one clip per GPU per step
-
-    # end to end through the public API with host buffers
-    tgt_host = torch.from_numpy(Zt.ravel().copy()).pin_memory()
-    mask_host = torch.empty(n * n, dtype=torch.uint8).pin_memory()
-    hist_host = torch.empty(iters + 1, dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    for i in range(max(1, min(args.steps, 5))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        target.copy_(tgt_host, non_blocking=True)
+        dv.devel_profile_stop(collect=False)
+        dv.devel_profile_start(1 << 16)
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            pev[i][0].record(stream)
+            step()
+            pev[i][1].record(stream)
+            torch.cuda.synchronize()
+            dv.devel_profile_collect()
+        ms_profiled = sum(a.elapsed_time(b) for a, b in pev) / args.steps
+        prof = dv.devel_profile_stop(collect=False)
+        # the dominant kernel class alone: events around its launches only, so that the
+        # other kernels run (and overlap their launches) as in the timed region
+        dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+        dv.devel_profile_select([dom])
+        dv.devel_profile_start(1 << 16)
         step()
-        mask_host.copy_(M, non_blocking=True)
-        hist_host.copy_(L, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
-    e2e_value = world * 1000.0 / job_time_ms(float(np.median(e2e_ms)), dist, dev)
+        dv.devel_profile_collect()
+        dv.devel_profile_stop(collect=False)
+        dv.devel_profile_start(1 << 16)
+        for i in range(args.steps):
+            flush.zero_()
+            step()
+            torch.cuda.synchronize()
+            dv.devel_profile_collect()
+        dom_prof = dv.devel_profile_stop(collect=False)[dom]
+        dv.devel_profile_select(None)
+        ms = job_time_ms(ms, dist, dev)
 
+        # end to end through the public API with host buffers
+        tgt_host = torch.from_numpy(Zt.ravel().copy()).pin_memory()
+        mask_host = torch.empty(n * n, dtype=torch.uint8).pin_memory()
+        hist_host = torch.empty(iters + 1, dtype=torch.float64).pin_memory()
+        e2e_ms = []
+        for i in range(max(1, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            target.copy_(tgt_host, non_blocking=True)
+            step()
+            mask_host.copy_(M, non_blocking=True)
+            hist_host.copy_(L, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+        e2e_value = world * 1000.0 / job_time_ms(float(np.median(e2e_ms)), dist, dev)
+        res = {"prec": prec_name, "ms": ms, "value": world * 1000.0 / ms, "clocks": clocks, "prof": prof,
+               "dom": dom, "dom_prof": dom_prof, "ms_profiled": ms_profiled, "e2e": e2e_value, "final_l2": int(l2[-1].item()),
+               "final_pvb": int(pvb[-1].item()), "final_loss": float(L[-1].item())}
+        dv.devel_optics_destroy(opt)
+        return res
+
+    results = [measure(p) for p in precs]
+    head = results[0]
     if rank == 0:
         hbm, bf16, src = measured_peaks()
-        sm_mhz = clocks.get("sm_mhz") or 2070.0
-        # dominant kernel class by summed device time
+        prof = head["prof"]
+        tc = head["prec"] == "bf16x3"
         tot = sum(v[1] for v in prof.values())
-        dom = max(prof.items(), key=lambda kv: kv[1][1])
-        name, (cnt, kms) = dom
-        kind, cost = kernel_cost(name, n, K, k)
+        kernels = {}
+        for kn, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            ent = {"launches": c, "ms": round(t, 3), "share": round(t / tot, 4),
+                   "avg_us": round(t / c * 1000.0, 2)}
+            b = kernel_bytes(kn, n, K, k, tc)
+            if b:
+                ent["gbs"] = round(b / (t / c / 1000.0) / 1e9, 1)
+                ent["frac_hbm"] = round(ent["gbs"] / hbm, 3)
+            kernels[kn] = ent
+        name = head["dom"]
+        cnt, kms = head["dom_prof"]
         avg_s = kms / cnt / 1000.0
-        if kind == "hbm":
-            ach = cost / avg_s / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "peak_source": src}
-        elif kind == "flops":
-            ach = cost / avg_s / 1e12
-            if name.startswith("tc_"):
-                roof = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                        "frac": ach / bf16, "peak_source": src}
-            else:
-                pk = simt_fp32_peak_tflops(sm_mhz)
-                roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                        "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
-        else:
-            roof = {"bound": None}
-        roof.update({"kernel": name, "launches_per_step": cnt / args.steps, "avg_launch_us": avg_s * 1e6,
-                     "share": kms / tot, "traffic": None,
-                     "timing": "CUDA events around each kernel, captured into the solve's graph, over a "
-                               "second pass of the K timed solves (%.2f ms/solve with the events vs %.2f ms)"
-                               % (ms_profiled, ms)})
-        kernels = {kn: {"launches": c, "ms": round(t, 3), "share": round(t / tot, 4)} for kn, (c, t) in
-                   sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        b = kernel_bytes(name, n, K, k, tc) or 0.0
+        ach = b / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": src + " (burst copy)", "traffic": TRAFFIC.get((name, head["prec"])),
+                "kernel": name, "bytes_per_launch": b, "launches_per_step": cnt / args.steps,
+                "avg_launch_us": avg_s * 1e6, "share": prof[name][1] / tot,
+                "timing": "CUDA events around this kernel's launches only, recorded inside the solve's graph, "
+                          "over K further solves; shares from a pass with events around every kernel "
+                          "(%.2f ms/solve with those events vs %.2f ms without)" % (head["ms_profiled"], head["ms"])}
         if args.no_cpu_baseline:
             cpu = None
         else:
             v, per_clip, sample = oracle_sample(wl)
             cpu = {"value": v, "unit": "clips/s", "cores": 1, "kind": "oracle", "sample": sample}
+        ms = head["ms"]
         out = {
-            "metric": METRIC, "value": value, "unit": "clips/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": head["value"], "unit": "clips/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+            "vs_baseline": None, "dtype": "f32" if head["prec"] == "fp32" else "bf16x3",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "K": K, "k": k, "iters": iters, "beta": beta,
                        "dt": 0.5, "lambda": 0.1, "reinit_every": 5, "clips_per_gpu_per_step": 1,
-                       "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "precision": head["prec"], "init": "zero level set (TSDF of the target)",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
             "litho_tflops": {"window_method": window_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12,
                              "socs_equivalent": algorithmic_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12},
-            "e2e": {"value": e2e_value, "unit": "clips/s", "h2d_bytes_per_step": n * n,
+            "e2e": {"value": head["e2e"], "unit": "clips/s", "h2d_bytes_per_step": n * n,
                     "d2h_bytes_per_step": n * n + 8 * (iters + 1)},
             "gpu_launches": int(sum(c for c, _ in prof.values())),
             "roofline": roof,
             "kernels": kernels,
-            "clocks": clocks,
+            "clocks": head["clocks"],
             "cpu_baseline": cpu,
-            "final_l2": int(l2[-1].item()), "final_pvb": int(pvb[-1].item()),
+            "final_l2": head["final_l2"], "final_pvb": head["final_pvb"],
         }
+        if len(results) > 1:
+            ref = results[1]
+            q_head = head["final_l2"] + head["final_pvb"]
+            q_ref = ref["final_l2"] + ref["final_pvb"]
+            out["plain_fp32"] = {"value": ref["value"], "ms_per_step": ref["ms"], "e2e": ref["e2e"],
+                                 "final_l2": ref["final_l2"], "final_pvb": ref["final_pvb"],
+                                 "clocks": ref["clocks"]}
+            out["converged"] = {"rule": "final L2 + PVB within 1% of the plain FP32 solve's",
+                                "ok": bool(q_head <= 1.01 * q_ref), "ratio": q_head / max(q_ref, 1),
+                                "speedup_vs_plain_fp32": head["value"] / ref["value"]}
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
@@ -366,11 +423,12 @@ def run_ours(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="manhattan2048")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["both", "fp32", "bf16x3"], default="both",
+                    help="both: the compensated-BF16 solve is the headline, the plain FP32 solve its comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -283,6 +283,11 @@ int devel_profile_collect(void);
 int devel_profile_stop(void);
 /* Number of kernel classes. */
 int devel_profile_kinds(void);
+/* Restrict the events of the next profiles to the kernel classes whose bit
+ * (1 << kind) is set in kind_mask (all classes by default): fewer events
+ * disturb the timing of the selected kernels less. DEVEL_EINVAL while a
+ * profile is open. */
+int devel_profile_select(unsigned long long kind_mask);
 /* Name, launch count and summed device time (ms) of kernel class `kind`
  * accumulated by devel_profile_collect. */
 int devel_profile_query(int kind, const char** name, int* launches, double* total_ms);

@@ -86,6 +86,7 @@ _sig("devel_profile_start", [_I])
 _sig("devel_profile_stop", [])
 _sig("devel_profile_collect", [])
 _sig("devel_profile_kinds", [])
+_sig("devel_profile_select", [ctypes.c_ulonglong])
 _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                              ctypes.POINTER(ctypes.c_double)])
 
@@ -94,7 +95,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_optics_n", "devel_optics_check", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
-            "devel_reinit_sdf_static")
+            "devel_reinit_sdf_static", "devel_profile_select")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -275,6 +276,30 @@ def devel_ilt_solve(params: devel_ilt_params, clips, status, stream=None):
 
 def devel_profile_start(capacity: int = 1 << 16):
     _check(_lib.devel_profile_start(capacity))
+
+
+def devel_profile_kind_names() -> list:
+    """Kernel class names, indexed by kind."""
+    names = []
+    for k in range(_lib.devel_profile_kinds()):
+        name = ctypes.c_char_p()
+        cnt = _I()
+        ms = ctypes.c_double()
+        _check(_lib.devel_profile_query(k, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)))
+        names.append(name.value.decode())
+    return names
+
+
+def devel_profile_select(kinds=None):
+    """Limit the events of the next profiles to the named kernel classes (None: all)."""
+    if kinds is None:
+        mask = (1 << 64) - 1
+    else:
+        names = devel_profile_kind_names()
+        mask = 0
+        for kname in kinds:
+            mask |= 1 << names.index(kname)
+    _check(_lib.devel_profile_select(mask))
 
 
 def devel_profile_collect():

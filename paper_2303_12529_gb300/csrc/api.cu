@@ -155,56 +155,132 @@ static void make_basis(int n, int kw, int ldk, std::vector<float>& t, std::vecto
 
 using namespace devel;
 
-static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
-                         cudaStream_t s) {
-    DEVEL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-    for (int c = 0; c < nclips; ++c) {
-        const devel_clip& cl = clips[c];
-        const devel_optics* o = cl.optics;
-        const int n = o->n;
-        const Workspace& w = o->ws;
-        float* phi = cl.phi;
-        float* phi_alt = w.phi2;
-        int rc;
-        if (!cl.phi_given) {
-            rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
-            if (rc) return rc;
-        }
-        const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-        rc = launch_mask_from_phi(n, phi, w.M, s);
+// All iterations of one clip on stream s (the clip's optics workspace is used
+// exclusively by this sequence of launches).
+static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* status, cudaStream_t s) {
+    const devel_optics* o = cl.optics;
+    const int n = o->n;
+    const Workspace& w = o->ws;
+    float* phi = cl.phi;
+    float* phi_alt = w.phi2;
+    int rc;
+    if (!cl.phi_given) {
+        rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
         if (rc) return rc;
-        if (tcp) {  // later masks come out of the level-set step already in bf16
-            rc = tc::launch_mask_bf16(w.M, n, o->ldn, o->Xhi, s);
+    }
+    const bool tcp = o->precision == DEVEL_PREC_BF16X3;
+    rc = launch_mask_from_phi(n, phi, w.M, s);
+    if (rc) return rc;
+    if (tcp) {  // later masks come out of the level-set step already in bf16
+        rc = tc::launch_mask_bf16(w.M, n, o->ldn, o->Xhi, s);
+        if (rc) return rc;
+    }
+    for (int t = 0; t <= p->iters; ++t) {
+        // image the current mask, resist loss and dL/dI (in place in bufI)
+        rc = tcp ? launch_spectrum_mask_resident(o, o->W, w.mhat, s) : launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
+        if (rc) return rc;
+        rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr,
+                                    cl.loss_hist ? cl.loss_hist + t : nullptr,
+                                    cl.l2_hist ? cl.l2_hist + t : nullptr,
+                                    cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
+        if (rc) return rc;
+        if (t == p->iters) break;  // the final mask is imaged for its metrics only
+        rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
+        if (rc) return rc;
+        rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
+                                  tcp ? o->Xhi : nullptr, o->ldn, s);
+        if (rc) return rc;
+        float* tmp = phi;
+        phi = phi_alt;
+        phi_alt = tmp;
+        const int gi = p->start_iter + t;
+        if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
+            rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
             if (rc) return rc;
         }
-        for (int t = 0; t <= p->iters; ++t) {
-            // image the current mask, resist loss and dL/dI (in place in bufI)
-            rc = tcp ? launch_spectrum_mask_resident(o, o->W, w.mhat, s) : launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
+    }
+    if (phi != cl.phi)
+        DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.phi, phi, sizeof(float) * n * n, cudaMemcpyDeviceToDevice, s));
+    if (cl.mask_out)
+        DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.mask_out, w.M, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    return DEVEL_OK;
+}
+
+// Several clips: clips that share an optics handle (and so its workspace) form a chain
+// run in order; chains are spread over up to kBranches streams forked from s and
+// joined back into it, so that independent clips' kernels run concurrently (as
+// parallel branches when captured into a graph). Chains go longest first to the
+// branch with the least work so far (work ~ n^2 per clip).
+constexpr int kBranches = 16;
+struct BranchPool {
+    cudaStream_t st[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
+    bool ready = false;
+};
+std::mutex g_branch_mu;
+BranchPool g_branch[64];
+
+// Streams and events of the device's branch pool (created on first use, outside any capture).
+static int branch_pool(int dev, BranchPool** out) {
+    BranchPool& b = g_branch[dev];
+    if (!b.ready) {
+        for (int i = 0; i < kBranches; ++i) {
+            DEVEL_CUDA_TRY(cudaStreamCreateWithFlags(&b.st[i], cudaStreamNonBlocking));
+            DEVEL_CUDA_TRY(cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming));
+        }
+        DEVEL_CUDA_TRY(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+        b.ready = true;
+    }
+    *out = &b;
+    return DEVEL_OK;
+}
+
+static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
+                         cudaStream_t s, BranchPool* pool) {
+    DEVEL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    std::vector<const devel_optics*> handles;
+    std::vector<std::vector<int>> chains;
+    for (int c = 0; c < nclips; ++c) {
+        size_t h = 0;
+        while (h < handles.size() && handles[h] != clips[c].optics) ++h;
+        if (h == handles.size()) {
+            handles.push_back(clips[c].optics);
+            chains.emplace_back();
+        }
+        chains[h].push_back(c);
+    }
+    if (chains.size() <= 1 || !pool) {
+        for (int c = 0; c < nclips; ++c) {
+            int rc = enqueue_clip(p, clips[c], status, s);
             if (rc) return rc;
-            rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr,
-                                        cl.loss_hist ? cl.loss_hist + t : nullptr,
-                                        cl.l2_hist ? cl.l2_hist + t : nullptr,
-                                        cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
-            if (rc) return rc;
-            if (t == p->iters) break;  // the final mask is imaged for its metrics only
-            rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
-            if (rc) return rc;
-            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
-                                      tcp ? o->Xhi : nullptr, o->ldn, s);
-            if (rc) return rc;
-            float* tmp = phi;
-            phi = phi_alt;
-            phi_alt = tmp;
-            const int gi = p->start_iter + t;
-            if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
-                rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
+        }
+        return DEVEL_OK;
+    }
+    const int nb = (int)std::min<size_t>(chains.size(), kBranches);
+    std::vector<double> cost(chains.size(), 0.0), load(nb, 0.0);
+    std::vector<int> order(chains.size());
+    for (size_t h = 0; h < chains.size(); ++h) {
+        for (int c : chains[h]) cost[h] += (double)clips[c].optics->n * clips[c].optics->n;
+        order[h] = (int)h;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> branch(nb);
+    for (int h : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] += cost[h];
+        branch[b].push_back(h);
+    }
+    DEVEL_CUDA_TRY(cudaEventRecord(pool->fork, s));
+    for (int b = 0; b < nb; ++b) {
+        cudaStream_t bs = pool->st[b];
+        DEVEL_CUDA_TRY(cudaStreamWaitEvent(bs, pool->fork, 0));
+        for (int h : branch[b])
+            for (int c : chains[h]) {
+                int rc = enqueue_clip(p, clips[c], status, bs);
                 if (rc) return rc;
             }
-        }
-        if (phi != cl.phi)
-            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.phi, phi, sizeof(float) * n * n, cudaMemcpyDeviceToDevice, s));
-        if (cl.mask_out)
-            DEVEL_CUDA_TRY(cudaMemcpyAsync(cl.mask_out, w.M, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+        DEVEL_CUDA_TRY(cudaEventRecord(pool->join[b], bs));
+        DEVEL_CUDA_TRY(cudaStreamWaitEvent(s, pool->join[b], 0));
     }
     return DEVEL_OK;
 }
@@ -254,7 +330,7 @@ static int solve_graph(const devel_ilt_params* p, int nclips, const devel_clip* 
                        cudaStream_t s) {
     int dev = 0;
     DEVEL_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return enqueue_solve(p, nclips, clips, status, s);
+    if (dev < 0 || dev >= 64) return enqueue_solve(p, nclips, clips, status, s, nullptr);
     std::vector<unsigned char> key = solve_key(p, nclips, clips, status, dev);
     std::lock_guard<std::mutex> lock(g_graph_mu);
     for (size_t i = 0; i < g_graphs.size(); ++i) {
@@ -269,8 +345,14 @@ static int solve_graph(const devel_ilt_params* p, int nclips, const devel_clip* 
     if (!g_capture_stream[dev])
         DEVEL_CUDA_TRY(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
     cudaStream_t cs = g_capture_stream[dev];
+    BranchPool* pool = nullptr;
+    {
+        std::lock_guard<std::mutex> bl(g_branch_mu);
+        int rc0 = branch_pool(dev, &pool);
+        if (rc0) return rc0;
+    }
     DEVEL_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_solve(p, nclips, clips, status, cs);
+    int rc = enqueue_solve(p, nclips, clips, status, cs, pool);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (rc) {
@@ -506,6 +588,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
             if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, w.ldk, o->ldn, o->ldn, w.ldk);
             if (!rc) rc = tc::make_map(&tw.m_basisT_hi, tw.basisT_hi, n, w.ldk, w.ldk, 128);
             if (!rc) rc = tc::make_map(&tw.m_basisT_lo, tw.basisT_lo, n, w.ldk, w.ldk, 128);
+            if (!rc) rc = tc::make_map(&tw.m_basisT64_hi, tw.basisT_hi, n, w.ldk, w.ldk, 64);
+            if (!rc) rc = tc::make_map(&tw.m_basisT64_lo, tw.basisT_lo, n, w.ldk, w.ldk, 64);
             if (!rc) rc = tc::make_map(&tw.m_acat_hi, o->Acat_hi, n, w.ldk, w.ldk, 128);
             if (!rc) rc = tc::make_map(&tw.m_acat_lo, o->Acat_lo, n, w.ldk, w.ldk, 128);
         }
@@ -634,7 +718,14 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         CHECK_OPT_PTR(cl.pvb_hist, "clip.pvb_hist");
     }
     if (p->use_graph) return solve_graph(p, nclips, clips, status, s);
-    return enqueue_solve(p, nclips, clips, status, s);
+    int dev = 0;
+    DEVEL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return enqueue_solve(p, nclips, clips, status, s, nullptr);
+    std::lock_guard<std::mutex> bl(g_branch_mu);  // the pool's events serve one call at a time
+    BranchPool* pool = nullptr;
+    int rc = branch_pool(dev, &pool);
+    if (rc) return rc;
+    return enqueue_solve(p, nclips, clips, status, s, pool);
 }
 
 }  // extern "C"

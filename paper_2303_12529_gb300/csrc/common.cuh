@@ -40,9 +40,13 @@ unsigned prof_generation();
 void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
 
-// Resist constants as the kernels use them (doses squared).
+// Per-corner constants of the resist (Sec. III-A), folded on the host:
+// exponent u_c = a_c I + b = -log2(e) sigma_z (d_c^2 I - I_th), so that Z_c = 1 / (1 + 2^u_c);
+// gradient coefficient k_c = 2 sigma_z coef_c d_c^2 (coef = alpha at nominal, beta at the corners).
 struct ResistArgs {
-    float sigma_z, I_th, alpha, beta, d2in, d2out;
+    float I_th, d2in, d2out;
+    float a_nom, a_in, a_out, b;
+    float k_nom, k_in, k_out;
 };
 
 // Epilogues of the contraction GEMMs.
@@ -114,7 +118,7 @@ struct Window {
 struct Workspace {
     float* Ppart = nullptr;    // [nsplit][n][ldk2] split-K slices of P (reduction stage 1)
     float* P = nullptr;        // [n][ldk2] stage-1 slices summed
-    float* Q = nullptr;        // [nq][ldk2][ldk2] split-K slices of reduction stage 2
+    float* Q = nullptr;        // [slices][ldk2][ldk2] partial sums of reduction stage 2
     float2* mhat = nullptr;    // [k*k]   mask spectrum on W, scaled 1/n^2
     float2* Ihat = nullptr;    // [k2*k2] aerial-image spectrum on W2
     float2* rhat = nullptr;    // [k2*k2] dL/dI spectrum on W2, scaled 1/n^2
@@ -143,6 +147,7 @@ struct TcWindow {
     __nv_bfloat16* basisT_lo = nullptr;
     CUtensorMap m_basis_hi, m_basis_lo, m_basisT_hi, m_basisT_lo, m_acat_hi, m_acat_lo;
     CUtensorMap m_basis128_hi, m_basis128_lo;  // same tables, 128-row boxes (fused reduction, phase 2)
+    CUtensorMap m_basisT64_hi, m_basisT64_lo;  // basis^T with 64-row boxes (expansion tiles of width 64)
 };
 
 }  // namespace devel
@@ -157,6 +162,7 @@ struct devel_optics {
     __nv_bfloat16* Acat_lo = nullptr;
     CUtensorMap m_X_hi, m_X_lo;
     int* tc_err = nullptr;            // device flag: DEVEL_ETIMEOUT from a bounded wait
+    int tc_expand_bn = 64;            // output tile width of the tensor-core expansion (64 or 128)
     int nsplit;               // split-K slices of reduction stage 1 (over x)
     int nq;                   // split-K slices of reduction stage 2 (over y)
     int npart_red;            // size of the generic reduction partial arrays

@@ -170,8 +170,10 @@ __global__ void k_sum_slices(const float* __restrict__ Ppart, int nz, size_t len
 
 // Xhat(a, b) = scale [(Q[a][b] - Q[kw+a][kw+b]) - i (Q[a][kw+b] + Q[kw+a][b])], Q summed over
 // nq partial slices. Block = (row a, 32 columns b); lane = column, warp w sums slices
-// w, w + 8, ... (coalesced row reads), then the 8 warp sums are added in warp order.
-constexpr int kFinWarps = 8;
+// w, w + 16, ... (coalesced row reads, eight slices' loads in flight), then the 16 warp
+// sums are added in warp order.
+constexpr int kFinWarps = 16;
+constexpr int kFinUnroll = 8;
 __global__ void __launch_bounds__(32 * kFinWarps)
 k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, float2* __restrict__ out) {
     __shared__ float2 part[kFinWarps][32];
@@ -180,12 +182,28 @@ k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, 
     float re = 0.f, im = 0.f;
     if (b < kw) {
         const size_t st = (size_t)ldq * ldq;
-        const float* q = Q + (size_t)w * st;
-        const float* r0 = q + (size_t)a * ldq;
-        const float* r1 = q + (size_t)(kw + a) * ldq;
-        for (int z = w; z < nq; z += kFinWarps, r0 += kFinWarps * st, r1 += kFinWarps * st) {
-            re += __ldcg(r0 + b) - __ldcg(r1 + kw + b);
-            im -= __ldcg(r0 + kw + b) + __ldcg(r1 + b);
+        const size_t o0 = (size_t)a * ldq + b, o1 = (size_t)(kw + a) * ldq + b;
+        int z = w;
+        for (; z + (kFinUnroll - 1) * kFinWarps < nq; z += kFinUnroll * kFinWarps) {
+            float v[kFinUnroll][4];
+#pragma unroll
+            for (int u = 0; u < kFinUnroll; ++u) {
+                const float* q = Q + (size_t)(z + u * kFinWarps) * st;
+                v[u][0] = __ldcg(q + o0);
+                v[u][1] = __ldcg(q + o1 + kw);
+                v[u][2] = __ldcg(q + o0 + kw);
+                v[u][3] = __ldcg(q + o1);
+            }
+#pragma unroll
+            for (int u = 0; u < kFinUnroll; ++u) {
+                re += v[u][0] - v[u][1];
+                im -= v[u][2] + v[u][3];
+            }
+        }
+        for (; z < nq; z += kFinWarps) {
+            const float* q = Q + (size_t)z * st;
+            re += __ldcg(q + o0) - __ldcg(q + o1 + kw);
+            im -= __ldcg(q + o0 + kw) + __ldcg(q + o1);
         }
     }
     part[w][lane] = make_float2(re, im);
@@ -206,6 +224,7 @@ void launch_spec_final(const float* Q, int nq, int ldq, int kw, float2* out, int
 // --------------------------------------------------------------------------
 // frequency-domain sums with the rank-K TCC (one warp per output frequency)
 // --------------------------------------------------------------------------
+
 // Fixed-order block reduction of a float2 over 128 threads (4 warps); valid in thread 0.
 __device__ __forceinline__ float2 block_sum2_128(float2 v, float2* sh) {
     v = warp_sum2(v);
@@ -473,9 +492,11 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
     ep.vpart = ws.vpart;
     if (tcp) {
         const TcWindow& tw = tc_window(o, w);
-        tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, &tw.m_basisT_hi, &tw.m_basisT_lo, 1};
-        if (nparts) *nparts = ((n + 127) / 128) * ((n + 127) / 128);
-        return tc::launch_gemm(op, 128, epi, PK_TC_EXPAND, n, n, w.ldk, (w.ldk + 63) / 64 * 64, ep, o->tc_err, s);
+        const int bn = o->tc_expand_bn;
+        tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, bn == 64 ? &tw.m_basisT64_hi : &tw.m_basisT_hi,
+                        bn == 64 ? &tw.m_basisT64_lo : &tw.m_basisT_lo, 1};
+        if (nparts) *nparts = tc::expand_grid(n, n, bn);
+        return tc::launch_expand(op, bn, epi, n, n, w.ldk, ep, o->tc_err, s);
     }
     if (nparts) *nparts = expand_parts(n);
     if (epi == EPI_VEL)

@@ -4,7 +4,8 @@
 // library is bracketed by two events recorded on the launching stream; after
 // devel_profile_stop the host reads per-kernel launch counts and summed
 // device time. Off by default; when off the cost is one branch per launch.
-// Not for use inside stream capture.
+// devel_profile_select limits the events to some kernel classes (fewer events
+// disturb the timed kernels less).
 #include <cstring>
 #include <vector>
 
@@ -32,12 +33,13 @@ static int g_launches[PROF_NKINDS];
 static double g_ms[PROF_NKINDS];
 static bool g_overflow = false;
 static unsigned g_generation = 0;  // bumped by every devel_profile_start
+static unsigned long long g_select = ~0ull;  // kernel classes that get events
 
 bool prof_on() { return g_on; }
 unsigned prof_generation() { return g_generation; }
 
 void prof_begin(int kind, cudaStream_t s) {
-    if (!g_on) return;
+    if (!g_on || !((g_select >> kind) & 1ull)) return;
     if (g_used >= g_pool.size()) {
         g_overflow = true;
         g_open_kind = -1;
@@ -62,6 +64,12 @@ void prof_end(int kind, cudaStream_t s) {
 using namespace devel;
 
 extern "C" {
+
+int devel_profile_select(unsigned long long kind_mask) {
+    if (g_on) return set_error(DEVEL_EINVAL, "devel_profile_select: a profile is open");
+    g_select = kind_mask;
+    return DEVEL_OK;
+}
 
 int devel_profile_start(int capacity) {
     if (capacity < 1 || capacity > (1 << 22))

@@ -7,7 +7,8 @@
 //
 //   k_edt_cols  one pass per column strip: g to the nearest pixel of each
 //               class along the column, both packed in one 32-bit word
-//               (two 16-bit distances, 0xFFFF = none);
+//               (two 16-bit distances, 0xFFFF = none), from per-segment bit
+//               masks and scans over the segments;
 //   k_edt_rows  one block per row: the row of packed g in shared memory; each
 //               pixel searches outwards |dx| = 1, 2, ... while dx^2 is below
 //               its best candidate, so the work per pixel is its distance.
@@ -23,61 +24,72 @@
 namespace devel {
 namespace {
 
-constexpr int kCW = 32;   // columns per block
-constexpr int kSeg = 32;  // segments per column
+constexpr int kCX = 8;     // columns per block
+constexpr int kSegs = 128; // segments per column (<= 64 rows each for n <= 8192)
 constexpr unsigned kNone = 0xFFFFu;
+constexpr int kNoPos = INT_MAX;
 
-__global__ void __launch_bounds__(kCW * kSeg)
+// Column pass. Thread (column x, segment sg) holds its segment's mask bits in one
+// 64-bit word; the nearest pixel of each class above the segment is the prefix
+// maximum of the segments' last positions, the nearest below the suffix minimum of
+// their first positions (Hillis-Steele scans over the block's segments). Every row
+// of the segment then finds its nearest pixel of each class on either side with one
+// leading/trailing-bit count, and g is written once.
+__global__ void __launch_bounds__(kCX * kSegs)
 k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g) {
-    __shared__ int lastv[2][kSeg][kCW];
-    __shared__ int firstv[2][kSeg][kCW];
+    __shared__ int sc[2][4][kSegs][kCX];  // [buffer][last0, last1, first0, first1][segment][column]
     const int cx = threadIdx.x, sg = threadIdx.y;
-    const int x = blockIdx.x * kCW + cx;
-    const int L = (n + kSeg - 1) / kSeg;
-    const int ys = min(n, sg * L), ye = min(n, ys + L);
-    int f0 = -1, f1 = -1, l0 = -1, l1 = -1;
+    const int x = blockIdx.x * kCX + cx;
+    const int L = (n + kSegs - 1) / kSegs;
+    const int ys = min(n, sg * L), len = min(n, ys + L) - ys;
+    unsigned long long bits = 0ull;
     if (x < n) {
-        for (int y = ys; y < ye; ++y) {
-            if (mask[(size_t)y * n + x]) {
-                if (f1 < 0) f1 = y;
-                l1 = y;
-            } else {
-                if (f0 < 0) f0 = y;
-                l0 = y;
-            }
+        for (int i = 0; i < len; ++i)
+            if (mask[(size_t)(ys + i) * n + x]) bits |= 1ull << i;
+    }
+    const unsigned long long valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
+    const unsigned long long b1 = bits, b0 = ~bits & valid;
+    sc[0][0][sg][cx] = b0 ? ys + 63 - __clzll((long long)b0) : -1;
+    sc[0][1][sg][cx] = b1 ? ys + 63 - __clzll((long long)b1) : -1;
+    sc[0][2][sg][cx] = b0 ? ys + __ffsll((long long)b0) - 1 : kNoPos;
+    sc[0][3][sg][cx] = b1 ? ys + __ffsll((long long)b1) - 1 : kNoPos;
+    int cur = 0;
+    for (int off = 1; off < kSegs; off <<= 1) {
+        __syncthreads();
+        int l0 = sc[cur][0][sg][cx], l1 = sc[cur][1][sg][cx];
+        int f0 = sc[cur][2][sg][cx], f1 = sc[cur][3][sg][cx];
+        if (sg >= off) {
+            l0 = max(l0, sc[cur][0][sg - off][cx]);
+            l1 = max(l1, sc[cur][1][sg - off][cx]);
         }
+        if (sg + off < kSegs) {
+            f0 = min(f0, sc[cur][2][sg + off][cx]);
+            f1 = min(f1, sc[cur][3][sg + off][cx]);
+        }
+        sc[cur ^ 1][0][sg][cx] = l0;
+        sc[cur ^ 1][1][sg][cx] = l1;
+        sc[cur ^ 1][2][sg][cx] = f0;
+        sc[cur ^ 1][3][sg][cx] = f1;
+        cur ^= 1;
     }
-    firstv[0][sg][cx] = f0;
-    firstv[1][sg][cx] = f1;
-    lastv[0][sg][cx] = l0;
-    lastv[1][sg][cx] = l1;
     __syncthreads();
-    if (x >= n) return;
-    int up0 = -1, up1 = -1, dn0 = -1, dn1 = -1;
-    for (int s = sg - 1; s >= 0 && (up0 < 0 || up1 < 0); --s) {
-        if (up0 < 0) up0 = lastv[0][s][cx];
-        if (up1 < 0) up1 = lastv[1][s][cx];
-    }
-    for (int s = sg + 1; s < kSeg && (dn0 < 0 || dn1 < 0); ++s) {
-        if (dn0 < 0) dn0 = firstv[0][s][cx];
-        if (dn1 < 0) dn1 = firstv[1][s][cx];
-    }
-    // downward sweep: distance to the nearest pixel of each class at or above
-    int p0 = up0, p1 = up1;
-    for (int y = ys; y < ye; ++y) {
-        if (mask[(size_t)y * n + x]) p1 = y; else p0 = y;
-        const unsigned d0 = p0 < 0 ? kNone : (unsigned)(y - p0);
-        const unsigned d1 = p1 < 0 ? kNone : (unsigned)(y - p1);
-        g[(size_t)y * n + x] = d0 | (d1 << 16);
-    }
-    // upward sweep: combine with the nearest at or below
-    int q0 = dn0, q1 = dn1;
-    for (int y = ye - 1; y >= ys; --y) {
-        if (mask[(size_t)y * n + x]) q1 = y; else q0 = y;
-        const unsigned w = g[(size_t)y * n + x];
-        unsigned d0 = w & 0xFFFFu, d1 = w >> 16;
-        if (q0 >= 0) d0 = min(d0, (unsigned)(q0 - y));
-        if (q1 >= 0) d1 = min(d1, (unsigned)(q1 - y));
+    if (x >= n || len == 0) return;
+    const int up0 = sg > 0 ? sc[cur][0][sg - 1][cx] : -1;
+    const int up1 = sg > 0 ? sc[cur][1][sg - 1][cx] : -1;
+    const int dn0 = sg + 1 < kSegs ? sc[cur][2][sg + 1][cx] : kNoPos;
+    const int dn1 = sg + 1 < kSegs ? sc[cur][3][sg + 1][cx] : kNoPos;
+    for (int i = 0; i < len; ++i) {
+        const int y = ys + i;
+        const unsigned long long le = (2ull << i) - 1ull, ge = ~0ull << i;
+        const unsigned long long a0 = b0 & le, a1 = b1 & le, c0 = b0 & ge, c1 = b1 & ge;
+        const int pa0 = a0 ? ys + 63 - __clzll((long long)a0) : up0;
+        const int pa1 = a1 ? ys + 63 - __clzll((long long)a1) : up1;
+        const int pb0 = c0 ? ys + __ffsll((long long)c0) - 1 : dn0;
+        const int pb1 = c1 ? ys + __ffsll((long long)c1) - 1 : dn1;
+        unsigned d0 = pa0 >= 0 ? (unsigned)(y - pa0) : kNone;
+        unsigned d1 = pa1 >= 0 ? (unsigned)(y - pa1) : kNone;
+        if (pb0 != kNoPos) d0 = min(d0, (unsigned)(pb0 - y));
+        if (pb1 != kNoPos) d1 = min(d1, (unsigned)(pb1 - y));
         g[(size_t)y * n + x] = d0 | (d1 << 16);
     }
 }
@@ -192,7 +204,7 @@ int reinit_init_attrs() {
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                   cudaStream_t s) {
     prof_begin(PK_EDT_COLS, s);
-    k_edt_cols<<<(n + kCW - 1) / kCW, dim3(kCW, kSeg), 0, s>>>(mask, n, reinterpret_cast<unsigned*>(d2));
+    k_edt_cols<<<(n + kCX - 1) / kCX, dim3(kCX, kSegs), 0, s>>>(mask, n, reinterpret_cast<unsigned*>(d2));
     prof_end(PK_EDT_COLS, s);
     DEVEL_LAUNCH_CHECK("k_edt_cols");
     prof_begin(PK_EDT_ROWS, s);

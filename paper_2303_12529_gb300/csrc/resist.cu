@@ -5,11 +5,10 @@
 // uses +/-2% dose). Sec. II-C: squared L2 = #{[I >= I_th] != Z_t}, PVBand =
 // #{[d_in^2 I >= I_th] xor [d_out^2 I >= I_th]}.
 //
-// The standalone kernel is one HBM pass (read I and Z_t, write R: 9 B/px);
-// inside the solver the same per-pixel code runs in the epilogue of the
-// forward expansion instead (resist.cuh). Sums are FP32 per thread, FP64 from
-// the warp up, reduced per block in a fixed order and then over blocks in
-// block order, so results are bitwise reproducible.
+// One HBM pass: read I and Z_t, write R (FP32, 9 B/px) or its bf16 hi/lo split
+// (the operand of the adjoint's reduction, 9 B/px). Sums are FP32 up to the warp,
+// FP64 from the block up, reduced in a fixed order and then over blocks in block
+// order, so results are bitwise reproducible.
 #include "resist.cuh"
 
 namespace devel {
@@ -90,53 +89,60 @@ __device__ void resist_final_block(const double* __restrict__ dpart, const long 
     if (status && !isfinite(L)) *status = DEVEL_ENAN;
 }
 
-// Rows y = blockIdx.x, blockIdx.x + gridDim.x, ...; each thread takes kGrp groups of
-// four adjacent pixels per pass, issuing all their loads before any arithmetic.
+// Rows y = blockIdx.x, blockIdx.x + gridDim.x, ... taken two at a time; each thread
+// takes kGrp groups of four adjacent pixels in both rows and issues all their loads
+// before any arithmetic.
 constexpr int kGrp = 2;
+constexpr int kItems = 2 * kGrp;
 
 __global__ void __launch_bounds__(kThreads)
 k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, int n, ResistArgs p,
          float* __restrict__ R, __nv_bfloat16* __restrict__ Rhi, __nv_bfloat16* __restrict__ Rlo, int ldr,
          double* __restrict__ dpart, long long* __restrict__ lpart, ResistOut out) {
-    __shared__ double sd[3][32];
-    __shared__ long long sl[2][32];
+    __shared__ float sf[3][32];
+    __shared__ int si[2][32];
     LossAcc acc;
     const bool vec = (n & 3) == 0;
     const int span = blockDim.x * 4;
-    for (int y = blockIdx.x; y < n; y += gridDim.x) {
-        const size_t base = (size_t)y * n;
+    for (int y0 = blockIdx.x; y0 < n; y0 += 2 * gridDim.x) {
         for (int xg = threadIdx.x * 4; xg < n; xg += kGrp * span) {
-            float iv[kGrp][4];
-            unsigned char zv[kGrp][4];
+            float iv[kItems][4];
+            unsigned char zv[kItems][4];
+            bool ok[kItems];
 #pragma unroll
-            for (int q = 0; q < kGrp; ++q) {
-                const int x0 = xg + q * span;
-                if (vec && x0 < n) {
-                    const float4 f = *reinterpret_cast<const float4*>(I + base + x0);
-                    const uchar4 z = *reinterpret_cast<const uchar4*>(Zt + base + x0);
-                    iv[q][0] = f.x; iv[q][1] = f.y; iv[q][2] = f.z; iv[q][3] = f.w;
-                    zv[q][0] = z.x; zv[q][1] = z.y; zv[q][2] = z.z; zv[q][3] = z.w;
+            for (int u = 0; u < kItems; ++u) {
+                const int y = y0 + (u / kGrp) * gridDim.x;
+                const int x0 = xg + (u % kGrp) * span;
+                ok[u] = y < n && x0 < n;
+                const size_t base = (size_t)y * n + x0;
+                if (ok[u] && vec) {
+                    const float4 f = *reinterpret_cast<const float4*>(I + base);
+                    const uchar4 z = *reinterpret_cast<const uchar4*>(Zt + base);
+                    iv[u][0] = f.x; iv[u][1] = f.y; iv[u][2] = f.z; iv[u][3] = f.w;
+                    zv[u][0] = z.x; zv[u][1] = z.y; zv[u][2] = z.z; zv[u][3] = z.w;
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const bool in = x0 + j < n;
-                        iv[q][j] = in ? I[base + x0 + j] : 0.f;
-                        zv[q][j] = in ? Zt[base + x0 + j] : 0;
+                        const bool in = ok[u] && x0 + j < n;
+                        iv[u][j] = in ? I[base + j] : 0.f;
+                        zv[u][j] = in ? Zt[base + j] : 0;
                     }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < kGrp; ++q) {
-                const int x0 = xg + q * span;
-                if (x0 >= n) break;
+            for (int u = 0; u < kItems; ++u) {
+                if (!ok[u]) continue;
+                const int y = y0 + (u / kGrp) * gridDim.x;
+                const int x0 = xg + (u % kGrp) * span;
+                const size_t base = (size_t)y * n + x0;
                 float rv[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) rv[j] = (x0 + j < n) ? resist_px(iv[q][j], zv[q][j] != 0, p, acc) : 0.f;
+                for (int j = 0; j < 4; ++j) rv[j] = (x0 + j < n) ? resist_px(iv[u][j], zv[u][j] != 0, p, acc) : 0.f;
                 if (R) {
                     if (vec) {
-                        *reinterpret_cast<float4*>(R + base + x0) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+                        *reinterpret_cast<float4*>(R + base) = make_float4(rv[0], rv[1], rv[2], rv[3]);
                     } else {
-                        for (int j = 0; j < 4 && x0 + j < n; ++j) R[base + x0 + j] = rv[j];
+                        for (int j = 0; j < 4 && x0 + j < n; ++j) R[base + j] = rv[j];
                     }
                 }
                 if (Rhi) {
@@ -160,7 +166,7 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, int 
             }
         }
     }
-    block_store_loss(acc, blockIdx.x, dpart, lpart, sd, sl);
+    block_store_loss(acc, blockIdx.x, dpart, lpart, sf, si);
     // the last block to finish sums all partials (fixed order) and resets the counter
     __shared__ bool last;
     if (threadIdx.x == 0) {

@@ -21,140 +21,17 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
 #include "tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace devel {
 namespace tc {
 namespace {
-
-constexpr int kBM = 128;
-constexpr int kBK = 64;             // bf16 elements per 128-byte swizzle row
-constexpr uint32_t kABytes = kBM * kBK * 2;
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bounded waits: 1 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        "  .reg .pred p;\n"
-        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "  selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase with the given parity; false (and *err set) after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) {
-            if (err) atomicExch(err, DEVEL_ETIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* tm, uint64_t* bar, void* dst, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void fence_before_sync() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after_sync() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride byte offset), start address >> 4 in bits [0, 14),
-// descriptor version 1 in bits [46, 48), layout type 2 (SWIZZLE_128B) in [61, 64).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(16u >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024u >> 4) << 32;   // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N >> 3, M >> 4.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        "  .reg .pred p;\n"
-        "  setp.ne.b32 p, %4, 0;\n"
-        "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 template <int BN>
 struct Cfg {
@@ -324,12 +201,23 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 // The slices are then summed (in slice order) and combined into the complex window spectrum.
 template <int BN>
 struct Cfg2 {
-    static constexpr uint32_t kB2 = BN * 128;                 // one k-block of B2 (bf16, 64 y)
-    static constexpr uint32_t kPhase2 = 4 * kB2 + 4 * kABytes; // B2 hi/lo x 2 k-blocks, A2 hi/lo x 2 k-blocks
+    static constexpr uint32_t kB2 = BN * 128;                  // one k-block of B2 (bf16, 64 y)
+    static constexpr int kMB = (BN + 127) / 128;                // 128-row blocks of c1
+    // all kMB blocks of A2 resident at once when they fit beside B2 (then the blocks'
+    // MMA chains interleave), else one block at a time in the same buffers
+    static constexpr uint32_t kPhase2All = 4 * kB2 + kMB * 4 * kABytes;
+    static constexpr bool kA2All = kPhase2All + 1024 + 512 <= 232448u;
+    static constexpr uint32_t kPhase2 = kA2All ? kPhase2All : 4 * kB2 + 4 * kABytes;
     static constexpr uint32_t kRing = Cfg<BN>::kStages * Cfg<BN>::kStage;
     static constexpr uint32_t kArena = kRing > kPhase2 ? kRing : kPhase2;
-    static constexpr int kMB = (BN + 127) / 128;               // 128-row blocks of c1
-    static constexpr uint32_t kCols = kMB > 1 ? 512 : Cfg<BN>::kCols;
+    // phase-1 accumulators: one per compensation product when three fit in TMEM (three
+    // independent MMA chains instead of one latency-bound chain), summed by the drain
+    static constexpr int kAcc1 = 3 * BN <= 512 ? 3 : 1;
+    // phase-2 accumulators: three products x one block, or one per block (at column 256 mb)
+    static constexpr int kAcc2 = kMB == 1 ? 3 : 1;
+    static constexpr int kNeed1 = kAcc1 * BN, kNeed2 = kMB == 1 ? 3 * BN : 256 + BN;
+    static constexpr int kNeed = kNeed1 > kNeed2 ? kNeed1 : kNeed2;
+    static constexpr uint32_t kCols = kNeed <= 32 ? 32 : kNeed <= 64 ? 64 : kNeed <= 128 ? 128 : kNeed <= 256 ? 256 : 512;
     static constexpr size_t kSmem = 1024 + (size_t)kArena + 512;
 };
 
@@ -356,6 +244,24 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     const int kb0 = blockIdx.z * kb_per_split;
     const int nkb = max(0, min(kb_per_split, kb_total - kb0));
 
+    auto stage_ptr = [&](int s, int which) -> uint8_t* {
+        uint8_t* base = smem + s * CF::kStage;
+        return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
+    };
+    const uint32_t bytes1 = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
+    auto issue1 = [&](int i) {
+        const int s = i % S;
+        mbar_arrive_expect_tx(&full[s], bytes1);
+        const int kc = (kb0 + i) * kBK;
+        tma_load_2d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0);
+        if (use_alo) tma_load_2d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0);
+        tma_load_2d(&tmBhi, &full[s], stage_ptr(s, 2), kc, 0);
+        tma_load_2d(&tmBlo, &full[s], stage_ptr(s, 3), kc, 0);
+    };
+
+    // thread 0 initialises the barriers and issues the first ring's copies before the
+    // CTA-wide barrier (they need no wait)
+    int issued = 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -367,6 +273,7 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             mbar_init(&acc2[i], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (; issued < nkb && issued < S; ++issued) issue1(issued);
     }
     if (warp == 1) tmem_alloc(tmem_slot, C2::kCols);
     fence_before_sync();
@@ -374,34 +281,24 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    auto stage_ptr = [&](int s, int which) -> uint8_t* {
-        uint8_t* base = smem + s * CF::kStage;
-        return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
-    };
     // phase-2 buffers overlay the ring once phase 1 is complete
     uint8_t* B2hi = smem;                 // [2 k-blocks][BN rows][128 B]
     uint8_t* B2lo = smem + 2 * C2::kB2;
-    uint8_t* A2hi = smem + 4 * C2::kB2;   // [2 k-blocks][128 rows][128 B]
-    uint8_t* A2lo = A2hi + 2 * kABytes;
+    uint8_t* A2 = smem + 4 * C2::kB2;     // [block][k-block][hi, lo][128 rows][128 B]
+    auto a2_ptr = [&](int mb, int kb, int lo) -> uint8_t* {
+        return A2 + (C2::kA2All ? mb : 0) * 4 * kABytes + (kb * 2 + lo) * kABytes;
+    };
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
 
     // ---------------- phase 1 ----------------
-    int issued = 0;
     bool ok = true;
     if (warp == 0 && lane == 0 && nkb > 0) {
-        const uint32_t bytes = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
-        for (int i = 0; i < nkb; ++i) {
-            const int s = i % S;
-            if (i >= S && !mbar_wait(&empty[s], ((i / S) - 1) & 1, err)) {
+        for (int i = issued; i < nkb; ++i) {
+            if (!mbar_wait(&empty[i % S], ((i / S) - 1) & 1, err)) {
                 ok = false;
                 break;
             }
-            mbar_arrive_expect_tx(&full[s], bytes);
-            const int kc = (kb0 + i) * kBK;
-            tma_load_2d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0);
-            if (use_alo) tma_load_2d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0);
-            tma_load_2d(&tmBhi, &full[s], stage_ptr(s, 2), kc, 0);
-            tma_load_2d(&tmBlo, &full[s], stage_ptr(s, 3), kc, 0);
+            issue1(i);
             ++issued;
         }
     } else if (warp == 1 && lane == 0 && nkb > 0) {
@@ -418,9 +315,16 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             const uint64_t dBlo = smem_desc_sw128(smem_u32(stage_ptr(s, 3)));
             for (int kk = 0; kk < kBK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
-                if (use_alo) mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
+                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+                if (C2::kAcc1 == 3) {
+                    mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
+                    mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
+                    if (use_alo) mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
+                } else {
+                    mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
+                    mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
+                    if (use_alo) mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
+                }
             }
             mma_commit(&empty[s]);
         }
@@ -433,68 +337,106 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     fence_after_sync();
 
     // ---------------- phase 2 ----------------
+    constexpr int kA2Now = C2::kA2All ? C2::kMB : 1;  // blocks of A2 loaded up front
     if (have) {
-        // A2 of the first c1 block: TMA into its buffers (the ring is idle now)
+        // A2 (the ring is idle now)
         if (warp == 0 && lane == 0) {
-            mbar_arrive_expect_tx(&a2full[0], 4 * kABytes);
-            for (int kb = 0; kb < 2; ++kb) {
-                tma_load_2d(&tmChi, &a2full[0], A2hi + kb * kABytes, m0 + kb * kBK, 0);
-                tma_load_2d(&tmClo, &a2full[0], A2lo + kb * kABytes, m0 + kb * kBK, 0);
+            for (int mb = 0; mb < kA2Now; ++mb) {
+                mbar_arrive_expect_tx(&a2full[mb], 4 * kABytes);
+                for (int kb = 0; kb < 2; ++kb) {
+                    tma_load_2d(&tmChi, &a2full[mb], a2_ptr(mb, kb, 0), m0 + kb * kBK, mb * kBM);
+                    tma_load_2d(&tmClo, &a2full[mb], a2_ptr(mb, kb, 1), m0 + kb * kBK, mb * kBM);
+                }
             }
         }
-        // drain D1: thread = row y of the tile, 16 columns at a time; write B2[c][y] (bf16 hi/lo)
+        // drain D1 (sum of the product accumulators): thread = row y of the tile; write
+        // B2[c][y] as bf16 hi/lo in the 128-byte-swizzled K-major layout
         const int yl = warp * 32 + lane;
         const uint32_t kbo = (uint32_t)(yl >> 6) * C2::kB2;
         const uint32_t chunk = (uint32_t)((yl & 63) >> 3), e2 = (uint32_t)(yl & 7) * 2;
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const int nacc = C2::kAcc1 == 3 ? (use_alo ? 3 : 2) : 1;
+        auto put = [&](uint32_t c2, float x) {
+            const uint32_t off = kbo + c2 * 128u + (((chunk ^ (c2 & 7u)) << 4) | e2);
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *reinterpret_cast<__nv_bfloat16*>(B2hi + off) = h;
+            *reinterpret_cast<__nv_bfloat16*>(B2lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+        };
+#pragma unroll 1
+        for (int c = 0; c + 32 <= BN; c += 32) {
+            uint32_t r[32];
+            tmem_ld32(trow + (uint32_t)c, r);
+            for (int a = 1; a < nacc; ++a) {
+                uint32_t q[32];
+                tmem_ld32(trow + (uint32_t)(a * BN + c), q);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const uint32_t c2 = (uint32_t)(c + j);
-                const uint32_t off = kbo + c2 * 128u + (((chunk ^ (c2 & 7u)) << 4) | e2);
-                const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
-                *reinterpret_cast<__nv_bfloat16*>(B2hi + off) = h;
-                *reinterpret_cast<__nv_bfloat16*>(B2lo + off) = __float2bfloat16_rn(v[j] - __bfloat162float(h));
+                for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(q[j]));
             }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) put((uint32_t)(c + j), __uint_as_float(r[j]));
+        }
+        if (BN % 32) {
+            const int c = BN / 32 * 32;
+            float v[16];
+            tmem_ld16(trow + (uint32_t)c, v);
+            for (int a = 1; a < nacc; ++a) {
+                float q[16];
+                tmem_ld16(trow + (uint32_t)(a * BN + c), q);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += q[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) put((uint32_t)(c + j), v[j]);
         }
         // generic-proxy stores -> visible to the tensor core (async proxy); TMEM reads done
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_proxy_async_smem();
         fence_before_sync();
     }
     __syncthreads();
     fence_after_sync();
-    bool ok2 = have;
     if (have && warp == 1 && lane == 0) {
-        for (int mb = 0; mb < C2::kMB && ok2; ++mb) {
-            if (!mbar_wait(&a2full[mb], 0, err)) {
-                ok2 = false;
-                break;
-            }
+        // D2 accumulators: kMB == 1: the three products at columns 0, BN, 2 BN;
+        // kMB == 2: one per block at column 256 mb (both blocks' chains interleaved when
+        // their A2 is resident together)
+        bool ok2 = true;
+        for (int g = 0; g < C2::kMB / kA2Now && ok2; ++g) {
+            for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb)
+                if (!mbar_wait(&a2full[mb], 0, err)) ok2 = false;
+            if (!ok2) break;
             fence_after_sync();
-            const uint32_t d2 = tmem + (uint32_t)(mb * 256);
             for (int kb = 0; kb < 2; ++kb) {
-                const uint64_t dAhi = smem_desc_sw128(smem_u32(A2hi + kb * kABytes));
-                const uint64_t dAlo = smem_desc_sw128(smem_u32(A2lo + kb * kABytes));
                 const uint64_t dBhi = smem_desc_sw128(smem_u32(B2hi + kb * C2::kB2));
                 const uint64_t dBlo = smem_desc_sw128(smem_u32(B2lo + kb * C2::kB2));
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                     const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                    mma_bf16(d2, dAhi + adv, dBhi + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(d2, dAhi + adv, dBlo + adv, idesc, 1u);
-                    mma_bf16(d2, dAlo + adv, dBhi + adv, idesc, 1u);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb) {
+                        const uint64_t dAhi = smem_desc_sw128(smem_u32(a2_ptr(mb, kb, 0)));
+                        const uint64_t dAlo = smem_desc_sw128(smem_u32(a2_ptr(mb, kb, 1)));
+                        if (C2::kAcc2 == 3) {
+                            mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
+                            mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
+                            mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
+                        } else {
+                            const uint32_t d2 = tmem + (uint32_t)(mb * 256);
+                            mma_bf16(d2, dAhi + adv, dBhi + adv, idesc, acc);
+                            mma_bf16(d2, dAhi + adv, dBlo + adv, idesc, 1u);
+                            mma_bf16(d2, dAlo + adv, dBhi + adv, idesc, 1u);
+                        }
+                    }
                 }
             }
-            mma_commit(&acc2[mb]);
+            for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb) mma_commit(&acc2[mb]);
         }
     }
-    if (have && C2::kMB > 1 && warp == 0 && lane == 0) {
-        // A2 of the second c1 block reuses the buffers once the first block's MMAs are done
-        if (mbar_wait(&acc2[0], 0, err)) {
-            mbar_arrive_expect_tx(&a2full[1], 4 * kABytes);
+    if (have && !C2::kA2All && C2::kMB > 1 && warp == 0 && lane == 0) {
+        // one block at a time: the next block's A2 reuses the buffers once the MMAs are done
+        for (int mb = 1; mb < C2::kMB; ++mb) {
+            if (!mbar_wait(&acc2[mb - 1], 0, err)) break;
+            mbar_arrive_expect_tx(&a2full[mb], 4 * kABytes);
             for (int kb = 0; kb < 2; ++kb) {
-                tma_load_2d(&tmChi, &a2full[1], A2hi + kb * kABytes, m0 + kb * kBK, kBM);
-                tma_load_2d(&tmClo, &a2full[1], A2lo + kb * kABytes, m0 + kb * kBK, kBM);
+                tma_load_2d(&tmChi, &a2full[mb], a2_ptr(mb, kb, 0), m0 + kb * kBK, mb * kBM);
+                tma_load_2d(&tmClo, &a2full[mb], a2_ptr(mb, kb, 1), m0 + kb * kBK, mb * kBM);
             }
         }
     }
@@ -508,10 +450,18 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         h2 = __all_sync(0xffffffffu, h2);
         fence_after_sync();
         const int c1 = mb * kBM + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(C2::kAcc2 == 3 ? 0 : mb * 256);
+#pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             if (h2) {
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mb * 256 + c), v);
+                tmem_ld16(trow + (uint32_t)c, v);
+                for (int a = 1; a < C2::kAcc2; ++a) {
+                    float q[16];
+                    tmem_ld16(trow + (uint32_t)(a * BN + c), q);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] += q[j];
+                }
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = 0.f;
@@ -533,6 +483,284 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         fence_after_sync();
         tmem_dealloc(tmem, C2::kCols);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent expansion GEMM: D = scale * A B^T over an n x n output
+// ---------------------------------------------------------------------------
+// A = [Re T | -Im T] rows (M x K, K = the window's ldk <= 64 KB), B = basis^T rows
+// (N x K). Each CTA owns a contiguous range of 128 x BN output tiles (row-major
+// tile order, so consecutive tiles share their A rows). Warp roles:
+//   warp 4 (one thread)  TMA producer: the CTA's A rows (all K, kept resident while
+//                        the tile row lasts) and the B slabs of every tile into an
+//                        S-slot ring;
+//   warp 5 (one thread)  MMA issuer into two TMEM accumulators (tile i in buffer i & 1),
+//                        so the epilogue of one tile overlaps the MMAs of the next;
+//   warps 0-3            epilogue: TMEM lanes 32w.. (tile rows), 32 columns at a time,
+//                        scaled, staged in shared memory (128-byte swizzle) and written
+//                        by TMA tensor stores (or plain stores when the output pitch is
+//                        not 16-byte aligned); EPI_VEL also keeps the CTA's max |D|.
+template <int BN, int KB>
+struct CfgX {
+    static constexpr uint32_t kA = KB * 2 * kABytes;       // A hi/lo, all K
+    static constexpr uint32_t kSlab = BN * kBK * 2;        // one 64-wide K slab of B (hi or lo)
+    static constexpr uint32_t kSlot = 2 * kSlab;
+    static constexpr uint32_t kStaging = 4 * 2 * 4096;     // 4 warps x 2 buffers x (32 rows x 128 B)
+    static constexpr uint32_t kFixed = 1024 + kA + kStaging + 256;
+    static constexpr int kFit = (int)((232448u - kFixed) / kSlot);
+    static constexpr int kS = kFit > 8 ? 8 : kFit;
+    static_assert(kFit >= 2, "expansion tile does not fit");
+    // Accumulators per TMEM buffer: the three compensation products go to separate
+    // accumulators when two buffers of three fit in TMEM, so that three independent MMA
+    // chains interleave (a single accumulate chain of narrow MMAs is latency-bound);
+    // they are summed in the epilogue.
+    static constexpr int kAcc = 2 * 3 * BN <= 512 ? 3 : 1;
+    static constexpr int kBuf = kAcc * BN;                 // TMEM columns of one buffer
+    static constexpr uint32_t kCols = 2 * kBuf <= 32 ? 32 : 2 * kBuf <= 64 ? 64 : 2 * kBuf <= 128 ? 128
+                                    : 2 * kBuf <= 256 ? 256 : 512;
+    static constexpr size_t kSmem = kFixed + (size_t)kS * kSlot;
+};
+
+template <int BN, int KB, int EPI>
+__global__ void __launch_bounds__(192, 1)
+k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+            const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+            const __grid_constant__ CUtensorMap tmC, int use_tma_store, int M, int N, int ksteps_last,
+            int tiles_n, int tiles, const EpiArgs ep, int* err) {
+    using CX = CfgX<BN, KB>;
+    constexpr int S = CX::kS;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + CX::kA;
+    uint8_t* sC = sB + S * CX::kSlot;
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(sC + CX::kStaging);
+    uint64_t* a_empty = a_full + 1;
+    uint64_t* b_full = a_empty + 1;
+    uint64_t* b_empty = b_full + S;
+    uint64_t* t_full = b_empty + S;
+    uint64_t* t_empty = t_full + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(t_empty + 2);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    __shared__ float red[4];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = (int)(((long long)blockIdx.x * tiles) / gridDim.x);
+    const int t1 = (int)(((long long)(blockIdx.x + 1) * tiles) / gridDim.x);
+    const bool producer = threadIdx.x == 128;  // warp 4, lane 0
+
+    // Producer state. The producer initialises the barriers and issues the copies that
+    // need no wait (the first A rows and up to S slabs) before the CTA-wide barrier.
+    int p_t = t0, p_kb = 0, p_slab = 0, p_aload = 0, p_prev_m = -1;
+    bool p_ok = true;
+    auto produce = [&](bool prologue) {
+        while (p_t < t1 && p_ok) {
+            const int mt = p_t / tiles_n, nt = p_t - mt * tiles_n;
+            if (p_kb == 0 && mt != p_prev_m) {
+                if (p_aload > 0) {
+                    if (prologue) return;
+                    if (!mbar_wait_ab(a_empty, (p_aload - 1) & 1, err, abort)) {
+                        p_ok = false;
+                        return;
+                    }
+                }
+                mbar_arrive_expect_tx(a_full, CX::kA);
+                for (int kb = 0; kb < KB; ++kb) {
+                    tma_load_2d(&tmAhi, a_full, sA + kb * 2 * kABytes, kb * kBK, mt * kBM);
+                    tma_load_2d(&tmAlo, a_full, sA + kb * 2 * kABytes + kABytes, kb * kBK, mt * kBM);
+                }
+                ++p_aload;
+                p_prev_m = mt;
+            }
+            const int sl = p_slab % S;
+            if (p_slab >= S) {
+                if (prologue) return;
+                if (!mbar_wait_ab(&b_empty[sl], ((p_slab / S) - 1) & 1, err, abort)) {
+                    p_ok = false;
+                    return;
+                }
+            }
+            mbar_arrive_expect_tx(&b_full[sl], CX::kSlot);
+            tma_load_2d(&tmBhi, &b_full[sl], sB + sl * CX::kSlot, p_kb * kBK, nt * BN);
+            tma_load_2d(&tmBlo, &b_full[sl], sB + sl * CX::kSlot + CX::kSlab, p_kb * kBK, nt * BN);
+            ++p_slab;
+            if (++p_kb == KB) {
+                p_kb = 0;
+                ++p_t;
+            }
+        }
+    };
+
+    if (producer) {
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&b_full[i], 1);
+            mbar_init(&b_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 4);  // one arrival per epilogue warp
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        produce(true);
+    }
+    if (warp == 5) tmem_alloc(tmem_slot, CX::kCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    float mx = 0.f;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            produce(false);
+            if (!p_ok || *abort) {  // wait (bounded) for the copies still in flight before the CTA exits
+                if (p_aload > 0) mbar_wait(a_full, (p_aload - 1) & 1, nullptr);
+                for (int i = max(0, p_slab - S); i < p_slab; ++i) mbar_wait(&b_full[i % S], (i / S) & 1, nullptr);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+            int slab = 0, aload = 0, prev_m = -1, ti = 0;
+            bool ok = true, pending = false;
+            for (int t = t0; t < t1 && ok; ++t, ++ti) {
+                const int mt = t / tiles_n;
+                if (mt != prev_m) {
+                    if (!mbar_wait_ab(a_full, aload & 1, err, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    ++aload;
+                    prev_m = mt;
+                }
+                const int buf = ti & 1;
+                if (ti >= 2 && !mbar_wait_ab(&t_empty[buf], ((ti >> 1) - 1) & 1, err, abort)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(buf * CX::kBuf);
+                for (int kb = 0; kb < KB; ++kb, ++slab) {
+                    const int sl = slab % S;
+                    if (!mbar_wait_ab(&b_full[sl], (slab / S) & 1, err, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const int ksteps = kb == KB - 1 ? ksteps_last : kBK / 16;
+                    const uint64_t dAhi = smem_desc_sw128(smem_u32(sA + kb * 2 * kABytes));
+                    const uint64_t dAlo = smem_desc_sw128(smem_u32(sA + kb * 2 * kABytes + kABytes));
+                    const uint64_t dBhi = smem_desc_sw128(smem_u32(sB + sl * CX::kSlot));
+                    const uint64_t dBlo = smem_desc_sw128(smem_u32(sB + sl * CX::kSlot + CX::kSlab));
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                        if (CX::kAcc == 3) {
+                            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
+                            mma_bf16(d + BN, dAhi + adv, dBlo + adv, idesc, acc);
+                            mma_bf16(d + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
+                        } else {
+                            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
+                            mma_bf16(d, dAhi + adv, dBlo + adv, idesc, 1u);
+                            mma_bf16(d, dAlo + adv, dBhi + adv, idesc, 1u);
+                        }
+                    }
+                    pending = true;
+                    mma_commit(&b_empty[sl]);
+                }
+                if (!ok) break;
+                mma_commit(&t_full[buf]);
+                pending = false;
+                if (t + 1 >= t1 || (t + 1) / tiles_n != mt) mma_commit(a_empty);
+            }
+            if (!ok && pending) {  // MMAs of an unfinished tile: let them complete before TMEM is freed
+                uint64_t* b = &t_full[ti & 1];
+                mma_commit(b);
+                mbar_wait(b, (ti >> 1) & 1, nullptr);
+            }
+        }
+    } else {
+        // epilogue warps 0-3
+        int ti = 0, chunk = 0;
+        const float scale = ep.scale;
+        for (int t = t0; t < t1; ++t, ++ti) {
+            const int mt = t / tiles_n, nt = t - mt * tiles_n;
+            const int buf = ti & 1;
+            bool h = mbar_wait_ab(&t_full[buf], (ti >> 1) & 1, err, abort);
+            h = __all_sync(0xffffffffu, h);
+            if (!h) break;
+            fence_after_sync();
+            const int row0 = mt * kBM + warp * 32;
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * CX::kBuf);
+            uint32_t r[BN];
+            if constexpr (BN == 128) tmem_ld128(taddr, r);
+            else tmem_ld64(taddr, r);
+            if constexpr (CX::kAcc == 3) {  // (hi hi + hi lo) + lo hi
+#pragma unroll
+                for (int a = 1; a < 3; ++a) {
+                    uint32_t q[BN];
+                    if constexpr (BN == 128) tmem_ld128(taddr + (uint32_t)(a * BN), q);
+                    else tmem_ld64(taddr + (uint32_t)(a * BN), q);
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(q[j]));
+                }
+            }
+            // the accumulator is in registers: hand the TMEM buffer back to the MMA thread
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[buf]);
+            const int row = row0 + lane;
+#pragma unroll
+            for (int c = 0; c < BN; c += 32, ++chunk) {
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[c + j]) * scale;
+                const int col0 = nt * BN + c;
+                if (EPI == EPI_VEL && row < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < N) mx = fmaxf(mx, fabsf(v[j]));
+                }
+                if (use_tma_store) {
+                    uint8_t* stg = sC + (warp * 2 + (chunk & 1)) * 4096;
+                    if (lane == 0) bulk_wait_read<1>();  // this buffer's previous store has been read
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4*>(stg + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && row0 < M && col0 < N) {  // boxes entirely outside are not issued
+                        tma_store_2d(&tmC, stg, col0, row0);
+                        bulk_commit();
+                    }
+                } else if (row < M) {
+                    float* dst = ep.C + (size_t)row * ep.ldc + col0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < N) dst[j] = v[j];
+                }
+            }
+        }
+        if (use_tma_store && lane == 0) bulk_wait_all();
+        if (EPI == EPI_VEL) {
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            if (lane == 0) red[warp] = mx;
+        }
+    }
+    __syncwarp();
+    fence_before_sync();
+    __syncthreads();
+    if (EPI == EPI_VEL && threadIdx.x == 0) ep.vpart[blockIdx.x] = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    if (warp == 5) {
+        fence_after_sync();
+        tmem_dealloc(tmem, CX::kCols);
+    }
+    if (EPI == EPI_VEL) vmax_last_block(ep.vpart, gridDim.x, ep.counter, ep.vmax, ep.status);
 }
 
 // ---------------------------------------------------------------------------
@@ -622,6 +850,85 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return DEVEL_OK;
+}
+
+// fp32 [rows][cols] output map (pitch ld elements, a multiple of 4): boxes of
+// 32 columns x 32 rows, 128-byte swizzle (the epilogue's staging layout).
+static int make_map_out(CUtensorMap* tm, const float* base, int rows, int cols, int ld) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+    return DEVEL_OK;
+}
+
+static int sm_count() {
+    int dev = 0, c = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return 148;
+    return c > 0 ? c : 148;
+}
+
+template <int BN, int KB, int EPI>
+static int launch_expand_cfg(const Operands& op, int M, int N, int ksteps_last, const EpiArgs& ep, int* err,
+                             cudaStream_t s) {
+    CUtensorMap tmC;
+    const bool tma_store = (ep.ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(ep.C) & 15u) == 0;
+    if (tma_store) {
+        int rc = make_map_out(&tmC, ep.C, M, N, ep.ldc);
+        if (rc) return rc;
+    } else {
+        std::memset(&tmC, 0, sizeof(tmC));
+    }
+    const int tiles_n = (N + BN - 1) / BN;
+    const int tiles = ((M + kBM - 1) / kBM) * tiles_n;
+    const int grid = std::min(tiles, sm_count());
+    k_tc_expand<BN, KB, EPI><<<grid, 192, CfgX<BN, KB>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, tmC,
+                                                                    tma_store ? 1 : 0, M, N, ksteps_last, tiles_n,
+                                                                    tiles, ep, err);
+    DEVEL_LAUNCH_CHECK("k_tc_expand");
+    return DEVEL_OK;
+}
+
+int expand_grid(int M, int N, int BN) {
+    const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
+    return std::min(tiles, sm_count());
+}
+
+int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, const EpiArgs& ep, int* err,
+                  cudaStream_t s) {
+    const int KB = (K + kBK - 1) / kBK;
+    if (K % 16 != 0 || KB < 1 || KB > 4 || (BN != 64 && BN != 128))
+        return set_error(DEVEL_EINVAL, "tc expand: contraction length %d / tile width %d unsupported", K, BN);
+    const int ksteps_last = (K - (KB - 1) * kBK) / 16;
+    prof_begin(PK_TC_EXPAND, s);
+    int rc = DEVEL_OK;
+#define DEVEL_X_CASE(bn, kb)                                                                              \
+    if (BN == bn && KB == kb)                                                                             \
+        rc = epi == EPI_VEL ? launch_expand_cfg<bn, kb, EPI_VEL>(op, M, N, ksteps_last, ep, err, s)       \
+                            : launch_expand_cfg<bn, kb, EPI_STORE>(op, M, N, ksteps_last, ep, err, s);
+    DEVEL_X_CASE(64, 1) DEVEL_X_CASE(64, 2) DEVEL_X_CASE(64, 3) DEVEL_X_CASE(64, 4)
+    DEVEL_X_CASE(128, 1) DEVEL_X_CASE(128, 2) DEVEL_X_CASE(128, 3) DEVEL_X_CASE(128, 4)
+#undef DEVEL_X_CASE
+    prof_end(PK_TC_EXPAND, s);
+    return rc;
+}
+
+template <int BN, int KB>
+static cudaError_t set_attr_expand() {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_expand<BN, KB, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CfgX<BN, KB>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tc_expand<BN, KB, EPI_VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CfgX<BN, KB>::kSmem);
+    return e;
 }
 
 int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
@@ -715,6 +1022,14 @@ int init_attrs() {
     DEVEL_SPEC2_ATTR(176) DEVEL_SPEC2_ATTR(192) DEVEL_SPEC2_ATTR(208) DEVEL_SPEC2_ATTR(224) DEVEL_SPEC2_ATTR(240)
     DEVEL_SPEC2_ATTR(256)
 #undef DEVEL_SPEC2_ATTR
+    if (e == cudaSuccess) e = set_attr_expand<64, 1>();
+    if (e == cudaSuccess) e = set_attr_expand<64, 2>();
+    if (e == cudaSuccess) e = set_attr_expand<64, 3>();
+    if (e == cudaSuccess) e = set_attr_expand<64, 4>();
+    if (e == cudaSuccess) e = set_attr_expand<128, 1>();
+    if (e == cudaSuccess) e = set_attr_expand<128, 2>();
+    if (e == cudaSuccess) e = set_attr_expand<128, 3>();
+    if (e == cudaSuccess) e = set_attr_expand<128, 4>();
     if (e != cudaSuccess) return cuda_error(e, "tc::init_attrs");
     return DEVEL_OK;
 }

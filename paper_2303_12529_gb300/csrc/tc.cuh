@@ -39,6 +39,15 @@ int spectrum2_slices(int M, int K);
 int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
                      float* Q, int* err, cudaStream_t s);
 
+// Persistent expansion D = ep.scale * A B^T (k_tc_expand), M x N output row-major in
+// ep.C with pitch ep.ldc; A [M][K] map with 128-row boxes, B [N][K] map with BN-row
+// boxes (BN = 64 or 128, the output tile width); K a multiple of 16 up to 256.
+// epi: EPI_STORE, or EPI_VEL (also max |D|: per-CTA values in ep.vpart,
+// expand_grid() of them, then the last CTA's FP64 max into ep.vmax).
+int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, const EpiArgs& ep, int* err,
+                  cudaStream_t s);
+int expand_grid(int M, int N, int BN);
+
 // Shared-memory opt-in of all tensor-core kernels (once per device).
 int init_attrs();
 

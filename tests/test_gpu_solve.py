@@ -79,3 +79,51 @@ def test_bf16x3_aerial_error_per_iteration():
         errs.append(float(np.abs(host(out, 256) - ref).max() / np.abs(ref).max()))
         phi, _ = solve.iterate(phi, Zt, o.H, o.w, p, t)
     assert max(errs) <= 2e-4, errs
+
+
+def _clip_job(dv, opt, Zt, iters):
+    n = Zt.shape[0]
+    phi = torch.zeros(n * n, dtype=torch.float32, device="cuda")
+    M = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    L = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    l2 = torch.zeros(iters + 1, dtype=torch.int64, device="cuda")
+    return dv.Clip(opt, dev(Zt), phi, mask_out=M, loss_hist=L, l2_hist=l2)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_uneven_clips_equal_single_solves(prec, use_graph):
+    """One devel_ilt_solve over clips of uneven sides (each side with its own window,
+    two clips sharing one handle) gives, clip for clip, bit-identical phi, masks and
+    loss histories to solving each clip alone: the concurrent branches change the
+    schedule, never a clip's arithmetic."""
+    dv = need_gpu()
+    iters = 6
+    sides = [(128, 9), (192, 11), (256, 15)]
+    opts = {n: dv.devel_optics_create(n, *_optics_arrays(n, k), prec) for n, k in sides}
+    targets = [synth.rect_clip(40 + i, n=n, border=8) for i, (n, _) in enumerate(sides)]
+    targets.append(synth.rect_clip(50, n=128, border=8))  # shares the 128 handle
+    handles = [opts[128], opts[192], opts[256], opts[128]]
+    p = dv.ilt_params(dv.resist_params(beta=2.0), iters=iters, reinit_every=3, use_graph=use_graph)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch = [_clip_job(dv, h, Zt, iters) for h, Zt in zip(handles, targets)]
+    dv.devel_ilt_solve(p, batch, st)
+    torch.cuda.synchronize()
+    assert int(host(st)[0]) == 0
+    for h, Zt, b in zip(handles, targets, batch):
+        one = _clip_job(dv, h, Zt, iters)
+        dv.devel_ilt_solve(p, [one], st)
+        torch.cuda.synchronize()
+        assert int(host(st)[0]) == 0
+        for name in ("phi", "mask_out", "loss_hist", "l2_hist"):
+            assert torch.equal(getattr(b, name), getattr(one, name)), name
+
+
+_OPTICS_CACHE = {}
+
+
+def _optics_arrays(n, k):
+    if (n, k) not in _OPTICS_CACHE:
+        o = synth.optics(n, 6, k)
+        _OPTICS_CACHE[(n, k)] = (o.H, o.w)
+    return _OPTICS_CACHE[(n, k)]
