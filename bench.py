@@ -33,6 +33,10 @@ WORKLOADS = {
     # name: (n, K, k, iters, beta, seed)
     "manhattan2048": dict(n=2048, K=24, k=35, iters=100, beta=7.5, seed=1000),
     "rect256": dict(n=256, K=8, k=15, iters=20, beta=0.0, seed=0),
+    # 64 Manhattan clips of sides drawn from {512, 1024, 1536, 2048} (seed 2000 draws the
+    # sides, seeds 2001.. the patterns), window k_n = 2 ceil(17 n / 2048) + 1 at 1 nm/px,
+    # compensated BF16, one devel_ilt_solve per step over the whole batch
+    "uneven64": dict(batch=64, sides=(512, 1024, 1536, 2048), K=24, iters=100, beta=7.5, seed=2000),
 }
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -208,6 +212,8 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if "batch" in wl:  # the oracle's clips/s on the full-size clip stands for every side
+        wl = WORKLOADS["manhattan2048"]
     t0 = time.perf_counter()
     vals = []
     sample = ""
@@ -420,6 +426,167 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_batched(args, wl):
+    """The batch workload: every step solves the whole batch of uneven clips in one
+    devel_ilt_solve (clips on parallel branches of one CUDA graph), after the tile
+    shapes of every handle were picked by devel_optics_autotune. Also times the same
+    clips solved one call at a time (the schedule without batching)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    B, K, iters, beta = wl["batch"], wl["K"], wl["iters"], wl["beta"]
+    rng = np.random.default_rng(wl["seed"])
+    sides = [int(x) for x in rng.choice(wl["sides"], size=B)]
+    seeds = [wl["seed"] + 1 + rank * B + i for i in range(B)]  # replicas: disjoint clips per rank
+    optics_of = {}
+    clips, handles = [], []
+    t_tune = 0.0
+    for n, sd in zip(sides, seeds):
+        k = 2 * synth.window_radius_for(n) + 1
+        if n not in optics_of:
+            optics_of[n] = synth.optics(n, K, k)
+        o = optics_of[n]
+        h = dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
+        t0 = time.perf_counter()
+        dv.devel_optics_autotune(h, stream)
+        t_tune += time.perf_counter() - t0
+        handles.append(h)
+        Zt = synth.manhattan_clip(sd, n=n)
+        clips.append(dv.Clip(h, torch.from_numpy(Zt.ravel().copy()).to(dev),
+                             torch.empty(n * n, dtype=torch.float32, device=dev),
+                             mask_out=torch.empty(n * n, dtype=torch.uint8, device=dev),
+                             l2_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev),
+                             pvb_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev)))
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(1, min(args.steps, 5))
+
+    def step():
+        dv.devel_ilt_solve(params, clips, st, stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    if int(st.item()) != 0:
+        raise RuntimeError(f"solver status {int(st.item())}")
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    clocks = sampler.stop()
+    # the same clips, one solve call each (no concurrency between clips)
+    for c in clips:
+        dv.devel_ilt_solve(params, [c], st, stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record(stream)
+    for c in clips:
+        dv.devel_ilt_solve(params, [c], st, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(b)
+    # per-kernel device times (events around every kernel, one more batch solve)
+    dv.devel_profile_start(1 << 20)
+    step()
+    torch.cuda.synchronize()
+    dv.devel_profile_collect()
+    dv.devel_profile_stop(collect=False)
+    dv.devel_profile_start(1 << 20)
+    step()
+    torch.cuda.synchronize()
+    prof = dv.devel_profile_stop(collect=True)
+    ms = job_time_ms(ms, dist, dev)
+    # end to end: targets in from pinned host memory, masks out, every step
+    tg_host = [c.target.cpu().pin_memory() for c in clips]
+    mk_host = [torch.empty_like(c.mask_out, device="cpu").pin_memory() for c in clips]
+    e2e = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, h in zip(clips, tg_host):
+            c.target.copy_(h, non_blocking=True)
+        step()
+        for c, h in zip(clips, mk_host):
+            h.copy_(c.mask_out, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1000.0)
+    e2e_ms = job_time_ms(float(np.median(e2e)), dist, dev)
+    if rank == 0:
+        hbm, _, src = measured_peaks()
+        tot = sum(t for _, t in prof.values())
+        # algorithmic bytes of every launch of a kernel class, summed over the clips
+        per_clip_launches = {kn: c / B for kn, (c, _) in prof.items()}
+        kernels = {}
+        for kn, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+            ent = {"launches": c, "ms": round(t, 3), "share": round(t / tot, 4)}
+            bsum = 0.0
+            for n in sides:
+                k = 2 * synth.window_radius_for(n) + 1
+                bb = kernel_bytes(kn, n, K, k, True)
+                bsum = None if (bb is None or bsum is None) else bsum + bb * per_clip_launches[kn]
+            if bsum:
+                ent["gbs"] = round(bsum / (t / 1000.0) / 1e9, 1)
+                ent["frac_hbm"] = round(ent["gbs"] / hbm, 3)
+            kernels[kn] = ent
+        dom = next(iter(kernels))
+        d = kernels[dom]
+        roof = {"bound": "hbm", "achieved": d.get("gbs"), "peak": hbm, "unit": "GB/s",
+                "frac": d.get("frac_hbm"), "peak_source": src + " (burst copy)", "traffic": None, "kernel": dom,
+                "timing": "CUDA events around every kernel of one batch solve (kernels of different clips "
+                          "overlap, so the per-kernel durations include the slowdown from sharing the GPU)"}
+        hist = {n: 0 for n in wl["sides"]}
+        for n in sides:
+            hist[n] += 1
+        px = sum(n * n for n in sides)
+        out = {
+            "metric": METRIC, "value": world * B * 1000.0 / ms, "unit": "clips/s", "n_gpus": world,
+            "steps": steps, "warmup": max(args.warmup, 1), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": args.workload, "clips_per_gpu_per_step": B, "sides": hist, "K": K,
+                       "k_per_side": {n: 2 * synth.window_radius_for(n) + 1 for n in wl["sides"]},
+                       "iters": iters, "beta": beta, "precision": "bf16x3",
+                       "schedule": "one devel_ilt_solve per step, clips on parallel graph branches",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "megapixel_iterations_per_s": world * px * iters / (ms / 1000.0) / 1e6,
+            "sequential": {"value": B * 1000.0 / ms_seq, "ms_per_step": ms_seq,
+                           "schedule": "one devel_ilt_solve per clip"},
+            "autotune": {"seconds": t_tune, "picked": {str(n): dv.devel_optics_config(handles[sides.index(n)])
+                                                      for n in sorted(set(sides))}},
+            "e2e": {"value": world * B * 1000.0 / e2e_ms, "unit": "clips/s", "h2d_bytes_per_step": px,
+                    "d2h_bytes_per_step": px},
+            "gpu_launches": int(sum(c for c, _ in prof.values())) * steps,
+            "roofline": roof, "kernels": kernels, "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +601,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif "batch" in wl:
+        run_batched(args, wl)
     else:
         run_ours(args, wl)
 

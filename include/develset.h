@@ -92,6 +92,20 @@ int devel_optics_n(const devel_optics* optics);
  */
 int devel_optics_check(const devel_optics* optics, cudaStream_t stream);
 
+/*
+ * Tile-shape tuner (no counterpart in the paper; it serves batches of clips of
+ * uneven sizes). Times the candidate tile shapes of the handle's tensor-core
+ * kernels on its own workspace (the output tile width of the expansions, the
+ * image columns per CTA of the reductions) and keeps the fastest for later
+ * calls. Synchronises `stream`; overwrites the handle's workspace, so call it
+ * between solves, not while a call on the handle is in flight. Results of later
+ * calls may differ from earlier ones in the last bits (the summation order
+ * depends on the tiles). A no-op for DEVEL_PREC_FP32 handles.
+ */
+int devel_optics_autotune(devel_optics* optics, cudaStream_t stream);
+/* The tile shapes in use (0 for FP32 handles). Either pointer may be NULL. */
+int devel_optics_config(const devel_optics* optics, int* expand_tile_n, int* reduce_split);
+
 /* ------------------------------------------------------------------------ */
 /* Lithography                                                              */
 /* ------------------------------------------------------------------------ */

@@ -121,6 +121,7 @@ static void free_optics(devel_optics* o) {
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
                     o->tcW2.basis_hi, o->tcW2.basis_lo, o->tcW2.basisT_hi, o->tcW2.basisT_lo,
+                    o->tcW.zm_hi, o->tcW.zm_lo, o->tcW2.zm_hi, o->tcW2.zm_lo,
                     o->Xhi, o->Xlo, o->Acat_hi, o->Acat_lo, o->tc_err, o->ws.counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -468,8 +469,17 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.Ppart, sizeof(float) * (size_t)o->nsplit * n * ld2);
     o->nq = std::max(1, std::min(16, n / 128));
     ALLOC(o->ws.P, sizeof(float) * (size_t)n * ld2);
-    const size_t nslices =
-        precision == DEVEL_PREC_BF16X3 ? (size_t)std::max(o->nq, tc::spectrum2_slices(n, o->ldn)) : (size_t)o->nq;
+    // the fused reduction's slices, for the narrowest split the tuner may pick (at most
+    // 256 slices)
+    if (precision == DEVEL_PREC_BF16X3) {
+        o->tc_split = std::min(256, o->ldn);
+        o->tc_split_min = o->tc_split;
+        while (o->tc_split_min > 64 && tc::spectrum2_slices(n, o->ldn, o->tc_split_min / 2) <= 256)
+            o->tc_split_min /= 2;
+    }
+    const size_t nslices = precision == DEVEL_PREC_BF16X3
+                               ? (size_t)std::max(o->nq, tc::spectrum2_slices(n, o->ldn, o->tc_split_min))
+                               : (size_t)o->nq;
     ALLOC(o->ws.Q, sizeof(float) * nslices * ld2 * ld2);
     ALLOC(o->ws.mhat, sizeof(float2) * kk);
     ALLOC(o->ws.Ihat, sizeof(float2) * kk2);
@@ -497,6 +507,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
             ALLOC(tw->basis_lo, bf * round_up(ldk, 128) * o->ldn);
             ALLOC(tw->basisT_hi, bf * (size_t)n * ldk);
             ALLOC(tw->basisT_lo, bf * (size_t)n * ldk);
+            ALLOC(tw->zm_hi, bf * (size_t)ldk * ldk);
+            ALLOC(tw->zm_lo, bf * (size_t)ldk * ldk);
         }
         ALLOC(o->Xhi, bf * (size_t)n * o->ldn);
         ALLOC(o->Xlo, bf * (size_t)n * o->ldn);
@@ -588,6 +600,12 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
             if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, w.ldk, o->ldn, o->ldn, w.ldk);
             if (!rc) rc = tc::make_map(&tw.m_basisT_hi, tw.basisT_hi, n, w.ldk, w.ldk, 128);
             if (!rc) rc = tc::make_map(&tw.m_basisT_lo, tw.basisT_lo, n, w.ldk, w.ldk, 128);
+            // Zm entries outside the window's 2 kw x 2 kw block are never written: zero them once
+            if (!rc && (cudaMemset(tw.zm_hi, 0, sizeof(__nv_bfloat16) * w.ldk * w.ldk) != cudaSuccess ||
+                        cudaMemset(tw.zm_lo, 0, sizeof(__nv_bfloat16) * w.ldk * w.ldk) != cudaSuccess))
+                rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
+            if (!rc) rc = tc::make_map(&tw.m_zm_hi, tw.zm_hi, w.ldk, w.ldk, w.ldk, kTileT);
+            if (!rc) rc = tc::make_map(&tw.m_zm_lo, tw.zm_lo, w.ldk, w.ldk, w.ldk, kTileT);
             if (!rc) rc = tc::make_map(&tw.m_basisT64_hi, tw.basisT_hi, n, w.ldk, w.ldk, 64);
             if (!rc) rc = tc::make_map(&tw.m_basisT64_lo, tw.basisT_lo, n, w.ldk, w.ldk, 64);
             if (!rc) rc = tc::make_map(&tw.m_acat_hi, o->Acat_hi, n, w.ldk, w.ldk, 128);
@@ -619,6 +637,84 @@ int devel_optics_destroy(devel_optics* o) {
     cudaError_t e = cudaDeviceSynchronize();
     free_optics(o);
     if (e != cudaSuccess) return cuda_error(e, "devel_optics_destroy: cudaDeviceSynchronize");
+    return DEVEL_OK;
+}
+
+// Tile-shape tuner: times each candidate on the handle's own tables and workspace
+// (whatever they hold; the timing does not depend on the values) and keeps the fastest.
+// Tuned: the output tile width of the tensor-core expansion and the image columns per
+// CTA of the fused reduction (which sets its grid: narrow clips want narrow slices to
+// fill the SMs). The FP32 path has nothing to tune.
+int devel_optics_autotune(devel_optics* o, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_optics_autotune: optics is NULL");
+    if (o->precision != DEVEL_PREC_BF16X3) return DEVEL_OK;
+    int rc = init_device_attrs();
+    if (rc) return rc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    DEVEL_CUDA_TRY(cudaEventCreate(&a));
+    cudaError_t ce = cudaEventCreate(&b);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_error(ce, "devel_optics_autotune: cudaEventCreate");
+    }
+    constexpr int kReps = 5;
+    // the two expansions and the two reductions of one iteration
+    auto expand_pair = [&]() -> int {
+        EpiArgs e1;
+        e1.C = o->ws.bufI;
+        int r = launch_expand(o, o->ws.Ihat, o->W2, EPI_STORE, e1, nullptr, s);
+        EpiArgs e2;
+        e2.C = o->ws.bufV;
+        return r ? r : launch_expand(o, o->ws.Shat, o->W, EPI_STORE, e2, nullptr, s);
+    };
+    auto reduce_pair = [&]() -> int {
+        int r = launch_spectrum_mask_resident(o, o->W, o->ws.mhat, s);
+        return r ? r : launch_spectrum_resident(o, o->W2, o->ws.rhat, s);
+    };
+    auto time_of = [&](auto&& fn, float* ms) -> int {
+        int r = fn();  // warm-up
+        for (int i = 0; i < kReps && !r; ++i) {
+            if (i == 0 && cudaEventRecord(a, s) != cudaSuccess) r = set_error(DEVEL_ECUDA, "autotune: event");
+            if (!r) r = fn();
+        }
+        if (!r && (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                   cudaEventElapsedTime(ms, a, b) != cudaSuccess))
+            r = set_error(DEVEL_ECUDA, "devel_optics_autotune: event timing");
+        return r;
+    };
+    float best = 1e30f, t = 0.f;
+    int best_bn = o->tc_expand_bn, best_split = o->tc_split;
+    for (int bn : {64, 128}) {
+        o->tc_expand_bn = bn;
+        rc = time_of(expand_pair, &t);
+        if (rc) break;
+        if (t < best) {
+            best = t;
+            best_bn = bn;
+        }
+    }
+    o->tc_expand_bn = best_bn;
+    best = 1e30f;
+    for (int split = o->tc_split_min; !rc && split <= std::min(512, o->ldn); split *= 2) {
+        if (o->ldn % 64) break;
+        o->tc_split = split;
+        rc = time_of(reduce_pair, &t);
+        if (!rc && t < best) {
+            best = t;
+            best_split = split;
+        }
+    }
+    o->tc_split = best_split;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    drop_graphs_of(o);  // graphs captured with the old shapes
+    return rc;
+}
+
+int devel_optics_config(const devel_optics* o, int* expand_tile_n, int* reduce_split) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_optics_config: optics is NULL");
+    if (expand_tile_n) *expand_tile_n = o->precision == DEVEL_PREC_BF16X3 ? o->tc_expand_bn : 0;
+    if (reduce_split) *reduce_split = o->precision == DEVEL_PREC_BF16X3 ? o->tc_split : 0;
     return DEVEL_OK;
 }
 

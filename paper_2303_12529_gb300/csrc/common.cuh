@@ -49,8 +49,12 @@ struct ResistArgs {
     float k_nom, k_in, k_out;
 };
 
+// N tile of the tensor-core GEMM T = E Z (a multiple of 16): narrow, so that the
+// GEMM over n rows and ldk <= 256 columns still spreads over several CTAs per row block.
+constexpr int kTileT = 48;
+
 // Epilogues of the contraction GEMMs.
-enum { EPI_STORE = 0, EPI_VEL = 1 };
+enum { EPI_STORE = 0, EPI_VEL = 1, EPI_SPLIT = 2 };
 
 struct EpiArgs {
     float* C = nullptr;              // output
@@ -63,9 +67,12 @@ struct EpiArgs {
     unsigned* counter = nullptr;
     double* vmax = nullptr;
     int* status = nullptr;
+    // EPI_SPLIT: out = bf16 hi/lo pair, row pitch ldh (elements)
+    __nv_bfloat16* Chi = nullptr;
+    __nv_bfloat16* Clo = nullptr;
+    int ldh = 0;
 };
 
-constexpr int kTcSplitK = 256;  // K slice of one split of the tensor-core reduction
 
 // Called by every thread of every block of an EPI_VEL expansion after the block has
 // stored its max |V| in vpart[its index]: the last block to arrive reduces all nparts
@@ -148,6 +155,11 @@ struct TcWindow {
     CUtensorMap m_basis_hi, m_basis_lo, m_basisT_hi, m_basisT_lo, m_acat_hi, m_acat_lo;
     CUtensorMap m_basis128_hi, m_basis128_lo;  // same tables, 128-row boxes (fused reduction, phase 2)
     CUtensorMap m_basisT64_hi, m_basisT64_lo;  // basis^T with 64-row boxes (expansion tiles of width 64)
+    // the window spectrum Z as the B operand of T = E Z: Zm[c][k] (ldk x ldk), rows
+    // c < kw: [Re Z(., c) | -Im Z(., c)], rows kw + c: [-Im Z(., c) | -Re Z(., c)]
+    __nv_bfloat16* zm_hi = nullptr;
+    __nv_bfloat16* zm_lo = nullptr;
+    CUtensorMap m_zm_hi, m_zm_lo;  // boxes of kTileT rows (the N tile of T = E Z)
 };
 
 }  // namespace devel
@@ -162,7 +174,10 @@ struct devel_optics {
     __nv_bfloat16* Acat_lo = nullptr;
     CUtensorMap m_X_hi, m_X_lo;
     int* tc_err = nullptr;            // device flag: DEVEL_ETIMEOUT from a bounded wait
-    int tc_expand_bn = 64;            // output tile width of the tensor-core expansion (64 or 128)
+    // tile shapes of the tensor-core path (devel_optics_autotune may change them)
+    int tc_expand_bn = 128;           // output tile width of the expansion (64 or 128)
+    int tc_split = 256;               // image columns per CTA of the fused reduction
+    int tc_split_min = 256;           // smallest split the Q workspace is sized for
     int nsplit;               // split-K slices of reduction stage 1 (over x)
     int nq;                   // split-K slices of reduction stage 2 (over y)
     int npart_red;            // size of the generic reduction partial arrays

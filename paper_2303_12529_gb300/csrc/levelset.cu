@@ -4,19 +4,27 @@
 // central differences of Eq. (numerical-settings), the curvature term of
 // Eq. (curva_numer), Godunov first-order upwinding for the transport term,
 // and the mask of Eq. (phi2mask). One HBM pass: read phi and V (and m),
-// write phi_out and the mask, 13 B/px (17 with m). The 3x3 neighbourhood
-// comes from a shared-memory tile with a one-pixel halo; borders replicate
-// the edge pixel (Neumann ghosts).
+// write phi_out and the mask, 13 B/px (17 with m; +2 with the bf16 mask of
+// the tensor-core path). Borders replicate the edge pixel (Neumann ghosts).
 #include "common.cuh"
 
 namespace devel {
 namespace {
 
-// One thread per four adjacent pixels of a row; its 3 x 6 neighbourhood comes
-// straight from global memory (rows y-1, y, y+1, columns x0-1 .. x0+4, borders
-// replicated), overlapping reads between threads being served by L1. Vector
-// loads and stores when the row is 16-byte aligned.
+// One thread per 4 adjacent pixels in each of kRows consecutive rows; its
+// (kRows + 2) x 6 neighbourhood comes straight from global memory (rows
+// y0-1 .. y0+kRows, columns x0-1 .. x0+4, borders replicated), each row loaded once
+// for all the thread's outputs; overlapping reads between threads are served by
+// L1. Vector loads and stores when the row is 16-byte aligned.
 constexpr int kPX = 4;
+constexpr int kRows = 2;
+
+// sqrt by the SFU (relative error ~2^-22; phi tolerances are far looser)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, float yp, float xpyp, float xmyp,
                                          float xpym, float xmym, float v, float inv_vmax, float dt, float lam,
@@ -30,7 +38,7 @@ __device__ __forceinline__ float step_px(float c, float xm, float xp, float ym, 
     const float b = pos ? fminf(dpx, 0.f) : fmaxf(dpx, 0.f);
     const float cc = pos ? fmaxf(dmy, 0.f) : fminf(dmy, 0.f);
     const float d = pos ? fminf(dpy, 0.f) : fmaxf(dpy, 0.f);
-    out -= F * sqrtf(a * a + b * b + cc * cc + d * d);
+    out -= F * sqrt_approx(a * a + b * b + cc * cc + d * d);
     if (lam != 0.f) {
         const float px = 0.5f * (xp - xm), py = 0.5f * (yp - ym);
         const float pxx = xp + xm - 2.f * c, pyy = yp + ym - 2.f * c;
@@ -60,60 +68,73 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
                 const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
                 int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
                 __nv_bfloat16* __restrict__ mask_bf, int ldb) {
-    const int y = blockIdx.y;
+    const int y0 = blockIdx.y * kRows;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kPX;
     if (x0 >= n) return;
     const double vm = *vmax;
     const float inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
     const bool vec = ((n & 3) == 0) && (x0 + kPX <= n);
-    const size_t prow = (size_t)y * n;
-    float rm[kPX + 2], r0[kPX + 2], rp[kPX + 2];
-    load_row6(phi + (size_t)max(y - 1, 0) * n, x0, n, vec, rm);
-    load_row6(phi + prow, x0, n, vec, r0);
-    load_row6(phi + (size_t)min(y + 1, n - 1) * n, x0, n, vec, rp);
-    float vv[kPX], mv[kPX];
-    if (vec) {
-        const float4 q = *reinterpret_cast<const float4*>(V + prow + x0);
-        vv[0] = q.x; vv[1] = q.y; vv[2] = q.z; vv[3] = q.w;
-        if (m) {
-            const float4 w = *reinterpret_cast<const float4*>(m + prow + x0);
-            mv[0] = w.x; mv[1] = w.y; mv[2] = w.z; mv[3] = w.w;
+    float rw[kRows + 2][kPX + 2];
+#pragma unroll
+    for (int r = 0; r < kRows + 2; ++r)
+        load_row6(phi + (size_t)min(max(y0 - 1 + r, 0), n - 1) * n, x0, n, vec, rw[r]);
+    float vv[kRows][kPX], mv[kRows][kPX];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int y = min(y0 + r, n - 1);
+        const size_t prow = (size_t)y * n;
+        if (vec) {
+            const float4 q = *reinterpret_cast<const float4*>(V + prow + x0);
+            vv[r][0] = q.x; vv[r][1] = q.y; vv[r][2] = q.z; vv[r][3] = q.w;
+            if (m) {
+                const float4 w = *reinterpret_cast<const float4*>(m + prow + x0);
+                mv[r][0] = w.x; mv[r][1] = w.y; mv[r][2] = w.z; mv[r][3] = w.w;
+            } else {
+                mv[r][0] = mv[r][1] = mv[r][2] = mv[r][3] = 1.f;
+            }
         } else {
-            mv[0] = mv[1] = mv[2] = mv[3] = 1.f;
-        }
-    } else {
 #pragma unroll
-        for (int j = 0; j < kPX; ++j) {
-            const bool in = x0 + j < n;
-            vv[j] = in ? V[prow + x0 + j] : 0.f;
-            mv[j] = (m && in) ? m[prow + x0 + j] : 1.f;
+            for (int j = 0; j < kPX; ++j) {
+                const bool in = x0 + j < n;
+                vv[r][j] = in ? V[prow + x0 + j] : 0.f;
+                mv[r][j] = (m && in) ? m[prow + x0 + j] : 1.f;
+            }
         }
     }
-    float o[kPX];
 #pragma unroll
-    for (int j = 0; j < kPX; ++j) {
-        const int i = j + 1;
-        o[j] = step_px(r0[i], r0[i - 1], r0[i + 1], rm[i], rp[i], rp[i + 1], rp[i - 1], rm[i + 1], rm[i - 1], vv[j],
-                       inv, dt, lam, mv[j]);
-    }
-    if (vec) {
-        *reinterpret_cast<float4*>(phi_out + prow + x0) = make_float4(o[0], o[1], o[2], o[3]);
-        if (mask_out)
-            *reinterpret_cast<uchar4*>(mask_out + prow + x0) =
-                make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
-        if (mask_bf) {
-            __nv_bfloat16 h[kPX];
-#pragma unroll
-            for (int j = 0; j < kPX; ++j) h[j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
-            *reinterpret_cast<uint2*>(mask_bf + (size_t)y * ldb + x0) = *reinterpret_cast<const uint2*>(h);
-        }
-    } else {
+    for (int r = 0; r < kRows; ++r) {
+        const int y = y0 + r;
+        if (y >= n) break;
+        const size_t prow = (size_t)y * n;
+        const float(&rm)[kPX + 2] = rw[r];
+        const float(&r0)[kPX + 2] = rw[r + 1];
+        const float(&rp)[kPX + 2] = rw[r + 2];
+        float o[kPX];
 #pragma unroll
         for (int j = 0; j < kPX; ++j) {
-            if (x0 + j < n) {
-                phi_out[prow + x0 + j] = o[j];
-                if (mask_out) mask_out[prow + x0 + j] = o[j] <= 0.f ? 1 : 0;
-                if (mask_bf) mask_bf[(size_t)y * ldb + x0 + j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
+            const int i = j + 1;
+            o[j] = step_px(r0[i], r0[i - 1], r0[i + 1], rm[i], rp[i], rp[i + 1], rp[i - 1], rm[i + 1], rm[i - 1],
+                           vv[r][j], inv, dt, lam, mv[r][j]);
+        }
+        if (vec) {
+            *reinterpret_cast<float4*>(phi_out + prow + x0) = make_float4(o[0], o[1], o[2], o[3]);
+            if (mask_out)
+                *reinterpret_cast<uchar4*>(mask_out + prow + x0) =
+                    make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
+            if (mask_bf) {
+                __nv_bfloat16 h[kPX];
+#pragma unroll
+                for (int j = 0; j < kPX; ++j) h[j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
+                *reinterpret_cast<uint2*>(mask_bf + (size_t)y * ldb + x0) = *reinterpret_cast<const uint2*>(h);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPX; ++j) {
+                if (x0 + j < n) {
+                    phi_out[prow + x0 + j] = o[j];
+                    if (mask_out) mask_out[prow + x0 + j] = o[j] <= 0.f ? 1 : 0;
+                    if (mask_bf) mask_bf[(size_t)y * ldb + x0 + j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
+                }
             }
         }
     }
@@ -142,7 +163,7 @@ int grid_for(size_t npix) {
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s) {
-    dim3 grid((n + 256 * kPX - 1) / (256 * kPX), n);
+    dim3 grid((n + 256 * kPX - 1) / (256 * kPX), (n + kRows - 1) / kRows);
     prof_begin(PK_STEP, s);
     k_levelset_step<<<grid, 256, 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
                                                     ldb);

@@ -233,13 +233,31 @@ __device__ __forceinline__ float2 block_sum2_128(float2 v, float2* sh) {
     return cadd(cadd(sh[0], sh[1]), cadd(sh[2], sh[3]));
 }
 
+// Tensor-core path: window spectrum entry Z(a, b) into the B operand of T = E Z
+// (bf16 hi/lo, [ldz][ldz]): with E's row y = [cos_a(y) | sin_a(y)],
+// T'(y, b) = Re T(y, b) needs Zm[b][a] = Re Z, Zm[b][kw + a] = -Im Z, and
+// T'(y, kw + b) = -Im T(y, b) needs Zm[kw + b][a] = -Im Z, Zm[kw + b][kw + a] = -Re Z.
+__device__ __forceinline__ void put_zm(__nv_bfloat16* hi, __nv_bfloat16* lo, int ldz, int kw, int a, int b,
+                                       float2 z) {
+    auto put = [&](int r, int c, float x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi[(size_t)r * ldz + c] = h;
+        lo[(size_t)r * ldz + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+    };
+    put(b, a, z.x);
+    put(b, kw + a, -z.y);
+    put(kw + b, a, -z.y);
+    put(kw + b, kw + a, -z.x);
+}
+
 // Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), one block of 128
 // threads per g; rect(g) = {a in W : a - g in W}, t = row-major index within rect(g).
 // The aerial image is real, so Ihat(-g) = conj(Ihat(g)): blocks cover the first half of
 // the k2 x k2 window (flat index g <= center) and write the mirrored entry as well.
 __global__ void __launch_bounds__(128)
 k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
-           const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat) {
+           const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat, __nv_bfloat16* __restrict__ zhi,
+           __nv_bfloat16* __restrict__ zlo, int ldz) {
     __shared__ float2 sh[4];
     const int k2 = 2 * k - 1, r2 = k - 1;
     const int g = blockIdx.x;
@@ -260,13 +278,18 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
     if (threadIdx.x == 0) {
         Ihat[g] = s;
         Ihat[k2 * k2 - 1 - g] = make_float2(s.x, -s.y);
+        if (zhi) {
+            put_zm(zhi, zlo, ldz, k2, c1, c2, s);
+            put_zm(zhi, zlo, ldz, k2, k2 - 1 - c1, k2 - 1 - c2, make_float2(s.x, -s.y));
+        }
     }
 }
 
 // Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f.
 __global__ void __launch_bounds__(128)
 k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
-           const float2* __restrict__ rhat, int k, float2* __restrict__ Shat) {
+           const float2* __restrict__ rhat, int k, float2* __restrict__ Shat, __nv_bfloat16* __restrict__ zhi,
+           __nv_bfloat16* __restrict__ zlo, int ldz) {
     __shared__ float2 sh[4];
     const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
     const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
@@ -279,18 +302,21 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
         acc = cadd(acc, cmulc(u, __ldg(row + a)));
     }
     const float2 s = block_sum2_128(acc, sh);
-    if (threadIdx.x == 0) Shat[f] = s;
+    if (threadIdx.x == 0) {
+        Shat[f] = s;
+        if (zhi) put_zm(zhi, zlo, ldz, k, f1, f2, s);
+    }
 }
 
-// T(y, b) = sum_a e^{+i theta_a y} Z(a, b) -> Acat[y] = [Re T | -Im T | 0 ...] (ldk columns),
-// as FP32 (Af) or as bf16 hi/lo (Ahi, Alo). A block of 256 threads takes kTRows rows; Z and
+// FP32 path: T(y, b) = sum_a e^{+i theta_a y} Z(a, b) -> Acat[y] = [Re T | -Im T | 0 ...]
+// (ldk columns). A block of 256 threads takes kTRows rows; Z and
 // the rows' cos / sin values are staged in shared memory; a warp per row, lane l computes
 // the columns b = l, l + 32, ... (and writes the zero padding beyond 2 kw).
 constexpr int kTRows = 8;
 
 __global__ void __launch_bounds__(256)
 k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n, int kw, int ldk,
-           float* __restrict__ Af, __nv_bfloat16* __restrict__ Ahi, __nv_bfloat16* __restrict__ Alo) {
+           float* __restrict__ Af) {
     extern __shared__ float2 zs[];  // [kw * kw] Z, then [kTRows][ldk] floats of basisT
     float* gs = reinterpret_cast<float*>(zs + kw * kw);
     const int y0 = blockIdx.x * kTRows;
@@ -345,19 +371,8 @@ k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n
             v0 = tr;
             v1 = -ti;
         }
-        if (Af) {
-            if (b < kw) Af[base + b] = v0;
-            Af[base + kw + b] = v1;
-        } else {
-            if (b < kw) {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
-                Ahi[base + b] = h0;
-                Alo[base + b] = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-            }
-            const __nv_bfloat16 h1 = __float2bfloat16_rn(v1);
-            Ahi[base + kw + b] = h1;
-            Alo[base + kw + b] = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-        }
+        if (b < kw) Af[base + b] = v0;
+        Af[base + kw + b] = v1;
     }
 }
 
@@ -416,10 +431,10 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
 int reduce_tc(const devel_optics* o, const Window& w, int use_alo, float2* out, cudaStream_t s) {
     const TcWindow& tw = tc_window(o, w);
     tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, use_alo};
-    int rc = tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, o->n, o->ldn, o->ws.Q,
-                                  o->tc_err, s);
+    int rc = tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, o->n, o->ldn, o->tc_split,
+                                  o->ws.Q, o->tc_err, s);
     if (rc) return rc;
-    launch_spec_final(o->ws.Q, tc::spectrum2_slices(o->n, o->ldn), w.ldk, w.kw, out, o->n, s);
+    launch_spec_final(o->ws.Q, tc::spectrum2_slices(o->n, o->ldn, o->tc_split), w.ldk, w.kw, out, o->n, s);
     DEVEL_LAUNCH_CHECK("k_spec_final");
     return DEVEL_OK;
 }
@@ -460,7 +475,10 @@ int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out
 
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_HOPKINS, s);
-    k_ihat_tcc<<<(o->k2 * o->k2 + 1) / 2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat);
+    const bool tcp = o->precision == DEVEL_PREC_BF16X3;
+    k_ihat_tcc<<<(o->k2 * o->k2 + 1) / 2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat,
+                                                        tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr,
+                                                        o->W2.ldk);
     prof_end(PK_HOPKINS, s);
     DEVEL_LAUNCH_CHECK("k_ihat_tcc");
     return DEVEL_OK;
@@ -468,7 +486,9 @@ int launch_ihat(const devel_optics* o, cudaStream_t s) {
 
 int launch_shat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_ADJ_WINDOW, s);
-    k_shat_tcc<<<o->k * o->k, 128, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat);
+    const bool tcp = o->precision == DEVEL_PREC_BF16X3;
+    k_shat_tcc<<<o->k * o->k, 128, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat,
+                                            tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk);
     prof_end(PK_ADJ_WINDOW, s);
     DEVEL_LAUNCH_CHECK("k_shat_tcc");
     return DEVEL_OK;
@@ -479,12 +499,6 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
     const int n = o->n;
     const Workspace& ws = o->ws;
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    prof_begin(PK_EXPAND_T, s);
-    k_expand_T<<<(n + kTRows - 1) / kTRows, 256, sizeof(float2) * w.kw * w.kw + sizeof(float) * kTRows * w.ldk, s>>>(
-        Z, w.basisT, n, w.kw, w.ldk, tcp ? nullptr : ws.Acat, tcp ? o->Acat_hi : nullptr,
-        tcp ? o->Acat_lo : nullptr);
-    prof_end(PK_EXPAND_T, s);
-    DEVEL_LAUNCH_CHECK("k_expand_T");
     EpiArgs ep = ep_in;
     ep.n = n;
     ep.ldc = n;
@@ -492,12 +506,26 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
     ep.vpart = ws.vpart;
     if (tcp) {
         const TcWindow& tw = tc_window(o, w);
+        // T = E Z on the tensor cores (Z is in tw.zm, written by the Hopkins sum that
+        // produced it), as the bf16 hi/lo operand of the expansion
+        tc::Operands opT{&tw.m_basisT_hi, &tw.m_basisT_lo, &tw.m_zm_hi, &tw.m_zm_lo, 1};
+        EpiArgs et;
+        et.Chi = o->Acat_hi;
+        et.Clo = o->Acat_lo;
+        et.ldh = w.ldk;
+        int rc = tc::launch_gemm_split(opT, kTileT, PK_EXPAND_T, n, w.ldk, w.ldk, et, o->tc_err, s);
+        if (rc) return rc;
         const int bn = o->tc_expand_bn;
         tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, bn == 64 ? &tw.m_basisT64_hi : &tw.m_basisT_hi,
                         bn == 64 ? &tw.m_basisT64_lo : &tw.m_basisT_lo, 1};
         if (nparts) *nparts = tc::expand_grid(n, n, bn);
         return tc::launch_expand(op, bn, epi, n, n, w.ldk, ep, o->tc_err, s);
     }
+    prof_begin(PK_EXPAND_T, s);
+    k_expand_T<<<(n + kTRows - 1) / kTRows, 256, sizeof(float2) * w.kw * w.kw + sizeof(float) * kTRows * w.ldk, s>>>(
+        Z, w.basisT, n, w.kw, w.ldk, ws.Acat);
+    prof_end(PK_EXPAND_T, s);
+    DEVEL_LAUNCH_CHECK("k_expand_T");
     if (nparts) *nparts = expand_parts(n);
     if (epi == EPI_VEL)
         return gemm_nt<float, float, EPI_VEL>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk, 1, ep, PK_EXPAND_GEMM,

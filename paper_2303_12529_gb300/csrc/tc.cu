@@ -1,23 +1,19 @@
-// Tensor-core (tcgen05) NT GEMM for the truncated-DFT contractions, sm_103a.
+// Tensor-core (tcgen05) kernels of the truncated-DFT contractions, sm_103a.
 //
-//   D[m][nn] = scale * sum_k A[m][k] B[nn][k]
+// Operands are bf16 hi/lo pairs (x = hi + lo, hi = rn_bf16(x), lo = rn_bf16(x - hi));
+// products are compensated, A B^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T, with
+// FP32 accumulation in TMEM (the A_lo term is skipped when A is exact in bf16, e.g.
+// a 0/1 mask). UMMA M = 128, cta_group::1, K-major operands in 128-byte-swizzled
+// shared memory fed by TMA.
 //
-// with A and B given as bf16 hi/lo pairs (x = hi + lo, hi = rn_bf16(x),
-// lo = rn_bf16(x - hi)) and the compensated product
-//   A B^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T      (FP32 accumulate)
-// (the A_lo term is skipped when A is exact in bf16, e.g. a 0/1 mask).
+//   k_tc_gemm    small NT GEMM, one 128 x BN tile per CTA, bf16 hi/lo output
+//                (the expansion operand T = E Z);
+//   k_tc_spec2   reduction of an image onto a window: both contractions in one CTA;
+//   k_tc_expand  persistent expansion of a window onto the image.
 //
-// One CTA computes a 128 x BN tile (UMMA M = 128, cta_group::1):
-//   warp 0, one thread   TMA producer: 64-element K slabs of A_hi, A_lo,
-//                        B_hi, B_lo (128-byte swizzle) into a STAGES ring;
-//   warp 1, one thread   MMA issuer: 4 K-steps of 16 per slab, 2-3 MMAs each,
-//                        accumulator in TMEM; tcgen05.commit frees a stage;
-//   warps 0-3            epilogue: tcgen05.ld 32 lanes x 16 columns at a
-//                        time, scale, store (and the per-CTA max |D|).
-// Split-K runs over gridDim.z; every split writes its own slice of D.
-// Every mbarrier wait is bounded (about one second of %globaltimer); a
-// timeout sets *err = DEVEL_ETIMEOUT and the CTA stops issuing work, waits
-// (bounded) for the copies it issued, frees its TMEM and returns.
+// Every mbarrier wait is bounded (about one second of %globaltimer); a timeout sets
+// *err = DEVEL_ETIMEOUT and the CTA stops issuing work, waits (bounded) for the
+// copies it issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -45,7 +41,13 @@ struct Cfg {
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
 };
 
-template <int BN, int EPI>
+// One 128 x BN tile of D = A B^T per CTA (split-K over gridDim.z is not used here):
+//   warp 0, one thread   TMA producer: 64-element K slabs of A_hi, A_lo, B_hi, B_lo
+//                        into a STAGES ring;
+//   warp 1, one thread   MMA issuer: 4 K-steps of 16 per slab, 3 MMAs each;
+//   warps 0-3            epilogue: tcgen05.ld 32 lanes x 16 columns, scale, bf16 hi/lo
+//                        split into ep.Chi / ep.Clo (row pitch ep.ldh).
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M, int N,
@@ -58,8 +60,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     uint64_t* empty = full + S;
     uint64_t* accum = empty + S;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-    __shared__ float red[4];
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int kb0 = blockIdx.z * kb_per_split;
@@ -134,9 +134,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     if (have) have = mbar_wait(accum, 0, err);
     have = __all_sync(0xffffffffu, have);  // tcgen05.ld below is warp-collective
     fence_after_sync();
-    float mx = 0.f;
     const int row = m0 + warp * 32 + lane;
-    float* Cz = ep.C ? ep.C + (size_t)blockIdx.z * ep.split_stride : nullptr;
     const float scale = ep.scale;
     for (int c = 0; c < BN; c += 16) {
         float v[16];
@@ -146,47 +144,40 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] *= scale;
         const int col0 = n0 + c;
-        if (row < M) {
-            float* dst = Cz + (size_t)row * ep.ldc + col0;
-            if (col0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        if (row < M && col0 < N) {
+            __nv_bfloat16* dh = ep.Chi + (size_t)row * ep.ldh + col0;
+            __nv_bfloat16* dl = ep.Clo + (size_t)row * ep.ldh + col0;
+            __align__(16) __nv_bfloat16 h[16], l[16];
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) {
-                    *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    if (EPI == EPI_VEL)
-                        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[j]), fabsf(v[j + 1])), fmaxf(fabsf(v[j + 2]), fabsf(v[j + 3]))));
-                }
+            for (int j = 0; j < 16; ++j) {
+                const float x = v[j] * scale;
+                h[j] = __float2bfloat16_rn(x);
+                l[j] = __float2bfloat16_rn(x - __bfloat162float(h[j]));
+            }
+            if (col0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dh) | reinterpret_cast<uintptr_t>(dl)) & 15u) == 0) {
+                reinterpret_cast<uint4*>(dh)[0] = reinterpret_cast<const uint4*>(h)[0];
+                reinterpret_cast<uint4*>(dh)[1] = reinterpret_cast<const uint4*>(h)[1];
+                reinterpret_cast<uint4*>(dl)[0] = reinterpret_cast<const uint4*>(l)[0];
+                reinterpret_cast<uint4*>(dl)[1] = reinterpret_cast<const uint4*>(l)[1];
             } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (col0 + j < N) {
-                        dst[j] = v[j];
-                        if (EPI == EPI_VEL) mx = fmaxf(mx, fabsf(v[j]));
-                    }
+                for (int j = 0; j < 16 && col0 + j < N; ++j) {
+                    dh[j] = h[j];
+                    dl[j] = l[j];
                 }
             }
         }
     }
-    if (EPI == EPI_VEL) {
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        if (lane == 0) red[warp] = mx;
-    }
-    const int part = blockIdx.y * gridDim.x + blockIdx.x;
     // a producer that stopped early waits (bounded) for the loads it issued
     if (warp == 0 && lane == 0 && !ok) {
         for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(&full[i % S], (i / S) & 1, nullptr);
     }
     fence_before_sync();
     __syncthreads();
-    if (EPI == EPI_VEL && threadIdx.x == 0)
-        ep.vpart[part] = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
     if (warp == 1) {
         fence_after_sync();
         tmem_dealloc(tmem, CF::kCols);
     }
-    if (EPI == EPI_VEL) vmax_last_block(ep.vpart, gridDim.x * gridDim.y, ep.counter, ep.vmax, ep.status);
 }
 
 // ---------------------------------------------------------------------------
@@ -734,8 +725,10 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
                             make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0 && row0 < M && col0 < N) {  // boxes entirely outside are not issued
-                        tma_store_2d(&tmC, stg, col0, row0);
+                    if (lane == 0) {  // boxes entirely outside are not issued; every chunk commits a
+                                      // (possibly empty) group, so the wait above always covers the
+                                      // store that last read this buffer
+                        if (row0 < M && col0 < N) tma_store_2d(&tmC, stg, col0, row0);
                         bulk_commit();
                     }
                 } else if (row < M) {
@@ -794,19 +787,19 @@ __global__ void k_mask_bf16(const unsigned char* __restrict__ M, int n, int ldo,
     }
 }
 
-template <int BN, int EPI>
+template <int BN>
 cudaError_t set_attr_bn() {
-    return cudaFuncSetAttribute(k_tc_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<BN>::kSmem);
 }
 
-template <int BN, int EPI>
+template <int BN>
 int launch_gemm_bn(const Operands& op, int M, int N, int kb_per_split, int kb_total, int ksteps_last, int splits,
                    const EpiArgs& ep, int* err, cudaStream_t s) {
     using CF = Cfg<BN>;
     dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
-    k_tc_gemm<BN, EPI><<<grid, 128, CF::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N, kb_per_split,
-                                                     kb_total, ksteps_last, op.use_alo, ep, err);
+    k_tc_gemm<BN><<<grid, 128, CF::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N, kb_per_split, kb_total,
+                                                ksteps_last, op.use_alo, ep, err);
     DEVEL_LAUNCH_CHECK("k_tc_gemm");
     return DEVEL_OK;
 }
@@ -931,37 +924,26 @@ static cudaError_t set_attr_expand() {
     return e;
 }
 
-int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
-                const EpiArgs& ep, int* err, cudaStream_t s) {
-    if (K % 16 != 0 || k_per_split % kBK != 0)
-        return set_error(DEVEL_EINVAL, "tc gemm: K=%d / split %d not aligned", K, k_per_split);
+int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, int K, const EpiArgs& ep, int* err,
+                      cudaStream_t s) {
+    if (K % 16 != 0) return set_error(DEVEL_EINVAL, "tc gemm: K=%d not a multiple of 16", K);
     const int kb_total = (K + kBK - 1) / kBK;
-    const int kb_per_split = k_per_split / kBK;
-    const int splits = (kb_total + kb_per_split - 1) / kb_per_split;
     const int ksteps_last = (K - (kb_total - 1) * kBK) / 16;
     prof_begin(prof_kind, s);
     int rc;
-#define DEVEL_TC_ARGS op, M, N, kb_per_split, kb_total, ksteps_last, splits, ep, err, s
-    if (BN == 128 && epi == EPI_VEL) {
-        rc = launch_gemm_bn<128, EPI_VEL>(DEVEL_TC_ARGS);
-    } else if (epi == EPI_STORE) {
-        switch (BN) {
-#define DEVEL_TC_CASE(bn)                                         \
-    case bn:                                                      \
-        rc = launch_gemm_bn<bn, EPI_STORE>(DEVEL_TC_ARGS);        \
+    switch (BN) {
+#define DEVEL_TC_CASE(bn)                                                                            \
+    case bn:                                                                                         \
+        rc = launch_gemm_bn<bn>(op, M, N, kb_total, kb_total, ksteps_last, 1, ep, err, s);            \
         break;
-            DEVEL_TC_CASE(16) DEVEL_TC_CASE(32) DEVEL_TC_CASE(48) DEVEL_TC_CASE(64) DEVEL_TC_CASE(80)
-            DEVEL_TC_CASE(96) DEVEL_TC_CASE(112) DEVEL_TC_CASE(128) DEVEL_TC_CASE(144) DEVEL_TC_CASE(160)
-            DEVEL_TC_CASE(176) DEVEL_TC_CASE(192) DEVEL_TC_CASE(208) DEVEL_TC_CASE(224) DEVEL_TC_CASE(240)
-            DEVEL_TC_CASE(256)
+        DEVEL_TC_CASE(16) DEVEL_TC_CASE(32) DEVEL_TC_CASE(48) DEVEL_TC_CASE(64) DEVEL_TC_CASE(80)
+        DEVEL_TC_CASE(96) DEVEL_TC_CASE(112) DEVEL_TC_CASE(128) DEVEL_TC_CASE(144) DEVEL_TC_CASE(160)
+        DEVEL_TC_CASE(176) DEVEL_TC_CASE(192) DEVEL_TC_CASE(208) DEVEL_TC_CASE(224) DEVEL_TC_CASE(240)
+        DEVEL_TC_CASE(256)
 #undef DEVEL_TC_CASE
-            default:
-                rc = set_error(DEVEL_EINVAL, "tc gemm: unsupported tile width %d", BN);
-        }
-    } else {
-        rc = set_error(DEVEL_EINVAL, "tc gemm: unsupported epilogue %d with tile width %d", epi, BN);
+        default:
+            rc = set_error(DEVEL_EINVAL, "tc gemm: unsupported tile width %d", BN);
     }
-#undef DEVEL_TC_ARGS
     prof_end(prof_kind, s);
     return rc;
 }
@@ -981,12 +963,13 @@ cudaError_t set_attr_spec2() {
     return cudaFuncSetAttribute(k_tc_spec2<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg2<BN>::kSmem);
 }
 
-int spectrum2_slices(int M, int K) { return ((M + kBM - 1) / kBM) * ((K + kTcSplitK - 1) / kTcSplitK); }
+int spectrum2_slices(int M, int K, int split) { return ((M + kBM - 1) / kBM) * ((K + split - 1) / split); }
 
 int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
-                     float* Q, int* err, cudaStream_t s) {
-    if (K % kBK != 0) return set_error(DEVEL_EINVAL, "tc spectrum: K=%d not a multiple of %d", K, kBK);
-    const int kb_total = K / kBK, kb_per_split = kTcSplitK / kBK;
+                     int split, float* Q, int* err, cudaStream_t s) {
+    if (K % kBK != 0 || split % kBK != 0 || split < kBK)
+        return set_error(DEVEL_EINVAL, "tc spectrum: K=%d / split %d not multiples of %d", K, split, kBK);
+    const int kb_total = K / kBK, kb_per_split = split / kBK;
     const int splits = (kb_total + kb_per_split - 1) / kb_per_split;
     prof_begin(PK_TC_SPECTRUM, s);
     int rc;
@@ -1010,8 +993,8 @@ int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorM
 // Shared-memory opt-in of every kernel instantiation (call once per device,
 // outside stream capture).
 int init_attrs() {
-    cudaError_t e = set_attr_bn<128, EPI_VEL>();
-#define DEVEL_TC_ATTR(bn) if (e == cudaSuccess) e = set_attr_bn<bn, EPI_STORE>();
+    cudaError_t e = cudaSuccess;
+#define DEVEL_TC_ATTR(bn) if (e == cudaSuccess) e = set_attr_bn<bn>();
     DEVEL_TC_ATTR(16) DEVEL_TC_ATTR(32) DEVEL_TC_ATTR(48) DEVEL_TC_ATTR(64) DEVEL_TC_ATTR(80) DEVEL_TC_ATTR(96)
     DEVEL_TC_ATTR(112) DEVEL_TC_ATTR(128) DEVEL_TC_ATTR(144) DEVEL_TC_ATTR(160) DEVEL_TC_ATTR(176)
     DEVEL_TC_ATTR(192) DEVEL_TC_ATTR(208) DEVEL_TC_ATTR(224) DEVEL_TC_ATTR(240) DEVEL_TC_ATTR(256)

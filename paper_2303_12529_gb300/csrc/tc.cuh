@@ -23,21 +23,21 @@ struct Operands {
 // elements; boxes of 64 columns x box_rows rows, 128-byte swizzle, zero fill.
 int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int box_rows);
 
-// D = ep.scale * A B^T (M x N, contraction length K, a multiple of 16), BN a
-// multiple of 16 up to 256; split-K slices of k_per_split (a multiple of 64).
-// epi: EPI_STORE (row-major into ep.C + z * split_stride) or EPI_VEL
-// (store and the per-CTA max |D| into ep.vpart; BN = 128).
-int launch_gemm(const Operands& op, int BN, int epi, int prof_kind, int M, int N, int K, int k_per_split,
-                const EpiArgs& ep, int* err, cudaStream_t s);
+// D = ep.scale * A B^T (M x N, contraction length K, a multiple of 16, all of it in
+// one CTA), tiles of 128 x BN (BN a multiple of 16 up to 256, the B map's box height),
+// written as bf16 hi/lo into ep.Chi / ep.Clo with row pitch ep.ldh.
+int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, int K, const EpiArgs& ep, int* err,
+                      cudaStream_t s);
 
 // Both contractions of a window reduction in one kernel (k_tc_spec2): the phase-1
 // operands as in launch_gemm (A = image [M rows][K], B = basis [BN rows][K]), and
 // Chi/Clo = the same basis tables with 128-row boxes (the phase-2 A operand).
-// Writes spectrum2_slices(M, K) partial [BN][BN] slices to Q; BN = the window's ldk,
-// K a multiple of 64.
-int spectrum2_slices(int M, int K);
+// Writes spectrum2_slices(M, K, split) partial [BN][BN] slices to Q; BN = the window's
+// ldk, K a multiple of 64.
+// Each CTA takes 128 rows and `split` columns of the image (split a multiple of 64).
+int spectrum2_slices(int M, int K, int split);
 int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
-                     float* Q, int* err, cudaStream_t s);
+                     int split, float* Q, int* err, cudaStream_t s);
 
 // Persistent expansion D = ep.scale * A B^T (k_tc_expand), M x N output row-major in
 // ep.C with pitch ep.ldc; A [M][K] map with 128-row boxes, B [N][K] map with BN-row

@@ -163,3 +163,32 @@ def test_adjoint_full_size(prec, tol):
                                 o.w.astype(np.float32).astype(np.float64))
     assert rel_err(host(V, n), ref) <= tol
     dv.devel_optics_check(opt)
+
+
+@pytest.mark.parametrize("n,K,k,kind", [(512, 6, 11, "optics"), (200, 6, 11, "optics")])
+def test_autotuned_tiles_keep_parity(n, K, k, kind):
+    """devel_optics_autotune only changes tile shapes: afterwards the forward image and
+    dL/dM still match the oracle within the compensated-BF16 tolerance, and the chosen
+    shapes are among the tuner's candidates."""
+    dv = need_gpu()
+    H, w = _model(n, K, k, kind)
+    opt = dv.devel_optics_create(n, H, w, dv.DEVEL_PREC_BF16X3)
+    dv.devel_optics_autotune(opt)
+    cfg = dv.devel_optics_config(opt)
+    ldn = -(-n // 64) * 64
+    assert cfg["expand_tile_n"] in (64, 128)
+    assert cfg["reduce_split"] % 64 == 0 and 64 <= cfg["reduce_split"] <= max(512, ldn)
+    Hc = H.astype(np.complex64).astype(np.complex128)
+    wc = w.astype(np.float32).astype(np.float64)
+    M = synth.rect_clip(2, n=n, border=4).astype(np.float32)
+    out = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    dv.devel_litho_forward(opt, dev(M), out)
+    R = synth.random_field(5, n, -1.0, 1.0).astype(np.float32)
+    V = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    vm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dv.devel_litho_adjoint(opt, dev(M), dev(R), V, vm)
+    torch.cuda.synchronize()
+    dv.devel_optics_check(opt)
+    assert rel_err(host(out, n), litho.aerial(M.astype(np.float64), Hc, wc)) <= TOL_BF16X3
+    refV = litho.aerial_gradient(M.astype(np.float64), R.astype(np.float64), Hc, wc)
+    assert rel_err(host(V, n), refV) <= TOL_BF16X3
