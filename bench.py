@@ -587,6 +587,40 @@ def run_batched(args, wl):
         dist.destroy_process_group()
 
 
+def run_calls_once(args, wl):
+    """Each ABI call of the hot path once at the workload's size, through the public
+    API (TSDF, forward, resist/loss, adjoint, level-set step), for kernel captures with
+    ncu; prints one line of results, no timing."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+    n, K, k, beta = wl["n"], wl["K"], wl["k"], wl["beta"]
+    prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3, "both": dv.DEVEL_PREC_BF16X3}[args.precision]
+    o = synth.optics(n, K, k)
+    Zt = synth.manhattan_clip(wl["seed"]) if n == 2048 else synth.rect_clip(wl["seed"], n=n)
+    opt = dv.devel_optics_create(n, o.H, o.w, prec)
+    N = n * n
+    tgt = torch.from_numpy(Zt.ravel().copy()).cuda()
+    m = tgt.float()
+    phi, phi2 = torch.empty(N, device="cuda"), torch.empty(N, device="cuda")
+    d2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    I, R, V = (torch.empty(N, device="cuda") for _ in range(3))
+    M = torch.empty(N, dtype=torch.uint8, device="cuda")
+    vm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L = torch.zeros(4, dtype=torch.float64, device="cuda")
+    C = torch.zeros(2, dtype=torch.int64, device="cuda")
+    dv.devel_reinit_sdf(n, tgt, phi, d2)
+    dv.devel_litho_forward(opt, m, I)
+    dv.devel_resist_loss(opt, I, tgt, dv.resist_params(beta=beta), R, L, C)
+    dv.devel_litho_adjoint(opt, m, R, V, vm)
+    dv.devel_levelset_step(n, phi, V, vm, None, 0.5, 0.1, phi2, M)
+    torch.cuda.synchronize()
+    dv.devel_optics_check(opt)
+    print(json.dumps({"calls_once": args.workload, "precision": args.precision, "loss": float(L[0]),
+                      "l2": int(C[0]), "pvb": int(C[1]), "vmax": float(vm[0])}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,10 +631,14 @@ def main():
     ap.add_argument("--precision", choices=["both", "fp32", "bf16x3"], default="both",
                     help="both: the compensated-BF16 solve is the headline, the plain FP32 solve its comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--calls-once", action="store_true",
+                    help="run each hot-path ABI call once at the workload size (for kernel captures)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.calls_once:
+        run_calls_once(args, wl)
     elif "batch" in wl:
         run_batched(args, wl)
     else:
