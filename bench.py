@@ -44,7 +44,12 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernels, from the ncu captures summarised under profiles/; a kernel changed since its
 # capture has no entry.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/kernels_manhattan2048_bf16x3.md: k_tc_spec2 inside the solve, mean of the
+    # mask launch (9.47 MB) and the dL/dI launch (18.91 MB); the partial spectra it writes
+    # stay in L2 for k_spec_final, so DRAM writes were 0
+    ("tc_spectrum", "bf16x3"): 14.19e6,
+}
 
 
 def algorithmic_flops_per_iter(n, K, k):
