@@ -93,6 +93,15 @@ int devel_optics_n(const devel_optics* optics);
 int devel_optics_check(const devel_optics* optics, cudaStream_t stream);
 
 /*
+ * Diagnostic (no counterpart in the paper): launches one thread that waits on a
+ * device barrier nothing signals, through the same bounded wait the tensor-core
+ * kernels use. The wait gives up after about one second and records
+ * DEVEL_ETIMEOUT in the handle's flag, which the next devel_optics_check
+ * returns (and clears); the context stays usable. Asynchronous on `stream`.
+ */
+int devel_selftest_bounded_wait(const devel_optics* optics, cudaStream_t stream);
+
+/*
  * Tile-shape tuner (no counterpart in the paper; it serves batches of clips of
  * uneven sizes). Times the candidate tile shapes of the handle's tensor-core
  * kernels on its own workspace (the output tile width of the expansions, the

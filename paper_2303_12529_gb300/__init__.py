@@ -88,6 +88,7 @@ _sig("devel_profile_collect", [])
 _sig("devel_profile_kinds", [])
 _sig("devel_profile_select", [ctypes.c_ulonglong])
 _sig("devel_optics_autotune", [_P, _P])
+_sig("devel_selftest_bounded_wait", [_P, _P])
 _sig("devel_optics_config", [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)])
 _sig("devel_profile_query", [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                              ctypes.POINTER(ctypes.c_double)])
@@ -97,7 +98,8 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_optics_n", "devel_optics_check", "devel_litho_forward", "devel_resist_loss", "devel_litho_adjoint",
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
-            "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config")
+            "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
+            "devel_selftest_bounded_wait")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -186,6 +188,12 @@ def devel_optics_config(optics: Optics) -> dict:
     bn, split = _I(), _I()
     _check(_lib.devel_optics_config(optics.handle, ctypes.byref(bn), ctypes.byref(split)))
     return {"expand_tile_n": bn.value, "reduce_split": split.value}
+
+
+def devel_selftest_bounded_wait(optics: Optics, stream=None):
+    """Diagnostic: a device wait on a barrier nothing signals gives up (about 1 s) and
+    leaves DEVEL_ETIMEOUT for the next devel_optics_check."""
+    _check(_lib.devel_selftest_bounded_wait(optics.handle, _stream(stream)))
 
 
 def devel_optics_destroy(optics: Optics):

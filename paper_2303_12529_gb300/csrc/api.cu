@@ -718,6 +718,11 @@ int devel_optics_config(const devel_optics* o, int* expand_tile_n, int* reduce_s
     return DEVEL_OK;
 }
 
+int devel_selftest_bounded_wait(const devel_optics* o, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_selftest_bounded_wait: optics is NULL");
+    return tc::launch_wait_selftest(o->tc_err, s);
+}
+
 int devel_optics_check(const devel_optics* o, cudaStream_t s) {
     if (!o) return set_error(DEVEL_EINVAL, "devel_optics_check: optics is NULL");
     DEVEL_CUDA_TRY(cudaStreamSynchronize(s));

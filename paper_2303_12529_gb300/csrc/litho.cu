@@ -29,6 +29,7 @@
 //   2. out = Acat basisT^T   (FP32 NT GEMM or tcgen05), with a fused epilogue:
 //      plain store, velocity (x2, max |.|) or the resist loss (dL/dI).
 #include <algorithm>
+#include <cfloat>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -130,7 +131,7 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, 
         __syncthreads();
     }
     float* Cz = ep.C + blockIdx.z * ep.split_stride;
-    float mx = 0.f;
+    int mxi = 0;  // max |out| as a float bit pattern: a NaN or inf exceeds every finite value
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int m = m0 + ty + 16 * i;
@@ -141,18 +142,18 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, 
             if (nn >= N) continue;
             const float v = acc[i][j] * ep.scale;
             Cz[(size_t)m * ep.ldc + nn] = v;
-            if (EPI == EPI_VEL) mx = fmaxf(mx, fabsf(v));
+            if (EPI == EPI_VEL) mxi = max(mxi, __float_as_int(fabsf(v)));
         }
     }
     const int part = blockIdx.y * gridDim.x + blockIdx.x;
     if (EPI == EPI_VEL) {
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0) red[tid >> 5] = mx;
+        for (int o = 16; o > 0; o >>= 1) mxi = max(mxi, __shfl_down_sync(0xffffffffu, mxi, o));
+        if ((tid & 31) == 0) red[tid >> 5] = __int_as_float(mxi);
         __syncthreads();
         if (tid == 0) {
-            float m = red[0];
-            for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
-            ep.vpart[part] = m;
+            int m = __float_as_int(red[0]);
+            for (int w = 1; w < kThreads / 32; ++w) m = max(m, __float_as_int(red[w]));
+            ep.vpart[part] = __int_as_float(m);
         }
         vmax_last_block(ep.vpart, gridDim.x * gridDim.y, ep.counter, ep.vmax, ep.status);
     }

@@ -49,7 +49,8 @@ struct Corner {
     float z, ez2;
 };
 __device__ __forceinline__ Corner resist_corner(float I, float a, float b) {
-    const float e = sfu_exp2(fminf(fmaf(a, I, b), 126.f));
+    const float u = fmaf(a, I, b);
+    const float e = sfu_exp2(u > 126.f ? 126.f : u);  // (a NaN stays NaN: fminf would drop it)
     const float z = sfu_rcp(1.f + e);
     return Corner{z, e * z * z};
 }

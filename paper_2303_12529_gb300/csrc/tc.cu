@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cstring>
 #include <mutex>
 
@@ -533,7 +534,7 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
     uint64_t* t_empty = t_full + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(t_empty + 2);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    __shared__ float red[4];
+    __shared__ int red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = (int)(((long long)blockIdx.x * tiles) / gridDim.x);
@@ -602,7 +603,7 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    float mx = 0.f;
+    int mxi = 0;  // max |D| as a float bit pattern (EPI_VEL)
 
     if (warp == 4) {
         if (lane == 0) {
@@ -711,9 +712,12 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[c + j]) * scale;
                 const int col0 = nt * BN + c;
                 if (EPI == EPI_VEL && row < M) {
+                    // max |V| on the bit patterns: for non-negative floats the integer order is
+                    // the float order, and a NaN (or inf) pattern exceeds every finite one, so
+                    // a non-finite value survives into the CTA's partial (fmaxf would drop a NaN)
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (col0 + j < N) mx = fmaxf(mx, fabsf(v[j]));
+                        if (col0 + j < N) mxi = max(mxi, __float_as_int(fabsf(v[j])));
                 }
                 if (use_tma_store) {
                     uint8_t* stg = sC + (warp * 2 + (chunk & 1)) * 4096;
@@ -741,19 +745,34 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
         }
         if (use_tma_store && lane == 0) bulk_wait_all();
         if (EPI == EPI_VEL) {
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-            if (lane == 0) red[warp] = mx;
+            for (int o = 16; o > 0; o >>= 1) mxi = max(mxi, __shfl_down_sync(0xffffffffu, mxi, o));
+            if (lane == 0) red[warp] = mxi;
         }
     }
     __syncwarp();
     fence_before_sync();
     __syncthreads();
-    if (EPI == EPI_VEL && threadIdx.x == 0) ep.vpart[blockIdx.x] = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    if (EPI == EPI_VEL && threadIdx.x == 0)
+        ep.vpart[blockIdx.x] = __int_as_float(max(max(red[0], red[1]), max(red[2], red[3])));
     if (warp == 5) {
         fence_after_sync();
         tmem_dealloc(tmem, CX::kCols);
     }
     if (EPI == EPI_VEL) vmax_last_block(ep.vpart, gridDim.x, ep.counter, ep.vmax, ep.status);
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing
+// arrives on; the wait gives up after its time limit and sets *err.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -988,6 +1007,12 @@ int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorM
     }
     prof_end(PK_TC_SPECTRUM, s);
     return rc;
+}
+
+int launch_wait_selftest(int* err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(err);
+    DEVEL_LAUNCH_CHECK("k_wait_selftest");
+    return DEVEL_OK;
 }
 
 // Shared-memory opt-in of every kernel instantiation (call once per device,

@@ -48,6 +48,10 @@ int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, cons
                   cudaStream_t s);
 int expand_grid(int M, int N, int BN);
 
+// One CTA whose thread waits (bounded) on an mbarrier that nothing signals: sets
+// *err = DEVEL_ETIMEOUT after the wait limit (about one second).
+int launch_wait_selftest(int* err, cudaStream_t s);
+
 // Shared-memory opt-in of all tensor-core kernels (once per device).
 int init_attrs();
 
