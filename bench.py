@@ -45,9 +45,9 @@ L2_BYTES = 129 * 1024 * 1024
 # kernels, from the ncu captures summarised under profiles/; a kernel changed since its
 # capture has no entry.
 TRAFFIC = {
-    # profiles/kernels_manhattan2048_bf16x3.md: k_tc_spec2 inside the solve, mean of the
-    # mask launch (9.47 MB) and the dL/dI launch (18.91 MB); the partial spectra it writes
-    # stay in L2 for k_spec_final, so DRAM writes were 0
+    # profiles/kernels_manhattan2048_bf16x3.md ("DRAM traffic inside the solve"): k_tc_spec2,
+    # mean of the mask launch (9.47 MB) and the dL/dI launch (18.91 MB); the partial
+    # spectra it writes stay in L2 for k_spec_final, so DRAM writes were 0
     ("tc_spectrum", "bf16x3"): 14.19e6,
 }
 
