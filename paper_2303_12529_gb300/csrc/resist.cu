@@ -6,9 +6,9 @@
 // #{[d_in^2 I >= I_th] xor [d_out^2 I >= I_th]}.
 //
 // One HBM pass: read I and Z_t, write R (FP32, 9 B/px) or its bf16 hi/lo split
-// (the operand of the adjoint's reduction, 9 B/px). Sums are FP32 up to the warp,
-// FP64 from the block up, reduced in a fixed order and then over blocks in block
-// order, so results are bitwise reproducible.
+// (the operand of the adjoint's reduction, 9 B/px). Sums are FP32 within a block
+// and FP64 across blocks (the global loss reduction), each in a fixed order, so
+// results are bitwise reproducible.
 #include "resist.cuh"
 
 namespace devel {

@@ -73,8 +73,9 @@ __device__ __forceinline__ float resist_px(float I, bool zt_on, const ResistArgs
     return fmaf(p.k_out * eo, co.ez2, g);
 }
 
-// Block reduction of the accumulators in a fixed order (FP32 / int within a warp,
-// FP64 / int64 across warps); thread 0 writes the block's partial to
+// Block reduction of the accumulators in a fixed order (FP32 / int within the block;
+// the partials are summed in FP64 / int64 across blocks); thread 0 writes the block's
+// partial to
 // dpart[part * 3 + {0,1,2}] and lpart[part * 2 + {0,1}]. Every thread of the block
 // must call it. sf/si: shared scratch of >= 32 entries.
 __device__ __forceinline__ void block_store_loss(const LossAcc& a, int part, double* dpart, long long* lpart,
@@ -97,10 +98,10 @@ __device__ __forceinline__ void block_store_loss(const LossAcc& a, int part, dou
         si[1][w] = pvb;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // FP32 over the block's warps (FP64 arithmetic is slow here)
         const int nw = (blockDim.x + 31) >> 5;
-        double x0 = 0, x1 = 0, x2 = 0;
-        long long c0 = 0, c1 = 0;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        int c0 = 0, c1 = 0;
         for (int i = 0; i < nw; ++i) {
             x0 += sf[0][i];
             x1 += sf[1][i];
