@@ -51,7 +51,7 @@ struct ResistArgs {
 
 // N tile of the tensor-core GEMM T = E Z (a multiple of 16): narrow, so that the
 // GEMM over n rows and ldk <= 256 columns still spreads over several CTAs per row block.
-constexpr int kTileT = 48;
+constexpr int kTileT = 16;
 
 // Epilogues of the contraction GEMMs.
 enum { EPI_STORE = 0, EPI_VEL = 1, EPI_SPLIT = 2 };
