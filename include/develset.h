@@ -52,6 +52,14 @@ extern "C" {
 #define DEVEL_PREC_FP32 0   /* FP32 FMA on the CUDA cores                         */
 #define DEVEL_PREC_BF16X3 1 /* tcgen05 BF16 hi+lo split, 3 products, FP32 accumulate */
 
+/* Upwind schemes of the level-set transport term (Sec. III-C names WENO for
+ * |grad phi| without specifying it): Godunov's flux with first-order one-sided
+ * differences, or with fifth-order WENO one-sided derivatives (Hamilton-Jacobi
+ * WENO: three third-order ENO candidates, ideal weights 0.1 / 0.6 / 0.3,
+ * smoothness indicators, eps = 1e-6 max v^2). */
+#define DEVEL_UPWIND_GODUNOV1 0
+#define DEVEL_UPWIND_WENO5 1
+
 /* Thread-local text of the last error returned on this thread ("" if none). */
 const char* devel_last_error(void);
 
@@ -194,6 +202,11 @@ int devel_litho_adjoint(const devel_optics* optics, const float* mask, const flo
 int devel_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                         const float* m, float dt, float lambda, float* phi_out,
                         unsigned char* mask_out, cudaStream_t stream);
+/* The same update with the WENO5 one-sided derivatives in the transport term
+ * (DEVEL_UPWIND_WENO5); same arguments and layout. */
+int devel_levelset_step_weno5(int n, const float* phi, const float* V, const double* vmax,
+                              const float* m, float dt, float lambda, float* phi_out,
+                              unsigned char* mask_out, cudaStream_t stream);
 
 /*
  * Truncated signed distance of a mask, Eqs. (sdf), (tsdf) (Alg. 1 CUDA_TSDF):
@@ -253,6 +266,8 @@ typedef struct {
                             on later calls with identical params and clip list (kernel
                             arguments are baked in; the data behind the pointers is read at
                             replay); 0: launch kernel by kernel. Ignored while a profile is open. */
+    int upwind;          /* one-sided derivatives of |grad phi|: DEVEL_UPWIND_GODUNOV1 (first order)
+                            or DEVEL_UPWIND_WENO5 (fifth-order WENO, Sec. III-C)                */
 } devel_ilt_params;
 
 typedef struct {

@@ -32,6 +32,7 @@ class SolveParams:
     start_iter: int = 0
     d_lo: float = sdf.D_LO
     d_hi: float = sdf.D_HI
+    weno: bool = False  # WENO5 one-sided derivatives in the upwind |grad phi|
 
 
 @dataclass
@@ -50,7 +51,7 @@ def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None):
     res = _resist.resist(I, Zt, p.resist)
     V = litho.aerial_gradient(M, res.R, H, w)
     vmax = float(np.abs(V).max())
-    phi, M = levelset.step(phi, V, vmax, m, p.dt, p.lam)
+    phi, M = levelset.step(phi, V, vmax, m, p.dt, p.lam, weno=p.weno)
     if p.reinit_every > 0 and (i + 1) % p.reinit_every == 0:
         phi = sdf.tsdf(M, p.d_lo, p.d_hi)
     return phi, res

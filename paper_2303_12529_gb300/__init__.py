@@ -25,6 +25,8 @@ DEVEL_ECUDA = -2
 DEVEL_ENOMEM = -3
 DEVEL_ETIMEOUT = -4
 DEVEL_ENAN = -5
+DEVEL_UPWIND_GODUNOV1 = 0
+DEVEL_UPWIND_WENO5 = 1
 DEVEL_PREC_FP32 = 0
 DEVEL_PREC_BF16X3 = 1
 
@@ -52,7 +54,8 @@ class devel_resist_params(ctypes.Structure):
 
 class devel_ilt_params(ctypes.Structure):
     _fields_ = [("resist", devel_resist_params), ("dt", _F), ("lambda_", _F), ("d_lo", _F),
-                ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I), ("use_graph", _I)]
+                ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I), ("use_graph", _I),
+                ("upwind", _I)]
 
 
 class devel_clip(ctypes.Structure):
@@ -79,6 +82,7 @@ _sig("devel_resist_loss", [_P, _P, _P, ctypes.POINTER(devel_resist_params), _P, 
 _sig("devel_litho_adjoint", [_P, _P, _P, _P, _P, _P])
 _sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
+_sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
@@ -99,7 +103,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
-            "devel_selftest_bounded_wait")
+            "devel_selftest_bounded_wait", "devel_levelset_step_weno5")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -232,10 +236,11 @@ def devel_litho_adjoint(optics: Optics, mask, dLdI, dLdM, vmax, stream=None):
 
 
 def devel_levelset_step(n: int, phi, V, vmax, m, dt: float, lam: float, phi_out, mask_out,
-                        stream=None):
+                        stream=None, weno5: bool = False):
     import torch
     N = n * n
-    _check(_lib.devel_levelset_step(n, _ptr(phi, torch.float32, N, "phi"),
+    fn = _lib.devel_levelset_step_weno5 if weno5 else _lib.devel_levelset_step
+    _check(fn(n, _ptr(phi, torch.float32, N, "phi"),
                                     _ptr(V, torch.float32, N, "V"),
                                     _ptr(vmax, torch.float64, 1, "vmax"),
                                     _ptr(m, torch.float32, N, "m"), dt, lam,
@@ -260,9 +265,10 @@ def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float
 
 
 def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,
-               reinit_every=5, start_iter=0, use_graph=True) -> devel_ilt_params:
+               reinit_every=5, start_iter=0, use_graph=True, upwind=0) -> devel_ilt_params:
+    """upwind: DEVEL_UPWIND_GODUNOV1 (0) or DEVEL_UPWIND_WENO5 (1)."""
     return devel_ilt_params(resist if resist is not None else resist_params(), dt, lam, d_lo, d_hi,
-                            iters, reinit_every, start_iter, int(bool(use_graph)))
+                            iters, reinit_every, start_iter, int(bool(use_graph)), int(upwind))
 
 
 @dataclass

@@ -189,7 +189,7 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
         rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
         if (rc) return rc;
         rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
-                                  tcp ? o->Xhi : nullptr, o->ldn, s);
+                                  tcp ? o->Xhi : nullptr, o->ldn, s, p->upwind);
         if (rc) return rc;
         float* tmp = phi;
         phi = phi_alt;
@@ -772,8 +772,9 @@ int devel_litho_adjoint(const devel_optics* o, const float* mask, const float* d
     return adjoint_from_mhat(o, dLdI, dLdM, vmax, nullptr, s);
 }
 
-int devel_levelset_step(int n, const float* phi, const float* V, const double* vmax, const float* m,
-                        float dt, float lambda, float* phi_out, unsigned char* mask_out, cudaStream_t s) {
+static int levelset_step_checked(int n, const float* phi, const float* V, const double* vmax, const float* m,
+                                 float dt, float lambda, float* phi_out, unsigned char* mask_out, cudaStream_t s,
+                                 int upwind) {
     if (n < 1 || n > 16384) return set_error(DEVEL_EINVAL, "devel_levelset_step: n=%d outside [1, 16384]", n);
     CHECK_PTR(phi, "phi");
     CHECK_PTR(V, "V");
@@ -784,7 +785,17 @@ int devel_levelset_step(int n, const float* phi, const float* V, const double* v
     if (phi == phi_out) return set_error(DEVEL_EINVAL, "devel_levelset_step: phi_out aliases phi");
     if (!std::isfinite(dt) || !std::isfinite(lambda))
         return set_error(DEVEL_EINVAL, "devel_levelset_step: dt/lambda not finite");
-    return launch_levelset_step(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, nullptr, 0, s);
+    return launch_levelset_step(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, nullptr, 0, s, upwind);
+}
+
+int devel_levelset_step(int n, const float* phi, const float* V, const double* vmax, const float* m,
+                        float dt, float lambda, float* phi_out, unsigned char* mask_out, cudaStream_t s) {
+    return levelset_step_checked(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, s, DEVEL_UPWIND_GODUNOV1);
+}
+
+int devel_levelset_step_weno5(int n, const float* phi, const float* V, const double* vmax, const float* m,
+                              float dt, float lambda, float* phi_out, unsigned char* mask_out, cudaStream_t s) {
+    return levelset_step_checked(n, phi, V, vmax, m, dt, lambda, phi_out, mask_out, s, DEVEL_UPWIND_WENO5);
 }
 
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
@@ -807,6 +818,8 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
     if (p->iters < 0 || p->reinit_every < 0 || p->start_iter < 0)
         return set_error(DEVEL_EINVAL, "devel_ilt_solve: negative iters/reinit_every/start_iter");
     if (!(p->d_lo <= p->d_hi)) return set_error(DEVEL_EINVAL, "devel_ilt_solve: d_lo > d_hi");
+    if (p->upwind != DEVEL_UPWIND_GODUNOV1 && p->upwind != DEVEL_UPWIND_WENO5)
+        return set_error(DEVEL_EINVAL, "devel_ilt_solve: unknown upwind scheme %d", p->upwind);
     for (int c = 0; c < nclips; ++c) {
         const devel_clip& cl = clips[c];
         if (!cl.optics) return set_error(DEVEL_EINVAL, "devel_ilt_solve: clip %d has no optics", c);

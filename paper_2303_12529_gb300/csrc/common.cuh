@@ -226,9 +226,11 @@ int resist_parts(int n);
 
 // levelset.cu
 // mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction
+// upwind: DEVEL_UPWIND_GODUNOV1 or DEVEL_UPWIND_WENO5 (one-sided derivatives of |grad phi|)
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
-                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s);
+                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s,
+                         int upwind = DEVEL_UPWIND_GODUNOV1);
 // tensor-core path: spectrum of the mask already in Xhi (bf16, exact)
 int launch_spectrum_mask_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s);
 int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s);

@@ -140,6 +140,94 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
     }
 }
 
+// ---------------------------------------------------------------------------
+// WENO5 variant: the same update with fifth-order WENO one-sided derivatives
+// (Hamilton-Jacobi WENO: three third-order ENO candidates on the one-sided
+// differences, ideal weights 0.1 / 0.6 / 0.3 modulated by the smoothness
+// indicators, eps = 1e-6 max v_k^2) in the Godunov flux. A block computes a
+// 32 x 8 tile from a shared-memory copy with a 3-pixel halo (borders replicated).
+// ---------------------------------------------------------------------------
+constexpr int kWX = 32, kWY = 8, kWH = 3;
+constexpr int kWTX = kWX + 2 * kWH, kWTY = kWY + 2 * kWH;
+
+// WENO5 derivative from the one-sided differences v1..v5 (v3 nearest the node on the
+// upwind side). The weights are invariant under v -> v / s (the smoothness
+// indicators and eps scale as s^2), so they are computed on v / max|v|: no overflow
+// in FP32 where the differences are tiny, and 0 where they all vanish.
+__device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5) {
+    const float s = fmaxf(fmaxf(fmaxf(fabsf(v1), fabsf(v2)), fmaxf(fabsf(v3), fabsf(v4))), fabsf(v5));
+    if (!(s > 0.f)) return 0.f;
+    const float r = 1.f / s;
+    const float u1 = v1 * r, u2 = v2 * r, u3 = v3 * r, u4 = v4 * r, u5 = v5 * r;
+    const float p1 = u1 * (1.f / 3.f) - u2 * (7.f / 6.f) + u3 * (11.f / 6.f);
+    const float p2 = -u2 * (1.f / 6.f) + u3 * (5.f / 6.f) + u4 * (1.f / 3.f);
+    const float p3 = u3 * (1.f / 3.f) + u4 * (5.f / 6.f) - u5 * (1.f / 6.f);
+    const float a = u1 - 2.f * u2 + u3, b = u1 - 4.f * u2 + 3.f * u3;
+    const float c = u2 - 2.f * u3 + u4, d = u2 - u4;
+    const float e = u3 - 2.f * u4 + u5, f = 3.f * u3 - 4.f * u4 + u5;
+    const float eps = 1e-6f;  // 1e-6 max u_k^2 with max |u_k| = 1
+    const float t1 = (13.f / 12.f) * a * a + 0.25f * b * b + eps;
+    const float t2 = (13.f / 12.f) * c * c + 0.25f * d * d + eps;
+    const float t3 = (13.f / 12.f) * e * e + 0.25f * f * f + eps;
+    const float a1 = 0.1f / (t1 * t1), a2 = 0.6f / (t2 * t2), a3 = 0.3f / (t3 * t3);
+    return s * (a1 * p1 + a2 * p2 + a3 * p3) / (a1 + a2 + a3);
+}
+
+__global__ void __launch_bounds__(kWX * kWY)
+k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
+                     const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
+                     int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
+                     __nv_bfloat16* __restrict__ mask_bf, int ldb) {
+    __shared__ float t[kWTY][kWTX + 1];
+    const int x0 = blockIdx.x * kWX, y0 = blockIdx.y * kWY;
+    for (int i = threadIdx.y * kWX + threadIdx.x; i < kWTX * kWTY; i += kWX * kWY) {
+        const int ty = i / kWTX, tx = i - ty * kWTX;
+        const int gy = min(max(y0 + ty - kWH, 0), n - 1), gx = min(max(x0 + tx - kWH, 0), n - 1);
+        t[ty][tx] = phi[(size_t)gy * n + gx];
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= n || y >= n) return;
+    const int cx = threadIdx.x + kWH, cy = threadIdx.y + kWH;
+    const float c = t[cy][cx];
+    const double vm = *vmax;
+    const float inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
+    const size_t p = (size_t)y * n + x;
+    const float F = -dt * (V[p] * inv);
+    float out = c;
+    if (F != 0.f) {
+        float dx[6], dy[6];  // d(k) = phi(k) - phi(k - 1), k = -2 .. 3 relative to the node
+#pragma unroll
+        for (int k = -2; k <= 3; ++k) {
+            dx[k + 2] = t[cy][cx + k] - t[cy][cx + k - 1];
+            dy[k + 2] = t[cy + k][cx] - t[cy + k - 1][cx];
+        }
+        const float dmx = weno5(dx[0], dx[1], dx[2], dx[3], dx[4]);
+        const float dpx = weno5(dx[5], dx[4], dx[3], dx[2], dx[1]);
+        const float dmy = weno5(dy[0], dy[1], dy[2], dy[3], dy[4]);
+        const float dpy = weno5(dy[5], dy[4], dy[3], dy[2], dy[1]);
+        const bool pos = F > 0.f;
+        const float a = pos ? fmaxf(dmx, 0.f) : fminf(dmx, 0.f);
+        const float b = pos ? fminf(dpx, 0.f) : fmaxf(dpx, 0.f);
+        const float cc = pos ? fmaxf(dmy, 0.f) : fminf(dmy, 0.f);
+        const float d = pos ? fminf(dpy, 0.f) : fmaxf(dpy, 0.f);
+        out -= F * sqrt_approx(a * a + b * b + cc * cc + d * d);
+    }
+    if (lam != 0.f) {
+        const float xm = t[cy][cx - 1], xp = t[cy][cx + 1], ym = t[cy - 1][cx], yp = t[cy + 1][cx];
+        const float px = 0.5f * (xp - xm), py = 0.5f * (yp - ym);
+        const float pxx = xp + xm - 2.f * c, pyy = yp + ym - 2.f * c;
+        const float pxy = 0.25f * ((t[cy + 1][cx + 1] - t[cy + 1][cx - 1]) - (t[cy - 1][cx + 1] - t[cy - 1][cx - 1]));
+        const float den = px * px + py * py;
+        float kc = 0.f;
+        if (den >= 1e-12f) kc = __fdividef(pxx * py * py - 2.f * px * py * pxy + pyy * px * px, den);
+        out += dt * lam * (m ? m[p] : 1.f) * kc;
+    }
+    phi_out[p] = out;
+    if (mask_out) mask_out[p] = out <= 0.f ? 1 : 0;
+    if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(out <= 0.f ? 1.f : 0.f);
+}
+
 __global__ void k_mask_from_phi(const float* __restrict__ phi, size_t npix, unsigned char* __restrict__ M) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride)
@@ -162,7 +250,15 @@ int grid_for(size_t npix) {
 
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
-                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s) {
+                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s, int upwind) {
+    if (upwind == DEVEL_UPWIND_WENO5) {
+        prof_begin(PK_STEP, s);
+        k_levelset_step_weno<<<dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY), dim3(kWX, kWY), 0, s>>>(
+            phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf, ldb);
+        prof_end(PK_STEP, s);
+        DEVEL_LAUNCH_CHECK("k_levelset_step_weno");
+        return DEVEL_OK;
+    }
     dim3 grid((n + 256 * kPX - 1) / (256 * kPX), (n + kRows - 1) / kRows);
     prof_begin(PK_STEP, s);
     k_levelset_step<<<grid, 256, 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,

@@ -57,3 +57,19 @@ def test_swapped_upwind_is_caught(monkeypatch):
     orig = levelset.upwind_gradients
     monkeypatch.setattr(levelset, "upwind_gradients", lambda phi: orig(phi)[::-1])
     _fails(tl.test_upwind_kink_follows_hopf_lax_solution)
+
+
+def test_wrong_weno_weights_are_caught(monkeypatch):
+    def swapped(v1, v2, v3, v4, v5):  # the ideal weights 0.1 and 0.3 exchanged
+        p1 = v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0
+        p2 = -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0
+        p3 = v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0
+        s1 = 13.0 / 12.0 * (v1 - 2 * v2 + v3) ** 2 + 0.25 * (v1 - 4 * v2 + 3 * v3) ** 2
+        s2 = 13.0 / 12.0 * (v2 - 2 * v3 + v4) ** 2 + 0.25 * (v2 - v4) ** 2
+        s3 = 13.0 / 12.0 * (v3 - 2 * v4 + v5) ** 2 + 0.25 * (3 * v3 - 4 * v4 + v5) ** 2
+        eps = 1e-6 * np.maximum.reduce([v1 * v1, v2 * v2, v3 * v3, v4 * v4, v5 * v5]) + 1e-99
+        a1, a2, a3 = 0.3 / (s1 + eps) ** 2, 0.6 / (s2 + eps) ** 2, 0.1 / (s3 + eps) ** 2
+        return (a1 * p1 + a2 * p2 + a3 * p3) / (a1 + a2 + a3)
+    monkeypatch.setattr(levelset, "weno5_combine", swapped)
+    import test_oracle_weno as tw
+    _fails(tw.test_weno_fifth_order_convergence)
