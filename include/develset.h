@@ -281,6 +281,11 @@ typedef struct {
                                       by iteration i; entry iters is the final mask's    */
     long long* l2_hist;            /* device long long[iters+1] or NULL                  */
     long long* pvb_hist;           /* device long long[iters+1] or NULL                  */
+    const devel_optics* optics_defocus; /* NULL: dose-only process corners (I_c = d_c^2 I). Else
+                                      the defocused optical system of the inner corner (Sec. II-C:
+                                      inner = defocus at dose_in, outer = nominal focus at dose_out):
+                                      same n, window and precision as `optics`, a handle of its own
+                                      (its workspace is used; no other clip of the call may use it) */
 } devel_clip;
 
 /*

@@ -7,7 +7,10 @@
       L_pvb = sum (Z_in - Z_t)^2 + sum (Z_out - Z_t)^2   (summed over pixels).
 * Process corners: a dose change d scales the mask amplitude, so the corner
   image is d^2 I; inner corner d_in = 0.98, outer d_out = 1.02 (Sec. II-C
-  uses +/-2% dose; its defocus half is not modelled here).
+  uses +/-2% dose). With a defocused optical system given (Sec. II-C: the
+  inner corner is defocus at -2% dose, the outer nominal focus at +2% dose),
+  the inner corner images through it: Z_in = Z(d_in^2 I_def), and
+  dL/dI splits into R (for I: nominal and outer terms) and R_def (for I_def).
 * R = dL_DSO/dI = sum_c coef_c 2 (Z_c - Z_t) sigma_z Z_c (1 - Z_c) d_c^2,
   the chain factor of Eqs. (ilt_gradient), (pvb_gradient).
 * Squared L2 error (Sec. II-C.1): #{ [I >= I_th] != Z_t } (pixels = nm^2 at 1 nm/px).
@@ -37,6 +40,7 @@ class ResistResult:
     R: np.ndarray      # dL/dI
     l2: int
     pvb: int
+    R_def: np.ndarray | None = None  # dL/dI_def when a defocused system images the inner corner
 
 
 def sigmoid_resist(I: np.ndarray, sigma_z: float, I_th: float) -> np.ndarray:
@@ -47,22 +51,27 @@ def threshold_resist(I: np.ndarray, I_th: float) -> np.ndarray:
     return (I >= I_th).astype(np.uint8)
 
 
-def resist(I: np.ndarray, Zt: np.ndarray, p: ResistParams) -> ResistResult:
+def resist(I: np.ndarray, Zt: np.ndarray, p: ResistParams, I_def: np.ndarray | None = None) -> ResistResult:
+    """Loss, dL/dI and metrics. With I_def (the defocused system's image) the
+    inner corner images through it, and the result carries R_def = dL/dI_def."""
     I = np.asarray(I, dtype=np.float64)
+    Id = I if I_def is None else np.asarray(I_def, dtype=np.float64)
     Zt = np.asarray(Zt, dtype=np.float64)
-    conds = ((1.0, p.alpha), (p.dose_in, p.beta), (p.dose_out, p.beta))
-    R = np.zeros_like(I)
+    conds = ((1.0, p.alpha, I, 0), (p.dose_in, p.beta, Id, 1), (p.dose_out, p.beta, I, 0))
+    R = [np.zeros_like(I), np.zeros_like(I)]
     terms = []
     loss = 0.0
-    for d, coef in conds:
-        Z = sigmoid_resist(d * d * I, p.sigma_z, p.I_th)
+    for d, coef, img, which in conds:
+        Z = sigmoid_resist(d * d * img, p.sigma_z, p.I_th)
         e = Z - Zt
         s = float(np.sum(e * e))
         terms.append(s)
         loss += coef * s
-        R += coef * 2.0 * e * p.sigma_z * Z * (1.0 - Z) * d * d
+        R[which] += coef * 2.0 * e * p.sigma_z * Z * (1.0 - Z) * d * d
     l2 = int(np.count_nonzero(threshold_resist(I, p.I_th) != Zt.astype(np.uint8)))
-    zin = threshold_resist(p.dose_in ** 2 * I, p.I_th)
+    zin = threshold_resist(p.dose_in ** 2 * Id, p.I_th)
     zout = threshold_resist(p.dose_out ** 2 * I, p.I_th)
     pvb = int(np.count_nonzero(zin != zout))
-    return ResistResult(loss=loss, loss_terms=tuple(terms), R=R, l2=l2, pvb=pvb)
+    if I_def is None:
+        return ResistResult(loss=loss, loss_terms=tuple(terms), R=R[0] + R[1], l2=l2, pvb=pvb)
+    return ResistResult(loss=loss, loss_terms=tuple(terms), R=R[0], l2=l2, pvb=pvb, R_def=R[1])

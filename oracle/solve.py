@@ -44,12 +44,18 @@ class SolveResult:
     pvb: list
 
 
-def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None):
-    """One DSO iteration at global index i. Returns (phi_next, ResistResult)."""
+def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None, defocus=None):
+    """One DSO iteration at global index i. Returns (phi_next, ResistResult).
+    defocus = (H_def, w_def): the inner process corner images through that system."""
     M = levelset.mask_from_phi(phi)
     I = litho.aerial(M, H, w)
-    res = _resist.resist(I, Zt, p.resist)
-    V = litho.aerial_gradient(M, res.R, H, w)
+    if defocus is None:
+        res = _resist.resist(I, Zt, p.resist)
+        V = litho.aerial_gradient(M, res.R, H, w)
+    else:
+        Hd, wd = defocus
+        res = _resist.resist(I, Zt, p.resist, litho.aerial(M, Hd, wd))
+        V = litho.aerial_gradient(M, res.R, H, w) + litho.aerial_gradient(M, res.R_def, Hd, wd)
     vmax = float(np.abs(V).max())
     phi, M = levelset.step(phi, V, vmax, m, p.dt, p.lam, weno=p.weno)
     if p.reinit_every > 0 and (i + 1) % p.reinit_every == 0:
@@ -57,17 +63,18 @@ def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None):
     return phi, res
 
 
-def ilt_solve(Zt, H, w, p: SolveParams, phi0=None, m=None) -> SolveResult:
+def ilt_solve(Zt, H, w, p: SolveParams, phi0=None, m=None, defocus=None) -> SolveResult:
     Zt = (np.asarray(Zt) != 0).astype(np.uint8)
     phi = sdf.tsdf(Zt, p.d_lo, p.d_hi) if phi0 is None else np.asarray(phi0, dtype=np.float64).copy()
     loss, l2, pvb = [], [], []
     for t in range(p.iters):
-        phi, res = iterate(phi, Zt, H, w, p, p.start_iter + t, m)
+        phi, res = iterate(phi, Zt, H, w, p, p.start_iter + t, m, defocus)
         loss.append(res.loss)
         l2.append(res.l2)
         pvb.append(res.pvb)
     M = levelset.mask_from_phi(phi)
-    res = _resist.resist(litho.aerial(M, H, w), Zt, p.resist)
+    Idef = None if defocus is None else litho.aerial(M, defocus[0], defocus[1])
+    res = _resist.resist(litho.aerial(M, H, w), Zt, p.resist, Idef)
     loss.append(res.loss)
     l2.append(res.l2)
     pvb.append(res.pvb)

@@ -60,7 +60,8 @@ class devel_ilt_params(ctypes.Structure):
 
 class devel_clip(ctypes.Structure):
     _fields_ = [("optics", _P), ("target", _P), ("phi", _P), ("phi_given", _I), ("m", _P),
-                ("mask_out", _P), ("loss_hist", _P), ("l2_hist", _P), ("pvb_hist", _P)]
+                ("mask_out", _P), ("loss_hist", _P), ("l2_hist", _P), ("pvb_hist", _P),
+                ("optics_defocus", _P)]
 
 
 def _sig(name, argtypes, restype=_I):
@@ -283,6 +284,7 @@ class Clip:
     loss_hist: object = None  # float64 [iters+1] or None
     l2_hist: object = None   # int64 [iters+1] or None
     pvb_hist: object = None  # int64 [iters+1] or None
+    optics_defocus: Optics = None  # defocused system of the inner process corner, or None
 
 
 def devel_ilt_solve(params: devel_ilt_params, clips, status, stream=None):
@@ -296,7 +298,8 @@ def devel_ilt_solve(params: devel_ilt_params, clips, status, stream=None):
                             _ptr(c.m, torch.float32, N, "m"), _ptr(c.mask_out, torch.uint8, N, "mask_out"),
                             _ptr(c.loss_hist, torch.float64, H, "loss_hist"),
                             _ptr(c.l2_hist, torch.int64, H, "l2_hist"),
-                            _ptr(c.pvb_hist, torch.int64, H, "pvb_hist"))
+                            _ptr(c.pvb_hist, torch.int64, H, "pvb_hist"),
+                            c.optics_defocus.handle if c.optics_defocus is not None else None)
     _check(_lib.devel_ilt_solve(ctypes.byref(params), len(clips), arr, _ptr(status, torch.int32, 1, "status"),
                                 _stream(stream)))
 

@@ -85,8 +85,9 @@ int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, c
 }
 
 // adjoint from ws.mhat (spectrum of the imaged mask) and the spectrum rhat of R
-static int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s) {
-    int rc = launch_shat(o, s);
+static int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s,
+                             const devel_optics* od = nullptr) {
+    int rc = launch_shat(o, s, od);
     if (rc) return rc;
     EpiArgs ep;
     ep.C = V;
@@ -160,6 +161,7 @@ using namespace devel;
 // exclusively by this sequence of launches).
 static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* status, cudaStream_t s) {
     const devel_optics* o = cl.optics;
+    const devel_optics* od = cl.optics_defocus;
     const int n = o->n;
     const Workspace& w = o->ws;
     float* phi = cl.phi;
@@ -180,13 +182,36 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
         // image the current mask, resist loss and dL/dI (in place in bufI)
         rc = tcp ? launch_spectrum_mask_resident(o, o->W, w.mhat, s) : launch_spectrum_u8(o, w.M, o->W, w.mhat, s);
         if (rc) return rc;
-        rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr,
-                                    cl.loss_hist ? cl.loss_hist + t : nullptr,
-                                    cl.l2_hist ? cl.l2_hist + t : nullptr,
-                                    cl.pvb_hist ? cl.pvb_hist + t : nullptr, status, s);
+        double* lh = cl.loss_hist ? cl.loss_hist + t : nullptr;
+        long long* l2h = cl.l2_hist ? cl.l2_hist + t : nullptr;
+        long long* pvbh = cl.pvb_hist ? cl.pvb_hist + t : nullptr;
+        if (od) {
+            // defocused inner corner: both systems image the same mask (same spectrum)
+            DEVEL_CUDA_TRY(cudaMemcpyAsync(od->ws.mhat, w.mhat, sizeof(float2) * o->k * o->k,
+                                           cudaMemcpyDeviceToDevice, s));
+            rc = forward_from_mhat(o, w.bufI, s);
+            if (!rc) rc = forward_from_mhat(od, od->ws.bufI, s);
+            if (!rc)
+                rc = launch_resist_defocus(n, w.bufI, od->ws.bufI, cl.target, p->resist, tcp ? nullptr : w.bufI,
+                                           tcp ? nullptr : od->ws.bufI, tcp ? o->Xhi : nullptr,
+                                           tcp ? o->Xlo : nullptr, tcp ? od->Xhi : nullptr,
+                                           tcp ? od->Xlo : nullptr, o->ldn, w.dpart, w.lpart, o->npart_red,
+                                           nullptr, nullptr, lh, l2h, pvbh, status, w.counters, s);
+        } else {
+            rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr, lh, l2h, pvbh, status, s);
+        }
         if (rc) return rc;
         if (t == p->iters) break;  // the final mask is imaged for its metrics only
-        rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
+        if (od) {
+            rc = tcp ? launch_spectrum_resident(o, o->W2, w.rhat, s)
+                     : launch_spectrum_f32(o, w.bufI, o->W2, w.rhat, s);
+            if (!rc)
+                rc = tcp ? launch_spectrum_resident(od, od->W2, od->ws.rhat, s)
+                         : launch_spectrum_f32(od, od->ws.bufI, od->W2, od->ws.rhat, s);
+            if (!rc) rc = adjoint_from_rhat(o, w.bufV, w.vmax, status, s, od);
+        } else {
+            rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
+        }
         if (rc) return rc;
         rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
                                   tcp ? o->Xhi : nullptr, o->ldn, s, p->upwind);
@@ -384,7 +409,7 @@ static void drop_graphs_of(const devel_optics* o) {
         for (size_t off = head; off + sizeof(devel_clip) <= k.size(); off += sizeof(devel_clip)) {
             devel_clip c;
             std::memcpy(&c, k.data() + off, sizeof(devel_clip));
-            if (c.optics == o) uses = true;
+            if (c.optics == o || c.optics_defocus == o) uses = true;
         }
         if (uses) {
             cudaGraphExecDestroy(g_graphs[i].exec);
@@ -830,6 +855,19 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
         CHECK_OPT_PTR(cl.loss_hist, "clip.loss_hist");
         CHECK_OPT_PTR(cl.l2_hist, "clip.l2_hist");
         CHECK_OPT_PTR(cl.pvb_hist, "clip.pvb_hist");
+        if (const devel_optics* od = cl.optics_defocus) {
+            if (od == cl.optics || od->n != cl.optics->n || od->k != cl.optics->k ||
+                od->precision != cl.optics->precision)
+                return set_error(DEVEL_EINVAL,
+                                 "devel_ilt_solve: clip %d: the defocus optics must be a separate handle with the "
+                                 "same n, window and precision",
+                                 c);
+            for (int d = 0; d < nclips; ++d) {  // its workspace belongs to this clip's chain alone
+                if (clips[d].optics == od ||
+                    (clips[d].optics_defocus == od && clips[d].optics != cl.optics))
+                    return set_error(DEVEL_EINVAL, "devel_ilt_solve: clip %d: defocus handle shared", c);
+            }
+        }
     }
     if (p->use_graph) return solve_graph(p, nclips, clips, status, s);
     int dev = 0;

@@ -203,7 +203,8 @@ int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out
 // Ihat (on W2) from mhat with the rank-K TCC
 int launch_ihat(const devel_optics* o, cudaStream_t s);
 // Shat (on W) from mhat and rhat with the rank-K TCC
-int launch_shat(const devel_optics* o, cudaStream_t s);
+// od: a second (defocused) system whose term is added (its TCC and rhat)
+int launch_shat(const devel_optics* o, cudaStream_t s, const devel_optics* od = nullptr);
 // out = mult * Re sum_{a,b} Z[a][b] e^{+2 pi i ((a-r)y + (b-r)x)/n} on window w; optional max|out|
 // epi: EPI_STORE (ep.C = out) or EPI_VEL (ep.C, max |out| partials);
 // *nparts = number of CTA partials.
@@ -223,6 +224,13 @@ int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_re
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
                   long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s);
 int resist_parts(int n);
+// Defocused inner corner: images In (nominal focus) and Id (defocused); dL/dIn and dL/dId as
+// FP32 images (Rn, Rd; may alias In, Id) or bf16 hi/lo operands (Rnhi.. with pitch ldr).
+int launch_resist_defocus(int n, const float* In, const float* Id, const unsigned char* Zt,
+                          const devel_resist_params& p, float* Rn, float* Rd, __nv_bfloat16* Rnhi,
+                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, double* dpart,
+                          long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
+                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s);
 
 // levelset.cu
 // mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction

@@ -286,11 +286,13 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
     }
 }
 
-// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f.
+// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f;
+// with a second system (TCC2, rhat2: the defocused corner) its term is added.
 __global__ void __launch_bounds__(128)
 k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
            const float2* __restrict__ rhat, int k, float2* __restrict__ Shat, __nv_bfloat16* __restrict__ zhi,
-           __nv_bfloat16* __restrict__ zlo, int ldz) {
+           __nv_bfloat16* __restrict__ zlo, int ldz, const float2* __restrict__ TCC2,
+           const float2* __restrict__ rhat2) {
     __shared__ float2 sh[4];
     const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
     const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
@@ -299,8 +301,11 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
 #pragma unroll 4
     for (int a = threadIdx.x; a < kk; a += 128) {
         const int a1 = a / k, a2 = a - a1 * k;
-        const float2 u = cmul(__ldg(mhat + a), __ldg(rhat + (f1 - a1 + r2) * k2 + (f2 - a2 + r2)));
-        acc = cadd(acc, cmulc(u, __ldg(row + a)));
+        const int g = (f1 - a1 + r2) * k2 + (f2 - a2 + r2);
+        const float2 ma = __ldg(mhat + a);
+        acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat + g)), __ldg(row + a)));
+        if (TCC2)  // the defocused system's term (its TCC, its dL/dI spectrum, the same mask)
+            acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat2 + g)), __ldg(TCC2 + (size_t)f * kk + a)));
     }
     const float2 s = block_sum2_128(acc, sh);
     if (threadIdx.x == 0) {
@@ -485,11 +490,12 @@ int launch_ihat(const devel_optics* o, cudaStream_t s) {
     return DEVEL_OK;
 }
 
-int launch_shat(const devel_optics* o, cudaStream_t s) {
+int launch_shat(const devel_optics* o, cudaStream_t s, const devel_optics* od) {
     prof_begin(PK_ADJ_WINDOW, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
     k_shat_tcc<<<o->k * o->k, 128, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat,
-                                            tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk);
+                                            tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk,
+                                            od ? od->TCC : nullptr, od ? od->ws.rhat : nullptr);
     prof_end(PK_ADJ_WINDOW, s);
     DEVEL_LAUNCH_CHECK("k_shat_tcc");
     return DEVEL_OK;

@@ -181,6 +181,48 @@ k_resist(const float* __restrict__ I, const unsigned char* __restrict__ Zt, int 
     if (threadIdx.x == 0) *out.counter = 0u;
 }
 
+// Two images (nominal focus In, defocused Id): one pixel per thread per pass, dL/dIn
+// and dL/dId written as FP32 images (Rn, Rd; may alias In, Id) or as bf16 hi/lo
+// operands (row pitch ldr); the same partial sums and last-block total as k_resist.
+__global__ void __launch_bounds__(kThreads)
+k_resist_defocus(const float* In, const float* Id, const unsigned char* __restrict__ Zt, int n, ResistArgs p,
+                 float* Rn, float* Rd, __nv_bfloat16* __restrict__ Rnhi, __nv_bfloat16* __restrict__ Rnlo,
+                 __nv_bfloat16* __restrict__ Rdhi, __nv_bfloat16* __restrict__ Rdlo, int ldr,
+                 double* __restrict__ dpart, long long* __restrict__ lpart, ResistOut out) {
+    __shared__ float sf[3][32];
+    __shared__ int si[2][32];
+    LossAcc acc;
+    const size_t npix = (size_t)n * n, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
+        float gD;
+        const float gN = resist_px2(In[i], Id[i], Zt[i] != 0, p, acc, gD);
+        if (Rn) {
+            Rn[i] = gN;
+            Rd[i] = gD;
+        }
+        if (Rnhi) {
+            const size_t y = i / (size_t)n, x = i - y * (size_t)n, q = y * ldr + x;
+            const __nv_bfloat16 hn = __float2bfloat16_rn(gN), hd = __float2bfloat16_rn(gD);
+            Rnhi[q] = hn;
+            Rnlo[q] = __float2bfloat16_rn(gN - __bfloat162float(hn));
+            Rdhi[q] = hd;
+            Rdlo[q] = __float2bfloat16_rn(gD - __bfloat162float(hd));
+        }
+    }
+    block_store_loss(acc, blockIdx.x, dpart, lpart, sf, si);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(out.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    resist_final_block(dpart, lpart, gridDim.x, out.alpha, out.beta, out.loss4, out.cnt2, out.loss_hist,
+                       out.l2_hist, out.pvb_hist, out.status);
+    if (threadIdx.x == 0) *out.counter = 0u;
+}
+
 }  // namespace
 
 int resist_parts(int n) { return n < kMaxParts ? n : kMaxParts; }  // <= 512 partials
@@ -194,6 +236,20 @@ int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_re
     k_resist<<<nparts, kThreads, 0, s>>>(I, Zt, n, make_resist_args(p), R, Rhi, Rlo, ldr, dpart, lpart, out);
     prof_end(PK_RESIST, s);
     DEVEL_LAUNCH_CHECK("k_resist");
+    return DEVEL_OK;
+}
+
+int launch_resist_defocus(int n, const float* In, const float* Id, const unsigned char* Zt,
+                          const devel_resist_params& p, float* Rn, float* Rd, __nv_bfloat16* Rnhi,
+                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, double* dpart,
+                          long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
+                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s) {
+    ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
+    prof_begin(PK_RESIST, s);
+    k_resist_defocus<<<nparts, kThreads, 0, s>>>(In, Id, Zt, n, make_resist_args(p), Rn, Rd, Rnhi, Rnlo, Rdhi, Rdlo,
+                                                 ldr, dpart, lpart, out);
+    prof_end(PK_RESIST, s);
+    DEVEL_LAUNCH_CHECK("k_resist_defocus");
     return DEVEL_OK;
 }
 

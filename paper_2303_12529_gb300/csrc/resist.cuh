@@ -73,6 +73,25 @@ __device__ __forceinline__ float resist_px(float I, bool zt_on, const ResistArgs
     return fmaf(p.k_out * eo, co.ez2, g);
 }
 
+// Defocused process corner (Sec. II-C): the inner corner images through the defocused
+// system (In: nominal-focus image, Id: defocused image). Returns dL/dIn (nominal and
+// outer terms) and sets gD = dL/dId (inner term).
+__device__ __forceinline__ float resist_px2(float In, float Id, bool zt_on, const ResistArgs& p, LossAcc& a,
+                                            float& gD) {
+    const float zt = zt_on ? 1.f : 0.f;
+    const Corner cn = resist_corner(In, p.a_nom, p.b);
+    const Corner ci = resist_corner(Id, p.a_in, p.b);
+    const Corner co = resist_corner(In, p.a_out, p.b);
+    const float en = cn.z - zt, ei = ci.z - zt, eo = co.z - zt;
+    a.s0 = fmaf(en, en, a.s0);
+    a.s1 = fmaf(ei, ei, a.s1);
+    a.s2 = fmaf(eo, eo, a.s2);
+    a.l2 += ((In >= p.I_th) != zt_on);
+    a.pvb += ((p.d2in * Id >= p.I_th) != (p.d2out * In >= p.I_th));
+    gD = (p.k_in * ei) * ci.ez2;
+    return fmaf(p.k_out * eo, co.ez2, (p.k_nom * en) * cn.ez2);
+}
+
 // Block reduction of the accumulators in a fixed order (FP32 / int within the block;
 // the partials are summed in FP64 / int64 across blocks); thread 0 writes the block's
 // partial to

@@ -204,7 +204,7 @@ def window_radius_for(n: int, r_ref: int = 17, n_ref: int = 2048) -> int:
     return int(math.ceil(r_ref * n / n_ref))
 
 
-def _tcc(k: int, f_cut: float, sigma_in: float, sigma_out: float, sub: int):
+def _tcc(k: int, f_cut: float, sigma_in: float, sigma_out: float, sub: int, defocus: float = 0.0):
     r = (k - 1) // 2
     step = 1.0 / sub
     smax = sigma_out * f_cut
@@ -216,14 +216,19 @@ def _tcc(k: int, f_cut: float, sigma_in: float, sigma_out: float, sub: int):
     J = np.full(sy.shape, 1.0 / sy.size)
     fu, fv = np.meshgrid(np.arange(-r, r + 1), np.arange(-r, r + 1), indexing="ij")
     fu, fv = fu.ravel().astype(np.float64), fv.ravel().astype(np.float64)
-    # P[s, f] = pupil(f + s): circular, cutoff f_cut, inclusive, no aberration
-    P = (np.hypot(fu[None, :] + sy[:, None], fv[None, :] + sx[:, None]) <= f_cut + 1e-12).astype(np.float64)
-    tcc = P.T @ (J[:, None] * P)
-    return tcc
+    # P[s, f] = pupil(f + s): circular, cutoff f_cut, inclusive; optional defocus phase
+    # exp(2 pi i W rho^2), rho = |f + s| / f_cut, W in waves at the pupil edge
+    rho = np.hypot(fu[None, :] + sy[:, None], fv[None, :] + sx[:, None])
+    P = (rho <= f_cut + 1e-12).astype(np.complex128)
+    if defocus != 0.0:
+        P = P * np.exp(2j * np.pi * defocus * (rho / f_cut) ** 2)
+    # TCC(f1, f2) = sum_s J(s) P(f1 + s) conj(P(f2 + s)), Hermitian PSD
+    tcc = P.T @ (J[:, None] * np.conj(P))
+    return tcc if defocus != 0.0 else tcc.real
 
 
 def optics(n: int, K: int, k: int, sigma_in: float = 0.6, sigma_out: float = 0.9,
-           sub: int = 4, phase_seed: int | None = 12345) -> Optics:
+           sub: int = 4, phase_seed: int | None = 12345, defocus: float = 0.0) -> Optics:
     """SOCS kernels of a synthetic annular-source Hopkins system.
 
     The pupil is the disc |f| <= f_cut with f_cut = r / (1 + sigma_out), so
@@ -233,12 +238,14 @@ def optics(n: int, K: int, k: int, sigma_in: float = 0.6, sigma_out: float = 0.9
     to TCC(0, 0) = 1. Kernels are the top-K eigenvectors (unit norm) times a
     seeded random unit phase each: eigenvector phase is arbitrary, and a
     non-trivial phase keeps the complex arithmetic of every consumer honest.
+    ``defocus`` (waves at the pupil edge) adds the phase exp(2 pi i W rho^2) to
+    the pupil: the optical system of a defocused process corner.
     """
     if k % 2 != 1:
         raise ValueError("window side k must be odd")
     r = (k - 1) // 2
     f_cut = r / (1.0 + sigma_out)
-    tcc = _tcc(k, f_cut, sigma_in, sigma_out, sub)
+    tcc = _tcc(k, f_cut, sigma_in, sigma_out, sub, defocus)
     evals, evecs = np.linalg.eigh(tcc)
     order = np.argsort(evals)[::-1][:K]
     w = np.clip(evals[order], 0.0, None)
