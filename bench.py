@@ -72,7 +72,7 @@ def window_flops_per_iter(n, K, k):
 # side k and k2 = 2k - 1, padded contraction lengths ldk / ldk2, bf16 hi/lo operands on
 # the tensor-core path). Every kernel of the loop is bounded by HBM (or by latency)
 # rather than by the tensor pipe: the contractions are only 2 ldk deep.
-def kernel_bytes(name, n, K, k, tc):
+def kernel_bytes(name, n, K, k, tc, defocus=False):
     px = n * n
     k2 = 2 * k - 1
     ldk, ldk2 = -(-2 * k // 16) * 16, -(-2 * k2 // 16) * 16
@@ -81,7 +81,9 @@ def kernel_bytes(name, n, K, k, tc):
     if name == "levelset_step":
         return (15 if tc else 13) * px            # phi, V in; phi, mask (+ bf16 mask) out
     if name == "resist":
-        return 9 * px                             # I, Z_t in; dL/dI (fp32, or bf16 hi + lo) out
+        # I, Z_t in; dL/dI (fp32, or bf16 hi + lo) out; with the defocused corner also
+        # I_def in and dL/dI_def out
+        return (17 if defocus else 9) * px
     if name == "edt_cols":
         return 5 * px                             # mask in, packed column distances out
     if name == "edt_rows":
@@ -91,9 +93,11 @@ def kernel_bytes(name, n, K, k, tc):
         ops = lambda l: 2 * n * l * (4 if tc else 4)
         return 4 * px + (ops(ldk2) + ops(ldk)) / 2
     if name in ("tc_spectrum", "spectrum_gemm"):
-        # image operand (mask: bf16 hi only; dL/dI: hi + lo) + partial spectra out
-        img = (2 * ldn * n + 4 * ldn * n) / 2 if tc else (1 * px + 4 * px) / 2
-        return img + slices * (ldk * ldk + ldk2 * ldk2) / 2 * 4
+        # image operand (mask: bf16 hi only; dL/dI: hi + lo) + partial spectra out; per
+        # iteration one mask launch and one dL/dI launch per optical system
+        nr = 2 if defocus else 1
+        img = (2 * ldn * n + nr * 4 * ldn * n) / (1 + nr) if tc else (1 * px + nr * 4 * px) / (1 + nr)
+        return img + slices * (ldk * ldk + nr * ldk2 * ldk2) / (1 + nr) * 4
     if name == "expand_T":
         return n * (ldk + ldk2) / 2 * (4 if tc else 4)
     if name == "spectrum_reduce":
@@ -101,7 +105,7 @@ def kernel_bytes(name, n, K, k, tc):
     if name == "ihat_tcc":
         return k ** 4 / 2 * 8
     if name == "shat_tcc":
-        return k ** 4 * 8
+        return k ** 4 * 8 * (2 if defocus else 1)
     return None
 
 
@@ -186,13 +190,14 @@ def simt_fp32_peak_tflops(sm_mhz):
 # --------------------------------------------------------------------------
 # the reference arm: the FP64 CPU oracle on a bounded sample
 # --------------------------------------------------------------------------
-def oracle_sample(wl, budget_s=30.0):
+def oracle_sample(wl, weno=False, defocus=0.0):
     """Time the oracle on a bounded sample of one clip's solve and scale it to
     clips/s: one full-size DSO iteration (image, loss, gradient, step) plus a
     re-initialisation measured on a row sample and amortised over 5 iterations."""
     from oracle import levelset, litho, resist, sdf
     n, K, k, iters, beta = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"]
     o = synth.optics(n, K, k)
+    od = synth.optics(n, K, k, defocus=defocus) if defocus else None
     Zt = synth.manhattan_clip(wl["seed"]) if n == 2048 else synth.rect_clip(wl["seed"], n=n)
     t0 = time.perf_counter()
     rows = np.arange(0, n, max(1, n // 64))
@@ -202,9 +207,12 @@ def oracle_sample(wl, budget_s=30.0):
     t0 = time.perf_counter()
     M = levelset.mask_from_phi(phi)
     I = litho.aerial(M, o.H, o.w)
-    res = resist.resist(I, Zt, resist.ResistParams(beta=beta))
+    Idef = litho.aerial(M, od.H, od.w) if od else None
+    res = resist.resist(I, Zt, resist.ResistParams(beta=beta), Idef)
     V = litho.aerial_gradient(M, res.R, o.H, o.w)
-    levelset.step(phi, V, float(np.abs(V).max()), None, 0.5, 0.1)
+    if od:
+        V = V + litho.aerial_gradient(M, res.R_def, od.H, od.w)
+    levelset.step(phi, V, float(np.abs(V).max()), None, 0.5, 0.1, weno=weno)
     t_iter = time.perf_counter() - t0
     per_clip = iters * t_iter + (iters / 5 + 1) * t_reinit + t_iter * 0.1
     sample = (f"one {n}^2 DSO iteration (K={K}, k={k}) timed in full ({t_iter:.1f} s) plus a TSDF on "
@@ -223,7 +231,7 @@ def run_reference(args, wl):
     vals = []
     sample = ""
     for _ in range(max(1, args.steps)):
-        v, per_clip, sample = oracle_sample(wl)
+        v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus)
         vals.append(v)
         if time.perf_counter() - t0 > 150:
             break
@@ -263,19 +271,24 @@ def run_ours(args, wl):
     Zt = synth.manhattan_clip(seed) if n == 2048 else synth.rect_clip(seed, n=n)
     target = torch.from_numpy(Zt.ravel().copy()).to(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
+    upwind = dv.DEVEL_UPWIND_WENO5 if args.upwind == "weno5" else dv.DEVEL_UPWIND_GODUNOV1
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5,
+                           upwind=upwind)
     precs = ["bf16x3", "fp32"] if args.precision == "both" else [args.precision]
+    od = synth.optics(n, K, k, defocus=args.defocus) if args.defocus else None
 
     def measure(prec_name):
         prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3}[prec_name]
         opt = dv.devel_optics_create(n, o.H, o.w, prec)
+        optd = dv.devel_optics_create(n, od.H, od.w, prec) if od else None
         phi = torch.empty(n * n, dtype=torch.float32, device=dev)
         M = torch.empty(n * n, dtype=torch.uint8, device=dev)
         L = torch.zeros(iters + 1, dtype=torch.float64, device=dev)
         l2 = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
         pvb = torch.zeros(iters + 1, dtype=torch.int64, device=dev)
         st = torch.zeros(1, dtype=torch.int32, device=dev)
-        clip = dv.Clip(opt, target, phi, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb)
+        clip = dv.Clip(opt, target, phi, mask_out=M, loss_hist=L, l2_hist=l2, pvb_hist=pvb,
+                       optics_defocus=optd)
 
         def step():
             dv.devel_ilt_solve(params, [clip], st, stream)
@@ -359,6 +372,8 @@ def run_ours(args, wl):
                "dom": dom, "dom_prof": dom_prof, "ms_profiled": ms_profiled, "e2e": e2e_value, "final_l2": int(l2[-1].item()),
                "final_pvb": int(pvb[-1].item()), "final_loss": float(L[-1].item())}
         dv.devel_optics_destroy(opt)
+        if optd:
+            dv.devel_optics_destroy(optd)
         return res
 
     results = [measure(p) for p in precs]
@@ -372,11 +387,13 @@ def run_ours(args, wl):
         hs, bclips = [], []
         for i in range(nb):
             h = dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
-            hs.append(h)
+            hd = dv.devel_optics_create(n, od.H, od.w, dv.DEVEL_PREC_BF16X3) if od else None
+            hs += [h] + ([hd] if hd else [])
             Zb = synth.manhattan_clip(seed + 10 * (i + 1)) if n == 2048 else synth.rect_clip(seed + 10 * (i + 1), n=n)
             bclips.append(dv.Clip(h, torch.from_numpy(Zb.ravel().copy()).to(dev),
                                   torch.empty(n * n, dtype=torch.float32, device=dev),
-                                  mask_out=torch.empty(n * n, dtype=torch.uint8, device=dev)))
+                                  mask_out=torch.empty(n * n, dtype=torch.uint8, device=dev),
+                                  optics_defocus=hd))
         bst = torch.zeros(1, dtype=torch.int32, device=dev)
         for _ in range(2):
             dv.devel_ilt_solve(params, bclips, bst, stream)
@@ -404,7 +421,7 @@ def run_ours(args, wl):
         for kn, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
             ent = {"launches": c, "ms": round(t, 3), "share": round(t / tot, 4),
                    "avg_us": round(t / c * 1000.0, 2)}
-            b = kernel_bytes(kn, n, K, k, tc)
+            b = kernel_bytes(kn, n, K, k, tc, bool(od))
             if b:
                 ent["gbs"] = round(b / (t / c / 1000.0) / 1e9, 1)
                 ent["frac_hbm"] = round(ent["gbs"] / hbm, 3)
@@ -412,10 +429,10 @@ def run_ours(args, wl):
         name = head["dom"]
         cnt, kms = head["dom_prof"]
         avg_s = kms / cnt / 1000.0
-        b = kernel_bytes(name, n, K, k, tc) or 0.0
+        b = kernel_bytes(name, n, K, k, tc, bool(od)) or 0.0
         ach = b / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "peak_source": src + " (burst copy)", "traffic": TRAFFIC.get((name, head["prec"])),
+                "peak_source": src + " (burst copy)", "traffic": None if od else TRAFFIC.get((name, head["prec"])),
                 "kernel": name, "bytes_per_launch": b, "launches_per_step": cnt / args.steps,
                 "avg_launch_us": avg_s * 1e6, "share": prof[name][1] / tot,
                 "timing": "CUDA events around this kernel's launches only, recorded inside the solve's graph, "
@@ -424,7 +441,7 @@ def run_ours(args, wl):
         if args.no_cpu_baseline:
             cpu = None
         else:
-            v, per_clip, sample = oracle_sample(wl)
+            v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus)
             cpu = {"value": v, "unit": "clips/s", "cores": 1, "kind": "oracle", "sample": sample}
         ms = head["ms"]
         out = {
@@ -435,7 +452,8 @@ def run_ours(args, wl):
             "config": {"workload": args.workload, "n": n, "K": K, "k": k, "iters": iters, "beta": beta,
                        "dt": 0.5, "lambda": 0.1, "reinit_every": 5, "clips_per_gpu_per_step": 1,
                        "precision": head["prec"], "init": "zero level set (TSDF of the target)",
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "upwind": args.upwind, "defocus_waves": args.defocus},
             "litho_tflops": {"window_method": window_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12,
                              "socs_equivalent": algorithmic_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12},
             "e2e": {"value": head["e2e"], "unit": "clips/s", "h2d_bytes_per_step": n * n,
@@ -490,25 +508,34 @@ def run_batched(args, wl):
     sides = [int(x) for x in rng.choice(wl["sides"], size=B)]
     seeds = [wl["seed"] + 1 + rank * B + i for i in range(B)]  # replicas: disjoint clips per rank
     optics_of = {}
-    clips, handles = [], []
+    clips, handles, defocus_handles = [], [], []
     t_tune = 0.0
     for n, sd in zip(sides, seeds):
         k = 2 * synth.window_radius_for(n) + 1
         if n not in optics_of:
-            optics_of[n] = synth.optics(n, K, k)
-        o = optics_of[n]
+            optics_of[n] = (synth.optics(n, K, k),
+                            synth.optics(n, K, k, defocus=args.defocus) if args.defocus else None)
+        o, od = optics_of[n]
         h = dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
         t0 = time.perf_counter()
         dv.devel_optics_autotune(h, stream)
         t_tune += time.perf_counter() - t0
         handles.append(h)
+        hd = None
+        if od:
+            hd = dv.devel_optics_create(n, od.H, od.w, dv.DEVEL_PREC_BF16X3)
+            dv.devel_optics_autotune(hd, stream)
+            defocus_handles.append(hd)
         Zt = synth.manhattan_clip(sd, n=n)
         clips.append(dv.Clip(h, torch.from_numpy(Zt.ravel().copy()).to(dev),
                              torch.empty(n * n, dtype=torch.float32, device=dev),
                              mask_out=torch.empty(n * n, dtype=torch.uint8, device=dev),
                              l2_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev),
-                             pvb_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev)))
-    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5)
+                             pvb_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev),
+                             optics_defocus=hd))
+    upwind = dv.DEVEL_UPWIND_WENO5 if args.upwind == "weno5" else dv.DEVEL_UPWIND_GODUNOV1
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5,
+                           upwind=upwind)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     steps = max(1, min(args.steps, 5))
@@ -585,7 +612,7 @@ def run_batched(args, wl):
             bsum = 0.0
             for n in sides:
                 k = 2 * synth.window_radius_for(n) + 1
-                bb = kernel_bytes(kn, n, K, k, True)
+                bb = kernel_bytes(kn, n, K, k, True, bool(args.defocus))
                 bsum = None if (bb is None or bsum is None) else bsum + bb * per_clip_launches[kn]
             if bsum:
                 ent["gbs"] = round(bsum / (t / 1000.0) / 1e9, 1)
@@ -609,7 +636,8 @@ def run_batched(args, wl):
                        "k_per_side": {n: 2 * synth.window_radius_for(n) + 1 for n in wl["sides"]},
                        "iters": iters, "beta": beta, "precision": "bf16x3",
                        "schedule": "one devel_ilt_solve per step, clips on parallel graph branches",
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "upwind": args.upwind, "defocus_waves": args.defocus},
             "megapixel_iterations_per_s": world * px * iters / (ms / 1000.0) / 1e6,
             "sequential": {"value": B * 1000.0 / ms_seq, "ms_per_step": ms_seq,
                            "schedule": "one devel_ilt_solve per clip"},
@@ -653,7 +681,7 @@ def run_calls_once(args, wl):
     dv.devel_litho_forward(opt, m, I)
     dv.devel_resist_loss(opt, I, tgt, dv.resist_params(beta=beta), R, L, C)
     dv.devel_litho_adjoint(opt, m, R, V, vm)
-    dv.devel_levelset_step(n, phi, V, vm, None, 0.5, 0.1, phi2, M)
+    dv.devel_levelset_step(n, phi, V, vm, None, 0.5, 0.1, phi2, M, weno5=args.upwind == "weno5")
     torch.cuda.synchronize()
     dv.devel_optics_check(opt)
     print(json.dumps({"calls_once": args.workload, "precision": args.precision, "loss": float(L[0]),
@@ -670,6 +698,11 @@ def main():
     ap.add_argument("--precision", choices=["both", "fp32", "bf16x3"], default="both",
                     help="both: the compensated-BF16 solve is the headline, the plain FP32 solve its comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--upwind", choices=["godunov1", "weno5"], default="godunov1",
+                    help="one-sided derivatives of the upwind |grad phi| (first order, or WENO5)")
+    ap.add_argument("--defocus", type=float, default=0.0,
+                    help="waves of defocus at the pupil edge for the inner process corner "
+                         "(0: dose-only corners)")
     ap.add_argument("--calls-once", action="store_true",
                     help="run each hot-path ABI call once at the workload size (for kernel captures)")
     args = ap.parse_args()

@@ -70,9 +70,14 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
                 __nv_bfloat16* __restrict__ mask_bf, int ldb) {
     const int y0 = blockIdx.y * kRows;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kPX;
+    __shared__ float s_inv;
+    if (threadIdx.x == 0) {  // 1 / max|V| once per block (the FP64 pipe is narrow)
+        const double vm = *vmax;
+        s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
+    }
+    __syncthreads();
     if (x0 >= n) return;
-    const double vm = *vmax;
-    const float inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
+    const float inv = s_inv;
     const bool vec = ((n & 3) == 0) && (x0 + kPX <= n);
     float rw[kRows + 2][kPX + 2];
 #pragma unroll
@@ -145,19 +150,27 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
 // (Hamilton-Jacobi WENO: three third-order ENO candidates on the one-sided
 // differences, ideal weights 0.1 / 0.6 / 0.3 modulated by the smoothness
 // indicators, eps = 1e-6 max v_k^2) in the Godunov flux. A block computes a
-// 32 x 8 tile from a shared-memory copy with a 3-pixel halo (borders replicated).
+// 32 x 16 tile (two rows per thread) from a shared-memory copy with a 3-pixel
+// halo (borders replicated).
 // ---------------------------------------------------------------------------
-constexpr int kWX = 32, kWY = 8, kWH = 3;
+constexpr int kWX = 32, kWY = 16, kWTh = 8, kWH = 3;
 constexpr int kWTX = kWX + 2 * kWH, kWTY = kWY + 2 * kWH;
 
 // WENO5 derivative from the one-sided differences v1..v5 (v3 nearest the node on the
-// upwind side). The weights are invariant under v -> v / s (the smoothness
-// indicators and eps scale as s^2), so they are computed on v / max|v|: no overflow
-// in FP32 where the differences are tiny, and 0 where they all vanish.
+// upwind side). The weights are invariant under v -> v / S (the smoothness
+// indicators and eps scale as S^2), so they are computed on u = v / S with S the
+// power of two at or below max|v| (an exact scaling; max|u| in [1, 2)): no overflow
+// or underflow in FP32 where the differences are huge or tiny, and 0 where they all
+// vanish. The normalised weights a_k / sum a_k with a_k = w_k / t_k^2 are formed as
+// b_k / sum b_k with b_k = w_k prod_{l != k} t_l^2 (one division instead of four);
+// with max|u| < 2 every t_k lies in [1e-6, 134], so the products stay in range.
 __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5) {
     const float s = fmaxf(fmaxf(fmaxf(fabsf(v1), fabsf(v2)), fmaxf(fabsf(v3), fabsf(v4))), fabsf(v5));
     if (!(s > 0.f)) return 0.f;
-    const float r = 1.f / s;
+    // S = 2^(E - 127) for the biased exponent E of s (E clamped to 253 so that 1/S is a
+    // normal float; an infinite s still yields a non-finite result)
+    const int eb = min(__float_as_int(s) & 0x7f800000, 253 << 23);
+    const float S = __int_as_float(eb), r = __int_as_float((254 << 23) - eb);
     const float u1 = v1 * r, u2 = v2 * r, u3 = v3 * r, u4 = v4 * r, u5 = v5 * r;
     const float p1 = u1 * (1.f / 3.f) - u2 * (7.f / 6.f) + u3 * (11.f / 6.f);
     const float p2 = -u2 * (1.f / 6.f) + u3 * (5.f / 6.f) + u4 * (1.f / 3.f);
@@ -165,35 +178,19 @@ __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, f
     const float a = u1 - 2.f * u2 + u3, b = u1 - 4.f * u2 + 3.f * u3;
     const float c = u2 - 2.f * u3 + u4, d = u2 - u4;
     const float e = u3 - 2.f * u4 + u5, f = 3.f * u3 - 4.f * u4 + u5;
-    const float eps = 1e-6f;  // 1e-6 max u_k^2 with max |u_k| = 1
+    const float sr = s * r;
+    const float eps = 1e-6f * sr * sr;
     const float t1 = (13.f / 12.f) * a * a + 0.25f * b * b + eps;
     const float t2 = (13.f / 12.f) * c * c + 0.25f * d * d + eps;
     const float t3 = (13.f / 12.f) * e * e + 0.25f * f * f + eps;
-    const float a1 = 0.1f / (t1 * t1), a2 = 0.6f / (t2 * t2), a3 = 0.3f / (t3 * t3);
-    return s * (a1 * p1 + a2 * p2 + a3 * p3) / (a1 + a2 + a3);
+    const float q12 = t1 * t2, q13 = t1 * t3, q23 = t2 * t3;
+    const float b1 = 0.1f * (q23 * q23), b2 = 0.6f * (q13 * q13), b3 = 0.3f * (q12 * q12);
+    return S * __fdividef(b1 * p1 + b2 * p2 + b3 * p3, b1 + b2 + b3);
 }
 
-__global__ void __launch_bounds__(kWX * kWY)
-k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
-                     const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
-                     int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
-                     __nv_bfloat16* __restrict__ mask_bf, int ldb) {
-    __shared__ float t[kWTY][kWTX + 1];
-    const int x0 = blockIdx.x * kWX, y0 = blockIdx.y * kWY;
-    for (int i = threadIdx.y * kWX + threadIdx.x; i < kWTX * kWTY; i += kWX * kWY) {
-        const int ty = i / kWTX, tx = i - ty * kWTX;
-        const int gy = min(max(y0 + ty - kWH, 0), n - 1), gx = min(max(x0 + tx - kWH, 0), n - 1);
-        t[ty][tx] = phi[(size_t)gy * n + gx];
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= n || y >= n) return;
-    const int cx = threadIdx.x + kWH, cy = threadIdx.y + kWH;
+__device__ __forceinline__ float weno_px(const float (*t)[kWTX + 1], int cy, int cx, float F, float dt,
+                                         float lam, float mm) {
     const float c = t[cy][cx];
-    const double vm = *vmax;
-    const float inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
-    const size_t p = (size_t)y * n + x;
-    const float F = -dt * (V[p] * inv);
     float out = c;
     if (F != 0.f) {
         float dx[6], dy[6];  // d(k) = phi(k) - phi(k - 1), k = -2 .. 3 relative to the node
@@ -221,11 +218,44 @@ k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
         const float den = px * px + py * py;
         float kc = 0.f;
         if (den >= 1e-12f) kc = __fdividef(pxx * py * py - 2.f * px * py * pxy + pyy * px * px, den);
-        out += dt * lam * (m ? m[p] : 1.f) * kc;
+        out += dt * lam * mm * kc;
     }
-    phi_out[p] = out;
-    if (mask_out) mask_out[p] = out <= 0.f ? 1 : 0;
-    if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(out <= 0.f ? 1.f : 0.f);
+    return out;
+}
+
+__global__ void __launch_bounds__(kWX * kWTh)
+k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
+                     const double* __restrict__ vmax, const float* __restrict__ m, float dt, float lam,
+                     int n, float* __restrict__ phi_out, unsigned char* __restrict__ mask_out,
+                     __nv_bfloat16* __restrict__ mask_bf, int ldb) {
+    __shared__ float t[kWTY][kWTX + 1];
+    __shared__ float s_inv;
+    const int x0 = blockIdx.x * kWX, y0 = blockIdx.y * kWY;
+    const int tid = threadIdx.y * kWX + threadIdx.x;
+    if (tid == 0) {  // 1 / max|V| once per block (FP64 operand)
+        const double vm = *vmax;
+        s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;
+    }
+    for (int i = tid; i < kWTX * kWTY; i += kWX * kWTh) {
+        const int ty = i / kWTX, tx = i - ty * kWTX;
+        const int gy = min(max(y0 + ty - kWH, 0), n - 1), gx = min(max(x0 + tx - kWH, 0), n - 1);
+        t[ty][tx] = phi[(size_t)gy * n + gx];
+    }
+    __syncthreads();
+    const float inv = s_inv;
+    const int x = x0 + threadIdx.x;
+    if (x >= n) return;
+#pragma unroll
+    for (int r = 0; r < kWY / kWTh; ++r) {
+        const int ly = threadIdx.y + r * kWTh, y = y0 + ly;
+        if (y >= n) break;
+        const size_t p = (size_t)y * n + x;
+        const float F = -dt * (V[p] * inv);
+        const float out = weno_px(t, ly + kWH, threadIdx.x + kWH, F, dt, lam, m ? m[p] : 1.f);
+        phi_out[p] = out;
+        if (mask_out) mask_out[p] = out <= 0.f ? 1 : 0;
+        if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(out <= 0.f ? 1.f : 0.f);
+    }
 }
 
 __global__ void k_mask_from_phi(const float* __restrict__ phi, size_t npix, unsigned char* __restrict__ M) {
@@ -253,7 +283,7 @@ int launch_levelset_step(int n, const float* phi, const float* V, const double* 
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s, int upwind) {
     if (upwind == DEVEL_UPWIND_WENO5) {
         prof_begin(PK_STEP, s);
-        k_levelset_step_weno<<<dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY), dim3(kWX, kWY), 0, s>>>(
+        k_levelset_step_weno<<<dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY), dim3(kWX, kWTh), 0, s>>>(
             phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf, ldb);
         prof_end(PK_STEP, s);
         DEVEL_LAUNCH_CHECK("k_levelset_step_weno");

@@ -43,6 +43,13 @@ __device__ __forceinline__ float sfu_rcp(float x) {
     return r;
 }
 
+// min(a, b) that returns NaN when either operand is NaN (fminf would drop it).
+__device__ __forceinline__ float min_nan(float a, float b) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // One corner: e = 2^u (u capped so that e stays finite), Z = 1 / (1 + e) and the
 // slope Z (1 - Z) = e Z^2 (no cancellation near Z = 1).
 struct Corner {
@@ -50,7 +57,7 @@ struct Corner {
 };
 __device__ __forceinline__ Corner resist_corner(float I, float a, float b) {
     const float u = fmaf(a, I, b);
-    const float e = sfu_exp2(u > 126.f ? 126.f : u);  // (a NaN stays NaN: fminf would drop it)
+    const float e = sfu_exp2(min_nan(u, 126.f));  // a NaN image stays NaN
     const float z = sfu_rcp(1.f + e);
     return Corner{z, e * z * z};
 }
