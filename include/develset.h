@@ -160,7 +160,8 @@ typedef struct {
  *   loss_out   device double[4]: {L, sum (Z_nom-Z_t)^2, sum (Z_in-Z_t)^2, sum (Z_out-Z_t)^2}
  *   counts_out device long long[2]: {L2, PVB}
  * n is the handle's; its workspace holds the reduction partials. The sums
- * are FP64 and reproducible (fixed reduction order).
+ * are FP32 within blocks of 256 threads and exact fixed-point (2^-32)
+ * across blocks, returned as FP64; reproducible bit for bit.
  */
 int devel_resist_loss(const devel_optics* optics, const float* intensity, const unsigned char* target,
                       const devel_resist_params* params, float* dLdI, double* loss_out,

@@ -75,13 +75,13 @@ int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s) {
 // the loss and metrics of this image go to the history slots (or loss4/cnt2).
 int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, const devel_resist_params& rp,
                            double* loss4, long long* cnt2, double* lh, long long* l2h, long long* pvbh,
-                           int* status, cudaStream_t s) {
+                           int* status, cudaStream_t s, bool alone = true) {
     int rc = forward_from_mhat(o, o->ws.bufI, s);
     if (rc) return rc;
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
     return launch_resist(o->n, o->ws.bufI, target, rp, tcp ? nullptr : o->ws.bufI, tcp ? o->Xhi : nullptr,
-                         tcp ? o->Xlo : nullptr, o->ldn, o->ws.dpart, o->ws.lpart, o->npart_red, loss4, cnt2, lh,
-                         l2h, pvbh, status, o->ws.counters, s);
+                         tcp ? o->Xlo : nullptr, o->ldn, o->ws.qpart, o->ws.lpart, o->npart_red, loss4, cnt2, lh,
+                         l2h, pvbh, status, o->ws.counters, s, alone);
 }
 
 // adjoint from ws.mhat (spectrum of the imaged mask) and the spectrum rhat of R
@@ -118,7 +118,7 @@ static void free_optics(devel_optics* o) {
     if (!o) return;
     void* ptrs[] = {o->W.basis, o->W.basisT, o->W2.basis, o->W2.basisT, o->TCC, o->Tdiff, o->goff,
                     o->ws.Ppart, o->ws.P, o->ws.Q, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat,
-                    o->ws.Acat, o->ws.dpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
+                    o->ws.Acat, o->ws.qpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
                     o->tcW2.basis_hi, o->tcW2.basis_lo, o->tcW2.basisT_hi, o->tcW2.basisT_lo,
@@ -159,7 +159,10 @@ using namespace devel;
 
 // All iterations of one clip on stream s (the clip's optics workspace is used
 // exclusively by this sequence of launches).
-static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* status, cudaStream_t s) {
+// alone: no other clip's kernels run beside this clip's (the resist kernel then takes
+// one CTA per SM; with concurrent clips, CTAs of 256 threads that pack between theirs)
+static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* status, cudaStream_t s,
+                        bool alone) {
     const devel_optics* o = cl.optics;
     const devel_optics* od = cl.optics_defocus;
     const int n = o->n;
@@ -195,10 +198,10 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
                 rc = launch_resist_defocus(n, w.bufI, od->ws.bufI, cl.target, p->resist, tcp ? nullptr : w.bufI,
                                            tcp ? nullptr : od->ws.bufI, tcp ? o->Xhi : nullptr,
                                            tcp ? o->Xlo : nullptr, tcp ? od->Xhi : nullptr,
-                                           tcp ? od->Xlo : nullptr, o->ldn, w.dpart, w.lpart, o->npart_red,
-                                           nullptr, nullptr, lh, l2h, pvbh, status, w.counters, s);
+                                           tcp ? od->Xlo : nullptr, o->ldn, w.qpart, w.lpart, o->npart_red,
+                                           nullptr, nullptr, lh, l2h, pvbh, status, w.counters, s, alone);
         } else {
-            rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr, lh, l2h, pvbh, status, s);
+            rc = forward_loss_from_mhat(o, cl.target, p->resist, nullptr, nullptr, lh, l2h, pvbh, status, s, alone);
         }
         if (rc) return rc;
         if (t == p->iters) break;  // the final mask is imaged for its metrics only
@@ -277,7 +280,7 @@ static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip
     }
     if (chains.size() <= 1 || !pool) {
         for (int c = 0; c < nclips; ++c) {
-            int rc = enqueue_clip(p, clips[c], status, s);
+            int rc = enqueue_clip(p, clips[c], status, s, true);
             if (rc) return rc;
         }
         return DEVEL_OK;
@@ -302,7 +305,7 @@ static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip
         DEVEL_CUDA_TRY(cudaStreamWaitEvent(bs, pool->fork, 0));
         for (int h : branch[b])
             for (int c : chains[h]) {
-                int rc = enqueue_clip(p, clips[c], status, bs);
+                int rc = enqueue_clip(p, clips[c], status, bs, false);
                 if (rc) return rc;
             }
         DEVEL_CUDA_TRY(cudaEventRecord(pool->join[b], bs));
@@ -511,7 +514,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.rhat, sizeof(float2) * kk2);
     ALLOC(o->ws.Shat, sizeof(float2) * kk);
     ALLOC(o->ws.Acat, sizeof(float) * (size_t)n * ld2);
-    ALLOC(o->ws.dpart, sizeof(double) * 3 * nred);
+    ALLOC(o->ws.qpart, sizeof(long long) * 3 * nred);
     ALLOC(o->ws.lpart, sizeof(long long) * 2 * nred);
     ALLOC(o->ws.vpart, sizeof(float) * expand_parts(n));
     ALLOC(o->ws.bufI, sizeof(float) * npix);
@@ -781,7 +784,7 @@ int devel_resist_loss(const devel_optics* o, const float* intensity, const unsig
     CHECK_PTR(dLdI, "dLdI");
     CHECK_PTR(loss_out, "loss_out");
     CHECK_PTR(counts_out, "counts_out");
-    return launch_resist(o->n, intensity, target, *p, dLdI, nullptr, nullptr, 0, o->ws.dpart, o->ws.lpart,
+    return launch_resist(o->n, intensity, target, *p, dLdI, nullptr, nullptr, 0, o->ws.qpart, o->ws.lpart,
                          o->npart_red, loss_out, counts_out, nullptr, nullptr, nullptr, nullptr, o->ws.counters, s);
 }
 

@@ -131,7 +131,7 @@ struct Workspace {
     float2* rhat = nullptr;    // [k2*k2] dL/dI spectrum on W2, scaled 1/n^2
     float2* Shat = nullptr;    // [k*k]   adjoint spectrum on W
     float* Acat = nullptr;     // [n][ldk2] expansion operand [Re T | -Im T]
-    double* dpart = nullptr;   // reduction partials, doubles
+    long long* qpart = nullptr; // loss partials, fixed point (x 2^32), 3 per block
     long long* lpart = nullptr;// reduction partials, counts
     float* vpart = nullptr;    // per-block max |V|
     // solver buffers
@@ -218,19 +218,22 @@ int expand_parts(int n);
 // dL/dI of the image I (n x n): into R (FP32, n x n) and/or into bf16 hi/lo
 // arrays of pitch ldr; loss partials, then the final reduction.
 // (one kernel: the last block to finish also does the final FP64 sums; `counter`
-// is a zeroed device word that the kernel leaves zeroed)
+// is a zeroed device word that the kernel leaves zeroed). alone: no other kernel runs
+// beside this one (one CTA per SM); else CTAs of 256 threads. Identical results.
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
-                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, double* dpart,
+                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, long long* qpart,
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
-                  long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s);
+                  long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
+                  bool alone = true);
 int resist_parts(int n);
 // Defocused inner corner: images In (nominal focus) and Id (defocused); dL/dIn and dL/dId as
 // FP32 images (Rn, Rd; may alias In, Id) or bf16 hi/lo operands (Rnhi.. with pitch ldr).
 int launch_resist_defocus(int n, const float* In, const float* Id, const unsigned char* Zt,
                           const devel_resist_params& p, float* Rn, float* Rd, __nv_bfloat16* Rnhi,
-                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, double* dpart,
+                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, long long* qpart,
                           long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
-                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s);
+                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
+                          bool alone = true);
 
 // levelset.cu
 // mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction

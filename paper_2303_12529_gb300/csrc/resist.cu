@@ -6,9 +6,10 @@
 // #{[d_in^2 I >= I_th] xor [d_out^2 I >= I_th]}.
 //
 // One HBM pass: read I and Z_t, write R (FP32, 9 B/px) or its bf16 hi/lo split
-// (the operand of the adjoint's reduction, 9 B/px). Sums are FP32 within a block
-// and FP64 across blocks (the global loss reduction), each in a fixed order, so
-// results are bitwise reproducible.
+// (the operand of the adjoint's reduction, 9 B/px). Loss sums are FP32 within a
+// block of 256 threads (in a fixed order) and exact fixed-point int64 across blocks,
+// converted to FP64 once (the global loss reduction), so results are bitwise
+// reproducible.
 #include <algorithm>
 
 #include "resist.cuh"
@@ -27,39 +28,64 @@ struct ResistOut {
     int* status;
 };
 
-// One block per SM (the grid is the SM count): a block of 1024 threads (768 for two
-// images, whose registers allow no more), so that every SM gets the same share of the
-// image; the block scheduler could otherwise stack several smaller blocks on some SMs
-// and leave others idle.
+// The image is split into "logical blocks" of 256 threads, as many as fit on every SM
+// at once (4 per SM for one image, 3 for two, whose registers allow no more), each over
+// an equal contiguous share of the image and each writing one loss partial. A CTA runs
+// LB logical blocks: LB = 1 (CTAs of 256 threads, for clips that share the GPU with
+// other clips' kernels) or LB = blocks per SM (one CTA per SM, which gives every SM the
+// same work when the clip runs alone). Every thread does the same work and every
+// partial is the same sum in the same order either way, so the results are identical.
+constexpr int kThreads = 256;
 template <bool kDef>
-__host__ __device__ constexpr int resist_threads() { return kDef ? 768 : 1024; }
-constexpr int kMaxParts = 512;  // most blocks (loss partials) of a resist kernel
+__host__ __device__ constexpr int resist_blocks_per_sm() { return kDef ? 3 : 4; }
+constexpr int kMaxParts = 1024;  // most blocks (loss partials) of a resist kernel
 
-// Final sum of the per-block partials by the first warp of the last block: lane l sums
-// partials l, l + 32, ... in order, then a fixed shuffle tree; the result does not
-// depend on timing. (One warp: the chain of dependent FP64 additions is ~10 long.)
-__device__ void resist_final_warp(const double* __restrict__ dpart, const long long* __restrict__ lpart,
-                                  int nparts, double alpha, double beta, double* loss4, long long* cnt2,
-                                  double* loss_hist, long long* l2_hist, long long* pvb_hist, int* status) {
-    const int lane = threadIdx.x;
-    double a = 0, b = 0, c = 0;
-    long long x = 0, y = 0;
+// Final sum of the per-block partials by all threads of the last CTA: thread t sums
+// the fixed-point partials t, t + blockDim.x, ... (one round of loads), then warp
+// shuffles and the first warp add the threads' sums, all in exact int64 arithmetic (the
+// result depends neither on timing nor on the CTA shape); the totals are converted to
+// FP64 once. Every thread of the CTA must call it.
+__device__ void resist_final_block(const long long* __restrict__ qpart, const long long* __restrict__ lpart,
+                                   int nparts, double alpha, double beta, double* loss4, long long* cnt2,
+                                   double* loss_hist, long long* l2_hist, long long* pvb_hist, int* status) {
+    __shared__ long long fq[5][32];
+    __shared__ int fbad;
+    long long v[5] = {0, 0, 0, 0, 0};
+    bool bad = false;
+    if (threadIdx.x == 0) fbad = 0;
 #pragma unroll 4
-    for (int i = lane; i < nparts; i += 32) {
-        a += __ldcg(dpart + i * 3 + 0);
-        b += __ldcg(dpart + i * 3 + 1);
-        c += __ldcg(dpart + i * 3 + 2);
-        x += __ldcg(lpart + i * 2 + 0);
-        y += __ldcg(lpart + i * 2 + 1);
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const long long va = __ldcg(qpart + i * 3 + 0), vb = __ldcg(qpart + i * 3 + 1),
+                        vc = __ldcg(qpart + i * 3 + 2);
+        bad |= (va == kQBad) | (vb == kQBad) | (vc == kQBad);
+        v[0] += va;
+        v[1] += vb;
+        v[2] += vc;
+        v[3] += __ldcg(lpart + i * 2 + 0);
+        v[4] += __ldcg(lpart + i * 2 + 1);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        y += __shfl_down_sync(0xffffffffu, y, o);
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();  // fbad initialised
+    if (bad) fbad = 1;
+    if (lane == 0)
+        for (int j = 0; j < 5; ++j) fq[j][w] = v[j];
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        v[j] = lane < nw ? fq[j][lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
     }
     if (lane != 0) return;
+    const long long x = v[3], y = v[4];
+    bad = fbad != 0;
+    constexpr double kScale = 1.0 / 4294967296.0;  // 2^-32
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const double a = bad ? nan : (double)v[0] * kScale, b = bad ? nan : (double)v[1] * kScale,
+                 c = bad ? nan : (double)v[2] * kScale;
     const double L = alpha * a + beta * (b + c);
     if (loss4) {
         loss4[0] = L;
@@ -116,23 +142,24 @@ __device__ __forceinline__ void split_store4(__nv_bfloat16* hi, __nv_bfloat16* l
     *reinterpret_cast<uint2*>(lo + q) = *reinterpret_cast<const uint2*>(l);
 }
 
-template <bool kDef>
-__global__ void __launch_bounds__(resist_threads<kDef>(), 1)
+template <bool kDef, int LB>
+__global__ void __launch_bounds__(kThreads * LB, resist_blocks_per_sm<kDef>() / LB)
 k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt, int n, ResistArgs p,
          float* Rn, float* Rd, __nv_bfloat16* __restrict__ Rnhi, __nv_bfloat16* __restrict__ Rnlo,
          __nv_bfloat16* __restrict__ Rdhi, __nv_bfloat16* __restrict__ Rdlo, int ldr,
-         double* __restrict__ dpart, long long* __restrict__ lpart, ResistOut out) {
+         long long* __restrict__ qpart, long long* __restrict__ lpart, ResistOut out) {
     __shared__ float sf[3][32];
     __shared__ int si[2][32];
-    constexpr int kThreads = resist_threads<kDef>();
     LossAcc acc;
     const long long npix = (long long)n * n;
+    // logical block lb of nlb, thread tid of its 256
+    const int nlb = gridDim.x * LB, lb = blockIdx.x * LB + threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
     if ((n & 3) == 0 && (!Rnhi || (ldr & 3) == 0)) {
         const int nq = n >> 2;  // groups per row
         const long long G = npix >> 2;
-        const long long g0 = G * blockIdx.x / gridDim.x, g1 = G * (blockIdx.x + 1) / gridDim.x;
-        long long g = g0 + threadIdx.x;
-        // row / group-in-row of g, advanced incrementally (the step is blockDim.x groups)
+        const long long g0 = G * lb / nlb, g1 = G * (lb + 1) / nlb;
+        long long g = g0 + tid;
+        // row / group-in-row of g, advanced incrementally (the step is kStep * 256 groups)
         int y = (int)(g / nq), xq = (int)(g - (long long)y * nq);
         Px4<kDef> cur[kStep];
 #pragma unroll
@@ -183,8 +210,8 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
             }
         }
     } else {  // ragged sides: one pixel at a time
-        const long long i0 = npix * blockIdx.x / gridDim.x, i1 = npix * (blockIdx.x + 1) / gridDim.x;
-        for (long long i = i0 + threadIdx.x; i < i1; i += kThreads) {
+        const long long i0 = npix * lb / nlb, i1 = npix * (lb + 1) / nlb;
+        for (long long i = i0 + tid; i < i1; i += kThreads) {
             float gD = 0.f;
             const float gN = kDef ? resist_px2(In[i], Id[i], Zt[i] != 0, p, acc, gD)
                                   : resist_px(In[i], Zt[i] != 0, p, acc);
@@ -205,7 +232,7 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
             }
         }
     }
-    block_store_loss(acc, blockIdx.x, dpart, lpart, sf, si);
+    block_store_loss(acc, blockIdx.x * LB, qpart, lpart, sf, si);
     // the last block to finish sums all partials (fixed order) and resets the counter
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -213,18 +240,20 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
         last = atomicAdd(out.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
+    if (!last) return;
     __threadfence();
-    resist_final_warp(dpart, lpart, gridDim.x, out.alpha, out.beta, out.loss4, out.cnt2, out.loss_hist,
-                      out.l2_hist, out.pvb_hist, out.status);
+    resist_final_block(qpart, lpart, nlb, out.alpha, out.beta, out.loss4, out.cnt2, out.loss_hist,
+                       out.l2_hist, out.pvb_hist, out.status);
     if (threadIdx.x == 0) *out.counter = 0u;
 }
 
 }  // namespace
 
-// Blocks of the resist kernels (= loss partials, <= 512): one per SM, fewer for small
-// images (at least 4096 pixels per block).
-int resist_parts(int n) {
+// Blocks of the resist kernels (= loss partials, <= 1024): resist_blocks_per_sm per SM
+// (the grid of the one-image kernel, which the two-image kernel's grid never exceeds;
+// that one uses the first 3 per SM), fewer for small images (at least 4096 pixels per
+// block).
+static int sm_total() {
     static int sms = 0;
     if (!sms) {
         int dev = 0, v = 0;
@@ -234,18 +263,34 @@ int resist_parts(int n) {
         else
             sms = 148;
     }
+    return sms;
+}
+static int resist_grid(int n, int per_sm) {
     const long long want = ((long long)n * n + 4095) / 4096;
-    return (int)std::max(1LL, std::min<long long>({want, (long long)sms, (long long)kMaxParts}));
+    return (int)std::max(1LL, std::min<long long>({want, (long long)per_sm * sm_total(), (long long)kMaxParts}));
+}
+int resist_parts(int n) { return resist_grid(n, resist_blocks_per_sm<false>()); }
+
+template <bool kDef, typename... A>
+static void launch_resist_kernel(int n, int nparts, bool alone, cudaStream_t s, A... args) {
+    constexpr int per_sm = resist_blocks_per_sm<kDef>();
+    const int nlb = std::min(nparts, resist_grid(n, per_sm));
+    if (alone && nlb % per_sm == 0)
+        k_resist<kDef, per_sm><<<nlb / per_sm, kThreads * per_sm, 0, s>>>(args...);
+    else
+        k_resist<kDef, 1><<<nlb, kThreads, 0, s>>>(args...);
 }
 
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
-                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, double* dpart,
+                  float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, long long* qpart,
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
-                  long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s) {
+                  long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
+                  bool alone) {
     ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
     prof_begin(PK_RESIST, s);
-    k_resist<false><<<nparts, resist_threads<false>(), 0, s>>>(I, nullptr, Zt, n, make_resist_args(p), R, nullptr, Rhi, Rlo,
-                                                nullptr, nullptr, ldr, dpart, lpart, out);
+    launch_resist_kernel<false>(n, nparts, alone, s, I, (const float*)nullptr, Zt, n, make_resist_args(p), R,
+                                (float*)nullptr, Rhi, Rlo, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, ldr,
+                                qpart, lpart, out);
     prof_end(PK_RESIST, s);
     DEVEL_LAUNCH_CHECK("k_resist");
     return DEVEL_OK;
@@ -253,13 +298,14 @@ int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_re
 
 int launch_resist_defocus(int n, const float* In, const float* Id, const unsigned char* Zt,
                           const devel_resist_params& p, float* Rn, float* Rd, __nv_bfloat16* Rnhi,
-                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, double* dpart,
+                          __nv_bfloat16* Rnlo, __nv_bfloat16* Rdhi, __nv_bfloat16* Rdlo, int ldr, long long* qpart,
                           long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
-                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s) {
+                          long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
+                          bool alone) {
     ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
     prof_begin(PK_RESIST, s);
-    k_resist<true><<<nparts, resist_threads<true>(), 0, s>>>(In, Id, Zt, n, make_resist_args(p), Rn, Rd, Rnhi, Rnlo, Rdhi, Rdlo,
-                                               ldr, dpart, lpart, out);
+    launch_resist_kernel<true>(n, nparts, alone, s, In, Id, Zt, n, make_resist_args(p), Rn, Rd, Rnhi, Rnlo, Rdhi,
+                               Rdlo, ldr, qpart, lpart, out);
     prof_end(PK_RESIST, s);
     DEVEL_LAUNCH_CHECK("k_resist_defocus");
     return DEVEL_OK;

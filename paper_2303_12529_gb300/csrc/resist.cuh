@@ -2,6 +2,8 @@
 // fixed-order block reduction of the loss partials.
 #pragma once
 
+#include <climits>
+
 #include "common.cuh"
 
 namespace devel {
@@ -23,8 +25,8 @@ inline ResistArgs make_resist_args(const devel_resist_params& p) {
     return a;
 }
 
-// Loss accumulators of one thread: FP32 sums of a few pixels (FP64 from the
-// warp level up) and the two binary-metric counts.
+// Loss accumulators of one thread: FP32 sums of a few pixels and the two
+// binary-metric counts.
 struct LossAcc {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     int l2 = 0, pvb = 0;
@@ -99,12 +101,29 @@ __device__ __forceinline__ float resist_px2(float In, float Id, bool zt_on, cons
     return fmaf(p.k_out * eo, co.ez2, (p.k_nom * en) * cn.ez2);
 }
 
-// Block reduction of the accumulators in a fixed order (FP32 / int within the block;
-// the partials are summed in FP64 / int64 across blocks); thread 0 writes the block's
-// partial to
-// dpart[part * 3 + {0,1,2}] and lpart[part * 2 + {0,1}]. Every thread of the block
-// must call it. sf/si: shared scratch of >= 32 entries.
-__device__ __forceinline__ void block_store_loss(const LossAcc& a, int part, double* dpart, long long* lpart,
+// x * 2^32 as an int64, rounded toward zero, from the bits of an FP32 value with
+// |x| < 2^30 (integer ALU only: FP64 instructions are slow here); kQBad for a
+// non-finite x. Summing these is exact and independent of the order; a partial of
+// e^2 terms (each <= 1) never approaches 2^30.
+constexpr long long kQBad = LLONG_MIN;
+__device__ __forceinline__ long long to_q32(float x) {
+    const unsigned u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xffu);
+    if (e == 0xff) return kQBad;
+    if (e == 0) return 0;  // zero or subnormal
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+    const int sh = e - 118;  // x 2^32 = m 2^(e - 127 - 23 + 32)
+    if (sh > 38) return kQBad;
+    const long long q = sh >= 0 ? (m << sh) : (sh <= -24 ? 0 : (m >> -sh));
+    return (u >> 31) ? -q : q;
+}
+
+// Reduction of the accumulators of each group of 256 threads (a logical block) in a
+// fixed order (FP32 / int within the group); the first thread of group j writes its
+// partial to qpart[(part0 + j) * 3 + {0,1,2}] (fixed point, to_q32) and
+// lpart[(part0 + j) * 2 + {0,1}]. Every thread of the CTA (at most 1024) must call
+// it. sf/si: shared scratch of >= 32 entries.
+__device__ __forceinline__ void block_store_loss(const LossAcc& a, int part0, long long* qpart, long long* lpart,
                                                  float (*sf)[32], int (*si)[32]) {
     float s0 = a.s0, s1 = a.s1, s2 = a.s2;
     int l2 = a.l2, pvb = a.pvb;
@@ -124,20 +143,21 @@ __device__ __forceinline__ void block_store_loss(const LossAcc& a, int part, dou
         si[1][w] = pvb;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // FP32 over the block's warps (FP64 arithmetic is slow here)
-        const int nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 255) == 0) {  // the group's 8 warps, in order
+        const int w0 = threadIdx.x >> 5;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
         int c0 = 0, c1 = 0;
-        for (int i = 0; i < nw; ++i) {
+        for (int i = w0; i < w0 + 8; ++i) {
             x0 += sf[0][i];
             x1 += sf[1][i];
             x2 += sf[2][i];
             c0 += si[0][i];
             c1 += si[1][i];
         }
-        dpart[part * 3 + 0] = x0;
-        dpart[part * 3 + 1] = x1;
-        dpart[part * 3 + 2] = x2;
+        const int part = part0 + (threadIdx.x >> 8);
+        qpart[part * 3 + 0] = to_q32(x0);
+        qpart[part * 3 + 1] = to_q32(x1);
+        qpart[part * 3 + 2] = to_q32(x2);
         lpart[part * 2 + 0] = c0;
         lpart[part * 2 + 1] = c1;
     }
