@@ -73,3 +73,35 @@ def test_wrong_weno_weights_are_caught(monkeypatch):
     monkeypatch.setattr(levelset, "weno5_combine", swapped)
     import test_oracle_weno as tw
     _fails(tw.test_weno_fifth_order_convergence)
+
+
+def test_fletcher_reeves_in_place_of_polak_ribiere_is_caught(monkeypatch):
+    from oracle import cg
+    import test_oracle_cg as tc
+
+    def fr(V, Vprev):
+        den = float(np.sum(Vprev * Vprev))
+        return 0.0 if den == 0.0 else float(np.sum(V * V)) / den
+    monkeypatch.setattr(cg, "pr_plus_beta", fr)
+    _fails(tc.test_polak_ribiere_is_zero_for_a_repeated_gradient)
+
+
+def test_dropped_previous_direction_in_cg_is_caught(monkeypatch):
+    from oracle import cg
+    import test_oracle_cg as tc
+    monkeypatch.setattr(cg, "direction", lambda V, Vp, Dp, restart: (np.asarray(V, float).copy(), 0.0))
+    _fails(tc.test_cg_finite_termination_on_a_quadratic, 0)
+
+
+def test_wrong_sign_of_beta_in_cg_is_caught(monkeypatch):
+    from oracle import cg
+    import test_oracle_cg as tc
+    orig = cg.direction
+
+    def minus(V, Vp, Dp, restart):
+        D, beta = orig(V, Vp, Dp, restart)
+        if restart or Vp is None:
+            return D, beta
+        return np.asarray(V, float) - beta * np.asarray(Dp, float), -beta
+    monkeypatch.setattr(cg, "direction", minus)
+    _fails(tc.test_cg_finite_termination_on_a_quadratic, 0)
