@@ -104,6 +104,10 @@ def kernel_bytes(name, n, K, k, tc, defocus=False):
         return slices * (ldk * ldk + ldk2 * ldk2) / 2 * 4
     if name == "ihat_tcc":
         return k ** 4 / 2 * 8
+    if name == "cg_dots":
+        return 8 * px                             # V, V_prev in
+    if name == "cg_update":
+        return 16 * px                            # V, D in; D, V_prev out
     if name == "shat_tcc":
         return k ** 4 * 8 * (2 if defocus else 1)
     return None
@@ -190,11 +194,11 @@ def simt_fp32_peak_tflops(sm_mhz):
 # --------------------------------------------------------------------------
 # the reference arm: the FP64 CPU oracle on a bounded sample
 # --------------------------------------------------------------------------
-def oracle_sample(wl, weno=False, defocus=0.0):
+def oracle_sample(wl, weno=False, defocus=0.0, cg_dir=False, dt=0.5, lam=0.1):
     """Time the oracle on a bounded sample of one clip's solve and scale it to
     clips/s: one full-size DSO iteration (image, loss, gradient, step) plus a
     re-initialisation measured on a row sample and amortised over 5 iterations."""
-    from oracle import levelset, litho, resist, sdf
+    from oracle import cg, levelset, litho, resist, sdf
     n, K, k, iters, beta = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"]
     o = synth.optics(n, K, k)
     od = synth.optics(n, K, k, defocus=defocus) if defocus else None
@@ -212,7 +216,9 @@ def oracle_sample(wl, weno=False, defocus=0.0):
     V = litho.aerial_gradient(M, res.R, o.H, o.w)
     if od:
         V = V + litho.aerial_gradient(M, res.R_def, od.H, od.w)
-    levelset.step(phi, V, float(np.abs(V).max()), None, 0.5, 0.1, weno=weno)
+    if cg_dir:  # the direction's cost: one more pass over V, V_prev and D
+        V, _ = cg.direction(V, 0.9 * V, V, restart=False)
+    levelset.step(phi, V, float(np.abs(V).max()), None, dt, lam, weno=weno)
     t_iter = time.perf_counter() - t0
     per_clip = iters * t_iter + (iters / 5 + 1) * t_reinit + t_iter * 0.1
     sample = (f"one {n}^2 DSO iteration (K={K}, k={k}) timed in full ({t_iter:.1f} s) plus a TSDF on "
@@ -231,7 +237,8 @@ def run_reference(args, wl):
     vals = []
     sample = ""
     for _ in range(max(1, args.steps)):
-        v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus)
+        v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus, args.optimizer == "cg",
+                                            args.dt, args.lam)
         vals.append(v)
         if time.perf_counter() - t0 > 150:
             break
@@ -272,8 +279,9 @@ def run_ours(args, wl):
     target = torch.from_numpy(Zt.ravel().copy()).to(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     upwind = dv.DEVEL_UPWIND_WENO5 if args.upwind == "weno5" else dv.DEVEL_UPWIND_GODUNOV1
-    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5,
-                           upwind=upwind)
+    optimizer = dv.DEVEL_OPT_CG if args.optimizer == "cg" else dv.DEVEL_OPT_STEEPEST
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=args.dt, lam=args.lam, iters=iters, reinit_every=5,
+                           upwind=upwind, optimizer=optimizer)
     precs = ["bf16x3", "fp32"] if args.precision == "both" else [args.precision]
     od = synth.optics(n, K, k, defocus=args.defocus) if args.defocus else None
 
@@ -441,7 +449,8 @@ def run_ours(args, wl):
         if args.no_cpu_baseline:
             cpu = None
         else:
-            v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus)
+            v, per_clip, sample = oracle_sample(wl, args.upwind == "weno5", args.defocus, args.optimizer == "cg",
+                                            args.dt, args.lam)
             cpu = {"value": v, "unit": "clips/s", "cores": 1, "kind": "oracle", "sample": sample}
         ms = head["ms"]
         out = {
@@ -450,10 +459,10 @@ def run_ours(args, wl):
             "vs_baseline": None, "dtype": "f32" if head["prec"] == "fp32" else "bf16x3",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "K": K, "k": k, "iters": iters, "beta": beta,
-                       "dt": 0.5, "lambda": 0.1, "reinit_every": 5, "clips_per_gpu_per_step": 1,
+                       "dt": args.dt, "lambda": args.lam, "reinit_every": 5, "clips_per_gpu_per_step": 1,
                        "precision": head["prec"], "init": "zero level set (TSDF of the target)",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
-                       "upwind": args.upwind, "defocus_waves": args.defocus},
+                       "upwind": args.upwind, "defocus_waves": args.defocus, "optimizer": args.optimizer},
             "litho_tflops": {"window_method": window_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12,
                              "socs_equivalent": algorithmic_flops_per_iter(n, K, k) * iters * world / (ms / 1000) / 1e12},
             "e2e": {"value": head["e2e"], "unit": "clips/s", "h2d_bytes_per_step": n * n,
@@ -534,8 +543,9 @@ def run_batched(args, wl):
                              pvb_hist=torch.zeros(iters + 1, dtype=torch.int64, device=dev),
                              optics_defocus=hd))
     upwind = dv.DEVEL_UPWIND_WENO5 if args.upwind == "weno5" else dv.DEVEL_UPWIND_GODUNOV1
-    params = dv.ilt_params(dv.resist_params(beta=beta), dt=0.5, lam=0.1, iters=iters, reinit_every=5,
-                           upwind=upwind)
+    optimizer = dv.DEVEL_OPT_CG if args.optimizer == "cg" else dv.DEVEL_OPT_STEEPEST
+    params = dv.ilt_params(dv.resist_params(beta=beta), dt=args.dt, lam=args.lam, iters=iters, reinit_every=5,
+                           upwind=upwind, optimizer=optimizer)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     steps = max(1, min(args.steps, 5))
@@ -634,10 +644,10 @@ def run_batched(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
             "config": {"workload": args.workload, "clips_per_gpu_per_step": B, "sides": hist, "K": K,
                        "k_per_side": {n: 2 * synth.window_radius_for(n) + 1 for n in wl["sides"]},
-                       "iters": iters, "beta": beta, "precision": "bf16x3",
+                       "iters": iters, "beta": beta, "precision": "bf16x3", "dt": args.dt, "lambda": args.lam,
                        "schedule": "one devel_ilt_solve per step, clips on parallel graph branches",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
-                       "upwind": args.upwind, "defocus_waves": args.defocus},
+                       "upwind": args.upwind, "defocus_waves": args.defocus, "optimizer": args.optimizer},
             "megapixel_iterations_per_s": world * px * iters / (ms / 1000.0) / 1e6,
             "sequential": {"value": B * 1000.0 / ms_seq, "ms_per_step": ms_seq,
                            "schedule": "one devel_ilt_solve per clip"},
@@ -700,6 +710,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--upwind", choices=["godunov1", "weno5"], default="godunov1",
                     help="one-sided derivatives of the upwind |grad phi| (first order, or WENO5)")
+    ap.add_argument("--optimizer", choices=["steepest", "cg"], default="steepest",
+                    help="front velocity: dL/dM itself, or its PR+ conjugate-gradient direction")
+    ap.add_argument("--dt", type=float, default=0.5, help="CFL number of the step (the paper: 0.85)")
+    ap.add_argument("--lam", type=float, default=0.1, help="curvature weight (the paper: 0.9)")
     ap.add_argument("--defocus", type=float, default=0.0,
                     help="waves of defocus at the pupil edge for the inner process corner "
                          "(0: dose-only corners)")

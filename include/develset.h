@@ -10,6 +10,7 @@
  *   devel_resist_loss     Sec. III-A sigmoid resist, L_ilt, L_pvb; Sec. II-C L2, PVBand
  *   devel_litho_adjoint   Eqs. (ilt_gradient), (pvb_gradient), (vel)  dL/dM from dL/dI
  *   devel_levelset_step   Eqs. (dso_evolution), (numerical-settings), (curva_numer), (phi2mask)
+ *   devel_cg_direction    Sec. III-C conjugate-gradient direction of the velocity
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
  *
  * Conventions shared by every call
@@ -60,6 +61,15 @@ extern "C" {
 #define DEVEL_UPWIND_GODUNOV1 0
 #define DEVEL_UPWIND_WENO5 1
 
+/* Optimisers of the solve (Sec. III-C: DSO optimises with conjugate gradient, the
+ * paper gives no update rule): the front moves with the velocity V = dL/dM itself
+ * (steepest descent), or with the nonlinear conjugate-gradient direction
+ * D = V + beta D_prev, beta = max(0, <V, V - V_prev> / <V_prev, V_prev>) (Polak-Ribiere,
+ * clipped at zero), restarted (D = V) at the first iteration of a solve and at every
+ * iteration that follows a re-initialisation. Either is normalised by its max. */
+#define DEVEL_OPT_STEEPEST 0
+#define DEVEL_OPT_CG 1
+
 /* Thread-local text of the last error returned on this thread ("" if none). */
 const char* devel_last_error(void);
 
@@ -78,10 +88,11 @@ typedef struct devel_optics devel_optics;
  *   w_host  host, float[K]: SOCS weights sigma_j >= 0
  *   precision DEVEL_PREC_FP32 or DEVEL_PREC_BF16X3
  * Requires 16 <= n <= 8192, k odd, 3 <= k, 2k - 1 <= n, 1 <= K <= k*k.
- * Copies everything it needs to the device ("loaded and pinned in GPU memory
- * throughout the optimization", Sec. III-A) and allocates the workspace of
- * devel_litho_* and devel_ilt_solve for this n (about 21 bytes per pixel plus
- * O(n k) tables). *out receives the handle; on error *out is left NULL.
+ * Copies everything it needs to the device (Sec. III-A keeps the optical
+ * kernels and weights resident on the GPU for the whole optimisation) and
+ * allocates the workspace of devel_litho_*, devel_cg_direction and
+ * devel_ilt_solve for this n (about 29 bytes per pixel plus O(n k) tables).
+ * *out receives the handle; on error *out is left NULL.
  * Returns DEVEL_EINVAL, DEVEL_ENOMEM or DEVEL_ECUDA on failure.
  */
 int devel_optics_create(int n, int K, int k, const float* H_host, const float* w_host,
@@ -269,6 +280,9 @@ typedef struct {
                             replay); 0: launch kernel by kernel. Ignored while a profile is open. */
     int upwind;          /* one-sided derivatives of |grad phi|: DEVEL_UPWIND_GODUNOV1 (first order)
                             or DEVEL_UPWIND_WENO5 (fifth-order WENO, Sec. III-C)                */
+    int optimizer;       /* DEVEL_OPT_STEEPEST or DEVEL_OPT_CG (Sec. III-C). With CG, a solve
+                            resumed at a multiple of reinit_every is bit-identical to the
+                            unsplit run (the direction restarts there)                     */
 } devel_ilt_params;
 
 typedef struct {
@@ -288,6 +302,26 @@ typedef struct {
                                       same n, window and precision as `optics`, a handle of its own
                                       (its workspace is used; no other clip of the call may use it) */
 } devel_clip;
+
+/*
+ * Conjugate-gradient direction of the level-set velocity (Sec. III-C; the rule
+ * of DEVEL_OPT_CG above):
+ *   restart != 0:  D = V, beta = 0
+ *   else:          beta = max(0, <V, V - Vprev> / <Vprev, Vprev>)  (0 if <Vprev, Vprev> = 0),
+ *                  D = V + beta D
+ * then Vprev = V and vmax_out = max |D| (the normaliser of the next
+ * devel_levelset_step, which takes D as its V). <.,.> sums over the n*n
+ * pixels: FP32 in a fixed order (reproducible); beta is computed in FP32.
+ *   V         device float[n*n]             Vprev  device float[n*n], in/out
+ *   D         device float[n*n], in/out (ignored on input when restarting)
+ *   beta_out  device double[1] or NULL      vmax_out device double[1]
+ *   status    device int[1] or NULL: set to DEVEL_ENAN if a dot product or D
+ *             is not finite
+ * V, Vprev and D must be distinct arrays; n is the handle's (its workspace
+ * holds the partial sums).
+ */
+int devel_cg_direction(const devel_optics* optics, const float* V, float* Vprev, float* D, int restart,
+                       double* beta_out, double* vmax_out, int* status, cudaStream_t stream);
 
 /*
  * Run `params->iters` DSO iterations on each clip (host array of nclips):

@@ -27,6 +27,8 @@ DEVEL_ETIMEOUT = -4
 DEVEL_ENAN = -5
 DEVEL_UPWIND_GODUNOV1 = 0
 DEVEL_UPWIND_WENO5 = 1
+DEVEL_OPT_STEEPEST = 0
+DEVEL_OPT_CG = 1
 DEVEL_PREC_FP32 = 0
 DEVEL_PREC_BF16X3 = 1
 
@@ -55,7 +57,7 @@ class devel_resist_params(ctypes.Structure):
 class devel_ilt_params(ctypes.Structure):
     _fields_ = [("resist", devel_resist_params), ("dt", _F), ("lambda_", _F), ("d_lo", _F),
                 ("d_hi", _F), ("iters", _I), ("reinit_every", _I), ("start_iter", _I), ("use_graph", _I),
-                ("upwind", _I)]
+                ("upwind", _I), ("optimizer", _I)]
 
 
 class devel_clip(ctypes.Structure):
@@ -84,6 +86,7 @@ _sig("devel_litho_adjoint", [_P, _P, _P, _P, _P, _P])
 _sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
 _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
+_sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
@@ -104,7 +107,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
-            "devel_selftest_bounded_wait", "devel_levelset_step_weno5")
+            "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -249,6 +252,18 @@ def devel_levelset_step(n: int, phi, V, vmax, m, dt: float, lam: float, phi_out,
                                     _ptr(mask_out, torch.uint8, N, "mask_out"), _stream(stream)))
 
 
+def devel_cg_direction(optics: Optics, V, Vprev, D, restart: bool, vmax, beta=None, status=None,
+                       stream=None):
+    """D = V + beta D (PR+ beta; restart: D = V), Vprev = V, vmax = max|D|."""
+    import torch
+    N = optics.n * optics.n
+    _check(_lib.devel_cg_direction(optics.handle, _ptr(V, torch.float32, N, "V"),
+                                   _ptr(Vprev, torch.float32, N, "Vprev"), _ptr(D, torch.float32, N, "D"),
+                                   int(bool(restart)), _ptr(beta, torch.float64, 1, "beta"),
+                                   _ptr(vmax, torch.float64, 1, "vmax"), _ptr(status, torch.int32, 1, "status"),
+                                   _stream(stream)))
+
+
 def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):
     import torch
     N = n * n
@@ -266,10 +281,11 @@ def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float
 
 
 def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,
-               reinit_every=5, start_iter=0, use_graph=True, upwind=0) -> devel_ilt_params:
-    """upwind: DEVEL_UPWIND_GODUNOV1 (0) or DEVEL_UPWIND_WENO5 (1)."""
+               reinit_every=5, start_iter=0, use_graph=True, upwind=0, optimizer=0) -> devel_ilt_params:
+    """upwind: DEVEL_UPWIND_GODUNOV1 (0) or DEVEL_UPWIND_WENO5 (1);
+    optimizer: DEVEL_OPT_STEEPEST (0) or DEVEL_OPT_CG (1)."""
     return devel_ilt_params(resist if resist is not None else resist_params(), dt, lam, d_lo, d_hi,
-                            iters, reinit_every, start_iter, int(bool(use_graph)), int(upwind))
+                            iters, reinit_every, start_iter, int(bool(use_graph)), int(upwind), int(optimizer))
 
 
 @dataclass

@@ -120,6 +120,7 @@ static void free_optics(devel_optics* o) {
                     o->ws.Ppart, o->ws.P, o->ws.Q, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat,
                     o->ws.Acat, o->ws.qpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
+                    o->ws.cgpart, o->ws.cgvpart, o->ws.cgbeta, o->ws.cg_vmax, o->ws.cgV, o->ws.cgD,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
                     o->tcW2.basis_hi, o->tcW2.basis_lo, o->tcW2.basisT_hi, o->tcW2.basisT_lo,
                     o->tcW.zm_hi, o->tcW.zm_lo, o->tcW2.zm_hi, o->tcW2.zm_lo,
@@ -216,13 +217,25 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
             rc = adjoint_resident(o, w.bufV, w.vmax, status, s);
         }
         if (rc) return rc;
-        rc = launch_levelset_step(n, phi, w.bufV, w.vmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
+        const float* vel = w.bufV;
+        const double* velmax = w.vmax;
+        const int gi = p->start_iter + t;
+        if (p->optimizer == DEVEL_OPT_CG) {
+            // conjugate-gradient direction; restarts at the first iteration and after each
+            // re-initialisation (global index), so a run resumed there is bit-identical
+            const bool restart = t == 0 || (p->reinit_every > 0 && gi % p->reinit_every == 0);
+            rc = launch_cg_direction(n, w.bufV, w.cgV, w.cgD, restart, w.cgpart, w.cgvpart, w.cgbeta, nullptr,
+                                     w.counters + 2, w.cg_vmax, status, s);
+            if (rc) return rc;
+            vel = w.cgD;
+            velmax = w.cg_vmax;
+        }
+        rc = launch_levelset_step(n, phi, vel, velmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
                                   tcp ? o->Xhi : nullptr, o->ldn, s, p->upwind);
         if (rc) return rc;
         float* tmp = phi;
         phi = phi_alt;
         phi_alt = tmp;
-        const int gi = p->start_iter + t;
         if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
             rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
             if (rc) return rc;
@@ -527,6 +540,12 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.cnt2, sizeof(long long) * 2);
     ALLOC(o->tc_err, sizeof(int));
     ALLOC(o->ws.counters, sizeof(unsigned) * 4);
+    ALLOC(o->ws.cgpart, sizeof(float) * 3 * cg_parts(n));
+    ALLOC(o->ws.cgvpart, sizeof(float) * cg_parts(n));
+    ALLOC(o->ws.cgbeta, sizeof(float));
+    ALLOC(o->ws.cg_vmax, sizeof(double));
+    ALLOC(o->ws.cgV, sizeof(float) * npix);
+    ALLOC(o->ws.cgD, sizeof(float) * npix);
     if (precision == DEVEL_PREC_BF16X3) {
         const size_t bf = sizeof(__nv_bfloat16);
         for (TcWindow* tw : {&o->tcW, &o->tcW2}) {
@@ -838,6 +857,21 @@ int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, floa
     return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s);
 }
 
+int devel_cg_direction(const devel_optics* o, const float* V, float* Vprev, float* D, int restart,
+                       double* beta_out, double* vmax_out, int* status, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_cg_direction: optics is NULL");
+    CHECK_PTR(V, "V");
+    CHECK_PTR(Vprev, "Vprev");
+    CHECK_PTR(D, "D");
+    CHECK_PTR(vmax_out, "vmax_out");
+    CHECK_OPT_PTR(beta_out, "beta_out");
+    CHECK_OPT_PTR(status, "status");
+    if ((const void*)V == (const void*)Vprev || (const void*)V == (const void*)D || Vprev == D)
+        return set_error(DEVEL_EINVAL, "devel_cg_direction: V, Vprev and D must be distinct arrays");
+    return launch_cg_direction(o->n, V, Vprev, D, restart != 0, o->ws.cgpart, o->ws.cgvpart, o->ws.cgbeta,
+                               beta_out, o->ws.counters + 2, vmax_out, status, s);
+}
+
 int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* clips, int* status,
                     cudaStream_t s) {
     if (!p) return set_error(DEVEL_EINVAL, "devel_ilt_solve: params is NULL");
@@ -848,6 +882,8 @@ int devel_ilt_solve(const devel_ilt_params* p, int nclips, const devel_clip* cli
     if (!(p->d_lo <= p->d_hi)) return set_error(DEVEL_EINVAL, "devel_ilt_solve: d_lo > d_hi");
     if (p->upwind != DEVEL_UPWIND_GODUNOV1 && p->upwind != DEVEL_UPWIND_WENO5)
         return set_error(DEVEL_EINVAL, "devel_ilt_solve: unknown upwind scheme %d", p->upwind);
+    if (p->optimizer != DEVEL_OPT_STEEPEST && p->optimizer != DEVEL_OPT_CG)
+        return set_error(DEVEL_EINVAL, "devel_ilt_solve: unknown optimizer %d", p->optimizer);
     for (int c = 0; c < nclips; ++c) {
         const devel_clip& cl = clips[c];
         if (!cl.optics) return set_error(DEVEL_EINVAL, "devel_ilt_solve: clip %d has no optics", c);

@@ -33,7 +33,7 @@ enum ProfKind {
     PK_SPECTRUM = 0, PK_SPECTRUM_REDUCE, PK_SOCS_Y, PK_HOPKINS, PK_ADJ_WINDOW,
     PK_EXPAND_T, PK_EXPAND_GEMM, PK_VMAX, PK_RESIST, PK_RESIST_FINAL,
     PK_STEP, PK_MASK, PK_EDT_COLS, PK_EDT_ROWS, PK_U8F32,
-    PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PROF_NKINDS
+    PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PK_CG_DOTS, PK_CG_UPDATE, PROF_NKINDS
 };
 bool prof_on();
 unsigned prof_generation();
@@ -143,7 +143,15 @@ struct Workspace {
     double* vmax = nullptr;    // [1]
     double* loss4 = nullptr;   // [4]
     long long* cnt2 = nullptr; // [2]
-    unsigned* counters = nullptr;  // [4] zeroed: last-block counters (0: resist, 1: max |V|)
+    unsigned* counters = nullptr;  // [4] zeroed: last-block counters (0: resist, 1: max |V|,
+                                   //     2: CG dot products, 3: max |D|)
+    // conjugate-gradient state (Sec. III-C)
+    float* cgpart = nullptr;   // [3 * cg_parts] FP32 block sums of V.V, V.Vp, Vp.Vp
+    float* cgvpart = nullptr;  // [cg_parts] per-block max |D|
+    float* cgbeta = nullptr;   // [1] beta of the current iteration
+    double* cg_vmax = nullptr; // [1] max |D|
+    float* cgV = nullptr;      // [n*n] velocity of the previous iteration (solve only)
+    float* cgD = nullptr;      // [n*n] direction (solve only)
 };
 
 // bf16 hi/lo tables and tensor maps of one window for the tensor-core path
@@ -238,6 +246,12 @@ int launch_resist_defocus(int n, const float* In, const float* Id, const unsigne
 // levelset.cu
 // mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction
 // upwind: DEVEL_UPWIND_GODUNOV1 or DEVEL_UPWIND_WENO5 (one-sided derivatives of |grad phi|)
+// cg.cu: D = V + beta D (PR+ beta from V, Vp; restart: D = V), Vp = V, max|D| -> vmax.
+// part: float[3 * cg_parts(n)], vpart: float[cg_parts(n)], counters: 2 zeroed words.
+int cg_parts(int n);
+int launch_cg_direction(int n, const float* V, float* Vp, float* D, bool restart, float* part, float* vpart,
+                        float* beta_f, double* beta_out, unsigned* counters, double* vmax, int* status,
+                        cudaStream_t s);
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s,

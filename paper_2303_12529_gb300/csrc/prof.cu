@@ -17,7 +17,8 @@ static const char* kNames[PROF_NKINDS] = {
     "spectrum_gemm", "spectrum_reduce", "unused",     "ihat_tcc",  "shat_tcc",
     "expand_T",      "expand_gemm",     "vmax_final", "resist",    "resist_final",
     "levelset_step", "mask_from_phi",   "edt_cols",   "edt_rows",  "u8_to_f32",
-    "tc_expand",     "tc_spectrum",     "spectrum_stage2", "tc_split",
+    "tc_expand",     "tc_spectrum",     "spectrum_stage2", "tc_split",  "cg_dots",
+    "cg_update",
 };
 
 struct Slot {

@@ -64,3 +64,20 @@ def test_argument_checks_need_no_device(lib):
     assert lib.devel_reinit_sdf(16, 17, 32, 48, 0.0, 1.0, None) == dv.DEVEL_EINVAL
     assert lib.devel_reinit_sdf(16, 16, 32, 48, 2.0, 1.0, None) == dv.DEVEL_EINVAL
     assert "d_lo" in dv.devel_last_error()
+    # the CG direction refuses a missing handle and aliased arrays before any launch
+    lib.devel_cg_direction.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 4
+    assert lib.devel_cg_direction(None, 16, 32, 48, 0, None, 64, None, None) == dv.DEVEL_EINVAL
+    assert "optics" in dv.devel_last_error()
+
+
+def test_ilt_params_layout_matches_the_header():
+    """The ctypes mirror of devel_ilt_params has the header's fields in order (the
+    new optimizer field last)."""
+    import paper_2303_12529_gb300 as dv
+    names = [f[0] for f in dv.devel_ilt_params._fields_]
+    assert names[-2:] == ["upwind", "optimizer"]
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} devel_ilt_params;", txt, flags=re.S).group(1)
+    fields = re.findall(r"\b(\w+)\s*(?:,\s*(\w+))?\s*;", body)
+    flat = [x for pair in fields for x in pair if x]
+    assert flat[-2:] == ["upwind", "optimizer"]

@@ -90,9 +90,10 @@ def _clip_job(dv, opt, Zt, iters):
     return dv.Clip(opt, dev(Zt), phi, mask_out=M, loss_hist=L, l2_hist=l2)
 
 
+@pytest.mark.parametrize("optimizer", [0, 1])
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batched_uneven_clips_equal_single_solves(prec, use_graph):
+def test_batched_uneven_clips_equal_single_solves(prec, use_graph, optimizer):
     """One devel_ilt_solve over clips of uneven sides (each side with its own window,
     two clips sharing one handle) gives, clip for clip, bit-identical phi, masks and
     loss histories to solving each clip alone: the concurrent branches change the
@@ -104,7 +105,8 @@ def test_batched_uneven_clips_equal_single_solves(prec, use_graph):
     targets = [synth.rect_clip(40 + i, n=n, border=8) for i, (n, _) in enumerate(sides)]
     targets.append(synth.rect_clip(50, n=128, border=8))  # shares the 128 handle
     handles = [opts[128], opts[192], opts[256], opts[128]]
-    p = dv.ilt_params(dv.resist_params(beta=2.0), iters=iters, reinit_every=3, use_graph=use_graph)
+    p = dv.ilt_params(dv.resist_params(beta=2.0), iters=iters, reinit_every=3, use_graph=use_graph,
+                      optimizer=optimizer)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     batch = [_clip_job(dv, h, Zt, iters) for h, Zt in zip(handles, targets)]
     dv.devel_ilt_solve(p, batch, st)
