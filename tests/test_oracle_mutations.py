@@ -105,3 +105,19 @@ def test_wrong_sign_of_beta_in_cg_is_caught(monkeypatch):
         return np.asarray(V, float) - beta * np.asarray(Dp, float), -beta
     monkeypatch.setattr(cg, "direction", minus)
     _fails(tc.test_cg_finite_termination_on_a_quadratic, 0)
+
+
+def test_shift_with_the_wrong_sign_is_caught(monkeypatch):
+    from oracle import modulation
+    import test_oracle_modulation as tm
+    monkeypatch.setattr(modulation, "candidates",
+                        lambda phi, dh: np.stack([(np.asarray(phi, float) - float(d) >= 0).astype(float) for d in dh]))
+    _fails(tm.test_candidates_limits_and_monotonicity)
+
+
+def test_ahf_with_eps_on_the_wrong_side_is_caught(monkeypatch):
+    from oracle import modulation
+    import test_oracle_modulation as tm
+    monkeypatch.setattr(modulation, "ahf",
+                        lambda phi, eps: 0.5 * (1.0 + (2.0 / np.pi) * np.arctan(np.asarray(phi, float) * eps)))
+    _fails(tm.test_ahf_identities)
