@@ -37,6 +37,10 @@ WORKLOADS = {
     # sides, seeds 2001.. the patterns), window k_n = 2 ceil(17 n / 2048) + 1 at 1 nm/px,
     # compensated BF16, one devel_ilt_solve per step over the whole batch
     "uneven64": dict(batch=64, sides=(512, 1024, 1536, 2048), K=24, iters=100, beta=7.5, seed=2000),
+    # modulation-branch labels (Sec. III-B): per clip a plain solve gives phi_gt, then 16
+    # candidate maps H(phi_gt + dh), dh ~ U[-20, 20], each solved (one devel_ilt_solve,
+    # one handle per candidate) and the smallest final L_DSO picked
+    "modgt256": dict(labels=16, n=256, K=8, k=15, iters=20, beta=7.5, seed=3000),
 }
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -664,6 +668,67 @@ def run_batched(args, wl):
         dist.destroy_process_group()
 
 
+def run_modgt(args, wl):
+    """Label generation for the modulation branch: one step = one clip's label (a plain
+    solve for phi_gt, the candidate maps, 16 candidate solves in one call, the argmin)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n, K, k, iters, beta, J = wl["n"], wl["K"], wl["k"], wl["iters"], wl["beta"], wl["labels"]
+    o = synth.optics(n, K, k)
+    base = dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
+    handles = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3) for _ in range(J)]
+    params = dv.ilt_params(dv.resist_params(beta=beta), iters=iters)
+    rng = np.random.default_rng(wl["seed"] + rank)
+    clips = [synth.rect_clip(wl["seed"] + 100 * rank + i) for i in range(max(args.steps, 1) + args.warmup)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def label(Zt):
+        tgt = torch.from_numpy(Zt.ravel().copy()).to(dev)
+        phi = torch.empty(n * n, dtype=torch.float32, device=dev)
+        dv.devel_ilt_solve(params, [dv.Clip(base, tgt, phi)], st, stream)
+        dh = rng.uniform(-20.0, 20.0, J).astype(np.float32)
+        return dv.modulation_search(handles, tgt, phi, dh, params, stream)[0]
+
+    for i in range(args.warmup):
+        label(clips[i])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    picks = []
+    for i in range(args.steps):
+        flush.zero_()
+        picks.append(label(clips[args.warmup + i]))
+    torch.cuda.synchronize()
+    ms = job_time_ms((time.perf_counter() - t0) * 1000.0 / max(args.steps, 1), dist, dev)
+    if rank == 0:
+        out = {"metric": "modulation-branch labels/sec (16 candidate DSO solves per clip, 256^2, 20 iterations)",
+               "value": world * 1000.0 / ms, "unit": "labels/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+               "config": {"workload": args.workload, "n": n, "K": K, "k": k, "iters": iters, "beta": beta,
+                          "candidates": J, "dh": "U[-20, 20]",
+                          "timing": "host clock around each label (the argmin reads the candidates' losses back)"},
+               "solves_per_s": world * (J + 1) * 1000.0 / ms, "picked": picks[:8]}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_calls_once(args, wl):
     """Each ABI call of the hot path once at the workload's size, through the public
     API (TSDF, forward, resist/loss, adjoint, level-set step), for kernel captures with
@@ -727,6 +792,8 @@ def main():
         run_calls_once(args, wl)
     elif "batch" in wl:
         run_batched(args, wl)
+    elif "labels" in wl:
+        run_modgt(args, wl)
     else:
         run_ours(args, wl)
 

@@ -11,6 +11,7 @@
  *   devel_litho_adjoint   Eqs. (ilt_gradient), (pvb_gradient), (vel)  dL/dM from dL/dI
  *   devel_levelset_step   Eqs. (dso_evolution), (numerical-settings), (curva_numer), (phi2mask)
  *   devel_cg_direction    Sec. III-C conjugate-gradient direction of the velocity
+ *   devel_modulation_candidates, devel_ahf_loss   Sec. III-B modulation-branch supervision
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
  *
  * Conventions shared by every call
@@ -322,6 +323,35 @@ typedef struct {
  */
 int devel_cg_direction(const devel_optics* optics, const float* V, float* Vprev, float* D, int restart,
                        double* beta_out, double* vmax_out, int* status, cudaStream_t stream);
+
+/*
+ * Supervision of the curvature modulation m_theta (Sec. III-B, modulation branch).
+ *
+ * Candidate maps: m_out[j][p] = H(phi_gt[p] + dh[j]) with the Heaviside of Eq.
+ * (heaviside), H(z) = 1 for z >= 0 (the sum in FP32), else 0; the paper draws dh
+ * from U[-20, 20]. The label m_gt is the candidate whose DSO run (a devel_ilt_solve
+ * with clip.m = m_out[j]) ends with the smallest L_DSO: run the candidates as clips of
+ * one devel_ilt_solve, each with a handle of its own to run them concurrently.
+ *   phi_gt  device float[n*n]           dh_host host float[ncand], finite
+ *   m_out   device float[ncand][n*n]    1 <= ncand <= DEVEL_MOD_MAX_CANDIDATES
+ */
+#define DEVEL_MOD_MAX_CANDIDATES 64
+int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const float* dh_host, float* m_out,
+                                cudaStream_t stream);
+
+/*
+ * Loss of the modulation branch against its label (Sec. III-B) with the approximated
+ * Heaviside H_eps(phi) = (1 + (2/pi) atan(phi / eps)) / 2 (the paper: eps = 0.03):
+ *   loss_out[0] = sum_p (H_eps(phi_m[p]) - m_gt[p])^2
+ *   grad_out[p] = 2 (H_eps(phi_m[p]) - m_gt[p]) (eps / pi) / (eps^2 + phi_m[p]^2)
+ * FP32 per pixel and within blocks, exact fixed point across blocks, FP64 result
+ * (NaN if any term is not finite).
+ *   phi_m, m_gt device float[n*n]   loss_out device double[1]
+ *   grad_out    device float[n*n] or NULL
+ * n is the handle's (its workspace holds the partial sums).
+ */
+int devel_ahf_loss(const devel_optics* optics, const float* phi_m, const float* m_gt, float eps,
+                   double* loss_out, float* grad_out, cudaStream_t stream);
 
 /*
  * Run `params->iters` DSO iterations on each clip (host array of nclips):

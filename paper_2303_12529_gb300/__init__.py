@@ -29,6 +29,7 @@ DEVEL_UPWIND_GODUNOV1 = 0
 DEVEL_UPWIND_WENO5 = 1
 DEVEL_OPT_STEEPEST = 0
 DEVEL_OPT_CG = 1
+DEVEL_MOD_MAX_CANDIDATES = 64
 DEVEL_PREC_FP32 = 0
 DEVEL_PREC_BF16X3 = 1
 
@@ -87,6 +88,8 @@ _sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
 _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
+_sig("devel_modulation_candidates", [_I, _P, _I, _P, _P, _P])
+_sig("devel_ahf_loss", [_P, _P, _P, _F, _P, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
@@ -107,7 +110,8 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_levelset_step", "devel_reinit_sdf", "devel_ilt_solve", "devel_profile_start",
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
-            "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction")
+            "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction",
+            "devel_modulation_candidates", "devel_ahf_loss")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -262,6 +266,50 @@ def devel_cg_direction(optics: Optics, V, Vprev, D, restart: bool, vmax, beta=No
                                    int(bool(restart)), _ptr(beta, torch.float64, 1, "beta"),
                                    _ptr(vmax, torch.float64, 1, "vmax"), _ptr(status, torch.int32, 1, "status"),
                                    _stream(stream)))
+
+
+def devel_modulation_candidates(n: int, phi_gt, dh, m_out, stream=None):
+    """m_out[j] = H(phi_gt + dh[j]) (Sec. III-B); m_out float32 [len(dh) * n * n]."""
+    import torch
+    N = n * n
+    dh_host = (ctypes.c_float * len(dh))(*[float(d) for d in dh])
+    _check(_lib.devel_modulation_candidates(n, _ptr(phi_gt, torch.float32, N, "phi_gt"), len(dh),
+                                            ctypes.cast(dh_host, _P), _ptr(m_out, torch.float32, N * len(dh), "m_out"),
+                                            _stream(stream)))
+
+
+def devel_ahf_loss(optics: Optics, phi_m, m_gt, eps: float, loss_out, grad_out=None, stream=None):
+    import torch
+    N = optics.n * optics.n
+    _check(_lib.devel_ahf_loss(optics.handle, _ptr(phi_m, torch.float32, N, "phi_m"),
+                               _ptr(m_gt, torch.float32, N, "m_gt"), float(eps),
+                               _ptr(loss_out, torch.float64, 1, "loss_out"),
+                               _ptr(grad_out, torch.float32, N, "grad_out"), _stream(stream)))
+
+
+def modulation_search(handles, target, phi_gt, dh, params: "devel_ilt_params", stream=None):
+    """The label search of Sec. III-B: candidate maps H(phi_gt + dh_j), one DSO solve per
+    candidate (the candidates are the clips of one devel_ilt_solve; handle j serves
+    candidate j, so distinct handles run concurrently), and the index of the smallest
+    final L_DSO (ties: the first). Returns (index, final losses as a host array,
+    candidate maps [len(dh), n*n])."""
+    import numpy as np
+    import torch
+    n = handles[0].n
+    N = n * n
+    dev = target.device
+    cands = torch.empty(len(dh) * N, dtype=torch.float32, device=dev)
+    devel_modulation_candidates(n, phi_gt, dh, cands, stream)
+    H = params.iters + 1
+    hist = torch.zeros(len(dh), (H + 1) // 2 * 2, dtype=torch.float64, device=dev)  # rows 16-byte aligned
+    clips = [Clip(handles[j], target, torch.empty(N, dtype=torch.float32, device=dev), m=cands[j * N:(j + 1) * N],
+                  loss_hist=hist[j, :H]) for j in range(len(dh))]
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    devel_ilt_solve(params, clips, st, stream)
+    final = hist[:, H - 1].cpu().numpy()   # the only device-to-host read: len(dh) doubles
+    if int(st.item()) != 0:
+        raise DevelError(int(st.item()), "modulation_search: a candidate solve reported a non-finite loss")
+    return int(np.argmin(final)), final, cands.view(len(dh), N)
 
 
 def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):

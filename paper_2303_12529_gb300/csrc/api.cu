@@ -539,7 +539,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.loss4, sizeof(double) * 4);
     ALLOC(o->ws.cnt2, sizeof(long long) * 2);
     ALLOC(o->tc_err, sizeof(int));
-    ALLOC(o->ws.counters, sizeof(unsigned) * 4);
+    ALLOC(o->ws.counters, sizeof(unsigned) * 8);
     ALLOC(o->ws.cgpart, sizeof(float) * 3 * cg_parts(n));
     ALLOC(o->ws.cgvpart, sizeof(float) * cg_parts(n));
     ALLOC(o->ws.cgbeta, sizeof(float));
@@ -622,7 +622,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     for (const Cp& c : cps)
         if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h, c.bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(o->tc_err, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(o->ws.counters, 0, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemset(o->ws.counters, 0, sizeof(unsigned) * 8);
     if (e != cudaSuccess) {
         free_optics(o);
         return cuda_error(e, "devel_optics_create: cudaMemcpy");
@@ -855,6 +855,33 @@ int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, floa
     int rc = init_device_attrs();
     if (rc) return rc;
     return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s);
+}
+
+int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const float* dh_host, float* m_out,
+                                cudaStream_t s) {
+    if (n < 1 || n > 8192) return set_error(DEVEL_EINVAL, "devel_modulation_candidates: n=%d outside [1, 8192]", n);
+    if (ncand < 1 || ncand > DEVEL_MOD_MAX_CANDIDATES)
+        return set_error(DEVEL_EINVAL, "devel_modulation_candidates: ncand=%d outside [1, %d]", ncand,
+                         DEVEL_MOD_MAX_CANDIDATES);
+    CHECK_PTR(phi_gt, "phi_gt");
+    CHECK_PTR(m_out, "m_out");
+    if (!dh_host) return set_error(DEVEL_EINVAL, "devel_modulation_candidates: dh_host is NULL");
+    for (int j = 0; j < ncand; ++j)
+        if (!std::isfinite(dh_host[j]))
+            return set_error(DEVEL_EINVAL, "devel_modulation_candidates: dh[%d] is not finite", j);
+    return launch_mod_candidates(n, phi_gt, ncand, dh_host, m_out, s);
+}
+
+int devel_ahf_loss(const devel_optics* o, const float* phi_m, const float* m_gt, float eps, double* loss_out,
+                   float* grad_out, cudaStream_t s) {
+    if (!o) return set_error(DEVEL_EINVAL, "devel_ahf_loss: optics is NULL");
+    CHECK_PTR(phi_m, "phi_m");
+    CHECK_PTR(m_gt, "m_gt");
+    CHECK_PTR(loss_out, "loss_out");
+    CHECK_OPT_PTR(grad_out, "grad_out");
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_error(DEVEL_EINVAL, "devel_ahf_loss: eps must be > 0");
+    return launch_ahf_loss(o->n, phi_m, m_gt, eps, grad_out, o->ws.qpart, o->npart_red, o->ws.counters + 4, loss_out,
+                           s);
 }
 
 int devel_cg_direction(const devel_optics* o, const float* V, float* Vprev, float* D, int restart,

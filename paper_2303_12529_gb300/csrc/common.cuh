@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA sources of libdevelset.
 #pragma once
 
+#include <climits>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -108,6 +110,23 @@ __device__ __forceinline__ void vmax_last_block(const float* vpart, int nparts, 
     }
 }
 
+// x * 2^32 as an int64, rounded toward zero, from the bits of an FP32 value with
+// |x| < 2^30 (integer ALU only: FP64 instructions are slow here); kQBad for a
+// non-finite x. Summing these is exact and independent of the order; a partial of
+// squared errors of values in [0, 1] (each term <= 1) never approaches 2^30.
+constexpr long long kQBad = LLONG_MIN;
+__device__ __forceinline__ long long to_q32(float x) {
+    const unsigned u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xffu);
+    if (e == 0xff) return kQBad;
+    if (e == 0) return 0;  // zero or subnormal
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+    const int sh = e - 118;  // x 2^32 = m 2^(e - 127 - 23 + 32)
+    if (sh > 38) return kQBad;
+    const long long q = sh >= 0 ? (m << sh) : (sh <= -24 ? 0 : (m >> -sh));
+    return (u >> 31) ? -q : q;
+}
+
 // Device-side limit of the window side handled by the FP32 kernels.
 constexpr int kMaxWindow = 63;
 
@@ -143,8 +162,8 @@ struct Workspace {
     double* vmax = nullptr;    // [1]
     double* loss4 = nullptr;   // [4]
     long long* cnt2 = nullptr; // [2]
-    unsigned* counters = nullptr;  // [4] zeroed: last-block counters (0: resist, 1: max |V|,
-                                   //     2: CG dot products, 3: max |D|)
+    unsigned* counters = nullptr;  // [8] zeroed: last-block counters (0: resist, 1: max |V|,
+                                   //     2: CG dot products, 3: max |D|, 4: AHF loss)
     // conjugate-gradient state (Sec. III-C)
     float* cgpart = nullptr;   // [3 * cg_parts] FP32 block sums of V.V, V.Vp, Vp.Vp
     float* cgvpart = nullptr;  // [cg_parts] per-block max |D|
@@ -246,6 +265,11 @@ int launch_resist_defocus(int n, const float* In, const float* Id, const unsigne
 // levelset.cu
 // mask_bf (optional): the new mask also as a bf16 [n][ldb] operand of the next reduction
 // upwind: DEVEL_UPWIND_GODUNOV1 or DEVEL_UPWIND_WENO5 (one-sided derivatives of |grad phi|)
+// modulation.cu: candidate maps H(phi + dh_j) (m: float[ncand][n*n]); AHF loss (qpart:
+// long long[>= nparts], counter: one zeroed word, loss: device double).
+int launch_mod_candidates(int n, const float* phi, int ncand, const float* dh_host, float* m, cudaStream_t s);
+int launch_ahf_loss(int n, const float* phi, const float* mgt, float eps, float* grad, long long* qpart, int nparts,
+                    unsigned* counter, double* loss, cudaStream_t s);
 // cg.cu: D = V + beta D (PR+ beta from V, Vp; restart: D = V), Vp = V, max|D| -> vmax.
 // part: float[3 * cg_parts(n)], vpart: float[cg_parts(n)], counters: 2 zeroed words.
 int cg_parts(int n);

@@ -2,8 +2,6 @@
 // fixed-order block reduction of the loss partials.
 #pragma once
 
-#include <climits>
-
 #include "common.cuh"
 
 namespace devel {
@@ -99,23 +97,6 @@ __device__ __forceinline__ float resist_px2(float In, float Id, bool zt_on, cons
     a.pvb += ((p.d2in * Id >= p.I_th) != (p.d2out * In >= p.I_th));
     gD = (p.k_in * ei) * ci.ez2;
     return fmaf(p.k_out * eo, co.ez2, (p.k_nom * en) * cn.ez2);
-}
-
-// x * 2^32 as an int64, rounded toward zero, from the bits of an FP32 value with
-// |x| < 2^30 (integer ALU only: FP64 instructions are slow here); kQBad for a
-// non-finite x. Summing these is exact and independent of the order; a partial of
-// e^2 terms (each <= 1) never approaches 2^30.
-constexpr long long kQBad = LLONG_MIN;
-__device__ __forceinline__ long long to_q32(float x) {
-    const unsigned u = __float_as_uint(x);
-    const int e = (int)((u >> 23) & 0xffu);
-    if (e == 0xff) return kQBad;
-    if (e == 0) return 0;  // zero or subnormal
-    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
-    const int sh = e - 118;  // x 2^32 = m 2^(e - 127 - 23 + 32)
-    if (sh > 38) return kQBad;
-    const long long q = sh >= 0 ? (m << sh) : (sh <= -24 ? 0 : (m >> -sh));
-    return (u >> 31) ? -q : q;
 }
 
 // Reduction of the accumulators of each group of 256 threads (a logical block) in a
