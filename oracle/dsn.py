@@ -1,0 +1,186 @@
+"""Level-set branch of DevelSet-Net (DSN), FP64 (test infrastructure only).
+
+Sec. III-B: a convolutional encoder-decoder maps the target image to an initial
+level-set function phi_0 for DSO, trained with the mean squared error to the
+level set that DSO converges to (phi_gt); DSO then refines it (Sec. III-C). The paper
+gives no layer list. Reading (the scope's learned-initialisation workload): four
+levels with widths c, 2c, 4c, 8c (c = 32: 32 .. 256 channels), two 3x3 convolutions
+(zero padding 1, bias, ReLU) per level, 2x2 average pooling down, nearest-neighbour
+2x upsampling up, the encoder's level output concatenated after the upsampled
+decoder input (channels [up, skip]), and a 1x1 convolution to one channel.
+
+Input and output are band-limited level sets: x = clip(TSDF(Z_t), -B, B) / B and the
+network predicts y = x + head(...) (a residual on the target's own TSDF, so a
+network with zero head weights returns the plain DSO start); phi_0 = B y. Labels are
+clip(phi_gt, -B, B) / B with B = 16 pixels; the loss is the mean over pixels of
+(y - label)^2.
+
+Tensors are NCHW float64. Parameters are a flat list in layer order, each layer's
+weight [cout][cin][k][k] then bias [cout]; Adam (Kingma & Ba) updates them.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+BAND = 16.0
+
+
+def layer_shapes(c: int):
+    """(cin, cout, k) of every convolution, in order."""
+    L = []
+    w = [c, 2 * c, 4 * c, 8 * c]
+    cin = 1
+    for lv in range(4):                       # encoder levels 1..3 and the bottleneck
+        L += [(cin, w[lv], 3), (w[lv], w[lv], 3)]
+        cin = w[lv]
+    for lv in (2, 1, 0):                      # decoder: up(from level lv+1) ++ skip(level lv)
+        L += [(w[lv + 1] + w[lv], w[lv], 3), (w[lv], w[lv], 3)]
+    L.append((w[0], 1, 1))                    # head
+    return L
+
+
+def init_params(c: int, seed: int):
+    """He-normal weights, zero biases (seeded)."""
+    rng = np.random.default_rng(seed)
+    P = []
+    for cin, cout, k in layer_shapes(c):
+        std = np.sqrt(2.0 / (cin * k * k))
+        P.append(rng.standard_normal((cout, cin, k, k)) * std)
+        P.append(np.zeros(cout))
+    return P
+
+
+def conv(x, W, b):
+    """Cross-correlation with zero padding (k - 1) / 2: y[n,o,i,j] = b[o] +
+    sum_{c,u,v} W[o,c,u,v] x[n,c,i+u-r,j+v-r]."""
+    k = W.shape[2]
+    r = (k - 1) // 2
+    N, C, H, Wd = x.shape
+    xp = np.pad(x, ((0, 0), (0, 0), (r, r), (r, r)))
+    y = np.zeros((N, W.shape[0], H, Wd))
+    for u in range(k):
+        for v in range(k):
+            y += np.einsum("oc,nchw->nohw", W[:, :, u, v], xp[:, :, u:u + H, v:v + Wd])
+    return y + b[None, :, None, None]
+
+
+def conv_backward(x, W, dy):
+    """Gradients of conv: (dx, dW, db)."""
+    k = W.shape[2]
+    r = (k - 1) // 2
+    N, C, H, Wd = x.shape
+    xp = np.pad(x, ((0, 0), (0, 0), (r, r), (r, r)))
+    dxp = np.zeros_like(xp)
+    dW = np.zeros_like(W)
+    for u in range(k):
+        for v in range(k):
+            dW[:, :, u, v] = np.einsum("nohw,nchw->oc", dy, xp[:, :, u:u + H, v:v + Wd])
+            dxp[:, :, u:u + H, v:v + Wd] += np.einsum("oc,nohw->nchw", W[:, :, u, v], dy)
+    return dxp[:, :, r:r + H, r:r + Wd], dW, dy.sum(axis=(0, 2, 3))
+
+
+def avgpool(x):
+    N, C, H, W = x.shape
+    return x.reshape(N, C, H // 2, 2, W // 2, 2).mean(axis=(3, 5))
+
+
+def avgpool_backward(dy):
+    return np.repeat(np.repeat(dy, 2, axis=2), 2, axis=3) / 4.0
+
+
+def upsample(x):
+    return np.repeat(np.repeat(x, 2, axis=2), 2, axis=3)
+
+
+def upsample_backward(dy):
+    N, C, H, W = dy.shape
+    return dy.reshape(N, C, H // 2, 2, W // 2, 2).sum(axis=(3, 5))
+
+
+def forward(P, x):
+    """Returns (y, cache). x: [N, 1, S, S] band-limited input level set."""
+    cache = []
+    li = [0]
+
+    def cv(h, relu=True):
+        W, b = P[2 * li[0]], P[2 * li[0] + 1]
+        li[0] += 1
+        z = conv(h, W, b)
+        out = np.maximum(z, 0.0) if relu else z
+        cache.append((h, W, out, relu))
+        return out
+
+    h = x
+    skips = []
+    for lv in range(4):
+        if lv > 0:
+            h = avgpool(h)
+        h = cv(cv(h))
+        skips.append(h)
+    for lv in (2, 1, 0):
+        h = np.concatenate([upsample(h), skips[lv]], axis=1)
+        h = cv(cv(h))
+    y = x + cv(h, relu=False)
+    return y, (cache, skips)
+
+
+def backward(P, x, cache, dy):
+    """Gradients of the parameters (flat list in P's order) for dL/dy = dy."""
+    convs, skips = cache
+    G = [None] * len(P)
+    ci = [len(convs)]
+
+    def cvb(dout):
+        ci[0] -= 1
+        h, W, out, relu = convs[ci[0]]
+        dz = dout * (out > 0) if relu else dout
+        dh, dW, db = conv_backward(h, W, dz)
+        G[2 * ci[0]], G[2 * ci[0] + 1] = dW, db
+        return dh
+
+    dh = cvb(dy)                                   # head
+    dskip = [np.zeros_like(s) for s in skips]
+    for lv in (0, 1, 2):                           # decoder in reverse
+        dcat = cvb(cvb(dh))
+        cu = dcat.shape[1] - skips[lv].shape[1]
+        dskip[lv] += dcat[:, cu:]
+        dh = upsample_backward(dcat[:, :cu])
+    for lv in (3, 2, 1, 0):                        # encoder in reverse
+        dh = dh + dskip[lv] if lv < 3 else dh
+        dh = cvb(cvb(dh))
+        if lv > 0:
+            dh = avgpool_backward(dh)
+    return G
+
+
+def mse(y, label):
+    d = y - label
+    return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+@dataclass
+class Adam:
+    lr: float = 1e-3
+    b1: float = 0.9
+    b2: float = 0.999
+    eps: float = 1e-8
+    t: int = 0
+
+    def step(self, P, G, state):
+        """One update of every parameter; state = list of (m, v), created on first use."""
+        self.t += 1
+        if not state:
+            state.extend((np.zeros_like(p), np.zeros_like(p)) for p in P)
+        c1 = 1.0 - self.b1 ** self.t
+        c2 = 1.0 - self.b2 ** self.t
+        for i, (p, g) in enumerate(zip(P, G)):
+            m, v = state[i]
+            m[...] = self.b1 * m + (1.0 - self.b1) * g
+            v[...] = self.b2 * v + (1.0 - self.b2) * g * g
+            p -= self.lr * (m / c1) / (np.sqrt(v / c2) + self.eps)
+
+
+def band(phi, B: float = BAND):
+    return np.clip(np.asarray(phi, dtype=np.float64), -B, B) / B

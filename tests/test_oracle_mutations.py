@@ -121,3 +121,23 @@ def test_ahf_with_eps_on_the_wrong_side_is_caught(monkeypatch):
     monkeypatch.setattr(modulation, "ahf",
                         lambda phi, eps: 0.5 * (1.0 + (2.0 / np.pi) * np.arctan(np.asarray(phi, float) * eps)))
     _fails(tm.test_ahf_identities)
+
+
+def test_avgpool_backward_without_the_quarter_is_caught(monkeypatch):
+    from oracle import dsn
+    import test_oracle_dsn as td
+    monkeypatch.setattr(dsn, "avgpool_backward", lambda dy: np.repeat(np.repeat(dy, 2, axis=2), 2, axis=3))
+    _fails(td.test_pool_and_upsample_adjoint_pairs)
+    _fails(td.test_network_gradient_matches_finite_differences)
+
+
+def test_conv_backward_with_the_taps_mirrored_is_caught(monkeypatch):
+    from oracle import dsn
+    import test_oracle_dsn as td
+    orig = dsn.conv_backward
+
+    def mirrored(x, W, dy):
+        dx, dW, db = orig(x, W[:, :, ::-1, ::-1], dy)
+        return dx, dW, db
+    monkeypatch.setattr(dsn, "conv_backward", mirrored)
+    _fails(td.test_conv_backward_matches_finite_differences)
