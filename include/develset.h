@@ -12,6 +12,7 @@
  *   devel_levelset_step   Eqs. (dso_evolution), (numerical-settings), (curva_numer), (phi2mask)
  *   devel_cg_direction    Sec. III-C conjugate-gradient direction of the velocity
  *   devel_modulation_candidates, devel_ahf_loss   Sec. III-B modulation-branch supervision
+ *   devel_dsn_*           Sec. III-B DSN level-set branch: learned initial level set, training
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
  *
  * Conventions shared by every call
@@ -352,6 +353,40 @@ int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const flo
  */
 int devel_ahf_loss(const devel_optics* optics, const float* phi_m, const float* m_gt, float eps,
                    double* loss_out, float* grad_out, cudaStream_t stream);
+
+/*
+ * Level-set branch of DevelSet-Net (Sec. III-B): a convolutional encoder-decoder
+ * that predicts the initial level set of DSO from the target (the paper gives no
+ * layer list; this one has four levels of widths w, 2w, 4w, 8w with two 3x3
+ * convolutions + ReLU each, 2x2 average pooling, nearest 2x upsampling with the
+ * encoder's level concatenated after it, and a 1x1 head added to the input).
+ * Input x = clip(tsdf, -band, band) / band of the target's TSDF; output
+ * phi0 = band * (x + head(...)), so zero head weights give back the band-limited
+ * TSDF (the plain DSO start). Trained with the mean squared error between
+ * x + head and clip(phi_gt, -band, band) / band (phi_gt: the level set DSO
+ * converges to) and Adam (lr given, beta1 0.9, beta2 0.999, eps 1e-8).
+ * Activations BF16, weights used in BF16 (FP32 master copy), FP32 accumulation,
+ * FP32 gradients; reductions in a fixed order (reproducible).
+ * Tensors are device float [nb][side][side], nb <= batch; side a multiple of 16.
+ * Parameters: a flat FP32 vector, per layer (in the order above, head last) the
+ * weights [cout][cin][k][k] then the biases [cout].
+ */
+typedef struct devel_dsn devel_dsn;
+int devel_dsn_create(int side, int batch, int width, devel_dsn** out);
+int devel_dsn_destroy(devel_dsn* dsn);
+long long devel_dsn_param_count(const devel_dsn* dsn);
+/* He-normal weights (splitmix64 + Box-Muller from seed), zero biases; resets Adam. */
+int devel_dsn_init(devel_dsn* dsn, unsigned long long seed);
+/* Host float[param_count] in / out (synchronous); set_params resets Adam. */
+int devel_dsn_set_params(devel_dsn* dsn, const float* host);
+int devel_dsn_get_params(const devel_dsn* dsn, float* host);
+/* Gradients of the last train step, host float[param_count] (synchronous). */
+int devel_dsn_grads(const devel_dsn* dsn, float* host);
+int devel_dsn_forward(devel_dsn* dsn, int nb, const float* tsdf, float band, float* phi0, cudaStream_t stream);
+/* One Adam step on a batch; loss_out: device double[1] (mean squared error before the
+ * step) or NULL. */
+int devel_dsn_train_step(devel_dsn* dsn, int nb, const float* tsdf, const float* phi_gt, float band, float lr,
+                         double* loss_out, cudaStream_t stream);
 
 /*
  * Run `params->iters` DSO iterations on each clip (host array of nclips):

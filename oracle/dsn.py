@@ -99,24 +99,30 @@ def upsample_backward(dy):
     return dy.reshape(N, C, H // 2, 2, W // 2, 2).sum(axis=(3, 5))
 
 
-def forward(P, x):
-    """Returns (y, cache). x: [N, 1, S, S] band-limited input level set."""
+def forward(P, x, store=None):
+    """Returns (y, cache). x: [N, 1, S, S] band-limited input level set.
+
+    store: optional rounding applied where a storage format is narrower than FP64
+    (the stored activations, the weights a convolution uses, the first layer's input;
+    e.g. BF16), so that decisions taken on stored values (the ReLU masks of the
+    backward pass) can be reproduced in another precision. None: plain FP64."""
+    rnd = store if store is not None else (lambda a: a)
     cache = []
     li = [0]
 
     def cv(h, relu=True):
-        W, b = P[2 * li[0]], P[2 * li[0] + 1]
+        W, b = rnd(P[2 * li[0]]), P[2 * li[0] + 1]
         li[0] += 1
         z = conv(h, W, b)
-        out = np.maximum(z, 0.0) if relu else z
+        out = rnd(np.maximum(z, 0.0)) if relu else z
         cache.append((h, W, out, relu))
         return out
 
-    h = x
+    h = rnd(x)
     skips = []
     for lv in range(4):
         if lv > 0:
-            h = avgpool(h)
+            h = rnd(avgpool(h))
         h = cv(cv(h))
         skips.append(h)
     for lv in (2, 1, 0):

@@ -90,6 +90,15 @@ _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
 _sig("devel_modulation_candidates", [_I, _P, _I, _P, _P, _P])
 _sig("devel_ahf_loss", [_P, _P, _P, _F, _P, _P, _P])
+_sig("devel_dsn_create", [_I, _I, _I, ctypes.POINTER(_P)])
+_sig("devel_dsn_destroy", [_P])
+_sig("devel_dsn_param_count", [_P], ctypes.c_longlong)
+_sig("devel_dsn_init", [_P, ctypes.c_ulonglong])
+_sig("devel_dsn_set_params", [_P, _P])
+_sig("devel_dsn_get_params", [_P, _P])
+_sig("devel_dsn_grads", [_P, _P])
+_sig("devel_dsn_forward", [_P, _I, _P, _F, _P, _P])
+_sig("devel_dsn_train_step", [_P, _I, _P, _P, _F, _F, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
@@ -111,7 +120,9 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
             "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction",
-            "devel_modulation_candidates", "devel_ahf_loss")
+            "devel_modulation_candidates", "devel_ahf_loss", "devel_dsn_create", "devel_dsn_destroy",
+            "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
+            "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -310,6 +321,62 @@ def modulation_search(handles, target, phi_gt, dh, params: "devel_ilt_params", s
     if int(st.item()) != 0:
         raise DevelError(int(st.item()), "modulation_search: a candidate solve reported a non-finite loss")
     return int(np.argmin(final)), final, cands.view(len(dh), N)
+
+
+class Dsn:
+    """Owner of a ``devel_dsn*`` (the DSN level-set branch, Sec. III-B)."""
+
+    def __init__(self, side: int, batch: int, width: int = 32, seed: int = 0):
+        h = _P()
+        _check(_lib.devel_dsn_create(side, batch, width, ctypes.byref(h)))
+        self.handle, self.side, self.batch, self.width = h.value, side, batch, width
+        _check(_lib.devel_dsn_init(self.handle, seed))
+
+    def close(self):
+        if self.handle:
+            _lib.devel_dsn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self) -> int:
+        return int(_lib.devel_dsn_param_count(self.handle))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.param_count, dtype=np.float32)
+        _check(_lib.devel_dsn_get_params(self.handle, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.param_count
+        _check(_lib.devel_dsn_set_params(self.handle, p.ctypes.data))
+
+    def grads(self):
+        import numpy as np
+        out = np.empty(self.param_count, dtype=np.float32)
+        _check(_lib.devel_dsn_grads(self.handle, out.ctypes.data))
+        return out
+
+    def forward(self, nb: int, tsdf, phi0, band: float = 16.0, stream=None):
+        import torch
+        N = nb * self.side * self.side
+        _check(_lib.devel_dsn_forward(self.handle, nb, _ptr(tsdf, torch.float32, N, "tsdf"), float(band),
+                                      _ptr(phi0, torch.float32, N, "phi0"), _stream(stream)))
+
+    def train_step(self, nb: int, tsdf, phi_gt, lr: float, loss_out=None, band: float = 16.0, stream=None):
+        import torch
+        N = nb * self.side * self.side
+        _check(_lib.devel_dsn_train_step(self.handle, nb, _ptr(tsdf, torch.float32, N, "tsdf"),
+                                         _ptr(phi_gt, torch.float32, N, "phi_gt"), float(band), float(lr),
+                                         _ptr(loss_out, torch.float64, 1, "loss_out"), _stream(stream)))
 
 
 def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):

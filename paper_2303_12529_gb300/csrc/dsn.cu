@@ -1,0 +1,745 @@
+// Level-set branch of DevelSet-Net (Sec. III-B): a 4-level convolutional
+// encoder-decoder that maps the band-limited TSDF of a target to an initial level set
+// for DSO, with its training step (MSE to the level set DSO converges to, Adam).
+//
+// Layers (width c): per encoder level two 3x3 convolutions (zero padding, bias, ReLU)
+// of widths c, 2c, 4c, 8c with 2x2 average pooling between levels; per decoder level
+// nearest 2x upsampling, concatenation [upsampled, encoder skip] and two 3x3
+// convolutions; a 1x1 head added to the input (y = x + head). Tensors are NCHW;
+// activations are stored in BF16, weights used in BF16 (FP32 master copy, updated by
+// Adam), every sum accumulates in FP32; gradients are FP32.
+//
+// Kernels (SIMT): k_conv3 (forward, and the input gradient as a convolution of the
+// output gradient with the flipped, transposed weights), k_conv3_wgrad (weight
+// gradients per spatial tile) + k_wgrad_reduce (fixed-order sum over tiles),
+// k_bias_grad, k_relu_mask, pooling / upsampling and their adjoints, the head, the MSE
+// and Adam. Every reduction runs in a fixed order: results are reproducible.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+struct devel_dsn;
+
+namespace devel {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kT = 16;      // output tile side
+constexpr int kCoB = 16;    // output channels per block (forward)
+constexpr int kCiC = 8;     // input channels per shared-memory chunk (forward)
+constexpr int kWC = 16;     // channels per block side (weight gradients)
+
+__device__ __forceinline__ float ld(const bf16* p, size_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
+
+// Y[n][co][y][x] = bias[co] + sum_{ci,u,v} W[co][ci][u][v] X[n][ci][y+u-1][x+v-1], X the
+// concatenation [XA (CA channels), XB (CB channels)] along channels, zero outside.
+// Output: bf16 (optional ReLU) into YA, or FP32 (stored or added) split along output
+// channels into YA (the first CYA channels) and YB.
+template <typename Tin, bool kBf16Out>
+__global__ void __launch_bounds__(256)
+k_conv3(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const bf16* __restrict__ W,
+        const float* __restrict__ bias, int relu, void* YA, int CYA, float* YB, int accumulate, int H, int Wd,
+        int Cout) {
+    __shared__ float patch[kCiC][kT + 2][kT + 2];
+    __shared__ __align__(16) float wsm[kCiC][9][kCoB];
+    const int tilesx = (Wd + kT - 1) / kT;
+    const int x0 = (blockIdx.x % tilesx) * kT, y0 = (blockIdx.x / tilesx) * kT;
+    const int co0 = blockIdx.y * kCoB, n = blockIdx.z;
+    const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;
+    const int Cin = CA + CB;
+    const size_t plane = (size_t)H * Wd;
+    float acc[kCoB];
+#pragma unroll
+    for (int j = 0; j < kCoB; ++j) acc[j] = 0.f;
+    for (int ci0 = 0; ci0 < Cin; ci0 += kCiC) {
+        for (int i = threadIdx.x; i < kCiC * (kT + 2) * (kT + 2); i += 256) {
+            const int c = i / ((kT + 2) * (kT + 2)), r = (i / (kT + 2)) % (kT + 2), q = i % (kT + 2);
+            const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
+            float v = 0.f;
+            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
+                const size_t off = (size_t)gy * Wd + gx;
+                v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
+                            : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
+            }
+            patch[c][r][q] = v;
+        }
+        for (int i = threadIdx.x; i < kCiC * 9 * kCoB; i += 256) {
+            const int c = i / (9 * kCoB), tap = (i / kCoB) % 9, co = i % kCoB;
+            const int ci = ci0 + c, o = co0 + co;
+            wsm[c][tap][co] = (ci < Cin && o < Cout) ? __bfloat162float(W[((size_t)o * Cin + ci) * 9 + tap]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int c = 0; c < kCiC; ++c) {
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const float v = patch[c][ty + tap / 3][tx + tap % 3];
+                const float4* w4 = reinterpret_cast<const float4*>(wsm[c][tap]);
+#pragma unroll
+                for (int j = 0; j < kCoB / 4; ++j) {
+                    const float4 w = w4[j];
+                    acc[4 * j + 0] = fmaf(v, w.x, acc[4 * j + 0]);
+                    acc[4 * j + 1] = fmaf(v, w.y, acc[4 * j + 1]);
+                    acc[4 * j + 2] = fmaf(v, w.z, acc[4 * j + 2]);
+                    acc[4 * j + 3] = fmaf(v, w.w, acc[4 * j + 3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int y = y0 + ty, x = x0 + tx;
+    if (y >= H || x >= Wd) return;
+    const size_t off = (size_t)y * Wd + x;
+#pragma unroll
+    for (int j = 0; j < kCoB; ++j) {
+        const int o = co0 + j;
+        if (o >= Cout) break;
+        float v = acc[j] + (bias ? bias[o] : 0.f);
+        if (kBf16Out) {
+            if (relu) v = fmaxf(v, 0.f);
+            static_cast<bf16*>(YA)[((size_t)n * Cout + o) * plane + off] = __float2bfloat16_rn(v);
+        } else {
+            float* dst = o < CYA ? static_cast<float*>(YA) + ((size_t)n * CYA + o) * plane + off
+                                 : YB + ((size_t)n * (Cout - CYA) + (o - CYA)) * plane + off;
+            *dst = accumulate ? *dst + v : v;
+        }
+    }
+}
+
+// Per spatial tile: part[tile][co][ci][9] = sum_n sum_{tile px} dZ[n][co][p] X[n][ci][p + tap]
+template <typename Tin>
+__global__ void __launch_bounds__(256)
+k_conv3_wgrad(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const float* __restrict__ dZ,
+              int Cout, int N, int H, int Wd, float* __restrict__ part) {
+    __shared__ float dz[kWC][kT][kT];
+    __shared__ float xp[kWC][kT + 2][kT + 2];
+    const int tilesx = (Wd + kT - 1) / kT;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % tilesx) * kT, y0 = (tile / tilesx) * kT;
+    const int co0 = blockIdx.y * kWC, ci0 = blockIdx.z * kWC;
+    const int col = threadIdx.x / kWC, cil = threadIdx.x % kWC;
+    const int Cin = CA + CB;
+    const size_t plane = (size_t)H * Wd;
+    float acc[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+    for (int n = 0; n < N; ++n) {
+        for (int i = threadIdx.x; i < kWC * kT * kT; i += 256) {
+            const int c = i / (kT * kT), r = (i / kT) % kT, q = i % kT;
+            const int o = co0 + c, gy = y0 + r, gx = x0 + q;
+            dz[c][r][q] = (o < Cout && gy < H && gx < Wd) ? dZ[((size_t)n * Cout + o) * plane + (size_t)gy * Wd + gx]
+                                                         : 0.f;
+        }
+        for (int i = threadIdx.x; i < kWC * (kT + 2) * (kT + 2); i += 256) {
+            const int c = i / ((kT + 2) * (kT + 2)), r = (i / (kT + 2)) % (kT + 2), q = i % (kT + 2);
+            const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
+            float v = 0.f;
+            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
+                const size_t off = (size_t)gy * Wd + gx;
+                v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
+                            : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
+            }
+            xp[c][r][q] = v;
+        }
+        __syncthreads();
+        for (int r = 0; r < kT; ++r) {
+#pragma unroll 4
+            for (int q = 0; q < kT; ++q) {
+                const float d = dz[col][r][q];
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc[t] = fmaf(d, xp[cil][r + t / 3][q + t % 3], acc[t]);
+            }
+        }
+        __syncthreads();
+    }
+    const int o = co0 + col, ci = ci0 + cil;
+    if (o < Cout && ci < Cin) {
+        float* dst = part + (((size_t)tile * Cout + o) * Cin + ci) * 9;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) dst[t] = acc[t];
+    }
+}
+
+// G[i] = sum over tiles of part[tile][i], in tile order
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int ntiles, size_t count, float* __restrict__ G) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int t = 0; t < ntiles; ++t) s += part[(size_t)t * count + i];
+    G[i] = s;
+}
+
+// fixed-order block sum of 256 values; valid in thread 0
+__device__ __forceinline__ float block_sum256(float v, float* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) s += sh[i];
+    return s;
+}
+
+// gb[c] = sum_{n,p} dZ[n][c][p] (one block per channel)
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ dZ, int C, int N, size_t plane,
+                                                   float* __restrict__ gb) {
+    __shared__ float sh[8];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int n = 0; n < N; ++n) {
+        const float* p = dZ + ((size_t)n * C + c) * plane;
+        for (size_t i = threadIdx.x; i < plane; i += 256) s += p[i];
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) gb[c] = s;
+}
+
+__global__ void k_relu_mask(float* __restrict__ dZ, const bf16* __restrict__ out, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(out[i]) > 0.f)) dZ[i] = 0.f;
+}
+
+__global__ void k_avgpool(const bf16* __restrict__ X, int H, int Wd, size_t planes, bf16* __restrict__ Y) {
+    const int h = H / 2, w = Wd / 2;
+    const size_t count = planes * h * w;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pl = i / ((size_t)h * w);
+        const int r = (int)((i / w) % h), q = (int)(i % w);
+        const bf16* p = X + pl * H * Wd + (size_t)(2 * r) * Wd + 2 * q;
+        const float s = (__bfloat162float(p[0]) + __bfloat162float(p[1])) +
+                        (__bfloat162float(p[Wd]) + __bfloat162float(p[Wd + 1]));
+        Y[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// dX[2r+i][2q+j] (+)= dY[r][q] / 4
+__global__ void k_avgpool_bwd(const float* __restrict__ dY, int H, int Wd, size_t planes, float* __restrict__ dX,
+                              int accumulate) {
+    const size_t count = planes * H * Wd;
+    const int w = Wd / 2;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pl = i / ((size_t)H * Wd);
+        const int r = (int)((i / Wd) % H), q = (int)(i % Wd);
+        const float v = 0.25f * dY[pl * (H / 2) * w + (size_t)(r / 2) * w + q / 2];
+        dX[i] = accumulate ? dX[i] + v : v;
+    }
+}
+
+__global__ void k_upsample(const bf16* __restrict__ X, int h, int w, size_t planes, bf16* __restrict__ Y) {
+    const size_t count = planes * 4 * h * w;
+    const int W2 = 2 * w;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pl = i / ((size_t)4 * h * w);
+        const int r = (int)((i / W2) % (2 * h)), q = (int)(i % W2);
+        Y[i] = X[pl * h * w + (size_t)(r / 2) * w + q / 2];
+    }
+}
+
+// dX[r][q] = sum of the four dY values it was copied to
+__global__ void k_upsample_bwd(const float* __restrict__ dY, int h, int w, size_t planes, float* __restrict__ dX) {
+    const size_t count = planes * h * w;
+    const int W2 = 2 * w;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pl = i / ((size_t)h * w);
+        const int r = (int)((i / w) % h), q = (int)(i % w);
+        const float* p = dY + pl * 4 * h * w + (size_t)(2 * r) * W2 + 2 * q;
+        dX[i] = (p[0] + p[1]) + (p[W2] + p[W2 + 1]);
+    }
+}
+
+// y[n][p] = x[n][p] + b + sum_c w[c] d[n][c][p]
+__global__ void k_head(const float* __restrict__ x, const bf16* __restrict__ d, const float* __restrict__ w,
+                       const float* __restrict__ b, int C, int N, size_t plane, float* __restrict__ y) {
+    const size_t count = (size_t)N * plane;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = i / plane, p = i % plane;
+        float s = b[0];
+        for (int c = 0; c < C; ++c)
+            s = fmaf(__bfloat162float(__float2bfloat16_rn(w[c])), __bfloat162float(d[(n * C + c) * plane + p]), s);
+        y[i] = x[i] + s;
+    }
+}
+
+// dd[n][c][p] = w[c] dy[n][p]
+__global__ void k_head_dgrad(const float* __restrict__ dy, const float* __restrict__ w, int C, int N, size_t plane,
+                             float* __restrict__ dd) {
+    const size_t count = (size_t)N * C * plane;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i % plane, nc = i / plane, n = nc / C;
+        const int c = (int)(nc % C);
+        dd[i] = __bfloat162float(__float2bfloat16_rn(w[c])) * dy[n * plane + p];
+    }
+}
+
+// gw[c] = sum_{n,p} dy[n][p] d[n][c][p] (blocks 0..C-1); gb = sum dy (block C)
+__global__ void __launch_bounds__(256) k_head_wgrad(const float* __restrict__ dy, const bf16* __restrict__ d, int C,
+                                                    int N, size_t plane, float* __restrict__ gw, float* __restrict__ gb) {
+    __shared__ float sh[8];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int n = 0; n < N; ++n)
+        for (size_t i = threadIdx.x; i < plane; i += 256) {
+            const float g = dy[(size_t)n * plane + i];
+            s += c < C ? g * __bfloat162float(d[((size_t)n * C + c) * plane + i]) : g;
+        }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) {
+        if (c < C)
+            gw[c] = s;
+        else
+            gb[0] = s;
+    }
+}
+
+// loss = mean (y - t)^2 (per-block FP32, exact fixed point across blocks), dy = 2 (y - t) / count
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const float* __restrict__ t, size_t count,
+                                             float* __restrict__ dy, long long* __restrict__ qpart, unsigned* counter,
+                                             double* loss) {
+    __shared__ float sh[8];
+    __shared__ bool last;
+    const float scale = 2.f / (float)count;
+    float s = 0.f;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < count; i += (size_t)gridDim.x * 256) {
+        const float d = y[i] - t[i];
+        s = fmaf(d, d, s);
+        dy[i] = scale * d;
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) {
+        qpart[blockIdx.x] = to_q32(s);
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    long long q = 0;
+    bool bad = false;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+        const long long v = __ldcg(qpart + i);
+        bad |= v == kQBad;
+        q += v;
+    }
+    *loss = bad ? __longlong_as_double(0x7ff8000000000000ll) : (double)q * (1.0 / 4294967296.0) / (double)count;
+    *counter = 0u;
+}
+
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M, float* __restrict__ V,
+                       size_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float m = b1 * M[i] + (1.f - b1) * g, v = b2 * V[i] + (1.f - b2) * g * g;
+        M[i] = m;
+        V[i] = v;
+        P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+// BF16 weights of a 3x3 layer, and the flipped, transposed copy of the input gradient
+__global__ void k_prep_w(const float* __restrict__ W, int Cout, int Cin, bf16* __restrict__ Wb, bf16* __restrict__ Wt) {
+    const size_t count = (size_t)Cout * Cin * 9;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const int tap = (int)(i % 9);
+        const size_t oc = i / 9;
+        const int ci = (int)(oc % Cin), co = (int)(oc / Cin);
+        const bf16 v = __float2bfloat16_rn(W[i]);
+        Wb[i] = v;
+        Wt[((size_t)ci * Cout + co) * 9 + (8 - tap)] = v;
+    }
+}
+
+// x = clip(phi, -B, B) / B as FP32 (residual path) and BF16 (first convolution)
+__global__ void k_band(const float* __restrict__ phi, size_t count, float B, float* __restrict__ x,
+                       bf16* __restrict__ xb) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = fminf(fmaxf(phi[i], -B), B) / B;
+        x[i] = v;
+        if (xb) xb[i] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void k_scale(const float* __restrict__ y, size_t count, float s, float* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = s * y[i];
+}
+
+bool bad_ptr(const void* p) { return !p || (reinterpret_cast<uintptr_t>(p) & 15u); }
+
+int grid1(size_t count) { return (int)std::max<size_t>(1, std::min<size_t>((count + 255) / 256, 152 * 16)); }
+
+}  // namespace
+}  // namespace devel
+
+// ---------------------------------------------------------------------------
+// The network object
+// ---------------------------------------------------------------------------
+struct devel_dsn {
+    int S = 0, batch = 0, c = 0;
+    struct Conv {
+        int cin, cout, k;
+        size_t w_off, b_off;  // into the flat parameter vector
+        __nv_bfloat16* Wb = nullptr;
+        __nv_bfloat16* Wt = nullptr;
+    };
+    std::vector<Conv> convs;
+    size_t nparams = 0;
+    float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+    int t = 0;  // Adam steps taken
+    // activations (bf16) and their gradients (fp32): index by name below
+    struct Act {
+        int C, side;
+        __nv_bfloat16* a = nullptr;
+        float* g = nullptr;
+    };
+    std::vector<Act> acts;
+    float* x = nullptr;     // [batch][S][S] band-limited input (fp32)
+    __nv_bfloat16* xb = nullptr;
+    float* y = nullptr;     // network output
+    float* dy = nullptr;
+    float* part = nullptr;  // weight-gradient partials
+    size_t part_count = 0;
+    long long* qpart = nullptr;
+    unsigned* counter = nullptr;
+    double* loss = nullptr;
+};
+
+namespace devel {
+namespace {
+
+enum ActId { A0, S0, P1, A1, S1, P2, A2, S2, P3, A3, S3, U2, D2A, D2, U1, D1A, D1, U0, D0A, D0, NACT };
+
+void free_dsn(devel_dsn* d) {
+    if (!d) return;
+    for (auto& cv : d->convs) {
+        cudaFree(cv.Wb);
+        cudaFree(cv.Wt);
+    }
+    for (auto& a : d->acts) {
+        cudaFree(a.a);
+        cudaFree(a.g);
+    }
+    for (void* p : {(void*)d->P, (void*)d->G, (void*)d->M, (void*)d->V, (void*)d->x, (void*)d->xb, (void*)d->y,
+                    (void*)d->dy, (void*)d->part, (void*)d->qpart, (void*)d->counter, (void*)d->loss})
+        if (p) cudaFree(p);
+    delete d;
+}
+
+int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
+             __nv_bfloat16* Y, cudaStream_t s) {
+    const auto& cv = d->convs[ci];
+    const int tiles = ((side + kT - 1) / kT) * ((side + kT - 1) / kT);
+    dim3 grid(tiles, (cv.cout + kCoB - 1) / kCoB, nb);
+    k_conv3<__nv_bfloat16, true><<<grid, 256, 0, s>>>(XA, CA, XB, CB, cv.Wb, d->P + cv.b_off, 1, Y, cv.cout, nullptr, 0,
+                                                     side, side, cv.cout);
+    DEVEL_LAUNCH_CHECK("k_conv3");
+    return DEVEL_OK;
+}
+
+// backward of conv ci: dZ (= dY masked by the ReLU of Y, in place), weight and bias
+// gradients, and (if dXA) the input gradient split into dXA / dXB (stored or added)
+int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
+             const __nv_bfloat16* Y, float* dY, float* dXA, float* dXB, int accumulate, cudaStream_t s) {
+    const auto& cv = d->convs[ci];
+    const size_t plane = (size_t)side * side;
+    const size_t cnt = (size_t)nb * cv.cout * plane;
+    k_relu_mask<<<grid1(cnt), 256, 0, s>>>(dY, Y, cnt);
+    const int tiles = ((side + kT - 1) / kT) * ((side + kT - 1) / kT);
+    dim3 gw(tiles, (cv.cout + kWC - 1) / kWC, (cv.cin + kWC - 1) / kWC);
+    k_conv3_wgrad<__nv_bfloat16><<<gw, 256, 0, s>>>(XA, CA, XB, CB, dY, cv.cout, nb, side, side, d->part);
+    const size_t wc = (size_t)cv.cout * cv.cin * 9;
+    k_wgrad_reduce<<<(unsigned)((wc + 255) / 256), 256, 0, s>>>(d->part, tiles, wc, d->G + cv.w_off);
+    k_bias_grad<<<cv.cout, 256, 0, s>>>(dY, cv.cout, nb, plane, d->G + cv.b_off);
+    if (dXA) {
+        dim3 gd(tiles, (cv.cin + kCoB - 1) / kCoB, nb);
+        k_conv3<float, false><<<gd, 256, 0, s>>>(dY, cv.cout, (const float*)nullptr, 0, cv.Wt, nullptr, 0, dXA, CA, dXB,
+                                                accumulate, side, side, cv.cin);
+    }
+    DEVEL_LAUNCH_CHECK("dsn conv backward");
+    return DEVEL_OK;
+}
+
+int prep_weights(devel_dsn* d, cudaStream_t s) {
+    for (auto& cv : d->convs) {
+        if (cv.k != 3) continue;
+        const size_t wc = (size_t)cv.cout * cv.cin * 9;
+        k_prep_w<<<grid1(wc), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.Wb, cv.Wt);
+    }
+    DEVEL_LAUNCH_CHECK("k_prep_w");
+    return DEVEL_OK;
+}
+
+int forward(devel_dsn* d, int nb, cudaStream_t s) {
+    auto& A = d->acts;
+    const int S = d->S, c = d->c;
+    const int w[4] = {c, 2 * c, 4 * c, 8 * c};
+    int rc = conv_fwd(d, 0, nb, d->xb, 1, nullptr, 0, S, A[A0].a, s);
+    if (!rc) rc = conv_fwd(d, 1, nb, A[A0].a, w[0], nullptr, 0, S, A[S0].a, s);
+    const int pin[3] = {S0, S1, S2}, pout[3] = {P1, P2, P3}, aa[3] = {A1, A2, A3}, ss[3] = {S1, S2, S3};
+    for (int lv = 1; lv < 4 && !rc; ++lv) {
+        const int side = S >> lv;
+        const size_t planes = (size_t)nb * w[lv - 1];
+        k_avgpool<<<grid1(planes * side * side), 256, 0, s>>>(A[pin[lv - 1]].a, 2 * side, 2 * side, planes,
+                                                            A[pout[lv - 1]].a);
+        rc = conv_fwd(d, 2 * lv, nb, A[pout[lv - 1]].a, w[lv - 1], nullptr, 0, side, A[aa[lv - 1]].a, s);
+        if (!rc) rc = conv_fwd(d, 2 * lv + 1, nb, A[aa[lv - 1]].a, w[lv], nullptr, 0, side, A[ss[lv - 1]].a, s);
+    }
+    // decoder: level lv takes up(previous) ++ skip(lv)
+    const int up[3] = {U2, U1, U0}, da[3] = {D2A, D1A, D0A}, dd[3] = {D2, D1, D0}, skip[3] = {S2, S1, S0};
+    int prev = S3;
+    for (int j = 0; j < 3 && !rc; ++j) {
+        const int lv = 2 - j, side = S >> lv;
+        const size_t planes = (size_t)nb * w[lv + 1];
+        k_upsample<<<grid1(planes * side * side), 256, 0, s>>>(A[prev].a, side / 2, side / 2, planes, A[up[j]].a);
+        rc = conv_fwd(d, 8 + 2 * j, nb, A[up[j]].a, w[lv + 1], A[skip[j]].a, w[lv], side, A[da[j]].a, s);
+        if (!rc) rc = conv_fwd(d, 9 + 2 * j, nb, A[da[j]].a, w[lv], nullptr, 0, side, A[dd[j]].a, s);
+        prev = dd[j];
+    }
+    if (rc) return rc;
+    const auto& h = d->convs[14];
+    k_head<<<grid1((size_t)nb * S * S), 256, 0, s>>>(d->x, A[D0].a, d->P + h.w_off, d->P + h.b_off, c, nb,
+                                                     (size_t)S * S, d->y);
+    DEVEL_LAUNCH_CHECK("dsn forward");
+    return DEVEL_OK;
+}
+
+int backward(devel_dsn* d, int nb, cudaStream_t s) {
+    auto& A = d->acts;
+    const int S = d->S, c = d->c;
+    const int w[4] = {c, 2 * c, 4 * c, 8 * c};
+    const size_t plane0 = (size_t)S * S;
+    const auto& h = d->convs[14];
+    k_head_dgrad<<<grid1((size_t)nb * c * plane0), 256, 0, s>>>(d->dy, d->P + h.w_off, c, nb, plane0, A[D0].g);
+    k_head_wgrad<<<c + 1, 256, 0, s>>>(d->dy, A[D0].a, c, nb, plane0, d->G + h.w_off, d->G + h.b_off);
+    const int up[3] = {U2, U1, U0}, da[3] = {D2A, D1A, D0A}, dd[3] = {D2, D1, D0}, skip[3] = {S2, S1, S0};
+    const int prevs[3] = {S3, D2, D1};
+    int rc = DEVEL_OK;
+    for (int j = 2; j >= 0 && !rc; --j) {  // decoder levels, last first
+        const int lv = 2 - j, side = S >> lv;
+        rc = conv_bwd(d, 9 + 2 * j, nb, A[da[j]].a, w[lv], nullptr, 0, side, A[dd[j]].a, A[dd[j]].g, A[da[j]].g,
+                      nullptr, 0, s);
+        // the skip's gradient starts here (stored); the upsampled part goes to up[j]
+        if (!rc)
+            rc = conv_bwd(d, 8 + 2 * j, nb, A[up[j]].a, w[lv + 1], A[skip[j]].a, w[lv], side, A[da[j]].a, A[da[j]].g,
+                          A[up[j]].g, A[skip[j]].g, 0, s);
+        const size_t planes = (size_t)nb * w[lv + 1];
+        k_upsample_bwd<<<grid1(planes * (side / 2) * (side / 2)), 256, 0, s>>>(A[up[j]].g, side / 2, side / 2, planes,
+                                                                                A[prevs[j]].g);
+    }
+    // encoder, bottleneck first; the gradient of each level's output already holds the
+    // skip contribution (levels 0-2) and gets the pooled path added
+    const int aa[4] = {A0, A1, A2, A3}, ss[4] = {S0, S1, S2, S3}, pp[4] = {-1, P1, P2, P3};
+    for (int lv = 3; lv >= 0 && !rc; --lv) {
+        const int side = S >> lv;
+        const __nv_bfloat16* in = lv == 0 ? d->xb : A[pp[lv]].a;
+        const int cin = lv == 0 ? 1 : w[lv - 1];
+        rc = conv_bwd(d, 2 * lv + 1, nb, A[aa[lv]].a, w[lv], nullptr, 0, side, A[ss[lv]].a, A[ss[lv]].g, A[aa[lv]].g,
+                      nullptr, 0, s);
+        if (!rc)
+            rc = conv_bwd(d, 2 * lv, nb, in, cin, nullptr, 0, side, A[aa[lv]].a, A[aa[lv]].g,
+                          lv == 0 ? nullptr : A[pp[lv]].g, nullptr, 0, s);
+        if (!rc && lv > 0) {
+            const size_t planes = (size_t)nb * w[lv - 1];
+            k_avgpool_bwd<<<grid1(planes * 4 * side * side), 256, 0, s>>>(A[pp[lv]].g, 2 * side, 2 * side, planes,
+                                                                          A[ss[lv - 1]].g, 1);
+        }
+    }
+    DEVEL_LAUNCH_CHECK("dsn backward");
+    return rc;
+}
+
+}  // namespace
+}  // namespace devel
+
+using namespace devel;
+
+extern "C" {
+
+int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
+    if (!out) return set_error(DEVEL_EINVAL, "devel_dsn_create: out is NULL");
+    *out = nullptr;
+    if (S < 16 || S > 2048 || S % 16) return set_error(DEVEL_EINVAL, "devel_dsn_create: side %d not a multiple of 16 in [16, 2048]", S);
+    if (batch < 1 || batch > 256) return set_error(DEVEL_EINVAL, "devel_dsn_create: batch %d outside [1, 256]", batch);
+    if (width < 1 || width > 64) return set_error(DEVEL_EINVAL, "devel_dsn_create: width %d outside [1, 64]", width);
+    devel_dsn* d = new devel_dsn;
+    d->S = S;
+    d->batch = batch;
+    d->c = width;
+    const int w[4] = {width, 2 * width, 4 * width, 8 * width};
+    std::vector<std::array<int, 3>> L;
+    int cin = 1;
+    for (int lv = 0; lv < 4; ++lv) {
+        L.push_back({cin, w[lv], 3});
+        L.push_back({w[lv], w[lv], 3});
+        cin = w[lv];
+    }
+    for (int lv = 2; lv >= 0; --lv) {
+        L.push_back({w[lv + 1] + w[lv], w[lv], 3});
+        L.push_back({w[lv], w[lv], 3});
+    }
+    L.push_back({w[0], 1, 1});
+    size_t off = 0, maxpart = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto& l : L) {
+        devel_dsn::Conv cv{l[0], l[1], l[2], off, 0};
+        off += (size_t)l[0] * l[1] * l[2] * l[2];
+        cv.b_off = off;
+        off += l[1];
+        if (l[2] == 3 && e == cudaSuccess) {
+            e = cudaMalloc(&cv.Wb, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
+            if (e == cudaSuccess) e = cudaMalloc(&cv.Wt, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
+        }
+        d->convs.push_back(cv);
+    }
+    d->nparams = off;
+    // activations: (channels, side) by id
+    const int spec[NACT][2] = {{w[0], S},      {w[0], S},      {w[0], S / 2},  {w[1], S / 2}, {w[1], S / 2},
+                               {w[1], S / 4},  {w[2], S / 4},  {w[2], S / 4},  {w[2], S / 8}, {w[3], S / 8},
+                               {w[3], S / 8},  {w[3], S / 4},  {w[2], S / 4},  {w[2], S / 4}, {w[2], S / 2},
+                               {w[1], S / 2},  {w[1], S / 2},  {w[1], S},      {w[0], S},     {w[0], S}};
+    for (int i = 0; i < NACT; ++i) {
+        devel_dsn::Act a{spec[i][0], spec[i][1]};
+        const size_t cnt = (size_t)batch * a.C * a.side * a.side;
+        if (e == cudaSuccess) e = cudaMalloc(&a.a, sizeof(__nv_bfloat16) * cnt);
+        if (e == cudaSuccess) e = cudaMalloc(&a.g, sizeof(float) * cnt);
+        d->acts.push_back(a);
+    }
+    // weight-gradient partials: spatial tiles x weights of the largest layer
+    for (size_t i = 0; i < d->convs.size(); ++i) {
+        const auto& cv = d->convs[i];
+        if (cv.k != 3) continue;
+        const int side = i < 8 ? S >> (i / 2) : S >> (2 - (int)(i - 8) / 2);
+        const size_t tiles = (size_t)((side + kT - 1) / kT) * ((side + kT - 1) / kT);
+        maxpart = std::max(maxpart, tiles * cv.cout * cv.cin * 9);
+    }
+    const size_t px = (size_t)batch * S * S;
+    const int mse_blocks = grid1(px);
+    if (e == cudaSuccess) e = cudaMalloc(&d->P, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&d->G, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&d->M, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&d->V, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&d->x, sizeof(float) * px);
+    if (e == cudaSuccess) e = cudaMalloc(&d->xb, sizeof(__nv_bfloat16) * px);
+    if (e == cudaSuccess) e = cudaMalloc(&d->y, sizeof(float) * px);
+    if (e == cudaSuccess) e = cudaMalloc(&d->dy, sizeof(float) * px);
+    if (e == cudaSuccess) e = cudaMalloc(&d->part, sizeof(float) * maxpart);
+    if (e == cudaSuccess) e = cudaMalloc(&d->qpart, sizeof(long long) * mse_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&d->counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&d->loss, sizeof(double));
+    d->part_count = maxpart;
+    if (e == cudaSuccess) e = cudaMemset(d->P, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(d->M, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(d->V, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(d->counter, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        free_dsn(d);
+        return cuda_error(e, "devel_dsn_create");
+    }
+    *out = d;
+    return DEVEL_OK;
+}
+
+int devel_dsn_destroy(devel_dsn* d) {
+    if (!d) return DEVEL_OK;
+    cudaDeviceSynchronize();
+    free_dsn(d);
+    return DEVEL_OK;
+}
+
+long long devel_dsn_param_count(const devel_dsn* d) { return d ? (long long)d->nparams : -1; }
+
+int devel_dsn_set_params(devel_dsn* d, const float* host) {
+    if (!d || !host) return set_error(DEVEL_EINVAL, "devel_dsn_set_params: NULL argument");
+    DEVEL_CUDA_TRY(cudaMemcpy(d->P, host, sizeof(float) * d->nparams, cudaMemcpyHostToDevice));
+    DEVEL_CUDA_TRY(cudaMemset(d->M, 0, sizeof(float) * d->nparams));
+    DEVEL_CUDA_TRY(cudaMemset(d->V, 0, sizeof(float) * d->nparams));
+    d->t = 0;
+    return DEVEL_OK;
+}
+
+int devel_dsn_get_params(const devel_dsn* d, float* host) {
+    if (!d || !host) return set_error(DEVEL_EINVAL, "devel_dsn_get_params: NULL argument");
+    DEVEL_CUDA_TRY(cudaMemcpy(host, d->P, sizeof(float) * d->nparams, cudaMemcpyDeviceToHost));
+    return DEVEL_OK;
+}
+
+int devel_dsn_init(devel_dsn* d, unsigned long long seed) {
+    if (!d) return set_error(DEVEL_EINVAL, "devel_dsn_init: dsn is NULL");
+    // He-normal weights from a splitmix64 stream and the Box-Muller transform, zero biases
+    std::vector<float> h(d->nparams, 0.f);
+    unsigned long long st = seed;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto uni = [&]() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+    for (auto& cv : d->convs) {
+        const size_t wc = (size_t)cv.cout * cv.cin * cv.k * cv.k;
+        const double sd = std::sqrt(2.0 / (cv.cin * cv.k * cv.k));
+        for (size_t i = 0; i < wc; ++i) {
+            const double u1 = uni(), u2 = uni();
+            h[cv.w_off + i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+    }
+    return devel_dsn_set_params(d, h.data());
+}
+
+int devel_dsn_forward(devel_dsn* d, int nb, const float* tsdf, float B, float* phi0, cudaStream_t s) {
+    if (!d) return set_error(DEVEL_EINVAL, "devel_dsn_forward: dsn is NULL");
+    if (nb < 1 || nb > d->batch) return set_error(DEVEL_EINVAL, "devel_dsn_forward: nb=%d outside [1, %d]", nb, d->batch);
+    if (bad_ptr(tsdf) || bad_ptr(phi0))
+        return set_error(DEVEL_EINVAL, "devel_dsn_forward: tsdf / phi0 NULL or not 16-byte aligned");
+    if (!(B > 0.f)) return set_error(DEVEL_EINVAL, "devel_dsn_forward: band B must be > 0");
+    const size_t px = (size_t)nb * d->S * d->S;
+    int rc = prep_weights(d, s);
+    if (rc) return rc;
+    k_band<<<grid1(px), 256, 0, s>>>(tsdf, px, B, d->x, d->xb);
+    rc = forward(d, nb, s);
+    if (rc) return rc;
+    k_scale<<<grid1(px), 256, 0, s>>>(d->y, px, B, phi0);
+    DEVEL_LAUNCH_CHECK("devel_dsn_forward");
+    return DEVEL_OK;
+}
+
+int devel_dsn_train_step(devel_dsn* d, int nb, const float* tsdf, const float* phi_gt, float B, float lr,
+                         double* loss_out, cudaStream_t s) {
+    if (!d) return set_error(DEVEL_EINVAL, "devel_dsn_train_step: dsn is NULL");
+    if (nb < 1 || nb > d->batch)
+        return set_error(DEVEL_EINVAL, "devel_dsn_train_step: nb=%d outside [1, %d]", nb, d->batch);
+    if (bad_ptr(tsdf) || bad_ptr(phi_gt))
+        return set_error(DEVEL_EINVAL, "devel_dsn_train_step: tsdf / phi_gt NULL or not 16-byte aligned");
+    if (!(B > 0.f) || !(lr >= 0.f)) return set_error(DEVEL_EINVAL, "devel_dsn_train_step: bad band or learning rate");
+    const size_t px = (size_t)nb * d->S * d->S;
+    int rc = prep_weights(d, s);
+    if (rc) return rc;
+    k_band<<<grid1(px), 256, 0, s>>>(tsdf, px, B, d->x, d->xb);
+    rc = forward(d, nb, s);
+    if (rc) return rc;
+    // labels band-limited into dy's buffer first, then the MSE overwrites it with dL/dy
+    k_band<<<grid1(px), 256, 0, s>>>(phi_gt, px, B, d->dy, nullptr);
+    const int mb = grid1(px);
+    k_mse<<<mb, 256, 0, s>>>(d->y, d->dy, px, d->dy, d->qpart, d->counter, loss_out ? loss_out : d->loss);
+    rc = backward(d, nb, s);
+    if (rc) return rc;
+    d->t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)d->t), c2 = 1.f - std::pow(b2, (float)d->t);
+    k_adam<<<grid1(d->nparams), 256, 0, s>>>(d->P, d->G, d->M, d->V, d->nparams, lr, b1, b2, 1e-8f, c1, c2);
+    DEVEL_LAUNCH_CHECK("devel_dsn_train_step");
+    return DEVEL_OK;
+}
+
+int devel_dsn_grads(const devel_dsn* d, float* host) {
+    if (!d || !host) return set_error(DEVEL_EINVAL, "devel_dsn_grads: NULL argument");
+    DEVEL_CUDA_TRY(cudaMemcpy(host, d->G, sizeof(float) * d->nparams, cudaMemcpyDeviceToHost));
+    return DEVEL_OK;
+}
+
+}  // extern "C"
