@@ -10,10 +10,10 @@
 // Adam), every sum accumulates in FP32; gradients are FP32.
 //
 // Kernels (SIMT): k_conv3 (forward, and the input gradient as a convolution of the
-// output gradient with the flipped, transposed weights), k_conv3_wgrad (weight
-// gradients per spatial tile) + k_wgrad_reduce (fixed-order sum over tiles),
-// k_bias_grad, k_relu_mask, pooling / upsampling and their adjoints, the head, the MSE
-// and Adam. Every reduction runs in a fixed order: results are reproducible.
+// output gradient with the flipped, transposed weights), k_conv3_wgrad (weight and
+// bias gradients per spatial tile) + k_wgrad_reduce (fixed-order sum over tiles),
+// k_relu_mask, pooling / upsampling and their adjoints, the head, the MSE and Adam.
+// Every reduction runs in a fixed order: results are reproducible.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -40,33 +40,55 @@ __device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
 // concatenation [XA (CA channels), XB (CB channels)] along channels, zero outside.
 // Output: bf16 (optional ReLU) into YA, or FP32 (stored or added) split along output
 // channels into YA (the first CYA channels) and YB.
+// A block computes a 32 x 32 pixel tile for 16 output channels in two groups of 128
+// threads (8 channels each); a thread computes 2 x 4 pixels x 8 channels: per input
+// channel it reads its 4 x 6 input window once and, per tap, two broadcast float4s of
+// weights (64 FMAs per two shared-memory loads).
+constexpr int kCT = 32;     // conv output tile side
 template <typename Tin, bool kBf16Out>
 __global__ void __launch_bounds__(256)
 k_conv3(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const bf16* __restrict__ W,
         const float* __restrict__ bias, int relu, void* YA, int CYA, float* YB, int accumulate, int H, int Wd,
         int Cout) {
-    __shared__ float patch[kCiC][kT + 2][kT + 2];
+    __shared__ float patch[kCiC][kCT + 2][kCT + 2];
     __shared__ __align__(16) float wsm[kCiC][9][kCoB];
-    const int tilesx = (Wd + kT - 1) / kT;
-    const int x0 = (blockIdx.x % tilesx) * kT, y0 = (blockIdx.x / tilesx) * kT;
+    const int tilesx = (Wd + kCT - 1) / kCT;
+    const int x0 = (blockIdx.x % tilesx) * kCT, y0 = (blockIdx.x / tilesx) * kCT;
     const int co0 = blockIdx.y * kCoB, n = blockIdx.z;
-    const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;
+    const int grp = threadIdx.x / 128, tid = threadIdx.x % 128;
+    const int tx = tid % 8, ty = tid / 8;  // pixels: rows 2ty, 2ty+1; columns 4tx .. 4tx+3
     const int Cin = CA + CB;
     const size_t plane = (size_t)H * Wd;
-    float acc[kCoB];
+    float acc[8][8];
 #pragma unroll
-    for (int j = 0; j < kCoB; ++j) acc[j] = 0.f;
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
+    constexpr int kPatch = kCiC * (kCT + 2) * (kCT + 2);
+    constexpr int kPerThread = (kPatch + 255) / 256;
     for (int ci0 = 0; ci0 < Cin; ci0 += kCiC) {
-        for (int i = threadIdx.x; i < kCiC * (kT + 2) * (kT + 2); i += 256) {
-            const int c = i / ((kT + 2) * (kT + 2)), r = (i / (kT + 2)) % (kT + 2), q = i % (kT + 2);
-            const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
-            float v = 0.f;
-            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
-                const size_t off = (size_t)gy * Wd + gx;
-                v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
-                            : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
+        // a thread's patch loads go out 8 at a time before they are stored (latency overlap)
+        constexpr int kG = 8;
+        for (int k0 = 0; k0 < kPerThread; k0 += kG) {
+            float pv[kG];
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = threadIdx.x + (k0 + k) * 256;
+                const int c = i / ((kCT + 2) * (kCT + 2)), r = (i / (kCT + 2)) % (kCT + 2), q = i % (kCT + 2);
+                const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
+                float v = 0.f;
+                if (i < kPatch && ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
+                    const size_t off = (size_t)gy * Wd + gx;
+                    v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
+                                : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
+                }
+                pv[k] = v;
             }
-            patch[c][r][q] = v;
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = threadIdx.x + (k0 + k) * 256;
+                if (i < kPatch) (&patch[0][0][0])[i] = pv[k];
+            }
         }
         for (int i = threadIdx.x; i < kCiC * 9 * kCoB; i += 256) {
             const int c = i / (9 * kCoB), tap = (i / kCoB) % 9, co = i % kCoB;
@@ -74,48 +96,63 @@ k_conv3(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, 
             wsm[c][tap][co] = (ci < Cin && o < Cout) ? __bfloat162float(W[((size_t)o * Cin + ci) * 9 + tap]) : 0.f;
         }
         __syncthreads();
-#pragma unroll 2
         for (int c = 0; c < kCiC; ++c) {
+            float win[4][6];  // input rows 2ty-1 .. 2ty+2, columns 4tx-1 .. 4tx+4 (tile coordinates)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) win[r][q] = patch[c][2 * ty + r][4 * tx + q];
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
-                const float v = patch[c][ty + tap / 3][tx + tap % 3];
-                const float4* w4 = reinterpret_cast<const float4*>(wsm[c][tap]);
+                const int u = tap / 3, v = tap % 3;
+                const float4* w4 = reinterpret_cast<const float4*>(&wsm[c][tap][8 * grp]);
+                const float4 wa = w4[0], wb = w4[1];
 #pragma unroll
-                for (int j = 0; j < kCoB / 4; ++j) {
-                    const float4 w = w4[j];
-                    acc[4 * j + 0] = fmaf(v, w.x, acc[4 * j + 0]);
-                    acc[4 * j + 1] = fmaf(v, w.y, acc[4 * j + 1]);
-                    acc[4 * j + 2] = fmaf(v, w.z, acc[4 * j + 2]);
-                    acc[4 * j + 3] = fmaf(v, w.w, acc[4 * j + 3]);
+                for (int q = 0; q < 8; ++q) {
+                    const float xv = win[u + q / 4][v + q % 4];
+                    acc[q][0] = fmaf(xv, wa.x, acc[q][0]);
+                    acc[q][1] = fmaf(xv, wa.y, acc[q][1]);
+                    acc[q][2] = fmaf(xv, wa.z, acc[q][2]);
+                    acc[q][3] = fmaf(xv, wa.w, acc[q][3]);
+                    acc[q][4] = fmaf(xv, wb.x, acc[q][4]);
+                    acc[q][5] = fmaf(xv, wb.y, acc[q][5]);
+                    acc[q][6] = fmaf(xv, wb.z, acc[q][6]);
+                    acc[q][7] = fmaf(xv, wb.w, acc[q][7]);
                 }
             }
         }
         __syncthreads();
     }
-    const int y = y0 + ty, x = x0 + tx;
-    if (y >= H || x >= Wd) return;
-    const size_t off = (size_t)y * Wd + x;
 #pragma unroll
-    for (int j = 0; j < kCoB; ++j) {
-        const int o = co0 + j;
-        if (o >= Cout) break;
-        float v = acc[j] + (bias ? bias[o] : 0.f);
-        if (kBf16Out) {
-            if (relu) v = fmaxf(v, 0.f);
-            static_cast<bf16*>(YA)[((size_t)n * Cout + o) * plane + off] = __float2bfloat16_rn(v);
-        } else {
-            float* dst = o < CYA ? static_cast<float*>(YA) + ((size_t)n * CYA + o) * plane + off
-                                 : YB + ((size_t)n * (Cout - CYA) + (o - CYA)) * plane + off;
-            *dst = accumulate ? *dst + v : v;
+    for (int q = 0; q < 8; ++q) {
+        const int y = y0 + 2 * ty + q / 4, x = x0 + 4 * tx + q % 4;
+        if (y >= H || x >= Wd) continue;
+        const size_t off = (size_t)y * Wd + x;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int o = co0 + 8 * grp + j;
+            if (o >= Cout) break;
+            float v = acc[q][j] + (bias ? bias[o] : 0.f);
+            if (kBf16Out) {
+                if (relu) v = fmaxf(v, 0.f);
+                static_cast<bf16*>(YA)[((size_t)n * Cout + o) * plane + off] = __float2bfloat16_rn(v);
+            } else {
+                float* dst = o < CYA ? static_cast<float*>(YA) + ((size_t)n * CYA + o) * plane + off
+                                     : YB + ((size_t)n * (Cout - CYA) + (o - CYA)) * plane + off;
+                *dst = accumulate ? *dst + v : v;
+            }
         }
     }
 }
 
-// Per spatial tile: part[tile][co][ci][9] = sum_n sum_{tile px} dZ[n][co][p] X[n][ci][p + tap]
+// Per spatial tile: part[tile][co][ci][9] = sum_n sum_{tile px} dZ[n][co][p] X[n][ci][p + tap],
+// and (blocks of the first input-channel group) bpart[tile][co] = sum_n sum_{tile px} dZ.
+// A thread (co, ci) slides a 3 x 3 register window along each row of its tile: per
+// pixel one dZ value and one new input column (4 shared-memory loads for 9 FMAs).
 template <typename Tin>
 __global__ void __launch_bounds__(256)
 k_conv3_wgrad(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const float* __restrict__ dZ,
-              int Cout, int N, int H, int Wd, float* __restrict__ part) {
+              int Cout, int N, int H, int Wd, float* __restrict__ part, float* __restrict__ bpart) {
     __shared__ float dz[kWC][kT][kT];
     __shared__ float xp[kWC][kT + 2][kT + 2];
     const int tilesx = (Wd + kT - 1) / kT;
@@ -125,34 +162,59 @@ k_conv3_wgrad(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, in
     const int col = threadIdx.x / kWC, cil = threadIdx.x % kWC;
     const int Cin = CA + CB;
     const size_t plane = (size_t)H * Wd;
-    float acc[9];
+    float acc[9], bsum = 0.f;
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+    constexpr int kDz = kWC * kT * kT, kXp = kWC * (kT + 2) * (kT + 2);
     for (int n = 0; n < N; ++n) {
-        for (int i = threadIdx.x; i < kWC * kT * kT; i += 256) {
+#pragma unroll 8
+        for (int k = 0; k < kDz / 256; ++k) {
+            const int i = threadIdx.x + k * 256;
             const int c = i / (kT * kT), r = (i / kT) % kT, q = i % kT;
             const int o = co0 + c, gy = y0 + r, gx = x0 + q;
-            dz[c][r][q] = (o < Cout && gy < H && gx < Wd) ? dZ[((size_t)n * Cout + o) * plane + (size_t)gy * Wd + gx]
-                                                         : 0.f;
+            (&dz[0][0][0])[i] = (o < Cout && gy < H && gx < Wd)
+                                    ? dZ[((size_t)n * Cout + o) * plane + (size_t)gy * Wd + gx]
+                                    : 0.f;
         }
-        for (int i = threadIdx.x; i < kWC * (kT + 2) * (kT + 2); i += 256) {
+#pragma unroll 8
+        for (int k = 0; k < (kXp + 255) / 256; ++k) {
+            const int i = threadIdx.x + k * 256;
             const int c = i / ((kT + 2) * (kT + 2)), r = (i / (kT + 2)) % (kT + 2), q = i % (kT + 2);
             const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
             float v = 0.f;
-            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
+            if (i < kXp && ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
                 const size_t off = (size_t)gy * Wd + gx;
                 v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
                             : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
             }
-            xp[c][r][q] = v;
+            if (i < kXp) (&xp[0][0][0])[i] = v;
         }
         __syncthreads();
         for (int r = 0; r < kT; ++r) {
-#pragma unroll 4
-            for (int q = 0; q < kT; ++q) {
-                const float d = dz[col][r][q];
+            float w0[3], w1[3];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) acc[t] = fmaf(d, xp[cil][r + t / 3][q + t % 3], acc[t]);
+            for (int u = 0; u < 3; ++u) {
+                w0[u] = xp[cil][r + u][0];
+                w1[u] = xp[cil][r + u][1];
+            }
+#pragma unroll
+            for (int q = 0; q < kT; ++q) {
+                float w2[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) w2[u] = xp[cil][r + u][q + 2];
+                const float d = dz[col][r][q];
+                bsum += d;
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    acc[3 * u + 0] = fmaf(d, w0[u], acc[3 * u + 0]);
+                    acc[3 * u + 1] = fmaf(d, w1[u], acc[3 * u + 1]);
+                    acc[3 * u + 2] = fmaf(d, w2[u], acc[3 * u + 2]);
+                }
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    w0[u] = w1[u];
+                    w1[u] = w2[u];
+                }
             }
         }
         __syncthreads();
@@ -163,6 +225,7 @@ k_conv3_wgrad(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, in
 #pragma unroll
         for (int t = 0; t < 9; ++t) dst[t] = acc[t];
     }
+    if (blockIdx.z == 0 && cil == 0 && o < Cout) bpart[(size_t)tile * Cout + o] = bsum;
 }
 
 // G[i] = sum over tiles of part[tile][i], in tile order
@@ -183,20 +246,6 @@ __device__ __forceinline__ float block_sum256(float v, float* sh) {
     if (threadIdx.x == 0)
         for (int i = 0; i < 8; ++i) s += sh[i];
     return s;
-}
-
-// gb[c] = sum_{n,p} dZ[n][c][p] (one block per channel)
-__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ dZ, int C, int N, size_t plane,
-                                                   float* __restrict__ gb) {
-    __shared__ float sh[8];
-    const int c = blockIdx.x;
-    float s = 0.f;
-    for (int n = 0; n < N; ++n) {
-        const float* p = dZ + ((size_t)n * C + c) * plane;
-        for (size_t i = threadIdx.x; i < plane; i += 256) s += p[i];
-    }
-    s = block_sum256(s, sh);
-    if (threadIdx.x == 0) gb[c] = s;
 }
 
 __global__ void k_relu_mask(float* __restrict__ dZ, const bf16* __restrict__ out, size_t count) {
@@ -276,24 +325,22 @@ __global__ void k_head_dgrad(const float* __restrict__ dy, const float* __restri
     }
 }
 
-// gw[c] = sum_{n,p} dy[n][p] d[n][c][p] (blocks 0..C-1); gb = sum dy (block C)
+// Head gradients per slice of the pixels: part[split][c] = sum dy d[c] over the split's
+// pixels (c < C), part[split][C] = sum dy; summed over the splits in order afterwards.
+constexpr int kHeadSplits = 64;
 __global__ void __launch_bounds__(256) k_head_wgrad(const float* __restrict__ dy, const bf16* __restrict__ d, int C,
-                                                    int N, size_t plane, float* __restrict__ gw, float* __restrict__ gb) {
+                                                    int N, size_t plane, float* __restrict__ part) {
     __shared__ float sh[8];
-    const int c = blockIdx.x;
+    const int c = blockIdx.x, sp = blockIdx.y;
+    const size_t total = (size_t)N * plane, i0 = total * sp / kHeadSplits, i1 = total * (sp + 1) / kHeadSplits;
     float s = 0.f;
-    for (int n = 0; n < N; ++n)
-        for (size_t i = threadIdx.x; i < plane; i += 256) {
-            const float g = dy[(size_t)n * plane + i];
-            s += c < C ? g * __bfloat162float(d[((size_t)n * C + c) * plane + i]) : g;
-        }
-    s = block_sum256(s, sh);
-    if (threadIdx.x == 0) {
-        if (c < C)
-            gw[c] = s;
-        else
-            gb[0] = s;
+    for (size_t i = i0 + threadIdx.x; i < i1; i += 256) {
+        const float g = dy[i];
+        const size_t n = i / plane, p = i % plane;
+        s += c < C ? g * __bfloat162float(d[(n * C + c) * plane + p]) : g;
     }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) part[(size_t)sp * (C + 1) + c] = s;
 }
 
 // loss = mean (y - t)^2 (per-block FP32, exact fixed point across blocks), dy = 2 (y - t) / count
@@ -432,8 +479,8 @@ void free_dsn(devel_dsn* d) {
 int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
              __nv_bfloat16* Y, cudaStream_t s) {
     const auto& cv = d->convs[ci];
-    const int tiles = ((side + kT - 1) / kT) * ((side + kT - 1) / kT);
-    dim3 grid(tiles, (cv.cout + kCoB - 1) / kCoB, nb);
+    const int ctiles = ((side + kCT - 1) / kCT) * ((side + kCT - 1) / kCT);
+    dim3 grid(ctiles, (cv.cout + kCoB - 1) / kCoB, nb);
     k_conv3<__nv_bfloat16, true><<<grid, 256, 0, s>>>(XA, CA, XB, CB, cv.Wb, d->P + cv.b_off, 1, Y, cv.cout, nullptr, 0,
                                                      side, side, cv.cout);
     DEVEL_LAUNCH_CHECK("k_conv3");
@@ -450,12 +497,15 @@ int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     k_relu_mask<<<grid1(cnt), 256, 0, s>>>(dY, Y, cnt);
     const int tiles = ((side + kT - 1) / kT) * ((side + kT - 1) / kT);
     dim3 gw(tiles, (cv.cout + kWC - 1) / kWC, (cv.cin + kWC - 1) / kWC);
-    k_conv3_wgrad<__nv_bfloat16><<<gw, 256, 0, s>>>(XA, CA, XB, CB, dY, cv.cout, nb, side, side, d->part);
     const size_t wc = (size_t)cv.cout * cv.cin * 9;
+    float* bpart = d->part + (size_t)tiles * wc;
+    k_conv3_wgrad<__nv_bfloat16><<<gw, 256, 0, s>>>(XA, CA, XB, CB, dY, cv.cout, nb, side, side, d->part, bpart);
     k_wgrad_reduce<<<(unsigned)((wc + 255) / 256), 256, 0, s>>>(d->part, tiles, wc, d->G + cv.w_off);
-    k_bias_grad<<<cv.cout, 256, 0, s>>>(dY, cv.cout, nb, plane, d->G + cv.b_off);
+    k_wgrad_reduce<<<(unsigned)((cv.cout + 255) / 256), 256, 0, s>>>(bpart, tiles, (size_t)cv.cout,
+                                                                     d->G + cv.b_off);
     if (dXA) {
-        dim3 gd(tiles, (cv.cin + kCoB - 1) / kCoB, nb);
+        const int ctiles = ((side + kCT - 1) / kCT) * ((side + kCT - 1) / kCT);
+        dim3 gd(ctiles, (cv.cin + kCoB - 1) / kCoB, nb);
         k_conv3<float, false><<<gd, 256, 0, s>>>(dY, cv.cout, (const float*)nullptr, 0, cv.Wt, nullptr, 0, dXA, CA, dXB,
                                                 accumulate, side, side, cv.cin);
     }
@@ -514,7 +564,9 @@ int backward(devel_dsn* d, int nb, cudaStream_t s) {
     const size_t plane0 = (size_t)S * S;
     const auto& h = d->convs[14];
     k_head_dgrad<<<grid1((size_t)nb * c * plane0), 256, 0, s>>>(d->dy, d->P + h.w_off, c, nb, plane0, A[D0].g);
-    k_head_wgrad<<<c + 1, 256, 0, s>>>(d->dy, A[D0].a, c, nb, plane0, d->G + h.w_off, d->G + h.b_off);
+    k_head_wgrad<<<dim3(c + 1, kHeadSplits), 256, 0, s>>>(d->dy, A[D0].a, c, nb, plane0, d->part);
+    // weights then bias are contiguous in G
+    k_wgrad_reduce<<<1, 256, 0, s>>>(d->part, kHeadSplits, (size_t)c + 1, d->G + h.w_off);
     const int up[3] = {U2, U1, U0}, da[3] = {D2A, D1A, D0A}, dd[3] = {D2, D1, D0}, skip[3] = {S2, S1, S0};
     const int prevs[3] = {S3, D2, D1};
     int rc = DEVEL_OK;
@@ -614,8 +666,9 @@ int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
         if (cv.k != 3) continue;
         const int side = i < 8 ? S >> (i / 2) : S >> (2 - (int)(i - 8) / 2);
         const size_t tiles = (size_t)((side + kT - 1) / kT) * ((side + kT - 1) / kT);
-        maxpart = std::max(maxpart, tiles * cv.cout * cv.cin * 9);
+        maxpart = std::max(maxpart, tiles * cv.cout * (cv.cin * 9 + 1));
     }
+    maxpart = std::max(maxpart, (size_t)kHeadSplits * (width + 1));
     const size_t px = (size_t)batch * S * S;
     const int mse_blocks = grid1(px);
     if (e == cudaSuccess) e = cudaMalloc(&d->P, sizeof(float) * off);
