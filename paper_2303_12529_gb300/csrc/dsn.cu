@@ -9,7 +9,8 @@
 // activations are stored in BF16, weights used in BF16 (FP32 master copy, updated by
 // Adam), every sum accumulates in FP32; gradients are FP32.
 //
-// Kernels (SIMT): k_conv3 (forward, and the input gradient as a convolution of the
+// Kernels: k_conv3_mma (forward convolutions on the tensor cores, warp-level BF16 MMA);
+// SIMT: k_conv3 (the input gradient as a convolution of the
 // output gradient with the flipped, transposed weights), k_conv3_wgrad (weight and
 // bias gradients per spatial tile) + k_wgrad_reduce (fixed-order sum over tiles),
 // k_relu_mask, pooling / upsampling and their adjoints, the head, the MSE and Adam.
@@ -21,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 struct devel_dsn;
 
@@ -142,6 +144,119 @@ k_conv3(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, 
                 *dst = accumulate ? *dst + v : v;
             }
         }
+    }
+}
+
+// Forward 3x3 convolution on the tensor cores (warp-level BF16 MMA, FP32 accumulate):
+// an implicit GEMM with M = 128 output pixels (4 rows x 32 columns), N = 64 output
+// channels, K = 16 input channels x 9 taps per step. The input tile (6 x 34 pixels x 16
+// channels, channel innermost, padded to 24 so ldmatrix rows hit distinct banks) and
+// the step's weights Wm[cb][tap][co][16] are staged in shared memory; warp w computes
+// row w % 4 (two 16-pixel fragments) for 32 channels (four 8-channel fragments).
+constexpr int kMRows = 4, kMCols = 32, kMCo = 64, kMPad = 24;
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256)
+k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int CB, const bf16* __restrict__ Wm,
+            int Coutp, const float* __restrict__ bias, int relu, bf16* __restrict__ Y, int H, int Wd, int Cout) {
+    __shared__ __align__(16) bf16 patch[kMRows + 2][kMCols + 2][kMPad];
+    __shared__ __align__(16) bf16 wsm[9][kMCo][kMPad];
+    const int tilesx = (Wd + kMCols - 1) / kMCols;
+    const int x0 = (blockIdx.x % tilesx) * kMCols, y0 = (blockIdx.x / tilesx) * kMRows;
+    const int co0 = blockIdx.y * kMCo, n = blockIdx.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int Cin = CA + CB, ncb = (Cin + 15) / 16;
+    const size_t plane = (size_t)H * Wd;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
+    constexpr int kPix = (kMRows + 2) * (kMCols + 2);
+    for (int cb = 0; cb < ncb; ++cb) {
+        // input tile, channel innermost (zero outside the image and past Cin)
+        for (int i = threadIdx.x; i < 16 * kPix; i += 256) {
+            const int c = i / kPix, pos = i % kPix, r = pos / (kMCols + 2), q = pos % (kMCols + 2);
+            const int ci = cb * 16 + c, gy = y0 + r - 1, gx = x0 + q - 1;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
+                const size_t off = (size_t)gy * Wd + gx;
+                v = ci < CA ? XA[((size_t)n * CA + ci) * plane + off] : XB[((size_t)n * CB + (ci - CA)) * plane + off];
+            }
+            patch[r][q][c] = v;
+        }
+        // weights of this channel block: 9 taps x 64 channels x 16, two uint4 per row
+        const uint4* wg = reinterpret_cast<const uint4*>(Wm + ((size_t)cb * 9 * Coutp + co0) * 16);
+        for (int i = threadIdx.x; i < 9 * kMCo * 2; i += 256) {
+            const int tap = i / (kMCo * 2), co = (i / 2) % kMCo, h = i & 1;
+            *reinterpret_cast<uint4*>(&wsm[tap][co][8 * h]) = wg[((size_t)tap * Coutp + co) * 2 + h];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int mat = lane >> 3, r = lane & 7;
+                const int m = (mat & 1) * 8 + r, koff = (mat >> 1) * 8;
+                ldsm_x4(tc::smem_u32(&patch[wm + dy][16 * mi + m + dx][koff]), a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+            }
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int mat = lane >> 3, r = lane & 7;
+                const int co = wn * 32 + 16 * pp + (mat >> 1) * 8 + r, koff = (mat & 1) * 8;
+                ldsm_x4(tc::smem_u32(&wsm[tap][co][koff]), b[2 * pp][0], b[2 * pp][1], b[2 * pp + 1][0], b[2 * pp + 1][1]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int nj = 0; nj < 4; ++nj) mma_16816(acc[mi][nj], a[mi], b[nj][0], b[nj][1]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, cpair = 2 * (lane & 3);
+    const int y = y0 + wm;
+    if (y >= H) return;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = x0 + 16 * mi + g + (e >> 1) * 8;
+                const int co = co0 + wn * 32 + 8 * nj + cpair + (e & 1);
+                if (x >= Wd || co >= Cout) continue;
+                float v = acc[mi][nj][e] + bias[co];
+                if (relu) v = fmaxf(v, 0.f);
+                Y[((size_t)n * Cout + co) * plane + (size_t)y * Wd + x] = __float2bfloat16_rn(v);
+            }
+}
+
+// weights of a 3x3 layer for k_conv3_mma: Wm[cb][tap][co < Coutp][16] (zero past Cin / Cout)
+__global__ void k_prep_wm(const float* __restrict__ W, int Cout, int Cin, int Coutp, bf16* __restrict__ Wm) {
+    const int ncb = (Cin + 15) / 16;
+    const size_t count = (size_t)ncb * 9 * Coutp * 16;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % 16);
+        const size_t r = i / 16;
+        const int co = (int)(r % Coutp), tap = (int)((r / Coutp) % 9), cb = (int)(r / ((size_t)Coutp * 9));
+        const int ci = cb * 16 + j;
+        Wm[i] = __float2bfloat16_rn((co < Cout && ci < Cin) ? W[((size_t)co * Cin + ci) * 9 + tap] : 0.f);
     }
 }
 
@@ -432,6 +547,8 @@ struct devel_dsn {
         size_t w_off, b_off;  // into the flat parameter vector
         __nv_bfloat16* Wb = nullptr;
         __nv_bfloat16* Wt = nullptr;
+        __nv_bfloat16* Wm = nullptr;  // tensor-core layout of the forward weights
+        int coutp = 0;
     };
     std::vector<Conv> convs;
     size_t nparams = 0;
@@ -465,6 +582,7 @@ void free_dsn(devel_dsn* d) {
     for (auto& cv : d->convs) {
         cudaFree(cv.Wb);
         cudaFree(cv.Wt);
+        cudaFree(cv.Wm);
     }
     for (auto& a : d->acts) {
         cudaFree(a.a);
@@ -479,11 +597,10 @@ void free_dsn(devel_dsn* d) {
 int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
              __nv_bfloat16* Y, cudaStream_t s) {
     const auto& cv = d->convs[ci];
-    const int ctiles = ((side + kCT - 1) / kCT) * ((side + kCT - 1) / kCT);
-    dim3 grid(ctiles, (cv.cout + kCoB - 1) / kCoB, nb);
-    k_conv3<__nv_bfloat16, true><<<grid, 256, 0, s>>>(XA, CA, XB, CB, cv.Wb, d->P + cv.b_off, 1, Y, cv.cout, nullptr, 0,
-                                                     side, side, cv.cout);
-    DEVEL_LAUNCH_CHECK("k_conv3");
+    const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
+    dim3 grid(mtiles, cv.coutp / kMCo, nb);
+    k_conv3_mma<<<grid, 256, 0, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y, side, side, cv.cout);
+    DEVEL_LAUNCH_CHECK("k_conv3_mma");
     return DEVEL_OK;
 }
 
@@ -518,6 +635,8 @@ int prep_weights(devel_dsn* d, cudaStream_t s) {
         if (cv.k != 3) continue;
         const size_t wc = (size_t)cv.cout * cv.cin * 9;
         k_prep_w<<<grid1(wc), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.Wb, cv.Wt);
+        const size_t wm = (size_t)((cv.cin + 15) / 16) * 9 * cv.coutp * 16;
+        k_prep_wm<<<grid1(wm), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.coutp, cv.Wm);
     }
     DEVEL_LAUNCH_CHECK("k_prep_w");
     return DEVEL_OK;
@@ -642,8 +761,11 @@ int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
         cv.b_off = off;
         off += l[1];
         if (l[2] == 3 && e == cudaSuccess) {
+            cv.coutp = (l[1] + kMCo - 1) / kMCo * kMCo;
             e = cudaMalloc(&cv.Wb, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
             if (e == cudaSuccess) e = cudaMalloc(&cv.Wt, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
+            if (e == cudaSuccess)
+                e = cudaMalloc(&cv.Wm, sizeof(__nv_bfloat16) * ((l[0] + 15) / 16) * 9 * cv.coutp * 16);
         }
         d->convs.push_back(cv);
     }
