@@ -860,11 +860,28 @@ def run_learned(args, wl):
 def run_calls_once(args, wl):
     """Each ABI call of the hot path once at the workload's size, through the public
     API (TSDF, forward, resist/loss, adjoint, level-set step), for kernel captures with
-    ncu; prints one line of results, no timing."""
+    ncu; prints one line of results, no timing. For the learned workload: one DSN
+    inference and one training step on a batch of synthetic targets."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2303_12529_gb300 as dv
+    if "learned" in wl:
+        n, B = wl["n"], wl["dsn_batch"]
+        d2 = torch.empty(n * n, dtype=torch.int32, device="cuda")
+        tsdf = torch.empty(B, n * n, dtype=torch.float32, device="cuda")
+        for i in range(B):
+            tgt = torch.from_numpy(synth.rect_clip(wl["seed_train"] + i).ravel().copy()).cuda()
+            dv.devel_reinit_sdf(n, tgt, tsdf[i], d2)
+        net = dv.Dsn(n, B, wl["width"], seed=1)
+        phi0 = torch.empty_like(tsdf)
+        net.forward(B, tsdf, phi0)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        net.train_step(B, tsdf, tsdf + 2.0, wl["lr"], loss)
+        torch.cuda.synchronize()
+        print(json.dumps({"calls_once": args.workload, "dsn_loss": float(loss.item()),
+                          "phi0_mean": float(phi0.mean().item())}), flush=True)
+        return
     n, K, k, beta = wl["n"], wl["K"], wl["k"], wl["beta"]
     prec = {"fp32": dv.DEVEL_PREC_FP32, "bf16x3": dv.DEVEL_PREC_BF16X3, "both": dv.DEVEL_PREC_BF16X3}[args.precision]
     o = synth.optics(n, K, k)
