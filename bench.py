@@ -749,6 +749,7 @@ def run_learned(args, wl):
     o = synth.optics(n, K, k)
     G = 64                                               # clips per devel_ilt_solve call
     handles = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3) for _ in range(G)]
+    handles32 = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_FP32) for _ in range(G)]
     N = n * n
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     d2 = torch.empty(N, dtype=torch.int32, device=dev)
@@ -758,12 +759,13 @@ def run_learned(args, wl):
 
     bufs = {}
 
-    def solve_all(tg, iters, phi0=None):
+    def solve_all(tg, iters, phi0=None, hs=None):
         """Solves every clip (phi0 given: from phi0, in place); returns (phi [count, N],
         final L2 + PVB per clip). Buffers persist per (set, iterations, start), so a
         repeated call replays the graphs captured by the first."""
         cnt = tg.shape[0]
-        key = (tg.data_ptr(), iters, phi0 is not None)
+        hs = hs or handles
+        key = (tg.data_ptr(), iters, phi0 is not None, id(hs))
         if key not in bufs:
             W = (iters + 2) // 2 * 2
             bufs[key] = (torch.empty(cnt, N, dtype=torch.float32, device=dev),
@@ -774,7 +776,7 @@ def run_learned(args, wl):
             phi = phi0
         p = dv.ilt_params(dv.resist_params(beta=beta), iters=iters, use_graph=tg.shape[0] <= 256)
         for c0 in range(0, cnt, G):
-            clips = [dv.Clip(handles[j], tg[c0 + j], phi[c0 + j], phi_given=phi0 is not None,
+            clips = [dv.Clip(hs[j], tg[c0 + j], phi[c0 + j], phi_given=phi0 is not None,
                              l2_hist=l2[c0 + j, :iters + 1], pvb_hist=pvb[c0 + j, :iters + 1])
                      for j in range(min(G, cnt - c0))]
             dv.devel_ilt_solve(p, clips, st, stream)
@@ -820,6 +822,13 @@ def run_learned(args, wl):
     _, q_plain = solve_all(te, wl["plain_iters"])
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
+    # the plain FP32 solver (the comparator the scope names): 100 iterations
+    solve_all(te, wl["plain_iters"], hs=handles32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, q_fp32 = solve_all(te, wl["plain_iters"], hs=handles32)
+    torch.cuda.synchronize()
+    t_fp32 = time.perf_counter() - t0
     # learned: DSN phi_0, then 15 iterations
     phi0 = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
 
@@ -839,7 +848,7 @@ def run_learned(args, wl):
     # the same 15 iterations from the plain start (what the learned phi_0 buys)
     _, q_short = solve_all(te, wl["refine_iters"])
     torch.cuda.synchronize()
-    qp, ql, qs = (q.double().mean().item() for q in (q_plain, q_learned, q_short))
+    qp, ql, qs, qf = (q.double().mean().item() for q in (q_plain, q_learned, q_short, q_fp32))
     out = {"metric": "ILT clips/sec to converged L2+PVB at 256^2 (DSN phi_0 + 15 iterations vs 100 plain)",
            "value": wl["test"] / t_learned, "unit": "clips/s", "n_gpus": 1, "steps": 1, "warmup": 1,
            "ms_per_step": t_learned * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -848,7 +857,10 @@ def run_learned(args, wl):
                                                                           "plain_iters", "refine_iters", "width",
                                                                           "dsn_batch", "epochs", "lr")},
                       "timing": "host clock around the whole test set, inputs resident"},
-           "plain": {"value": wl["test"] / t_plain, "mean_l2_pvb": qp},
+           "plain": {"value": wl["test"] / t_plain, "mean_l2_pvb": qp, "precision": "bf16x3"},
+           "plain_fp32": {"value": wl["test"] / t_fp32, "mean_l2_pvb": qf,
+                          "speedup_learned_bf16_vs_plain_fp32": t_fp32 / t_learned,
+                          "learned_ratio_to_fp32": ql / qf},
            "learned": {"mean_l2_pvb": ql, "ratio_to_plain": ql / qp, "converged_within_1pct": bool(ql <= 1.01 * qp)},
            "plain_15_iterations": {"mean_l2_pvb": qs, "ratio_to_plain": qs / qp},
            "speedup_vs_plain": t_plain / t_learned,
