@@ -387,6 +387,16 @@ int devel_dsn_forward(devel_dsn* dsn, int nb, const float* tsdf, float band, flo
  * step) or NULL. */
 int devel_dsn_train_step(devel_dsn* dsn, int nb, const float* tsdf, const float* phi_gt, float band, float lr,
                          double* loss_out, cudaStream_t stream);
+/* The same network as the modulation branch (Sec. III-B): its output y is read as
+ * phi_m and m = H_eps(y) = (1 + (2/pi) atan(y / eps)) / 2 (the approximated Heaviside;
+ * the paper: eps = 0.03). forward_ahf writes m (device float [nb][side][side]);
+ * train_step_ahf takes one Adam step on mean (H_eps(y) - m_gt)^2 (the per-pixel L_m,
+ * averaged) against 0 / 1 label maps m_gt (devel_modulation_candidates, picked by the
+ * label search). */
+int devel_dsn_forward_ahf(devel_dsn* dsn, int nb, const float* tsdf, float band, float eps, float* m_out,
+                          cudaStream_t stream);
+int devel_dsn_train_step_ahf(devel_dsn* dsn, int nb, const float* tsdf, const float* m_gt, float band, float eps,
+                             float lr, double* loss_out, cudaStream_t stream);
 
 /*
  * Run `params->iters` DSO iterations on each clip (host array of nclips):

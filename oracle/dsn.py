@@ -166,6 +166,18 @@ def mse(y, label):
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
+def ahf_mean(y, m_gt, eps: float):
+    """Loss of the modulation branch (Sec. III-B, L_m per pixel, averaged): the branch's
+    output y is read as phi_m and passed through the approximated Heaviside
+    H_eps(y) = (1 + (2/pi) atan(y/eps)) / 2; returns mean (H_eps(y) - m_gt)^2 and its
+    gradient in y."""
+    y = np.asarray(y, dtype=np.float64)
+    h = 0.5 * (1.0 + (2.0 / np.pi) * np.arctan(y / eps))
+    r = h - np.asarray(m_gt, dtype=np.float64)
+    dh = (1.0 / np.pi) * eps / (eps * eps + y * y)
+    return float(np.mean(r * r)), 2.0 * r * dh / r.size
+
+
 @dataclass
 class Adam:
     lr: float = 1e-3

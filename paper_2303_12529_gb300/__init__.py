@@ -99,6 +99,8 @@ _sig("devel_dsn_get_params", [_P, _P])
 _sig("devel_dsn_grads", [_P, _P])
 _sig("devel_dsn_forward", [_P, _I, _P, _F, _P, _P])
 _sig("devel_dsn_train_step", [_P, _I, _P, _P, _F, _F, _P, _P])
+_sig("devel_dsn_forward_ahf", [_P, _I, _P, _F, _F, _P, _P])
+_sig("devel_dsn_train_step_ahf", [_P, _I, _P, _P, _F, _F, _F, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
@@ -122,7 +124,8 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction",
             "devel_modulation_candidates", "devel_ahf_loss", "devel_dsn_create", "devel_dsn_destroy",
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
-            "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step")
+            "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
+            "devel_dsn_train_step_ahf")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -370,6 +373,21 @@ class Dsn:
         N = nb * self.side * self.side
         _check(_lib.devel_dsn_forward(self.handle, nb, _ptr(tsdf, torch.float32, N, "tsdf"), float(band),
                                       _ptr(phi0, torch.float32, N, "phi0"), _stream(stream)))
+
+    def forward_ahf(self, nb: int, tsdf, m_out, eps: float = 0.03, band: float = 16.0, stream=None):
+        import torch
+        N = nb * self.side * self.side
+        _check(_lib.devel_dsn_forward_ahf(self.handle, nb, _ptr(tsdf, torch.float32, N, "tsdf"), float(band),
+                                          float(eps), _ptr(m_out, torch.float32, N, "m_out"), _stream(stream)))
+
+    def train_step_ahf(self, nb: int, tsdf, m_gt, lr: float, loss_out=None, eps: float = 0.03, band: float = 16.0,
+                       stream=None):
+        import torch
+        N = nb * self.side * self.side
+        _check(_lib.devel_dsn_train_step_ahf(self.handle, nb, _ptr(tsdf, torch.float32, N, "tsdf"),
+                                             _ptr(m_gt, torch.float32, N, "m_gt"), float(band), float(eps),
+                                             float(lr), _ptr(loss_out, torch.float64, 1, "loss_out"),
+                                             _stream(stream)))
 
     def train_step(self, nb: int, tsdf, phi_gt, lr: float, loss_out=None, band: float = 16.0, stream=None):
         import torch

@@ -491,6 +491,47 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const 
     *counter = 0u;
 }
 
+// modulation-branch loss: loss = mean (H_eps(y) - m)^2, dy = 2 (H_eps(y) - m) H_eps'(y) / count
+// with H_eps(y) = 1/2 + atan(y / eps) / pi (exact fixed point across blocks)
+__global__ void __launch_bounds__(256) k_ahf_mse(const float* __restrict__ y, const float* __restrict__ m, size_t count,
+                                                 float eps, float* __restrict__ dy, long long* __restrict__ qpart,
+                                                 unsigned* counter, double* loss) {
+    __shared__ float sh[8];
+    __shared__ bool last;
+    const float scale = 2.f / (float)count, inv_eps = 1.f / eps;
+    float s = 0.f;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < count; i += (size_t)gridDim.x * 256) {
+        const float v = y[i];
+        const float r = 0.5f + atanf(v * inv_eps) * 0.318309886f - m[i];
+        s = fmaf(r, r, s);
+        dy[i] = scale * r * (eps * 0.318309886f) / fmaf(v, v, eps * eps);
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) {
+        qpart[blockIdx.x] = to_q32(s);
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    long long q = 0;
+    bool bad = false;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+        const long long v = __ldcg(qpart + i);
+        bad |= v == kQBad;
+        q += v;
+    }
+    *loss = bad ? __longlong_as_double(0x7ff8000000000000ll) : (double)q * (1.0 / 4294967296.0) / (double)count;
+    *counter = 0u;
+}
+
+__global__ void k_ahf_out(const float* __restrict__ y, size_t count, float eps, float* __restrict__ m) {
+    const float inv_eps = 1.f / eps;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        m[i] = 0.5f + atanf(y[i] * inv_eps) * 0.318309886f;
+}
+
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M, float* __restrict__ V,
                        size_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -883,8 +924,54 @@ int devel_dsn_forward(devel_dsn* d, int nb, const float* tsdf, float B, float* p
     return DEVEL_OK;
 }
 
+}  // extern "C"
+
+namespace devel {
+namespace {
+// one training step; ahf_eps > 0: the modulation branch's loss against labels in
+// `label` (0 / 1 maps), else the MSE against the band-limited level set `label`
+int dsn_train(devel_dsn* d, int nb, const float* tsdf, const float* label, float B, float lr, float ahf_eps,
+              double* loss_out, cudaStream_t s);
+}  // namespace
+}  // namespace devel
+
+extern "C" {
+
 int devel_dsn_train_step(devel_dsn* d, int nb, const float* tsdf, const float* phi_gt, float B, float lr,
                          double* loss_out, cudaStream_t s) {
+    return dsn_train(d, nb, tsdf, phi_gt, B, lr, 0.f, loss_out, s);
+}
+
+int devel_dsn_train_step_ahf(devel_dsn* d, int nb, const float* tsdf, const float* m_gt, float B, float eps, float lr,
+                             double* loss_out, cudaStream_t s) {
+    if (!(eps > 0.f)) return set_error(DEVEL_EINVAL, "devel_dsn_train_step_ahf: eps must be > 0");
+    return dsn_train(d, nb, tsdf, m_gt, B, lr, eps, loss_out, s);
+}
+
+int devel_dsn_forward_ahf(devel_dsn* d, int nb, const float* tsdf, float B, float eps, float* m_out, cudaStream_t s) {
+    if (!d) return set_error(DEVEL_EINVAL, "devel_dsn_forward_ahf: dsn is NULL");
+    if (nb < 1 || nb > d->batch)
+        return set_error(DEVEL_EINVAL, "devel_dsn_forward_ahf: nb=%d outside [1, %d]", nb, d->batch);
+    if (bad_ptr(tsdf) || bad_ptr(m_out))
+        return set_error(DEVEL_EINVAL, "devel_dsn_forward_ahf: tsdf / m_out NULL or not 16-byte aligned");
+    if (!(B > 0.f) || !(eps > 0.f)) return set_error(DEVEL_EINVAL, "devel_dsn_forward_ahf: band and eps must be > 0");
+    const size_t px = (size_t)nb * d->S * d->S;
+    int rc = prep_weights(d, s);
+    if (rc) return rc;
+    k_band<<<grid1(px), 256, 0, s>>>(tsdf, px, B, d->x, d->xb);
+    rc = forward(d, nb, s);
+    if (rc) return rc;
+    k_ahf_out<<<grid1(px), 256, 0, s>>>(d->y, px, eps, m_out);
+    DEVEL_LAUNCH_CHECK("devel_dsn_forward_ahf");
+    return DEVEL_OK;
+}
+
+}  // extern "C"
+
+namespace devel {
+namespace {
+int dsn_train(devel_dsn* d, int nb, const float* tsdf, const float* phi_gt, float B, float lr, float ahf_eps,
+              double* loss_out, cudaStream_t s) {
     if (!d) return set_error(DEVEL_EINVAL, "devel_dsn_train_step: dsn is NULL");
     if (nb < 1 || nb > d->batch)
         return set_error(DEVEL_EINVAL, "devel_dsn_train_step: nb=%d outside [1, %d]", nb, d->batch);
@@ -897,10 +984,15 @@ int devel_dsn_train_step(devel_dsn* d, int nb, const float* tsdf, const float* p
     k_band<<<grid1(px), 256, 0, s>>>(tsdf, px, B, d->x, d->xb);
     rc = forward(d, nb, s);
     if (rc) return rc;
-    // labels band-limited into dy's buffer first, then the MSE overwrites it with dL/dy
-    k_band<<<grid1(px), 256, 0, s>>>(phi_gt, px, B, d->dy, nullptr);
     const int mb = grid1(px);
-    k_mse<<<mb, 256, 0, s>>>(d->y, d->dy, px, d->dy, d->qpart, d->counter, loss_out ? loss_out : d->loss);
+    if (ahf_eps > 0.f) {
+        k_ahf_mse<<<mb, 256, 0, s>>>(d->y, phi_gt, px, ahf_eps, d->dy, d->qpart, d->counter,
+                                     loss_out ? loss_out : d->loss);
+    } else {
+        // labels band-limited into dy's buffer first, then the MSE overwrites it with dL/dy
+        k_band<<<grid1(px), 256, 0, s>>>(phi_gt, px, B, d->dy, nullptr);
+        k_mse<<<mb, 256, 0, s>>>(d->y, d->dy, px, d->dy, d->qpart, d->counter, loss_out ? loss_out : d->loss);
+    }
     rc = backward(d, nb, s);
     if (rc) return rc;
     d->t += 1;
@@ -910,6 +1002,10 @@ int devel_dsn_train_step(devel_dsn* d, int nb, const float* tsdf, const float* p
     DEVEL_LAUNCH_CHECK("devel_dsn_train_step");
     return DEVEL_OK;
 }
+}  // namespace
+}  // namespace devel
+
+extern "C" {
 
 int devel_dsn_grads(const devel_dsn* d, float* host) {
     if (!d || !host) return set_error(DEVEL_EINVAL, "devel_dsn_grads: NULL argument");

@@ -123,3 +123,31 @@ def test_training_lowers_the_loss():
         torch.cuda.synchronize()
         hist.append(float(host(loss)[0]))
     assert np.isfinite(hist).all() and hist[-1] < 0.5 * hist[0]
+
+
+def test_modulation_branch_step_matches_oracle():
+    """The modulation branch (Sec. III-B): H_eps of the output, the averaged L_m, its
+    gradients and the first Adam step, against the oracle storing in BF16 where the GPU
+    does."""
+    dv = need_gpu()
+    net = dv.Dsn(SIDE, BATCH, WIDTH, seed=7)
+    flat0 = net.get_params()
+    P = _unflatten(flat0, WIDTH)
+    tsdf, _ = _batch(5)
+    m_gt = (tsdf > 1.5).astype(np.float32)           # a 0 / 1 label map
+    x = dsn.band(tsdf[:, None].astype(np.float64), B)
+    m = torch.empty(BATCH * SIDE * SIDE, dtype=torch.float32, device="cuda")
+    net.forward_ahf(BATCH, dev(tsdf), m, 0.03, B)
+    torch.cuda.synchronize()
+    y16, cache = dsn.forward(P, x, store=bf16)
+    from oracle import modulation
+    assert rel_err(host(m).reshape(y16.shape), modulation.ahf(y16, 0.03)) <= 2e-2
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.train_step_ahf(BATCH, dev(tsdf), dev(m_gt), 1e-3, loss, 0.03, B)
+    torch.cuda.synchronize()
+    L, dy = dsn.ahf_mean(y16, m_gt[:, None].astype(np.float64), 0.03)
+    G = dsn.backward(P, x, cache, dy)
+    assert abs(float(host(loss)[0]) - L) <= 1e-2 * L
+    Gg = _unflatten(net.grads(), WIDTH)
+    for i, (a, b) in enumerate(zip(Gg, G)):
+        assert rel_err(a, b) <= 5e-2, (i, rel_err(a, b))

@@ -97,3 +97,21 @@ def test_zero_head_returns_the_input_level_set():
     P[-1][...] = 0.0
     x = dsn.band(np.random.default_rng(2).uniform(-30, 30, (1, 1, 16, 16)))
     assert np.array_equal(dsn.forward(P, x)[0], x)
+
+
+def test_modulation_loss_gradient_and_limits():
+    """The modulation branch's loss: gradient against finite differences; zero when
+    the labels equal H_eps of the output; its H_eps is the one of the modulation
+    supervision (oracle/modulation.py)."""
+    from oracle import modulation
+    rng = np.random.default_rng(9)
+    y = rng.uniform(-0.2, 0.2, (1, 1, 5, 5))
+    m = (rng.random((1, 1, 5, 5)) < 0.5).astype(float)
+    L, g = dsn.ahf_mean(y, m, 0.03)
+    h = 1e-7
+    for idx in [(0, 0, 0, 0), (0, 0, 2, 3), (0, 0, 4, 4)]:
+        e = np.zeros_like(y); e[idx] = h
+        fd = (dsn.ahf_mean(y + e, m, 0.03)[0] - dsn.ahf_mean(y - e, m, 0.03)[0]) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    assert dsn.ahf_mean(y, modulation.ahf(y, 0.03), 0.03)[0] == 0.0
+    assert L * y.size == pytest.approx(modulation.ahf_loss(y, m, 0.03)[0], rel=1e-12)
