@@ -45,7 +45,9 @@ WORKLOADS = {
     # rectangle clips labelled with this solver's converged phi (100 plain iterations),
     # then on 256 held-out clips compare DSN phi_0 + 15 iterations with 100 plain ones
     "learned256": dict(learned=True, n=256, K=8, k=15, beta=7.5, train=2000, test=256, seed_train=10000,
-                       seed_test=20000, plain_iters=100, refine_iters=15, width=32, dsn_batch=16, epochs=6, lr=1e-3),
+                       seed_test=20000, plain_iters=100, refine_iters=15, width=32, dsn_batch=16, epochs=6, lr=1e-3,
+                       # modulation branch: labels for the first 256 training clips from 8 shifts each
+                       mod_train=256, mod_cands=8, mod_epochs=8, ahf_eps=0.03),
 }
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -759,13 +761,13 @@ def run_learned(args, wl):
 
     bufs = {}
 
-    def solve_all(tg, iters, phi0=None, hs=None):
+    def solve_all(tg, iters, phi0=None, hs=None, m=None):
         """Solves every clip (phi0 given: from phi0, in place); returns (phi [count, N],
         final L2 + PVB per clip). Buffers persist per (set, iterations, start), so a
         repeated call replays the graphs captured by the first."""
         cnt = tg.shape[0]
         hs = hs or handles
-        key = (tg.data_ptr(), iters, phi0 is not None, id(hs))
+        key = (tg.data_ptr(), iters, phi0 is not None, id(hs), None if m is None else m.data_ptr())
         if key not in bufs:
             W = (iters + 2) // 2 * 2
             bufs[key] = (torch.empty(cnt, N, dtype=torch.float32, device=dev),
@@ -777,6 +779,7 @@ def run_learned(args, wl):
         p = dv.ilt_params(dv.resist_params(beta=beta), iters=iters, use_graph=tg.shape[0] <= 256)
         for c0 in range(0, cnt, G):
             clips = [dv.Clip(hs[j], tg[c0 + j], phi[c0 + j], phi_given=phi0 is not None,
+                             m=None if m is None else m[c0 + j],
                              l2_hist=l2[c0 + j, :iters + 1], pvb_hist=pvb[c0 + j, :iters + 1])
                      for j in range(min(G, cnt - c0))]
             dv.devel_ilt_solve(p, clips, st, stream)
@@ -812,6 +815,40 @@ def run_learned(args, wl):
     t_train = time.perf_counter() - t0
     steps = wl["epochs"] * (wl["train"] // B)
 
+    # modulation branch (Sec. III-B): labels by search over H(phi_gt + dh), then training
+    t0 = time.perf_counter()
+    Nm, J = wl["mod_train"], wl["mod_cands"]
+    cand = torch.empty(Nm * J, N, dtype=torch.float32, device=dev)
+    dh_all = rng.uniform(-20.0, 20.0, (Nm, J)).astype(np.float32)
+    for i in range(Nm):
+        dv.devel_modulation_candidates(n, phi_gt[i], list(dh_all[i]), cand[i * J:(i + 1) * J])
+    tg_rep = tr[:Nm].repeat_interleave(J, dim=0).contiguous()
+    cphi = torch.empty(Nm * J, N, dtype=torch.float32, device=dev)
+    W = (wl["plain_iters"] + 2) // 2 * 2
+    closs = torch.zeros(Nm * J, W, dtype=torch.float64, device=dev)
+    pl = dv.ilt_params(dv.resist_params(beta=beta), iters=wl["plain_iters"], use_graph=False)
+    for c0 in range(0, Nm * J, G):
+        clips = [dv.Clip(handles[j], tg_rep[c0 + j], cphi[c0 + j], m=cand[c0 + j],
+                         loss_hist=closs[c0 + j, :wl["plain_iters"] + 1]) for j in range(min(G, Nm * J - c0))]
+        dv.devel_ilt_solve(pl, clips, st, stream)
+    best = closs[:, wl["plain_iters"]].view(Nm, J).argmin(dim=1)
+    m_gt = cand.view(Nm, J, N)[torch.arange(Nm, device=dev), best].contiguous()
+    torch.cuda.synchronize()
+    t_mlabel = time.perf_counter() - t0
+    mnet = dv.Dsn(n, B, wl["width"], seed=2)
+    mlosses = []
+    t0 = time.perf_counter()
+    for ep in range(wl["mod_epochs"]):
+        order = torch.from_numpy(rng.permutation(Nm)).to(dev)
+        lr = wl["lr"] * (0.5 ** (ep // 2))
+        for b0 in range(0, Nm - B + 1, B):
+            idx = order[b0:b0 + B]
+            mnet.train_step_ahf(B, x_tr[idx].contiguous(), m_gt[idx].contiguous(), lr, loss, wl["ahf_eps"], 16.0,
+                                stream)
+        torch.cuda.synchronize()
+        mlosses.append(float(loss.item()))
+    t_mtrain = time.perf_counter() - t0
+
     te = targets(wl["seed_test"], wl["test"])
     x_te = tsdf_all(te)
     torch.cuda.synchronize()
@@ -845,10 +882,27 @@ def run_learned(args, wl):
     _, q_learned = solve_all(te, wl["refine_iters"], phi0)
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
+    # learned phi_0 and learned modulation m = H_eps(phi_m): both branches, then 15 iterations
+    m_te = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
+
+    def predict_both():
+        predict()
+        for b0 in range(0, wl["test"], B):
+            nb = min(B, wl["test"] - b0)
+            mnet.forward_ahf(nb, x_te[b0:b0 + nb].contiguous(), m_te[b0:b0 + nb], wl["ahf_eps"], 16.0, stream)
+
+    predict_both()
+    solve_all(te, wl["refine_iters"], phi0, m=m_te)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    predict_both()
+    _, q_mod = solve_all(te, wl["refine_iters"], phi0, m=m_te)
+    torch.cuda.synchronize()
+    t_mod = time.perf_counter() - t0
     # the same 15 iterations from the plain start (what the learned phi_0 buys)
     _, q_short = solve_all(te, wl["refine_iters"])
     torch.cuda.synchronize()
-    qp, ql, qs, qf = (q.double().mean().item() for q in (q_plain, q_learned, q_short, q_fp32))
+    qp, ql, qs, qf, qm = (q.double().mean().item() for q in (q_plain, q_learned, q_short, q_fp32, q_mod))
     out = {"metric": "ILT clips/sec to converged L2+PVB at 256^2 (DSN phi_0 + 15 iterations vs 100 plain)",
            "value": wl["test"] / t_learned, "unit": "clips/s", "n_gpus": 1, "steps": 1, "warmup": 1,
            "ms_per_step": t_learned * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -863,6 +917,12 @@ def run_learned(args, wl):
                           "learned_ratio_to_fp32": ql / qf},
            "learned": {"mean_l2_pvb": ql, "ratio_to_plain": ql / qp, "converged_within_1pct": bool(ql <= 1.01 * qp)},
            "plain_15_iterations": {"mean_l2_pvb": qs, "ratio_to_plain": qs / qp},
+           "learned_with_modulation": {"value": wl["test"] / t_mod, "mean_l2_pvb": qm, "ratio_to_plain": qm / qp,
+                                       "ratio_to_learned": qm / ql,
+                                       "labels": {"clips": wl["mod_train"], "candidates": wl["mod_cands"],
+                                                  "seconds": t_mlabel,
+                                                  "picked_histogram": torch.bincount(best, minlength=J).tolist()},
+                                       "training": {"seconds": t_mtrain, "epoch_losses": mlosses}},
            "speedup_vs_plain": t_plain / t_learned,
            "training": {"seconds": t_train, "steps": steps, "samples_per_s": steps * B / t_train,
                         "epoch_losses": losses, "label_seconds": t_label}}
