@@ -389,7 +389,8 @@ def run_ours(args, wl):
         e2e_value = world * 1000.0 / job_time_ms(float(np.median(e2e_ms)), dist, dev)
         res = {"prec": prec_name, "ms": ms, "value": world * 1000.0 / ms, "clocks": clocks, "prof": prof,
                "dom": dom, "dom_prof": dom_prof, "ms_profiled": ms_profiled, "e2e": e2e_value, "final_l2": int(l2[-1].item()),
-               "final_pvb": int(pvb[-1].item()), "final_loss": float(L[-1].item())}
+               "final_pvb": int(pvb[-1].item()), "final_loss": float(L[-1].item()),
+               "final_shots": dv.devel_shot_count(M.view(n, n).cpu().numpy())}
         dv.devel_optics_destroy(opt)
         if optd:
             dv.devel_optics_destroy(optd)
@@ -483,7 +484,7 @@ def run_ours(args, wl):
             "kernels": kernels,
             "clocks": head["clocks"],
             "cpu_baseline": cpu,
-            "final_l2": head["final_l2"], "final_pvb": head["final_pvb"],
+            "final_l2": head["final_l2"], "final_pvb": head["final_pvb"], "final_shots": head["final_shots"],
         }
         if batch_info:
             out["batched_4_clips"] = batch_info
@@ -493,6 +494,7 @@ def run_ours(args, wl):
             q_ref = ref["final_l2"] + ref["final_pvb"]
             out["plain_fp32"] = {"value": ref["value"], "ms_per_step": ref["ms"], "e2e": ref["e2e"],
                                  "final_l2": ref["final_l2"], "final_pvb": ref["final_pvb"],
+                                 "final_shots": ref["final_shots"],
                                  "clocks": ref["clocks"]}
             out["converged"] = {"rule": "final L2 + PVB within 1% of the plain FP32 solve's",
                                 "ok": bool(q_head <= 1.01 * q_ref), "ratio": q_head / max(q_ref, 1),

@@ -13,6 +13,7 @@
  *   devel_cg_direction    Sec. III-C conjugate-gradient direction of the velocity
  *   devel_modulation_candidates, devel_ahf_loss   Sec. III-B modulation-branch supervision
  *   devel_dsn_*           Sec. III-B DSN level-set branch: learned initial level set, training
+ *   devel_shot_count      Sec. II-C.3 mask fracturing shot count (host)
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
  *
  * Conventions shared by every call
@@ -353,6 +354,16 @@ int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const flo
  */
 int devel_ahf_loss(const devel_optics* optics, const float* phi_m, const float* m_gt, float eps,
                    double* loss_out, float* grad_out, cudaStream_t stream);
+
+/*
+ * Mask fracturing shot count (Sec. II-C.3): the number of rectangles the mask is
+ * fractured into, read as the minimum number of non-overlapping axis-aligned
+ * rectangles whose union is the mask (exact: per 4-connected piece, vertices / 2 +
+ * holes - g - 1 with g the largest set of non-intersecting chords between reflex
+ * vertices, from a bipartite matching). Host code, synchronous.
+ *   mask_host  host uint8[n*n] (nonzero = mask)    count_out  host long long[1]
+ */
+int devel_shot_count(int n, const unsigned char* mask_host, long long* count_out);
 
 /*
  * Level-set branch of DevelSet-Net (Sec. III-B): a convolutional encoder-decoder

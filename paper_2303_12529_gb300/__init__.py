@@ -90,6 +90,7 @@ _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
 _sig("devel_modulation_candidates", [_I, _P, _I, _P, _P, _P])
 _sig("devel_ahf_loss", [_P, _P, _P, _F, _P, _P, _P])
+_sig("devel_shot_count", [_I, _P, ctypes.POINTER(ctypes.c_longlong)])
 _sig("devel_dsn_create", [_I, _I, _I, ctypes.POINTER(_P)])
 _sig("devel_dsn_destroy", [_P])
 _sig("devel_dsn_param_count", [_P], ctypes.c_longlong)
@@ -122,7 +123,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_profile_stop", "devel_profile_kinds", "devel_profile_query", "devel_profile_collect",
             "devel_reinit_sdf_static", "devel_profile_select", "devel_optics_autotune", "devel_optics_config",
             "devel_selftest_bounded_wait", "devel_levelset_step_weno5", "devel_cg_direction",
-            "devel_modulation_candidates", "devel_ahf_loss", "devel_dsn_create", "devel_dsn_destroy",
+            "devel_modulation_candidates", "devel_ahf_loss", "devel_shot_count", "devel_dsn_create", "devel_dsn_destroy",
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
             "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
             "devel_dsn_train_step_ahf")
@@ -324,6 +325,16 @@ def modulation_search(handles, target, phi_gt, dh, params: "devel_ilt_params", s
     if int(st.item()) != 0:
         raise DevelError(int(st.item()), "modulation_search: a candidate solve reported a non-finite loss")
     return int(np.argmin(final)), final, cands.view(len(dh), N)
+
+
+def devel_shot_count(mask) -> int:
+    """Minimum rectangle partition of a square host mask (numpy uint8 [n, n])."""
+    import numpy as np
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    assert m.ndim == 2 and m.shape[0] == m.shape[1]
+    out = ctypes.c_longlong()
+    _check(_lib.devel_shot_count(m.shape[0], m.ctypes.data, ctypes.byref(out)))
+    return int(out.value)
 
 
 class Dsn:
