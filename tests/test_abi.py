@@ -81,3 +81,25 @@ def test_ilt_params_layout_matches_the_header():
     fields = re.findall(r"\b(\w+)\s*(?:,\s*(\w+))?\s*;", body)
     flat = [x for pair in fields for x in pair if x]
     assert flat[-2:] == ["upwind", "optimizer"]
+
+
+def test_new_entry_points_refuse_bad_arguments_without_a_device(lib):
+    import paper_2303_12529_gb300 as dv
+    c = ctypes
+    lib.devel_modulation_candidates.argtypes = [c.c_int, c.c_void_p, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p]
+    dh = (c.c_float * 2)(1.0, float("nan"))
+    assert lib.devel_modulation_candidates(64, 16, 0, dh, 32, None) == dv.DEVEL_EINVAL        # no candidates
+    assert lib.devel_modulation_candidates(64, 16, 65, dh, 32, None) == dv.DEVEL_EINVAL       # too many
+    assert lib.devel_modulation_candidates(64, 16, 2, dh, 32, None) == dv.DEVEL_EINVAL        # NaN shift
+    assert "finite" in dv.devel_last_error()
+    lib.devel_ahf_loss.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p, c.c_float, c.c_void_p, c.c_void_p, c.c_void_p]
+    assert lib.devel_ahf_loss(None, 16, 32, 0.03, 48, None, None) == dv.DEVEL_EINVAL
+    h = c.c_void_p()
+    lib.devel_dsn_create.argtypes = [c.c_int, c.c_int, c.c_int, c.POINTER(c.c_void_p)]
+    assert lib.devel_dsn_create(40, 2, 4, c.byref(h)) == dv.DEVEL_EINVAL                      # side % 16
+    assert lib.devel_dsn_create(32, 0, 4, c.byref(h)) == dv.DEVEL_EINVAL                      # batch
+    assert h.value is None
+    lib.devel_shot_count.argtypes = [c.c_int, c.c_void_p, c.c_void_p]
+    assert lib.devel_shot_count(0, None, None) == dv.DEVEL_EINVAL
+    # the shot count is host code: it runs here
+    assert dv.devel_shot_count(np.eye(5, dtype=np.uint8)) == 5
