@@ -167,11 +167,21 @@ __device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4],
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Shared memory of k_conv3_mma: two stages (input tile and weights) so that the global
+// loads of channel block cb + 1 are in flight while block cb's MMAs run.
+constexpr int kMTile = (kMRows + 2) * (kMCols + 2) * kMPad;  // bf16 elements
+constexpr int kMW = 9 * kMCo * kMPad;
+constexpr size_t kMSmem = 2 * (size_t)(kMTile + kMW) * sizeof(bf16);
+constexpr int kMPairs = 16 * (kMRows + 2) * ((kMCols + 4) / 2);  // bf16 pairs of a tile (columns x0-2 .. x0+33)
+constexpr int kMPairPT = (kMPairs + 255) / 256;
+constexpr int kMWPT = (9 * kMCo * 2 + 255) / 256;                // uint4 of weights per thread
+
 __global__ void __launch_bounds__(256)
 k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int CB, const bf16* __restrict__ Wm,
             int Coutp, const float* __restrict__ bias, int relu, bf16* __restrict__ Y, int H, int Wd, int Cout) {
-    __shared__ __align__(16) bf16 patch[kMRows + 2][kMCols + 2][kMPad];
-    __shared__ __align__(16) bf16 wsm[9][kMCo][kMPad];
+    extern __shared__ __align__(16) uint8_t msm[];
+    bf16* patch_s = reinterpret_cast<bf16*>(msm);                  // [2][rows + 2][cols + 2][kMPad]
+    bf16* w_s = patch_s + 2 * kMTile;                              // [2][9][kMCo][kMPad]
     const int tilesx = (Wd + kMCols - 1) / kMCols;
     const int x0 = (blockIdx.x % tilesx) * kMCols, y0 = (blockIdx.x / tilesx) * kMRows;
     const int co0 = blockIdx.y * kMCo, n = blockIdx.z;
@@ -179,6 +189,69 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
     const int wm = warp & 3, wn = warp >> 2;
     const int Cin = CA + CB, ncb = (Cin + 15) / 16;
     const size_t plane = (size_t)H * Wd;
+    constexpr int kRowPairs = (kMCols + 4) / 2, kTilePairs = (kMRows + 2) * kRowPairs;
+    uint32_t pv[kMPairPT];
+    uint4 wv[kMWPT];
+    auto pix = [&](int ci, int gy, int gx) -> unsigned short {
+        if (ci >= Cin || gy < 0 || gy >= H || gx < 0 || gx >= Wd) return 0;
+        const size_t off = (size_t)gy * Wd + gx;
+        const bf16 v = ci < CA ? XA[((size_t)n * CA + ci) * plane + off] : XB[((size_t)n * CB + (ci - CA)) * plane + off];
+        return __bfloat16_as_ushort(v);
+    };
+    // global -> registers: the tile as bf16 pairs (columns x0-2+2p, x0-1+2p), and the weights
+    auto load = [&](int cb) {
+#pragma unroll
+        for (int k = 0; k < kMPairPT; ++k) {
+            const int i = threadIdx.x + k * 256;
+            uint32_t v = 0;
+            if (i < kMPairs) {
+                const int c = i / kTilePairs, rp = i % kTilePairs, r = rp / kRowPairs, p = rp % kRowPairs;
+                const int ci = cb * 16 + c, gy = y0 + r - 1, gx = x0 - 2 + 2 * p;
+                if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx + 1 < Wd) {
+                    const size_t off = (size_t)gy * Wd + gx;
+                    const bf16* src = ci < CA ? XA + ((size_t)n * CA + ci) * plane + off
+                                              : XB + ((size_t)n * CB + (ci - CA)) * plane + off;
+                    v = *reinterpret_cast<const uint32_t*>(src);
+                } else {
+                    v = (uint32_t)pix(ci, gy, gx) | ((uint32_t)pix(ci, gy, gx + 1) << 16);
+                }
+            }
+            pv[k] = v;
+        }
+        const uint4* wg = reinterpret_cast<const uint4*>(Wm + ((size_t)cb * 9 * Coutp + co0) * 16);
+#pragma unroll
+        for (int k = 0; k < kMWPT; ++k) {
+            const int i = threadIdx.x + k * 256;
+            if (i < 9 * kMCo * 2) {
+                const int tap = i / (kMCo * 2), co = (i / 2) % kMCo, h = i & 1;
+                wv[k] = wg[((size_t)tap * Coutp + co) * 2 + h];
+            }
+        }
+    };
+    // registers -> stage st of shared memory (tile channel innermost)
+    auto store = [&](int st) {
+        bf16* pt = patch_s + st * kMTile;
+#pragma unroll
+        for (int k = 0; k < kMPairPT; ++k) {
+            const int i = threadIdx.x + k * 256;
+            if (i < kMPairs) {
+                const int c = i / kTilePairs, rp = i % kTilePairs, r = rp / kRowPairs, p = rp % kRowPairs;
+                const int q0 = 2 * p - 1, q1 = 2 * p;  // tile columns of the pair (x0 - 1 is column 0)
+                if (q0 >= 0) pt[(r * (kMCols + 2) + q0) * kMPad + c] = __ushort_as_bfloat16((unsigned short)(pv[k] & 0xffff));
+                if (q1 < kMCols + 2)
+                    pt[(r * (kMCols + 2) + q1) * kMPad + c] = __ushort_as_bfloat16((unsigned short)(pv[k] >> 16));
+            }
+        }
+        bf16* wt = w_s + st * kMW;
+#pragma unroll
+        for (int k = 0; k < kMWPT; ++k) {
+            const int i = threadIdx.x + k * 256;
+            if (i < 9 * kMCo * 2) {
+                const int tap = i / (kMCo * 2), co = (i / 2) % kMCo, h = i & 1;
+                *reinterpret_cast<uint4*>(wt + (tap * kMCo + co) * kMPad + 8 * h) = wv[k];
+            }
+        }
+    };
     float acc[2][4][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -186,26 +259,14 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
-    constexpr int kPix = (kMRows + 2) * (kMCols + 2);
+    load(0);
+    store(0);
+    __syncthreads();
     for (int cb = 0; cb < ncb; ++cb) {
-        // input tile, channel innermost (zero outside the image and past Cin)
-        for (int i = threadIdx.x; i < 16 * kPix; i += 256) {
-            const int c = i / kPix, pos = i % kPix, r = pos / (kMCols + 2), q = pos % (kMCols + 2);
-            const int ci = cb * 16 + c, gy = y0 + r - 1, gx = x0 + q - 1;
-            bf16 v = __float2bfloat16_rn(0.f);
-            if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
-                const size_t off = (size_t)gy * Wd + gx;
-                v = ci < CA ? XA[((size_t)n * CA + ci) * plane + off] : XB[((size_t)n * CB + (ci - CA)) * plane + off];
-            }
-            patch[r][q][c] = v;
-        }
-        // weights of this channel block: 9 taps x 64 channels x 16, two uint4 per row
-        const uint4* wg = reinterpret_cast<const uint4*>(Wm + ((size_t)cb * 9 * Coutp + co0) * 16);
-        for (int i = threadIdx.x; i < 9 * kMCo * 2; i += 256) {
-            const int tap = i / (kMCo * 2), co = (i / 2) % kMCo, h = i & 1;
-            *reinterpret_cast<uint4*>(&wsm[tap][co][8 * h]) = wg[((size_t)tap * Coutp + co) * 2 + h];
-        }
-        __syncthreads();
+        const int st = cb & 1;
+        if (cb + 1 < ncb) load(cb + 1);  // in flight during this block's MMAs
+        const bf16* pt = patch_s + st * kMTile;
+        const bf16* wt = w_s + st * kMW;
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3;
@@ -214,19 +275,22 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
             for (int mi = 0; mi < 2; ++mi) {
                 const int mat = lane >> 3, r = lane & 7;
                 const int m = (mat & 1) * 8 + r, koff = (mat >> 1) * 8;
-                ldsm_x4(tc::smem_u32(&patch[wm + dy][16 * mi + m + dx][koff]), a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+                ldsm_x4(tc::smem_u32(pt + ((wm + dy) * (kMCols + 2) + 16 * mi + m + dx) * kMPad + koff), a[mi][0],
+                        a[mi][1], a[mi][2], a[mi][3]);
             }
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
                 const int mat = lane >> 3, r = lane & 7;
                 const int co = wn * 32 + 16 * pp + (mat >> 1) * 8 + r, koff = (mat & 1) * 8;
-                ldsm_x4(tc::smem_u32(&wsm[tap][co][koff]), b[2 * pp][0], b[2 * pp][1], b[2 * pp + 1][0], b[2 * pp + 1][1]);
+                ldsm_x4(tc::smem_u32(wt + (tap * kMCo + co) * kMPad + koff), b[2 * pp][0], b[2 * pp][1],
+                        b[2 * pp + 1][0], b[2 * pp + 1][1]);
             }
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
                 for (int nj = 0; nj < 4; ++nj) mma_16816(acc[mi][nj], a[mi], b[nj][0], b[nj][1]);
         }
+        if (cb + 1 < ncb) store(st ^ 1);  // the other stage was last read before the previous barrier
         __syncthreads();
     }
     const int g = lane >> 2, cpair = 2 * (lane & 3);
@@ -640,7 +704,13 @@ int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     const auto& cv = d->convs[ci];
     const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
     dim3 grid(mtiles, cv.coutp / kMCo, nb);
-    k_conv3_mma<<<grid, 256, 0, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y, side, side, cv.cout);
+    static bool attr = false;
+    if (!attr) {
+        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem));
+        attr = true;
+    }
+    k_conv3_mma<<<grid, 256, kMSmem, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y, side, side,
+                                          cv.cout);
     DEVEL_LAUNCH_CHECK("k_conv3_mma");
     return DEVEL_OK;
 }
