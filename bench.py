@@ -148,7 +148,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples kept for inspection (the JSON line carries their summary)
+        out = os.environ.get("DEVEL_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
