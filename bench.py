@@ -863,7 +863,7 @@ def run_learned(args, wl):
     _, q_plain = solve_all(te, wl["plain_iters"])
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    # the plain FP32 solver (the comparator the scope names): 100 iterations
+    # the plain FP32 solver (the comparator of the learned + BF16 path): 100 iterations
     solve_all(te, wl["plain_iters"], hs=handles32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

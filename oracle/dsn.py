@@ -3,7 +3,7 @@
 Sec. III-B: a convolutional encoder-decoder maps the target image to an initial
 level-set function phi_0 for DSO, trained with the mean squared error to the
 level set that DSO converges to (phi_gt); DSO then refines it (Sec. III-C). The paper
-gives no layer list. Reading (the scope's learned-initialisation workload): four
+gives no layer list. Reading: four
 levels with widths c, 2c, 4c, 8c (c = 32: 32 .. 256 channels), two 3x3 convolutions
 (zero padding 1, bias, ReLU) per level, 2x2 average pooling down, nearest-neighbour
 2x upsampling up, the encoder's level output concatenated after the upsampled
