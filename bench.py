@@ -246,6 +246,8 @@ def run_reference(args, wl):
         return
     if "batch" in wl:  # the oracle's clips/s on the full-size clip stands for every side
         wl = WORKLOADS["manhattan2048"]
+    if "learned" in wl:  # the oracle's plain solve of one 256^2 clip
+        wl = dict(WORKLOADS["rect256"], iters=wl["plain_iters"], beta=wl["beta"])
     t0 = time.perf_counter()
     vals = []
     sample = ""
