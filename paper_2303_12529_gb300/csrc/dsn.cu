@@ -7,14 +7,15 @@
 // nearest 2x upsampling, concatenation [upsampled, encoder skip] and two 3x3
 // convolutions; a 1x1 head added to the input (y = x + head). Tensors are NCHW;
 // activations are stored in BF16, weights used in BF16 (FP32 master copy, updated by
-// Adam), every sum accumulates in FP32; gradients are FP32.
+// Adam), every sum accumulates in FP32; gradients are FP32 in memory (rounded to BF16
+// where they enter a tensor-core convolution).
 //
-// Kernels: k_conv3_mma (forward convolutions on the tensor cores, warp-level BF16 MMA);
-// SIMT: k_conv3 (the input gradient as a convolution of the
-// output gradient with the flipped, transposed weights), k_conv3_wgrad (weight and
-// bias gradients per spatial tile) + k_wgrad_reduce (fixed-order sum over tiles),
-// k_relu_mask, pooling / upsampling and their adjoints, the head, the MSE and Adam.
-// Every reduction runs in a fixed order: results are reproducible.
+// Kernels: k_conv3_mma (on the tensor cores, warp-level BF16 MMA: the forward
+// convolutions, and the input gradients as convolutions of the output gradients with
+// the flipped, transposed weights); SIMT: k_conv3_wgrad (weight and bias gradients per
+// spatial tile) + k_wgrad_reduce (fixed-order sum over tiles), k_relu_mask, pooling /
+// upsampling and their adjoints, the head, the MSE and Adam. Every reduction runs in a
+// fixed order: results are reproducible.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -31,121 +32,9 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 constexpr int kT = 16;      // output tile side
-constexpr int kCoB = 16;    // output channels per block (forward)
-constexpr int kCiC = 8;     // input channels per shared-memory chunk (forward)
 constexpr int kWC = 16;     // channels per block side (weight gradients)
 
 __device__ __forceinline__ float ld(const bf16* p, size_t i) { return __bfloat162float(p[i]); }
-__device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
-
-// Y[n][co][y][x] = bias[co] + sum_{ci,u,v} W[co][ci][u][v] X[n][ci][y+u-1][x+v-1], X the
-// concatenation [XA (CA channels), XB (CB channels)] along channels, zero outside.
-// Output: bf16 (optional ReLU) into YA, or FP32 (stored or added) split along output
-// channels into YA (the first CYA channels) and YB.
-// A block computes a 32 x 32 pixel tile for 16 output channels in two groups of 128
-// threads (8 channels each); a thread computes 2 x 4 pixels x 8 channels: per input
-// channel it reads its 4 x 6 input window once and, per tap, two broadcast float4s of
-// weights (64 FMAs per two shared-memory loads).
-constexpr int kCT = 32;     // conv output tile side
-template <typename Tin, bool kBf16Out>
-__global__ void __launch_bounds__(256)
-k_conv3(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const bf16* __restrict__ W,
-        const float* __restrict__ bias, int relu, void* YA, int CYA, float* YB, int accumulate, int H, int Wd,
-        int Cout) {
-    __shared__ float patch[kCiC][kCT + 2][kCT + 2];
-    __shared__ __align__(16) float wsm[kCiC][9][kCoB];
-    const int tilesx = (Wd + kCT - 1) / kCT;
-    const int x0 = (blockIdx.x % tilesx) * kCT, y0 = (blockIdx.x / tilesx) * kCT;
-    const int co0 = blockIdx.y * kCoB, n = blockIdx.z;
-    const int grp = threadIdx.x / 128, tid = threadIdx.x % 128;
-    const int tx = tid % 8, ty = tid / 8;  // pixels: rows 2ty, 2ty+1; columns 4tx .. 4tx+3
-    const int Cin = CA + CB;
-    const size_t plane = (size_t)H * Wd;
-    float acc[8][8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
-    constexpr int kPatch = kCiC * (kCT + 2) * (kCT + 2);
-    constexpr int kPerThread = (kPatch + 255) / 256;
-    for (int ci0 = 0; ci0 < Cin; ci0 += kCiC) {
-        // a thread's patch loads go out 8 at a time before they are stored (latency overlap)
-        constexpr int kG = 8;
-        for (int k0 = 0; k0 < kPerThread; k0 += kG) {
-            float pv[kG];
-#pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const int i = threadIdx.x + (k0 + k) * 256;
-                const int c = i / ((kCT + 2) * (kCT + 2)), r = (i / (kCT + 2)) % (kCT + 2), q = i % (kCT + 2);
-                const int ci = ci0 + c, gy = y0 + r - 1, gx = x0 + q - 1;
-                float v = 0.f;
-                if (i < kPatch && ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) {
-                    const size_t off = (size_t)gy * Wd + gx;
-                    v = ci < CA ? ld(XA, ((size_t)n * CA + ci) * plane + off)
-                                : ld(XB, ((size_t)n * CB + (ci - CA)) * plane + off);
-                }
-                pv[k] = v;
-            }
-#pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const int i = threadIdx.x + (k0 + k) * 256;
-                if (i < kPatch) (&patch[0][0][0])[i] = pv[k];
-            }
-        }
-        for (int i = threadIdx.x; i < kCiC * 9 * kCoB; i += 256) {
-            const int c = i / (9 * kCoB), tap = (i / kCoB) % 9, co = i % kCoB;
-            const int ci = ci0 + c, o = co0 + co;
-            wsm[c][tap][co] = (ci < Cin && o < Cout) ? __bfloat162float(W[((size_t)o * Cin + ci) * 9 + tap]) : 0.f;
-        }
-        __syncthreads();
-        for (int c = 0; c < kCiC; ++c) {
-            float win[4][6];  // input rows 2ty-1 .. 2ty+2, columns 4tx-1 .. 4tx+4 (tile coordinates)
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) win[r][q] = patch[c][2 * ty + r][4 * tx + q];
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int u = tap / 3, v = tap % 3;
-                const float4* w4 = reinterpret_cast<const float4*>(&wsm[c][tap][8 * grp]);
-                const float4 wa = w4[0], wb = w4[1];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float xv = win[u + q / 4][v + q % 4];
-                    acc[q][0] = fmaf(xv, wa.x, acc[q][0]);
-                    acc[q][1] = fmaf(xv, wa.y, acc[q][1]);
-                    acc[q][2] = fmaf(xv, wa.z, acc[q][2]);
-                    acc[q][3] = fmaf(xv, wa.w, acc[q][3]);
-                    acc[q][4] = fmaf(xv, wb.x, acc[q][4]);
-                    acc[q][5] = fmaf(xv, wb.y, acc[q][5]);
-                    acc[q][6] = fmaf(xv, wb.z, acc[q][6]);
-                    acc[q][7] = fmaf(xv, wb.w, acc[q][7]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int y = y0 + 2 * ty + q / 4, x = x0 + 4 * tx + q % 4;
-        if (y >= H || x >= Wd) continue;
-        const size_t off = (size_t)y * Wd + x;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int o = co0 + 8 * grp + j;
-            if (o >= Cout) break;
-            float v = acc[q][j] + (bias ? bias[o] : 0.f);
-            if (kBf16Out) {
-                if (relu) v = fmaxf(v, 0.f);
-                static_cast<bf16*>(YA)[((size_t)n * Cout + o) * plane + off] = __float2bfloat16_rn(v);
-            } else {
-                float* dst = o < CYA ? static_cast<float*>(YA) + ((size_t)n * CYA + o) * plane + off
-                                     : YB + ((size_t)n * (Cout - CYA) + (o - CYA)) * plane + off;
-                *dst = accumulate ? *dst + v : v;
-            }
-        }
-    }
-}
 
 // Forward 3x3 convolution on the tensor cores (warp-level BF16 MMA, FP32 accumulate):
 // an implicit GEMM with M = 128 output pixels (4 rows x 32 columns), N = 64 output
@@ -176,9 +65,24 @@ constexpr int kMPairs = 16 * (kMRows + 2) * ((kMCols + 4) / 2);  // bf16 pairs o
 constexpr int kMPairPT = (kMPairs + 255) / 256;
 constexpr int kMWPT = (9 * kMCo * 2 + 255) / 256;                // uint4 of weights per thread
 
+// Tin = bf16: the forward (bias, ReLU, bf16 output). Tin = float: the input gradient of a
+// forward layer (the output gradient, rounded to bf16 on the way into shared memory,
+// convolved with the flipped, transposed weights), FP32 output split along channels
+// into YA (the first CYA) and YB, stored or added.
+__device__ __forceinline__ uint32_t pair_bits(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t pair_bits(const float* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+__device__ __forceinline__ unsigned short one_bits(const bf16* p) { return __bfloat16_as_ushort(*p); }
+__device__ __forceinline__ unsigned short one_bits(const float* p) { return __bfloat16_as_ushort(__float2bfloat16_rn(*p)); }
+
+template <typename Tin, bool kBf16Out>
 __global__ void __launch_bounds__(256)
-k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int CB, const bf16* __restrict__ Wm,
-            int Coutp, const float* __restrict__ bias, int relu, bf16* __restrict__ Y, int H, int Wd, int Cout) {
+k_conv3_mma(const Tin* __restrict__ XA, int CA, const Tin* __restrict__ XB, int CB, const bf16* __restrict__ Wm,
+            int Coutp, const float* __restrict__ bias, int relu, void* YA, int CYA, float* YB, int accumulate, int H,
+            int Wd, int Cout) {
     extern __shared__ __align__(16) uint8_t msm[];
     bf16* patch_s = reinterpret_cast<bf16*>(msm);                  // [2][rows + 2][cols + 2][kMPad]
     bf16* w_s = patch_s + 2 * kMTile;                              // [2][9][kMCo][kMPad]
@@ -195,8 +99,8 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
     auto pix = [&](int ci, int gy, int gx) -> unsigned short {
         if (ci >= Cin || gy < 0 || gy >= H || gx < 0 || gx >= Wd) return 0;
         const size_t off = (size_t)gy * Wd + gx;
-        const bf16 v = ci < CA ? XA[((size_t)n * CA + ci) * plane + off] : XB[((size_t)n * CB + (ci - CA)) * plane + off];
-        return __bfloat16_as_ushort(v);
+        return one_bits(ci < CA ? XA + ((size_t)n * CA + ci) * plane + off
+                                : XB + ((size_t)n * CB + (ci - CA)) * plane + off);
     };
     // global -> registers: the tile as bf16 pairs (columns x0-2+2p, x0-1+2p), and the weights
     auto load = [&](int cb) {
@@ -209,9 +113,9 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
                 const int ci = cb * 16 + c, gy = y0 + r - 1, gx = x0 - 2 + 2 * p;
                 if (ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx + 1 < Wd) {
                     const size_t off = (size_t)gy * Wd + gx;
-                    const bf16* src = ci < CA ? XA + ((size_t)n * CA + ci) * plane + off
-                                              : XB + ((size_t)n * CB + (ci - CA)) * plane + off;
-                    v = *reinterpret_cast<const uint32_t*>(src);
+                    const Tin* src = ci < CA ? XA + ((size_t)n * CA + ci) * plane + off
+                                             : XB + ((size_t)n * CB + (ci - CA)) * plane + off;
+                    v = pair_bits(src);
                 } else {
                     v = (uint32_t)pix(ci, gy, gx) | ((uint32_t)pix(ci, gy, gx + 1) << 16);
                 }
@@ -305,14 +209,26 @@ k_conv3_mma(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, in
                 const int x = x0 + 16 * mi + g + (e >> 1) * 8;
                 const int co = co0 + wn * 32 + 8 * nj + cpair + (e & 1);
                 if (x >= Wd || co >= Cout) continue;
-                float v = acc[mi][nj][e] + bias[co];
-                if (relu) v = fmaxf(v, 0.f);
-                Y[((size_t)n * Cout + co) * plane + (size_t)y * Wd + x] = __float2bfloat16_rn(v);
+                const size_t off = (size_t)y * Wd + x;
+                if (kBf16Out) {
+                    float v = acc[mi][nj][e] + (bias ? bias[co] : 0.f);
+                    if (relu) v = fmaxf(v, 0.f);
+                    static_cast<bf16*>(YA)[((size_t)n * Cout + co) * plane + off] = __float2bfloat16_rn(v);
+                } else {
+                    const float v = acc[mi][nj][e];
+                    float* dst = co < CYA ? static_cast<float*>(YA) + ((size_t)n * CYA + co) * plane + off
+                                          : YB + ((size_t)n * (Cout - CYA) + (co - CYA)) * plane + off;
+                    *dst = accumulate ? *dst + v : v;
+                }
             }
 }
 
-// weights of a 3x3 layer for k_conv3_mma: Wm[cb][tap][co < Coutp][16] (zero past Cin / Cout)
-__global__ void k_prep_wm(const float* __restrict__ W, int Cout, int Cin, int Coutp, bf16* __restrict__ Wm) {
+// weights of a 3x3 layer for k_conv3_mma: Wm[cb][tap][co < Coutp][16] (zero past Cin / Cout);
+// transposed: the layer seen from its output gradient (co <-> ci, taps mirrored), so the
+// same kernel computes the input gradient
+template <bool kT>
+__global__ void k_prep_wm(const float* __restrict__ W, int CoutF, int CinF, int Coutp, bf16* __restrict__ Wm) {
+    const int Cout = kT ? CinF : CoutF, Cin = kT ? CoutF : CinF;
     const int ncb = (Cin + 15) / 16;
     const size_t count = (size_t)ncb * 9 * Coutp * 16;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -320,7 +236,10 @@ __global__ void k_prep_wm(const float* __restrict__ W, int Cout, int Cin, int Co
         const size_t r = i / 16;
         const int co = (int)(r % Coutp), tap = (int)((r / Coutp) % 9), cb = (int)(r / ((size_t)Coutp * 9));
         const int ci = cb * 16 + j;
-        Wm[i] = __float2bfloat16_rn((co < Cout && ci < Cin) ? W[((size_t)co * Cin + ci) * 9 + tap] : 0.f);
+        float v = 0.f;
+        if (co < Cout && ci < Cin)
+            v = kT ? W[((size_t)ci * CinF + co) * 9 + (8 - tap)] : W[((size_t)co * Cin + ci) * 9 + tap];
+        Wm[i] = __float2bfloat16_rn(v);
     }
 }
 
@@ -607,19 +526,6 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
     }
 }
 
-// BF16 weights of a 3x3 layer, and the flipped, transposed copy of the input gradient
-__global__ void k_prep_w(const float* __restrict__ W, int Cout, int Cin, bf16* __restrict__ Wb, bf16* __restrict__ Wt) {
-    const size_t count = (size_t)Cout * Cin * 9;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const int tap = (int)(i % 9);
-        const size_t oc = i / 9;
-        const int ci = (int)(oc % Cin), co = (int)(oc / Cin);
-        const bf16 v = __float2bfloat16_rn(W[i]);
-        Wb[i] = v;
-        Wt[((size_t)ci * Cout + co) * 9 + (8 - tap)] = v;
-    }
-}
-
 // x = clip(phi, -B, B) / B as FP32 (residual path) and BF16 (first convolution)
 __global__ void k_band(const float* __restrict__ phi, size_t count, float B, float* __restrict__ x,
                        bf16* __restrict__ xb) {
@@ -650,10 +556,9 @@ struct devel_dsn {
     struct Conv {
         int cin, cout, k;
         size_t w_off, b_off;  // into the flat parameter vector
-        __nv_bfloat16* Wb = nullptr;
-        __nv_bfloat16* Wt = nullptr;
-        __nv_bfloat16* Wm = nullptr;  // tensor-core layout of the forward weights
-        int coutp = 0;
+        __nv_bfloat16* Wm = nullptr;   // tensor-core layout of the forward weights
+        __nv_bfloat16* Wtm = nullptr;  // ... of the input-gradient (transposed, mirrored) weights
+        int coutp = 0, cinp = 0;
     };
     std::vector<Conv> convs;
     size_t nparams = 0;
@@ -685,9 +590,8 @@ enum ActId { A0, S0, P1, A1, S1, P2, A2, S2, P3, A3, S3, U2, D2A, D2, U1, D1A, D
 void free_dsn(devel_dsn* d) {
     if (!d) return;
     for (auto& cv : d->convs) {
-        cudaFree(cv.Wb);
-        cudaFree(cv.Wt);
         cudaFree(cv.Wm);
+        cudaFree(cv.Wtm);
     }
     for (auto& a : d->acts) {
         cudaFree(a.a);
@@ -706,11 +610,14 @@ int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     dim3 grid(mtiles, cv.coutp / kMCo, nb);
     static bool attr = false;
     if (!attr) {
-        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem));
+        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<__nv_bfloat16, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem));
+        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kMSmem));
         attr = true;
     }
-    k_conv3_mma<<<grid, 256, kMSmem, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y, side, side,
-                                          cv.cout);
+    k_conv3_mma<__nv_bfloat16, true><<<grid, 256, kMSmem, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y,
+                                                               cv.cout, nullptr, 0, side, side, cv.cout);
     DEVEL_LAUNCH_CHECK("k_conv3_mma");
     return DEVEL_OK;
 }
@@ -731,11 +638,11 @@ int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     k_wgrad_reduce<<<(unsigned)((wc + 255) / 256), 256, 0, s>>>(d->part, tiles, wc, d->G + cv.w_off);
     k_wgrad_reduce<<<(unsigned)((cv.cout + 255) / 256), 256, 0, s>>>(bpart, tiles, (size_t)cv.cout,
                                                                      d->G + cv.b_off);
-    if (dXA) {
-        const int ctiles = ((side + kCT - 1) / kCT) * ((side + kCT - 1) / kCT);
-        dim3 gd(ctiles, (cv.cin + kCoB - 1) / kCoB, nb);
-        k_conv3<float, false><<<gd, 256, 0, s>>>(dY, cv.cout, (const float*)nullptr, 0, cv.Wt, nullptr, 0, dXA, CA, dXB,
-                                                accumulate, side, side, cv.cin);
+    if (dXA) {  // the forward kernel sets the shared-memory attribute of both instances first
+        const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
+        dim3 gd(mtiles, cv.cinp / kMCo, nb);
+        k_conv3_mma<float, false><<<gd, 256, kMSmem, s>>>(dY, cv.cout, (const float*)nullptr, 0, cv.Wtm, cv.cinp,
+                                                          nullptr, 0, dXA, CA, dXB, accumulate, side, side, cv.cin);
     }
     DEVEL_LAUNCH_CHECK("dsn conv backward");
     return DEVEL_OK;
@@ -744,12 +651,12 @@ int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
 int prep_weights(devel_dsn* d, cudaStream_t s) {
     for (auto& cv : d->convs) {
         if (cv.k != 3) continue;
-        const size_t wc = (size_t)cv.cout * cv.cin * 9;
-        k_prep_w<<<grid1(wc), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.Wb, cv.Wt);
         const size_t wm = (size_t)((cv.cin + 15) / 16) * 9 * cv.coutp * 16;
-        k_prep_wm<<<grid1(wm), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.coutp, cv.Wm);
+        k_prep_wm<false><<<grid1(wm), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.coutp, cv.Wm);
+        const size_t wt = (size_t)((cv.cout + 15) / 16) * 9 * cv.cinp * 16;
+        k_prep_wm<true><<<grid1(wt), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.cinp, cv.Wtm);
     }
-    DEVEL_LAUNCH_CHECK("k_prep_w");
+    DEVEL_LAUNCH_CHECK("k_prep_wm");
     return DEVEL_OK;
 }
 
@@ -873,10 +780,10 @@ int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
         off += l[1];
         if (l[2] == 3 && e == cudaSuccess) {
             cv.coutp = (l[1] + kMCo - 1) / kMCo * kMCo;
-            e = cudaMalloc(&cv.Wb, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
-            if (e == cudaSuccess) e = cudaMalloc(&cv.Wt, sizeof(__nv_bfloat16) * l[0] * l[1] * 9);
+            e = cudaMalloc(&cv.Wm, sizeof(__nv_bfloat16) * ((l[0] + 15) / 16) * 9 * cv.coutp * 16);
+            cv.cinp = (l[0] + kMCo - 1) / kMCo * kMCo;
             if (e == cudaSuccess)
-                e = cudaMalloc(&cv.Wm, sizeof(__nv_bfloat16) * ((l[0] + 15) / 16) * 9 * cv.coutp * 16);
+                e = cudaMalloc(&cv.Wtm, sizeof(__nv_bfloat16) * ((l[1] + 15) / 16) * 9 * cv.cinp * 16);
         }
         d->convs.push_back(cv);
     }
