@@ -200,5 +200,36 @@ class Adam:
             p -= self.lr * (m / c1) / (np.sqrt(v / c2) + self.eps)
 
 
+def phi_downsample(phi, f: int):
+    """Level set on the coarse grid of a DSN that runs at 1/f of the clip's side (Sec.
+    III-B/C: the network predicts phi_0, DSO refines it on the clip's own grid).
+    Reading: each coarse pixel takes the mean of its f x f block, and distances are
+    re-expressed in coarse pixels (divided by f). phi: [..., n, n], n a multiple of f."""
+    a = np.asarray(phi, dtype=np.float64)
+    n = a.shape[-1]
+    m = n // f
+    out = np.zeros(a.shape[:-2] + (m, m))
+    for I in range(m):
+        for J in range(m):
+            out[..., I, J] = a[..., f * I:f * I + f, f * J:f * J + f].mean(axis=(-2, -1)) / f
+    return out
+
+
+def phi_upsample(c, f: int):
+    """The coarse level set back on the fine grid: bilinear interpolation with the
+    pixel centres aligned (fine centre p sits at coarse coordinate (p + 1/2) / f - 1/2),
+    coarse indices clamped to the grid, distances back in fine pixels (times f)."""
+    c = np.asarray(c, dtype=np.float64)
+    m = c.shape[-1]
+    n = m * f
+    pos = (np.arange(n) + 0.5) / f - 0.5
+    i0 = np.floor(pos).astype(np.int64)
+    t = pos - i0
+    ia, ib = np.clip(i0, 0, m - 1), np.clip(i0 + 1, 0, m - 1)
+    rows = (1.0 - t)[:, None] * c[..., ia, :] + t[:, None] * c[..., ib, :]            # [..., n, m]
+    out = (1.0 - t)[None, :] * rows[..., :, ia] + t[None, :] * rows[..., :, ib]       # [..., n, n]
+    return f * out
+
+
 def band(phi, B: float = BAND):
     return np.clip(np.asarray(phi, dtype=np.float64), -B, B) / B

@@ -115,3 +115,64 @@ def test_modulation_loss_gradient_and_limits():
         assert g[idx] == pytest.approx(fd, rel=1e-6, abs=1e-10)
     assert dsn.ahf_mean(y, modulation.ahf(y, 0.03), 0.03)[0] == 0.0
     assert L * y.size == pytest.approx(modulation.ahf_loss(y, m, 0.03)[0], rel=1e-12)
+
+
+# Resampling between a clip's grid and the DSN's coarser grid (the learned start of a
+# clip larger than the network's side).
+
+def _affine(a, b, c, rows, cols, f=1):
+    """a x + b y + c at pixel indices (x = column, y = row), shape [rows, cols]."""
+    y, x = np.mgrid[0:rows, 0:cols].astype(np.float64)
+    return a * x + b * y + c
+
+
+@pytest.mark.parametrize("f", [1, 2, 3, 4])
+def test_phi_downsample_of_an_affine_field_is_its_centre_value_in_coarse_pixels(f):
+    m = 5
+    fine = _affine(0.7, -1.9, 3.25, m * f, m * f)
+    I, J = np.mgrid[0:m, 0:m].astype(np.float64)
+    want = (0.7 * (f * J + (f - 1) / 2) - 1.9 * (f * I + (f - 1) / 2) + 3.25) / f
+    assert np.allclose(dsn.phi_downsample(fine, f), want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("f", [1, 2, 3, 4])
+def test_phi_upsample_matches_scipy_linear_zoom(f):
+    from scipy.ndimage import zoom
+    c = np.random.default_rng(f).standard_normal((2, 7, 7))
+    got = dsn.phi_upsample(c, f)
+    for b in range(2):
+        ref = f * zoom(c[b], f, order=1, mode="nearest", grid_mode=True)
+        assert np.allclose(got[b], ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_phi_upsample_reproduces_an_affine_field_between_the_outer_centres(f):
+    m = 6
+    c = _affine(0.3, 1.7, -2.0, m, m)
+    fine = dsn.phi_upsample(c, f)
+    pos = (np.arange(m * f) + 0.5) / f - 0.5
+    inside = (pos >= 0) & (pos <= m - 1)
+    Y, X = np.meshgrid(pos, pos, indexing="ij")
+    want = f * (0.3 * X + 1.7 * Y - 2.0)
+    sel = inside[:, None] & inside[None, :]
+    assert np.allclose(fine[sel], want[sel], rtol=0, atol=1e-12)
+    # beyond the outer centres the field is held at its value there (edge clamp)
+    top, right = fine[pos < 0], fine[:, pos > m - 1]
+    assert len(top) == f // 2 and np.allclose(top, top[0], rtol=0, atol=1e-12)
+    assert np.allclose(top[0][inside], f * (0.3 * pos[inside] - 2.0), rtol=0, atol=1e-12)
+    assert right.shape[1] == f // 2 and np.allclose(right, right[:, :1], rtol=0, atol=1e-12)
+    assert np.allclose(right[inside, 0], f * (0.3 * (m - 1) + 1.7 * pos[inside] - 2.0), rtol=0, atol=1e-12)
+
+
+def test_phi_resampling_round_trips_and_keeps_the_zero_level_of_a_half_plane():
+    f, m = 4, 8
+    k = np.full((m, m), -3.5)
+    assert np.allclose(dsn.phi_downsample(dsn.phi_upsample(k, f), f), k, rtol=0, atol=1e-12)
+    # signed distance to the vertical line x = 13.5 - 1/2 (between fine columns 12 and 13):
+    # a distance field in fine pixels becomes one in coarse pixels, with the same zero set
+    fine = np.arange(m * f)[None, :].repeat(m * f, axis=0) - 12.5
+    coarse = dsn.phi_downsample(fine, f)
+    assert np.allclose(coarse, (np.arange(m)[None, :] * f + 1.5 - 12.5) / f * np.ones((m, 1)), atol=1e-12)
+    back = dsn.phi_upsample(coarse, f)
+    inner = slice(f, m * f - f)
+    assert np.allclose(back[:, inner], fine[:, inner], rtol=0, atol=1e-12)

@@ -141,3 +141,32 @@ def test_conv_backward_with_the_taps_mirrored_is_caught(monkeypatch):
         return dx, dW, db
     monkeypatch.setattr(dsn, "conv_backward", mirrored)
     _fails(td.test_conv_backward_matches_finite_differences)
+
+
+def test_resampling_without_centre_alignment_or_unit_change_is_caught(monkeypatch):
+    from oracle import dsn
+    import test_oracle_dsn as td
+    orig_up, orig_down = dsn.phi_upsample, dsn.phi_downsample
+
+    def up_corner_aligned(c, f):                 # fine pixel p read at coarse p / f
+        c = np.asarray(c, dtype=np.float64)
+        m = c.shape[-1]
+        pos = np.arange(m * f) / f
+        i0 = np.floor(pos).astype(np.int64)
+        t = pos - i0
+        ia, ib = np.clip(i0, 0, m - 1), np.clip(i0 + 1, 0, m - 1)
+        rows = (1.0 - t)[:, None] * c[..., ia, :] + t[:, None] * c[..., ib, :]
+        return f * ((1.0 - t)[None, :] * rows[..., :, ia] + t[None, :] * rows[..., :, ib])
+    monkeypatch.setattr(dsn, "phi_upsample", up_corner_aligned)
+    _fails(td.test_phi_upsample_matches_scipy_linear_zoom, 2)
+    _fails(td.test_phi_upsample_reproduces_an_affine_field_between_the_outer_centres, 4)
+    monkeypatch.setattr(dsn, "phi_upsample", lambda c, f: orig_up(c, f) / f)     # units not converted
+    _fails(td.test_phi_upsample_matches_scipy_linear_zoom, 2)
+    monkeypatch.setattr(dsn, "phi_upsample", lambda c, f: orig_up(np.swapaxes(c, -1, -2), f))  # transposed
+    _fails(td.test_phi_upsample_reproduces_an_affine_field_between_the_outer_centres, 2)
+    monkeypatch.setattr(dsn, "phi_upsample", orig_up)
+    monkeypatch.setattr(dsn, "phi_downsample", lambda a, f: orig_down(a, f) * f)  # mean kept in fine pixels
+    _fails(td.test_phi_downsample_of_an_affine_field_is_its_centre_value_in_coarse_pixels, 4)
+    monkeypatch.setattr(dsn, "phi_downsample",                                     # block's first pixel only
+                        lambda a, f: np.asarray(a, dtype=np.float64)[..., ::f, ::f] / f)
+    _fails(td.test_phi_downsample_of_an_affine_field_is_its_centre_value_in_coarse_pixels, 4)
