@@ -48,6 +48,14 @@ WORKLOADS = {
                        seed_test=20000, plain_iters=100, refine_iters=15, width=32, dsn_batch=16, epochs=6, lr=1e-3,
                        # modulation branch: labels for the first 256 training clips from 8 shifts each
                        mod_train=256, mod_cands=8, mod_epochs=8, ahf_eps=0.03),
+    # learned initialisation at the full clip size: the DSN runs on the 512^2 grid (f = 4),
+    # its input the 2048^2 target's TSDF block-averaged down, its phi_0 upsampled to 2048^2
+    # (devel_phi_downsample / devel_phi_upsample); trained on 2000 Manhattan clips labelled
+    # with this solver's converged phi, tested on 256 held-out ones: DSN phi_0 + 15
+    # iterations against 100 plain iterations (compensated BF16, and the plain FP32 solver)
+    "learned2048": dict(learned=True, n=2048, f=4, K=24, k=35, beta=7.5, train=2000, test=256, seed_train=10000,
+                        seed_test=20000, plain_iters=100, refine_iters=15, width=32, dsn_batch=16, epochs=4,
+                        lr=1e-3, handles=32, group=250, band=16.0),
 }
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -246,8 +254,9 @@ def run_reference(args, wl):
         return
     if "batch" in wl:  # the oracle's clips/s on the full-size clip stands for every side
         wl = WORKLOADS["manhattan2048"]
-    if "learned" in wl:  # the oracle's plain solve of one 256^2 clip
-        wl = dict(WORKLOADS["rect256"], iters=wl["plain_iters"], beta=wl["beta"])
+    if "learned" in wl:  # the oracle's plain solve of one clip of the workload's side
+        base = "manhattan2048" if wl["n"] == 2048 else "rect256"
+        wl = dict(WORKLOADS[base], iters=wl["plain_iters"], beta=wl["beta"])
     t0 = time.perf_counter()
     vals = []
     sample = ""
@@ -935,6 +944,169 @@ def run_learned(args, wl):
     print(json.dumps(out), flush=True)
 
 
+def run_learned_full_size(args, wl):
+    """Learned initialisation of full-size clips (rank 0 only: one GPU). The network
+    works on the (n/f)^2 grid: its input is the target's TSDF block-averaged down, its
+    labels the converged phi likewise, and its phi_0 is upsampled back to n^2 before
+    the refining iterations. The learned arm's time covers the whole learned start
+    (TSDF of the target, downsampling, DSN inference, upsampling) and the iterations."""
+    import multiprocessing as mp
+    # targets are drawn by worker processes started with spawn (independent of the
+    # CUDA context of this process)
+    pool = mp.get_context("spawn").Pool(max(1, min(15, (os.cpu_count() or 2) - 1)))
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+    if int(os.environ.get("RANK", "0")) != 0:
+        pool.terminate()
+        return
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, f, K, k, beta, B = wl["n"], wl["f"], wl["K"], wl["k"], wl["beta"], wl["band"]
+    m, N = n // f, n * n
+    Nc = m * m
+    o = synth.optics(n, K, k)
+    G = wl["handles"]
+    handles = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3) for _ in range(G)]
+    handles32 = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_FP32) for _ in range(G)]
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    d2 = torch.empty(N, dtype=torch.int32, device=dev)
+    shifts = torch.arange(7, -1, -1, dtype=torch.uint8, device=dev)
+
+    def targets(seed0, count):
+        """[count, N] uint8 on the device (unpacked from the workers' packed bits)."""
+        t0 = time.perf_counter()
+        bits = pool.map(synth.manhattan_clip_bits, range(seed0, seed0 + count), chunksize=4)
+        packed = torch.from_numpy(np.stack(bits)).to(dev)
+        out = ((packed[:, :, None] >> shifts) & 1).reshape(count, N).contiguous()
+        return out, time.perf_counter() - t0
+
+    W = (wl["plain_iters"] + 2) // 2 * 2
+
+    def solve(tg, iters, hs, phi, phi_given=False):
+        """All clips of tg in one devel_ilt_solve (clip i on handle i % G); phi [count, N]
+        in/out. Returns the final L2 + PVB of every clip."""
+        cnt = tg.shape[0]
+        l2 = torch.zeros(cnt, W, dtype=torch.int64, device=dev)
+        pvb = torch.zeros(cnt, W, dtype=torch.int64, device=dev)
+        p = dv.ilt_params(dv.resist_params(beta=beta), iters=iters, use_graph=False)
+        clips = [dv.Clip(hs[i % G], tg[i], phi[i], phi_given=phi_given,
+                         l2_hist=l2[i, :iters + 1], pvb_hist=pvb[i, :iters + 1]) for i in range(cnt)]
+        dv.devel_ilt_solve(p, clips, st, stream)
+        return l2[:, iters] + pvb[:, iters]
+
+    def tsdf_coarse(tg, out, tmp):
+        """The targets' TSDFs, block-averaged down to the network's grid."""
+        for b0 in range(0, tg.shape[0], tmp.shape[0]):
+            nb = min(tmp.shape[0], tg.shape[0] - b0)
+            for i in range(nb):
+                dv.devel_reinit_sdf(n, tg[b0 + i], tmp[i], d2)
+            dv.devel_phi_downsample(n, f, tmp[:nb], out[b0:b0 + nb])
+
+    # training labels: 100 plain iterations per clip, in groups (phi of a group on the
+    # device at a time), then the label and input block-averaged down
+    t0 = time.perf_counter()
+    tr, t_gen = targets(wl["seed_train"], wl["train"])
+    x_tr = torch.empty(wl["train"], Nc, dtype=torch.float32, device=dev)
+    y_tr = torch.empty(wl["train"], Nc, dtype=torch.float32, device=dev)
+    grp = wl["group"]
+    phi_g = torch.empty(grp, N, dtype=torch.float32, device=dev)
+    for c0 in range(0, wl["train"], grp):
+        cnt = min(grp, wl["train"] - c0)
+        solve(tr[c0:c0 + cnt], wl["plain_iters"], handles, phi_g[:cnt])
+        dv.devel_phi_downsample(n, f, phi_g[:cnt], y_tr[c0:c0 + cnt])
+    tsdf_coarse(tr, x_tr, phi_g)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    del tr
+
+    Bt = wl["dsn_batch"]
+    net = dv.Dsn(m, Bt, wl["width"], seed=1)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(0)
+    losses = []
+    t0 = time.perf_counter()
+    for ep in range(wl["epochs"]):
+        order = torch.from_numpy(rng.permutation(wl["train"])).to(dev)
+        lr = wl["lr"] * (0.5 ** (ep // 2))
+        for b0 in range(0, wl["train"] - Bt + 1, Bt):
+            idx = order[b0:b0 + Bt]
+            net.train_step(Bt, x_tr[idx].contiguous(), y_tr[idx].contiguous(), lr, loss, B, stream)
+        torch.cuda.synchronize()
+        losses.append(float(loss.item()))
+    t_train = time.perf_counter() - t0
+    steps = wl["epochs"] * (wl["train"] // Bt)
+    del x_tr, y_tr, phi_g
+
+    T = wl["test"]
+    te, _ = targets(wl["seed_test"], T)
+    pool.close()
+    phi = torch.empty(T, N, dtype=torch.float32, device=dev)
+    tmp = torch.empty(Bt, N, dtype=torch.float32, device=dev)
+    xc = torch.empty(Bt, Nc, dtype=torch.float32, device=dev)
+    pc = torch.empty(Bt, Nc, dtype=torch.float32, device=dev)
+
+    def learned_start():
+        for b0 in range(0, T, Bt):
+            nb = min(Bt, T - b0)
+            tsdf_coarse(te[b0:b0 + nb], xc, tmp)
+            net.forward(nb, xc[:nb], pc[:nb], B, stream)
+            dv.devel_phi_upsample(n, f, pc[:nb], phi[b0:b0 + nb])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # warm-up: every kernel of every arm once, on a few clips
+    wc = min(G, T)
+    solve(te[:wc], 2, handles, phi[:wc])
+    solve(te[:wc], 2, handles32, phi[:wc])
+    learned_start()
+    solve(te[:wc], 2, handles, phi[:wc], phi_given=True)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    q_plain, t_plain = timed(lambda: solve(te, wl["plain_iters"], handles, phi))
+    q_fp32, t_fp32 = timed(lambda: solve(te, wl["plain_iters"], handles32, phi))
+
+    def learned():
+        learned_start()
+        return solve(te, wl["refine_iters"], handles, phi, phi_given=True)
+    q_learned, t_learned = timed(learned)
+    clocks = clk.stop()
+    _, t_start = timed(learned_start)
+    q_short, _ = timed(lambda: solve(te, wl["refine_iters"], handles, phi))
+    qp, ql, qs, qf = (q.double().mean().item() for q in (q_plain, q_learned, q_short, q_fp32))
+    out = {"metric": f"ILT clips/sec to converged L2+PVB at {n}^2 (DSN phi_0 on {m}^2 + {wl['refine_iters']} "
+                     f"iterations vs {wl['plain_iters']} plain)",
+           "value": T / t_learned, "unit": "clips/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "ms_per_step": t_learned * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3", "data": "synthetic",
+           "config": {"workload": args.workload, **{kk: wl[kk] for kk in ("n", "f", "K", "k", "beta", "train", "test",
+                                                                          "plain_iters", "refine_iters", "width",
+                                                                          "dsn_batch", "epochs", "lr", "band")},
+                      "timing": "host clock around the whole test set, targets resident (each arm's set is "
+                                f"{T} x {n}^2 clips, far larger than L2)"},
+           "clocks": clocks,
+           "plain": {"value": T / t_plain, "mean_l2_pvb": qp, "precision": "bf16x3"},
+           "plain_fp32": {"value": T / t_fp32, "mean_l2_pvb": qf,
+                          "speedup_learned_bf16_vs_plain_fp32": t_fp32 / t_learned,
+                          "learned_ratio_to_fp32": ql / qf,
+                          "converged_within_1pct_of_fp32": bool(ql <= 1.01 * qf)},
+           "learned": {"mean_l2_pvb": ql, "ratio_to_plain": ql / qp, "converged_within_1pct": bool(ql <= 1.01 * qp),
+                       "start_seconds": t_start},
+           "plain_15_iterations": {"mean_l2_pvb": qs, "ratio_to_plain": qs / qp},
+           "speedup_vs_plain": t_plain / t_learned,
+           "training": {"seconds": t_train, "steps": steps, "samples_per_s": steps * Bt / t_train,
+                        "epoch_losses": losses, "label_seconds": t_label, "target_draw_seconds": t_gen}}
+    print(json.dumps(out), flush=True)
+
+
 def run_calls_once(args, wl):
     """Each ABI call of the hot path once at the workload's size, through the public
     API (TSDF, forward, resist/loss, adjoint, level-set step), for kernel captures with
@@ -1017,6 +1189,8 @@ def main():
         run_batched(args, wl)
     elif "labels" in wl:
         run_modgt(args, wl)
+    elif "learned" in wl and "f" in wl:
+        run_learned_full_size(args, wl)
     elif "learned" in wl:
         run_learned(args, wl)
     else:

@@ -410,6 +410,24 @@ int devel_dsn_train_step_ahf(devel_dsn* dsn, int nb, const float* tsdf, const fl
                              float lr, double* loss_out, cudaStream_t stream);
 
 /*
+ * Level sets between a fine n x n grid and the coarse (n/f) x (n/f) grid a DSN runs
+ * on, for clips larger than the network's side (Sec. III-B/C: the network predicts
+ * phi_0, DSO refines it at the clip's own resolution). Distances are kept in the
+ * pixels of each grid, so both maps also scale values by f.
+ *   downsample: coarse[b][I][J] = (1 / f^3) sum_{u,v < f} fine[b][f I + u][f J + v]
+ *               (the mean over the f x f block, in coarse pixels; the block mean of
+ *               an affine function is its value at the block centre).
+ *   upsample:   fine[b][p][q] = f * bilinear(coarse[b], (p + 1/2) / f - 1/2,
+ *               (q + 1/2) / f - 1/2), pixel centres aligned, coarse indices clamped
+ *               to the grid (constant beyond the outer coarse centres).
+ * fine: device float [nb][n][n]; coarse: device float [nb][n/f][n/f]; both 16-byte
+ * aligned, not overlapping. n >= 1, f >= 1, n % f == 0, nb >= 0 (0: nothing to do);
+ * otherwise DEVEL_EINVAL. Asynchronous on `stream`; FP32, sums in a fixed order.
+ */
+int devel_phi_downsample(int n, int f, int nb, const float* fine, float* coarse, cudaStream_t stream);
+int devel_phi_upsample(int n, int f, int nb, const float* coarse, float* fine, cudaStream_t stream);
+
+/*
  * Run `params->iters` DSO iterations on each clip (host array of nclips):
  * image, resist loss, adjoint velocity, level-set step, periodic TSDF
  * re-initialisation, all on `stream`, nothing copied to the host.

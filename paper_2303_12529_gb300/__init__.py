@@ -103,6 +103,8 @@ _sig("devel_dsn_train_step", [_P, _I, _P, _P, _F, _F, _P, _P])
 _sig("devel_dsn_forward_ahf", [_P, _I, _P, _F, _F, _P, _P])
 _sig("devel_dsn_train_step_ahf", [_P, _I, _P, _P, _F, _F, _F, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
+_sig("devel_phi_downsample", [_I, _I, _I, _P, _P, _P])
+_sig("devel_phi_upsample", [_I, _I, _I, _P, _P, _P])
 
 _sig("devel_reinit_sdf_static", [_I, _P, _P, _F, _F, _P])
 _sig("devel_profile_start", [_I])
@@ -126,7 +128,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_modulation_candidates", "devel_ahf_loss", "devel_shot_count", "devel_dsn_create", "devel_dsn_destroy",
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
             "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
-            "devel_dsn_train_step_ahf")
+            "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -422,6 +424,26 @@ def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float
     N = n * n
     _check(_lib.devel_reinit_sdf_static(n, _ptr(mask, torch.uint8, N, "mask"),
                                         _ptr(phi, torch.float32, N, "phi"), d_lo, d_hi, _stream(stream)))
+
+
+def devel_phi_downsample(n: int, f: int, fine, coarse, stream=None):
+    """fine: float [nb, n*n] (or [n*n]) -> coarse: float [nb, (n/f)^2], the f x f block
+    means divided by f (distances in coarse pixels)."""
+    import torch
+    N, m = n * n, n // f if f > 0 else 0
+    nb = fine.numel() // N if N else 0
+    _check(_lib.devel_phi_downsample(n, f, nb, _ptr(fine, torch.float32, nb * N, "fine"),
+                                     _ptr(coarse, torch.float32, nb * m * m, "coarse"), _stream(stream)))
+
+
+def devel_phi_upsample(n: int, f: int, coarse, fine, stream=None):
+    """coarse: float [nb, (n/f)^2] -> fine: float [nb, n*n], f times the bilinear
+    interpolation at the fine pixel centres."""
+    import torch
+    N, m = n * n, n // f if f > 0 else 0
+    nb = fine.numel() // N if N else 0
+    _check(_lib.devel_phi_upsample(n, f, nb, _ptr(coarse, torch.float32, nb * m * m, "coarse"),
+                                   _ptr(fine, torch.float32, nb * N, "fine"), _stream(stream)))
 
 
 def ilt_params(resist: devel_resist_params = None, dt=0.5, lam=0.1, d_lo=-100.0, d_hi=900.0, iters=20,

@@ -541,6 +541,45 @@ __global__ void k_scale(const float* __restrict__ y, size_t count, float s, floa
         out[i] = s * y[i];
 }
 
+// coarse[b][I][J] = (sum of the f x f block of fine) * inv, inv = 1 / f^3; the block's
+// rows in order, each left to right
+__global__ void k_phi_down(const float* __restrict__ fine, int n, int f, size_t count, float inv,
+                           float* __restrict__ coarse) {
+    const int m = n / f;
+    const size_t mm = (size_t)m * m, nn = (size_t)n * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / mm;
+        const int r = (int)(i - b * mm), I = r / m, J = r - (r / m) * m;
+        const float* src = fine + b * nn + (size_t)I * f * n + (size_t)J * f;
+        float s = 0.f;
+        for (int u = 0; u < f; ++u)
+            for (int v = 0; v < f; ++v) s += src[(size_t)u * n + v];
+        coarse[i] = s * inv;
+    }
+}
+
+// fine[b][p][q] = f * bilinear interpolation of coarse[b] at ((p + 1/2) / f - 1/2,
+// (q + 1/2) / f - 1/2), coarse indices clamped to [0, m - 1]
+__global__ void k_phi_up(const float* __restrict__ coarse, int n, int f, size_t count, float* __restrict__ fine) {
+    const int m = n / f;
+    const size_t mm = (size_t)m * m, nn = (size_t)n * n;
+    const float two_f = 2.f * (float)f, ff = (float)f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / nn;
+        const int r = (int)(i - b * nn), p = r / n, q = r - (r / n) * n;
+        const float yc = (float)(2 * p + 1 - f) / two_f, xc = (float)(2 * q + 1 - f) / two_f;
+        const float fy = floorf(yc), fx = floorf(xc);
+        const float ty = yc - fy, tx = xc - fx;
+        const int i0 = (int)fy, j0 = (int)fx;
+        const int ia = min(max(i0, 0), m - 1), ib = min(max(i0 + 1, 0), m - 1);
+        const int ja = min(max(j0, 0), m - 1), jb = min(max(j0 + 1, 0), m - 1);
+        const float* c = coarse + b * mm;
+        const float top = (1.f - tx) * c[(size_t)ia * m + ja] + tx * c[(size_t)ia * m + jb];
+        const float bot = (1.f - tx) * c[(size_t)ib * m + ja] + tx * c[(size_t)ib * m + jb];
+        fine[i] = ff * ((1.f - ty) * top + ty * bot);
+    }
+}
+
 bool bad_ptr(const void* p) { return !p || (reinterpret_cast<uintptr_t>(p) & 15u); }
 
 int grid1(size_t count) { return (int)std::max<size_t>(1, std::min<size_t>((count + 255) / 256, 152 * 16)); }
@@ -987,6 +1026,41 @@ extern "C" {
 int devel_dsn_grads(const devel_dsn* d, float* host) {
     if (!d || !host) return set_error(DEVEL_EINVAL, "devel_dsn_grads: NULL argument");
     DEVEL_CUDA_TRY(cudaMemcpy(host, d->G, sizeof(float) * d->nparams, cudaMemcpyDeviceToHost));
+    return DEVEL_OK;
+}
+
+}  // extern "C"
+
+namespace devel {
+namespace {
+int resample_args(const char* where, int n, int f, int nb, const float* a, const float* b) {
+    if (n < 1 || n > 16384 || f < 1 || n % f)
+        return set_error(DEVEL_EINVAL, "%s: n=%d, f=%d (need 1 <= n <= 16384, f >= 1, n %% f == 0)", where, n, f);
+    if (nb < 0) return set_error(DEVEL_EINVAL, "%s: nb=%d < 0", where, nb);
+    if (nb > 0 && (bad_ptr(a) || bad_ptr(b)))
+        return set_error(DEVEL_EINVAL, "%s: NULL or not 16-byte aligned argument", where);
+    return DEVEL_OK;
+}
+}  // namespace
+}  // namespace devel
+
+extern "C" {
+
+int devel_phi_downsample(int n, int f, int nb, const float* fine, float* coarse, cudaStream_t s) {
+    const int rc = resample_args("devel_phi_downsample", n, f, nb, fine, coarse);
+    if (rc || nb == 0) return rc;
+    const size_t count = (size_t)nb * (n / f) * (n / f);
+    k_phi_down<<<grid1(count), 256, 0, s>>>(fine, n, f, count, (float)(1.0 / ((double)f * f * f)), coarse);
+    DEVEL_LAUNCH_CHECK("devel_phi_downsample");
+    return DEVEL_OK;
+}
+
+int devel_phi_upsample(int n, int f, int nb, const float* coarse, float* fine, cudaStream_t s) {
+    const int rc = resample_args("devel_phi_upsample", n, f, nb, coarse, fine);
+    if (rc || nb == 0) return rc;
+    const size_t count = (size_t)nb * n * n;
+    k_phi_up<<<grid1(count), 256, 0, s>>>(coarse, n, f, count, fine);
+    DEVEL_LAUNCH_CHECK("devel_phi_upsample");
     return DEVEL_OK;
 }
 

@@ -227,6 +227,12 @@ def _tcc(k: int, f_cut: float, sigma_in: float, sigma_out: float, sub: int, defo
     return tcc if defocus != 0.0 else tcc.real
 
 
+def manhattan_clip_bits(seed: int) -> np.ndarray:
+    """``manhattan_clip(seed)`` packed eight pixels per byte (``np.packbits``, row-major),
+    for handing many clips between processes."""
+    return np.packbits(manhattan_clip(seed))
+
+
 def optics(n: int, K: int, k: int, sigma_in: float = 0.6, sigma_out: float = 0.9,
            sub: int = 4, phase_seed: int | None = 12345, defocus: float = 0.0) -> Optics:
     """SOCS kernels of a synthetic annular-source Hopkins system.

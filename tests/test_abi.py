@@ -68,6 +68,16 @@ def test_argument_checks_need_no_device(lib):
     lib.devel_cg_direction.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 4
     assert lib.devel_cg_direction(None, 16, 32, 48, 0, None, 64, None, None) == dv.DEVEL_EINVAL
     assert "optics" in dv.devel_last_error()
+    # resampling: sides that the factor does not divide, a zero factor, a negative batch
+    # and misaligned pointers are refused; an empty batch is a no-op
+    for fn in (lib.devel_phi_downsample, lib.devel_phi_upsample):
+        fn.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 3
+        assert fn(64, 3, 1, 16, 32, None) == dv.DEVEL_EINVAL
+        assert fn(64, 0, 1, 16, 32, None) == dv.DEVEL_EINVAL
+        assert fn(64, 4, -1, 16, 32, None) == dv.DEVEL_EINVAL
+        assert fn(64, 4, 1, 17, 32, None) == dv.DEVEL_EINVAL
+        assert fn(64, 4, 1, None, 32, None) == dv.DEVEL_EINVAL
+        assert fn(64, 4, 0, None, None, None) == dv.DEVEL_OK
 
 
 def test_ilt_params_layout_matches_the_header():

@@ -151,3 +151,82 @@ def test_modulation_branch_step_matches_oracle():
     Gg = _unflatten(net.grads(), WIDTH)
     for i, (a, b) in enumerate(zip(Gg, G)):
         assert rel_err(a, b) <= 5e-2, (i, rel_err(a, b))
+
+
+# Resampling between a clip's grid and the network's coarser grid, against the oracle
+# (oracle/dsn.py phi_downsample / phi_upsample). FP32 on the GPU: the block sum has
+# f^2 - 1 roundings and the interpolation a handful, hence the bounds below.
+
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("n,f,nb", [(64, 4, 3), (96, 3, 2), (30, 5, 1), (16, 1, 2)])
+def test_phi_resampling_matches_oracle(n, f, nb):
+    dv = need_gpu()
+    rng = np.random.default_rng(n + f)
+    m = n // f
+    fine = (rng.standard_normal((nb, n, n)) * 40.0).astype(np.float32)
+    coarse = (rng.standard_normal((nb, m, m)) * 10.0).astype(np.float32)
+    c_gpu = torch.empty(nb * m * m, dtype=torch.float32, device="cuda")
+    f_gpu = torch.empty(nb * n * n, dtype=torch.float32, device="cuda")
+    dv.devel_phi_downsample(n, f, dev(fine), c_gpu)
+    dv.devel_phi_upsample(n, f, dev(coarse), f_gpu)
+    torch.cuda.synchronize()
+    down, up = host(c_gpu).reshape(nb, m, m), host(f_gpu).reshape(nb, n, n)
+    ref_down, ref_up = dsn.phi_downsample(fine, f), dsn.phi_upsample(coarse, f)
+    if f == 1:                       # identity maps: bit-exact
+        assert np.array_equal(down, fine) and np.array_equal(up, coarse)
+    tol_down = (f * f + 1) * U32 * np.abs(fine).max() / f
+    assert np.abs(down - ref_down).max() <= tol_down
+    tol_up = f * np.abs(coarse).max() * (8 + 2 * m) * U32
+    assert np.abs(up - ref_up).max() <= tol_up
+
+
+def test_phi_resampling_at_full_clip_size():
+    """The bench's sizes (2048^2 clips, a 512^2 network grid, f = 4): every coarse pixel
+    of the upsampled-then-downsampled field, and sampled windows of each map against the
+    oracle."""
+    dv = need_gpu()
+    n, f, nb = 2048, 4, 2
+    m = n // f
+    rng = np.random.default_rng(7)
+    coarse = (rng.standard_normal((nb, m, m)) * 10.0).astype(np.float32)
+    f_gpu = torch.empty(nb * n * n, dtype=torch.float32, device="cuda")
+    c_gpu = torch.empty(nb * m * m, dtype=torch.float32, device="cuda")
+    dv.devel_phi_upsample(n, f, dev(coarse), f_gpu)
+    dv.devel_phi_downsample(n, f, f_gpu, c_gpu)
+    torch.cuda.synchronize()
+    up = host(f_gpu).reshape(nb, n, n)
+    down = host(c_gpu).reshape(nb, m, m)
+    ref_up = dsn.phi_upsample(coarse, f)
+    assert np.abs(up - ref_up).max() <= f * np.abs(coarse).max() * 16 * U32   # power-of-two f: exact positions
+    for b, I, J in [(0, 0, 0), (1, 496, 3), (0, 255, 256), (1, 496, 496)]:   # 16 x 16 windows inside 512^2
+        win = up[b, I * f:I * f + 16 * f, J * f:J * f + 16 * f]
+        ref = dsn.phi_downsample(win, f)
+        got = down[b, I:I + 16, J:J + 16]
+        assert np.abs(got - ref).max() <= (f * f + 1) * U32 * np.abs(win).max() / f
+
+
+def test_network_on_the_full_clip_grid():
+    """The network at the side the full-size learned start uses (512^2, width 32): a zero
+    head returns the band-limited input exactly, and a training step gives a finite loss
+    and finite outputs."""
+    dv = need_gpu()
+    S, nb = 512, 2
+    net = dv.Dsn(S, nb, 32, seed=5)
+    p = net.get_params()
+    p[-33:] = 0.0
+    net.set_params(p)
+    yy, xx = np.mgrid[0:S, 0:S]
+    tsdf = np.stack([np.hypot(yy - 200.0, xx - 260.0) - 90.0, 300.0 - np.abs(xx - 256.0) - 0.5]).astype(np.float32)
+    out = torch.empty(nb * S * S, dtype=torch.float32, device="cuda")
+    net.forward(nb, dev(tsdf), out, B)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out).reshape(tsdf.shape), np.clip(tsdf, -B, B))
+    net = dv.Dsn(S, nb, 32, seed=6)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.train_step(nb, dev(tsdf), dev(tsdf + 3.0), 1e-3, loss, B)
+    net.forward(nb, dev(tsdf), out, B)
+    torch.cuda.synchronize()
+    assert np.isfinite(loss.item()) and loss.item() > 0
+    assert np.all(np.isfinite(host(out)))
