@@ -170,3 +170,11 @@ def test_resampling_without_centre_alignment_or_unit_change_is_caught(monkeypatc
     monkeypatch.setattr(dsn, "phi_downsample",                                     # block's first pixel only
                         lambda a, f: np.asarray(a, dtype=np.float64)[..., ::f, ::f] / f)
     _fails(td.test_phi_downsample_of_an_affine_field_is_its_centre_value_in_coarse_pixels, 4)
+
+
+def test_sigmoid_with_the_wrong_sign_is_caught(monkeypatch):
+    from oracle import resist
+    import test_oracle_resist as tr
+    monkeypatch.setattr(resist, "sigmoid_resist", lambda I, sz, th: 1.0 / (1.0 + np.exp(sz * (I - th))))
+    _fails(tr.test_sigmoid_midpoint_symmetry_and_limits)
+    _fails(tr.test_saturated_loss_counts_misprinted_pixels)

@@ -58,3 +58,35 @@ def test_beta_zero_drops_corner_terms():
     b = resist.resist(I, Zt, resist.ResistParams(beta=7.5))
     assert abs(a.loss - a.loss_terms[0]) == 0.0
     assert abs(b.loss - (b.loss_terms[0] + 7.5 * (b.loss_terms[1] + b.loss_terms[2]))) <= 1e-13 * b.loss
+
+
+def test_sigmoid_midpoint_symmetry_and_limits():
+    """The sigmoid resist prints half at the threshold, is point-symmetric about it,
+    saturates to 0 / 1 within exp(-sigma_z) one unit away, and its slope at the
+    threshold is sigma_z / 4 (central difference)."""
+    th, sz = 0.225, 50.0
+    assert resist.sigmoid_resist(np.array(th), sz, th) == 0.5
+    x = np.linspace(-0.3, 0.3, 61)
+    s = resist.sigmoid_resist(th + x, sz, th) + resist.sigmoid_resist(th - x, sz, th)
+    assert np.allclose(s, 1.0, rtol=0, atol=1e-15)
+    assert 1.0 - resist.sigmoid_resist(np.array(th + 1.0), sz, th) <= 1e-21
+    assert resist.sigmoid_resist(np.array(th - 1.0), sz, th) < 1e-21
+    h = 1e-6
+    slope = (resist.sigmoid_resist(np.array(th + h), sz, th) - resist.sigmoid_resist(np.array(th - h), sz, th)) / (2 * h)
+    assert abs(slope - sz / 4) <= 1e-6 * sz
+
+
+def test_saturated_loss_counts_misprinted_pixels():
+    """Far above (below) the threshold every corner prints (does not print), so the
+    loss is the count of target pixels that disagree, weighted alpha + 2 beta, and
+    dL/dI vanishes; the metrics count the same pixels."""
+    n = 12
+    rng = np.random.default_rng(3)
+    Zt = (rng.random((n, n)) < 0.4).astype(np.uint8)
+    for level, printed in ((5.0, 1), (-5.0, 0)):
+        I = np.full((n, n), level)
+        out = resist.resist(I, Zt, resist.ResistParams(alpha=1.0, beta=7.5))
+        wrong = int(np.count_nonzero(Zt != printed))
+        assert abs(out.loss - (1.0 + 2 * 7.5) * wrong) <= 1e-12 * max(wrong, 1)
+        assert np.abs(out.R).max() <= 1e-60
+        assert out.l2 == wrong and out.pvb == 0
