@@ -37,6 +37,8 @@ WORKLOADS = {
     # sides, seeds 2001.. the patterns), window k_n = 2 ceil(17 n / 2048) + 1 at 1 nm/px,
     # compensated BF16, one devel_ilt_solve per step over the whole batch
     "uneven64": dict(batch=64, sides=(512, 1024, 1536, 2048), K=24, iters=100, beta=7.5, seed=2000),
+    # the same schedule with every clip at 2048^2 (64 full-size clips per call)
+    "batch2048": dict(batch=64, sides=(2048,), K=24, iters=100, beta=7.5, seed=2000),
     # modulation-branch labels (Sec. III-B): per clip a plain solve gives phi_gt, then 16
     # candidate maps H(phi_gt + dh), dh ~ U[-20, 20], each solved (one devel_ilt_solve,
     # one handle per candidate) and the smallest final L_DSO picked
