@@ -10,9 +10,11 @@
  *   devel_resist_loss     Sec. III-A sigmoid resist, L_ilt, L_pvb; Sec. II-C L2, PVBand
  *   devel_litho_adjoint   Eqs. (ilt_gradient), (pvb_gradient), (vel)  dL/dM from dL/dI
  *   devel_levelset_step   Eqs. (dso_evolution), (numerical-settings), (curva_numer), (phi2mask)
+ *   devel_levelset_step_weno5   the same step with WENO5 one-sided derivatives (Sec. III-C)
  *   devel_cg_direction    Sec. III-C conjugate-gradient direction of the velocity
  *   devel_modulation_candidates, devel_ahf_loss   Sec. III-B modulation-branch supervision
  *   devel_dsn_*           Sec. III-B DSN level-set branch: learned initial level set, training
+ *   devel_phi_downsample, devel_phi_upsample   level sets between a clip's grid and the DSN's
  *   devel_shot_count      Sec. II-C.3 mask fracturing shot count (host)
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
  *
