@@ -35,3 +35,19 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--workload", "rect256", "--steps", "1", "--gpus", "2")
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_flop_and_byte_accounting():
+    """The benchmark's accounting against the figures the scope states: the truncated-DFT
+    method's real flops per iteration (0.142 GFLOP at 256^2, K = 8, k = 15; 58.5 GFLOP at
+    2048^2, K = 24, k = 35) and the per-pixel algorithmic bytes of the streaming kernels."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert abs(bench.algorithmic_flops_per_iter(256, 8, 15) / 1e9 - 0.142) < 0.0005
+    assert abs(bench.algorithmic_flops_per_iter(2048, 24, 35) / 1e9 - 58.5) < 0.05
+    px = 2048 * 2048
+    assert bench.kernel_bytes("resist", 2048, 24, 35, True) == 9 * px
+    assert bench.kernel_bytes("levelset_step", 2048, 24, 35, False) == 13 * px
+    assert bench.kernel_bytes("edt_rows", 2048, 24, 35, True) == 13 * px
+    # the difference window removes the K dependence of the n^2-sized work
+    assert bench.window_flops_per_iter(2048, 24, 35) < bench.algorithmic_flops_per_iter(2048, 24, 35) / 10
