@@ -178,3 +178,35 @@ def test_sigmoid_with_the_wrong_sign_is_caught(monkeypatch):
     monkeypatch.setattr(resist, "sigmoid_resist", lambda I, sz, th: 1.0 / (1.0 + np.exp(sz * (I - th))))
     _fails(tr.test_sigmoid_midpoint_symmetry_and_limits)
     _fails(tr.test_saturated_loss_counts_misprinted_pixels)
+
+
+def test_tsdf_without_the_half_pixel_or_with_city_block_distance_is_caught(monkeypatch):
+    from oracle import sdf
+    import test_oracle_sdf as ts
+    orig = sdf.opposite_class_d2
+
+    def tsdf_no_half(mask, d_lo=sdf.D_LO, d_hi=sdf.D_HI, rows=None):
+        mask = (np.asarray(mask) != 0).astype(np.uint8)
+        d = orig(mask, rows)
+        m = mask if rows is None else mask[np.asarray(rows)]
+        dist = np.where(d < 0, np.inf, np.sqrt(np.where(d < 0, 0, d).astype(np.float64)))
+        return np.clip(np.where(m == 0, dist, -dist), d_lo, d_hi)
+    monkeypatch.setattr(sdf, "tsdf", tsdf_no_half)
+    _fails(ts.test_tsdf_hand_values)
+    _fails(ts.test_tsdf_clamps_and_degenerate_masks)
+    monkeypatch.undo()
+
+    def city_block(mask, value):                 # |dy| + |dx| instead of dy^2 + dx^2
+        M = np.asarray(mask) != 0
+        src = np.argwhere(M == bool(value))
+        H, W = M.shape
+        out = np.full((H, W), sdf.INF, dtype=np.int64)
+        for y in range(H):
+            for x in range(W):
+                if len(src):
+                    d = np.abs(src[:, 0] - y) + np.abs(src[:, 1] - x)
+                    out[y, x] = int((d.min()) ** 2)
+        return out
+    monkeypatch.setattr(sdf, "edt_sq_rows", lambda mask, value, rows=None, g=None:
+                        city_block(mask, value) if rows is None else city_block(mask, value)[np.asarray(rows)])
+    _fails(ts.test_edt_sampled_rows_match_bruteforce)
