@@ -210,3 +210,19 @@ def test_tsdf_without_the_half_pixel_or_with_city_block_distance_is_caught(monke
     monkeypatch.setattr(sdf, "edt_sq_rows", lambda mask, value, rows=None, g=None:
                         city_block(mask, value) if rows is None else city_block(mask, value)[np.asarray(rows)])
     _fails(ts.test_edt_sampled_rows_match_bruteforce)
+
+
+def test_reinitialisation_one_iteration_early_is_caught(monkeypatch):
+    from oracle import levelset as ls, litho as lt, resist as rs, sdf, solve
+    import test_oracle_solve as tso
+
+    def iterate_early(phi, Zt, H, w, p, i, m=None, defocus=None, cg_state=None):
+        M = ls.mask_from_phi(phi)
+        res = rs.resist(lt.aerial(M, H, w), Zt, p.resist)
+        V = lt.aerial_gradient(M, res.R, H, w)
+        phi, M = ls.step(phi, V, float(np.abs(V).max()), m, p.dt, p.lam, weno=p.weno)
+        if p.reinit_every > 0 and i % p.reinit_every == 0:       # i instead of i + 1
+            phi = sdf.tsdf(M, p.d_lo, p.d_hi)
+        return phi, res
+    monkeypatch.setattr(solve, "iterate", iterate_early)
+    _fails(tso.test_reinitialisation_schedule)

@@ -49,3 +49,14 @@ def test_loop_improves_printability():
     out = solve.ilt_solve(Zt, o.H, o.w, p)
     assert out.loss[-1] < 0.8 * out.loss[0]
     assert out.l2[-1] < out.l2[0]
+
+
+def test_reinitialisation_schedule():
+    """Reading of the re-initialisation period: phi becomes the TSDF of its mask right
+    after the update of every iteration i with (i + 1) a multiple of reinit_every
+    (global index), and only then."""
+    o, Zt = _setup()
+    for iters, start, reinit in ((5, 0, True), (4, 0, False), (6, 0, False), (2, 3, True), (2, 4, False)):
+        out = solve.ilt_solve(Zt, o.H, o.w, solve.SolveParams(iters=iters, reinit_every=5, start_iter=start))
+        is_tsdf = np.array_equal(out.phi, sdf.tsdf(out.mask))
+        assert is_tsdf == reinit, (iters, start)
