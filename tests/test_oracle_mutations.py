@@ -226,3 +226,10 @@ def test_reinitialisation_one_iteration_early_is_caught(monkeypatch):
         return phi, res
     monkeypatch.setattr(solve, "iterate", iterate_early)
     _fails(tso.test_reinitialisation_schedule)
+
+
+def test_aerial_image_without_the_socs_weights_is_caught(monkeypatch):
+    monkeypatch.setattr(litho, "aerial", lambda M, H, w: sum(np.abs(litho.coherent_field(M, H[j])) ** 2
+                                                             for j in range(H.shape[0])))
+    _fails(tli.test_clear_field_is_dc_response)
+    _fails(tli.test_pinhole_images_kernel_intensity)
