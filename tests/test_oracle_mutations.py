@@ -233,3 +233,23 @@ def test_aerial_image_without_the_socs_weights_is_caught(monkeypatch):
                                                              for j in range(H.shape[0])))
     _fails(tli.test_clear_field_is_dc_response)
     _fails(tli.test_pinhole_images_kernel_intensity)
+
+
+def test_pvband_as_union_or_with_linear_dose_is_caught(monkeypatch):
+    import dataclasses
+    from oracle import resist
+    import test_oracle_resist as tr
+    orig = resist.resist
+
+    def with_pvb(rule):
+        def f(I, Zt, p, I_def=None):
+            r = orig(I, Zt, p, I_def)
+            return dataclasses.replace(r, pvb=rule(np.asarray(I, dtype=np.float64), p))
+        return f
+    union = lambda I, p: int(np.count_nonzero(resist.threshold_resist(p.dose_in ** 2 * I, p.I_th)
+                                              | resist.threshold_resist(p.dose_out ** 2 * I, p.I_th)))
+    linear = lambda I, p: int(np.count_nonzero(resist.threshold_resist(p.dose_in * I, p.I_th)
+                                               != resist.threshold_resist(p.dose_out * I, p.I_th)))
+    for rule in (union, linear):
+        monkeypatch.setattr(resist, "resist", with_pvb(rule))
+        _fails(tr.test_pvband_hand_count)
