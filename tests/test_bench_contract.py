@@ -38,9 +38,10 @@ def test_reference_arm_other_ranks_exit_quietly():
 
 
 def test_flop_and_byte_accounting():
-    """The benchmark's accounting against the figures the scope states: the truncated-DFT
-    method's real flops per iteration (0.142 GFLOP at 256^2, K = 8, k = 15; 58.5 GFLOP at
-    2048^2, K = 24, k = 35) and the per-pixel algorithmic bytes of the streaming kernels."""
+    """The benchmark's accounting: the truncated-DFT method's real flops per iteration,
+    16 K k n^2 + 8 k n^2 + 16 K n k^2 + 16 n k^2 (0.142 GFLOP at 256^2, K = 8, k = 15;
+    58.5 GFLOP at 2048^2, K = 24, k = 35), and the per-pixel algorithmic bytes of the
+    streaming kernels."""
     sys.path.insert(0, ROOT)
     import bench
     assert abs(bench.algorithmic_flops_per_iter(256, 8, 15) / 1e9 - 0.142) < 0.0005
