@@ -1062,7 +1062,10 @@ def run_learned_full_size(args, wl):
         t0 = time.perf_counter()
         r = fn()
         torch.cuda.synchronize()
-        return r, time.perf_counter() - t0
+        t = time.perf_counter() - t0
+        if int(st.item()) != 0:          # the solves' status word (non-finite loss or velocity)
+            raise RuntimeError(f"solver status {int(st.item())}")
+        return r, t
 
     # warm-up: every kernel of every arm once, on a few clips
     wc = min(G, T)
