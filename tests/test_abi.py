@@ -113,3 +113,26 @@ def test_new_entry_points_refuse_bad_arguments_without_a_device(lib):
     assert lib.devel_shot_count(0, None, None) == dv.DEVEL_EINVAL
     # the shot count is host code: it runs here
     assert dv.devel_shot_count(np.eye(5, dtype=np.uint8)) == 5
+
+
+def test_last_error_is_per_thread(lib):
+    """devel_last_error() is thread-local: two threads failing in different calls each read
+    their own message (no device needed: the checks refuse the arguments first)."""
+    import threading
+    import paper_2303_12529_gb300 as dv
+    for fn in (lib.devel_phi_downsample, lib.devel_phi_upsample):
+        fn.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 3
+    lib.devel_last_error.restype = ctypes.c_char_p
+    out = {}
+    go = threading.Barrier(2)
+
+    def fail(name, call):
+        rc = call()
+        go.wait()                      # both have failed before either reads
+        out[name] = (rc, lib.devel_last_error().decode())
+
+    t1 = threading.Thread(target=fail, args=("a", lambda: lib.devel_phi_downsample(64, 3, 1, 16, 32, None)))
+    t2 = threading.Thread(target=fail, args=("b", lambda: lib.devel_phi_upsample(64, 4, -2, 16, 32, None)))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert out["a"][0] == dv.DEVEL_EINVAL and "devel_phi_downsample" in out["a"][1] and "f=3" in out["a"][1]
+    assert out["b"][0] == dv.DEVEL_EINVAL and "devel_phi_upsample" in out["b"][1] and "nb=-2" in out["b"][1]
