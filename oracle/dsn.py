@@ -82,19 +82,23 @@ def conv_backward(x, W, dy):
 
 
 def avgpool(x):
+    """Down one level of the encoder (Sec. III-B reading): the mean of each 2 x 2 block."""
     N, C, H, W = x.shape
     return x.reshape(N, C, H // 2, 2, W // 2, 2).mean(axis=(3, 5))
 
 
 def avgpool_backward(dy):
+    """Adjoint of avgpool: each gradient spread over its 2 x 2 block, times 1/4."""
     return np.repeat(np.repeat(dy, 2, axis=2), 2, axis=3) / 4.0
 
 
 def upsample(x):
+    """Up one level of the decoder (Sec. III-B reading): nearest-neighbour 2x."""
     return np.repeat(np.repeat(x, 2, axis=2), 2, axis=3)
 
 
 def upsample_backward(dy):
+    """Adjoint of upsample: the sum over each 2 x 2 block."""
     N, C, H, W = dy.shape
     return dy.reshape(N, C, H // 2, 2, W // 2, 2).sum(axis=(3, 5))
 
@@ -162,6 +166,7 @@ def backward(P, x, cache, dy):
 
 
 def mse(y, label):
+    """Training loss of the level-set branch (Sec. III-B): mean (y - label)^2 and its gradient in y."""
     d = y - label
     return float(np.mean(d * d)), 2.0 * d / d.size
 
@@ -180,6 +185,7 @@ def ahf_mean(y, m_gt, eps: float):
 
 @dataclass
 class Adam:
+    """Adam (Kingma and Ba) with bias correction, the optimiser of the network's training."""
     lr: float = 1e-3
     b1: float = 0.9
     b2: float = 0.999
@@ -232,4 +238,5 @@ def phi_upsample(c, f: int):
 
 
 def band(phi, B: float = BAND):
+    """Band-limited level set in network units: clip(phi, -B, B) / B."""
     return np.clip(np.asarray(phi, dtype=np.float64), -B, B) / B

@@ -37,6 +37,7 @@ def mask_from_phi(phi: np.ndarray) -> np.ndarray:
 
 
 def _pad(phi):
+    """Replicate-edge ghost pixels for the stencils (Neumann borders; the paper states no border rule)."""
     return np.pad(np.asarray(phi, dtype=np.float64), 1, mode="edge")
 
 

@@ -25,6 +25,7 @@ import numpy as np
 
 @dataclass
 class ResistParams:
+    """Resist and loss constants: sigma_z, I_th (Sec. IV values), loss weights alpha / beta (Sec. III-A), dose corners (Sec. II-C)."""
     sigma_z: float = 50.0     # Sec. IV hyper-parameters
     I_th: float = 0.225
     alpha: float = 1.0
@@ -35,6 +36,7 @@ class ResistParams:
 
 @dataclass
 class ResistResult:
+    """L_DSO, its three squared-error terms, dL/dI (and dL/dI_def), and the binary L2 and PVBand counts."""
     loss: float
     loss_terms: tuple  # (sum (Z_nom-Zt)^2, sum (Z_in-Zt)^2, sum (Z_out-Zt)^2)
     R: np.ndarray      # dL/dI
@@ -44,10 +46,12 @@ class ResistResult:
 
 
 def sigmoid_resist(I: np.ndarray, sigma_z: float, I_th: float) -> np.ndarray:
+    """Sigmoid resist of Sec. III-A: Z = 1 / (1 + exp(-sigma_z (I - I_th)))."""
     return 1.0 / (1.0 + np.exp(-sigma_z * (I - I_th)))
 
 
 def threshold_resist(I: np.ndarray, I_th: float) -> np.ndarray:
+    """Constant-threshold resist of Sec. II-B: Z = [I >= I_th] (a tie prints)."""
     return (I >= I_th).astype(np.uint8)
 
 

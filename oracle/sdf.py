@@ -78,6 +78,7 @@ def edt_sq_rows(mask: np.ndarray, value: int, rows=None, g=None) -> np.ndarray:
 
 
 def edt_sq(mask: np.ndarray, value: int) -> np.ndarray:
+    """Exact squared distance of every pixel to the nearest pixel equal to value (Eq. sdf), all rows."""
     return edt_sq_rows(mask, value)
 
 

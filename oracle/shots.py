@@ -17,6 +17,7 @@ import numpy as np
 
 
 def min_partition(mask: np.ndarray) -> int:
+    """Shot count of a small mask (Sec. II-C.3 reading): the fewest rectangles partitioning it, by memoised search."""
     M = (np.asarray(mask) != 0)
     H, W = M.shape
     full = 0

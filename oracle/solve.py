@@ -26,6 +26,7 @@ from . import cg, litho, resist as _resist, levelset, sdf
 
 @dataclass
 class SolveParams:
+    """Parameters of the DSO loop (Sec. III-C, Sec. IV): resist, dt, lambda, iterations, re-initialisation period, start index, clamp, options."""
     resist: _resist.ResistParams = field(default_factory=_resist.ResistParams)
     dt: float = 0.5
     lam: float = 0.1
@@ -40,6 +41,7 @@ class SolveParams:
 
 @dataclass
 class SolveResult:
+    """Final phi and mask, and per-iteration L_DSO, L2 and PVBand (entry iters: the final mask)."""
     phi: np.ndarray
     mask: np.ndarray
     loss: list
@@ -76,6 +78,7 @@ def iterate(phi, Zt, H, w, p: SolveParams, i: int, m=None, defocus=None, cg_stat
 
 
 def ilt_solve(Zt, H, w, p: SolveParams, phi0=None, m=None, defocus=None) -> SolveResult:
+    """The DSO loop of Sec. III-A / III-C from phi0 (default: the TSDF of the target, Eq. tsdf), m the optional modulation map."""
     Zt = (np.asarray(Zt) != 0).astype(np.uint8)
     phi = sdf.tsdf(Zt, p.d_lo, p.d_hi) if phi0 is None else np.asarray(phi0, dtype=np.float64).copy()
     loss, l2, pvb = [], [], []
