@@ -1,4 +1,4 @@
-// Optional per-kernel timing with CUDA events.
+// Optional per-kernel timing with CUDA events (tracing; no counterpart in the paper).
 //
 // When a profile is open (devel_profile_start), every kernel launch of the
 // library is bracketed by two events recorded on the launching stream; after

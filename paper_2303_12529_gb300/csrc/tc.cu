@@ -1,4 +1,6 @@
-// Tensor-core (tcgen05) kernels of the truncated-DFT contractions, sm_103a.
+// Tensor-core (tcgen05) kernels of the truncated-DFT contractions, sm_103a: the
+// n^2-sized work of the SOCS image of Sec. II-B (forward) and of its gradient, Eqs.
+// (ilt_gradient), (pvb_gradient) (adjoint), both taken through the difference window.
 //
 // Operands are bf16 hi/lo pairs (x = hi + lo, hi = rn_bf16(x), lo = rn_bf16(x - hi));
 // products are compensated, A B^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T, with
