@@ -20,3 +20,10 @@ def test_oracle_solve_matches_its_record():
     assert np.allclose(got["loss"], rec["loss"], rtol=1e-9, atol=0)
     assert got["l2"] == rec["l2"] and got["pvb"] == rec["pvb"]
     assert got["mask_pixels"] == rec["mask_pixels"]
+    assert np.allclose([got["phi_sum"], got["phi_sq_sum"]], [rec["phi_sum"], rec["phi_sq_sum"]], rtol=1e-9)
+    for name, stored in rec["variants"].items():
+        got = mk.run(rec["case"], mk.VARIANTS[name])
+        assert np.allclose(got["loss"], stored["loss"], rtol=1e-9, atol=0), name
+        assert got["l2"] == stored["l2"] and got["pvb"] == stored["pvb"], name
+        assert np.allclose([got["phi_sum"], got["phi_sq_sum"]], [stored["phi_sum"], stored["phi_sq_sum"]],
+                           rtol=1e-9), name
