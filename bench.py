@@ -778,6 +778,11 @@ def run_learned(args, wl):
 
     bufs = {}
 
+    def check_status():
+        """The last solve's status word (non-finite loss or velocity): read after a sync."""
+        if int(st.item()) != 0:
+            raise RuntimeError(f"solver status {int(st.item())}")
+
     def solve_all(tg, iters, phi0=None, hs=None, m=None):
         """Solves every clip (phi0 given: from phi0, in place); returns (phi [count, N],
         final L2 + PVB per clip). Buffers persist per (set, iterations, start), so a
@@ -876,6 +881,7 @@ def run_learned(args, wl):
     _, q_plain = solve_all(te, wl["plain_iters"])
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
+    check_status()
     # the plain FP32 solver (the comparator of the learned + BF16 path): 100 iterations
     solve_all(te, wl["plain_iters"], hs=handles32)
     torch.cuda.synchronize()
@@ -883,6 +889,7 @@ def run_learned(args, wl):
     _, q_fp32 = solve_all(te, wl["plain_iters"], hs=handles32)
     torch.cuda.synchronize()
     t_fp32 = time.perf_counter() - t0
+    check_status()
     # learned: DSN phi_0, then 15 iterations
     phi0 = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
 
@@ -899,6 +906,7 @@ def run_learned(args, wl):
     _, q_learned = solve_all(te, wl["refine_iters"], phi0)
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
+    check_status()
     # learned phi_0 and learned modulation m = H_eps(phi_m): both branches, then 15 iterations
     m_te = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
 
@@ -916,6 +924,7 @@ def run_learned(args, wl):
     _, q_mod = solve_all(te, wl["refine_iters"], phi0, m=m_te)
     torch.cuda.synchronize()
     t_mod = time.perf_counter() - t0
+    check_status()
     # the same 15 iterations from the plain start (what the learned phi_0 buys)
     _, q_short = solve_all(te, wl["refine_iters"])
     torch.cuda.synchronize()
