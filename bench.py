@@ -778,10 +778,19 @@ def run_learned(args, wl):
 
     bufs = {}
 
-    def check_status():
-        """The last solve's status word (non-finite loss or velocity): read after a sync."""
-        if int(st.item()) != 0:
-            raise RuntimeError(f"solver status {int(st.item())}")
+    st_any = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def fold_status():
+        """Keeps the first non-zero status of any call (each devel_ilt_solve clears st at
+        its start), on the device, without a synchronisation."""
+        st_any.copy_(torch.where(st_any != 0, st_any, st))
+
+    def check_status(what):
+        """Every solve since the last check (non-finite loss or velocity): read after a sync."""
+        torch.cuda.synchronize()
+        code = int(st_any.item())
+        if code != 0:
+            raise RuntimeError(f"solver status {code} in {what}")
 
     def solve_all(tg, iters, phi0=None, hs=None, m=None):
         """Solves every clip (phi0 given: from phi0, in place); returns (phi [count, N],
@@ -805,6 +814,7 @@ def run_learned(args, wl):
                              l2_hist=l2[c0 + j, :iters + 1], pvb_hist=pvb[c0 + j, :iters + 1])
                      for j in range(min(G, cnt - c0))]
             dv.devel_ilt_solve(p, clips, st, stream)
+            fold_status()
         return phi, (l2[:, iters] + pvb[:, iters])
 
     def tsdf_all(tg):
@@ -819,6 +829,7 @@ def run_learned(args, wl):
     x_tr = tsdf_all(tr)
     torch.cuda.synchronize()
     t_label = time.perf_counter() - t0
+    check_status("the label solves")
 
     B = wl["dsn_batch"]
     net = dv.Dsn(n, B, wl["width"], seed=1)
@@ -853,6 +864,8 @@ def run_learned(args, wl):
         clips = [dv.Clip(handles[j], tg_rep[c0 + j], cphi[c0 + j], m=cand[c0 + j],
                          loss_hist=closs[c0 + j, :wl["plain_iters"] + 1]) for j in range(min(G, Nm * J - c0))]
         dv.devel_ilt_solve(pl, clips, st, stream)
+        fold_status()
+    check_status("the modulation-label solves")
     best = closs[:, wl["plain_iters"]].view(Nm, J).argmin(dim=1)
     m_gt = cand.view(Nm, J, N)[torch.arange(Nm, device=dev), best].contiguous()
     torch.cuda.synchronize()
@@ -881,7 +894,7 @@ def run_learned(args, wl):
     _, q_plain = solve_all(te, wl["plain_iters"])
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    check_status()
+    check_status("the plain arm")
     # the plain FP32 solver (the comparator of the learned + BF16 path): 100 iterations
     solve_all(te, wl["plain_iters"], hs=handles32)
     torch.cuda.synchronize()
@@ -889,7 +902,7 @@ def run_learned(args, wl):
     _, q_fp32 = solve_all(te, wl["plain_iters"], hs=handles32)
     torch.cuda.synchronize()
     t_fp32 = time.perf_counter() - t0
-    check_status()
+    check_status("the fp32 arm")
     # learned: DSN phi_0, then 15 iterations
     phi0 = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
 
@@ -906,7 +919,7 @@ def run_learned(args, wl):
     _, q_learned = solve_all(te, wl["refine_iters"], phi0)
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
-    check_status()
+    check_status("the learned arm")
     # learned phi_0 and learned modulation m = H_eps(phi_m): both branches, then 15 iterations
     m_te = torch.empty(wl["test"], N, dtype=torch.float32, device=dev)
 
@@ -924,10 +937,10 @@ def run_learned(args, wl):
     _, q_mod = solve_all(te, wl["refine_iters"], phi0, m=m_te)
     torch.cuda.synchronize()
     t_mod = time.perf_counter() - t0
-    check_status()
+    check_status("the mod arm")
     # the same 15 iterations from the plain start (what the learned phi_0 buys)
     _, q_short = solve_all(te, wl["refine_iters"])
-    torch.cuda.synchronize()
+    check_status("the 15-iteration plain arm")
     qp, ql, qs, qf, qm = (q.double().mean().item() for q in (q_plain, q_learned, q_short, q_fp32, q_mod))
     out = {"metric": "ILT clips/sec to converged L2+PVB at 256^2 (DSN phi_0 + 15 iterations vs 100 plain)",
            "value": wl["test"] / t_learned, "unit": "clips/s", "n_gpus": 1, "steps": 1, "warmup": 1,

@@ -255,7 +255,9 @@ int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, floa
  *     that loads the library, until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     before any stream capture begins. The address is kept for the life of
+ *     the process: after a cudaDeviceReset of that device it is stale, so do
+ *     not call this entry point again in a process that reset the device.
  *   - All calls share the one array: calls whose kernels overlap on the GPU
  *     (other streams, other threads) race on it; serialise them.
  *   - The array keeps the last call's contents; a call writes every word it

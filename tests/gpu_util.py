@@ -31,3 +31,12 @@ def rel_err(got, ref):
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def loss_bound(I, R, L, image_tol):
+    """How far a loss evaluated on an image with normwise error <= image_tol may sit from
+    the oracle's L: to first order |dL| <= sum_p |dL/dI(p)| |dI(p)| <= image_tol max|I|
+    sum_p |R(p)| (R = dL/dI of the oracle), plus 1e-5 |L| for the FP32 per-pixel resist
+    (the resist test's tolerance given the same image), with 10% slack for the
+    second-order term (|d2L/dI2| <= (2 sigma_z)^2 per pixel and image_tol^2 ~ 4e-8)."""
+    return 1.1 * image_tol * float(np.abs(I).max()) * float(np.abs(R).sum()) + 1e-5 * abs(float(L))

@@ -43,6 +43,19 @@ def test_binding_covers_the_header(lib):
     assert dv.devel_version() >> 16 == 1
 
 
+def test_binding_constants_match_the_header():
+    """The binding's copies of the header's limits and codes are the header's values."""
+    import paper_2303_12529_gb300 as dv
+    txt = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(DEVEL_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt))
+    assert int(defs["DEVEL_REINIT_STATIC_MAX_N"]) == dv.REINIT_STATIC_MAX_N
+    assert int(defs["DEVEL_MOD_MAX_CANDIDATES"]) == dv.DEVEL_MOD_MAX_CANDIDATES
+    for name in ("DEVEL_OK", "DEVEL_EINVAL", "DEVEL_ECUDA", "DEVEL_ENOMEM", "DEVEL_ETIMEOUT", "DEVEL_ENAN",
+                 "DEVEL_PREC_FP32", "DEVEL_PREC_BF16X3", "DEVEL_UPWIND_GODUNOV1", "DEVEL_UPWIND_WENO5",
+                 "DEVEL_OPT_STEEPEST", "DEVEL_OPT_CG"):
+        assert int(defs[name]) == getattr(dv, name), name
+
+
 def test_argument_checks_need_no_device(lib):
     import paper_2303_12529_gb300 as dv
     H = np.zeros((2, 5, 5), np.complex64)

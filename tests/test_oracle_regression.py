@@ -25,5 +25,6 @@ def test_oracle_solve_matches_its_record():
         got = mk.run(rec["case"], mk.VARIANTS[name])
         assert np.allclose(got["loss"], stored["loss"], rtol=1e-9, atol=0), name
         assert got["l2"] == stored["l2"] and got["pvb"] == stored["pvb"], name
+        assert got["mask_pixels"] == stored["mask_pixels"], name
         assert np.allclose([got["phi_sum"], got["phi_sq_sum"]], [stored["phi_sum"], stored["phi_sq_sum"]],
                            rtol=1e-9), name

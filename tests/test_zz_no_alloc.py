@@ -51,4 +51,4 @@ def test_static_scratch_refuses_sizes_beyond_the_array():
     phi = torch.empty(n * n, dtype=torch.float32, device="cuda")
     with pytest.raises(dv.DevelError) as e:
         dv.devel_reinit_sdf_static(n, M, phi)
-    assert e.value.code == dv.DEVEL_EINVAL and "2048" in str(e.value)
+    assert e.value.code == dv.DEVEL_EINVAL and str(dv.REINIT_STATIC_MAX_N) in str(e.value)
