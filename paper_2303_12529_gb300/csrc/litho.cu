@@ -432,17 +432,13 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
     return DEVEL_OK;
 }
 
-// tensor-core reduction: both contractions in one kernel (bf16 operand already in
-// Xhi/Xlo), then the slice sum and complex combination
+// tensor-core reduction: both contractions and the complex combination per CTA (bf16
+// operand already in Xhi/Xlo), then the sum of the CTAs' partial spectra
 int reduce_tc(const devel_optics* o, const Window& w, int use_alo, float2* out, cudaStream_t s) {
     const TcWindow& tw = tc_window(o, w);
     tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, use_alo};
-    int rc = tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, o->n, o->ldn, o->tc_split,
-                                  o->ws.Q, o->tc_err, s);
-    if (rc) return rc;
-    launch_spec_final(o->ws.Q, tc::spectrum2_slices(o->n, o->ldn, o->tc_split), w.ldk, w.kw, out, o->n, s);
-    DEVEL_LAUNCH_CHECK("k_spec_final");
-    return DEVEL_OK;
+    return tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, w.kw, o->n, o->n, o->ldn,
+                                o->tc_split, reinterpret_cast<float2*>(o->ws.Q), out, o->tc_err, s);
 }
 
 }  // namespace

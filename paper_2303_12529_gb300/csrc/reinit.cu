@@ -94,106 +94,133 @@ k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     }
 }
 
-// Row pass: d2(x) = min_x' [(x - x')^2 + g(x')^2] over the columns x' where the
-// wanted class occurs. One block per row, the row of packed g in shared memory;
-// each pixel searches outwards |x - x'| = 1, 2, ... while (x - x')^2 is below its
-// best candidate. Per 16-column block the smaller g of each class is kept, and
-// the search skips the rest of a block when even its best case (distance to the
-// nearest unscanned column squared plus the block minimum squared) cannot beat
-// the candidate (about 6 steps per pixel on a Manhattan clip).
+// Row pass: d2(x) = min_x' [(x - x')^2 + f(x')] with f = g^2 over the columns x' where
+// the wanted class occurs (an inside pixel looks for class 0, an outside one for class 1).
+// One block per row, the row's f of both classes in shared memory, with lower bounds on
+// 16-column blocks k (columns b0 .. b1): the block minimum of f and the lower envelope at
+// both edges, eR(k) = min (b1 - x')^2 + f(x'), eL(k) = min (x' - b0)^2 + f(x'). For x > b1
+// every column of k costs at least (x - b1)^2 + eR(k), since
+// (x - x')^2 >= (x - b1)^2 + (b1 - x')^2 (symmetrically eL for x < b0).
+// A warp takes 32 consecutive pixels and searches for all of them together, so that its
+// control flow is uniform: it scans the tile's own two blocks unless no lane's bound can
+// win, then walks outwards block by block while some lane's distance to the block is below
+// its best candidate, scanning (all 16 columns, every lane) each block whose bound can win
+// for some lane. Every skipped column provably cannot lower a lane's minimum, so the result
+// is the exact minimum.
 constexpr int kBlk = 16;
 constexpr int kEnvMaxN = 8192;
 
 // Squared column distance, or kFar when the column has no pixel of the class; kFar
-// plus any squared row distance (< 2^28 for n <= 8192) stays below INT_MAX.
+// plus a few squared distances (each < 2^26 for n <= 8192) stays below INT_MAX.
 constexpr int kFar = 1 << 30;
+
+__host__ __device__ constexpr int edt_nb(int n) { return (n + kBlk - 1) / kBlk; }
+
+// all 32 lanes: best = min(best, (x - x')^2 + f(x')) over the 16 columns of block k
+__device__ __forceinline__ int scan_block(const int* f, int x, int k, int best) {
+    const int b0 = k * kBlk;
+#pragma unroll
+    for (int j = 0; j < kBlk; ++j) {
+        const int d = x - (b0 + j);
+        best = min(best, d * d + f[b0 + j]);
+    }
+    return best;
+}
 
 __global__ void __launch_bounds__(256)
 k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g,
            float* __restrict__ phi, float d_lo, float d_hi) {
-    extern __shared__ int sfx[];  // f0[n], f1[n]: g^2 per class; b0[nb], b1[nb]: block minima
-    const int nb = (n + kBlk - 1) / kBlk;
-    int* f0 = sfx;
-    int* f1 = f0 + n;
-    int* b0 = f1 + n;
-    int* b1 = b0 + nb;
+    extern __shared__ int sfx[];
+    const int nb = edt_nb(n), npad = nb * kBlk;
+    // per class c: f at c npad, then the block minima, eL and eR at 2 npad + (0 / 2 / 4 + c) nb
+    int* const F = sfx;
+    int* const BM = sfx + 2 * npad;
+    int* const EL = BM + 2 * nb;
+    int* const ER = BM + 4 * nb;
     const int y = blockIdx.x;
     const size_t base = (size_t)y * n;
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        const unsigned w = g[base + x];
+    for (int x = threadIdx.x; x < npad; x += blockDim.x) {
+        const unsigned w = x < n ? g[base + x] : (kNone | (kNone << 16));
         const unsigned a = w & 0xFFFFu, b = w >> 16;
-        f0[x] = a == kNone ? kFar : (int)(a * a);
-        f1[x] = b == kNone ? kFar : (int)(b * b);
+        F[x] = a == kNone ? kFar : (int)(a * a);
+        F[npad + x] = b == kNone ? kFar : (int)(b * b);
     }
     __syncthreads();
     bool any0 = false, any1 = false;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        int m0 = kFar, m1 = kFar;
-        for (int x = b * kBlk; x < min(n, (b + 1) * kBlk); ++x) {
-            m0 = min(m0, f0[x]);
-            m1 = min(m1, f1[x]);
+    for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) {  // (class, block) pairs
+        const int c = i / nb, k = i - c * nb;
+        const int* fc = F + c * npad + k * kBlk;
+        int m = kFar, l = kFar, r = kFar;
+#pragma unroll
+        for (int j = 0; j < kBlk; ++j) {
+            const int v = fc[j];
+            m = min(m, v);
+            l = min(l, v + j * j);
+            r = min(r, v + (kBlk - 1 - j) * (kBlk - 1 - j));
         }
-        b0[b] = m0;
-        b1[b] = m1;
-        any0 |= m0 < kFar;
-        any1 |= m1 < kFar;
+        BM[c * nb + k] = m;
+        EL[c * nb + k] = l;
+        ER[c * nb + k] = r;
+        if (c == 0) any0 |= m < kFar;
+        else any1 |= m < kFar;
     }
     // rows in which a class never occurs (in any column) need no search for it
     const bool has0 = __syncthreads_or(any0), has1 = __syncthreads_or(any1);
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        const bool inside = mask[base + x] != 0;
-        // an inside pixel looks for class 0, an outside one for class 1
-        const int* f = inside ? f0 : f1;
-        const int* bm = inside ? b0 : b1;
-        int best = f[x];
-        if (inside ? has0 : has1) {
-            int L = x - 1, R = x + 1;
-            while (true) {
-                const int dl = x - L, dr = R - x;
-                const int dl2 = dl * dl, dr2 = dr * dr;
-                const bool lok = L >= 0 && dl2 < best;
-                const bool rok = R < n && dr2 < best;
-                if (!lok && !rok) break;
-                // skip the rest of the 16-column block holding L (or R) when even the block's
-                // minimum at the nearest unscanned column cannot win; valid at any position,
-                // since every unscanned column of the block is at least that far
-                if (lok) {
-                    if (dl2 + bm[L >> 4] >= best) {
-                        L = (L & ~(kBlk - 1)) - 1;
-                    } else {
-                        best = min(best, dl2 + f[L]);
-                        --L;
-                    }
-                }
-                if (rok) {
-                    if (dr2 + bm[R >> 4] >= best) {
-                        R = (R | (kBlk - 1)) + 1;
-                    } else {
-                        best = min(best, dr2 + f[R]);
-                        ++R;
-                    }
-                }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int x0 = warp * 32; x0 < n; x0 += nwarps * 32) {
+        const int x = x0 + lane;
+        const bool valid = x < n;
+        const bool inside = valid && mask[base + x] != 0;
+        const int c = inside ? 0 : 1;
+        const int* f = F + c * npad;
+        const int* bm = BM + c * nb;
+        const int* el = EL + c * nb;
+        const int* er = ER + c * nb;
+        const bool active = valid && (inside ? has0 : has1);
+        int best = valid ? f[x] : kFar;
+        // the tile's own blocks
+        const int tb0 = x0 / kBlk, tb1 = min(nb - 1, (x0 + 31) / kBlk);
+        for (int k = tb0; k <= tb1; ++k) {
+            const int b0 = k * kBlk, b1 = b0 + kBlk - 1;
+            int bound;
+            if (x < b0) bound = (b0 - x) * (b0 - x) + el[k];
+            else if (x > b1) bound = (x - b1) * (x - b1) + er[k];
+            else bound = 1 + bm[k];  // every other column of x's own block is >= 1 away
+            if (__any_sync(0xffffffffu, active && bound < best)) best = scan_block(f, x, k, best);
+        }
+        for (int k = tb0 - 1; k >= 0; --k) {  // blocks to the left, nearest first
+            const int d = x - (k * kBlk + kBlk - 1), dd = d * d;
+            const bool alive = active && dd < best;
+            if (!__any_sync(0xffffffffu, alive)) break;
+            if (__any_sync(0xffffffffu, alive && dd + er[k] < best)) best = scan_block(f, x, k, best);
+        }
+        for (int k = tb1 + 1; k < nb; ++k) {  // blocks to the right
+            const int d = k * kBlk - x, dd = d * d;
+            const bool alive = active && dd < best;
+            if (!__any_sync(0xffffffffu, alive)) break;
+            if (__any_sync(0xffffffffu, alive && dd + el[k] < best)) best = scan_block(f, x, k, best);
+        }
+        if (valid) {
+            float v;
+            int d2;
+            if (best >= kFar) {
+                d2 = -1;
+                v = inside ? d_lo : d_hi;
+            } else {
+                d2 = best;
+                const float dist = sqrtf((float)best) - 0.5f;
+                v = inside ? -dist : dist;
+                v = fminf(fmaxf(v, d_lo), d_hi);
             }
+            g[base + x] = (unsigned)d2;
+            phi[base + x] = v;
         }
-        float v;
-        int d2;
-        if (best >= kFar) {
-            d2 = -1;
-            v = inside ? d_lo : d_hi;
-        } else {
-            d2 = best;
-            const float dist = sqrtf((float)best) - 0.5f;
-            v = inside ? -dist : dist;
-            v = fminf(fmaxf(v, d_lo), d_hi);
-        }
-        g[base + x] = (unsigned)d2;
-        phi[base + x] = v;
     }
 }
 
 }  // namespace
 
-static size_t edt_rows_smem(int n) { return sizeof(int) * 2 * (n + (n + kBlk - 1) / kBlk); }
+static size_t edt_rows_smem(int n) { return sizeof(int) * (2 * edt_nb(n) * kBlk + 6 * edt_nb(n)); }
 
 int reinit_init_attrs() {
     DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -186,13 +186,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // Fused reduction onto a window: both contractions in one kernel
 // ---------------------------------------------------------------------------
-// CTA (row tile m0 of 128 image rows y, K slice z of 256 columns x):
+// CTA (row tile m0 of 128 image rows y, K slice z of `split` columns x):
 //   phase 1  D1[y][c] = sum_x X[y][x] basis[c][x]            (the mainloop above, M = 128, N = BN)
 //   phase 2  D1 is drained from TMEM, split to bf16 hi/lo and written transposed into shared
 //            memory as a K-major operand B2[c2][y] (128-byte swizzle, as TMA would lay it out);
 //            D2[c1][c2] = sum_y basis[c1][y] D1[y][c2] for c1 in 128-row blocks (A2 by TMA)
-//   out      D2 rows c1 < BN to Q + slice * BN^2, slice = m-tile * splits + z (BN = ldk)
-// The slices are then summed (in slice order) and combined into the complex window spectrum.
+//   combine  D2 (BN = ldk rows of cos / sin) becomes the CTA's partial complex spectrum
+//            P(a, b) = (D2[a][b] - D2[kw+a][kw+b]) - i (D2[a][kw+b] + D2[kw+a][b]), a, b < kw,
+//            assembled in shared memory and stored contiguously as slice
+//            blockIdx.y * gridDim.z + blockIdx.z of G ([slices][kw * kw] complex);
+// k_spec_sum then adds the slices in slice order and scales by 1/n^2.
+// Every sum runs in a fixed order, so the result does not depend on timing.
 template <int BN>
 struct Cfg2 {
     static constexpr uint32_t kB2 = BN * 128;                  // one k-block of B2 (bf16, 64 y)
@@ -215,12 +219,17 @@ struct Cfg2 {
     static constexpr size_t kSmem = 1024 + (size_t)kArena + 512;
 };
 
+struct SpecOut {
+    int kw;               // window side (kw <= BN / 2)
+    float2* G;            // [slices][kw * kw] partial spectra
+};
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
 k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
            const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
            const __grid_constant__ CUtensorMap tmChi, const __grid_constant__ CUtensorMap tmClo,
-           int kb_per_split, int kb_total, int use_alo, float* __restrict__ Q, int* err) {
+           int M, int kb_per_split, int kb_total, int use_alo, const SpecOut so, int* err) {
     using CF = Cfg<BN>;
     using C2 = Cfg2<BN>;
     constexpr int S = CF::kStages;
@@ -236,7 +245,7 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM;
     const int kb0 = blockIdx.z * kb_per_split;
-    const int nkb = max(0, min(kb_per_split, kb_total - kb0));
+    const int nkb = m0 < M ? max(0, min(kb_per_split, kb_total - kb0)) : 0;
 
     auto stage_ptr = [&](int s, int which) -> uint8_t* {
         uint8_t* base = smem + s * CF::kStage;
@@ -435,37 +444,62 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         }
     }
     __syncwarp();
-    // epilogue: D2 row c1 = mb * 128 + lane-row of this warp; write the slice of Q
-    const int slice = blockIdx.y * gridDim.z + blockIdx.z;
-    float* Qs = Q + (size_t)slice * BN * BN;
-    for (int mb = 0; mb < C2::kMB; ++mb) {
-        bool h2 = have;
+    // ---- epilogue. Every thread waits for all phase-2 MMAs (they read the shared memory
+    // that D2 is drained into); D2 row c1 = mb * 128 + the lane-row of this warp.
+    bool h2 = have;
+    for (int mb = 0; mb < C2::kMB; ++mb)
         if (h2) h2 = mbar_wait(&acc2[mb], 0, err);
-        h2 = __all_sync(0xffffffffu, h2);
-        fence_after_sync();
-        const int c1 = mb * kBM + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(C2::kAcc2 == 3 ? 0 : mb * 256);
+    h2 = __all_sync(0xffffffffu, h2);  // tcgen05.ld below is warp-collective
+    fence_after_sync();
+    // combine, in rounds over chunks of A row pairs: the rows a in [a0, a0 + A) and kw + a
+    // are drained into shared memory (row pitch kDP, columns < 2 kw), then every thread
+    // forms entries (a, b) = (D2[a][b] - D2[kw+a][kw+b], -(D2[a][kw+b] + D2[kw+a][b])) and
+    // stores them into the CTA's slice of G
+    const int kw = so.kw, E = kw * kw;
+    const int kc = (2 * kw + 15) / 16 * 16;         // drained columns (16-column chunks)
+    const int kDP = kc + 4;                           // row pitch in floats (16-byte rows)
+    const int A = min(kw, (int)(C2::kArena / (2u * 4u * (unsigned)kDP)));
+    float* Dsm = reinterpret_cast<float*>(smem);     // [2 A][kDP]
+    float2* Gs = so.G + (size_t)(blockIdx.y * gridDim.z + blockIdx.z) * E;
+    for (int a0 = 0; a0 < kw; a0 += A) {
+        const int na = min(A, kw - a0);
+        for (int mb = 0; mb < C2::kMB; ++mb) {
+            const int c1 = mb * kBM + warp * 32 + lane;
+            int r = -1;  // row of c1 in Dsm
+            if (c1 >= a0 && c1 < a0 + na) r = c1 - a0;
+            else if (c1 >= kw + a0 && c1 < kw + a0 + na) r = A + (c1 - kw - a0);
+            if (!__any_sync(0xffffffffu, r >= 0)) continue;  // warp-uniform: no TMEM traffic
+            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(C2::kAcc2 == 3 ? 0 : mb * 256);
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            if (h2) {
-                tmem_ld16(trow + (uint32_t)c, v);
-                for (int a = 1; a < C2::kAcc2; ++a) {
-                    float q[16];
-                    tmem_ld16(trow + (uint32_t)(a * BN + c), q);
+            for (int c = 0; c < kc; c += 16) {
+                float v[16];
+                if (h2) {
+                    tmem_ld16(trow + (uint32_t)c, v);
+                    for (int q = 1; q < C2::kAcc2; ++q) {
+                        float w[16];
+                        tmem_ld16(trow + (uint32_t)(q * BN + c), w);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] += q[j];
+                        for (int j = 0; j < 16; ++j) v[j] += w[j];
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
                 }
-            } else {
+                if (r >= 0) {
+                    float4* d4 = reinterpret_cast<float4*>(Dsm + r * kDP + c);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-            }
-            if (c1 < BN) {  // BN == ldk: each row of the slice is 16-float aligned
-                float4* q4 = reinterpret_cast<float4*>(Qs + (size_t)c1 * BN + c);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) q4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    for (int j = 0; j < 4; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
             }
         }
+        __syncthreads();
+        for (int e = threadIdx.x; e < na * kw; e += blockDim.x) {
+            const int i = e / kw, b = e - i * kw;
+            const float* rc = Dsm + i * kDP;          // row a = a0 + i (cos)
+            const float* rs = Dsm + (A + i) * kDP;    // row kw + a (sin)
+            Gs[(a0 + i) * kw + b] = make_float2(rc[b] - rs[kw + b], -(rc[kw + b] + rs[b]));
+        }
+        __syncthreads();
     }
     // a producer that stopped early waits (bounded) for the loads it issued
     if (warp == 0 && lane == 0 && !ok) {
@@ -764,6 +798,47 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------------------
+// Sum of the reduction's slices: out[e] = scale sum_s G[s][e], s in order. Block =
+// 32 entries (lane = entry) x kSumWarps warps; warp w adds slices w, w + kSumWarps, ...
+// (all its loads issued before the adds), then the warps' sums are added in warp order.
+// ---------------------------------------------------------------------------
+constexpr int kSumWarps = 16;
+__global__ void __launch_bounds__(32 * kSumWarps)
+k_spec_sum(const float2* __restrict__ G, int slices, int E, float scale, float2* __restrict__ out) {
+    __shared__ float2 part[kSumWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float re = 0.f, im = 0.f;
+    if (e < E) {
+        int sl = w;
+        for (; sl + 7 * kSumWarps < slices; sl += 8 * kSumWarps) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(G + (size_t)(sl + u * kSumWarps) * E + e);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                re += v[u].x;
+                im += v[u].y;
+            }
+        }
+        for (; sl < slices; sl += kSumWarps) {
+            const float2 v = __ldcg(G + (size_t)sl * E + e);
+            re += v.x;
+            im += v.y;
+        }
+    }
+    part[w][lane] = make_float2(re, im);
+    __syncthreads();
+    if (w != 0 || e >= E) return;
+    float2 t = part[0][lane];
+    for (int i = 1; i < kSumWarps; ++i) {
+        t.x += part[i][lane].x;
+        t.y += part[i][lane].y;
+    }
+    out[e] = make_float2(t.x * scale, t.y * scale);
+}
+
+// ---------------------------------------------------------------------------
 // Self-test of the bounded waits: one thread waits on an mbarrier that nothing
 // arrives on; the wait gives up after its time limit and sets *err.
 // ---------------------------------------------------------------------------
@@ -971,10 +1046,10 @@ int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, i
 
 template <int BN>
 int launch_spec2_bn(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int M, int kb_per_split,
-                    int kb_total, int splits, float* Q, int* err, cudaStream_t s) {
+                    int kb_total, int splits, SpecOut so, int* err, cudaStream_t s) {
     dim3 grid(1, (M + kBM - 1) / kBM, splits);
-    k_tc_spec2<BN><<<grid, 128, Cfg2<BN>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, *Chi, *Clo, kb_per_split,
-                                                      kb_total, op.use_alo, Q, err);
+    k_tc_spec2<BN><<<grid, 128, Cfg2<BN>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, *Chi, *Clo, M, kb_per_split,
+                                                      kb_total, op.use_alo, so, err);
     DEVEL_LAUNCH_CHECK("k_tc_spec2");
     return DEVEL_OK;
 }
@@ -986,18 +1061,22 @@ cudaError_t set_attr_spec2() {
 
 int spectrum2_slices(int M, int K, int split) { return ((M + kBM - 1) / kBM) * ((K + split - 1) / split); }
 
-int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
-                     int split, float* Q, int* err, cudaStream_t s) {
+int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int kw, int n,
+                     int M, int K, int split, float2* G, float2* out, int* err, cudaStream_t s) {
     if (K % kBK != 0 || split % kBK != 0 || split < kBK)
         return set_error(DEVEL_EINVAL, "tc spectrum: K=%d / split %d not multiples of %d", K, split, kBK);
+    if (2 * kw > BN) return set_error(DEVEL_EINVAL, "tc spectrum: window %d wider than half of %d", kw, BN);
     const int kb_total = K / kBK, kb_per_split = split / kBK;
     const int splits = (kb_total + kb_per_split - 1) / kb_per_split;
+    SpecOut so;
+    so.kw = kw;
+    so.G = G;
     prof_begin(PK_TC_SPECTRUM, s);
     int rc;
     switch (BN) {
 #define DEVEL_SPEC2_CASE(bn)                                                                               \
     case bn:                                                                                               \
-        rc = launch_spec2_bn<bn>(op, Chi, Clo, M, kb_per_split, kb_total, splits, Q, err, s);              \
+        rc = launch_spec2_bn<bn>(op, Chi, Clo, M, kb_per_split, kb_total, splits, so, err, s);             \
         break;
         DEVEL_SPEC2_CASE(16) DEVEL_SPEC2_CASE(32) DEVEL_SPEC2_CASE(48) DEVEL_SPEC2_CASE(64) DEVEL_SPEC2_CASE(80)
         DEVEL_SPEC2_CASE(96) DEVEL_SPEC2_CASE(112) DEVEL_SPEC2_CASE(128) DEVEL_SPEC2_CASE(144)
@@ -1008,7 +1087,13 @@ int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorM
             rc = set_error(DEVEL_EINVAL, "tc spectrum: unsupported window width %d", BN);
     }
     prof_end(PK_TC_SPECTRUM, s);
-    return rc;
+    if (rc) return rc;
+    const int E = kw * kw, slices = spectrum2_slices(M, K, split);
+    prof_begin(PK_SPECTRUM_REDUCE, s);
+    k_spec_sum<<<(E + 31) / 32, 32 * kSumWarps, 0, s>>>(G, slices, E, 1.0f / ((float)n * (float)n), out);
+    prof_end(PK_SPECTRUM_REDUCE, s);
+    DEVEL_LAUNCH_CHECK("k_spec_sum");
+    return DEVEL_OK;
 }
 
 int launch_wait_selftest(int* err, cudaStream_t s) {

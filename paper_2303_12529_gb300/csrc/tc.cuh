@@ -29,15 +29,16 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
 int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, int K, const EpiArgs& ep, int* err,
                       cudaStream_t s);
 
-// Both contractions of a window reduction in one kernel (k_tc_spec2): the phase-1
-// operands as in launch_gemm (A = image [M rows][K], B = basis [BN rows][K]), and
-// Chi/Clo = the same basis tables with 128-row boxes (the phase-2 A operand).
-// Writes spectrum2_slices(M, K, split) partial [BN][BN] slices to Q; BN = the window's
-// ldk, K a multiple of 64.
-// Each CTA takes 128 rows and `split` columns of the image (split a multiple of 64).
+// A window reduction (k_tc_spec2, then k_spec_sum): the phase-1 operands as in
+// launch_gemm (A = image [M rows][K], B = basis [BN rows][K]), Chi/Clo = the same basis
+// tables with 128-row boxes (the phase-2 A operand); BN = the window's ldk, kw its side,
+// K a multiple of 64. Each CTA takes 128 rows and `split` columns of the image (split a
+// multiple of 64) and stores its partial complex spectrum as one of the
+// spectrum2_slices(M, K, split) slices of G ([slices][kw * kw]); the slices are then added
+// in order: out[a][b] = n^-2 sum_p X(p) e^{-2 pi i ((a-r) y + (b-r) x) / n}.
 int spectrum2_slices(int M, int K, int split);
-int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int M, int K,
-                     int split, float* Q, int* err, cudaStream_t s);
+int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int kw, int n,
+                     int M, int K, int split, float2* G, float2* out, int* err, cudaStream_t s);
 
 // Persistent expansion D = ep.scale * A B^T (k_tc_expand), M x N output row-major in
 // ep.C with pitch ep.ldc; A [M][K] map with 128-row boxes, B [N][K] map with BN-row
