@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -29,6 +30,14 @@ int cuda_error(cudaError_t e, const char* where) {
 }
 
 int expand_parts(int n);
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("DEVEL_NO_PDL");
+        return !(v && v[0] && v[0] != '0');
+    }();
+    return on;
+}
 
 // Shared-memory opt-ins of every kernel, once per device, outside any stream capture.
 static int init_device_attrs() {

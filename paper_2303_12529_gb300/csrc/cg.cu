@@ -39,6 +39,8 @@ __device__ __forceinline__ float4 ld4_last(const float* p, long long g) {
 __global__ void __launch_bounds__(kCgThreads)
 k_cg_dots(const float* __restrict__ V, const float* __restrict__ Vp, long long npix, float* __restrict__ part,
           unsigned* counter, double* beta_out, float* beta_f, int* status) {
+    pdl_trigger();
+    pdl_wait();
     float vv = 0.f, vp = 0.f, pp = 0.f;
     const int b = blockIdx.x, nb = gridDim.x;
     if ((npix & 3) == 0) {
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(kCgThreads)
 k_cg_update(const float* __restrict__ V, float* __restrict__ Vp, float* __restrict__ D, long long npix,
             const float* __restrict__ beta_f, float* __restrict__ vpart, unsigned* counter, double* vmax,
             int* status) {
+    pdl_trigger();
+    pdl_wait();
     const float beta = beta_f ? *beta_f : 0.f;
     const int b = blockIdx.x, nb = gridDim.x;
     // max of |D| as the integer max of its bit pattern: a NaN (pattern above +Inf)
@@ -209,17 +213,19 @@ int launch_cg_direction(int n, const float* V, float* Vp, float* D, bool restart
     const int nb = cg_parts(n);
     if (!restart) {
         prof_begin(PK_CG_DOTS, s);
-        k_cg_dots<<<nb, kCgThreads, 0, s>>>(V, Vp, npix, part, counters, beta_out, beta_f, status);
+        cudaError_t e = launch_pdl(k_cg_dots, dim3(nb), dim3(kCgThreads), 0, s, V, (const float*)Vp, npix, part,
+                                   counters, beta_out, beta_f, status);
         prof_end(PK_CG_DOTS, s);
-        DEVEL_LAUNCH_CHECK("k_cg_dots");
+        if (e != cudaSuccess) return cuda_error(e, "k_cg_dots");
     } else if (beta_out) {
         DEVEL_CUDA_TRY(cudaMemsetAsync(beta_out, 0, sizeof(double), s));
     }
     prof_begin(PK_CG_UPDATE, s);
-    k_cg_update<<<nb, kCgThreads, 0, s>>>(V, Vp, D, npix, restart ? nullptr : beta_f, vpart, counters + 1, vmax,
-                                          status);
+    cudaError_t e = launch_pdl(k_cg_update, dim3(nb), dim3(kCgThreads), 0, s, V, Vp, D, npix,
+                               restart ? (const float*)nullptr : (const float*)beta_f, vpart, counters + 1, vmax,
+                               status);
     prof_end(PK_CG_UPDATE, s);
-    DEVEL_LAUNCH_CHECK("k_cg_update");
+    if (e != cudaSuccess) return cuda_error(e, "k_cg_update");
     return DEVEL_OK;
 }
 

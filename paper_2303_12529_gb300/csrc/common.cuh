@@ -30,6 +30,42 @@ int cuda_error(cudaError_t e, const char* where);
         if (_e != cudaSuccess) return ::devel::cuda_error(_e, where); \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// programmatic dependent launch
+// ---------------------------------------------------------------------------
+// The kernels of the solve loop are launched with programmatic stream serialization: a
+// kernel may be scheduled while the previous kernel on its stream is still running, so
+// that its launch and prologue (barrier set-up, TMEM allocation, loads of the constant
+// DFT and TCC tables) overlap that kernel's tail. Every such kernel
+//   - calls pdl_trigger() as it starts (its dependents may then be scheduled once all of
+//     its CTAs are resident), and
+//   - calls pdl_wait() before it reads anything the previous kernel writes and before it
+//     writes global memory; pdl_wait() returns once the previous kernel has completed and
+//     its writes are visible. Since each kernel completes only after its own wait, that
+//     covers every earlier kernel of the stream too.
+// Both are no-ops for a kernel launched without the attribute. DEVEL_NO_PDL=1 in the
+// environment launches every kernel with plain stream serialization.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+bool pdl_enabled();
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 // kernel classes of the optional event profiler (prof.cu)
 enum ProfKind {
     PK_SPECTRUM = 0, PK_SPECTRUM_REDUCE, PK_SOCS_Y, PK_HOPKINS, PK_ADJ_WINDOW,

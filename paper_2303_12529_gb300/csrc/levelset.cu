@@ -71,6 +71,8 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
     const int y0 = blockIdx.y * kRows;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kPX;
     __shared__ float s_inv;
+    pdl_trigger();
+    pdl_wait();
     if (threadIdx.x == 0) {  // 1 / max|V| once per block (the FP64 pipe is narrow)
         const double vm = *vmax;
         s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
@@ -230,6 +232,8 @@ k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
                      __nv_bfloat16* __restrict__ mask_bf, int ldb) {
     __shared__ float t[kWTY][kWTX + 1];
     __shared__ float s_inv;
+    pdl_trigger();
+    pdl_wait();
     const int x0 = blockIdx.x * kWX, y0 = blockIdx.y * kWY;
     const int tid = threadIdx.y * kWX + threadIdx.x;
     if (tid == 0) {  // 1 / max|V| once per block (FP64 operand)
@@ -283,18 +287,19 @@ int launch_levelset_step(int n, const float* phi, const float* V, const double* 
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s, int upwind) {
     if (upwind == DEVEL_UPWIND_WENO5) {
         prof_begin(PK_STEP, s);
-        k_levelset_step_weno<<<dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY), dim3(kWX, kWTh), 0, s>>>(
-            phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf, ldb);
+        cudaError_t e = launch_pdl(k_levelset_step_weno, dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY),
+                                   dim3(kWX, kWTh), 0, s, phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
+                                   ldb);
         prof_end(PK_STEP, s);
-        DEVEL_LAUNCH_CHECK("k_levelset_step_weno");
+        if (e != cudaSuccess) return cuda_error(e, "k_levelset_step_weno");
         return DEVEL_OK;
     }
     dim3 grid((n + 256 * kPX - 1) / (256 * kPX), (n + kRows - 1) / kRows);
     prof_begin(PK_STEP, s);
-    k_levelset_step<<<grid, 256, 0, s>>>(phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
-                                                    ldb);
+    cudaError_t e = launch_pdl(k_levelset_step, grid, dim3(256), 0, s, phi, V, vmax, m, dt, lambda, n, phi_out,
+                               mask_out, mask_bf, ldb);
     prof_end(PK_STEP, s);
-    DEVEL_LAUNCH_CHECK("k_levelset_step");
+    if (e != cudaSuccess) return cuda_error(e, "k_levelset_step");
     return DEVEL_OK;
 }
 

@@ -55,6 +55,9 @@ __device__ __forceinline__ float2 warp_sum2(float2 v) {
     return v;
 }
 
+// L2 prefetch of the 128-byte line holding p
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(unsigned char v) { return v ? 1.f : 0.f; }
 
@@ -73,6 +76,8 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, 
     __shared__ float As[gBK][gBM + 4];
     __shared__ float Bs[gBK][gBN + 4];
     __shared__ float red[kThreads / 32];
+    pdl_trigger();
+    pdl_wait();
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * gBM, n0 = blockIdx.x * gBN;
     const int kb = blockIdx.z * kchunk;
@@ -161,6 +166,8 @@ k_gemm_nt(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, 
 
 // P = sum_z Ppart[z] over the split-K slices of stage 1, elementwise in slice order.
 __global__ void k_sum_slices(const float* __restrict__ Ppart, int nz, size_t len, float* __restrict__ P) {
+    pdl_trigger();
+    pdl_wait();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         float v = 0.f;
@@ -178,6 +185,8 @@ constexpr int kFinUnroll = 8;
 __global__ void __launch_bounds__(32 * kFinWarps)
 k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, float2* __restrict__ out) {
     __shared__ float2 part[kFinWarps][32];
+    pdl_trigger();
+    pdl_wait();
     const int a = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b = blockIdx.y * 32 + lane;
     float re = 0.f, im = 0.f;
@@ -218,7 +227,7 @@ k_spec_final(const float* __restrict__ Q, int nq, int ldq, int kw, float scale, 
 void launch_spec_final(const float* Q, int nq, int ldq, int kw, float2* out, int n, cudaStream_t s) {
     const float scale = 1.0f / ((float)n * (float)n);
     prof_begin(PK_SPECTRUM_REDUCE, s);
-    k_spec_final<<<dim3(kw, (kw + 31) / 32), 32 * kFinWarps, 0, s>>>(Q, nq, ldq, kw, scale, out);
+    launch_pdl(k_spec_final, dim3(kw, (kw + 31) / 32), dim3(32 * kFinWarps), 0, s, Q, nq, ldq, kw, scale, out);
     prof_end(PK_SPECTRUM_REDUCE, s);
 }
 
@@ -267,6 +276,10 @@ k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
     const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
     const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
     const float2* T = Tdiff + goff[g];
+    // the TCC entries (constant) into L2 while the previous kernel finishes
+    pdl_trigger();
+    for (int i = threadIdx.x * 16; i < total; i += blockDim.x * 16) prefetch_l2(T + i);
+    pdl_wait();
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int t = threadIdx.x; t < total; t += 128) {
@@ -297,6 +310,12 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
     const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
     const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
     const float2* row = TCC + (size_t)f * kk;
+    pdl_trigger();
+    for (int i = threadIdx.x * 16; i < kk; i += blockDim.x * 16) {
+        prefetch_l2(row + i);
+        if (TCC2) prefetch_l2(TCC2 + (size_t)f * kk + i);
+    }
+    pdl_wait();
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int a = threadIdx.x; a < kk; a += 128) {
@@ -325,6 +344,8 @@ k_expand_T(const float2* __restrict__ Z, const float* __restrict__ basisT, int n
            float* __restrict__ Af) {
     extern __shared__ float2 zs[];  // [kw * kw] Z, then [kTRows][ldk] floats of basisT
     float* gs = reinterpret_cast<float*>(zs + kw * kw);
+    pdl_trigger();
+    pdl_wait();
     const int y0 = blockIdx.x * kTRows;
     // stage Z with batches of independent loads in flight (latency, not bandwidth, bound)
     {
@@ -388,9 +409,10 @@ int gemm_nt(const TA* A, int lda, const TB* B, int ldb, int M, int N, int K, int
     const int kchunk = ((K + splits - 1) / splits + gBK - 1) / gBK * gBK;
     dim3 grid((N + gBN - 1) / gBN, (M + gBM - 1) / gBM, splits);
     prof_begin(kind, s);
-    k_gemm_nt<TA, TB, EPI, BN_MAJOR><<<grid, kThreads, 0, s>>>(A, lda, B, ldb, M, N, K, kchunk, ep);
+    cudaError_t e = launch_pdl(k_gemm_nt<TA, TB, EPI, BN_MAJOR>, grid, dim3(kThreads), 0, s, A, lda, B, ldb, M, N, K,
+                               kchunk, ep);
     prof_end(kind, s);
-    DEVEL_LAUNCH_CHECK(what);
+    if (e != cudaSuccess) return cuda_error(e, what);
     return DEVEL_OK;
 }
 
@@ -416,9 +438,10 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
     const Workspace& ws = o->ws;
     const size_t len = (size_t)n * w.ldk;
     prof_begin(PK_SPECTRUM_STAGE2, s);
-    k_sum_slices<<<(int)std::min<size_t>((len + 255) / 256, 4 * 148), 256, 0, s>>>(ws.Ppart, o->nsplit, len, ws.P);
+    cudaError_t e = launch_pdl(k_sum_slices, dim3((unsigned)std::min<size_t>((len + 255) / 256, 4 * 148)), dim3(256), 0,
+                               s, (const float*)ws.Ppart, o->nsplit, len, ws.P);
     prof_end(PK_SPECTRUM_STAGE2, s);
-    DEVEL_LAUNCH_CHECK("k_sum_slices");
+    if (e != cudaSuccess) return cuda_error(e, "k_sum_slices");
     EpiArgs ep;
     ep.C = ws.Q;
     ep.ldc = w.ldk;
@@ -478,22 +501,23 @@ int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_HOPKINS, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    k_ihat_tcc<<<(o->k2 * o->k2 + 1) / 2, 128, 0, s>>>(o->Tdiff, o->goff, o->ws.mhat, o->k, o->ws.Ihat,
-                                                        tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr,
-                                                        o->W2.ldk);
+    cudaError_t e = launch_pdl(k_ihat_tcc, dim3((o->k2 * o->k2 + 1) / 2), dim3(128), 0, s, (const float2*)o->Tdiff,
+                               (const int*)o->goff, (const float2*)o->ws.mhat, o->k, o->ws.Ihat,
+                               tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr, o->W2.ldk);
     prof_end(PK_HOPKINS, s);
-    DEVEL_LAUNCH_CHECK("k_ihat_tcc");
+    if (e != cudaSuccess) return cuda_error(e, "k_ihat_tcc");
     return DEVEL_OK;
 }
 
 int launch_shat(const devel_optics* o, cudaStream_t s, const devel_optics* od) {
     prof_begin(PK_ADJ_WINDOW, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    k_shat_tcc<<<o->k * o->k, 128, 0, s>>>(o->TCC, o->ws.mhat, o->ws.rhat, o->k, o->ws.Shat,
-                                            tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk,
-                                            od ? od->TCC : nullptr, od ? od->ws.rhat : nullptr);
+    cudaError_t e = launch_pdl(k_shat_tcc, dim3(o->k * o->k), dim3(128), 0, s, (const float2*)o->TCC,
+                               (const float2*)o->ws.mhat, (const float2*)o->ws.rhat, o->k, o->ws.Shat,
+                               tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk,
+                               od ? (const float2*)od->TCC : nullptr, od ? (const float2*)od->ws.rhat : nullptr);
     prof_end(PK_ADJ_WINDOW, s);
-    DEVEL_LAUNCH_CHECK("k_shat_tcc");
+    if (e != cudaSuccess) return cuda_error(e, "k_shat_tcc");
     return DEVEL_OK;
 }
 
@@ -525,10 +549,11 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
         return tc::launch_expand(op, bn, epi, n, n, w.ldk, ep, o->tc_err, s);
     }
     prof_begin(PK_EXPAND_T, s);
-    k_expand_T<<<(n + kTRows - 1) / kTRows, 256, sizeof(float2) * w.kw * w.kw + sizeof(float) * kTRows * w.ldk, s>>>(
-        Z, w.basisT, n, w.kw, w.ldk, ws.Acat);
+    cudaError_t e = launch_pdl(k_expand_T, dim3((n + kTRows - 1) / kTRows), dim3(256),
+                               sizeof(float2) * w.kw * w.kw + sizeof(float) * kTRows * w.ldk, s, Z,
+                               (const float*)w.basisT, n, w.kw, w.ldk, ws.Acat);
     prof_end(PK_EXPAND_T, s);
-    DEVEL_LAUNCH_CHECK("k_expand_T");
+    if (e != cudaSuccess) return cuda_error(e, "k_expand_T");
     if (nparts) *nparts = expand_parts(n);
     if (epi == EPI_VEL)
         return gemm_nt<float, float, EPI_VEL>(ws.Acat, w.ldk, w.basisT, w.ldk, n, n, w.ldk, 1, ep, PK_EXPAND_GEMM,

@@ -38,6 +38,8 @@ constexpr int kNoPos = INT_MAX;
 __global__ void __launch_bounds__(kCX * kSegs)
 k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g) {
     __shared__ int sc[2][4][kSegs][kCX];  // [buffer][last0, last1, first0, first1][segment][column]
+    pdl_trigger();
+    pdl_wait();
     const int cx = threadIdx.x, sg = threadIdx.y;
     const int x = blockIdx.x * kCX + cx;
     const int L = (n + kSegs - 1) / kSegs;
@@ -131,6 +133,8 @@ __global__ void __launch_bounds__(256)
 k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g,
            float* __restrict__ phi, float d_lo, float d_hi) {
     extern __shared__ int sfx[];
+    pdl_trigger();
+    pdl_wait();
     const int nb = edt_nb(n), npad = nb * kBlk;
     // per class c: f at c npad, then the block minima, eL and eR at 2 npad + (0 / 2 / 4 + c) nb
     int* const F = sfx;
@@ -231,13 +235,15 @@ int reinit_init_attrs() {
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                   cudaStream_t s) {
     prof_begin(PK_EDT_COLS, s);
-    k_edt_cols<<<(n + kCX - 1) / kCX, dim3(kCX, kSegs), 0, s>>>(mask, n, reinterpret_cast<unsigned*>(d2));
+    cudaError_t e = launch_pdl(k_edt_cols, dim3((n + kCX - 1) / kCX), dim3(kCX, kSegs), 0, s, mask, n,
+                               reinterpret_cast<unsigned*>(d2));
     prof_end(PK_EDT_COLS, s);
-    DEVEL_LAUNCH_CHECK("k_edt_cols");
+    if (e != cudaSuccess) return cuda_error(e, "k_edt_cols");
     prof_begin(PK_EDT_ROWS, s);
-    k_edt_rows<<<n, 256, edt_rows_smem(n), s>>>(mask, n, reinterpret_cast<unsigned*>(d2), phi, d_lo, d_hi);
+    e = launch_pdl(k_edt_rows, dim3(n), dim3(256), edt_rows_smem(n), s, mask, n, reinterpret_cast<unsigned*>(d2), phi,
+                   d_lo, d_hi);
     prof_end(PK_EDT_ROWS, s);
-    DEVEL_LAUNCH_CHECK("k_edt_rows");
+    if (e != cudaSuccess) return cuda_error(e, "k_edt_rows");
     return DEVEL_OK;
 }
 

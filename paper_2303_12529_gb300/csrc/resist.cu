@@ -150,6 +150,8 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
          long long* __restrict__ qpart, long long* __restrict__ lpart, ResistOut out) {
     __shared__ float sf[3][32];
     __shared__ int si[2][32];
+    pdl_trigger();
+    pdl_wait();
     LossAcc acc;
     const long long npix = (long long)n * n;
     // logical block lb of nlb, thread tid of its 256
@@ -272,13 +274,12 @@ static int resist_grid(int n, int per_sm) {
 int resist_parts(int n) { return resist_grid(n, resist_blocks_per_sm<false>()); }
 
 template <bool kDef, typename... A>
-static void launch_resist_kernel(int n, int nparts, bool alone, cudaStream_t s, A... args) {
+static cudaError_t launch_resist_kernel(int n, int nparts, bool alone, cudaStream_t s, A... args) {
     constexpr int per_sm = resist_blocks_per_sm<kDef>();
     const int nlb = std::min(nparts, resist_grid(n, per_sm));
     if (alone && nlb % per_sm == 0)
-        k_resist<kDef, per_sm><<<nlb / per_sm, kThreads * per_sm, 0, s>>>(args...);
-    else
-        k_resist<kDef, 1><<<nlb, kThreads, 0, s>>>(args...);
+        return launch_pdl(k_resist<kDef, per_sm>, dim3(nlb / per_sm), dim3(kThreads * per_sm), 0, s, args...);
+    return launch_pdl(k_resist<kDef, 1>, dim3(nlb), dim3(kThreads), 0, s, args...);
 }
 
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
@@ -288,11 +289,12 @@ int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_re
                   bool alone) {
     ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
     prof_begin(PK_RESIST, s);
-    launch_resist_kernel<false>(n, nparts, alone, s, I, (const float*)nullptr, Zt, n, make_resist_args(p), R,
-                                (float*)nullptr, Rhi, Rlo, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, ldr,
-                                qpart, lpart, out);
+    cudaError_t e = launch_resist_kernel<false>(n, nparts, alone, s, I, (const float*)nullptr, Zt, n,
+                                                make_resist_args(p), R, (float*)nullptr, Rhi, Rlo,
+                                                (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, ldr, qpart, lpart,
+                                                out);
     prof_end(PK_RESIST, s);
-    DEVEL_LAUNCH_CHECK("k_resist");
+    if (e != cudaSuccess) return cuda_error(e, "k_resist");
     return DEVEL_OK;
 }
 
@@ -304,10 +306,10 @@ int launch_resist_defocus(int n, const float* In, const float* Id, const unsigne
                           bool alone) {
     ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
     prof_begin(PK_RESIST, s);
-    launch_resist_kernel<true>(n, nparts, alone, s, In, Id, Zt, n, make_resist_args(p), Rn, Rd, Rnhi, Rnlo, Rdhi,
-                               Rdlo, ldr, qpart, lpart, out);
+    cudaError_t e = launch_resist_kernel<true>(n, nparts, alone, s, In, Id, Zt, n, make_resist_args(p), Rn, Rd,
+                                               Rnhi, Rnlo, Rdhi, Rdlo, ldr, qpart, lpart, out);
     prof_end(PK_RESIST, s);
-    DEVEL_LAUNCH_CHECK("k_resist_defocus");
+    if (e != cudaSuccess) return cuda_error(e, "k_resist_defocus");
     return DEVEL_OK;
 }
 

@@ -68,6 +68,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     const int kb0 = blockIdx.z * kb_per_split;
     const int nkb = max(0, min(kb_per_split, kb_total - kb0));
 
+    auto stage_ptr = [&](int s, int which) -> uint8_t* {
+        // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
+        uint8_t* base = smem + s * CF::kStage;
+        return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
+    };
+    const uint32_t bytes = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
+    pdl_trigger();
+    int issued = 0;  // producer: slabs whose loads were issued
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -75,6 +83,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
         mbar_init(accum, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // A (a DFT table, constant) of the first stages before the previous kernel has
+        // finished; B (its output) after the wait
+        const int npre = min(nkb, S);
+        for (int i = 0; i < npre; ++i) {
+            mbar_arrive_expect_tx(&full[i], bytes);
+            tma_load_2d(&tmAhi, &full[i], stage_ptr(i, 0), (kb0 + i) * kBK, m0);
+            if (use_alo) tma_load_2d(&tmAlo, &full[i], stage_ptr(i, 1), (kb0 + i) * kBK, m0);
+        }
+        pdl_wait();
+        for (int i = 0; i < npre; ++i) {
+            tma_load_2d(&tmBhi, &full[i], stage_ptr(i, 2), (kb0 + i) * kBK, n0);
+            tma_load_2d(&tmBlo, &full[i], stage_ptr(i, 3), (kb0 + i) * kBK, n0);
+        }
+        issued = npre;
     }
     if (warp == 1) tmem_alloc(tmem_slot, CF::kCols);
     fence_before_sync();
@@ -82,17 +104,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    auto stage_ptr = [&](int s, int which) -> uint8_t* {
-        // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
-        uint8_t* base = smem + s * CF::kStage;
-        return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
-    };
-
-    int issued = 0;  // producer: slabs whose loads were issued
     bool ok = true;
     if (warp == 0 && lane == 0 && nkb > 0) {
-        const uint32_t bytes = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
-        for (int i = 0; i < nkb; ++i) {
+        for (int i = issued; i < nkb; ++i) {
             const int s = i % S;
             if (i >= S && !mbar_wait(&empty[s], ((i / S) - 1) & 1, err)) {
                 ok = false;
@@ -252,6 +266,7 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         return which < 2 ? base + which * kABytes : base + 2 * kABytes + (which - 2) * CF::kBBytes;
     };
     const uint32_t bytes1 = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
+    pdl_trigger();
     auto issue1 = [&](int i) {
         const int s = i % S;
         mbar_arrive_expect_tx(&full[s], bytes1);
@@ -276,7 +291,20 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             mbar_init(&acc2[i], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (; issued < nkb && issued < S; ++issued) issue1(issued);
+        // B (the DFT table, constant) of the first stages before the previous kernel has
+        // finished; A (the image it wrote) after the wait
+        const int npre = min(nkb, S);
+        for (int i = 0; i < npre; ++i) {
+            mbar_arrive_expect_tx(&full[i], bytes1);
+            tma_load_2d(&tmBhi, &full[i], stage_ptr(i, 2), (kb0 + i) * kBK, 0);
+            tma_load_2d(&tmBlo, &full[i], stage_ptr(i, 3), (kb0 + i) * kBK, 0);
+        }
+        pdl_wait();
+        for (int i = 0; i < npre; ++i) {
+            tma_load_2d(&tmAhi, &full[i], stage_ptr(i, 0), (kb0 + i) * kBK, m0);
+            if (use_alo) tma_load_2d(&tmAlo, &full[i], stage_ptr(i, 1), (kb0 + i) * kBK, m0);
+        }
+        issued = npre;
     }
     if (warp == 1) tmem_alloc(tmem_slot, C2::kCols);
     fence_before_sync();
@@ -619,6 +647,7 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
         }
     };
 
+    pdl_trigger();
     if (producer) {
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
@@ -632,6 +661,7 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        pdl_wait();  // the A operand is the previous kernel's output; outputs follow from it
         produce(true);
     }
     if (warp == 5) tmem_alloc(tmem_slot, CX::kCols);
@@ -806,6 +836,8 @@ constexpr int kSumWarps = 16;
 __global__ void __launch_bounds__(32 * kSumWarps)
 k_spec_sum(const float2* __restrict__ G, int slices, int E, float scale, float2* __restrict__ out) {
     __shared__ float2 part[kSumWarps][32];
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
     float re = 0.f, im = 0.f;
@@ -894,9 +926,9 @@ int launch_gemm_bn(const Operands& op, int M, int N, int kb_per_split, int kb_to
                    const EpiArgs& ep, int* err, cudaStream_t s) {
     using CF = Cfg<BN>;
     dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
-    k_tc_gemm<BN><<<grid, 128, CF::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N, kb_per_split, kb_total,
-                                                ksteps_last, op.use_alo, ep, err);
-    DEVEL_LAUNCH_CHECK("k_tc_gemm");
+    cudaError_t e = launch_pdl(k_tc_gemm<BN>, grid, dim3(128), CF::kSmem, s, *op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N,
+                               kb_per_split, kb_total, ksteps_last, op.use_alo, ep, err);
+    if (e != cudaSuccess) return cuda_error(e, "k_tc_gemm");
     return DEVEL_OK;
 }
 
@@ -979,10 +1011,10 @@ static int launch_expand_cfg(const Operands& op, int M, int N, int ksteps_last, 
     const int tiles_n = (N + BN - 1) / BN;
     const int tiles = ((M + kBM - 1) / kBM) * tiles_n;
     const int grid = std::min(tiles, sm_count());
-    k_tc_expand<BN, KB, EPI><<<grid, 192, CfgX<BN, KB>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, tmC,
-                                                                    tma_store ? 1 : 0, M, N, ksteps_last, tiles_n,
-                                                                    tiles, ep, err);
-    DEVEL_LAUNCH_CHECK("k_tc_expand");
+    cudaError_t e = launch_pdl(k_tc_expand<BN, KB, EPI>, dim3(grid), dim3(192), CfgX<BN, KB>::kSmem, s, *op.Ahi,
+                               *op.Alo, *op.Bhi, *op.Blo, tmC, tma_store ? 1 : 0, M, N, ksteps_last, tiles_n, tiles,
+                               ep, err);
+    if (e != cudaSuccess) return cuda_error(e, "k_tc_expand");
     return DEVEL_OK;
 }
 
@@ -1048,9 +1080,9 @@ template <int BN>
 int launch_spec2_bn(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int M, int kb_per_split,
                     int kb_total, int splits, SpecOut so, int* err, cudaStream_t s) {
     dim3 grid(1, (M + kBM - 1) / kBM, splits);
-    k_tc_spec2<BN><<<grid, 128, Cfg2<BN>::kSmem, s>>>(*op.Ahi, *op.Alo, *op.Bhi, *op.Blo, *Chi, *Clo, M, kb_per_split,
-                                                      kb_total, op.use_alo, so, err);
-    DEVEL_LAUNCH_CHECK("k_tc_spec2");
+    cudaError_t e = launch_pdl(k_tc_spec2<BN>, grid, dim3(128), Cfg2<BN>::kSmem, s, *op.Ahi, *op.Alo, *op.Bhi,
+                               *op.Blo, *Chi, *Clo, M, kb_per_split, kb_total, op.use_alo, so, err);
+    if (e != cudaSuccess) return cuda_error(e, "k_tc_spec2");
     return DEVEL_OK;
 }
 
@@ -1090,9 +1122,10 @@ int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorM
     if (rc) return rc;
     const int E = kw * kw, slices = spectrum2_slices(M, K, split);
     prof_begin(PK_SPECTRUM_REDUCE, s);
-    k_spec_sum<<<(E + 31) / 32, 32 * kSumWarps, 0, s>>>(G, slices, E, 1.0f / ((float)n * (float)n), out);
+    cudaError_t e = launch_pdl(k_spec_sum, dim3((E + 31) / 32), dim3(32 * kSumWarps), 0, s, (const float2*)G, slices,
+                               E, 1.0f / ((float)n * (float)n), out);
     prof_end(PK_SPECTRUM_REDUCE, s);
-    DEVEL_LAUNCH_CHECK("k_spec_sum");
+    if (e != cudaSuccess) return cuda_error(e, "k_spec_sum");
     return DEVEL_OK;
 }
 
