@@ -460,9 +460,10 @@ int devel_ilt_solve(const devel_ilt_params* params, int nclips, const devel_clip
 int devel_profile_start(int capacity);
 /*
  * Wait for the events recorded so far and add their launch counts and times
- * to the per-kernel totals. With kernel-by-kernel launches call it once before
- * devel_profile_stop; a solve captured into a CUDA graph while the profile is
- * open records its events on every replay, so call it after each replay.
+ * to the per-kernel totals. Events of kernel-by-kernel launches are counted
+ * once (their slots are released); a solve captured into a CUDA graph while
+ * the profile is open records its events on every replay, so call it after
+ * each replay (both kinds may be mixed).
  */
 int devel_profile_collect(void);
 /* Close the profile (the totals stay readable). */

@@ -71,7 +71,8 @@ enum ProfKind {
     PK_SPECTRUM = 0, PK_SPECTRUM_REDUCE, PK_SOCS_Y, PK_HOPKINS, PK_ADJ_WINDOW,
     PK_EXPAND_T, PK_EXPAND_GEMM, PK_VMAX, PK_RESIST, PK_RESIST_FINAL,
     PK_STEP, PK_MASK, PK_EDT_COLS, PK_EDT_ROWS, PK_U8F32,
-    PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PK_CG_DOTS, PK_CG_UPDATE, PROF_NKINDS
+    PK_TC_EXPAND, PK_TC_SPECTRUM, PK_SPECTRUM_STAGE2, PK_TC_SPLIT, PK_CG_DOTS, PK_CG_UPDATE,
+    PK_DSN_CONV, PK_DSN_MISC, PK_RESAMPLE, PROF_NKINDS
 };
 bool prof_on();
 unsigned prof_generation();

@@ -603,6 +603,9 @@ struct devel_dsn {
     size_t nparams = 0;
     float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
     int t = 0;  // Adam steps taken
+    // the tensor-core weight layouts (Wm, Wtm) no longer match P: rebuilt by the next pass
+    // (set when the parameters change: init, set_params, every Adam step)
+    bool wm_stale = true;
     // activations (bf16) and their gradients (fp32): index by name below
     struct Act {
         int C, side;
@@ -655,8 +658,10 @@ int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
                                             (int)kMSmem));
         attr = true;
     }
+    prof_begin(PK_DSN_CONV, s);
     k_conv3_mma<__nv_bfloat16, true><<<grid, 256, kMSmem, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y,
                                                                cv.cout, nullptr, 0, side, side, cv.cout);
+    prof_end(PK_DSN_CONV, s);
     DEVEL_LAUNCH_CHECK("k_conv3_mma");
     return DEVEL_OK;
 }
@@ -688,6 +693,8 @@ int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
 }
 
 int prep_weights(devel_dsn* d, cudaStream_t s) {
+    if (!d->wm_stale) return DEVEL_OK;
+    prof_begin(PK_DSN_MISC, s);
     for (auto& cv : d->convs) {
         if (cv.k != 3) continue;
         const size_t wm = (size_t)((cv.cin + 15) / 16) * 9 * cv.coutp * 16;
@@ -695,7 +702,9 @@ int prep_weights(devel_dsn* d, cudaStream_t s) {
         const size_t wt = (size_t)((cv.cout + 15) / 16) * 9 * cv.cinp * 16;
         k_prep_wm<true><<<grid1(wt), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.cinp, cv.Wtm);
     }
+    prof_end(PK_DSN_MISC, s);
     DEVEL_LAUNCH_CHECK("k_prep_wm");
+    d->wm_stale = false;
     return DEVEL_OK;
 }
 
@@ -709,8 +718,10 @@ int forward(devel_dsn* d, int nb, cudaStream_t s) {
     for (int lv = 1; lv < 4 && !rc; ++lv) {
         const int side = S >> lv;
         const size_t planes = (size_t)nb * w[lv - 1];
+        prof_begin(PK_DSN_MISC, s);
         k_avgpool<<<grid1(planes * side * side), 256, 0, s>>>(A[pin[lv - 1]].a, 2 * side, 2 * side, planes,
                                                             A[pout[lv - 1]].a);
+        prof_end(PK_DSN_MISC, s);
         rc = conv_fwd(d, 2 * lv, nb, A[pout[lv - 1]].a, w[lv - 1], nullptr, 0, side, A[aa[lv - 1]].a, s);
         if (!rc) rc = conv_fwd(d, 2 * lv + 1, nb, A[aa[lv - 1]].a, w[lv], nullptr, 0, side, A[ss[lv - 1]].a, s);
     }
@@ -720,15 +731,19 @@ int forward(devel_dsn* d, int nb, cudaStream_t s) {
     for (int j = 0; j < 3 && !rc; ++j) {
         const int lv = 2 - j, side = S >> lv;
         const size_t planes = (size_t)nb * w[lv + 1];
+        prof_begin(PK_DSN_MISC, s);
         k_upsample<<<grid1(planes * side * side), 256, 0, s>>>(A[prev].a, side / 2, side / 2, planes, A[up[j]].a);
+        prof_end(PK_DSN_MISC, s);
         rc = conv_fwd(d, 8 + 2 * j, nb, A[up[j]].a, w[lv + 1], A[skip[j]].a, w[lv], side, A[da[j]].a, s);
         if (!rc) rc = conv_fwd(d, 9 + 2 * j, nb, A[da[j]].a, w[lv], nullptr, 0, side, A[dd[j]].a, s);
         prev = dd[j];
     }
     if (rc) return rc;
     const auto& h = d->convs[14];
+    prof_begin(PK_DSN_MISC, s);
     k_head<<<grid1((size_t)nb * S * S), 256, 0, s>>>(d->x, A[D0].a, d->P + h.w_off, d->P + h.b_off, c, nb,
                                                      (size_t)S * S, d->y);
+    prof_end(PK_DSN_MISC, s);
     DEVEL_LAUNCH_CHECK("dsn forward");
     return DEVEL_OK;
 }
@@ -890,6 +905,7 @@ int devel_dsn_set_params(devel_dsn* d, const float* host) {
     DEVEL_CUDA_TRY(cudaMemset(d->M, 0, sizeof(float) * d->nparams));
     DEVEL_CUDA_TRY(cudaMemset(d->V, 0, sizeof(float) * d->nparams));
     d->t = 0;
+    d->wm_stale = true;
     return DEVEL_OK;
 }
 
@@ -932,10 +948,14 @@ int devel_dsn_forward(devel_dsn* d, int nb, const float* tsdf, float B, float* p
     const size_t px = (size_t)nb * d->S * d->S;
     int rc = prep_weights(d, s);
     if (rc) return rc;
+    prof_begin(PK_DSN_MISC, s);
     k_band<<<grid1(px), 256, 0, s>>>(tsdf, px, B, d->x, d->xb);
+    prof_end(PK_DSN_MISC, s);
     rc = forward(d, nb, s);
     if (rc) return rc;
+    prof_begin(PK_DSN_MISC, s);
     k_scale<<<grid1(px), 256, 0, s>>>(d->y, px, B, phi0);
+    prof_end(PK_DSN_MISC, s);
     DEVEL_LAUNCH_CHECK("devel_dsn_forward");
     return DEVEL_OK;
 }
@@ -1015,6 +1035,7 @@ int dsn_train(devel_dsn* d, int nb, const float* tsdf, const float* phi_gt, floa
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)d->t), c2 = 1.f - std::pow(b2, (float)d->t);
     k_adam<<<grid1(d->nparams), 256, 0, s>>>(d->P, d->G, d->M, d->V, d->nparams, lr, b1, b2, 1e-8f, c1, c2);
+    d->wm_stale = true;
     DEVEL_LAUNCH_CHECK("devel_dsn_train_step");
     return DEVEL_OK;
 }
@@ -1050,7 +1071,9 @@ int devel_phi_downsample(int n, int f, int nb, const float* fine, float* coarse,
     const int rc = resample_args("devel_phi_downsample", n, f, nb, fine, coarse);
     if (rc || nb == 0) return rc;
     const size_t count = (size_t)nb * (n / f) * (n / f);
+    prof_begin(PK_RESAMPLE, s);
     k_phi_down<<<grid1(count), 256, 0, s>>>(fine, n, f, count, (float)(1.0 / ((double)f * f * f)), coarse);
+    prof_end(PK_RESAMPLE, s);
     DEVEL_LAUNCH_CHECK("devel_phi_downsample");
     return DEVEL_OK;
 }
@@ -1059,7 +1082,9 @@ int devel_phi_upsample(int n, int f, int nb, const float* coarse, float* fine, c
     const int rc = resample_args("devel_phi_upsample", n, f, nb, coarse, fine);
     if (rc || nb == 0) return rc;
     const size_t count = (size_t)nb * n * n;
+    prof_begin(PK_RESAMPLE, s);
     k_phi_up<<<grid1(count), 256, 0, s>>>(coarse, n, f, count, fine);
+    prof_end(PK_RESAMPLE, s);
     DEVEL_LAUNCH_CHECK("devel_phi_upsample");
     return DEVEL_OK;
 }

@@ -6,6 +6,7 @@
 // device time. Off by default; when off the cost is one branch per launch.
 // devel_profile_select limits the events to some kernel classes (fewer events
 // disturb the timed kernels less).
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -18,12 +19,13 @@ static const char* kNames[PROF_NKINDS] = {
     "expand_T",      "expand_gemm",     "vmax_final", "resist",    "resist_final",
     "levelset_step", "mask_from_phi",   "edt_cols",   "edt_rows",  "u8_to_f32",
     "tc_expand",     "tc_spectrum",     "spectrum_stage2", "tc_split",  "cg_dots",
-    "cg_update",
+    "cg_update",     "dsn_conv",        "dsn_misc",   "phi_resample",
 };
 
 struct Slot {
     int kind;
     cudaEvent_t a, b;
+    bool captured;  // recorded into a captured graph (re-timestamped by every replay)
 };
 
 static bool g_on = false;
@@ -39,6 +41,20 @@ static unsigned long long g_select = ~0ull;  // kernel classes that get events
 bool prof_on() { return g_on; }
 unsigned prof_generation() { return g_generation; }
 
+// Inside a stream capture an external record becomes an event-record node that
+// timestamps the event on every replay (not a capture-internal dependency); outside a
+// capture a plain record (the external flag is only valid while capturing).
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+static void record(cudaEvent_t e, cudaStream_t s) {
+    if (capturing(s))
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 void prof_begin(int kind, cudaStream_t s) {
     if (!g_on || !((g_select >> kind) & 1ull)) return;
     if (g_used >= g_pool.size()) {
@@ -47,15 +63,14 @@ void prof_begin(int kind, cudaStream_t s) {
         return;
     }
     g_pool[g_used].kind = kind;
-    // external record: inside a stream capture this becomes an event-record node
-    // that timestamps the event on every replay (not a capture-internal dependency)
-    cudaEventRecordWithFlags(g_pool[g_used].a, s, cudaEventRecordExternal);
+    g_pool[g_used].captured = capturing(s);
+    record(g_pool[g_used].a, s);
     g_open_kind = kind;
 }
 
 void prof_end(int kind, cudaStream_t s) {
     if (!g_on || g_open_kind != kind) return;
-    cudaEventRecordWithFlags(g_pool[g_used].b, s, cudaEventRecordExternal);
+    record(g_pool[g_used].b, s);
     ++g_used;
     g_open_kind = -1;
 }
@@ -78,7 +93,7 @@ int devel_profile_start(int capacity) {
     if (g_on) return set_error(DEVEL_EINVAL, "devel_profile_start: a profile is already open");
     if ((int)g_pool.size() < capacity) {
         for (size_t i = g_pool.size(); i < (size_t)capacity; ++i) {
-            Slot sl{0, nullptr, nullptr};
+            Slot sl{0, nullptr, nullptr, false};
             DEVEL_CUDA_TRY(cudaEventCreate(&sl.a));
             DEVEL_CUDA_TRY(cudaEventCreate(&sl.b));
             g_pool.push_back(sl);
@@ -101,6 +116,12 @@ int devel_profile_collect(void) {
         g_launches[g_pool[i].kind] += 1;
         g_ms[g_pool[i].kind] += ms;
     }
+    // events of direct launches are counted once: their slots go back to the pool, while
+    // the slots of captured graphs stay (every replay records into them again)
+    std::stable_partition(g_pool.begin(), g_pool.begin() + (long)g_used, [](const Slot& sl) { return sl.captured; });
+    size_t kept = 0;
+    while (kept < g_used && g_pool[kept].captured) ++kept;
+    g_used = kept;
     if (g_overflow) return set_error(DEVEL_EINVAL, "devel_profile_collect: capacity exceeded, profile truncated");
     return DEVEL_OK;
 }
