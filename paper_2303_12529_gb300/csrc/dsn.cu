@@ -19,10 +19,12 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "conv_tc.cuh"
 #include "tc_ptx.cuh"
 
 struct devel_dsn;
@@ -598,6 +600,10 @@ struct devel_dsn {
         __nv_bfloat16* Wm = nullptr;   // tensor-core layout of the forward weights
         __nv_bfloat16* Wtm = nullptr;  // ... of the input-gradient (transposed, mirrored) weights
         int coutp = 0, cinp = 0;
+        int side = 0;                  // plane side of the layer's output
+        // tcgen05 forward path (conv_tc.cu), when the layer's shape allows it
+        __nv_bfloat16* Wtc = nullptr;  // weights [ceil(Cin / 64)][9][Cout][64]
+        CUtensorMap mWtc;
     };
     std::vector<Conv> convs;
     size_t nparams = 0;
@@ -634,6 +640,7 @@ void free_dsn(devel_dsn* d) {
     for (auto& cv : d->convs) {
         cudaFree(cv.Wm);
         cudaFree(cv.Wtm);
+        if (cv.Wtc) cudaFree(cv.Wtc);
     }
     for (auto& a : d->acts) {
         cudaFree(a.a);
@@ -648,6 +655,12 @@ void free_dsn(devel_dsn* d) {
 int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
              __nv_bfloat16* Y, cudaStream_t s) {
     const auto& cv = d->convs[ci];
+    if (cv.Wtc && side == cv.side) {
+        prof_begin(PK_DSN_CONV, s);
+        const int rc = launch_conv3_tc(XA, CA, XB, CB, cv.mWtc, d->P + cv.b_off, Y, cv.cout, nb, side, s);
+        prof_end(PK_DSN_CONV, s);
+        return rc;
+    }
     const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
     dim3 grid(mtiles, cv.coutp / kMCo, nb);
     static bool attr = false;
@@ -697,6 +710,10 @@ int prep_weights(devel_dsn* d, cudaStream_t s) {
     prof_begin(PK_DSN_MISC, s);
     for (auto& cv : d->convs) {
         if (cv.k != 3) continue;
+        if (cv.Wtc) {
+            const int rc = launch_prep_wtc(d->P + cv.w_off, cv.cout, cv.cin, cv.Wtc, s);
+            if (rc) return rc;
+        }
         const size_t wm = (size_t)((cv.cin + 15) / 16) * 9 * cv.coutp * 16;
         k_prep_wm<false><<<grid1(wm), 256, 0, s>>>(d->P + cv.w_off, cv.cout, cv.cin, cv.coutp, cv.Wm);
         const size_t wt = (size_t)((cv.cout + 15) / 16) * 9 * cv.cinp * 16;
@@ -842,6 +859,20 @@ int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
         d->convs.push_back(cv);
     }
     d->nparams = off;
+    // the plane side of each 3 x 3 layer (encoder levels 0-3, decoder levels 2, 1, 0) and,
+    // where the tcgen05 kernel takes the layer, its weight layout and TMA map
+    // (DEVEL_DSN_NO_TC=1 in the environment keeps every layer on the warp-level kernel)
+    const char* no_tc = std::getenv("DEVEL_DSN_NO_TC");
+    const bool use_tc = !(no_tc && no_tc[0] && no_tc[0] != '0');
+    if (use_tc && e == cudaSuccess && conv3_tc_init_attrs() != DEVEL_OK) e = cudaErrorUnknown;
+    for (size_t i = 0; i < d->convs.size() && e == cudaSuccess; ++i) {
+        auto& cv = d->convs[i];
+        if (cv.k != 3) continue;
+        cv.side = i < 8 ? S >> (i / 2) : S >> (2 - (int)(i - 8) / 2);
+        if (!use_tc || !conv3_tc_supported(cv.cin, cv.cout, cv.side)) continue;
+        e = cudaMalloc(&cv.Wtc, sizeof(__nv_bfloat16) * conv3_tc_weight_elems(cv.cin, cv.cout));
+        if (e == cudaSuccess && conv3_tc_make_map(&cv.mWtc, cv.Wtc, cv.cin, cv.cout) != DEVEL_OK) e = cudaErrorUnknown;
+    }
     // activations: (channels, side) by id
     const int spec[NACT][2] = {{w[0], S},      {w[0], S},      {w[0], S / 2},  {w[1], S / 2}, {w[1], S / 2},
                                {w[1], S / 4},  {w[2], S / 4},  {w[2], S / 4},  {w[2], S / 8}, {w[3], S / 8},
