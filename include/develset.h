@@ -346,6 +346,29 @@ int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const flo
                                 cudaStream_t stream);
 
 /*
+ * The label search of the modulation branch (Sec. III-B) in one call: the candidate
+ * maps m_out[j] = H(phi_gt + dh[j]) (as devel_modulation_candidates), a DSO solve of
+ * every candidate with clip.m = m_out[j] from the TSDF of the target (the candidates are
+ * the clips of one devel_ilt_solve, candidate j on handles[j], so distinct handles run
+ * concurrently), and the index of the smallest final L_DSO (ties: the first; a non-finite
+ * loss never wins) written to *best_dev. Everything is enqueued on `stream`; nothing is
+ * read back. The solves' status word (as devel_ilt_solve's) goes to *status_dev.
+ *   params    the solve's parameters (params->iters >= 0)
+ *   handles   host array of ncand handles of side n (distinct handles run concurrently)
+ *   target    device uint8[n*n]          phi_gt  device float[n*n]
+ *   dh_host   host float[ncand], finite  1 <= ncand <= DEVEL_MOD_MAX_CANDIDATES
+ *   m_out     device float[ncand][n*n]   the candidate maps (written)
+ *   phi_work  device float[ncand][n*n]   the candidates' level sets (written)
+ *   loss_hist device double[ncand][ldh]  per-candidate L_DSO history (iters + 1 entries
+ *             per row); ldh >= iters + 1, even (16-byte rows)
+ *   best_dev  device int[1]              status_dev device int[1]
+ */
+int devel_modulation_search(const devel_ilt_params* params, int ncand, devel_optics* const* handles,
+                            const unsigned char* target, const float* phi_gt, const float* dh_host, float* m_out,
+                            float* phi_work, double* loss_hist, int ldh, int* best_dev, int* status_dev,
+                            cudaStream_t stream);
+
+/*
  * Loss of the modulation branch against its label (Sec. III-B) with the approximated
  * Heaviside H_eps(phi) = (1 + (2/pi) atan(phi / eps)) / 2 (the paper: eps = 0.03):
  *   loss_out[0] = sum_p (H_eps(phi_m[p]) - m_gt[p])^2

@@ -90,6 +90,8 @@ _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
 _sig("devel_modulation_candidates", [_I, _P, _I, _P, _P, _P])
 _sig("devel_ahf_loss", [_P, _P, _P, _F, _P, _P, _P])
+_sig("devel_modulation_search", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(_P), _P, _P, _P, _P, _P, _P,
+                                 _I, _P, _P, _P])
 _sig("devel_shot_count", [_I, _P, ctypes.POINTER(ctypes.c_longlong)])
 _sig("devel_dsn_create", [_I, _I, _I, ctypes.POINTER(_P)])
 _sig("devel_dsn_destroy", [_P])
@@ -128,7 +130,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_modulation_candidates", "devel_ahf_loss", "devel_shot_count", "devel_dsn_create", "devel_dsn_destroy",
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
             "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
-            "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample")
+            "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample", "devel_modulation_search")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -305,28 +307,34 @@ def devel_ahf_loss(optics: Optics, phi_m, m_gt, eps: float, loss_out, grad_out=N
 
 
 def modulation_search(handles, target, phi_gt, dh, params: "devel_ilt_params", stream=None):
-    """The label search of Sec. III-B: candidate maps H(phi_gt + dh_j), one DSO solve per
-    candidate (the candidates are the clips of one devel_ilt_solve; handle j serves
-    candidate j, so distinct handles run concurrently), and the index of the smallest
-    final L_DSO (ties: the first). Returns (index, final losses as a host array,
-    candidate maps [len(dh), n*n])."""
-    import numpy as np
+    """The label search of Sec. III-B through devel_modulation_search (candidate maps
+    H(phi_gt + dh_j), one DSO solve per candidate on handle j, the device argmin of the
+    final L_DSO). Returns (index, final losses as a host array, candidate maps
+    [len(dh), n*n])."""
     import torch
     n = handles[0].n
     N = n * n
     dev = target.device
-    cands = torch.empty(len(dh) * N, dtype=torch.float32, device=dev)
-    devel_modulation_candidates(n, phi_gt, dh, cands, stream)
+    J = len(dh)
+    cands = torch.empty(J * N, dtype=torch.float32, device=dev)
+    phi_work = torch.empty(J * N, dtype=torch.float32, device=dev)
     H = params.iters + 1
-    hist = torch.zeros(len(dh), (H + 1) // 2 * 2, dtype=torch.float64, device=dev)  # rows 16-byte aligned
-    clips = [Clip(handles[j], target, torch.empty(N, dtype=torch.float32, device=dev), m=cands[j * N:(j + 1) * N],
-                  loss_hist=hist[j, :H]) for j in range(len(dh))]
+    ldh = (H + 1) // 2 * 2                                   # rows 16-byte aligned
+    hist = torch.zeros(J, ldh, dtype=torch.float64, device=dev)
+    best = torch.zeros(1, dtype=torch.int32, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
-    devel_ilt_solve(params, clips, st, stream)
-    final = hist[:, H - 1].cpu().numpy()   # the only device-to-host read: len(dh) doubles
+    harr = (_P * J)(*[h.handle for h in handles])
+    dh_host = (ctypes.c_float * J)(*[float(d) for d in dh])
+    _check(_lib.devel_modulation_search(ctypes.byref(params), J, harr, _ptr(target, torch.uint8, N, "target"),
+                                        _ptr(phi_gt, torch.float32, N, "phi_gt"), ctypes.cast(dh_host, _P),
+                                        _ptr(cands, torch.float32, J * N, "m_out"),
+                                        _ptr(phi_work, torch.float32, J * N, "phi_work"),
+                                        _ptr(hist, torch.float64, J * ldh, "loss_hist"), ldh,
+                                        _ptr(best, torch.int32, 1, "best"), _ptr(st, torch.int32, 1, "status"),
+                                        _stream(stream)))
     if int(st.item()) != 0:
         raise DevelError(int(st.item()), "modulation_search: a candidate solve reported a non-finite loss")
-    return int(np.argmin(final)), final, cands.view(len(dh), N)
+    return int(best.item()), hist[:, H - 1].cpu().numpy(), cands.view(J, N)
 
 
 def devel_shot_count(mask) -> int:

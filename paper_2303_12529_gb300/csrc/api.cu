@@ -881,6 +881,51 @@ int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const flo
     return launch_mod_candidates(n, phi_gt, ncand, dh_host, m_out, s);
 }
 
+int devel_modulation_search(const devel_ilt_params* p, int ncand, devel_optics* const* handles,
+                            const unsigned char* target, const float* phi_gt, const float* dh_host, float* m_out,
+                            float* phi_work, double* loss_hist, int ldh, int* best_dev, int* status_dev,
+                            cudaStream_t s) {
+    if (!p) return set_error(DEVEL_EINVAL, "devel_modulation_search: params is NULL");
+    if (ncand < 1 || ncand > DEVEL_MOD_MAX_CANDIDATES)
+        return set_error(DEVEL_EINVAL, "devel_modulation_search: ncand=%d outside [1, %d]", ncand,
+                         DEVEL_MOD_MAX_CANDIDATES);
+    if (!handles || !handles[0]) return set_error(DEVEL_EINVAL, "devel_modulation_search: handles is NULL");
+    const int n = handles[0]->n;
+    for (int j = 1; j < ncand; ++j)
+        if (!handles[j] || handles[j]->n != n)
+            return set_error(DEVEL_EINVAL, "devel_modulation_search: handle %d missing or of another size", j);
+    if (p->iters < 0 || ldh < p->iters + 1 || (ldh & 1))
+        return set_error(DEVEL_EINVAL, "devel_modulation_search: ldh=%d must be even and >= iters + 1", ldh);
+    CHECK_PTR(target, "target");
+    CHECK_PTR(phi_gt, "phi_gt");
+    CHECK_PTR(m_out, "m_out");
+    CHECK_PTR(phi_work, "phi_work");
+    CHECK_PTR(loss_hist, "loss_hist");
+    CHECK_PTR(best_dev, "best_dev");
+    CHECK_PTR(status_dev, "status_dev");
+    if (!dh_host) return set_error(DEVEL_EINVAL, "devel_modulation_search: dh_host is NULL");
+    for (int j = 0; j < ncand; ++j)
+        if (!std::isfinite(dh_host[j]))
+            return set_error(DEVEL_EINVAL, "devel_modulation_search: dh[%d] is not finite", j);
+    int rc = launch_mod_candidates(n, phi_gt, ncand, dh_host, m_out, s);
+    if (rc) return rc;
+    const size_t N = (size_t)n * n;
+    std::vector<devel_clip> clips(ncand);
+    for (int j = 0; j < ncand; ++j) {
+        devel_clip& c = clips[j];
+        std::memset(&c, 0, sizeof(c));
+        c.optics = handles[j];
+        c.target = target;
+        c.phi = phi_work + (size_t)j * N;
+        c.phi_given = 0;
+        c.m = m_out + (size_t)j * N;
+        c.loss_hist = loss_hist + (size_t)j * ldh;
+    }
+    rc = devel_ilt_solve(p, ncand, clips.data(), status_dev, s);
+    if (rc) return rc;
+    return launch_argmin_final(loss_hist, ncand, ldh, p->iters, best_dev, s);
+}
+
 int devel_ahf_loss(const devel_optics* o, const float* phi_m, const float* m_gt, float eps, double* loss_out,
                    float* grad_out, cudaStream_t s) {
     if (!o) return set_error(DEVEL_EINVAL, "devel_ahf_loss: optics is NULL");

@@ -305,6 +305,8 @@ int launch_resist_defocus(int n, const float* In, const float* Id, const unsigne
 // modulation.cu: candidate maps H(phi + dh_j) (m: float[ncand][n*n]); AHF loss (qpart:
 // long long[>= nparts], counter: one zeroed word, loss: device double).
 int launch_mod_candidates(int n, const float* phi, int ncand, const float* dh_host, float* m, cudaStream_t s);
+// *best = argmin_j hist[j * ldh + col] over finite entries (ties: the first)
+int launch_argmin_final(const double* hist, int ncand, int ldh, int col, int* best, cudaStream_t s);
 int launch_ahf_loss(int n, const float* phi, const float* mgt, float eps, float* grad, long long* qpart, int nparts,
                     unsigned* counter, double* loss, cudaStream_t s);
 // cg.cu: D = V + beta D (PR+ beta from V, Vp; restart: D = V), Vp = V, max|D| -> vmax.

@@ -5,8 +5,10 @@
 //   k_ahf_loss        L_m = sum (H_eps(phi_m) - m_gt)^2 with the approximated
 //                     Heaviside H_eps(phi) = (1 + (2/pi) atan(phi/eps)) / 2, and
 //                     dL_m/dphi_m = 2 (H_eps - m_gt) (eps/pi) / (eps^2 + phi^2).
-// The label search itself (a DSO solve per candidate, argmin of the final L_DSO) runs
-// the candidates as clips of one devel_ilt_solve.
+// The label search itself (devel_modulation_search) runs the candidates as clips of one
+// devel_ilt_solve, then
+//   k_argmin_final    the index of the smallest final L_DSO (ties: the first; a
+//                     non-finite loss never wins).
 #include <algorithm>
 
 #include "common.cuh"
@@ -114,7 +116,37 @@ k_ahf_loss(const float* __restrict__ phi, const float* __restrict__ mgt, long lo
     *counter = 0u;
 }
 
+// One warp: lane j reads candidates j, j + 32, ...; a candidate wins over another with a
+// strictly smaller finite loss, or with an equal loss and a smaller index.
+__global__ void k_argmin_final(const double* __restrict__ hist, int ncand, int ldh, int col, int* best) {
+    const int lane = threadIdx.x;
+    double v = 0.0;
+    int i = -1;
+    for (int j = lane; j < ncand; j += 32) {
+        const double x = hist[(size_t)j * ldh + col];
+        if (isfinite(x) && (i < 0 || x < v)) {
+            v = x;
+            i = j;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_down_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+        if (i2 >= 0 && (i < 0 || v2 < v || (v2 == v && i2 < i))) {
+            v = v2;
+            i = i2;
+        }
+    }
+    if (lane == 0) *best = i < 0 ? 0 : i;
+}
+
 }  // namespace
+
+int launch_argmin_final(const double* hist, int ncand, int ldh, int col, int* best, cudaStream_t s) {
+    k_argmin_final<<<1, 32, 0, s>>>(hist, ncand, ldh, col, best);
+    DEVEL_LAUNCH_CHECK("k_argmin_final");
+    return DEVEL_OK;
+}
 
 int launch_mod_candidates(int n, const float* phi, int ncand, const float* dh_host, float* m, cudaStream_t s) {
     Shifts sh{};

@@ -43,6 +43,20 @@ def test_binding_covers_the_header(lib):
     assert dv.devel_version() >> 16 == 1
 
 
+def test_modulation_search_checks_its_arguments(lib):
+    """devel_modulation_search refuses a missing parameter block, a candidate count
+    outside [1, DEVEL_MOD_MAX_CANDIDATES] and a missing handle list before any launch."""
+    import paper_2303_12529_gb300 as dv
+    f = dv._lib.devel_modulation_search
+    P = dv.ilt_params(iters=3)
+    null = (dv._P * 1)(None)
+    assert f(None, 1, null, None, None, None, None, None, None, 4, None, None, None) == dv.DEVEL_EINVAL
+    for ncand in (0, dv.DEVEL_MOD_MAX_CANDIDATES + 1):
+        rc = f(ctypes.byref(P), ncand, null, None, None, None, None, None, None, 4, None, None, None)
+        assert rc == dv.DEVEL_EINVAL and "ncand" in dv.devel_last_error()
+    assert f(ctypes.byref(P), 1, null, None, None, None, None, None, None, 4, None, None, None) == dv.DEVEL_EINVAL
+
+
 def test_binding_constants_match_the_header():
     """The binding's copies of the header's limits and codes are the header's values."""
     import paper_2303_12529_gb300 as dv

@@ -68,6 +68,7 @@ def test_label_search_matches_oracle():
     # each candidate's final L_DSO within 1% of the oracle's; the chosen label is the
     # oracle's best or within 1% of it
     assert np.all(np.abs(final - rfinal) <= 0.01 * np.abs(rfinal))
+    assert best == int(np.argmin(final))            # the device argmin (ties: the first)
     assert rfinal[best] <= 1.01 * min(rfinal)
     assert np.array_equal(host(cands).reshape(len(dh), n, n)[rbest], rcands[rbest].astype(np.float32)) or \
         np.count_nonzero(host(cands).reshape(len(dh), n, n)[rbest] != rcands[rbest]) <= 2
