@@ -72,6 +72,9 @@ L2_BYTES = 129 * 1024 * 1024
 # kernels, from the ncu captures summarised under profiles/; a kernel changed since its
 # capture has no entry.
 TRAFFIC = {
+    # profiles/kernels_manhattan2048_bf16x3.md ("DRAM traffic inside the solve"): k_tc_spec2,
+    # the mean of the mask launch (9.47 MB) and the dL/dI launch (18.91 MB)
+    ("tc_spectrum", "bf16x3"): 14.19e6,
 }
 
 
@@ -1579,11 +1582,11 @@ def run_calls_once(args, wl):
     if "headline" in wl:
         wl = WORKLOADS["manhattan2048"]
     if "learned" in wl:
-        n, B = wl["n"], wl["dsn_batch"]
+        n, B = wl["n"] // wl.get("f", 1), wl["dsn_batch"]   # the network's grid
         d2 = torch.empty(n * n, dtype=torch.int32, device="cuda")
         tsdf = torch.empty(B, n * n, dtype=torch.float32, device="cuda")
         for i in range(B):
-            tgt = torch.from_numpy(synth.rect_clip(wl["seed_train"] + i).ravel().copy()).cuda()
+            tgt = torch.from_numpy(synth.rect_clip(wl["seed_train"] + i, n=n).ravel().copy()).cuda()
             dv.devel_reinit_sdf(n, tgt, tsdf[i], d2)
         net = dv.Dsn(n, B, wl["width"], seed=1)
         phi0 = torch.empty_like(tsdf)

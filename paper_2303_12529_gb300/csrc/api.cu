@@ -263,6 +263,16 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
 // parallel branches when captured into a graph). Chains go longest first to the
 // branch with the least work so far (work ~ n^2 per clip).
 constexpr int kBranches = 16;
+// Concurrent branches of a batch: kBranches, or DEVEL_MAX_BRANCHES (1 .. kBranches) from
+// the environment.
+static int branch_limit() {
+    static const int lim = [] {
+        const char* v = std::getenv("DEVEL_MAX_BRANCHES");
+        const int b = v ? std::atoi(v) : 0;
+        return b >= 1 && b <= kBranches ? b : kBranches;
+    }();
+    return lim;
+}
 struct BranchPool {
     cudaStream_t st[kBranches] = {};
     cudaEvent_t fork = nullptr, join[kBranches] = {};
@@ -307,7 +317,7 @@ static int enqueue_solve(const devel_ilt_params* p, int nclips, const devel_clip
         }
         return DEVEL_OK;
     }
-    const int nb = (int)std::min<size_t>(chains.size(), kBranches);
+    const int nb = (int)std::min<size_t>(chains.size(), (size_t)branch_limit());
     std::vector<double> cost(chains.size(), 0.0), load(nb, 0.0);
     std::vector<int> order(chains.size());
     for (size_t h = 0; h < chains.size(); ++h) {

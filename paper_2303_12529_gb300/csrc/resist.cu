@@ -131,15 +131,16 @@ __device__ __forceinline__ Px4<kDef> load4(const float* In, const float* Id, con
     return v;
 }
 
+// hi = rn_bf16(r), lo = rn_bf16(r - hi) for four values, two per packed conversion
 __device__ __forceinline__ void split_store4(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t q, const float (&r)[4]) {
-    __nv_bfloat16 h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        h[j] = __float2bfloat16_rn(r[j]);
-        l[j] = __float2bfloat16_rn(r[j] - __bfloat162float(h[j]));
-    }
-    *reinterpret_cast<uint2*>(hi + q) = *reinterpret_cast<const uint2*>(h);
-    *reinterpret_cast<uint2*>(lo + q) = *reinterpret_cast<const uint2*>(l);
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(r[0], r[1]), h23 = __floats2bfloat162_rn(r[2], r[3]);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(r[0] - f01.x, r[1] - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(r[2] - f23.x, r[3] - f23.y);
+    *reinterpret_cast<uint2*>(hi + q) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    *reinterpret_cast<uint2*>(lo + q) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
 }
 
 template <bool kDef, int LB>

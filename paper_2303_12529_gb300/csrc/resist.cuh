@@ -50,25 +50,36 @@ __device__ __forceinline__ float min_nan(float a, float b) {
     return r;
 }
 
-// One corner: e = 2^u (u capped so that e stays finite), Z = 1 / (1 + e) and the
-// slope Z (1 - Z) = e Z^2 (no cancellation near Z = 1).
+// One corner: e = 2^u, Z = 1 / (1 + e) and the slope Z (1 - Z) = e Z^2 (no
+// cancellation near Z = 1).
 struct Corner {
     float z, ez2;
 };
-__device__ __forceinline__ Corner resist_corner(float I, float a, float b) {
-    const float u = fmaf(a, I, b);
-    const float e = sfu_exp2(min_nan(u, 126.f));  // a NaN image stays NaN
-    const float z = sfu_rcp(1.f + e);
-    return Corner{z, e * z * z};
+
+// The three corners of one pixel with one reciprocal: with q_c = 1 + e_c and
+// r = 1 / (q_1 q_2 q_3), Z_1 = q_2 q_3 r and so on. u is capped at 40 (a NaN stays NaN),
+// so the product stays below 2^121; where the cap applies Z is below 2^-40 and its
+// absolute error is too.
+__device__ __forceinline__ void resist_corners(float I1, float I2, float I3, float a1, float a2, float a3, float b,
+                                               Corner& c1, Corner& c2, Corner& c3) {
+    const float e1 = sfu_exp2(min_nan(fmaf(a1, I1, b), 40.f));
+    const float e2 = sfu_exp2(min_nan(fmaf(a2, I2, b), 40.f));
+    const float e3 = sfu_exp2(min_nan(fmaf(a3, I3, b), 40.f));
+    const float q1 = 1.f + e1, q2 = 1.f + e2, q3 = 1.f + e3;
+    const float q23 = q2 * q3;
+    const float r = sfu_rcp(q1 * q23);
+    const float z1 = q23 * r, z2 = (q1 * q3) * r, z3 = (q1 * q2) * r;
+    c1 = Corner{z1, e1 * z1 * z1};
+    c2 = Corner{z2, e2 * z2 * z2};
+    c3 = Corner{z3, e3 * z3 * z3};
 }
 
 // Z_c = sigmoid(sigma_z (d_c^2 I - I_th)) at nominal / inner / outer dose;
 // returns dL/dI = sum_c coef_c 2 (Z_c - Z_t) sigma_z Z_c (1 - Z_c) d_c^2.
 __device__ __forceinline__ float resist_px(float I, bool zt_on, const ResistArgs& p, LossAcc& a) {
     const float zt = zt_on ? 1.f : 0.f;
-    const Corner cn = resist_corner(I, p.a_nom, p.b);
-    const Corner ci = resist_corner(I, p.a_in, p.b);
-    const Corner co = resist_corner(I, p.a_out, p.b);
+    Corner cn, ci, co;
+    resist_corners(I, I, I, p.a_nom, p.a_in, p.a_out, p.b, cn, ci, co);
     const float en = cn.z - zt, ei = ci.z - zt, eo = co.z - zt;
     a.s0 = fmaf(en, en, a.s0);
     a.s1 = fmaf(ei, ei, a.s1);
@@ -86,9 +97,8 @@ __device__ __forceinline__ float resist_px(float I, bool zt_on, const ResistArgs
 __device__ __forceinline__ float resist_px2(float In, float Id, bool zt_on, const ResistArgs& p, LossAcc& a,
                                             float& gD) {
     const float zt = zt_on ? 1.f : 0.f;
-    const Corner cn = resist_corner(In, p.a_nom, p.b);
-    const Corner ci = resist_corner(Id, p.a_in, p.b);
-    const Corner co = resist_corner(In, p.a_out, p.b);
+    Corner cn, ci, co;
+    resist_corners(In, Id, In, p.a_nom, p.a_in, p.a_out, p.b, cn, ci, co);
     const float en = cn.z - zt, ei = ci.z - zt, eo = co.z - zt;
     a.s0 = fmaf(en, en, a.s0);
     a.s1 = fmaf(ei, ei, a.s1);
