@@ -17,6 +17,7 @@
  *   devel_phi_downsample, devel_phi_upsample   level sets between a clip's grid and the DSN's
  *   devel_shot_count      Sec. II-C.3 mask fracturing shot count (host)
  *   devel_ilt_solve       Sec. III-A / III-C: the whole loop for a batch of clips
+ *   devel_ilt_solve_batch the same loop with each stage launched once over all clips
  *
  * Conventions shared by every call
  * --------------------------------
@@ -467,6 +468,36 @@ int devel_phi_upsample(int n, int f, int nb, const float* coarse, float* fine, c
  */
 int devel_ilt_solve(const devel_ilt_params* params, int nclips, const devel_clip* clips,
                     int* status_dev, cudaStream_t stream);
+
+/*
+ * Batched solve (Sec. III-A / III-C, the loop of devel_ilt_solve): up to `capacity`
+ * clips on one compensated-BF16 optics handle, every stage of every iteration launched
+ * once over all clips of the call (the reduction, Hopkins sums, expansions, resist,
+ * level-set step and re-initialisation each take the clip as one more grid dimension),
+ * so each launch moves the whole batch's data. Results per clip equal devel_ilt_solve's
+ * up to FP32 rounding (the same arithmetic per clip; only the resist kernel's CTA shape
+ * and the reduction's partial-spectrum order may differ).
+ * devel_batch_create: the batch's workspace for `capacity` clips of the handle's n (about
+ * 90 MB per clip at n = 2048); the handle must be DEVEL_PREC_BF16X3 and must outlive the
+ * batch; its tables are shared, not copied. DEVEL_EINVAL for a bad argument, DEVEL_ENOMEM.
+ * devel_ilt_solve_batch: nclips in [0, capacity]; arrays hold clip c at c times the
+ * per-clip size:
+ *   target     device uint8 [nclips][n*n]       phi   device float [nclips][n*n], in/out
+ *   phi_given  0: phi_0 = TSDF(target)           m     device float [nclips][n*n] or NULL
+ *   mask_out   device uint8 [nclips][n*n] or NULL
+ *   loss_hist, l2_hist, pvb_hist  device [nclips][ldh] or NULL (ldh >= iters + 1)
+ *   status_dev device int[1], as devel_ilt_solve's
+ * params: the steepest-descent optimizer, either upwind scheme; DEVEL_EINVAL otherwise.
+ * With use_graph the first call with an argument set is captured and later calls replay
+ * it. Calls on one batch must not run concurrently.
+ */
+typedef struct devel_batch devel_batch;
+int devel_batch_create(const devel_optics* optics, int capacity, devel_batch** out);
+int devel_batch_destroy(devel_batch* batch);
+int devel_ilt_solve_batch(const devel_ilt_params* params, devel_batch* batch, int nclips,
+                          const unsigned char* target, float* phi, int phi_given, const float* m,
+                          unsigned char* mask_out, double* loss_hist, long long* l2_hist, long long* pvb_hist,
+                          int ldh, int* status_dev, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Optional kernel timing (tracing)                                          */

@@ -105,6 +105,10 @@ _sig("devel_dsn_train_step", [_P, _I, _P, _P, _F, _F, _P, _P])
 _sig("devel_dsn_forward_ahf", [_P, _I, _P, _F, _F, _P, _P])
 _sig("devel_dsn_train_step_ahf", [_P, _I, _P, _P, _F, _F, _F, _P, _P])
 _sig("devel_ilt_solve", [ctypes.POINTER(devel_ilt_params), _I, ctypes.POINTER(devel_clip), _P, _P])
+_sig("devel_batch_create", [_P, _I, ctypes.POINTER(_P)])
+_sig("devel_batch_destroy", [_P])
+_sig("devel_ilt_solve_batch", [ctypes.POINTER(devel_ilt_params), _P, _I, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P,
+                               _P])
 _sig("devel_phi_downsample", [_I, _I, _I, _P, _P, _P])
 _sig("devel_phi_upsample", [_I, _I, _I, _P, _P, _P])
 
@@ -130,7 +134,8 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_modulation_candidates", "devel_ahf_loss", "devel_shot_count", "devel_dsn_create", "devel_dsn_destroy",
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
             "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
-            "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample", "devel_modulation_search")
+            "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample", "devel_modulation_search",
+            "devel_batch_create", "devel_batch_destroy", "devel_ilt_solve_batch")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -492,6 +497,50 @@ def devel_ilt_solve(params: devel_ilt_params, clips, status, stream=None):
                             c.optics_defocus.handle if c.optics_defocus is not None else None)
     _check(_lib.devel_ilt_solve(ctypes.byref(params), len(clips), arr, _ptr(status, torch.int32, 1, "status"),
                                 _stream(stream)))
+
+
+class Batch:
+    """Owner of a ``devel_batch*``: the workspace of up to ``capacity`` clips on one
+    compensated-BF16 optics handle (kept alive by this object)."""
+
+    def __init__(self, optics: Optics, capacity: int):
+        out = _P()
+        _check(_lib.devel_batch_create(optics.handle, int(capacity), ctypes.byref(out)))
+        self.handle = out.value
+        self.optics = optics
+        self.capacity = int(capacity)
+
+    def close(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(_lib.devel_batch_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def devel_ilt_solve_batch(params: devel_ilt_params, batch: Batch, target, phi, status, phi_given: bool = False,
+                          m=None, mask_out=None, loss_hist=None, l2_hist=None, pvb_hist=None, stream=None):
+    """The solve of ``nclips = target.shape[0]`` clips with every stage launched once over
+    the batch. target uint8 [nclips, n*n]; phi float32 [nclips, n*n] in/out; m float32
+    [nclips, n*n] or None; mask_out uint8 [nclips, n*n] or None; histories [nclips, ldh]
+    (float64 / int64 / int64, ldh >= iters + 1) or None; status int32 [1]."""
+    import torch
+    B = int(target.shape[0]) if target.dim() == 2 else 1
+    N = batch.optics.n * batch.optics.n
+    hists = [h for h in (loss_hist, l2_hist, pvb_hist) if h is not None]
+    ldh = int(hists[0].shape[-1]) if hists else 0
+    _check(_lib.devel_ilt_solve_batch(ctypes.byref(params), batch.handle, B, _ptr(target, torch.uint8, B * N, "target"),
+                                      _ptr(phi, torch.float32, B * N, "phi"), int(bool(phi_given)),
+                                      _ptr(m, torch.float32, B * N, "m"),
+                                      _ptr(mask_out, torch.uint8, B * N, "mask_out"),
+                                      _ptr(loss_hist, torch.float64, B * ldh, "loss_hist"),
+                                      _ptr(l2_hist, torch.int64, B * ldh, "l2_hist"),
+                                      _ptr(pvb_hist, torch.int64, B * ldh, "pvb_hist"), ldh,
+                                      _ptr(status, torch.int32, 1, "status"), _stream(stream)))
 
 
 def devel_profile_start(capacity: int = 1 << 16):

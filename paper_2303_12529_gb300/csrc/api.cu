@@ -94,8 +94,8 @@ int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, c
 }
 
 // adjoint from ws.mhat (spectrum of the imaged mask) and the spectrum rhat of R
-static int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s,
-                             const devel_optics* od = nullptr) {
+int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s,
+                      const devel_optics* od) {
     int rc = launch_shat(o, s, od);
     if (rc) return rc;
     EpiArgs ep;
@@ -127,7 +127,7 @@ static void free_optics(devel_optics* o) {
     if (!o) return;
     void* ptrs[] = {o->W.basis, o->W.basisT, o->W2.basis, o->W2.basisT, o->TCC, o->Tdiff, o->goff,
                     o->ws.Ppart, o->ws.P, o->ws.Q, o->ws.mhat, o->ws.Ihat, o->ws.rhat, o->ws.Shat,
-                    o->ws.Acat, o->ws.qpart, o->ws.lpart, o->ws.vpart, o->ws.bufI, o->ws.bufV, o->ws.phi2,
+                    o->ws.Acat, o->ws.qpart, o->ws.lpart, o->ws.vpart, o->ws.vbits, o->ws.bufI, o->ws.bufV, o->ws.phi2,
                     o->ws.M, o->ws.d2, o->ws.vmax, o->ws.loss4, o->ws.cnt2,
                     o->ws.cgpart, o->ws.cgvpart, o->ws.cgbeta, o->ws.cg_vmax, o->ws.cgV, o->ws.cgD,
                     o->tcW.basis_hi, o->tcW.basis_lo, o->tcW.basisT_hi, o->tcW.basisT_lo,
@@ -159,6 +159,39 @@ static void make_basis(int n, int kw, int ldk, std::vector<float>& t, std::vecto
             t[(size_t)(kw + a) * n + x] = sn;
             tT[(size_t)x * ldk + a] = c;
             tT[(size_t)x * ldk + kw + a] = sn;
+        }
+    }
+}
+
+// Folded table of the tensor-core path as bf16 hi/lo pairs (x = hi + lo, hi = rn(x),
+// lo = rn(x - hi), x the FP32 value): row j = cos(2 pi j x / n), j = 0..r, row r + j =
+// sin(2 pi j x / n), j = 1..r; basis [rows][ldn] (rows >= kw and columns >= n zero) and
+// its transpose basisT [n][ldf] (columns >= kw zero). Angles reduced exactly in integers
+// and evaluated in double, as in make_basis.
+static void make_basis_folded(int n, int kw, int ldf, int rows, int ldn, std::vector<__nv_bfloat16>& bh,
+                              std::vector<__nv_bfloat16>& bl, std::vector<__nv_bfloat16>& th,
+                              std::vector<__nv_bfloat16>& tl) {
+    const int r = (kw - 1) / 2;
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    bh.assign((size_t)rows * ldn, z);
+    bl.assign((size_t)rows * ldn, z);
+    th.assign((size_t)n * ldf, z);
+    tl.assign((size_t)n * ldf, z);
+    for (int j = 0; j <= r; ++j) {
+        for (int x = 0; x < n; ++x) {
+            const long long m = ((long long)j * x) % n;
+            const double ang = 2.0 * M_PI * (double)m / (double)n;
+            const float v[2] = {(float)std::cos(ang), (float)std::sin(ang)};
+            for (int q = 0; q < 2; ++q) {
+                if (q == 1 && j == 0) continue;
+                const int row = q == 0 ? j : r + j;
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[q]);
+                const __nv_bfloat16 l = __float2bfloat16_rn(v[q] - __bfloat162float(h));
+                bh[(size_t)row * ldn + x] = h;
+                bl[(size_t)row * ldn + x] = l;
+                th[(size_t)x * ldf + row] = h;
+                tl[(size_t)x * ldf + row] = l;
+            }
         }
     }
 }
@@ -549,6 +582,7 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.qpart, sizeof(long long) * 3 * nred);
     ALLOC(o->ws.lpart, sizeof(long long) * 2 * nred);
     ALLOC(o->ws.vpart, sizeof(float) * expand_parts(n));
+    ALLOC(o->ws.vbits, sizeof(unsigned));
     ALLOC(o->ws.bufI, sizeof(float) * npix);
     ALLOC(o->ws.bufV, sizeof(float) * npix);
     ALLOC(o->ws.phi2, sizeof(float) * npix);
@@ -567,19 +601,21 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
     ALLOC(o->ws.cgD, sizeof(float) * npix);
     if (precision == DEVEL_PREC_BF16X3) {
         const size_t bf = sizeof(__nv_bfloat16);
+        o->tcW.ldf = round_up(k, 16);
+        o->tcW2.ldf = round_up(o->k2, 16);
         for (TcWindow* tw : {&o->tcW, &o->tcW2}) {
-            const int ldk = (tw == &o->tcW) ? o->W.ldk : ld2;
-            ALLOC(tw->basis_hi, bf * round_up(ldk, 128) * o->ldn);
-            ALLOC(tw->basis_lo, bf * round_up(ldk, 128) * o->ldn);
-            ALLOC(tw->basisT_hi, bf * (size_t)n * ldk);
-            ALLOC(tw->basisT_lo, bf * (size_t)n * ldk);
-            ALLOC(tw->zm_hi, bf * (size_t)ldk * ldk);
-            ALLOC(tw->zm_lo, bf * (size_t)ldk * ldk);
+            const int ldf = tw->ldf;
+            ALLOC(tw->basis_hi, bf * round_up(ldf, 128) * o->ldn);
+            ALLOC(tw->basis_lo, bf * round_up(ldf, 128) * o->ldn);
+            ALLOC(tw->basisT_hi, bf * (size_t)n * ldf);
+            ALLOC(tw->basisT_lo, bf * (size_t)n * ldf);
+            ALLOC(tw->zm_hi, bf * (size_t)ldf * ldf);
+            ALLOC(tw->zm_lo, bf * (size_t)ldf * ldf);
         }
         ALLOC(o->Xhi, bf * (size_t)n * o->ldn);
         ALLOC(o->Xlo, bf * (size_t)n * o->ldn);
-        ALLOC(o->Acat_hi, bf * (size_t)n * ld2);
-        ALLOC(o->Acat_lo, bf * (size_t)n * ld2);
+        ALLOC(o->Acat_hi, bf * (size_t)n * o->tcW2.ldf);
+        ALLOC(o->Acat_lo, bf * (size_t)n * o->tcW2.ldf);
     }
 #undef ALLOC
 
@@ -642,48 +678,52 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
         if (e == cudaSuccess) e = cudaMemcpy(c.d, c.h, c.bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(o->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(o->ws.counters, 0, sizeof(unsigned) * 8);
+    if (e == cudaSuccess) e = cudaMemset(o->ws.vbits, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
         free_optics(o);
         return cuda_error(e, "devel_optics_create: cudaMemcpy");
     }
     if (precision == DEVEL_PREC_BF16X3) {
-        // bf16 hi/lo DFT tables (split on the device from the FP32 tables) and tensor maps
+        // folded bf16 hi/lo DFT tables and their tensor maps
         int rc = DEVEL_OK;
+        std::vector<__nv_bfloat16> bh, bl, th, tl;
         for (int wi = 0; wi < 2 && rc == DEVEL_OK; ++wi) {
             const Window& w = wi ? o->W2 : o->W;
             TcWindow& tw = wi ? o->tcW2 : o->tcW;
-            const int rows128 = round_up(w.ldk, 128);
-            if (cudaMemset(tw.basis_hi, 0, sizeof(__nv_bfloat16) * rows128 * o->ldn) != cudaSuccess ||
-                cudaMemset(tw.basis_lo, 0, sizeof(__nv_bfloat16) * rows128 * o->ldn) != cudaSuccess) {
-                rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
+            const int ldf = tw.ldf, rows128 = round_up(ldf, 128);
+            make_basis_folded(n, w.kw, ldf, rows128, o->ldn, bh, bl, th, tl);
+            const size_t bf = sizeof(__nv_bfloat16);
+            if (cudaMemcpy(tw.basis_hi, bh.data(), bf * bh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(tw.basis_lo, bl.data(), bf * bl.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(tw.basisT_hi, th.data(), bf * th.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(tw.basisT_lo, tl.data(), bf * tl.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemcpy of the folded tables");
                 break;
             }
-            rc = tc::launch_split(w.basis, w.ldk, n, n, o->ldn, tw.basis_hi, tw.basis_lo, 0);
-            if (!rc) rc = tc::make_map(&tw.m_basis128_hi, tw.basis_hi, rows128, o->ldn, o->ldn, 128);
+            rc = tc::make_map(&tw.m_basis128_hi, tw.basis_hi, rows128, o->ldn, o->ldn, 128);
             if (!rc) rc = tc::make_map(&tw.m_basis128_lo, tw.basis_lo, rows128, o->ldn, o->ldn, 128);
-            if (!rc) rc = tc::launch_split(w.basisT, n, w.ldk, w.ldk, w.ldk, tw.basisT_hi, tw.basisT_lo, 0);
-            if (!rc) rc = tc::make_map(&tw.m_basis_hi, tw.basis_hi, w.ldk, o->ldn, o->ldn, w.ldk);
-            if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, w.ldk, o->ldn, o->ldn, w.ldk);
-            if (!rc) rc = tc::make_map(&tw.m_basisT_hi, tw.basisT_hi, n, w.ldk, w.ldk, 128);
-            if (!rc) rc = tc::make_map(&tw.m_basisT_lo, tw.basisT_lo, n, w.ldk, w.ldk, 128);
-            // Zm entries outside the window's 2 kw x 2 kw block are never written: zero them once
-            if (!rc && (cudaMemset(tw.zm_hi, 0, sizeof(__nv_bfloat16) * w.ldk * w.ldk) != cudaSuccess ||
-                        cudaMemset(tw.zm_lo, 0, sizeof(__nv_bfloat16) * w.ldk * w.ldk) != cudaSuccess))
+            if (!rc) rc = tc::make_map(&tw.m_basis_hi, tw.basis_hi, ldf, o->ldn, o->ldn, ldf);
+            if (!rc) rc = tc::make_map(&tw.m_basis_lo, tw.basis_lo, ldf, o->ldn, o->ldn, ldf);
+            if (!rc) rc = tc::make_map(&tw.m_basisT_hi, tw.basisT_hi, n, ldf, ldf, 128);
+            if (!rc) rc = tc::make_map(&tw.m_basisT_lo, tw.basisT_lo, n, ldf, ldf, 128);
+            // Zm entries outside the window's kw x kw block are never written: zero them once
+            if (!rc && (cudaMemset(tw.zm_hi, 0, bf * ldf * ldf) != cudaSuccess ||
+                        cudaMemset(tw.zm_lo, 0, bf * ldf * ldf) != cudaSuccess))
                 rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
-            if (!rc) rc = tc::make_map(&tw.m_zm_hi, tw.zm_hi, w.ldk, w.ldk, w.ldk, kTileT);
-            if (!rc) rc = tc::make_map(&tw.m_zm_lo, tw.zm_lo, w.ldk, w.ldk, w.ldk, kTileT);
-            if (!rc) rc = tc::make_map(&tw.m_basisT64_hi, tw.basisT_hi, n, w.ldk, w.ldk, 64);
-            if (!rc) rc = tc::make_map(&tw.m_basisT64_lo, tw.basisT_lo, n, w.ldk, w.ldk, 64);
-            if (!rc) rc = tc::make_map(&tw.m_acat_hi, o->Acat_hi, n, w.ldk, w.ldk, 128);
-            if (!rc) rc = tc::make_map(&tw.m_acat_lo, o->Acat_lo, n, w.ldk, w.ldk, 128);
+            if (!rc) rc = tc::make_map3(&tw.m_zm_hi, tw.zm_hi, 1, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
+            if (!rc) rc = tc::make_map3(&tw.m_zm_lo, tw.zm_lo, 1, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
+            if (!rc) rc = tc::make_map(&tw.m_basisT64_hi, tw.basisT_hi, n, ldf, ldf, 64);
+            if (!rc) rc = tc::make_map(&tw.m_basisT64_lo, tw.basisT_lo, n, ldf, ldf, 64);
+            if (!rc) rc = tc::make_map3(&tw.m_acat_hi, o->Acat_hi, 1, n, ldf, ldf, (size_t)n * ldf, 128);
+            if (!rc) rc = tc::make_map3(&tw.m_acat_lo, o->Acat_lo, 1, n, ldf, ldf, (size_t)n * ldf, 128);
         }
         // the operand's pad columns [n, ldn) must read as zeros: only kernels that
         // write zeros there (or nothing) ever touch them afterwards
         if (!rc && (cudaMemset(o->Xhi, 0, sizeof(__nv_bfloat16) * (size_t)n * o->ldn) != cudaSuccess ||
                     cudaMemset(o->Xlo, 0, sizeof(__nv_bfloat16) * (size_t)n * o->ldn) != cudaSuccess))
             rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
-        if (!rc) rc = tc::make_map(&o->m_X_hi, o->Xhi, n, o->ldn, o->ldn, 128);
-        if (!rc) rc = tc::make_map(&o->m_X_lo, o->Xlo, n, o->ldn, o->ldn, 128);
+        if (!rc) rc = tc::make_map3(&o->m_X_hi, o->Xhi, 1, n, o->ldn, o->ldn, (size_t)n * o->ldn, 128);
+        if (!rc) rc = tc::make_map3(&o->m_X_lo, o->Xlo, 1, n, o->ldn, o->ldn, (size_t)n * o->ldn, 128);
         if (!rc) {
             cudaError_t e2 = cudaDeviceSynchronize();
             if (e2 != cudaSuccess) rc = cuda_error(e2, "devel_optics_create: table split");

@@ -98,14 +98,17 @@ enum { EPI_STORE = 0, EPI_VEL = 1, EPI_SPLIT = 2 };
 struct EpiArgs {
     float* C = nullptr;              // output
     int ldc = 0;
-    size_t split_stride = 0;         // offset of split-K slice z: C + z * split_stride
+    size_t split_stride = 0;         // FP32 GEMM: offset of split-K slice z (C + z * split_stride);
+                                     // tensor-core GEMMs: offset of clip z's output
     float scale = 1.f;
-    float* vpart = nullptr;          // EPI_VEL: per-CTA max |out|
+    float* vpart = nullptr;          // EPI_VEL (FP32 GEMM): per-CTA max |out|
     int n = 0;
-    // EPI_VEL: the last CTA reduces vpart into *vmax (FP64), flags non-finite in *status
+    // EPI_VEL: the last CTA reduces the maxima into vmax (FP64), flags non-finite in *status
     unsigned* counter = nullptr;
-    double* vmax = nullptr;
+    double* vmax = nullptr;          // tensor-core expansion: [nclips]
     int* status = nullptr;
+    unsigned* vbits = nullptr;       // tensor-core expansion: [nclips] zeroed words (max |out| bits)
+    int nclips = 1;
     // EPI_SPLIT: out = bf16 hi/lo pair, row pitch ldh (elements)
     __nv_bfloat16* Chi = nullptr;
     __nv_bfloat16* Clo = nullptr;
@@ -189,7 +192,8 @@ struct Workspace {
     float* Acat = nullptr;     // [n][ldk2] expansion operand [Re T | -Im T]
     long long* qpart = nullptr; // loss partials, fixed point (x 2^32), 3 per block
     long long* lpart = nullptr;// reduction partials, counts
-    float* vpart = nullptr;    // per-block max |V|
+    float* vpart = nullptr;    // per-block max |V| (FP32 path)
+    unsigned* vbits = nullptr; // [batch] zeroed words: max |V| bit patterns (tensor-core path)
     // solver buffers
     float* bufI = nullptr;     // [n*n] intensity, then dL/dI (in place)
     float* bufV = nullptr;     // [n*n] dL/dM
@@ -210,17 +214,23 @@ struct Workspace {
     float* cgD = nullptr;      // [n*n] direction (solve only)
 };
 
-// bf16 hi/lo tables and tensor maps of one window for the tensor-core path
+// bf16 hi/lo tables and tensor maps of one window for the tensor-core path.
+// The images are real, so each frequency pair +-j needs one cosine and one sine row:
+// the folded table has kw = 2r + 1 rows, row j = cos(2 pi j x / n) for j = 0..r and
+// row r + j = sin(2 pi j x / n) for j = 1..r, zero-padded to ldf = round_up(kw, 16)
+// (about half the 2 kw rows of the FP32 path's tables, so every contraction of the
+// tensor-core path is about half as wide).
 struct TcWindow {
-    __nv_bfloat16* basis_hi = nullptr;   // [round_up(ldk, 128)][ldn], rows >= ldk zero
+    int ldf = 0;                         // rows of the folded table: round_up(kw, 16)
+    __nv_bfloat16* basis_hi = nullptr;   // [round_up(ldf, 128)][ldn], rows >= kw zero
     __nv_bfloat16* basis_lo = nullptr;
-    __nv_bfloat16* basisT_hi = nullptr;  // [n][ldk]
+    __nv_bfloat16* basisT_hi = nullptr;  // [n][ldf]
     __nv_bfloat16* basisT_lo = nullptr;
     CUtensorMap m_basis_hi, m_basis_lo, m_basisT_hi, m_basisT_lo, m_acat_hi, m_acat_lo;
     CUtensorMap m_basis128_hi, m_basis128_lo;  // same tables, 128-row boxes (fused reduction, phase 2)
     CUtensorMap m_basisT64_hi, m_basisT64_lo;  // basis^T with 64-row boxes (expansion tiles of width 64)
-    // the window spectrum Z as the B operand of T = E Z: Zm[c][k] (ldk x ldk), rows
-    // c < kw: [Re Z(., c) | -Im Z(., c)], rows kw + c: [-Im Z(., c) | -Re Z(., c)]
+    // the window spectrum Z folded onto the table's rows, as the B operand of T = E Z
+    // (ldf x ldf; written by the Hopkins sums, see put_zm_folded)
     __nv_bfloat16* zm_hi = nullptr;
     __nv_bfloat16* zm_lo = nullptr;
     CUtensorMap m_zm_hi, m_zm_lo;  // boxes of kTileT rows (the N tile of T = E Z)
@@ -230,11 +240,15 @@ struct TcWindow {
 
 struct devel_optics {
     int n, K, k, r, k2, r2, precision;
+    // clips whose workspace this struct describes: 1 for a handle; a batch's view of its
+    // handle (devel_batch) shares the handle's tables and has B clips' workspace, every
+    // per-clip array holding clip c at c times its single-clip size
+    int batch = 1;
     int ldn = 0;                  // tensor-core path: round_up(n, 64)
     devel::TcWindow tcW, tcW2;
     __nv_bfloat16* Xhi = nullptr;     // [n][ldn] operand of the reductions
     __nv_bfloat16* Xlo = nullptr;
-    __nv_bfloat16* Acat_hi = nullptr; // [n][ldk2] operand of the expansions
+    __nv_bfloat16* Acat_hi = nullptr; // [n][ldf] operand of the expansions (ldf of the window)
     __nv_bfloat16* Acat_lo = nullptr;
     CUtensorMap m_X_hi, m_X_lo;
     int* tc_err = nullptr;            // device flag: DEVEL_ETIMEOUT from a bounded wait
@@ -284,11 +298,14 @@ int expand_parts(int n);
 // (one kernel: the last block to finish also does the final FP64 sums; `counter`
 // is a zeroed device word that the kernel leaves zeroed). alone: no other kernel runs
 // beside this one (one CTA per SM); else CTAs of 256 threads. Identical results.
+// B > 1: a batch of B clips (256-thread CTAs, grid nparts x B): clip c's image and target
+// at c n^2, its bf16 outputs at c n ldr, partials at c 3 nparts / c 2 nparts, counter
+// counter + c, history entries at c hist_stride; loss4 / cnt2 must then be NULL.
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
                   float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, long long* qpart,
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
                   long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
-                  bool alone = true);
+                  bool alone = true, int B = 1, int hist_stride = 0);
 int resist_parts(int n);
 // Defocused inner corner: images In (nominal focus) and Id (defocused); dL/dIn and dL/dId as
 // FP32 images (Rn, Rd; may alias In, Id) or bf16 hi/lo operands (Rnhi.. with pitch ldr).
@@ -315,13 +332,15 @@ int cg_parts(int n);
 int launch_cg_direction(int n, const float* V, float* Vp, float* D, bool restart, float* part, float* vpart,
                         float* beta_f, double* beta_out, unsigned* counters, double* vmax, int* status,
                         cudaStream_t s);
+// B > 1: a batch of B clips, each array's clip c at c n^2 (mask_bf: c n ldb, vmax: c; m: c n^2
+// or NULL)
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s,
-                         int upwind = DEVEL_UPWIND_GODUNOV1);
+                         int upwind = DEVEL_UPWIND_GODUNOV1, int B = 1);
 // tensor-core path: spectrum of the mask already in Xhi (bf16, exact)
 int launch_spectrum_mask_resident(const devel_optics* o, const Window& w, float2* out, cudaStream_t s);
-int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s);
+int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s, int B = 1);
 int launch_u8_to_f32(int n, const unsigned char* M, float* out, cudaStream_t s);
 
 // one-time kernel attributes (api.cu calls them once per device)
@@ -329,8 +348,9 @@ int litho_init_attrs();
 int reinit_init_attrs();
 
 // reinit.cu
+// B > 1: a batch of B clips, each array's clip c at c n^2
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
-                  cudaStream_t s);
+                  cudaStream_t s, int B = 1);
 
 // forward / adjoint bodies shared by the ABI and the solver (api.cu)
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s);
@@ -339,5 +359,9 @@ int forward_loss_from_mhat(const devel_optics* o, const unsigned char* target, c
                            int* status, cudaStream_t s);
 int adjoint_from_mhat(const devel_optics* o, const float* R, float* V, double* vmax, int* status,
                       cudaStream_t s);
+// adjoint from ws.mhat and the spectrum ws.rhat of dL/dI: Shat, then V with max |V| in vmax
+// (od: a second, defocused system whose term is added, or NULL)
+int adjoint_from_rhat(const devel_optics* o, float* V, double* vmax, int* status, cudaStream_t s,
+                      const devel_optics* od = nullptr);
 
 }  // namespace devel

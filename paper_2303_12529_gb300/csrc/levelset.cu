@@ -73,6 +73,16 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
     __shared__ float s_inv;
     pdl_trigger();
     pdl_wait();
+    {  // clip blockIdx.z of a batch: its images n^2 apart, its bf16 mask n * ldb apart
+        const size_t c = blockIdx.z, np = (size_t)n * n;
+        phi += c * np;
+        V += c * np;
+        vmax += c;
+        if (m) m += c * np;
+        phi_out += c * np;
+        if (mask_out) mask_out += c * np;
+        if (mask_bf) mask_bf += c * (size_t)n * ldb;
+    }
     if (threadIdx.x == 0) {  // 1 / max|V| once per block (the FP64 pipe is narrow)
         const double vm = *vmax;
         s_inv = vm > 0.0 ? 1.0f / (float)vm : 0.f;  // F = 0 (no transport) when max|V| = 0
@@ -234,6 +244,16 @@ k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
     __shared__ float s_inv;
     pdl_trigger();
     pdl_wait();
+    {  // clip blockIdx.z of a batch
+        const size_t c = blockIdx.z, np = (size_t)n * n;
+        phi += c * np;
+        V += c * np;
+        vmax += c;
+        if (m) m += c * np;
+        phi_out += c * np;
+        if (mask_out) mask_out += c * np;
+        if (mask_bf) mask_bf += c * (size_t)n * ldb;
+    }
     const int x0 = blockIdx.x * kWX, y0 = blockIdx.y * kWY;
     const int tid = threadIdx.y * kWX + threadIdx.x;
     if (tid == 0) {  // 1 / max|V| once per block (FP64 operand)
@@ -284,17 +304,18 @@ int grid_for(size_t npix) {
 
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
-                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s, int upwind) {
+                         unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s, int upwind,
+                         int B) {
     if (upwind == DEVEL_UPWIND_WENO5) {
         prof_begin(PK_STEP, s);
-        cudaError_t e = launch_pdl(k_levelset_step_weno, dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY),
+        cudaError_t e = launch_pdl(k_levelset_step_weno, dim3((n + kWX - 1) / kWX, (n + kWY - 1) / kWY, B),
                                    dim3(kWX, kWTh), 0, s, phi, V, vmax, m, dt, lambda, n, phi_out, mask_out, mask_bf,
                                    ldb);
         prof_end(PK_STEP, s);
         if (e != cudaSuccess) return cuda_error(e, "k_levelset_step_weno");
         return DEVEL_OK;
     }
-    dim3 grid((n + 256 * kPX - 1) / (256 * kPX), (n + kRows - 1) / kRows);
+    dim3 grid((n + 256 * kPX - 1) / (256 * kPX), (n + kRows - 1) / kRows, B);
     prof_begin(PK_STEP, s);
     cudaError_t e = launch_pdl(k_levelset_step, grid, dim3(256), 0, s, phi, V, vmax, m, dt, lambda, n, phi_out,
                                mask_out, mask_bf, ldb);
@@ -303,8 +324,8 @@ int launch_levelset_step(int n, const float* phi, const float* V, const double* 
     return DEVEL_OK;
 }
 
-int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s) {
-    const size_t npix = (size_t)n * n;
+int launch_mask_from_phi(int n, const float* phi, unsigned char* M, cudaStream_t s, int B) {
+    const size_t npix = (size_t)n * n * B;
     prof_begin(PK_MASK, s);
     k_mask_from_phi<<<grid_for(npix), 256, 0, s>>>(phi, npix, M);
     prof_end(PK_MASK, s);

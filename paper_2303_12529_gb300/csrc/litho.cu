@@ -28,6 +28,11 @@
 //   1. T(y, b) = sum_a e^{+i theta_a y} Z(a, b), stored as Acat = [Re T | -Im T]
 //   2. out = Acat basisT^T   (FP32 NT GEMM or tcgen05), with a fused epilogue:
 //      plain store, velocity (x2, max |.|) or the resist loss (dL/dI).
+// The tensor-core path runs both on folded tables (one cosine row per |frequency| and
+// one sine row per nonzero |frequency|, kw rows instead of 2 kw): the reduction's
+// second contraction then yields cos / sin products at |u1|, |u2|, from which every
+// entry (+-u1, +-u2) is formed with signs (real image: cos is even, sin odd), and the
+// expansion's operand folds T at +-u2 into one cosine and one sine column.
 #include <algorithm>
 #include <cfloat>
 
@@ -235,101 +240,172 @@ void launch_spec_final(const float* Q, int nq, int ldq, int kw, float2* out, int
 // frequency-domain sums with the rank-K TCC (one warp per output frequency)
 // --------------------------------------------------------------------------
 
-// Fixed-order block reduction of a float2 over 128 threads (4 warps); valid in thread 0.
-__device__ __forceinline__ float2 block_sum2_128(float2 v, float2* sh) {
+// Fixed-order sums of a float2 over each group of 128 threads (4 warps) of a block of
+// 128 G threads; valid in thread 0 for every group q: (w0 + w1) + (w2 + w3) of its warps.
+template <int G>
+__device__ __forceinline__ void group_sums2_128(float2 v, float2* sh, float2* out) {
     v = warp_sum2(v);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    return cadd(cadd(sh[0], sh[1]), cadd(sh[2], sh[3]));
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < G; ++q) out[q] = cadd(cadd(sh[4 * q], sh[4 * q + 1]), cadd(sh[4 * q + 2], sh[4 * q + 3]));
 }
 
-// Tensor-core path: window spectrum entry Z(a, b) into the B operand of T = E Z
-// (bf16 hi/lo, [ldz][ldz]): with E's row y = [cos_a(y) | sin_a(y)],
-// T'(y, b) = Re T(y, b) needs Zm[b][a] = Re Z, Zm[b][kw + a] = -Im Z, and
-// T'(y, kw + b) = -Im T(y, b) needs Zm[kw + b][a] = -Im Z, Zm[kw + b][kw + a] = -Re Z.
-__device__ __forceinline__ void put_zm(__nv_bfloat16* hi, __nv_bfloat16* lo, int ldz, int kw, int a, int b,
-                                       float2 z) {
-    auto put = [&](int r, int c, float x) {
+// Tensor-core path: the four window spectrum entries Z(+-j1, +-j2) folded into the B
+// operand of T = E Z over the folded table (rows c(j) = j: cos, s(j) = r + j: sin), as
+// bf16 hi/lo [ldz][ldz] (row = output column of T, column = table row):
+//   P = Z(j1, j2), Q = Z(j1, -j2), R = Z(-j1, j2), T = Z(-j1, -j2)
+// (an entry whose sign flip is the same frequency, j = 0, is counted once). With
+// T(y, u2) = sum_u1 e^{+i theta u1 y} Z(u1, u2) and the expansion's operand
+// [T(y, j2) + T(y, -j2)] real part on cos rows, -[Im T(y, j2) - Im T(y, -j2)] on sin rows:
+//   Zm[c(j2)][c(j1)] = Re (P + Q + R + T)            Zm[c(j2)][s(j1)] = -Im (P - R + Q - T)
+//   Zm[s(j2)][c(j1)] = -Im (P - Q + R - T)            Zm[s(j2)][s(j1)] = Re (-P + Q + R - T)
+__device__ __forceinline__ void put_zm_folded(__nv_bfloat16* hi, __nv_bfloat16* lo, int ldz, int r, int j1, int j2,
+                                              float2 P, float2 Q, float2 R, float2 T) {
+    auto put = [&](int row, int col, float x) {
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi[(size_t)r * ldz + c] = h;
-        lo[(size_t)r * ldz + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi[(size_t)row * ldz + col] = h;
+        lo[(size_t)row * ldz + col] = __float2bfloat16_rn(x - __bfloat162float(h));
     };
-    put(b, a, z.x);
-    put(b, kw + a, -z.y);
-    put(kw + b, a, -z.y);
-    put(kw + b, kw + a, -z.x);
+    const bool hq = j2 > 0, hr = j1 > 0, ht = hq && hr;
+    const float cc = P.x + (hq ? Q.x : 0.f) + (hr ? R.x : 0.f) + (ht ? T.x : 0.f);
+    put(j2, j1, cc);
+    if (hr) put(j2, r + j1, -((P.y - R.y) + (hq ? Q.y - T.y : 0.f)));
+    if (hq) put(r + j2, j1, -((P.y - Q.y) + (hr ? R.y - T.y : 0.f)));
+    if (ht) put(r + j2, r + j1, (-P.x + Q.x) + (R.x - T.x));
 }
 
-// Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), one block of 128
-// threads per g; rect(g) = {a in W : a - g in W}, t = row-major index within rect(g).
-// The aerial image is real, so Ihat(-g) = conj(Ihat(g)): blocks cover the first half of
-// the k2 x k2 window (flat index g <= center) and write the mirrored entry as well.
-__global__ void __launch_bounds__(128)
-k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
-           const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat, __nv_bfloat16* __restrict__ zhi,
-           __nv_bfloat16* __restrict__ zlo, int ldz) {
-    __shared__ float2 sh[4];
+// Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), rect(g) = {a in W :
+// a - g in W}, t = row-major index within rect(g). The aerial image is real, so
+// Ihat(-g) = conj(Ihat(g)): one block per (j1, j2) in [0, r2]^2 whose two halves of 128
+// threads sum g = (j1, j2) and g = (j1, -j2) (the latter when j1, j2 > 0) and write the four
+// entries (+-j1, +-j2), and for the tensor-core path their folded operand entries.
+__device__ __forceinline__ float2 ihat_sum(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
+                                           const float2* __restrict__ mhat, int k, int c1, int c2, int tid) {
     const int k2 = 2 * k - 1, r2 = k - 1;
-    const int g = blockIdx.x;
-    const int c1 = g / k2, c2 = g - c1 * k2;
     const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
     const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
     const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
-    const float2* T = Tdiff + goff[g];
-    // the TCC entries (constant) into L2 while the previous kernel finishes
-    pdl_trigger();
-    for (int i = threadIdx.x * 16; i < total; i += blockDim.x * 16) prefetch_l2(T + i);
-    pdl_wait();
+    const float2* T = Tdiff + goff[c1 * k2 + c2];
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int t = threadIdx.x; t < total; t += 128) {
+    for (int t = tid; t < total; t += 128) {
         const int i1 = t / n2, i2 = t - i1 * n2;
         const int a1 = a1lo + i1, a2 = a2lo + i2;
         const int b1 = a1 - c1 + r2, b2 = a2 - c2 + r2;
         acc = cadd(acc, cmul(__ldg(T + t), cmulc(__ldg(mhat + a1 * k + a2), __ldg(mhat + b1 * k + b2))));
     }
-    const float2 s = block_sum2_128(acc, sh);
-    if (threadIdx.x == 0) {
-        Ihat[g] = s;
-        Ihat[k2 * k2 - 1 - g] = make_float2(s.x, -s.y);
+    return acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
+           const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat, __nv_bfloat16* __restrict__ zhi,
+           __nv_bfloat16* __restrict__ zlo, int ldz) {
+    __shared__ float2 sh[8];
+    __shared__ float2 res[2];
+    const int k2 = 2 * k - 1, r2 = k - 1;
+    const int j1 = blockIdx.x / (r2 + 1), j2 = blockIdx.x - j1 * (r2 + 1);
+    {  // clip blockIdx.y of a batch
+        const size_t c = blockIdx.y;
+        mhat += c * k * k;
+        Ihat += c * k2 * k2;
         if (zhi) {
-            put_zm(zhi, zlo, ldz, k2, c1, c2, s);
-            put_zm(zhi, zlo, ldz, k2, k2 - 1 - c1, k2 - 1 - c2, make_float2(s.x, -s.y));
+            zhi += c * ldz * ldz;
+            zlo += c * ldz * ldz;
         }
+    }
+    const int half = threadIdx.x >> 7, tid = threadIdx.x & 127;
+    const bool two = j1 > 0 && j2 > 0;
+    const int c1 = r2 + j1, c2 = half ? r2 - j2 : r2 + j2;
+    const bool active = half == 0 || two;
+    // the TCC entries (constant) into L2 while the previous kernel finishes
+    pdl_trigger();
+    if (active) {
+        const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
+        const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
+        const float2* T = Tdiff + goff[c1 * k2 + c2];
+        const int total = (a1hi - a1lo) * (a2hi - a2lo);
+        for (int i = tid * 16; i < total; i += 128 * 16) prefetch_l2(T + i);
+    }
+    pdl_wait();
+    const float2 acc = active ? ihat_sum(Tdiff, goff, mhat, k, c1, c2, tid) : make_float2(0.f, 0.f);
+    group_sums2_128<2>(acc, sh, res);
+    if (threadIdx.x == 0) {
+        const float2 A = res[0], Ac = make_float2(A.x, -A.y);
+        const int g = c1 * k2 + (r2 + j2);
+        Ihat[g] = A;
+        Ihat[k2 * k2 - 1 - g] = Ac;
+        float2 B = Ac, Bc = Ac;
+        if (two) {
+            B = res[1];
+            Bc = make_float2(B.x, -B.y);
+            const int gb = c1 * k2 + (r2 - j2);
+            Ihat[gb] = B;
+            Ihat[k2 * k2 - 1 - gb] = Bc;
+        }
+        // Q = Ihat(j1, -j2), R = Ihat(-j1, j2) = conj(Q), T = Ihat(-j1, -j2) = conj(A)
+        if (zhi) put_zm_folded(zhi, zlo, ldz, r2, j1, j2, A, j1 > 0 ? B : Ac, j2 > 0 ? Bc : Ac, Ac);
     }
 }
 
-// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a), one block of 128 threads per f;
-// with a second system (TCC2, rhat2: the defocused corner) its term is added.
-__global__ void __launch_bounds__(128)
+// Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a); with a second system (TCC2,
+// rhat2: the defocused corner) its term is added. One block per (j1, j2) in [0, r]^2 whose
+// four groups of 128 threads sum f = (j1, j2), (j1, -j2), (-j1, j2), (-j1, -j2) (each sign
+// flip taken only for j > 0), then write those entries, and for the tensor-core path their
+// folded operand entries.
+__global__ void __launch_bounds__(512)
 k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
            const float2* __restrict__ rhat, int k, float2* __restrict__ Shat, __nv_bfloat16* __restrict__ zhi,
            __nv_bfloat16* __restrict__ zlo, int ldz, const float2* __restrict__ TCC2,
            const float2* __restrict__ rhat2) {
-    __shared__ float2 sh[4];
-    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
-    const int f = blockIdx.x, f1 = f / k, f2 = f - f1 * k;
+    __shared__ float2 sh[16];
+    __shared__ float2 res[4];
+    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k, r = (k - 1) / 2;
+    const int j1 = blockIdx.x / (r + 1), j2 = blockIdx.x - j1 * (r + 1);
+    {  // clip blockIdx.y of a batch
+        const size_t c = blockIdx.y;
+        mhat += c * kk;
+        rhat += c * k2 * k2;
+        if (rhat2) rhat2 += c * k2 * k2;
+        Shat += c * kk;
+        if (zhi) {
+            zhi += c * ldz * ldz;
+            zlo += c * ldz * ldz;
+        }
+    }
+    const int q = threadIdx.x >> 7, tid = threadIdx.x & 127;
+    const int s1 = (q & 2) ? -1 : 1, s2 = (q & 1) ? -1 : 1;
+    const bool active = (s1 > 0 || j1 > 0) && (s2 > 0 || j2 > 0);
+    const int f1 = r + s1 * j1, f2 = r + s2 * j2, f = f1 * k + f2;
     const float2* row = TCC + (size_t)f * kk;
     pdl_trigger();
-    for (int i = threadIdx.x * 16; i < kk; i += blockDim.x * 16) {
-        prefetch_l2(row + i);
-        if (TCC2) prefetch_l2(TCC2 + (size_t)f * kk + i);
-    }
+    if (active)
+        for (int i = tid * 16; i < kk; i += 128 * 16) {
+            prefetch_l2(row + i);
+            if (TCC2) prefetch_l2(TCC2 + (size_t)f * kk + i);
+        }
     pdl_wait();
     float2 acc = make_float2(0.f, 0.f);
+    if (active) {
 #pragma unroll 4
-    for (int a = threadIdx.x; a < kk; a += 128) {
-        const int a1 = a / k, a2 = a - a1 * k;
-        const int g = (f1 - a1 + r2) * k2 + (f2 - a2 + r2);
-        const float2 ma = __ldg(mhat + a);
-        acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat + g)), __ldg(row + a)));
-        if (TCC2)  // the defocused system's term (its TCC, its dL/dI spectrum, the same mask)
-            acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat2 + g)), __ldg(TCC2 + (size_t)f * kk + a)));
+        for (int a = tid; a < kk; a += 128) {
+            const int a1 = a / k, a2 = a - a1 * k;
+            const int g = (f1 - a1 + r2) * k2 + (f2 - a2 + r2);
+            const float2 ma = __ldg(mhat + a);
+            acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat + g)), __ldg(row + a)));
+            if (TCC2)  // the defocused system's term (its TCC, its dL/dI spectrum, the same mask)
+                acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat2 + g)), __ldg(TCC2 + (size_t)f * kk + a)));
+        }
     }
-    const float2 s = block_sum2_128(acc, sh);
+    group_sums2_128<4>(acc, sh, res);
     if (threadIdx.x == 0) {
-        Shat[f] = s;
-        if (zhi) put_zm(zhi, zlo, ldz, k, f1, f2, s);
+        for (int g = 0; g < 4; ++g) {
+            const int t1 = (g & 2) ? -1 : 1, t2 = (g & 1) ? -1 : 1;
+            if ((t1 > 0 || j1 > 0) && (t2 > 0 || j2 > 0)) Shat[(r + t1 * j1) * k + (r + t2 * j2)] = res[g];
+        }
+        if (zhi) put_zm_folded(zhi, zlo, ldz, r, j1, j2, res[0], res[1], res[2], res[3]);
     }
 }
 
@@ -460,8 +536,8 @@ int reduce_finish(const devel_optics* o, const Window& w, float2* out, cudaStrea
 int reduce_tc(const devel_optics* o, const Window& w, int use_alo, float2* out, cudaStream_t s) {
     const TcWindow& tw = tc_window(o, w);
     tc::Operands op{&o->m_X_hi, &o->m_X_lo, &tw.m_basis_hi, &tw.m_basis_lo, use_alo};
-    return tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, w.ldk, w.kw, o->n, o->n, o->ldn,
-                                o->tc_split, reinterpret_cast<float2*>(o->ws.Q), out, o->tc_err, s);
+    return tc::launch_spectrum2(op, &tw.m_basis128_hi, &tw.m_basis128_lo, tw.ldf, w.kw, o->n, o->n, o->ldn,
+                                o->tc_split, o->batch, o->ws.Q, out, o->tc_err, s);
 }
 
 }  // namespace
@@ -501,9 +577,9 @@ int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_HOPKINS, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    cudaError_t e = launch_pdl(k_ihat_tcc, dim3((o->k2 * o->k2 + 1) / 2), dim3(128), 0, s, (const float2*)o->Tdiff,
+    cudaError_t e = launch_pdl(k_ihat_tcc, dim3(o->k * o->k, o->batch), dim3(256), 0, s, (const float2*)o->Tdiff,
                                (const int*)o->goff, (const float2*)o->ws.mhat, o->k, o->ws.Ihat,
-                               tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr, o->W2.ldk);
+                               tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr, o->tcW2.ldf);
     prof_end(PK_HOPKINS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_ihat_tcc");
     return DEVEL_OK;
@@ -512,9 +588,10 @@ int launch_ihat(const devel_optics* o, cudaStream_t s) {
 int launch_shat(const devel_optics* o, cudaStream_t s, const devel_optics* od) {
     prof_begin(PK_ADJ_WINDOW, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    cudaError_t e = launch_pdl(k_shat_tcc, dim3(o->k * o->k), dim3(128), 0, s, (const float2*)o->TCC,
+    cudaError_t e = launch_pdl(k_shat_tcc, dim3((o->r + 1) * (o->r + 1), o->batch), dim3(512), 0, s,
+                               (const float2*)o->TCC,
                                (const float2*)o->ws.mhat, (const float2*)o->ws.rhat, o->k, o->ws.Shat,
-                               tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->W.ldk,
+                               tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->tcW.ldf,
                                od ? (const float2*)od->TCC : nullptr, od ? (const float2*)od->ws.rhat : nullptr);
     prof_end(PK_ADJ_WINDOW, s);
     if (e != cudaSuccess) return cuda_error(e, "k_shat_tcc");
@@ -539,14 +616,17 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
         EpiArgs et;
         et.Chi = o->Acat_hi;
         et.Clo = o->Acat_lo;
-        et.ldh = w.ldk;
-        int rc = tc::launch_gemm_split(opT, kTileT, PK_EXPAND_T, n, w.ldk, w.ldk, et, o->tc_err, s);
+        et.ldh = tw.ldf;
+        et.split_stride = (size_t)n * tw.ldf;  // clip stride of the operand
+        int rc = tc::launch_gemm_split(opT, kTileT, PK_EXPAND_T, n, tw.ldf, tw.ldf, o->batch, et, o->tc_err, s);
         if (rc) return rc;
         const int bn = o->tc_expand_bn;
         tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, bn == 64 ? &tw.m_basisT64_hi : &tw.m_basisT_hi,
                         bn == 64 ? &tw.m_basisT64_lo : &tw.m_basisT_lo, 1};
         if (nparts) *nparts = tc::expand_grid(n, n, bn);
-        return tc::launch_expand(op, bn, epi, n, n, w.ldk, ep, o->tc_err, s);
+        ep.split_stride = (size_t)n * n;  // clip stride of the output image
+        ep.vbits = ws.vbits;
+        return tc::launch_expand(op, bn, epi, n, n, tw.ldf, o->batch, ep, o->tc_err, s);
     }
     prof_begin(PK_EXPAND_T, s);
     cudaError_t e = launch_pdl(k_expand_T, dim3((n + kTRows - 1) / kTRows), dim3(256),

@@ -40,6 +40,8 @@ k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     __shared__ int sc[2][4][kSegs][kCX];  // [buffer][last0, last1, first0, first1][segment][column]
     pdl_trigger();
     pdl_wait();
+    mask += (size_t)blockIdx.y * n * n;  // clip blockIdx.y of a batch
+    g += (size_t)blockIdx.y * n * n;
     const int cx = threadIdx.x, sg = threadIdx.y;
     const int x = blockIdx.x * kCX + cx;
     const int L = (n + kSegs - 1) / kSegs;
@@ -135,6 +137,9 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     extern __shared__ int sfx[];
     pdl_trigger();
     pdl_wait();
+    mask += (size_t)blockIdx.y * n * n;  // clip blockIdx.y of a batch
+    g += (size_t)blockIdx.y * n * n;
+    phi += (size_t)blockIdx.y * n * n;
     const int nb = edt_nb(n), npad = nb * kBlk;
     // per class c: f at c npad, then the block minima, eL and eR at 2 npad + (0 / 2 / 4 + c) nb
     int* const F = sfx;
@@ -233,14 +238,14 @@ int reinit_init_attrs() {
 }
 
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
-                  cudaStream_t s) {
+                  cudaStream_t s, int B) {
     prof_begin(PK_EDT_COLS, s);
-    cudaError_t e = launch_pdl(k_edt_cols, dim3((n + kCX - 1) / kCX), dim3(kCX, kSegs), 0, s, mask, n,
+    cudaError_t e = launch_pdl(k_edt_cols, dim3((n + kCX - 1) / kCX, B), dim3(kCX, kSegs), 0, s, mask, n,
                                reinterpret_cast<unsigned*>(d2));
     prof_end(PK_EDT_COLS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_edt_cols");
     prof_begin(PK_EDT_ROWS, s);
-    e = launch_pdl(k_edt_rows, dim3(n), dim3(256), edt_rows_smem(n), s, mask, n, reinterpret_cast<unsigned*>(d2), phi,
+    e = launch_pdl(k_edt_rows, dim3(n, B), dim3(256), edt_rows_smem(n), s, mask, n, reinterpret_cast<unsigned*>(d2), phi,
                    d_lo, d_hi);
     prof_end(PK_EDT_ROWS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_edt_rows");

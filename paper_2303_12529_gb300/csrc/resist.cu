@@ -26,6 +26,9 @@ struct ResistOut {
     long long* l2_hist;
     long long* pvb_hist;
     int* status;
+    // clip blockIdx.y of a batch: images (and targets) n^2 apart, bf16 outputs n ldr apart,
+    // partials 3 / 2 x part_stride apart, counters 1 apart, history entries hist_stride apart
+    int part_stride, hist_stride;
 };
 
 // The image is split into "logical blocks" of 256 threads, as many as fit on every SM
@@ -153,6 +156,28 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
     __shared__ int si[2][32];
     pdl_trigger();
     pdl_wait();
+    if (blockIdx.y) {
+        const size_t c = blockIdx.y, np = (size_t)n * n;
+        In += c * np;
+        if (kDef) Id += c * np;
+        Zt += c * np;
+        if (Rn) Rn += c * np;
+        if (kDef && Rd) Rd += c * np;
+        if (Rnhi) {
+            Rnhi += c * (size_t)n * ldr;
+            Rnlo += c * (size_t)n * ldr;
+        }
+        if (kDef && Rdhi) {
+            Rdhi += c * (size_t)n * ldr;
+            Rdlo += c * (size_t)n * ldr;
+        }
+        qpart += c * 3 * (size_t)out.part_stride;
+        lpart += c * 2 * (size_t)out.part_stride;
+        out.counter += c;
+        if (out.loss_hist) out.loss_hist += c * out.hist_stride;
+        if (out.l2_hist) out.l2_hist += c * out.hist_stride;
+        if (out.pvb_hist) out.pvb_hist += c * out.hist_stride;
+    }
     LossAcc acc;
     const long long npix = (long long)n * n;
     // logical block lb of nlb, thread tid of its 256
@@ -275,22 +300,23 @@ static int resist_grid(int n, int per_sm) {
 int resist_parts(int n) { return resist_grid(n, resist_blocks_per_sm<false>()); }
 
 template <bool kDef, typename... A>
-static cudaError_t launch_resist_kernel(int n, int nparts, bool alone, cudaStream_t s, A... args) {
+static cudaError_t launch_resist_kernel(int n, int nparts, bool alone, int B, cudaStream_t s, A... args) {
     constexpr int per_sm = resist_blocks_per_sm<kDef>();
     const int nlb = std::min(nparts, resist_grid(n, per_sm));
-    if (alone && nlb % per_sm == 0)
+    if (alone && B == 1 && nlb % per_sm == 0)
         return launch_pdl(k_resist<kDef, per_sm>, dim3(nlb / per_sm), dim3(kThreads * per_sm), 0, s, args...);
-    return launch_pdl(k_resist<kDef, 1>, dim3(nlb), dim3(kThreads), 0, s, args...);
+    return launch_pdl(k_resist<kDef, 1>, dim3(nlb, B), dim3(kThreads), 0, s, args...);
 }
 
 int launch_resist(int n, const float* I, const unsigned char* Zt, const devel_resist_params& p,
                   float* R, __nv_bfloat16* Rhi, __nv_bfloat16* Rlo, int ldr, long long* qpart,
                   long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
                   long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
-                  bool alone) {
-    ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
+                  bool alone, int B, int hist_stride) {
+    ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status,
+                  nparts, hist_stride};
     prof_begin(PK_RESIST, s);
-    cudaError_t e = launch_resist_kernel<false>(n, nparts, alone, s, I, (const float*)nullptr, Zt, n,
+    cudaError_t e = launch_resist_kernel<false>(n, nparts, alone, B, s, I, (const float*)nullptr, Zt, n,
                                                 make_resist_args(p), R, (float*)nullptr, Rhi, Rlo,
                                                 (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, ldr, qpart, lpart,
                                                 out);
@@ -305,9 +331,10 @@ int launch_resist_defocus(int n, const float* In, const float* Id, const unsigne
                           long long* lpart, int nparts, double* loss4, long long* cnt2, double* loss_hist,
                           long long* l2_hist, long long* pvb_hist, int* status, unsigned* counter, cudaStream_t s,
                           bool alone) {
-    ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status};
+    ResistOut out{counter, (double)p.alpha, (double)p.beta, loss4, cnt2, loss_hist, l2_hist, pvb_hist, status,
+                  nparts, 0};
     prof_begin(PK_RESIST, s);
-    cudaError_t e = launch_resist_kernel<true>(n, nparts, alone, s, In, Id, Zt, n, make_resist_args(p), Rn, Rd,
+    cudaError_t e = launch_resist_kernel<true>(n, nparts, alone, 1, s, In, Id, Zt, n, make_resist_args(p), Rn, Rd,
                                                Rnhi, Rnlo, Rdhi, Rdlo, ldr, qpart, lpart, out);
     prof_end(PK_RESIST, s);
     if (e != cudaSuccess) return cuda_error(e, "k_resist_defocus");

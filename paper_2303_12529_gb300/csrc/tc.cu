@@ -44,7 +44,8 @@ struct Cfg {
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
 };
 
-// One 128 x BN tile of D = A B^T per CTA (split-K over gridDim.z is not used here):
+// One 128 x BN tile of D = A B^T per CTA, clip blockIdx.z of a batch (B: a 3-D map over the
+// clips; D of clip z at ep.Chi / ep.Clo + z * ep.split_stride):
 //   warp 0, one thread   TMA producer: 64-element K slabs of A_hi, A_lo, B_hi, B_lo
 //                        into a STAGES ring;
 //   warp 1, one thread   MMA issuer: 4 K-steps of 16 per slab, 3 MMAs each;
@@ -54,7 +55,7 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M, int N,
-          int kb_per_split, int kb_total, int ksteps_last, int use_alo, const EpiArgs ep, int* err) {
+          int kb_total, int ksteps_last, int use_alo, const EpiArgs ep, int* err) {
     using CF = Cfg<BN>;
     constexpr int S = CF::kStages;
     extern __shared__ uint8_t smem_raw[];
@@ -64,9 +65,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     uint64_t* accum = empty + S;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
-    const int kb0 = blockIdx.z * kb_per_split;
-    const int nkb = max(0, min(kb_per_split, kb_total - kb0));
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN, clip = blockIdx.z;
+    const int kb0 = 0, nkb = kb_total;
 
     auto stage_ptr = [&](int s, int which) -> uint8_t* {
         // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
@@ -93,8 +93,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
         pdl_wait();
         for (int i = 0; i < npre; ++i) {
-            tma_load_2d(&tmBhi, &full[i], stage_ptr(i, 2), (kb0 + i) * kBK, n0);
-            tma_load_2d(&tmBlo, &full[i], stage_ptr(i, 3), (kb0 + i) * kBK, n0);
+            tma_load_3d(&tmBhi, &full[i], stage_ptr(i, 2), (kb0 + i) * kBK, n0, clip);
+            tma_load_3d(&tmBlo, &full[i], stage_ptr(i, 3), (kb0 + i) * kBK, n0, clip);
         }
         issued = npre;
     }
@@ -116,8 +116,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             const int kc = (kb0 + i) * kBK;
             tma_load_2d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0);
             if (use_alo) tma_load_2d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0);
-            tma_load_2d(&tmBhi, &full[s], stage_ptr(s, 2), kc, n0);
-            tma_load_2d(&tmBlo, &full[s], stage_ptr(s, 3), kc, n0);
+            tma_load_3d(&tmBhi, &full[s], stage_ptr(s, 2), kc, n0, clip);
+            tma_load_3d(&tmBlo, &full[s], stage_ptr(s, 3), kc, n0, clip);
             ++issued;
         }
     } else if (warp == 1 && lane == 0 && nkb > 0) {
@@ -163,8 +163,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
         }
         const int col0 = n0 + c;
         if (row < M && col0 < N) {
-            __nv_bfloat16* dh = ep.Chi + (size_t)row * ep.ldh + col0;
-            __nv_bfloat16* dl = ep.Clo + (size_t)row * ep.ldh + col0;
+            __nv_bfloat16* dh = ep.Chi + clip * ep.split_stride + (size_t)row * ep.ldh + col0;
+            __nv_bfloat16* dl = ep.Clo + clip * ep.split_stride + (size_t)row * ep.ldh + col0;
             __align__(16) __nv_bfloat16 h[16], l[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -200,61 +200,63 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // Fused reduction onto a window: both contractions in one kernel
 // ---------------------------------------------------------------------------
+// The table is the folded one (BN = ldf rows: cos j for j = 0..r, sin j at row r + j).
 // CTA (row tile m0 of 128 image rows y, K slice z of `split` columns x):
-//   phase 1  D1[y][c] = sum_x X[y][x] basis[c][x]            (the mainloop above, M = 128, N = BN)
+//   phase 1  D1[y][c] = sum_x X[y][x] basis[c][x]            (M = 128, N = BN)
 //   phase 2  D1 is drained from TMEM, split to bf16 hi/lo and written transposed into shared
 //            memory as a K-major operand B2[c2][y] (128-byte swizzle, as TMA would lay it out);
-//            D2[c1][c2] = sum_y basis[c1][y] D1[y][c2] for c1 in 128-row blocks (A2 by TMA)
-//   combine  D2 (BN = ldk rows of cos / sin) becomes the CTA's partial complex spectrum
-//            P(a, b) = (D2[a][b] - D2[kw+a][kw+b]) - i (D2[a][kw+b] + D2[kw+a][b]), a, b < kw,
-//            assembled in shared memory and stored contiguously as slice
-//            blockIdx.y * gridDim.z + blockIdx.z of G ([slices][kw * kw] complex);
-// k_spec_sum then adds the slices in slice order and scales by 1/n^2.
-// Every sum runs in a fixed order, so the result does not depend on timing.
+//            D2[c1][c2] = sum_y basis[c1][y] D1[y][c2]       (M = 128 >= BN, A2 by TMA)
+//   store    the kw x kw block of D2 (cos / sin products at |frequencies| j1, j2) is staged
+//            in shared memory and copied with coalesced rows to slice
+//            blockIdx.y * gridDim.z + blockIdx.z of clip blockIdx.x's slices in G
+//            ([clips][slices][kw][kc] floats, kc = round_up(kw, 16));
+// k_spec_sum then adds the slices in slice order, forms the complex entries (+-j1, +-j2)
+// and scales by 1/n^2.
+// Every sum runs in a fixed order, so the result does not depend on timing. 8 warps: warps
+// w and w + 4 share TMEM lanes 32 (w % 4).. and split the drains' 16-column chunks. Two
+// CTAs fit on an SM (shared memory and TMEM), so one CTA's drains and second contraction
+// overlap the other's loads.
 template <int BN>
 struct Cfg2 {
+    static_assert(BN <= 128, "the folded table of a window fits one 128-row block");
     static constexpr uint32_t kB2 = BN * 128;                  // one k-block of B2 (bf16, 64 y)
-    static constexpr int kMB = (BN + 127) / 128;                // 128-row blocks of c1
-    // all kMB blocks of A2 resident at once when they fit beside B2 (then the blocks'
-    // MMA chains interleave), else one block at a time in the same buffers
-    static constexpr uint32_t kPhase2All = 4 * kB2 + kMB * 4 * kABytes;
-    static constexpr bool kA2All = kPhase2All + 1024 + 512 <= 232448u;
-    static constexpr uint32_t kPhase2 = kA2All ? kPhase2All : 4 * kB2 + 4 * kABytes;
-    static constexpr uint32_t kRing = Cfg<BN>::kStages * Cfg<BN>::kStage;
+    static constexpr uint32_t kStage = Cfg<BN>::kStage;
+    // ring stages: as many as leave room for two CTAs per SM (at least 2, at most 4)
+    static constexpr int kFit = (int)((110u * 1024u) / kStage);
+    static constexpr int kStages = kFit < 2 ? 2 : kFit > 4 ? 4 : kFit;
+    static constexpr uint32_t kPhase2 = 4 * kB2 + 4 * kABytes;  // B2 hi/lo, A2 hi/lo (2 k-blocks each)
+    static constexpr uint32_t kRing = kStages * kStage;
     static constexpr uint32_t kArena = kRing > kPhase2 ? kRing : kPhase2;
-    // phase-1 accumulators: one per compensation product when three fit in TMEM (three
-    // independent MMA chains instead of one latency-bound chain), summed by the drain
-    static constexpr int kAcc1 = 3 * BN <= 512 ? 3 : 1;
-    // phase-2 accumulators: three products x one block, or one per block (at column 256 mb)
-    static constexpr int kAcc2 = kMB == 1 ? 3 : 1;
-    static constexpr int kNeed1 = kAcc1 * BN, kNeed2 = kMB == 1 ? 3 * BN : 256 + BN;
-    static constexpr int kNeed = kNeed1 > kNeed2 ? kNeed1 : kNeed2;
+    // one accumulator per compensation product (three independent MMA chains, summed by the
+    // drains) while three fit in 256 TMEM columns, so that two CTAs share the SM's 512
+    static constexpr int kAcc = 3 * BN <= 256 ? 3 : 1;
+    static constexpr int kNeed = kAcc * BN;
     static constexpr uint32_t kCols = kNeed <= 32 ? 32 : kNeed <= 64 ? 64 : kNeed <= 128 ? 128 : kNeed <= 256 ? 256 : 512;
     static constexpr size_t kSmem = 1024 + (size_t)kArena + 512;
 };
 
 struct SpecOut {
-    int kw;               // window side (kw <= BN / 2)
-    float2* G;            // [slices][kw * kw] partial spectra
+    int kw;               // window side (kw <= BN)
+    float* G;             // [slices][kw][round_up(kw, 16)] partial D2 blocks
 };
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 2)
 k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
            const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
            const __grid_constant__ CUtensorMap tmChi, const __grid_constant__ CUtensorMap tmClo,
            int M, int kb_per_split, int kb_total, int use_alo, const SpecOut so, int* err) {
     using CF = Cfg<BN>;
     using C2 = Cfg2<BN>;
-    constexpr int S = CF::kStages;
+    constexpr int S = C2::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C2::kArena);
     uint64_t* empty = full + S;
     uint64_t* accum = empty + S;
-    uint64_t* a2full = accum + 1;  // [2]
-    uint64_t* acc2 = a2full + 2;   // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc2 + 2);
+    uint64_t* a2full = accum + 1;
+    uint64_t* acc2 = a2full + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc2 + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM;
@@ -267,12 +269,13 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     };
     const uint32_t bytes1 = (use_alo ? 2 : 1) * kABytes + 2 * CF::kBBytes;
     pdl_trigger();
+    const int clip = blockIdx.x;  // clip of a batch: the image maps are 3-D
     auto issue1 = [&](int i) {
         const int s = i % S;
         mbar_arrive_expect_tx(&full[s], bytes1);
         const int kc = (kb0 + i) * kBK;
-        tma_load_2d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0);
-        if (use_alo) tma_load_2d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0);
+        tma_load_3d(&tmAhi, &full[s], stage_ptr(s, 0), kc, m0, clip);
+        if (use_alo) tma_load_3d(&tmAlo, &full[s], stage_ptr(s, 1), kc, m0, clip);
         tma_load_2d(&tmBhi, &full[s], stage_ptr(s, 2), kc, 0);
         tma_load_2d(&tmBlo, &full[s], stage_ptr(s, 3), kc, 0);
     };
@@ -286,10 +289,8 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&a2full[i], 1);
-            mbar_init(&acc2[i], 1);
-        }
+        mbar_init(a2full, 1);
+        mbar_init(acc2, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // B (the DFT table, constant) of the first stages before the previous kernel has
         // finished; A (the image it wrote) after the wait
@@ -301,8 +302,8 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         }
         pdl_wait();
         for (int i = 0; i < npre; ++i) {
-            tma_load_2d(&tmAhi, &full[i], stage_ptr(i, 0), (kb0 + i) * kBK, m0);
-            if (use_alo) tma_load_2d(&tmAlo, &full[i], stage_ptr(i, 1), (kb0 + i) * kBK, m0);
+            tma_load_3d(&tmAhi, &full[i], stage_ptr(i, 0), (kb0 + i) * kBK, m0, clip);
+            if (use_alo) tma_load_3d(&tmAlo, &full[i], stage_ptr(i, 1), (kb0 + i) * kBK, m0, clip);
         }
         issued = npre;
     }
@@ -315,10 +316,8 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     // phase-2 buffers overlay the ring once phase 1 is complete
     uint8_t* B2hi = smem;                 // [2 k-blocks][BN rows][128 B]
     uint8_t* B2lo = smem + 2 * C2::kB2;
-    uint8_t* A2 = smem + 4 * C2::kB2;     // [block][k-block][hi, lo][128 rows][128 B]
-    auto a2_ptr = [&](int mb, int kb, int lo) -> uint8_t* {
-        return A2 + (C2::kA2All ? mb : 0) * 4 * kABytes + (kb * 2 + lo) * kABytes;
-    };
+    uint8_t* A2 = smem + 4 * C2::kB2;     // [k-block][hi, lo][128 rows][128 B]
+    auto a2_ptr = [&](int kb, int lo) -> uint8_t* { return A2 + (kb * 2 + lo) * kABytes; };
     constexpr uint32_t idesc = idesc_bf16(kBM, BN);
 
     // ---------------- phase 1 ----------------
@@ -347,7 +346,7 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             for (int kk = 0; kk < kBK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 32) >> 4;
                 const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-                if (C2::kAcc1 == 3) {
+                if (C2::kAcc == 3) {
                     mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
                     mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
                     if (use_alo) mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
@@ -368,25 +367,23 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     fence_after_sync();
 
     // ---------------- phase 2 ----------------
-    constexpr int kA2Now = C2::kA2All ? C2::kMB : 1;  // blocks of A2 loaded up front
     if (have) {
         // A2 (the ring is idle now)
         if (warp == 0 && lane == 0) {
-            for (int mb = 0; mb < kA2Now; ++mb) {
-                mbar_arrive_expect_tx(&a2full[mb], 4 * kABytes);
-                for (int kb = 0; kb < 2; ++kb) {
-                    tma_load_2d(&tmChi, &a2full[mb], a2_ptr(mb, kb, 0), m0 + kb * kBK, mb * kBM);
-                    tma_load_2d(&tmClo, &a2full[mb], a2_ptr(mb, kb, 1), m0 + kb * kBK, mb * kBM);
-                }
+            mbar_arrive_expect_tx(a2full, 4 * kABytes);
+            for (int kb = 0; kb < 2; ++kb) {
+                tma_load_2d(&tmChi, a2full, a2_ptr(kb, 0), m0 + kb * kBK, 0);
+                tma_load_2d(&tmClo, a2full, a2_ptr(kb, 1), m0 + kb * kBK, 0);
             }
         }
-        // drain D1 (sum of the product accumulators): thread = row y of the tile; write
-        // B2[c][y] as bf16 hi/lo in the 128-byte-swizzled K-major layout
-        const int yl = warp * 32 + lane;
+        // drain D1 (sum of the product accumulators): thread = row y of the tile, warp group
+        // grp = 16-column chunks grp, grp + 2, ...; write B2[c][y] as bf16 hi/lo in the
+        // 128-byte-swizzled K-major layout
+        const int yl = (warp & 3) * 32 + lane, grp = warp >> 2;
         const uint32_t kbo = (uint32_t)(yl >> 6) * C2::kB2;
         const uint32_t chunk = (uint32_t)((yl & 63) >> 3), e2 = (uint32_t)(yl & 7) * 2;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        const int nacc = C2::kAcc1 == 3 ? (use_alo ? 3 : 2) : 1;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int nacc = C2::kAcc == 3 ? (use_alo ? 3 : 2) : 1;
         auto put = [&](uint32_t c2, float x) {
             const uint32_t off = kbo + c2 * 128u + (((chunk ^ (c2 & 7u)) << 4) | e2);
             const __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -394,20 +391,7 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             *reinterpret_cast<__nv_bfloat16*>(B2lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
         };
 #pragma unroll 1
-        for (int c = 0; c + 32 <= BN; c += 32) {
-            uint32_t r[32];
-            tmem_ld32(trow + (uint32_t)c, r);
-            for (int a = 1; a < nacc; ++a) {
-                uint32_t q[32];
-                tmem_ld32(trow + (uint32_t)(a * BN + c), q);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(q[j]));
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) put((uint32_t)(c + j), __uint_as_float(r[j]));
-        }
-        if (BN % 32) {
-            const int c = BN / 32 * 32;
+        for (int c = 16 * grp; c < BN; c += 32) {
             float v[16];
             tmem_ld16(trow + (uint32_t)c, v);
             for (int a = 1; a < nacc; ++a) {
@@ -426,108 +410,71 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
     __syncthreads();
     fence_after_sync();
     if (have && warp == 1 && lane == 0) {
-        // D2 accumulators: kMB == 1: the three products at columns 0, BN, 2 BN;
-        // kMB == 2: one per block at column 256 mb (both blocks' chains interleaved when
-        // their A2 is resident together)
-        bool ok2 = true;
-        for (int g = 0; g < C2::kMB / kA2Now && ok2; ++g) {
-            for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb)
-                if (!mbar_wait(&a2full[mb], 0, err)) ok2 = false;
-            if (!ok2) break;
+        // D2: the three products at TMEM columns 0, BN, 2 BN (or one accumulator)
+        if (mbar_wait(a2full, 0, err)) {
             fence_after_sync();
             for (int kb = 0; kb < 2; ++kb) {
                 const uint64_t dBhi = smem_desc_sw128(smem_u32(B2hi + kb * C2::kB2));
                 const uint64_t dBlo = smem_desc_sw128(smem_u32(B2lo + kb * C2::kB2));
+                const uint64_t dAhi = smem_desc_sw128(smem_u32(a2_ptr(kb, 0)));
+                const uint64_t dAlo = smem_desc_sw128(smem_u32(a2_ptr(kb, 1)));
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                     const uint64_t adv = (uint64_t)(kk * 32) >> 4;
                     const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                    for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb) {
-                        const uint64_t dAhi = smem_desc_sw128(smem_u32(a2_ptr(mb, kb, 0)));
-                        const uint64_t dAlo = smem_desc_sw128(smem_u32(a2_ptr(mb, kb, 1)));
-                        if (C2::kAcc2 == 3) {
-                            mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
-                            mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
-                            mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
-                        } else {
-                            const uint32_t d2 = tmem + (uint32_t)(mb * 256);
-                            mma_bf16(d2, dAhi + adv, dBhi + adv, idesc, acc);
-                            mma_bf16(d2, dAhi + adv, dBlo + adv, idesc, 1u);
-                            mma_bf16(d2, dAlo + adv, dBhi + adv, idesc, 1u);
-                        }
+                    if (C2::kAcc == 3) {
+                        mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
+                        mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
+                        mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
+                    } else {
+                        mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
+                        mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
+                        mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
                     }
                 }
             }
-            for (int mb = g * kA2Now; mb < (g + 1) * kA2Now; ++mb) mma_commit(&acc2[mb]);
-        }
-    }
-    if (have && !C2::kA2All && C2::kMB > 1 && warp == 0 && lane == 0) {
-        // one block at a time: the next block's A2 reuses the buffers once the MMAs are done
-        for (int mb = 1; mb < C2::kMB; ++mb) {
-            if (!mbar_wait(&acc2[mb - 1], 0, err)) break;
-            mbar_arrive_expect_tx(&a2full[mb], 4 * kABytes);
-            for (int kb = 0; kb < 2; ++kb) {
-                tma_load_2d(&tmChi, &a2full[mb], a2_ptr(mb, kb, 0), m0 + kb * kBK, mb * kBM);
-                tma_load_2d(&tmClo, &a2full[mb], a2_ptr(mb, kb, 1), m0 + kb * kBK, mb * kBM);
-            }
+            mma_commit(acc2);
         }
     }
     __syncwarp();
-    // ---- epilogue. Every thread waits for all phase-2 MMAs (they read the shared memory
-    // that D2 is drained into); D2 row c1 = mb * 128 + the lane-row of this warp.
+    // ---- epilogue. Every thread waits for the phase-2 MMAs (they read the shared memory
+    // that D2 is drained into); D2 row c1 = the lane-row of this warp.
     bool h2 = have;
-    for (int mb = 0; mb < C2::kMB; ++mb)
-        if (h2) h2 = mbar_wait(&acc2[mb], 0, err);
-    h2 = __all_sync(0xffffffffu, h2);  // tcgen05.ld below is warp-collective
+    if (h2) h2 = mbar_wait(acc2, 0, err);
+    h2 = __syncthreads_and(h2);
     fence_after_sync();
-    // combine, in rounds over chunks of A row pairs: the rows a in [a0, a0 + A) and kw + a
-    // are drained into shared memory (row pitch kDP, columns < 2 kw), then every thread
-    // forms entries (a, b) = (D2[a][b] - D2[kw+a][kw+b], -(D2[a][kw+b] + D2[kw+a][b])) and
-    // stores them into the CTA's slice of G
-    const int kw = so.kw, E = kw * kw;
-    const int kc = (2 * kw + 15) / 16 * 16;         // drained columns (16-column chunks)
+    const int kw = so.kw;
+    const int kc = (kw + 15) / 16 * 16;               // drained columns (16-column chunks)
     const int kDP = kc + 4;                           // row pitch in floats (16-byte rows)
-    const int A = min(kw, (int)(C2::kArena / (2u * 4u * (unsigned)kDP)));
-    float* Dsm = reinterpret_cast<float*>(smem);     // [2 A][kDP]
-    float2* Gs = so.G + (size_t)(blockIdx.y * gridDim.z + blockIdx.z) * E;
-    for (int a0 = 0; a0 < kw; a0 += A) {
-        const int na = min(A, kw - a0);
-        for (int mb = 0; mb < C2::kMB; ++mb) {
-            const int c1 = mb * kBM + warp * 32 + lane;
-            int r = -1;  // row of c1 in Dsm
-            if (c1 >= a0 && c1 < a0 + na) r = c1 - a0;
-            else if (c1 >= kw + a0 && c1 < kw + a0 + na) r = A + (c1 - kw - a0);
-            if (!__any_sync(0xffffffffu, r >= 0)) continue;  // warp-uniform: no TMEM traffic
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(C2::kAcc2 == 3 ? 0 : mb * 256);
+    float* Dsm = reinterpret_cast<float*>(smem);     // [kw][kDP]
+    float* Gs = so.G + ((size_t)(clip * gridDim.y + blockIdx.y) * gridDim.z + blockIdx.z) * kw * kc;
+    if (h2 && (warp & 3) * 32 < kw) {  // warp-uniform: rows c1 >= kw are not needed
+        const int c1 = (warp & 3) * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < kc; c += 16) {
-                float v[16];
-                if (h2) {
-                    tmem_ld16(trow + (uint32_t)c, v);
-                    for (int q = 1; q < C2::kAcc2; ++q) {
-                        float w[16];
-                        tmem_ld16(trow + (uint32_t)(q * BN + c), w);
+        for (int c = 16 * (warp >> 2); c < kc; c += 32) {
+            float v[16];
+            tmem_ld16(trow + (uint32_t)c, v);
+            for (int q = 1; q < C2::kAcc; ++q) {
+                float w[16];
+                tmem_ld16(trow + (uint32_t)(q * BN + c), w);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] += w[j];
-                    }
-                } else {
+                for (int j = 0; j < 16; ++j) v[j] += w[j];
+            }
+            if (c1 < kw) {
+                float4* d4 = reinterpret_cast<float4*>(Dsm + c1 * kDP + c);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
-                }
-                if (r >= 0) {
-                    float4* d4 = reinterpret_cast<float4*>(Dsm + r * kDP + c);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                }
+                for (int j = 0; j < 4; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             }
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < na * kw; e += blockDim.x) {
-            const int i = e / kw, b = e - i * kw;
-            const float* rc = Dsm + i * kDP;          // row a = a0 + i (cos)
-            const float* rs = Dsm + (A + i) * kDP;    // row kw + a (sin)
-            Gs[(a0 + i) * kw + b] = make_float2(rc[b] - rs[kw + b], -(rc[kw + b] + rs[b]));
+    }
+    __syncthreads();
+    // D2 rows to the slice: a warp per row, a lane per 16-byte column group (kc / 4 <= 32)
+    for (int row = warp; row < kw; row += 8) {
+        if (lane < kc / 4) {
+            const float4 v = h2 ? *reinterpret_cast<const float4*>(Dsm + row * kDP + 4 * lane)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(Gs + (size_t)row * kc)[lane] = v;
         }
-        __syncthreads();
     }
     // a producer that stopped early waits (bounded) for the loads it issued
     if (warp == 0 && lane == 0 && !ok) {
@@ -555,7 +502,10 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
 //   warps 0-3            epilogue: TMEM lanes 32w.. (tile rows), 32 columns at a time,
 //                        scaled, staged in shared memory (128-byte swizzle) and written
 //                        by TMA tensor stores (or plain stores when the output pitch is
-//                        not 16-byte aligned); EPI_VEL also keeps the CTA's max |D|.
+//                        not 16-byte aligned); EPI_VEL also folds each tile's max |D|
+//                        into its clip's word (ep.vbits), and the last CTA converts them.
+// For a batch of clips the tiles run clip by clip (A and C are 3-D maps over the clips;
+// B, the table, is shared).
 template <int BN, int KB>
 struct CfgX {
     static constexpr uint32_t kA = KB * 2 * kABytes;       // A hi/lo, all K
@@ -582,7 +532,7 @@ __global__ void __launch_bounds__(192, 1)
 k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
             const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
             const __grid_constant__ CUtensorMap tmC, int use_tma_store, int M, int N, int ksteps_last,
-            int tiles_n, int tiles, const EpiArgs ep, int* err) {
+            int tiles_m, int tiles_n, int tiles, const EpiArgs ep, int* err) {
     using CX = CfgX<BN, KB>;
     constexpr int S = CX::kS;
     extern __shared__ uint8_t smem_raw[];
@@ -598,8 +548,6 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
     uint64_t* t_empty = t_full + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(t_empty + 2);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    __shared__ int red[4];
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = (int)(((long long)blockIdx.x * tiles) / gridDim.x);
     const int t1 = (int)(((long long)(blockIdx.x + 1) * tiles) / gridDim.x);
@@ -621,9 +569,10 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
                     }
                 }
                 mbar_arrive_expect_tx(a_full, CX::kA);
+                const int clip = mt / tiles_m, my = (mt - clip * tiles_m) * kBM;
                 for (int kb = 0; kb < KB; ++kb) {
-                    tma_load_2d(&tmAhi, a_full, sA + kb * 2 * kABytes, kb * kBK, mt * kBM);
-                    tma_load_2d(&tmAlo, a_full, sA + kb * 2 * kABytes + kABytes, kb * kBK, mt * kBM);
+                    tma_load_3d(&tmAhi, a_full, sA + kb * 2 * kABytes, kb * kBK, my, clip);
+                    tma_load_3d(&tmAlo, a_full, sA + kb * 2 * kABytes + kABytes, kb * kBK, my, clip);
                 }
                 ++p_aload;
                 p_prev_m = mt;
@@ -745,7 +694,8 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
         int ti = 0, chunk = 0;
         const float scale = ep.scale;
         for (int t = t0; t < t1; ++t, ++ti) {
-            const int mt = t / tiles_n, nt = t - mt * tiles_n;
+            const int mg = t / tiles_n, nt = t - mg * tiles_n;   // global row tile: clip * tiles_m + mt
+            const int clip = mg / tiles_m, mt = mg - clip * tiles_m;
             const int buf = ti & 1;
             bool h = mbar_wait_ab(&t_full[buf], (ti >> 1) & 1, err, abort);
             h = __all_sync(0xffffffffu, h);
@@ -798,76 +748,128 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
                     if (lane == 0) {  // boxes entirely outside are not issued; every chunk commits a
                                       // (possibly empty) group, so the wait above always covers the
                                       // store that last read this buffer
-                        if (row0 < M && col0 < N) tma_store_2d(&tmC, stg, col0, row0);
+                        if (row0 < M && col0 < N) tma_store_3d(&tmC, stg, col0, row0, clip);
                         bulk_commit();
                     }
                 } else if (row < M) {
-                    float* dst = ep.C + (size_t)row * ep.ldc + col0;
+                    float* dst = ep.C + clip * ep.split_stride + (size_t)row * ep.ldc + col0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (col0 + j < N) dst[j] = v[j];
                 }
             }
+            if (EPI == EPI_VEL) {
+                // the tile's max |V| into its clip's word (integer max of the bit patterns:
+                // exact and order-independent)
+                for (int o = 16; o > 0; o >>= 1) mxi = max(mxi, __shfl_down_sync(0xffffffffu, mxi, o));
+                if (lane == 0) atomicMax(ep.vbits + clip, (unsigned)mxi);
+                mxi = 0;
+            }
         }
         if (use_tma_store && lane == 0) bulk_wait_all();
-        if (EPI == EPI_VEL) {
-            for (int o = 16; o > 0; o >>= 1) mxi = max(mxi, __shfl_down_sync(0xffffffffu, mxi, o));
-            if (lane == 0) red[warp] = mxi;
-        }
+        if (EPI == EPI_VEL) __threadfence();  // the atomics above before this CTA's arrival
     }
     __syncwarp();
     fence_before_sync();
     __syncthreads();
-    if (EPI == EPI_VEL && threadIdx.x == 0)
-        ep.vpart[blockIdx.x] = __int_as_float(max(max(red[0], red[1]), max(red[2], red[3])));
     if (warp == 5) {
         fence_after_sync();
         tmem_dealloc(tmem, CX::kCols);
     }
-    if (EPI == EPI_VEL) vmax_last_block(ep.vpart, gridDim.x, ep.counter, ep.vmax, ep.status);
+    if (EPI == EPI_VEL) {
+        // the last CTA to finish turns every clip's word into max |V| (FP64), flags a
+        // non-finite value (an inf or NaN pattern is >= 0x7f800000) and clears the words
+        __shared__ bool s_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(ep.counter, 1u) == gridDim.x - 1u;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (int c = threadIdx.x; c < ep.nclips; c += blockDim.x) {
+                const unsigned b = atomicExch(ep.vbits + c, 0u);
+                ep.vmax[c] = (double)__uint_as_float(b);
+                if (b >= 0x7f800000u && ep.status) *ep.status = DEVEL_ENAN;
+            }
+            if (threadIdx.x == 0) *ep.counter = 0u;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Sum of the reduction's slices: out[e] = scale sum_s G[s][e], s in order. Block =
-// 32 entries (lane = entry) x kSumWarps warps; warp w adds slices w, w + kSumWarps, ...
-// (all its loads issued before the adds), then the warps' sums are added in warp order.
+// Sum of the reduction's slices and the complex spectrum. A lane owns one position
+// (j1, j2) in [0, r]^2 of the folded block (block = 32 positions x kSumWarps warps; warp w
+// adds slices w, w + kSumWarps, ... with up to four slices' loads issued before the adds,
+// so 128 slices take one round of loads; then the warps' sums are added in warp order)
+// and sums its four products over the slices:
+//   CC = D2[j1][j2], CS = D2[j1][r + j2], SC = D2[r + j1][j2], SS = D2[r + j1][r + j2]
+// (a sine at |frequency| 0 is absent). With the signs t1, t2 of (u1, u2) = (t1 j1, t2 j2),
+//   out(u1, u2) = scale [(CC - t1 t2 SS) - i (t2 CS + t1 SC)],
+// written for every sign pair (each sign flip taken only for j > 0).
 // ---------------------------------------------------------------------------
-constexpr int kSumWarps = 16;
+constexpr int kSumWarps = 32;
 __global__ void __launch_bounds__(32 * kSumWarps)
-k_spec_sum(const float2* __restrict__ G, int slices, int E, float scale, float2* __restrict__ out) {
-    __shared__ float2 part[kSumWarps][32];
+k_spec_sum(const float* __restrict__ G, int slices, int kw, int kc, float scale, float2* __restrict__ out) {
+    __shared__ float4 part[kSumWarps][32];
     pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * 32 + lane;
-    float re = 0.f, im = 0.f;
-    if (e < E) {
+    const int r = (kw - 1) / 2, np = (r + 1) * (r + 1);
+    const int p = blockIdx.x * 32 + lane;
+    G += (size_t)blockIdx.y * slices * kw * kc;  // clip blockIdx.y of a batch
+    out += (size_t)blockIdx.y * kw * kw;
+    const int j1 = p / (r + 1), j2 = p - j1 * (r + 1);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);  // CC, CS, SC, SS
+    if (p < np) {
+        const size_t E = (size_t)kw * kc;
+        // offsets of the four products (a missing sine reads the cosine entry, weight 0)
+        const size_t o_cc = (size_t)j1 * kc + j2;
+        const size_t o_cs = j2 > 0 ? (size_t)j1 * kc + r + j2 : o_cc;
+        const size_t o_sc = j1 > 0 ? (size_t)(r + j1) * kc + j2 : o_cc;
+        const size_t o_ss = (j1 > 0 && j2 > 0) ? (size_t)(r + j1) * kc + r + j2 : o_cc;
         int sl = w;
-        for (; sl + 7 * kSumWarps < slices; sl += 8 * kSumWarps) {
-            float2 v[8];
+        for (; sl + 3 * kSumWarps < slices; sl += 4 * kSumWarps) {
+            float4 v[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(G + (size_t)(sl + u * kSumWarps) * E + e);
+            for (int u = 0; u < 4; ++u) {
+                const float* g = G + (size_t)(sl + u * kSumWarps) * E;
+                v[u] = make_float4(__ldcg(g + o_cc), __ldcg(g + o_cs), __ldcg(g + o_sc), __ldcg(g + o_ss));
+            }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                re += v[u].x;
-                im += v[u].y;
+            for (int u = 0; u < 4; ++u) {
+                acc.x += v[u].x;
+                acc.y += v[u].y;
+                acc.z += v[u].z;
+                acc.w += v[u].w;
             }
         }
         for (; sl < slices; sl += kSumWarps) {
-            const float2 v = __ldcg(G + (size_t)sl * E + e);
-            re += v.x;
-            im += v.y;
+            const float* g = G + (size_t)sl * E;
+            acc.x += __ldcg(g + o_cc);
+            acc.y += __ldcg(g + o_cs);
+            acc.z += __ldcg(g + o_sc);
+            acc.w += __ldcg(g + o_ss);
         }
     }
-    part[w][lane] = make_float2(re, im);
+    part[w][lane] = acc;
     __syncthreads();
-    if (w != 0 || e >= E) return;
-    float2 t = part[0][lane];
+    if (w != 0 || p >= np) return;
+    float4 t = part[0][lane];
     for (int i = 1; i < kSumWarps; ++i) {
         t.x += part[i][lane].x;
         t.y += part[i][lane].y;
+        t.z += part[i][lane].z;
+        t.w += part[i][lane].w;
     }
-    out[e] = make_float2(t.x * scale, t.y * scale);
+    const float cc = t.x, cs = j2 > 0 ? t.y : 0.f, sc = j1 > 0 ? t.z : 0.f, ss = (j1 > 0 && j2 > 0) ? t.w : 0.f;
+    for (int q = 0; q < 4; ++q) {
+        const int t1 = (q & 2) ? -1 : 1, t2 = (q & 1) ? -1 : 1;
+        if ((t1 < 0 && j1 == 0) || (t2 < 0 && j2 == 0)) continue;
+        const float f1 = (float)t1, f2 = (float)t2;
+        out[(r + t1 * j1) * kw + (r + t2 * j2)] =
+            make_float2((cc - f1 * f2 * ss) * scale, -(f2 * cs + f1 * sc) * scale);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -902,11 +904,12 @@ __global__ void k_split_rows(const float* __restrict__ X, int rows, int cols, in
     }
 }
 
-// 0/1 mask row -> bf16 row of pitch ldo, four pixels per thread.
+// 0/1 mask row -> bf16 row of pitch ldo, four pixels per thread (clip blockIdx.z of a
+// batch: masks n^2 apart, outputs n ldo apart).
 __global__ void k_mask_bf16(const unsigned char* __restrict__ M, int n, int ldo, __nv_bfloat16* __restrict__ hi) {
     const int r = blockIdx.y;
-    const unsigned char* mr = M + (size_t)r * n;
-    __nv_bfloat16* hr = hi + (size_t)r * ldo;
+    const unsigned char* mr = M + (size_t)blockIdx.z * n * n + (size_t)r * n;
+    __nv_bfloat16* hr = hi + (size_t)blockIdx.z * n * ldo + (size_t)r * ldo;
     const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < ldo; c += gridDim.x * blockDim.x * 4) {
 #pragma unroll
@@ -922,12 +925,12 @@ cudaError_t set_attr_bn() {
 }
 
 template <int BN>
-int launch_gemm_bn(const Operands& op, int M, int N, int kb_per_split, int kb_total, int ksteps_last, int splits,
-                   const EpiArgs& ep, int* err, cudaStream_t s) {
+int launch_gemm_bn(const Operands& op, int M, int N, int kb_total, int ksteps_last, int B, const EpiArgs& ep,
+                   int* err, cudaStream_t s) {
     using CF = Cfg<BN>;
-    dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
+    dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, B);
     cudaError_t e = launch_pdl(k_tc_gemm<BN>, grid, dim3(128), CF::kSmem, s, *op.Ahi, *op.Alo, *op.Bhi, *op.Blo, M, N,
-                               kb_per_split, kb_total, ksteps_last, op.use_alo, ep, err);
+                               kb_total, ksteps_last, op.use_alo, ep, err);
     if (e != cudaSuccess) return cuda_error(e, "k_tc_gemm");
     return DEVEL_OK;
 }
@@ -973,16 +976,37 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
     return DEVEL_OK;
 }
 
-// fp32 [rows][cols] output map (pitch ld elements, a multiple of 4): boxes of
-// 32 columns x 32 rows, 128-byte swizzle (the epilogue's staging layout).
-static int make_map_out(CUtensorMap* tm, const float* base, int rows, int cols, int ld) {
+// 3-D bf16 tensor map over depth arrays [rows][cols] (row pitch ld elements), array d at
+// base + d * dld elements: one array per clip of a batch; box = 64 columns x box_rows rows
+// x 1 array, 128-byte swizzle, zero fill (rows past `rows` of an array read as zeros).
+int make_map3(CUtensorMap* tm, const void* base, int depth, int rows, int cols, int ld, size_t dld, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {32, 32};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((size_t)ld * 2) % 16 != 0 || (dld * 2) % 16 != 0 ||
+        box_rows > 256 || depth < 1)
+        return set_error(DEVEL_EINVAL, "tensor map: misaligned base/pitch or box too tall");
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)depth};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)dld * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
+    return DEVEL_OK;
+}
+
+// fp32 output map over depth arrays [rows][cols] (pitch ld elements, a multiple of 4;
+// array d at base + d * dld elements): boxes of 32 columns x 32 rows x 1 array, 128-byte
+// swizzle (the epilogue's staging layout).
+static int make_map_out(CUtensorMap* tm, const float* base, int depth, int rows, int cols, int ld, size_t dld) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)depth};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)dld * 4};
+    cuuint32_t box[3] = {32, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
@@ -998,22 +1022,25 @@ static int sm_count() {
 }
 
 template <int BN, int KB, int EPI>
-static int launch_expand_cfg(const Operands& op, int M, int N, int ksteps_last, const EpiArgs& ep, int* err,
+static int launch_expand_cfg(const Operands& op, int M, int N, int ksteps_last, int B, const EpiArgs& ep, int* err,
                              cudaStream_t s) {
     CUtensorMap tmC;
-    const bool tma_store = (ep.ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(ep.C) & 15u) == 0;
+    const bool tma_store = (ep.ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(ep.C) & 15u) == 0 &&
+                           (ep.split_stride % 4) == 0;
     if (tma_store) {
-        int rc = make_map_out(&tmC, ep.C, M, N, ep.ldc);
+        int rc = make_map_out(&tmC, ep.C, B, M, N, ep.ldc, B > 1 ? ep.split_stride : (size_t)M * ep.ldc);
         if (rc) return rc;
     } else {
         std::memset(&tmC, 0, sizeof(tmC));
     }
-    const int tiles_n = (N + BN - 1) / BN;
-    const int tiles = ((M + kBM - 1) / kBM) * tiles_n;
+    const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
+    const int tiles = B * tiles_m * tiles_n;
     const int grid = std::min(tiles, sm_count());
+    EpiArgs e2 = ep;
+    e2.nclips = B;
     cudaError_t e = launch_pdl(k_tc_expand<BN, KB, EPI>, dim3(grid), dim3(192), CfgX<BN, KB>::kSmem, s, *op.Ahi,
-                               *op.Alo, *op.Bhi, *op.Blo, tmC, tma_store ? 1 : 0, M, N, ksteps_last, tiles_n, tiles,
-                               ep, err);
+                               *op.Alo, *op.Bhi, *op.Blo, tmC, tma_store ? 1 : 0, M, N, ksteps_last, tiles_m, tiles_n,
+                               tiles, e2, err);
     if (e != cudaSuccess) return cuda_error(e, "k_tc_expand");
     return DEVEL_OK;
 }
@@ -1023,7 +1050,7 @@ int expand_grid(int M, int N, int BN) {
     return std::min(tiles, sm_count());
 }
 
-int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, const EpiArgs& ep, int* err,
+int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, int B, const EpiArgs& ep, int* err,
                   cudaStream_t s) {
     const int KB = (K + kBK - 1) / kBK;
     if (K % 16 != 0 || KB < 1 || KB > 4 || (BN != 64 && BN != 128))
@@ -1033,8 +1060,8 @@ int launch_expand(const Operands& op, int BN, int epi, int M, int N, int K, cons
     int rc = DEVEL_OK;
 #define DEVEL_X_CASE(bn, kb)                                                                              \
     if (BN == bn && KB == kb)                                                                             \
-        rc = epi == EPI_VEL ? launch_expand_cfg<bn, kb, EPI_VEL>(op, M, N, ksteps_last, ep, err, s)       \
-                            : launch_expand_cfg<bn, kb, EPI_STORE>(op, M, N, ksteps_last, ep, err, s);
+        rc = epi == EPI_VEL ? launch_expand_cfg<bn, kb, EPI_VEL>(op, M, N, ksteps_last, B, ep, err, s)    \
+                            : launch_expand_cfg<bn, kb, EPI_STORE>(op, M, N, ksteps_last, B, ep, err, s);
     DEVEL_X_CASE(64, 1) DEVEL_X_CASE(64, 2) DEVEL_X_CASE(64, 3) DEVEL_X_CASE(64, 4)
     DEVEL_X_CASE(128, 1) DEVEL_X_CASE(128, 2) DEVEL_X_CASE(128, 3) DEVEL_X_CASE(128, 4)
 #undef DEVEL_X_CASE
@@ -1052,8 +1079,8 @@ static cudaError_t set_attr_expand() {
     return e;
 }
 
-int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, int K, const EpiArgs& ep, int* err,
-                      cudaStream_t s) {
+int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, int K, int B, const EpiArgs& ep,
+                      int* err, cudaStream_t s) {
     if (K % 16 != 0) return set_error(DEVEL_EINVAL, "tc gemm: K=%d not a multiple of 16", K);
     const int kb_total = (K + kBK - 1) / kBK;
     const int ksteps_last = (K - (kb_total - 1) * kBK) / 16;
@@ -1062,7 +1089,7 @@ int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, i
     switch (BN) {
 #define DEVEL_TC_CASE(bn)                                                                            \
     case bn:                                                                                         \
-        rc = launch_gemm_bn<bn>(op, M, N, kb_total, kb_total, ksteps_last, 1, ep, err, s);            \
+        rc = launch_gemm_bn<bn>(op, M, N, kb_total, ksteps_last, B, ep, err, s);                      \
         break;
         DEVEL_TC_CASE(16) DEVEL_TC_CASE(32) DEVEL_TC_CASE(48) DEVEL_TC_CASE(64) DEVEL_TC_CASE(80)
         DEVEL_TC_CASE(96) DEVEL_TC_CASE(112) DEVEL_TC_CASE(128) DEVEL_TC_CASE(144) DEVEL_TC_CASE(160)
@@ -1078,9 +1105,9 @@ int launch_gemm_split(const Operands& op, int BN, int prof_kind, int M, int N, i
 
 template <int BN>
 int launch_spec2_bn(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int M, int kb_per_split,
-                    int kb_total, int splits, SpecOut so, int* err, cudaStream_t s) {
-    dim3 grid(1, (M + kBM - 1) / kBM, splits);
-    cudaError_t e = launch_pdl(k_tc_spec2<BN>, grid, dim3(128), Cfg2<BN>::kSmem, s, *op.Ahi, *op.Alo, *op.Bhi,
+                    int kb_total, int splits, int B, SpecOut so, int* err, cudaStream_t s) {
+    dim3 grid(B, (M + kBM - 1) / kBM, splits);
+    cudaError_t e = launch_pdl(k_tc_spec2<BN>, grid, dim3(256), Cfg2<BN>::kSmem, s, *op.Ahi, *op.Alo, *op.Bhi,
                                *op.Blo, *Chi, *Clo, M, kb_per_split, kb_total, op.use_alo, so, err);
     if (e != cudaSuccess) return cuda_error(e, "k_tc_spec2");
     return DEVEL_OK;
@@ -1094,10 +1121,10 @@ cudaError_t set_attr_spec2() {
 int spectrum2_slices(int M, int K, int split) { return ((M + kBM - 1) / kBM) * ((K + split - 1) / split); }
 
 int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorMap* Clo, int BN, int kw, int n,
-                     int M, int K, int split, float2* G, float2* out, int* err, cudaStream_t s) {
+                     int M, int K, int split, int B, float* G, float2* out, int* err, cudaStream_t s) {
     if (K % kBK != 0 || split % kBK != 0 || split < kBK)
         return set_error(DEVEL_EINVAL, "tc spectrum: K=%d / split %d not multiples of %d", K, split, kBK);
-    if (2 * kw > BN) return set_error(DEVEL_EINVAL, "tc spectrum: window %d wider than half of %d", kw, BN);
+    if (kw > BN) return set_error(DEVEL_EINVAL, "tc spectrum: window %d wider than the table's %d rows", kw, BN);
     const int kb_total = K / kBK, kb_per_split = split / kBK;
     const int splits = (kb_total + kb_per_split - 1) / kb_per_split;
     SpecOut so;
@@ -1108,22 +1135,20 @@ int launch_spectrum2(const Operands& op, const CUtensorMap* Chi, const CUtensorM
     switch (BN) {
 #define DEVEL_SPEC2_CASE(bn)                                                                               \
     case bn:                                                                                               \
-        rc = launch_spec2_bn<bn>(op, Chi, Clo, M, kb_per_split, kb_total, splits, so, err, s);             \
+        rc = launch_spec2_bn<bn>(op, Chi, Clo, M, kb_per_split, kb_total, splits, B, so, err, s);          \
         break;
         DEVEL_SPEC2_CASE(16) DEVEL_SPEC2_CASE(32) DEVEL_SPEC2_CASE(48) DEVEL_SPEC2_CASE(64) DEVEL_SPEC2_CASE(80)
-        DEVEL_SPEC2_CASE(96) DEVEL_SPEC2_CASE(112) DEVEL_SPEC2_CASE(128) DEVEL_SPEC2_CASE(144)
-        DEVEL_SPEC2_CASE(160) DEVEL_SPEC2_CASE(176) DEVEL_SPEC2_CASE(192) DEVEL_SPEC2_CASE(208)
-        DEVEL_SPEC2_CASE(224) DEVEL_SPEC2_CASE(240) DEVEL_SPEC2_CASE(256)
+        DEVEL_SPEC2_CASE(96) DEVEL_SPEC2_CASE(112) DEVEL_SPEC2_CASE(128)
 #undef DEVEL_SPEC2_CASE
         default:
             rc = set_error(DEVEL_EINVAL, "tc spectrum: unsupported window width %d", BN);
     }
     prof_end(PK_TC_SPECTRUM, s);
     if (rc) return rc;
-    const int E = kw * kw, slices = spectrum2_slices(M, K, split);
+    const int slices = spectrum2_slices(M, K, split), r = (kw - 1) / 2, np = (r + 1) * (r + 1);
     prof_begin(PK_SPECTRUM_REDUCE, s);
-    cudaError_t e = launch_pdl(k_spec_sum, dim3((E + 31) / 32), dim3(32 * kSumWarps), 0, s, (const float2*)G, slices,
-                               E, 1.0f / ((float)n * (float)n), out);
+    cudaError_t e = launch_pdl(k_spec_sum, dim3((np + 31) / 32, B), dim3(32 * kSumWarps), 0, s, (const float*)G, slices,
+                               kw, (kw + 15) / 16 * 16, 1.0f / ((float)n * (float)n), out);
     prof_end(PK_SPECTRUM_REDUCE, s);
     if (e != cudaSuccess) return cuda_error(e, "k_spec_sum");
     return DEVEL_OK;
@@ -1146,9 +1171,7 @@ int init_attrs() {
 #undef DEVEL_TC_ATTR
 #define DEVEL_SPEC2_ATTR(bn) if (e == cudaSuccess) e = set_attr_spec2<bn>();
     DEVEL_SPEC2_ATTR(16) DEVEL_SPEC2_ATTR(32) DEVEL_SPEC2_ATTR(48) DEVEL_SPEC2_ATTR(64) DEVEL_SPEC2_ATTR(80)
-    DEVEL_SPEC2_ATTR(96) DEVEL_SPEC2_ATTR(112) DEVEL_SPEC2_ATTR(128) DEVEL_SPEC2_ATTR(144) DEVEL_SPEC2_ATTR(160)
-    DEVEL_SPEC2_ATTR(176) DEVEL_SPEC2_ATTR(192) DEVEL_SPEC2_ATTR(208) DEVEL_SPEC2_ATTR(224) DEVEL_SPEC2_ATTR(240)
-    DEVEL_SPEC2_ATTR(256)
+    DEVEL_SPEC2_ATTR(96) DEVEL_SPEC2_ATTR(112) DEVEL_SPEC2_ATTR(128)
 #undef DEVEL_SPEC2_ATTR
     if (e == cudaSuccess) e = set_attr_expand<64, 1>();
     if (e == cudaSuccess) e = set_attr_expand<64, 2>();
@@ -1171,9 +1194,9 @@ int launch_split(const float* X, int rows, int cols, int ldx, int ldo, __nv_bflo
     return DEVEL_OK;
 }
 
-int launch_mask_bf16(const unsigned char* M, int n, int ldo, __nv_bfloat16* hi, cudaStream_t s) {
+int launch_mask_bf16(const unsigned char* M, int n, int ldo, __nv_bfloat16* hi, cudaStream_t s, int B) {
     prof_begin(PK_TC_SPLIT, s);
-    k_mask_bf16<<<dim3((ldo + 1023) / 1024, n), 256, 0, s>>>(M, n, ldo, hi);
+    k_mask_bf16<<<dim3((ldo + 1023) / 1024, n, B), 256, 0, s>>>(M, n, ldo, hi);
     prof_end(PK_TC_SPLIT, s);
     DEVEL_LAUNCH_CHECK("k_mask_bf16");
     return DEVEL_OK;

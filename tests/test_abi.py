@@ -140,6 +140,21 @@ def test_new_entry_points_refuse_bad_arguments_without_a_device(lib):
     assert lib.devel_shot_count(0, None, None) == dv.DEVEL_EINVAL
     # the shot count is host code: it runs here
     assert dv.devel_shot_count(np.eye(5, dtype=np.uint8)) == 5
+    # the batched solve: a missing handle, batch or params is refused before any device call
+    lib.devel_batch_create.argtypes = [c.c_void_p, c.c_int, c.POINTER(c.c_void_p)]
+    assert lib.devel_batch_create(None, 4, c.byref(h)) == dv.DEVEL_EINVAL
+    assert h.value is None
+    assert lib.devel_batch_create(None, 4, None) == dv.DEVEL_EINVAL
+    lib.devel_batch_destroy.argtypes = [c.c_void_p]
+    assert lib.devel_batch_destroy(None) == dv.DEVEL_OK
+    p = dv.ilt_params(iters=4)
+    lib.devel_ilt_solve_batch.argtypes = [c.POINTER(dv.devel_ilt_params)] + [c.c_void_p, c.c_int, c.c_void_p,
+                                          c.c_void_p, c.c_int] + [c.c_void_p] * 5 + [c.c_int, c.c_void_p, c.c_void_p]
+    assert lib.devel_ilt_solve_batch(c.byref(p), None, 1, 16, 16, 0, None, None, None, None, None, 0, 16,
+                                     None) == dv.DEVEL_EINVAL
+    assert "batch is NULL" in dv.devel_last_error()
+    assert lib.devel_ilt_solve_batch(None, None, 1, 16, 16, 0, None, None, None, None, None, 0, 16,
+                                     None) == dv.DEVEL_EINVAL
 
 
 def test_last_error_is_per_thread(lib):
