@@ -63,7 +63,7 @@ WORKLOADS = {
     # iterations, on 64 held-out 2048^2 clips; a step is one batch of 16 clips through an arm
     "headline2048": dict(headline=True, n=2048, f=4, K=24, k=35, beta=7.5, train=2000, test=64, batch=16,
                          seed_train=10000, seed_test=20000, plain_iters=100, refine_iters=15, width=32,
-                         dsn_batch=16, epochs=4, lr=1e-3, label_handles=32, group=250, band=16.0),
+                         dsn_batch=16, epochs=4, lr=1e-3, group=250, band=16.0),
 }
 METRIC = "ILT clips/sec to converged L2/PVB at 2048^2 (learned+BF16 vs plain FP32); litho TFLOP/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -72,9 +72,9 @@ L2_BYTES = 129 * 1024 * 1024
 # kernels, from the ncu captures summarised under profiles/; a kernel changed since its
 # capture has no entry.
 TRAFFIC = {
-    # profiles/kernels_manhattan2048_bf16x3.md ("DRAM traffic inside the solve"): k_tc_spec2,
-    # the mean of the mask launch (9.47 MB) and the dL/dI launch (18.91 MB)
-    ("tc_spectrum", "bf16x3"): 14.19e6,
+    # DRAM bytes per launch from ncu captures of the current kernels (dram__bytes_read.sum +
+    # dram__bytes_write.sum), keyed (class, precision[, clips per launch]); a kernel that
+    # changes after its capture loses its entry until it is captured again
 }
 
 
@@ -1270,8 +1270,6 @@ def run_headline(args, wl):
     o = synth.optics(n, K, k)
     handles = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3) for _ in range(G)]
     handles32 = [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_FP32) for _ in range(G)]
-    label_h = handles + [dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
-                         for _ in range(wl["label_handles"] - G)]
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     st_any = torch.zeros(1, dtype=torch.int32, device=dev)
     d2 = torch.empty(N, dtype=torch.int32, device=dev)
@@ -1299,12 +1297,11 @@ def run_headline(args, wl):
     y_tr = torch.empty(wl["train"], Nc, dtype=torch.float32, device=dev)
     grp = wl["group"]
     phi_g = torch.empty(grp, N, dtype=torch.float32, device=dev)
-    Wh = (wl["plain_iters"] + 2) // 2 * 2
     lp = dv.ilt_params(dv.resist_params(beta=beta), iters=wl["plain_iters"], use_graph=False)
+    label_bt = dv.Batch(handles[0], grp)  # the label solves, each stage over `group` clips
     for c0 in range(0, wl["train"], grp):
         cnt = min(grp, wl["train"] - c0)
-        clips = [dv.Clip(label_h[i % len(label_h)], tr[c0 + i], phi_g[i]) for i in range(cnt)]
-        dv.devel_ilt_solve(lp, clips, st, stream)
+        dv.devel_ilt_solve_batch(lp, label_bt, tr[c0:c0 + cnt], phi_g[:cnt], st, stream=stream)
         fold_status()
         dv.devel_phi_downsample(n, f, phi_g[:cnt], y_tr[c0:c0 + cnt])
         for i in range(cnt):
@@ -1313,8 +1310,7 @@ def run_headline(args, wl):
     check_status("the label solves")
     t_label = time.perf_counter() - t0 - t_draw
     del tr, phi_g
-    for h in label_h[G:]:
-        dv.devel_optics_destroy(h)
+    label_bt.close()
     Bt = wl["dsn_batch"]
     net = dv.Dsn(m, Bt, wl["width"], seed=1)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -1346,11 +1342,12 @@ def run_headline(args, wl):
     xc = torch.empty(G, Nc, dtype=torch.float32, device=dev)
     pc = torch.empty(G, Nc, dtype=torch.float32, device=dev)
     arms = {}
+    bt = dv.Batch(handles[0], G)  # the BF16x3 arms: every stage launched once over the 16 clips
     for name, hs, iters, learned in (("learned", handles, wl["refine_iters"], True),
                                      ("plain_bf16", handles, wl["plain_iters"], False),
                                      ("plain_fp32", handles32, wl["plain_iters"], False)):
         Wa = (iters + 2) // 2 * 2
-        a = dict(name=name, iters=iters, learned=learned,
+        a = dict(name=name, iters=iters, learned=learned, batched=name != "plain_fp32",
                  phi=torch.empty(G, N, dtype=torch.float32, device=dev),
                  M=torch.empty(G, N, dtype=torch.uint8, device=dev),
                  l2=torch.zeros(G, Wa, dtype=torch.int64, device=dev),
@@ -1369,12 +1366,18 @@ def run_headline(args, wl):
         dv.devel_phi_upsample(n, f, pc, phi, stream)
 
     def step(a, b, from_host=False):
-        """One batch through an arm; the solve is one replay of its captured graph."""
+        """One batch through an arm; the solve is one replay of its captured graph (the
+        BF16x3 arms: devel_ilt_solve_batch; the FP32 comparator: one handle per clip on
+        parallel graph branches)."""
         src = te_host if from_host else te
         tg.copy_(src[b * G:(b + 1) * G], non_blocking=from_host)
         if a["learned"]:
             learned_start(a["phi"])
-        dv.devel_ilt_solve(a["params"], a["clips"], st, stream)
+        if a["batched"]:
+            dv.devel_ilt_solve_batch(a["params"], bt, tg, a["phi"], st, phi_given=a["learned"], mask_out=a["M"],
+                                     l2_hist=a["l2"], pvb_hist=a["pvb"], stream=stream)
+        else:
+            dv.devel_ilt_solve(a["params"], a["clips"], st, stream)
         fold_status()
 
     def time_arm(a, sampler=None):
@@ -1442,7 +1445,7 @@ def run_headline(args, wl):
     e2e_value = world * G * 1000.0 / job_time_ms(float(np.median(e2e_ms)), dist, dev)
 
     # ---- per-kernel device time of the learned step (the library's event profiler, an event
-    # pair around every kernel: shares only; the 16 clips' kernels overlap on the branches)
+    # pair around every kernel: shares only)
     a = arms["learned"]
     Kp = max(3, min(args.steps, 10))
 
@@ -1472,8 +1475,13 @@ def run_headline(args, wl):
         fold_status()
 
     prof1 = profile(solve_one)
-    dom = max(prof1.items(), key=lambda kv: kv[1][1])[0]
-    dom_cnt, dom_ms = profile(solve_one, [dom])[dom]
+    # the roofline: the dominant kernel class of the batched plain BF16x3 step (the hot path
+    # at the workload's scale, every launch over the 16 clips), then that class alone with
+    # events around its launches (its per-launch time)
+    plain = arms["plain_bf16"]
+    profb = profile(lambda i: step(plain, i % nbatch))
+    dom = max(profb.items(), key=lambda kv: kv[1][1])[0]
+    dom_cnt, dom_ms = profile(lambda i: step(plain, i % nbatch), [dom])[dom]
     check_status("the profiled steps")
     if rank == 0:
         hbm, bf16, src = measured_peaks()
@@ -1492,25 +1500,30 @@ def run_headline(args, wl):
                 ent["bytes_per_launch"] = b
             kernels1[kn] = ent
         avg_s = dom_ms / dom_cnt / 1000.0
-        bts = kernel_bytes(dom, n, K, k, True) or 0.0
+        bts = (kernel_bytes(dom, n, K, k, True) or 0.0) * G
         ach = bts / avg_s / 1e9
-        traffic = TRAFFIC.get((dom, "bf16x3"))
+        traffic = TRAFFIC.get((dom, "bf16x3", G))
+        totb = sum(v[1] for v in profb.values())
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "peak_source": src + " (burst copy)", "traffic": traffic,
                 "traffic_over_bytes": traffic / bts if traffic and bts else None,
-                "kernel": dom, "scope": "the dominant kernel class of the level-set ILT hot path (a plain "
-                                        "100-iteration BF16x3 solve of one held-out clip, its kernels alone on "
-                                        "the GPU)",
-                "bytes_per_launch": bts, "launches_per_solve": dom_cnt / Kp, "avg_launch_us": avg_s * 1e6,
-                "share": prof1[dom][1] / tot1,
+                "kernel": dom, "scope": f"the dominant kernel class of the level-set ILT hot path: the batched "
+                                        f"plain 100-iteration BF16x3 solve of {G} held-out clips, each launch "
+                                        f"over all {G}",
+                "bytes_per_launch": bts, "launches_per_step": dom_cnt / Kp, "avg_launch_us": avg_s * 1e6,
+                "share": profb[dom][1] / totb,
+                "kernels_plain_step": {kn: {"launches_per_step": c / Kp, "share": round(t / totb, 4),
+                                            "avg_us_with_events": round(t / c * 1000.0, 2)}
+                                       for kn, (c, t) in sorted(profb.items(), key=lambda kv: -kv[1][1])},
                 "timing": "CUDA events around this kernel class's launches only, recorded inside the solve's "
-                          "graph, over %d solves" % Kp}
+                          "graph, over %d steps" % Kp}
         roof_dsn = None
         if "dsn_conv" in prof:
             c, t = prof["dsn_conv"]
             fl = dsn_forward_flops(m, G, wl["width"])
             ach_t = fl / (t / Kp / 1000.0) / 1e12
-            roof_dsn = {"bound": "tensor", "kernel": "k_conv3_mma (DSN 3x3 convolutions, warp-level BF16 MMA)",
+            roof_dsn = {"bound": "tensor", "kernel": "DSN 3x3 convolutions (k_conv3_tc on tcgen05 for planes "
+                                                     "of side >= 128, k_conv3_mma below)",
                         "achieved": ach_t, "peak": bf16_sus, "unit": "TFLOP/s", "frac": ach_t / bf16_sus,
                         "peak_source": src + " (sustained cuBLAS bf16)", "flops_per_step": fl,
                         "share": t / tot, "timing": "event pairs around every kernel (profiled pass)"}
@@ -1533,7 +1546,9 @@ def run_headline(args, wl):
                        "training": f"{wl['train']} clips labelled by {wl['plain_iters']} plain iterations, "
                                    f"{wl['epochs']} epochs (timed separately, in setup)",
                        "l2": "inputs larger than L2 (16 targets and 16 level sets of 16 MiB per step)",
-                       "parallelism": f"replicas x{world}", "timing": "CUDA events per step, graph replay"},
+                       "parallelism": f"replicas x{world}", "timing": "CUDA events per step, graph replay",
+                       "engine": "BF16x3 arms: devel_ilt_solve_batch (each stage one launch over the 16 clips); "
+                                 "FP32 arm: devel_ilt_solve (one handle per clip, parallel graph branches)"},
             "e2e": {"value": e2e_value, "unit": "clips/s", "h2d_bytes_per_step": G * N,
                     "d2h_bytes_per_step": G * N + 2 * G * 8},
             "gpu_launches": gpu_launches,
@@ -1563,6 +1578,7 @@ def run_headline(args, wl):
         }
         print(json.dumps(out), flush=True)
     pool.close()
+    bt.close()
     for h in handles + handles32:
         dv.devel_optics_destroy(h)
     if dist:

@@ -712,6 +712,8 @@ int devel_optics_create(int n, int K, int k, const float* H_host, const float* w
                 rc = set_error(DEVEL_ECUDA, "devel_optics_create: cudaMemset");
             if (!rc) rc = tc::make_map3(&tw.m_zm_hi, tw.zm_hi, 1, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
             if (!rc) rc = tc::make_map3(&tw.m_zm_lo, tw.zm_lo, 1, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
+            if (!rc) rc = tc::make_map3(&tw.m_zmw_hi, tw.zm_hi, 1, ldf, ldf, ldf, (size_t)ldf * ldf, ldf);
+            if (!rc) rc = tc::make_map3(&tw.m_zmw_lo, tw.zm_lo, 1, ldf, ldf, ldf, (size_t)ldf * ldf, ldf);
             if (!rc) rc = tc::make_map(&tw.m_basisT64_hi, tw.basisT_hi, n, ldf, ldf, 64);
             if (!rc) rc = tc::make_map(&tw.m_basisT64_lo, tw.basisT_lo, n, ldf, ldf, 64);
             if (!rc) rc = tc::make_map3(&tw.m_acat_hi, o->Acat_hi, 1, n, ldf, ldf, (size_t)n * ldf, 128);

@@ -120,6 +120,8 @@ extern "C" int devel_batch_create(const devel_optics* o, int capacity, devel_bat
         const int ldf = tw->ldf;
         if (!rc) rc = tc::make_map3(&tw->m_zm_hi, tw->zm_hi, ci, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
         if (!rc) rc = tc::make_map3(&tw->m_zm_lo, tw->zm_lo, ci, ldf, ldf, ldf, (size_t)ldf * ldf, kTileT);
+        if (!rc) rc = tc::make_map3(&tw->m_zmw_hi, tw->zm_hi, ci, ldf, ldf, ldf, (size_t)ldf * ldf, ldf);
+        if (!rc) rc = tc::make_map3(&tw->m_zmw_lo, tw->zm_lo, ci, ldf, ldf, ldf, (size_t)ldf * ldf, ldf);
         if (!rc) rc = tc::make_map3(&tw->m_acat_hi, v.Acat_hi, ci, ni, ldf, ldf, n * ldf, 128);
         if (!rc) rc = tc::make_map3(&tw->m_acat_lo, v.Acat_lo, ci, ni, ldf, ldf, n * ldf, 128);
     }

@@ -233,7 +233,8 @@ struct TcWindow {
     // (ldf x ldf; written by the Hopkins sums, see put_zm_folded)
     __nv_bfloat16* zm_hi = nullptr;
     __nv_bfloat16* zm_lo = nullptr;
-    CUtensorMap m_zm_hi, m_zm_lo;  // boxes of kTileT rows (the N tile of T = E Z)
+    CUtensorMap m_zm_hi, m_zm_lo;    // boxes of kTileT rows (the N tile of T = E Z)
+    CUtensorMap m_zmw_hi, m_zmw_lo;  // boxes of ldf rows (one N tile over the whole width)
 };
 
 }  // namespace devel

@@ -366,6 +366,31 @@ __global__ void k_avgpool(const bf16* __restrict__ X, int H, int Wd, size_t plan
     }
 }
 
+// The same pooling, four outputs of one row per thread from two 16-byte loads (8 inputs of
+// each of its two input rows), the same sums in the same order; rows = planes * (H / 2),
+// w = Wd / 2 a multiple of 4.
+__global__ void k_avgpool4(const bf16* __restrict__ X, int w, size_t rows, bf16* __restrict__ Y) {
+    const int wq = w >> 2;
+    const size_t count = rows * wq;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / wq;
+        const int q4 = (int)(i - row * wq);
+        const bf16* p0 = X + (2 * row) * (size_t)(2 * w) + 8 * q4;
+        const uint4 a = *reinterpret_cast<const uint4*>(p0);
+        const uint4 b = *reinterpret_cast<const uint4*>(p0 + 2 * w);
+        const bf16* ha = reinterpret_cast<const bf16*>(&a);
+        const bf16* hb = reinterpret_cast<const bf16*>(&b);
+        __align__(8) bf16 o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float sum = (__bfloat162float(ha[2 * j]) + __bfloat162float(ha[2 * j + 1])) +
+                              (__bfloat162float(hb[2 * j]) + __bfloat162float(hb[2 * j + 1]));
+            o[j] = __float2bfloat16_rn(0.25f * sum);
+        }
+        *reinterpret_cast<uint2*>(Y + row * w + 4 * q4) = *reinterpret_cast<const uint2*>(o);
+    }
+}
+
 // dX[2r+i][2q+j] (+)= dY[r][q] / 4
 __global__ void k_avgpool_bwd(const float* __restrict__ dY, int H, int Wd, size_t planes, float* __restrict__ dX,
                               int accumulate) {
@@ -389,6 +414,27 @@ __global__ void k_upsample(const bf16* __restrict__ X, int h, int w, size_t plan
     }
 }
 
+// The same copy, four source pixels of one row per thread (one 8-byte load) into 8 pixels
+// of each of its two output rows (two 16-byte stores); rows = planes * h, w a multiple of 4.
+__global__ void k_upsample4(const bf16* __restrict__ X, int w, size_t rows, bf16* __restrict__ Y) {
+    const int wq = w >> 2;
+    const size_t count = rows * wq;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / wq;
+        const int q4 = (int)(i - row * wq);
+        const uint2 v = *reinterpret_cast<const uint2*>(X + row * w + 4 * q4);
+        const uint32_t p01 = v.x, p23 = v.y;  // bf16 pairs (x0, x1), (x2, x3)
+        uint4 o;
+        o.x = __byte_perm(p01, 0, 0x1010);     // x0 x0
+        o.y = __byte_perm(p01, 0, 0x3232);     // x1 x1
+        o.z = __byte_perm(p23, 0, 0x1010);     // x2 x2
+        o.w = __byte_perm(p23, 0, 0x3232);     // x3 x3
+        bf16* d = Y + (2 * row) * (size_t)(2 * w) + 8 * q4;
+        *reinterpret_cast<uint4*>(d) = o;
+        *reinterpret_cast<uint4*>(d + 2 * w) = o;
+    }
+}
+
 // dX[r][q] = sum of the four dY values it was copied to
 __global__ void k_upsample_bwd(const float* __restrict__ dY, int h, int w, size_t planes, float* __restrict__ dX) {
     const size_t count = planes * h * w;
@@ -401,16 +447,26 @@ __global__ void k_upsample_bwd(const float* __restrict__ dY, int h, int w, size_
     }
 }
 
-// y[n][p] = x[n][p] + b + sum_c w[c] d[n][c][p]
-__global__ void k_head(const float* __restrict__ x, const bf16* __restrict__ d, const float* __restrict__ w,
-                       const float* __restrict__ b, int C, int N, size_t plane, float* __restrict__ y) {
-    const size_t count = (size_t)N * plane;
+// y[n][p] = x[n][p] + b + sum_c w[c] d[n][c][p] (w rounded to BF16, the sum in channel order):
+// eight pixels per thread (one 16-byte load per channel); plane a multiple of 8.
+__global__ void k_head8(const float* __restrict__ x, const bf16* __restrict__ d, const float* __restrict__ w,
+                        const float* __restrict__ b, int C, int N, size_t plane, float* __restrict__ y) {
+    const size_t count = (size_t)N * plane / 8;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t n = i / plane, p = i % plane;
-        float s = b[0];
-        for (int c = 0; c < C; ++c)
-            s = fmaf(__bfloat162float(__float2bfloat16_rn(w[c])), __bfloat162float(d[(n * C + c) * plane + p]), s);
-        y[i] = x[i] + s;
+        const size_t e = 8 * i, n = e / plane, p = e - n * plane;
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = b[0];
+        for (int c = 0; c < C; ++c) {
+            const float wc = __bfloat162float(__float2bfloat16_rn(w[c]));
+            const uint4 v = *reinterpret_cast<const uint4*>(d + (n * C + c) * plane + p);
+            const bf16* h = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = fmaf(wc, __bfloat162float(h[j]), acc[j]);
+        }
+        const float4 x0 = *reinterpret_cast<const float4*>(x + e), x1 = *reinterpret_cast<const float4*>(x + e + 4);
+        *reinterpret_cast<float4*>(y + e) = make_float4(x0.x + acc[0], x0.y + acc[1], x0.z + acc[2], x0.w + acc[3]);
+        *reinterpret_cast<float4*>(y + e + 4) = make_float4(x1.x + acc[4], x1.y + acc[5], x1.z + acc[6], x1.w + acc[7]);
     }
 }
 
@@ -736,8 +792,12 @@ int forward(devel_dsn* d, int nb, cudaStream_t s) {
         const int side = S >> lv;
         const size_t planes = (size_t)nb * w[lv - 1];
         prof_begin(PK_DSN_MISC, s);
-        k_avgpool<<<grid1(planes * side * side), 256, 0, s>>>(A[pin[lv - 1]].a, 2 * side, 2 * side, planes,
-                                                            A[pout[lv - 1]].a);
+        if (side % 4 == 0)
+            k_avgpool4<<<grid1(planes * side * side / 4), 256, 0, s>>>(A[pin[lv - 1]].a, side, planes * side,
+                                                                     A[pout[lv - 1]].a);
+        else
+            k_avgpool<<<grid1(planes * side * side), 256, 0, s>>>(A[pin[lv - 1]].a, 2 * side, 2 * side, planes,
+                                                                A[pout[lv - 1]].a);
         prof_end(PK_DSN_MISC, s);
         rc = conv_fwd(d, 2 * lv, nb, A[pout[lv - 1]].a, w[lv - 1], nullptr, 0, side, A[aa[lv - 1]].a, s);
         if (!rc) rc = conv_fwd(d, 2 * lv + 1, nb, A[aa[lv - 1]].a, w[lv], nullptr, 0, side, A[ss[lv - 1]].a, s);
@@ -749,7 +809,12 @@ int forward(devel_dsn* d, int nb, cudaStream_t s) {
         const int lv = 2 - j, side = S >> lv;
         const size_t planes = (size_t)nb * w[lv + 1];
         prof_begin(PK_DSN_MISC, s);
-        k_upsample<<<grid1(planes * side * side), 256, 0, s>>>(A[prev].a, side / 2, side / 2, planes, A[up[j]].a);
+        if ((side / 2) % 4 == 0)
+            k_upsample4<<<grid1(planes * side * side / 16), 256, 0, s>>>(A[prev].a, side / 2, planes * (side / 2),
+                                                                       A[up[j]].a);
+        else
+            k_upsample<<<grid1(planes * side * side), 256, 0, s>>>(A[prev].a, side / 2, side / 2, planes,
+                                                                 A[up[j]].a);
         prof_end(PK_DSN_MISC, s);
         rc = conv_fwd(d, 8 + 2 * j, nb, A[up[j]].a, w[lv + 1], A[skip[j]].a, w[lv], side, A[da[j]].a, s);
         if (!rc) rc = conv_fwd(d, 9 + 2 * j, nb, A[da[j]].a, w[lv], nullptr, 0, side, A[dd[j]].a, s);
@@ -758,8 +823,8 @@ int forward(devel_dsn* d, int nb, cudaStream_t s) {
     if (rc) return rc;
     const auto& h = d->convs[14];
     prof_begin(PK_DSN_MISC, s);
-    k_head<<<grid1((size_t)nb * S * S), 256, 0, s>>>(d->x, A[D0].a, d->P + h.w_off, d->P + h.b_off, c, nb,
-                                                     (size_t)S * S, d->y);
+    k_head8<<<grid1((size_t)nb * S * S / 8), 256, 0, s>>>(d->x, A[D0].a, d->P + h.w_off, d->P + h.b_off, c, nb,
+                                                          (size_t)S * S, d->y);
     prof_end(PK_DSN_MISC, s);
     DEVEL_LAUNCH_CHECK("dsn forward");
     return DEVEL_OK;

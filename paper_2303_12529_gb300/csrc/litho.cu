@@ -240,17 +240,11 @@ void launch_spec_final(const float* Q, int nq, int ldq, int kw, float2* out, int
 // frequency-domain sums with the rank-K TCC (one warp per output frequency)
 // --------------------------------------------------------------------------
 
-// Fixed-order sums of a float2 over each group of 128 threads (4 warps) of a block of
-// 128 G threads; valid in thread 0 for every group q: (w0 + w1) + (w2 + w3) of its warps.
-template <int G>
-__device__ __forceinline__ void group_sums2_128(float2 v, float2* sh, float2* out) {
-    v = warp_sum2(v);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int q = 0; q < G; ++q) out[q] = cadd(cadd(sh[4 * q], sh[4 * q + 1]), cadd(sh[4 * q + 2], sh[4 * q + 3]));
-}
+// clips per block of the Hopkins sums (each TCC entry loaded once for all of them). The
+// forward sum reads each clip's mhat (k^2 entries, 10 KB at k = 35), so four clips' share
+// L1; the adjoint sum also reads rhat ((2k-1)^2 entries, 38 KB), and one clip per block
+// keeps its working set in L1 (four per block measured 1.4x slower).
+constexpr int kIhatClips = 4, kShatClips = 1;
 
 // Tensor-core path: the four window spectrum entries Z(+-j1, +-j2) folded into the B
 // operand of T = E Z over the folded table (rows c(j) = j: cos, s(j) = r + j: sin), as
@@ -278,134 +272,151 @@ __device__ __forceinline__ void put_zm_folded(__nv_bfloat16* hi, __nv_bfloat16* 
 
 // Ihat(g) = sum_{a in rect(g)} Tdiff[off(g) + t] mhat(a) conj(mhat(a - g)), rect(g) = {a in W :
 // a - g in W}, t = row-major index within rect(g). The aerial image is real, so
-// Ihat(-g) = conj(Ihat(g)): one block per (j1, j2) in [0, r2]^2 whose two halves of 128
-// threads sum g = (j1, j2) and g = (j1, -j2) (the latter when j1, j2 > 0) and write the four
-// entries (+-j1, +-j2), and for the tensor-core path their folded operand entries.
-__device__ __forceinline__ float2 ihat_sum(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
-                                           const float2* __restrict__ mhat, int k, int c1, int c2, int tid) {
-    const int k2 = 2 * k - 1, r2 = k - 1;
-    const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
-    const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
-    const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
-    const float2* T = Tdiff + goff[c1 * k2 + c2];
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int t = tid; t < total; t += 128) {
-        const int i1 = t / n2, i2 = t - i1 * n2;
-        const int a1 = a1lo + i1, a2 = a2lo + i2;
-        const int b1 = a1 - c1 + r2, b2 = a2 - c2 + r2;
-        acc = cadd(acc, cmul(__ldg(T + t), cmulc(__ldg(mhat + a1 * k + a2), __ldg(mhat + b1 * k + b2))));
-    }
-    return acc;
-}
-
+// Ihat(-g) = conj(Ihat(g)): one block per (j1, j2) in [0, r2]^2 and per CB clips of a batch,
+// whose two halves of 128 threads sum g = (j1, j2) and g = (j1, -j2) (the latter when
+// j1, j2 > 0) for each of its clips, every TCC entry loaded once for all of them; thread q
+// then writes clip q's four entries (+-j1, +-j2), and for the tensor-core path their folded
+// operand entries. Each clip's sum runs in the same order whatever CB is.
+template <int CB>
 __global__ void __launch_bounds__(256)
 k_ihat_tcc(const float2* __restrict__ Tdiff, const int* __restrict__ goff,
-           const float2* __restrict__ mhat, int k, float2* __restrict__ Ihat, __nv_bfloat16* __restrict__ zhi,
+           const float2* __restrict__ mhat, int k, int B, float2* __restrict__ Ihat, __nv_bfloat16* __restrict__ zhi,
            __nv_bfloat16* __restrict__ zlo, int ldz) {
-    __shared__ float2 sh[8];
-    __shared__ float2 res[2];
-    const int k2 = 2 * k - 1, r2 = k - 1;
+    __shared__ float2 sh[CB][8];
+    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k;
     const int j1 = blockIdx.x / (r2 + 1), j2 = blockIdx.x - j1 * (r2 + 1);
-    {  // clip blockIdx.y of a batch
-        const size_t c = blockIdx.y;
-        mhat += c * k * k;
-        Ihat += c * k2 * k2;
-        if (zhi) {
-            zhi += c * ldz * ldz;
-            zlo += c * ldz * ldz;
-        }
-    }
+    const int c0 = blockIdx.y * CB, nc = min(CB, B - c0);
     const int half = threadIdx.x >> 7, tid = threadIdx.x & 127;
     const bool two = j1 > 0 && j2 > 0;
     const int c1 = r2 + j1, c2 = half ? r2 - j2 : r2 + j2;
     const bool active = half == 0 || two;
+    const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
+    const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
+    const int n2 = a2hi - a2lo, total = (a1hi - a1lo) * n2;
+    const float2* T = Tdiff + goff[c1 * k2 + c2];
     // the TCC entries (constant) into L2 while the previous kernel finishes
     pdl_trigger();
-    if (active) {
-        const int a1lo = max(0, c1 - r2), a1hi = min(k, c1 - r2 + k);
-        const int a2lo = max(0, c2 - r2), a2hi = min(k, c2 - r2 + k);
-        const float2* T = Tdiff + goff[c1 * k2 + c2];
-        const int total = (a1hi - a1lo) * (a2hi - a2lo);
+    if (active)
         for (int i = tid * 16; i < total; i += 128 * 16) prefetch_l2(T + i);
-    }
     pdl_wait();
-    const float2 acc = active ? ihat_sum(Tdiff, goff, mhat, k, c1, c2, tid) : make_float2(0.f, 0.f);
-    group_sums2_128<2>(acc, sh, res);
-    if (threadIdx.x == 0) {
-        const float2 A = res[0], Ac = make_float2(A.x, -A.y);
+    const float2* mh = mhat + (size_t)c0 * kk;
+    float2 acc[CB];
+#pragma unroll
+    for (int q = 0; q < CB; ++q) acc[q] = make_float2(0.f, 0.f);
+    if (active) {
+#pragma unroll 2
+        for (int t = tid; t < total; t += 128) {
+            const int i1 = t / n2, i2 = t - i1 * n2;
+            const int a1 = a1lo + i1, a2 = a2lo + i2;
+            const int ia = a1 * k + a2, ib = (a1 - c1 + r2) * k + (a2 - c2 + r2);
+            const float2 tv = __ldg(T + t);
+#pragma unroll
+            for (int q = 0; q < CB; ++q)
+                if (q < nc)
+                    acc[q] = cadd(acc[q], cmul(tv, cmulc(__ldg(mh + (size_t)q * kk + ia), __ldg(mh + (size_t)q * kk + ib))));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+        const float2 v = warp_sum2(acc[q]);
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int q = threadIdx.x;
+        const size_t c = (size_t)c0 + q;
+        float2* Ih = Ihat + c * k2 * k2;
+        const float2 A = cadd(cadd(sh[q][0], sh[q][1]), cadd(sh[q][2], sh[q][3]));
+        const float2 Ac = make_float2(A.x, -A.y);
         const int g = c1 * k2 + (r2 + j2);
-        Ihat[g] = A;
-        Ihat[k2 * k2 - 1 - g] = Ac;
-        float2 B = Ac, Bc = Ac;
+        Ih[g] = A;
+        Ih[k2 * k2 - 1 - g] = Ac;
+        float2 Bq = Ac, Bc = Ac;
         if (two) {
-            B = res[1];
-            Bc = make_float2(B.x, -B.y);
+            Bq = cadd(cadd(sh[q][4], sh[q][5]), cadd(sh[q][6], sh[q][7]));
+            Bc = make_float2(Bq.x, -Bq.y);
             const int gb = c1 * k2 + (r2 - j2);
-            Ihat[gb] = B;
-            Ihat[k2 * k2 - 1 - gb] = Bc;
+            Ih[gb] = Bq;
+            Ih[k2 * k2 - 1 - gb] = Bc;
         }
         // Q = Ihat(j1, -j2), R = Ihat(-j1, j2) = conj(Q), T = Ihat(-j1, -j2) = conj(A)
-        if (zhi) put_zm_folded(zhi, zlo, ldz, r2, j1, j2, A, j1 > 0 ? B : Ac, j2 > 0 ? Bc : Ac, Ac);
+        if (zhi)
+            put_zm_folded(zhi + c * ldz * ldz, zlo + c * ldz * ldz, ldz, r2, j1, j2, A, j1 > 0 ? Bq : Ac,
+                          j2 > 0 ? Bc : Ac, Ac);
     }
 }
 
 // Shat(f) = sum_{a in W} conj(TCC[f][a]) mhat(a) rhat(f - a); with a second system (TCC2,
-// rhat2: the defocused corner) its term is added. One block per (j1, j2) in [0, r]^2 whose
-// four groups of 128 threads sum f = (j1, j2), (j1, -j2), (-j1, j2), (-j1, -j2) (each sign
-// flip taken only for j > 0), then write those entries, and for the tensor-core path their
-// folded operand entries.
+// rhat2: the defocused corner) its term is added. One block per (j1, j2) in [0, r]^2 and
+// per CB clips of a batch, whose four groups of 128 threads sum f = (j1, j2), (j1, -j2),
+// (-j1, j2), (-j1, -j2) (each sign flip taken only for j > 0) for each of its clips, every
+// TCC entry loaded once for all of them; thread q then writes clip q's entries, and for the
+// tensor-core path their folded operand entries. Each clip's sum runs in the same order
+// whatever CB is.
+template <int CB>
 __global__ void __launch_bounds__(512)
 k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
-           const float2* __restrict__ rhat, int k, float2* __restrict__ Shat, __nv_bfloat16* __restrict__ zhi,
+           const float2* __restrict__ rhat, int k, int B, float2* __restrict__ Shat, __nv_bfloat16* __restrict__ zhi,
            __nv_bfloat16* __restrict__ zlo, int ldz, const float2* __restrict__ TCC2,
            const float2* __restrict__ rhat2) {
-    __shared__ float2 sh[16];
-    __shared__ float2 res[4];
-    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k, r = (k - 1) / 2;
+    __shared__ float2 sh[CB][16];
+    const int k2 = 2 * k - 1, r2 = k - 1, kk = k * k, r = (k - 1) / 2, kk2 = k2 * k2;
     const int j1 = blockIdx.x / (r + 1), j2 = blockIdx.x - j1 * (r + 1);
-    {  // clip blockIdx.y of a batch
-        const size_t c = blockIdx.y;
-        mhat += c * kk;
-        rhat += c * k2 * k2;
-        if (rhat2) rhat2 += c * k2 * k2;
-        Shat += c * kk;
-        if (zhi) {
-            zhi += c * ldz * ldz;
-            zlo += c * ldz * ldz;
-        }
-    }
-    const int q = threadIdx.x >> 7, tid = threadIdx.x & 127;
-    const int s1 = (q & 2) ? -1 : 1, s2 = (q & 1) ? -1 : 1;
+    const int c0 = blockIdx.y * CB, nc = min(CB, B - c0);
+    const int grp = threadIdx.x >> 7, tid = threadIdx.x & 127;
+    const int s1 = (grp & 2) ? -1 : 1, s2 = (grp & 1) ? -1 : 1;
     const bool active = (s1 > 0 || j1 > 0) && (s2 > 0 || j2 > 0);
     const int f1 = r + s1 * j1, f2 = r + s2 * j2, f = f1 * k + f2;
     const float2* row = TCC + (size_t)f * kk;
+    const float2* row2 = TCC2 ? TCC2 + (size_t)f * kk : nullptr;
     pdl_trigger();
     if (active)
         for (int i = tid * 16; i < kk; i += 128 * 16) {
             prefetch_l2(row + i);
-            if (TCC2) prefetch_l2(TCC2 + (size_t)f * kk + i);
+            if (row2) prefetch_l2(row2 + i);
         }
     pdl_wait();
-    float2 acc = make_float2(0.f, 0.f);
+    const float2* mh = mhat + (size_t)c0 * kk;
+    const float2* rh = rhat + (size_t)c0 * kk2;
+    const float2* rh2 = rhat2 ? rhat2 + (size_t)c0 * kk2 : nullptr;
+    float2 acc[CB];
+#pragma unroll
+    for (int q = 0; q < CB; ++q) acc[q] = make_float2(0.f, 0.f);
     if (active) {
-#pragma unroll 4
+#pragma unroll 2
         for (int a = tid; a < kk; a += 128) {
             const int a1 = a / k, a2 = a - a1 * k;
             const int g = (f1 - a1 + r2) * k2 + (f2 - a2 + r2);
-            const float2 ma = __ldg(mhat + a);
-            acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat + g)), __ldg(row + a)));
-            if (TCC2)  // the defocused system's term (its TCC, its dL/dI spectrum, the same mask)
-                acc = cadd(acc, cmulc(cmul(ma, __ldg(rhat2 + g)), __ldg(TCC2 + (size_t)f * kk + a)));
+            const float2 ta = __ldg(row + a);
+            const float2 tb = row2 ? __ldg(row2 + a) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < CB; ++q)
+                if (q < nc) {
+                    const float2 ma = __ldg(mh + (size_t)q * kk + a);
+                    acc[q] = cadd(acc[q], cmulc(cmul(ma, __ldg(rh + (size_t)q * kk2 + g)), ta));
+                    if (row2)  // the defocused system's term (its TCC, its dL/dI spectrum, the same mask)
+                        acc[q] = cadd(acc[q], cmulc(cmul(ma, __ldg(rh2 + (size_t)q * kk2 + g)), tb));
+                }
         }
     }
-    group_sums2_128<4>(acc, sh, res);
-    if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+        const float2 v = warp_sum2(acc[q]);
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int q = threadIdx.x;
+        const size_t c = (size_t)c0 + q;
+        float2 res[4];
+        for (int g = 0; g < 4; ++g)
+            res[g] = cadd(cadd(sh[q][4 * g], sh[q][4 * g + 1]), cadd(sh[q][4 * g + 2], sh[q][4 * g + 3]));
+        float2* Sh = Shat + c * kk;
         for (int g = 0; g < 4; ++g) {
             const int t1 = (g & 2) ? -1 : 1, t2 = (g & 1) ? -1 : 1;
-            if ((t1 > 0 || j1 > 0) && (t2 > 0 || j2 > 0)) Shat[(r + t1 * j1) * k + (r + t2 * j2)] = res[g];
+            if ((t1 > 0 || j1 > 0) && (t2 > 0 || j2 > 0)) Sh[(r + t1 * j1) * k + (r + t2 * j2)] = res[g];
         }
-        if (zhi) put_zm_folded(zhi, zlo, ldz, r, j1, j2, res[0], res[1], res[2], res[3]);
+        if (zhi) put_zm_folded(zhi + c * ldz * ldz, zlo + c * ldz * ldz, ldz, r, j1, j2, res[0], res[1], res[2], res[3]);
     }
 }
 
@@ -577,8 +588,10 @@ int launch_spectrum_resident(const devel_optics* o, const Window& w, float2* out
 int launch_ihat(const devel_optics* o, cudaStream_t s) {
     prof_begin(PK_HOPKINS, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    cudaError_t e = launch_pdl(k_ihat_tcc, dim3(o->k * o->k, o->batch), dim3(256), 0, s, (const float2*)o->Tdiff,
-                               (const int*)o->goff, (const float2*)o->ws.mhat, o->k, o->ws.Ihat,
+    // one instantiation for every batch size (a clip's arithmetic never depends on it)
+    const int chunks = (o->batch + kIhatClips - 1) / kIhatClips;
+    cudaError_t e = launch_pdl(k_ihat_tcc<kIhatClips>, dim3(o->k * o->k, chunks), dim3(256), 0, s, (const float2*)o->Tdiff, (const int*)o->goff,
+                               (const float2*)o->ws.mhat, o->k, o->batch, o->ws.Ihat,
                                tcp ? o->tcW2.zm_hi : nullptr, tcp ? o->tcW2.zm_lo : nullptr, o->tcW2.ldf);
     prof_end(PK_HOPKINS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_ihat_tcc");
@@ -588,9 +601,10 @@ int launch_ihat(const devel_optics* o, cudaStream_t s) {
 int launch_shat(const devel_optics* o, cudaStream_t s, const devel_optics* od) {
     prof_begin(PK_ADJ_WINDOW, s);
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
-    cudaError_t e = launch_pdl(k_shat_tcc, dim3((o->r + 1) * (o->r + 1), o->batch), dim3(512), 0, s,
-                               (const float2*)o->TCC,
-                               (const float2*)o->ws.mhat, (const float2*)o->ws.rhat, o->k, o->ws.Shat,
+    cudaError_t e = launch_pdl(k_shat_tcc<kShatClips>,
+                               dim3((o->r + 1) * (o->r + 1), (o->batch + kShatClips - 1) / kShatClips),
+                               dim3(512), 0, s, (const float2*)o->TCC, (const float2*)o->ws.mhat,
+                               (const float2*)o->ws.rhat, o->k, o->batch, o->ws.Shat,
                                tcp ? o->tcW.zm_hi : nullptr, tcp ? o->tcW.zm_lo : nullptr, o->tcW.ldf,
                                od ? (const float2*)od->TCC : nullptr, od ? (const float2*)od->ws.rhat : nullptr);
     prof_end(PK_ADJ_WINDOW, s);
@@ -612,13 +626,18 @@ int launch_expand(const devel_optics* o, const float2* Z, const Window& w, int e
         const TcWindow& tw = tc_window(o, w);
         // T = E Z on the tensor cores (Z is in tw.zm, written by the Hopkins sum that
         // produced it), as the bf16 hi/lo operand of the expansion
-        tc::Operands opT{&tw.m_basisT_hi, &tw.m_basisT_lo, &tw.m_zm_hi, &tw.m_zm_lo, 1};
+        // a batch: one CTA per 128 rows and clip spans the whole table width (enough CTAs);
+        // one clip: 16-column tiles, so that its 128-row blocks spread over more SMs
+        const bool wide = o->batch > 1;
+        tc::Operands opT{&tw.m_basisT_hi, &tw.m_basisT_lo, wide ? &tw.m_zmw_hi : &tw.m_zm_hi,
+                         wide ? &tw.m_zmw_lo : &tw.m_zm_lo, 1};
         EpiArgs et;
         et.Chi = o->Acat_hi;
         et.Clo = o->Acat_lo;
         et.ldh = tw.ldf;
         et.split_stride = (size_t)n * tw.ldf;  // clip stride of the operand
-        int rc = tc::launch_gemm_split(opT, kTileT, PK_EXPAND_T, n, tw.ldf, tw.ldf, o->batch, et, o->tc_err, s);
+        int rc = tc::launch_gemm_split(opT, wide ? tw.ldf : kTileT, PK_EXPAND_T, n, tw.ldf, tw.ldf, o->batch, et,
+                                       o->tc_err, s);
         if (rc) return rc;
         const int bn = o->tc_expand_bn;
         tc::Operands op{&tw.m_acat_hi, &tw.m_acat_lo, bn == 64 ? &tw.m_basisT64_hi : &tw.m_basisT_hi,

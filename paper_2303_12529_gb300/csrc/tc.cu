@@ -36,9 +36,10 @@ template <int BN>
 struct Cfg {
     static constexpr uint32_t kBBytes = BN * kBK * 2;
     static constexpr uint32_t kStage = 2 * kABytes + 2 * kBBytes;
-    // as many stages (2..4) as fit in 227 KB of shared memory with the alignment slack
+    // two stages: the GEMM's contraction (a folded table's width, <= 128) is at most two
+    // k-blocks deep, and two or more CTAs then fit on an SM
     static constexpr int kFit = (int)((227u * 1024u - 2048u) / kStage);
-    static constexpr int kStages = kFit > 4 ? 4 : kFit;
+    static constexpr int kStages = kFit > 2 ? 2 : kFit;
     static_assert(kFit >= 2, "tile too wide for double buffering");
     static constexpr uint32_t kCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
