@@ -4,7 +4,7 @@
 //   D[p][co] = sum_{tap, ci} X[ci][y + dy - 1][x + dx - 1] W[co][ci][tap]      (zero padding)
 //
 // with M = 128 output pixels of one image row (x0 .. x0 + 127), N = Cout (32, 64 or 128),
-// and K = 9 taps x Cin channels, 16 channels per MMA. A CTA computes TR (3, 2, 1 for
+// and K = 9 taps x Cin channels, 16 channels per MMA. A CTA computes TR (2, 2, 1 for
 // N = 32, 64, 128) consecutive output rows of one 128-pixel segment; two CTAs share an SM.
 //
 // Operands:
@@ -44,17 +44,39 @@ constexpr int kHaloRows = 136;                      // pixel rows of one halo bl
 constexpr uint32_t kHaloBytes = kHaloRows * 128;    // 17 KiB, a multiple of 1024
 
 // Per output-channel count N: TR output rows per CTA and kBS weight slots, sized so that
-// two CTAs share an SM (one's producer runs while the other's MMAs do).
+// two CTAs share an SM (one's producer runs while the other's MMAs do). For N = 32 the nine
+// taps' weights of a channel block all fit (TR = 2 leaves the room): a tap's MMAs take
+// about a tenth of a TMA round trip, so a ring of a few slots left the MMA issuer waiting
+// for weights (measured: 6.6 us of a 14 us CTA with TR = 3 and four slots).
 template <int N>
 struct CfgC {
-    static constexpr int TR = N == 32 ? 3 : N == 64 ? 2 : 1;
-    static constexpr int kBS = N == 128 ? 3 : 4;
+    static constexpr int TR = N == 128 ? 1 : 2;
+    static constexpr int kBS = N == 32 ? 9 : N == 64 ? 4 : 3;
     static constexpr uint32_t kA = (TR + 2) * kHaloBytes;   // the halo rows of one channel block
     static constexpr uint32_t kB = N * 128;                 // one (channel block, tap) weight box
     static constexpr uint32_t kCols = TR * N <= 32 ? 32 : TR * N <= 64 ? 64 : TR * N <= 128 ? 128 : 256;
     static constexpr size_t kSmem = 1024 + (size_t)kA + (size_t)kBS * kB + 256;
     static_assert(kSmem <= 113 * 1024, "two CTAs per SM");
 };
+
+// The MMAs of one (channel block, tap): TR output rows x KS 16-channel steps, unrolled
+// (compile-time counts: a runtime-bounded issue loop measured about twice the cycles per
+// MMA of a straight run of them).
+template <int N, int TR, int KS>
+__device__ __forceinline__ void conv_tap_mmas(uint32_t tmem, uint32_t stage, uint64_t bdesc, int dy, int dx,
+                                              bool first) {
+    constexpr uint32_t idesc = idesc_bf16(128, N);
+    uint64_t adesc[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) adesc[r] = smem_desc_sw128(stage + (uint32_t)((r + dy) * kHaloBytes + dx * 128));
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int kk = 0; kk < KS; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            mma_bf16(tmem + (uint32_t)(r * N), adesc[r] + adv, bdesc + adv, idesc, (first && kk == 0) ? 0u : 1u);
+        }
+}
 
 template <int N>
 __global__ void __launch_bounds__(192, 2)
@@ -117,11 +139,11 @@ k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int
             const int ci0 = cb * 64, ncg = min(64, Cin - ci0) / 8;
             uint8_t* stage = sA + s * CF::kA;
             const int ntask = (TR + 2) * 18 * ncg;
-            for (int task = t; task < ntask; task += 128) {
+            // two tasks per round (t and t + 128): their sixteen loads are in flight together
+            auto load = [&](int task, uint4 (&v)[8]) {
                 const int cg = task % ncg, rest = task / ncg, g = rest % 18, hr = rest / 18;
                 const int gy = y0 - 1 + hr, gx = x0 - 8 + 8 * g;
-                const bool in = gy >= 0 && gy < H && gx >= 0 && gx + 8 <= Wd;
-                uint4 v[8];
+                const bool in = task < ntask && gy >= 0 && gy < H && gx >= 0 && gx + 8 <= Wd;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int ci = ci0 + cg * 8 + c;
@@ -132,6 +154,10 @@ k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int
                         v[c] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)gy * Wd + gx));
                     }
                 }
+            };
+            auto store = [&](int task, const uint4 (&v)[8]) {
+                const int cg = task % ncg, rest = task / ncg, g = rest % 18, hr = rest / 18;
+                const int gx = x0 - 8 + 8 * g;
                 uint8_t* blk = stage + hr * kHaloBytes;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {  // pixel gx + j: channels cg * 8 .. + 7
@@ -147,6 +173,13 @@ k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int
                     }
                     *reinterpret_cast<uint4*>(blk + p * 128 + ((cg ^ (p & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
                 }
+            };
+            for (int task = t; task < ntask; task += 256) {
+                uint4 va[8], vb[8];
+                load(task, va);
+                load(task + 128, vb);
+                store(task, va);
+                if (task + 128 < ntask) store(task + 128, vb);
             }
             fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
             __syncwarp();
@@ -170,7 +203,6 @@ k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int
     } else {
         // ---------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(128, N);
             int slot = 0;
             bool ok = true;
             for (int cb = 0; cb < ncb && ok; ++cb) {
@@ -190,13 +222,12 @@ k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int
                     }
                     fence_after_sync();
                     const uint64_t bdesc = smem_desc_sw128(smem_u32(sB + sl * CF::kB));
-                    for (int r = 0; r < TR; ++r) {
-                        const uint64_t adesc = smem_desc_sw128(stage + (uint32_t)((r + dy) * kHaloBytes + dx * 128));
-                        for (int kk = 0; kk < ksteps; ++kk) {
-                            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                            mma_bf16(tmem + (uint32_t)(r * N), adesc + adv, bdesc + adv, idesc,
-                                     (cb > 0 || tap > 0 || kk > 0) ? 1u : 0u);
-                        }
+                    const bool first = cb == 0 && tap == 0;
+                    switch (ksteps) {
+                        case 4: conv_tap_mmas<N, TR, 4>(tmem, stage, bdesc, dy, dx, first); break;
+                        case 3: conv_tap_mmas<N, TR, 3>(tmem, stage, bdesc, dy, dx, first); break;
+                        case 2: conv_tap_mmas<N, TR, 2>(tmem, stage, bdesc, dy, dx, first); break;
+                        default: conv_tap_mmas<N, TR, 1>(tmem, stage, bdesc, dy, dx, first); break;
                     }
                     mma_commit(&b_empty[sl]);
                 }

@@ -391,6 +391,64 @@ __global__ void k_avgpool4(const bf16* __restrict__ X, int w, size_t rows, bf16*
     }
 }
 
+// The first convolution (one input channel): Y[n][co] = ReLU(b[co] + sum_tap w[co][tap] X[n]
+// shifted by the tap), zero padding, weights rounded to BF16 as on the tensor-core path,
+// FP32 sums, BF16 output. A thread computes 8 consecutive pixels of one row for every
+// output channel from its 3 x 10 input window (the tensor-core kernels would pad the one
+// channel to 16). side % 8 == 0, Cout <= kC1Max.
+constexpr int kC1Max = 64;
+__global__ void __launch_bounds__(256) k_conv3_c1(const bf16* __restrict__ X, const float* __restrict__ W,
+                                                 const float* __restrict__ bias, int Cout, int side, int nb,
+                                                 bf16* __restrict__ Y) {
+    __shared__ float ws[kC1Max * 9], bs[kC1Max];
+    for (int i = threadIdx.x; i < Cout * 9; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16_rn(W[i]));
+    for (int i = threadIdx.x; i < Cout; i += blockDim.x) bs[i] = bias[i];
+    __syncthreads();
+    const size_t plane = (size_t)side * side;
+    const int q8 = side / 8;
+    const size_t count = (size_t)nb * side * q8;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / q8;                     // n * side + y
+        const int x0 = 8 * (int)(i - row * q8);
+        const size_t n = row / side;
+        const int y = (int)(row - n * side);
+        const bf16* Xn = X + n * plane;
+        float win[3][10];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int yy = y + r - 1;
+            if (yy < 0 || yy >= side) {
+#pragma unroll
+                for (int j = 0; j < 10; ++j) win[r][j] = 0.f;
+                continue;
+            }
+            const bf16* xr = Xn + (size_t)yy * side;
+            const uint4 v = *reinterpret_cast<const uint4*>(xr + x0);
+            const bf16* h = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) win[r][1 + j] = __bfloat162float(h[j]);
+            win[r][0] = x0 > 0 ? __bfloat162float(xr[x0 - 1]) : 0.f;
+            win[r][9] = x0 + 8 < side ? __bfloat162float(xr[x0 + 8]) : 0.f;
+        }
+        bf16* Yr = Y + n * Cout * plane + (size_t)y * side + x0;
+        for (int co = 0; co < Cout; ++co) {
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float wv = ws[co * 9 + t];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] = fmaf(wv, win[t / 3][j + t % 3], acc[j]);
+            }
+            __align__(16) bf16 o[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(fmaxf(acc[j] + bs[co], 0.f));
+            *reinterpret_cast<uint4*>(Yr + co * plane) = *reinterpret_cast<const uint4*>(o);
+        }
+    }
+}
+
 // dX[2r+i][2q+j] (+)= dY[r][q] / 4
 __global__ void k_avgpool_bwd(const float* __restrict__ dY, int H, int Wd, size_t planes, float* __restrict__ dX,
                               int accumulate) {
@@ -711,6 +769,14 @@ void free_dsn(devel_dsn* d) {
 int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, const __nv_bfloat16* XB, int CB, int side,
              __nv_bfloat16* Y, cudaStream_t s) {
     const auto& cv = d->convs[ci];
+    if (cv.cin == 1 && CA == 1 && !XB && side % 8 == 0 && cv.cout <= kC1Max) {
+        prof_begin(PK_DSN_CONV, s);
+        k_conv3_c1<<<grid1((size_t)nb * side * side / 8), 256, 0, s>>>(XA, d->P + cv.w_off, d->P + cv.b_off, cv.cout,
+                                                                       side, nb, Y);
+        prof_end(PK_DSN_CONV, s);
+        DEVEL_LAUNCH_CHECK("k_conv3_c1");
+        return DEVEL_OK;
+    }
     if (cv.Wtc && side == cv.side) {
         prof_begin(PK_DSN_CONV, s);
         const int rc = launch_conv3_tc(XA, CA, XB, CB, cv.mWtc, d->P + cv.b_off, Y, cv.cout, nb, side, s);

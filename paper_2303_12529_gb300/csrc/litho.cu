@@ -383,7 +383,7 @@ k_shat_tcc(const float2* __restrict__ TCC, const float2* __restrict__ mhat,
 #pragma unroll
     for (int q = 0; q < CB; ++q) acc[q] = make_float2(0.f, 0.f);
     if (active) {
-#pragma unroll 2
+#pragma unroll 4
         for (int a = tid; a < kk; a += 128) {
             const int a1 = a / k, a2 = a - a1 * k;
             const int g = (f1 - a1 + r2) * k2 + (f2 - a2 + r2);

@@ -32,6 +32,47 @@ namespace devel {
 namespace tc {
 namespace {
 
+// The compensated products of one 64-wide K slab, KS 16-deep steps, issued as one unrolled
+// run (counts known at compile time: the issuing thread measured about twice the cycles per
+// MMA when a runtime-bounded loop or a runtime branch sat between the MMAs).
+//   ACC3: the three products into accumulators d, d + dstep, d + 2 dstep (summed later),
+//         else all three into d;
+//   ALO:  the A_lo B_hi product (skipped when A is exact in bf16);
+//   first: the first slab of the accumulation (its first step overwrites).
+template <int KS, bool ACC3, bool ALO>
+__device__ __forceinline__ void slab_mmas(uint32_t d, uint32_t dstep, uint64_t dAhi, uint64_t dAlo, uint64_t dBhi,
+                                          uint64_t dBlo, uint32_t idesc, bool first) {
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+        const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        if (ACC3) {
+            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
+            mma_bf16(d + dstep, dAhi + adv, dBlo + adv, idesc, acc);
+            if (ALO) mma_bf16(d + 2 * dstep, dAlo + adv, dBhi + adv, idesc, acc);
+        } else {
+            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
+            mma_bf16(d, dAhi + adv, dBlo + adv, idesc, 1u);
+            if (ALO) mma_bf16(d, dAlo + adv, dBhi + adv, idesc, 1u);
+        }
+    }
+}
+
+// slab_mmas with the step count and the A_lo product chosen at run time (one branch per slab)
+template <bool ACC3>
+__device__ __forceinline__ void slab_mmas_rt(int ks, bool alo, uint32_t d, uint32_t dstep, uint64_t dAhi,
+                                             uint64_t dAlo, uint64_t dBhi, uint64_t dBlo, uint32_t idesc,
+                                             bool first) {
+#define DEVEL_SLAB(k)                                                                               \
+    if (ks == k) {                                                                                  \
+        if (alo) slab_mmas<k, ACC3, true>(d, dstep, dAhi, dAlo, dBhi, dBlo, idesc, first);          \
+        else slab_mmas<k, ACC3, false>(d, dstep, dAhi, dAlo, dBhi, dBlo, idesc, first);             \
+        return;                                                                                     \
+    }
+    DEVEL_SLAB(4) DEVEL_SLAB(3) DEVEL_SLAB(2) DEVEL_SLAB(1)
+#undef DEVEL_SLAB
+}
+
 template <int BN>
 struct Cfg {
     static constexpr uint32_t kBBytes = BN * kBK * 2;
@@ -135,12 +176,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             const uint64_t dAlo = smem_desc_sw128(smem_u32(stage_ptr(s, 1)));
             const uint64_t dBhi = smem_desc_sw128(smem_u32(stage_ptr(s, 2)));
             const uint64_t dBlo = smem_desc_sw128(smem_u32(stage_ptr(s, 3)));
-            for (int kk = 0; kk < ksteps; ++kk) {
-                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
-                mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
-                if (use_alo) mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
-            }
+            slab_mmas_rt<false>(ksteps, use_alo != 0, tmem, 0u, dAhi, dAlo, dBhi, dBlo, idesc, i == 0);
             mma_commit(&empty[s]);
         }
         if (ok) mma_commit(accum);
@@ -344,19 +380,8 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
             const uint64_t dAlo = smem_desc_sw128(smem_u32(stage_ptr(s, 1)));
             const uint64_t dBhi = smem_desc_sw128(smem_u32(stage_ptr(s, 2)));
             const uint64_t dBlo = smem_desc_sw128(smem_u32(stage_ptr(s, 3)));
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-                if (C2::kAcc == 3) {
-                    mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
-                    mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
-                    if (use_alo) mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
-                } else {
-                    mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
-                    mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
-                    if (use_alo) mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
-                }
-            }
+            if (use_alo) slab_mmas<kBK / 16, C2::kAcc == 3, true>(tmem, BN, dAhi, dAlo, dBhi, dBlo, idesc, i == 0);
+            else slab_mmas<kBK / 16, C2::kAcc == 3, false>(tmem, BN, dAhi, dAlo, dBhi, dBlo, idesc, i == 0);
             mma_commit(&empty[s]);
         }
         if (ok) mma_commit(accum);
@@ -414,25 +439,12 @@ k_tc_spec2(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CU
         // D2: the three products at TMEM columns 0, BN, 2 BN (or one accumulator)
         if (mbar_wait(a2full, 0, err)) {
             fence_after_sync();
-            for (int kb = 0; kb < 2; ++kb) {
-                const uint64_t dBhi = smem_desc_sw128(smem_u32(B2hi + kb * C2::kB2));
-                const uint64_t dBlo = smem_desc_sw128(smem_u32(B2lo + kb * C2::kB2));
-                const uint64_t dAhi = smem_desc_sw128(smem_u32(a2_ptr(kb, 0)));
-                const uint64_t dAlo = smem_desc_sw128(smem_u32(a2_ptr(kb, 1)));
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                    if (C2::kAcc == 3) {
-                        mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
-                        mma_bf16(tmem + BN, dAhi + adv, dBlo + adv, idesc, acc);
-                        mma_bf16(tmem + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
-                    } else {
-                        mma_bf16(tmem, dAhi + adv, dBhi + adv, idesc, acc);
-                        mma_bf16(tmem, dAhi + adv, dBlo + adv, idesc, 1u);
-                        mma_bf16(tmem, dAlo + adv, dBhi + adv, idesc, 1u);
-                    }
-                }
-            }
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb)
+                slab_mmas<kBK / 16, C2::kAcc == 3, true>(
+                    tmem, BN, smem_desc_sw128(smem_u32(a2_ptr(kb, 0))), smem_desc_sw128(smem_u32(a2_ptr(kb, 1))),
+                    smem_desc_sw128(smem_u32(B2hi + kb * C2::kB2)), smem_desc_sw128(smem_u32(B2lo + kb * C2::kB2)),
+                    idesc, kb == 0);
             mma_commit(acc2);
         }
     }
@@ -663,19 +675,10 @@ k_tc_expand(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ C
                     const uint64_t dAlo = smem_desc_sw128(smem_u32(sA + kb * 2 * kABytes + kABytes));
                     const uint64_t dBhi = smem_desc_sw128(smem_u32(sB + sl * CX::kSlot));
                     const uint64_t dBlo = smem_desc_sw128(smem_u32(sB + sl * CX::kSlot + CX::kSlab));
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                        if (CX::kAcc == 3) {
-                            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
-                            mma_bf16(d + BN, dAhi + adv, dBlo + adv, idesc, acc);
-                            mma_bf16(d + 2 * BN, dAlo + adv, dBhi + adv, idesc, acc);
-                        } else {
-                            mma_bf16(d, dAhi + adv, dBhi + adv, idesc, acc);
-                            mma_bf16(d, dAhi + adv, dBlo + adv, idesc, 1u);
-                            mma_bf16(d, dAlo + adv, dBhi + adv, idesc, 1u);
-                        }
-                    }
+                    if (ksteps == kBK / 16)
+                        slab_mmas<kBK / 16, CX::kAcc == 3, true>(d, BN, dAhi, dAlo, dBhi, dBlo, idesc, kb == 0);
+                    else
+                        slab_mmas_rt<CX::kAcc == 3>(ksteps, true, d, BN, dAhi, dAlo, dBhi, dBlo, idesc, kb == 0);
                     pending = true;
                     mma_commit(&b_empty[sl]);
                 }
