@@ -39,6 +39,9 @@ WORKLOADS = {
     "uneven64": dict(batch=64, sides=(512, 1024, 1536, 2048), K=24, iters=100, beta=7.5, seed=2000),
     # the same schedule with every clip at 2048^2 (64 full-size clips per call)
     "batch2048": dict(batch=64, sides=(2048,), K=24, iters=100, beta=7.5, seed=2000),
+    # the plain solve at scale without the network: 16 full-size clips, every stage of the
+    # 100 BF16x3 iterations launched once over all 16 (devel_ilt_solve_batch)
+    "batched2048": dict(engine=True, n=2048, K=24, k=35, beta=7.5, iters=100, clips=16, seed=20000),
     # modulation-branch labels (Sec. III-B): per clip a plain solve gives phi_gt, then 16
     # candidate maps H(phi_gt + dh), dh ~ U[-20, 20], each solved (one devel_ilt_solve,
     # one handle per candidate) and the smallest final L_DSO picked
@@ -74,7 +77,9 @@ L2_BYTES = 129 * 1024 * 1024
 TRAFFIC = {
     # DRAM bytes per launch from ncu captures of the current kernels (dram__bytes_read.sum +
     # dram__bytes_write.sum), keyed (class, precision[, clips per launch]); a kernel that
-    # changes after its capture loses its entry until it is captured again
+    # changes after its capture loses its entry until it is captured again.
+    # profiles/kernels_batched2048_levelset.md: 536.9 MB read + 427.3 MB written
+    ("levelset_step", "bf16x3", 16): 964.2e6,
 }
 
 
@@ -320,7 +325,7 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if "batch" in wl and "headline" not in wl:  # the full-size clip's clips/s stands for every side
+    if ("batch" in wl or "engine" in wl) and "headline" not in wl:  # the full-size clip stands for all
         wl = WORKLOADS["manhattan2048"]
     if "learned" in wl or "headline" in wl:  # the oracle has no network: its plain solve of one clip
         base = "manhattan2048" if wl["n"] == 2048 else "rect256"
@@ -1586,6 +1591,136 @@ def run_headline(args, wl):
         dist.destroy_process_group()
 
 
+def run_engine(args, wl):
+    """The batched plain solve: a step is one devel_ilt_solve_batch of `clips` full-size
+    clips (100 BF16x3 iterations from the TSDF of each target, one graph replay), timed with
+    CUDA events over K steps after W warm-up steps; the step's data (16 targets, 16 level
+    sets of 16 MiB and the workspace) is far larger than L2. Reports the per-class kernel
+    shares and the dominant class's roofline (events around its launches only)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_12529_gb300 as dv
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n, K, k, G, iters, beta = wl["n"], wl["K"], wl["k"], wl["clips"], wl["iters"], wl["beta"]
+    if args.clips > 0:
+        G = args.clips
+    N = n * n
+    o = synth.optics(n, K, k)
+    h = dv.devel_optics_create(n, o.H, o.w, dv.DEVEL_PREC_BF16X3)
+    bt = dv.Batch(h, G)
+    seeds = [wl["seed"] + rank * G + i for i in range(G)]  # replicas: disjoint clips per rank
+    tg_host = torch.stack([torch.from_numpy(synth.manhattan_clip(sd).reshape(-1)) for sd in seeds]).pin_memory()
+    tg = tg_host.to(dev)
+    phi = torch.empty(G, N, dtype=torch.float32, device=dev)
+    M = torch.empty(G, N, dtype=torch.uint8, device=dev)
+    Wh = (iters + 2) // 2 * 2
+    l2 = torch.zeros(G, Wh, dtype=torch.int64, device=dev)
+    pvb = torch.zeros(G, Wh, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    p = dv.ilt_params(dv.resist_params(beta=beta), iters=iters, use_graph=True)
+
+    def step():
+        dv.devel_ilt_solve_batch(p, bt, tg, phi, st, mask_out=M, l2_hist=l2, pvb_hist=pvb, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    if int(st.item()) != 0:
+        raise RuntimeError(f"solver status {int(st.item())}")
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = job_time_ms(sum(a.elapsed_time(b) for a, b in ev) / args.steps, dist, dev)
+    # end to end: the targets from pinned host memory, masks and final L2 / PVB back, every step
+    M_host = torch.empty(G, N, dtype=torch.uint8).pin_memory()
+    h_host = torch.empty(2, G, dtype=torch.int64).pin_memory()
+    e2e = []
+    for _ in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tg.copy_(tg_host, non_blocking=True)
+        step()
+        M_host.copy_(M, non_blocking=True)
+        h_host.copy_(torch.stack([l2[:, iters], pvb[:, iters]]), non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1000.0)
+    e2e_ms = job_time_ms(float(np.median(e2e)), dist, dev)
+    if int(st.item()) != 0:
+        raise RuntimeError(f"solver status {int(st.item())}")
+    Kp = max(2, min(args.steps, 5))
+
+    def profile(kinds=None):
+        dv.devel_profile_select(kinds)
+        for r in range(2):  # the first session captures a new graph: discarded
+            dv.devel_profile_start(1 << 18)
+            for _ in range(1 if r == 0 else Kp):
+                step()
+                torch.cuda.synchronize()
+                dv.devel_profile_collect()
+            out = dv.devel_profile_stop(collect=False)
+        dv.devel_profile_select(None)
+        return out
+
+    prof = profile()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    dom_cnt, dom_ms = profile([dom])[dom]
+    if rank == 0:
+        hbm, _, src = measured_peaks()
+        tot = sum(v[1] for v in prof.values())
+        avg_s = dom_ms / dom_cnt / 1000.0
+        bts = (kernel_bytes(dom, n, K, k, True) or 0.0) * G
+        traffic = TRAFFIC.get((dom, "bf16x3", G))
+        ach = bts / avg_s / 1e9
+        out = {
+            "metric": "ILT clips/sec of the plain batched BF16x3 solve at 2048^2", "value": world * G * 1000.0 / ms,
+            "unit": "clips/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "K": K, "k": k, "beta": beta, "iters": iters,
+                       "clips_per_step": G, "engine": "devel_ilt_solve_batch", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (16 targets, 16 level sets of 16 MiB, the batch workspace)"},
+            "e2e": {"value": world * G * 1000.0 / e2e_ms, "unit": "clips/s", "h2d_bytes_per_step": G * N,
+                    "d2h_bytes_per_step": G * N + 2 * G * 8},
+            "gpu_launches": int(round(sum(c for c, _ in prof.values()) / Kp * args.steps)),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "peak_source": src + " (burst copy)", "traffic": traffic,
+                         "traffic_over_bytes": traffic / bts if traffic and bts else None, "kernel": dom,
+                         "bytes_per_launch": bts, "launches_per_step": dom_cnt / Kp,
+                         "avg_launch_us": avg_s * 1e6, "share": prof[dom][1] / tot,
+                         "timing": "CUDA events around this kernel class's launches only, inside the graph"},
+            "kernels": {kn: {"launches_per_step": c / Kp, "share": round(t / tot, 4),
+                             "avg_us_with_events": round(t / c * 1000.0, 2)}
+                        for kn, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "final_mean_l2_pvb": float((l2[:, iters] + pvb[:, iters]).double().mean().item()),
+            "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(out), flush=True)
+    bt.close()
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_calls_once(args, wl):
     """Each ABI call of the hot path once at the workload's size, through the public
     API (TSDF, forward, resist/loss, adjoint, level-set step), for kernel captures with
@@ -1649,6 +1784,8 @@ def main():
     ap.add_argument("--precision", choices=["both", "fp32", "bf16x3"], default="both",
                     help="both: the compensated-BF16 solve is the headline, the plain FP32 solve its comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clips", type=int, default=0,
+                    help="batched2048: clips per step instead of the workload's 16 (a small case for ncu)")
     ap.add_argument("--upwind", choices=["godunov1", "weno5"], default="godunov1",
                     help="one-sided derivatives of the upwind |grad phi| (first order, or WENO5)")
     ap.add_argument("--optimizer", choices=["steepest", "cg"], default="steepest",
@@ -1668,6 +1805,8 @@ def main():
         run_calls_once(args, wl)
     elif "headline" in wl:
         run_headline(args, wl)
+    elif "engine" in wl:
+        run_engine(args, wl)
     elif "batch" in wl:
         run_batched(args, wl)
     elif "labels" in wl:
