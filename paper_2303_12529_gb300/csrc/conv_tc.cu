@@ -4,30 +4,35 @@
 //   D[p][co] = sum_{tap, ci} X[ci][y + dy - 1][x + dx - 1] W[co][ci][tap]      (zero padding)
 //
 // with M = 128 output pixels of one image row (x0 .. x0 + 127), N = Cout (32, 64 or 128),
-// and K = 9 taps x Cin channels, 16 channels per MMA. A CTA computes TR (2, 2, 1 for
-// N = 32, 64, 128) consecutive output rows of one 128-pixel segment; two CTAs share an SM.
+// and K = 9 taps x Cin channels, 16 channels per MMA. A tile is TR = 2 consecutive output
+// rows of one 128-pixel segment; a unit is one tile's 64-channel block.
 //
 // Operands:
-//   A  the input rows y0 - 1 .. y0 + TR, transposed by the producer warps into
-//      shared memory as "halo rows": per input row a 1024-byte-aligned block of 136
-//      pixel rows (pixel x0 - 1 + p at row p), each 128 bytes = 64 channels, in the
-//      128-byte-swizzled K-major layout (16-byte chunk c of row p at ((c ^ (p & 7)) << 4)).
-//      Tap (dy, dx) of output row r reads the 128 rows dx .. dx + 127 of the halo block of
-//      input row r + dy: a descriptor whose start is dx rows into the block. The swizzle
-//      is a function of the shared-memory address (measured on this part: views starting
-//      1, 2 or 7 rows into a 1024-byte pattern read exactly, with the descriptor's base
-//      offset field left 0), so the shifted views need no copy.
-//   B  the weights, prepared as Wtc[cb][tap][co][64] (bf16, channels of block cb,
-//      zero past Cin), one [Cout x 64] box per (channel block, tap), by TMA into a ring.
+//   A  the input rows y0 - 1 .. y0 + TR of a unit as "halo rows": per input row a
+//      1024-byte-aligned block of 136 pixel rows (pixel x0 - 1 + p at row p), each 128
+//      bytes = 64 channels, in the 128-byte-swizzled K-major layout (16-byte chunk c of row
+//      p at ((c ^ (p & 7)) << 4)). Tap (dy, dx) of output row r reads the 128 rows
+//      dx .. dx + 127 of the block of input row r + dy: a descriptor whose start is dx rows
+//      into the block. The swizzle is a function of the shared-memory address (measured on
+//      this part: views starting 1, 2 or 7 rows into a 1024-byte pattern read exactly, with
+//      the descriptor's base offset field left 0), so the shifted views need no copy.
+//   B  the weights, prepared as Wtc[cb][tap][co][64] (bf16, channels of block cb, zero past
+//      Cin), one [Cout x 64] box per (channel block, tap), by TMA: resident for the whole
+//      kernel when all of a layer's boxes fit, else through a ring.
 //
-// Warp roles (192 threads): warps 0-3 fill the halo rows (16-byte loads of 8 pixels along
-// the NCHW planes of 8 channels, transposed in registers into one 16-byte chunk per pixel
-// row) and, after the last MMA, drain TMEM (thread = output pixel) with the
-// bias and ReLU into the NCHW bf16 output; warp 4 lane 0 loads the weights; warp 5
-// lane 0 issues the MMAs. Every mbarrier wait is bounded; after a timeout the CTA stops
+// The halo rows are built on chip: TMA copies the raw NCHW row segments (8 channel planes
+// x 152 pixels from x0 - 8 per box; outside the image the copy fills zeros, which is the
+// padding) into a ring of raw rows, and four warps transpose them with ldmatrix /
+// stmatrix.trans. The kernel is persistent (one CTA per SM over a contiguous range of
+// tiles), warp-specialised, with one mbarrier pair per halo row and per raw-row slot, so
+// that the transposes of a unit's first halo rows overlap the MMAs still reading its
+// predecessor's last ones, and with two TMEM accumulators, so that a tile's epilogue
+// overlaps the next tile's MMAs. Every wait is bounded; after a timeout the CTA stops
 // issuing and writes NaN outputs (which the solve's non-finite checks report).
 #include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "conv_tc.cuh"
@@ -42,232 +47,371 @@ using namespace tc;
 
 constexpr int kHaloRows = 136;                      // pixel rows of one halo block (130 used)
 constexpr uint32_t kHaloBytes = kHaloRows * 128;    // 17 KiB, a multiple of 1024
+constexpr int kStgPx = 152;                         // pixels of a raw row box: x0 - 8 .. x0 + 143
+constexpr uint32_t kStgBox = kStgPx * 8 * 2;        // one box: 8 planes x 152 pixels (19 x 128 B)
+constexpr uint32_t kStgRow = 8 * kStgBox;           // the 64 channels of one raw row (19 KiB)
+constexpr uint32_t kSmemMax = 232448;               // 227 KiB of dynamic shared memory per CTA
 
-// Per output-channel count N: TR output rows per CTA and kBS weight slots, sized so that
-// two CTAs share an SM (one's producer runs while the other's MMAs do). For N = 32 the nine
-// taps' weights of a channel block all fit (TR = 2 leaves the room): a tap's MMAs take
-// about a tenth of a TMA round trip, so a ring of a few slots left the MMA issuer waiting
-// for weights (measured: 6.6 us of a 14 us CTA with TR = 3 and four slots).
+// Per output-channel count N: TR output rows per tile, HR = TR + 2 halo rows, RS raw-row
+// slots, and as many weight "tap rows" (the three boxes of one (channel block, dy), at most
+// 9) as fit beside them in one CTA per SM.
 template <int N>
 struct CfgC {
-    static constexpr int TR = N == 128 ? 1 : 2;
-    static constexpr int kBS = N == 32 ? 9 : N == 64 ? 4 : 3;
-    static constexpr uint32_t kA = (TR + 2) * kHaloBytes;   // the halo rows of one channel block
-    static constexpr uint32_t kB = N * 128;                 // one (channel block, tap) weight box
-    static constexpr uint32_t kCols = TR * N <= 32 ? 32 : TR * N <= 64 ? 64 : TR * N <= 128 ? 128 : 256;
-    static constexpr size_t kSmem = 1024 + (size_t)kA + (size_t)kBS * kB + 256;
-    static_assert(kSmem <= 113 * 1024, "two CTAs per SM");
+    static constexpr int TR = 2;
+    static constexpr int HR = TR + 2;
+    static constexpr int RS = N == 128 ? 3 : 4;
+    static constexpr uint32_t kA = HR * kHaloBytes;
+    static constexpr uint32_t kStg = RS * kStgRow;
+    static constexpr uint32_t kB = N * 128;           // one (channel block, tap) weight box
+    static constexpr uint32_t kFixed = 1024 + kA + kStg + 1024;  // alignment, halo, raw rows, barriers
+    static constexpr int kFit = (int)((kSmemMax - kFixed) / (3 * kB));
+    static constexpr int kRows = kFit > 9 ? 9 : kFit;  // weight tap-row slots
+    static_assert(kFit >= 2, "weight ring too small");
+    static constexpr int kAcc = TR * N;               // TMEM columns of one accumulator
+    static_assert(2 * kAcc <= 512, "two accumulators in TMEM");
+    static constexpr uint32_t kCols = 2 * kAcc <= 32 ? 32 : 2 * kAcc <= 64 ? 64 : 2 * kAcc <= 128 ? 128
+                                    : 2 * kAcc <= 256 ? 256 : 512;
+    static constexpr size_t kSmem = kFixed + (size_t)kRows * 3 * kB;
+    static_assert(kSmem <= kSmemMax, "shared memory");
 };
 
-// The MMAs of one (channel block, tap): TR output rows x KS 16-channel steps, unrolled
-// (compile-time counts: a runtime-bounded issue loop measured about twice the cycles per
-// MMA of a straight run of them).
-template <int N, int TR, int KS>
-__device__ __forceinline__ void conv_tap_mmas(uint32_t tmem, uint32_t stage, uint64_t bdesc, int dy, int dx,
-                                              bool first) {
-    constexpr uint32_t idesc = idesc_bf16(128, N);
-    uint64_t adesc[TR];
-#pragma unroll
-    for (int r = 0; r < TR; ++r) adesc[r] = smem_desc_sw128(stage + (uint32_t)((r + dy) * kHaloBytes + dx * 128));
-#pragma unroll
-    for (int r = 0; r < TR; ++r)
-#pragma unroll
-        for (int kk = 0; kk < KS; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            mma_bf16(tmem + (uint32_t)(r * N), adesc[r] + adv, bdesc + adv, idesc, (first && kk == 0) ? 0u : 1u);
-        }
+// 8x8 b16 matrices between shared memory and registers. ldmatrix: lane 8 m + r gives the
+// address of row r of matrix m, and thread t receives row t / 4, columns 2 (t % 4) .. + 1;
+// stmatrix.trans stores the transpose (lane 8 m + j gives the address of the stored row j,
+// which is column j of the fragment).
+__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&v)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void stsm_x4_trans(uint32_t a, const uint32_t (&v)[4]) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};"
+                 ::"r"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t a, uint32_t (&v)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(a)
+                 : "memory");
+}
+__device__ __forceinline__ void stsm_x2_trans(uint32_t a, const uint32_t (&v)[2]) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(a), "r"(v[0]), "r"(v[1])
+                 : "memory");
 }
 
-template <int N>
-__global__ void __launch_bounds__(192, 2)
-k_conv3_tc(const bf16* __restrict__ XA, int CA, const bf16* __restrict__ XB, int CB,
-           const __grid_constant__ CUtensorMap tmW, const float* __restrict__ bias, bf16* __restrict__ Y, int H,
-           int Wd) {
+// Shared-memory barriers of the kernel (one block; see k_conv3_tc for who arrives where)
+struct ConvBars {
+    uint64_t *st_full, *st_empty, *h_full, *h_empty, *t_full, *t_empty, *mma_done, *w_full, *w_empty;
+};
+
+// Tap row DY of one unit: waits for the halo rows it is the first to read (and, with a
+// weight ring, for its three weight boxes), then 3 taps x TR output rows x KS 16-channel
+// steps of MMAs with every descriptor a compile-time offset from two bases, then commits
+// the halo rows it is the last to read (and its weight slot). Straight-line issue: a
+// runtime loop, switch or branch between tcgen05.mma instructions measured ~60-250 extra
+// cycles per MMA against ~46-64 for a straight run.
+template <int N, int KS, bool RES, int DY>
+__device__ __forceinline__ bool conv_tap_row(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb, uint32_t accf,
+                                             const ConvBars& b, volatile int* abort) {
     using CF = CfgC<N>;
-    constexpr int TR = CF::TR, SA = 1, kBSlots = CF::kBS;
+    constexpr int TR = CF::TR, HR = CF::HR, R = CF::kRows;
+    constexpr int r0 = DY == 0 ? 0 : TR + DY - 1, r1 = TR + DY;  // halo rows first read here
+#pragma unroll
+    for (int hr = r0; hr < r1; ++hr)
+        if (!mbar_wait_ab(&b.h_full[hr], (uint32_t)u & 1u, nullptr, abort)) return false;
+    int slot;
+    if constexpr (RES) {
+        slot = cb * 3 + DY;
+    } else {
+        const int g = u * 3 + DY;
+        slot = g % R;
+        if (!mbar_wait_ab(&b.w_full[slot], (uint32_t)(g / R) & 1u, nullptr, abort)) return false;
+    }
+    fence_after_sync();
+    constexpr uint32_t idesc = idesc_bf16(128, N);
+    const uint64_t a0 = smem_desc_sw128(halo), b0 = smem_desc_sw128(wsm + (uint32_t)slot * 3u * CF::kB);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const uint64_t ad = a0 + (uint64_t)((((r + DY) * kHaloBytes + dx * 128) >> 4) + kk * 2);
+                const uint64_t bd = b0 + (uint64_t)(((dx * CF::kB) >> 4) + kk * 2);
+                mma_bf16(acc + (uint32_t)(r * N), ad, bd, idesc, (DY == 0 && dx == 0 && kk == 0) ? accf : 1u);
+            }
+    if constexpr (!RES) mma_commit(&b.w_empty[slot]);
+    if constexpr (DY < 2) {
+        mma_commit(&b.h_empty[DY]);
+    } else {
+#pragma unroll
+        for (int hr = 2; hr < HR; ++hr) mma_commit(&b.h_empty[hr]);
+    }
+    return true;
+}
+
+template <int N, int KS, bool RES>
+__device__ __forceinline__ bool conv_unit(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb, uint32_t accf,
+                                          const ConvBars& b, volatile int* abort) {
+    return conv_tap_row<N, KS, RES, 0>(acc, halo, wsm, u, cb, accf, b, abort) &&
+           conv_tap_row<N, KS, RES, 1>(acc, halo, wsm, u, cb, accf, b, abort) &&
+           conv_tap_row<N, KS, RES, 2>(acc, halo, wsm, u, cb, accf, b, abort);
+}
+
+// The MMA issuer (one thread): tile i into TMEM accumulator i & 1, its channel blocks in
+// order (the first overwrites the accumulator), then a commit to t_full. With resident
+// weights every tap row's boxes are waited for once, before the first tile.
+template <int N, bool RES>
+__device__ __forceinline__ void conv_mma_role(int T, int ncb, int Cin, uint32_t tmem, uint32_t halo, uint32_t wsm,
+                                              const ConvBars& b, volatile int* abort) {
+    bool ok = true;
+    if constexpr (RES)
+        for (int g = 0; g < 3 * ncb && ok; ++g) ok = mbar_wait_ab(&b.w_full[g], 0u, nullptr, abort);
+    for (int i = 0; i < T && ok; ++i) {
+        const int buf = i & 1;
+        if (i >= 2 && !mbar_wait_ab(&b.t_empty[buf], (uint32_t)((i >> 1) - 1) & 1u, nullptr, abort)) {
+            ok = false;
+            break;
+        }
+        fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(buf * CfgC<N>::kAcc);
+        for (int cb = 0; cb < ncb && ok; ++cb) {
+            const int u = i * ncb + cb;
+            const uint32_t accf = cb == 0 ? 0u : 1u;
+            switch (min(64, Cin - cb * 64) / 16) {
+                case 4: ok = conv_unit<N, 4, RES>(acc, halo, wsm, u, cb, accf, b, abort); break;
+                case 3: ok = conv_unit<N, 3, RES>(acc, halo, wsm, u, cb, accf, b, abort); break;
+                case 2: ok = conv_unit<N, 2, RES>(acc, halo, wsm, u, cb, accf, b, abort); break;
+                default: ok = conv_unit<N, 1, RES>(acc, halo, wsm, u, cb, accf, b, abort); break;
+            }
+        }
+        if (ok) mma_commit(&b.t_full[buf]);
+    }
+    mma_commit(b.mma_done);  // also after a failure: the MMAs in flight complete before TMEM is freed
+    mbar_wait(b.mma_done, 0, nullptr);
+}
+
+// Persistent, warp-specialised. CTA b takes the contiguous tiles [t0, t1) of the list
+// (image n, row group, 128-pixel segment), n-major, and each tile's ceil(Cin / 64) channel
+// blocks in order (units u = 0 .. U - 1); raw row k = HR u + hr is halo row hr of unit u.
+// Roles (320 threads):
+//   warp 8, lane 0   TMA, polling two queues: raw row k into slot k % RS once the
+//                    transposers have emptied the slot, and the weights by tap row (the
+//                    three boxes of one (channel block, dy)): all at the start when
+//                    resident, else one tap row per (unit, dy) into a ring slot the MMAs
+//                    have released;
+//   warps 4-7        halo row hr of unit u from raw row k, once the MMAs of unit u - 1 have
+//                    released that halo row (rows 0 and 1 after their taps dy = 0 and 1,
+//                    the others after the last tap);
+//   warp 9, lane 0   the MMAs of a tile into TMEM accumulator i & 1 (tile i), tap row dy as
+//                    soon as halo rows dy .. dy + TR - 1 of the unit are in (conv_mma_role);
+//   warps 0-3        a tile's epilogue (TMEM lane = pixel; bias, ReLU, bf16 NCHW stores)
+//                    while the next tile's MMAs run.
+template <int N>
+__global__ void __launch_bounds__(320, 1)
+k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUtensorMap tmXB, int CA, int CB,
+           const __grid_constant__ CUtensorMap tmW, const float* __restrict__ bias, bf16* __restrict__ Y, int H,
+           int Wd, int nb, int pb) {
+    using CF = CfgC<N>;
+    constexpr int TR = CF::TR, HR = CF::HR, RS = CF::RS, R = CF::kRows;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;                          // [SA][TR + 2][kHaloRows][128 B]
-    uint8_t* sB = smem + SA * CF::kA;            // [kBSlots][N][128 B]
-    uint64_t* a_full = reinterpret_cast<uint64_t*>(sB + kBSlots * CF::kB);
-    uint64_t* a_empty = a_full + SA;
-    uint64_t* b_full = a_empty + SA;
-    uint64_t* b_empty = b_full + kBSlots;
-    uint64_t* acc_full = b_empty + kBSlots;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+    uint8_t* sA = smem;                    // [HR][kHaloRows][128 B] halo rows
+    uint8_t* sS = sA + CF::kA;             // [RS][8 channel groups][8 planes][152 px] raw rows
+    uint8_t* misc = sS + CF::kStg;         // barriers, TMEM address, abort flag, dummy rows
+    uint8_t* sB = misc + 1024;             // [R][3 taps][N][128 B] weight boxes
+    uint64_t* st_full = reinterpret_cast<uint64_t*>(misc);  // [RS]
+    uint64_t* st_empty = st_full + 4;      // [RS]
+    uint64_t* h_full = st_full + 8;        // [HR]
+    uint64_t* h_empty = st_full + 12;      // [HR]
+    uint64_t* t_full = st_full + 16;       // [2]
+    uint64_t* t_empty = st_full + 18;      // [2]
+    uint64_t* mma_done = st_full + 20;
+    uint64_t* w_full = st_full + 21;       // [R]
+    uint64_t* w_empty = w_full + R;        // [R]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(w_empty + R);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint8_t* dummy = misc + 896;           // 8 x 16 B: stored matrix rows that fall outside a halo block
+    static_assert(HR <= 4 && RS <= 4 && (21 + 2 * R) * 8 + 8 <= 896, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * TR, n = blockIdx.z;
     const int Cin = CA + CB, ncb = (Cin + 63) / 64;
+    const bool resident = 3 * ncb <= R;    // every weight box of the layer stays in shared memory
+    const int segs = (Wd + 127) / 128, rgroups = (H + TR - 1) / TR;
+    const long long tiles = (long long)nb * rgroups * segs;
+    const int t0 = (int)(tiles * blockIdx.x / gridDim.x), t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
+    const int T = t1 - t0, U = T * ncb;
     const size_t plane = (size_t)H * Wd;
+    auto tile_of = [&](int t, int& n, int& y0, int& x0) {
+        x0 = (t % segs) * 128;
+        const int r = t / segs;
+        y0 = (r % rgroups) * TR;
+        n = r / rgroups;
+    };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SA; ++s) {
-            mbar_init(&a_full[s], 4);  // one arrival per producer warp
-            mbar_init(&a_empty[s], 1);
+        for (int i = 0; i < RS; ++i) {
+            mbar_init(&st_full[i], 1);
+            mbar_init(&st_empty[i], 4);  // one arrival per transposing warp
         }
-        for (int s = 0; s < kBSlots; ++s) {
-            mbar_init(&b_full[s], 1);
-            mbar_init(&b_empty[s], 1);
+        for (int i = 0; i < HR; ++i) {
+            mbar_init(&h_full[i], 4);
+            mbar_init(&h_empty[i], 1);   // MMA commit
         }
-        mbar_init(acc_full, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(mma_done, 1);
+        for (int i = 0; i < R; ++i) {
+            mbar_init(&w_full[i], 1);
+            mbar_init(&w_empty[i], 1);
+        }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) tmem_alloc(tmem_slot, CF::kCols);
+    if (warp == 9) tmem_alloc(tmem_slot, CF::kCols);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 4) {
-        // ---------------- producer: halo rows of channel block cb into stage cb % SA
-        const int t = threadIdx.x;  // pixel rows t and t + 128 (< 130)
-        bool ok = true;
-        for (int cb = 0; cb < ncb && ok; ++cb) {
-            const int s = cb % SA;
-            if (cb >= SA) {
-                ok = mbar_wait_ab(&a_empty[s], ((cb / SA) - 1) & 1, nullptr, abort);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
+    if (warp == 8) {
+        // ---------------- TMA: raw rows and weight boxes
+        if (lane == 0 && U > 0) {
+            const int rows = U * HR, wtot = resident ? 3 * ncb : 3 * U;
+            int k = 0, ws = 0;
+            bool idle = false;
+            unsigned long long t_idle = 0;
+            while (k < rows || ws < wtot) {
+                bool prog = false;
+                if (k < rows && (k < RS || mbar_test_wait(&st_empty[k % RS], (uint32_t)((k / RS) - 1) & 1u))) {
+                    const int u = k / HR, hr = k % HR, cb = u % ncb, ci0 = cb * 64, ncg = min(64, Cin - ci0) / 8;
+                    int n, y0, x0;
+                    tile_of(t0 + u / ncb, n, y0, x0);
+                    uint8_t* dst = sS + (k % RS) * kStgRow;
+                    mbar_arrive_expect_tx(&st_full[k % RS], (uint32_t)ncg * kStgBox);
+                    for (int g = 0; g < ncg; g += pb / 8) {  // boxes of pb planes (8 or 32)
+                        const int ci = ci0 + 8 * g;
+                        if (ci < CA) tma_load_3d(&tmXA, &st_full[k % RS], dst + g * kStgBox, x0 - 8, y0 - 1 + hr, n * CA + ci);
+                        else tma_load_3d(&tmXB, &st_full[k % RS], dst + g * kStgBox, x0 - 8, y0 - 1 + hr, n * CB + (ci - CA));
+                    }
+                    ++k;
+                    prog = true;
+                }
+                if (ws < wtot && (resident || ws < R || mbar_test_wait(&w_empty[ws % R], (uint32_t)((ws / R) - 1) & 1u))) {
+                    // tap row ws: (channel block, dy) = (ws / 3, ws % 3) resident, else
+                    // (unit ws / 3, dy ws % 3); its boxes are 9 cb + 3 dy + dx
+                    const int sl = resident ? ws : ws % R;
+                    const int box = resident ? 3 * ws : ((ws / 3) % ncb) * 9 + (ws % 3) * 3;
+                    mbar_arrive_expect_tx(&w_full[sl], 3 * CF::kB);
+                    for (int dx = 0; dx < 3; ++dx)
+                        tma_load_2d(&tmW, &w_full[sl], sB + (sl * 3 + dx) * CF::kB, 0, (box + dx) * N);
+                    ++ws;
+                    prog = true;
+                }
+                if (prog) {
+                    idle = false;
+                } else if (!idle) {
+                    idle = true;
+                    t_idle = globaltimer();
+                } else if (*abort || globaltimer() - t_idle > kWaitNs) {
+                    *abort = 1;
+                    break;
+                }
             }
-            // tasks: (halo row, 8-pixel group, 8-channel group); a group of 8 aligned pixels
-            // x0 - 8 + 8 g (g < 18) covers the halo columns x0 - 1 .. x0 + 128. Per task eight
-            // 16-byte loads (eight channels, along the NCHW planes), an 8 x 8 transpose by
-            // byte permutes, and one 16-byte store per halo pixel row.
-            const int ci0 = cb * 64, ncg = min(64, Cin - ci0) / 8;
-            uint8_t* stage = sA + s * CF::kA;
-            const int ntask = (TR + 2) * 18 * ncg;
-            // two tasks per round (t and t + 128): their sixteen loads are in flight together
-            auto load = [&](int task, uint4 (&v)[8]) {
-                const int cg = task % ncg, rest = task / ncg, g = rest % 18, hr = rest / 18;
-                const int gy = y0 - 1 + hr, gx = x0 - 8 + 8 * g;
-                const bool in = task < ntask && gy >= 0 && gy < H && gx >= 0 && gx + 8 <= Wd;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int ci = ci0 + cg * 8 + c;
-                    v[c] = make_uint4(0u, 0u, 0u, 0u);
-                    if (in) {
-                        const bf16* src = ci < CA ? XA + ((size_t)n * CA + ci) * plane
-                                                  : XB + ((size_t)n * CB + (ci - CA)) * plane;
-                        v[c] = __ldg(reinterpret_cast<const uint4*>(src + (size_t)gy * Wd + gx));
-                    }
+            if (*abort) {  // the copies still in flight land before the CTA exits (bounded waits)
+                for (int j = max(0, k - RS); j < k; ++j) mbar_wait(&st_full[j % RS], (uint32_t)(j / RS) & 1u, nullptr);
+                for (int j = resident ? 0 : max(0, ws - R); j < ws; ++j)
+                    mbar_wait(&w_full[resident ? j : j % R], resident ? 0u : (uint32_t)(j / R) & 1u, nullptr);
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- halo rows from raw rows: 8 planes x 8 pixels per matrix
+        const int tw = warp - 4, m = lane >> 3, r = lane & 7;
+        for (int k = 0; k < U * HR; ++k) {
+            const int u = k / HR, hr = k % HR, cb = u % ncb, ncg = min(64, Cin - cb * 64) / 8;
+            bool w = mbar_wait_ab(&st_full[k % RS], (uint32_t)(k / RS) & 1u, nullptr, abort);
+            if (w && u > 0) w = mbar_wait_ab(&h_empty[hr], (uint32_t)(u - 1) & 1u, nullptr, abort);
+            if (!__all_sync(0xffffffffu, w)) break;
+            const uint8_t* raw = sS + (k % RS) * kStgRow;
+            uint8_t* blk = sA + hr * kHaloBytes;
+            // items (channel group g, part): parts 0-3 transpose pixel blocks 4 part + m
+            // (x4), part 4 blocks 16 and 17 (x2); pixel block b holds pixels x0 - 8 + 8 b ..,
+            // stored at halo row p = 8 b + j - 7 (rows outside 0 .. 135 go to the dummy rows)
+            for (int it = tw; it < ncg * 5; it += 4) {
+                const int part = it % 5, g = it / 5;
+                const int b = part < 4 ? 4 * part + m : 16 + (m & 1);
+                const uint32_t la = smem_u32(raw + g * kStgBox + r * (kStgPx * 2) + b * 16);
+                const int p = 8 * b + r - 7;
+                const uint32_t sa = (p >= 0 && p < kHaloRows)
+                                        ? smem_u32(blk + p * 128 + (((uint32_t)g ^ (uint32_t)(p & 7)) << 4))
+                                        : smem_u32(dummy + r * 16);
+                if (part < 4) {
+                    uint32_t v[4];
+                    ldsm_x4(la, v);
+                    stsm_x4_trans(sa, v);
+                } else {
+                    uint32_t v[2];
+                    ldsm_x2(la, v);
+                    stsm_x2_trans(sa, v);
                 }
-            };
-            auto store = [&](int task, const uint4 (&v)[8]) {
-                const int cg = task % ncg, rest = task / ncg, g = rest % 18, hr = rest / 18;
-                const int gx = x0 - 8 + 8 * g;
-                uint8_t* blk = stage + hr * kHaloBytes;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {  // pixel gx + j: channels cg * 8 .. + 7
-                    const int p = gx + j - (x0 - 1);
-                    if (p < 0 || p >= 130) continue;
-                    const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;
-                    uint32_t o[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t* a = reinterpret_cast<const uint32_t*>(&v[2 * k]);
-                        const uint32_t* b = reinterpret_cast<const uint32_t*>(&v[2 * k + 1]);
-                        o[k] = __byte_perm(a[j >> 1], b[j >> 1], sel);
-                    }
-                    *reinterpret_cast<uint4*>(blk + p * 128 + ((cg ^ (p & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
-                }
-            };
-            for (int task = t; task < ntask; task += 256) {
-                uint4 va[8], vb[8];
-                load(task, va);
-                load(task + 128, vb);
-                store(task, va);
-                if (task + 128 < ntask) store(task + 128, vb);
             }
             fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
             __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[s]);
-        }
-    } else if (warp == 4) {
-        // ---------------- weights: one [N x 64] box per (channel block, tap)
-        if (lane == 0) {
-            int slot = 0;
-            for (int cb = 0; cb < ncb; ++cb) {
-                for (int tap = 0; tap < 9; ++tap, ++slot) {
-                    const int sl = slot % kBSlots;
-                    if (slot >= kBSlots && !mbar_wait_ab(&b_empty[sl], ((slot / kBSlots) - 1) & 1, nullptr, abort))
-                        goto weights_done;
-                    mbar_arrive_expect_tx(&b_full[sl], CF::kB);
-                    tma_load_2d(&tmW, &b_full[sl], sB + sl * CF::kB, 0, (cb * 9 + tap) * N);
-                }
+            if (lane == 0) {
+                mbar_arrive(&h_full[hr]);
+                mbar_arrive(&st_empty[k % RS]);
             }
-        weights_done:;
         }
-    } else {
+    } else if (warp == 9) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int slot = 0;
-            bool ok = true;
-            for (int cb = 0; cb < ncb && ok; ++cb) {
-                const int s = cb % SA;
-                if (!mbar_wait_ab(&a_full[s], (cb / SA) & 1, nullptr, abort)) {
-                    ok = false;
-                    break;
-                }
-                fence_after_sync();
-                const int ksteps = min(64, Cin - cb * 64) / 16;
-                const uint32_t stage = smem_u32(sA + s * CF::kA);
-                for (int tap = 0; tap < 9 && ok; ++tap, ++slot) {
-                    const int sl = slot % kBSlots, dy = tap / 3, dx = tap % 3;
-                    if (!mbar_wait_ab(&b_full[sl], (slot / kBSlots) & 1, nullptr, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after_sync();
-                    const uint64_t bdesc = smem_desc_sw128(smem_u32(sB + sl * CF::kB));
-                    const bool first = cb == 0 && tap == 0;
-                    switch (ksteps) {
-                        case 4: conv_tap_mmas<N, TR, 4>(tmem, stage, bdesc, dy, dx, first); break;
-                        case 3: conv_tap_mmas<N, TR, 3>(tmem, stage, bdesc, dy, dx, first); break;
-                        case 2: conv_tap_mmas<N, TR, 2>(tmem, stage, bdesc, dy, dx, first); break;
-                        default: conv_tap_mmas<N, TR, 1>(tmem, stage, bdesc, dy, dx, first); break;
-                    }
-                    mma_commit(&b_empty[sl]);
-                }
-                mma_commit(&a_empty[s]);
+            const ConvBars bars{st_full, st_empty, h_full, h_empty, t_full, t_empty, mma_done, w_full, w_empty};
+            if (resident) conv_mma_role<N, true>(T, ncb, Cin, tmem, smem_u32(sA), smem_u32(sB), bars, abort);
+            else conv_mma_role<N, false>(T, ncb, Cin, tmem, smem_u32(sA), smem_u32(sB), bars, abort);
+        }
+    } else {
+        // ---------------- epilogue: TMEM lanes 32 w .. (pixels), columns r N + co of accumulator i & 1
+        bool good = true;
+        for (int i = 0; i < T; ++i) {
+            const int buf = i & 1;
+            if (good) {
+                const bool w = mbar_wait_ab(&t_full[buf], (uint32_t)(i >> 1) & 1u, nullptr, abort);
+                good = __all_sync(0xffffffffu, w);
             }
-            mma_commit(acc_full);  // also after a failure: the MMAs in flight complete first
+            fence_after_sync();
+            int n, y0, x0;
+            tile_of(t0 + i, n, y0, x0);
+            const int x = x0 + warp * 32 + lane;
+            for (int r = 0; r < TR; ++r) {
+                const int y = y0 + r;
+                for (int c = 0; c < N; c += 32) {
+                    uint32_t v[32];
+                    if (good) {
+                        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * CF::kAcc + r * N + c), v);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = 0x7fc00000u;  // NaN: the result is unusable
+                    }
+                    if (x < Wd && y < H) {
+                        bf16* dst = Y + ((size_t)n * N + c) * plane + (size_t)y * Wd + x;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float o = fmaxf(__uint_as_float(v[j]) + bias[c + j], 0.f);
+                            dst[(size_t)j * plane] = __float2bfloat16_rn(good ? o : __uint_as_float(v[j]));
+                        }
+                    }
+                }
+            }
+            if (good) {
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[buf]);
+            }
         }
     }
     __syncwarp();
-
-    // ---------------- epilogue: TMEM lanes 32 w .. (pixels), columns r N + co
-    if (warp < 4) {
-        bool h = mbar_wait(acc_full, 0, nullptr);
-        h = __all_sync(0xffffffffu, h) && !*abort;
-        fence_after_sync();
-        const int x = x0 + warp * 32 + lane;
-        for (int r = 0; r < TR; ++r) {
-            const int y = y0 + r;
-            for (int c = 0; c < N; c += 32) {
-                uint32_t v[32];
-                if (h) {
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * N + c), v);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0x7fc00000u;  // NaN: the result is unusable
-                }
-                if (x < Wd && y < H) {
-                    bf16* dst = Y + ((size_t)n * N + c) * plane + (size_t)y * Wd + x;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float o = fmaxf(__uint_as_float(v[j]) + bias[c + j], 0.f);
-                        dst[(size_t)j * plane] = __float2bfloat16_rn(h ? o : __uint_as_float(v[j]));
-                    }
-                }
-            }
-        }
-    }
     fence_before_sync();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == 9) {
         fence_after_sync();
         tmem_dealloc(tmem, CF::kCols);
     }
@@ -291,10 +435,17 @@ cudaError_t set_attr_conv() {
     return cudaFuncSetAttribute(k_conv3_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CfgC<N>::kSmem);
 }
 
+// raw-row map over the NCHW planes of X[nb][C][side][side]: boxes of 152 pixels x 1 row x pb
+// planes (a box of pb planes lands as pb / 8 consecutive 8-plane groups of a raw row)
+int make_map_rows(CUtensorMap* tm, const bf16* X, int C, int nb, int side, int pb) {
+    return tc::make_map_plain3(tm, X, (uint64_t)side, (uint64_t)side, (uint64_t)nb * C, (uint64_t)side * 2,
+                               (uint64_t)side * side * 2, kStgPx, 1, (uint32_t)pb);
+}
+
 }  // namespace
 
 bool conv3_tc_supported(int Cin, int Cout, int side) {
-    return (Cout == 32 || Cout == 64 || Cout == 128) && Cin % 16 == 0 && Cin >= 16 && side >= 128;
+    return (Cout == 32 || Cout == 64 || Cout == 128) && Cin % 16 == 0 && Cin >= 16 && side >= 128 && side % 8 == 0;
 }
 
 size_t conv3_tc_weight_elems(int Cin, int Cout) { return (size_t)((Cin + 63) / 64) * 9 * Cout * 64; }
@@ -321,20 +472,34 @@ int launch_prep_wtc(const float* W, int Cout, int Cin, bf16* Wt, cudaStream_t s)
 
 int launch_conv3_tc(const bf16* XA, int CA, const bf16* XB, int CB, const CUtensorMap& tmW, const float* bias,
                     bf16* Y, int Cout, int nb, int side, cudaStream_t s) {
-    const int TR = Cout == 32 ? CfgC<32>::TR : Cout == 64 ? CfgC<64>::TR : CfgC<128>::TR;
-    dim3 grid((side + 127) / 128, (side + TR - 1) / TR, nb);
+    if (!conv3_tc_supported(CA + CB, Cout, side) || CA % 8 || CB % 8 || CA < 0 || CB < 0 || (CB > 0 && !XB) || nb < 1)
+        return set_error(DEVEL_EINVAL, "conv3_tc: shape (CA %d, CB %d, Cout %d, side %d, nb %d) unsupported", CA, CB,
+                         Cout, side, nb);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        DEVEL_CUDA_TRY(cudaGetDevice(&dev));
+        DEVEL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // 32-plane boxes when no 32-channel group straddles the two sources or a channel block's
+    // end (CA, CB multiples of 32; every channel block then holds 32 or 64 channels), else 8
+    const int pb = CA % 32 == 0 && CB % 32 == 0 ? 32 : 8;
+    CUtensorMap mA, mB;
+    int rc = make_map_rows(&mA, XA, CA, nb, side, pb);
+    if (rc == DEVEL_OK) rc = make_map_rows(&mB, CB > 0 ? XB : XA, CB > 0 ? CB : CA, nb, side, pb);
+    if (rc != DEVEL_OK) return rc;
+    const long long tiles = (long long)nb * ((side + 1) / 2) * ((side + 127) / 128);  // TR = 2 rows per tile
+    const unsigned grid = (unsigned)std::min<long long>(tiles, sms);
     switch (Cout) {
         case 32:
-            k_conv3_tc<32><<<grid, 192, CfgC<32>::kSmem, s>>>(XA, CA, XB, CB, tmW, bias, Y, side, side);
+            k_conv3_tc<32><<<grid, 320, CfgC<32>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
             break;
         case 64:
-            k_conv3_tc<64><<<grid, 192, CfgC<64>::kSmem, s>>>(XA, CA, XB, CB, tmW, bias, Y, side, side);
-            break;
-        case 128:
-            k_conv3_tc<128><<<grid, 192, CfgC<128>::kSmem, s>>>(XA, CA, XB, CB, tmW, bias, Y, side, side);
+            k_conv3_tc<64><<<grid, 320, CfgC<64>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
             break;
         default:
-            return set_error(DEVEL_EINVAL, "conv3_tc: Cout %d unsupported", Cout);
+            k_conv3_tc<128><<<grid, 320, CfgC<128>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
+            break;
     }
     DEVEL_LAUNCH_CHECK("k_conv3_tc");
     return DEVEL_OK;

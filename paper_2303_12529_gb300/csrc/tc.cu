@@ -1000,6 +1000,26 @@ int make_map3(CUtensorMap* tm, const void* base, int depth, int rows, int cols, 
     return DEVEL_OK;
 }
 
+// 3-D bf16 tensor map without swizzle: dims (d0 innermost, d1, d2), byte strides s1, s2 of
+// dims 1 and 2, box (b0, b1, b2), zero fill (the raw boxes a kernel rearranges itself).
+int make_map_plain3(CUtensorMap* tm, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1,
+                    uint64_t s2, uint32_t b0, uint32_t b1, uint32_t b2) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (s1 % 16) || (s2 % 16) || ((uint64_t)b0 * 2) % 16 ||
+        b0 > 256 || b1 > 256 || b2 > 256)
+        return set_error(DEVEL_EINVAL, "tensor map: misaligned base / strides or box");
+    cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
+    cuuint32_t box[3] = {b0, b1, b2};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(DEVEL_ECUDA, "cuTensorMapEncodeTiled (plain) failed (%d)", (int)r);
+    return DEVEL_OK;
+}
+
 // fp32 output map over depth arrays [rows][cols] (pitch ld elements, a multiple of 4;
 // array d at base + d * dld elements): boxes of 32 columns x 32 rows x 1 array, 128-byte
 // swizzle (the epilogue's staging layout).

@@ -25,6 +25,10 @@ int make_map(CUtensorMap* tm, const void* base, int rows, int cols, int ld, int 
 // The same over `depth` such arrays, array d at base + d * dld elements (one per clip of a
 // batch; loads give the clip as the third coordinate).
 int make_map3(CUtensorMap* tm, const void* base, int depth, int rows, int cols, int ld, size_t dld, int box_rows);
+// 3-D bf16 map without swizzle: dims (d0 innermost, d1, d2), byte strides s1 and s2 of dims 1
+// and 2, box (b0, b1, b2) (b0 * 2 bytes a multiple of 16), zero fill.
+int make_map_plain3(CUtensorMap* tm, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1,
+                    uint64_t s2, uint32_t b0, uint32_t b1, uint32_t b2);
 
 // D = ep.scale * A B^T (M x N, contraction length K, a multiple of 16, all of it in
 // one CTA), tiles of 128 x BN (BN a multiple of 16 up to 256, the B map's box height),

@@ -232,10 +232,14 @@ def test_network_on_the_full_clip_grid():
     assert np.all(np.isfinite(host(out)))
 
 
-def test_tensor_core_convolutions_match_oracle():
+@pytest.mark.parametrize("S,nb,width", [(256, 2, 32), (512, 1, 16)])
+def test_tensor_core_convolutions_match_oracle(S, nb, width):
     """At side 256 and width 32 the layers with 32, 64 or 128 output channels on planes of
     side >= 128 run on the tcgen05 implicit-GEMM kernel (the layers of levels 0 and 1 and
-    of the decoder's levels 1 and 0). The forward pass matches the oracle storing in BF16
+    of the decoder's levels 1 and 0); at side 512 and width 16 so do those of levels 1 and 2
+    and of the decoder's levels 2 and 1, among them 16 -> 32 (one 16-channel step per
+    channel block, raw rows copied 8 planes per box) and 96 -> 32 (a 64- and a 32-channel
+    block). The forward pass matches the oracle storing in BF16
     where the GPU does, and the same network computed entirely with the warp-level MMA
     kernel (DEVEL_DSN_NO_TC=1 at creation). At this width the 15 layers store about 10^7
     BF16 activations, and FP32 sums (either kernel) against the oracle's FP64 sums flip some
@@ -244,7 +248,6 @@ def test_tensor_core_convolutions_match_oracle():
     established one, and the two paths to 2.5% of each other."""
     import os
     dv = need_gpu()
-    S, nb, width = 256, 2, 32
     net = dv.Dsn(S, nb, width, seed=11)
     P = _unflatten(net.get_params(), width)
     P = [p if p.ndim > 1 else p + 0.05 for p in P]      # non-zero biases
@@ -253,7 +256,7 @@ def test_tensor_core_convolutions_match_oracle():
     P = _unflatten(net.get_params(), width)
     yy, xx = np.mgrid[0:S, 0:S]
     tsdf = np.stack([np.hypot(yy - 100.0, xx - 140.0) - 40.0,
-                     np.minimum(np.abs(yy - 128.0) - 20.5, 60.0 - np.abs(xx - 90.0))]).astype(np.float32)
+                     np.minimum(np.abs(yy - 128.0) - 20.5, 60.0 - np.abs(xx - 90.0))])[:nb].astype(np.float32)
     out = torch.empty(nb * S * S, dtype=torch.float32, device="cuda")
     net.forward(nb, dev(tsdf), out, B)
     os.environ["DEVEL_DSN_NO_TC"] = "1"
