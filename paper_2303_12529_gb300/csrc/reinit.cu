@@ -24,77 +24,104 @@
 namespace devel {
 namespace {
 
-constexpr int kCX = 8;     // columns per block
-constexpr int kSegs = 128; // segments per column (<= 64 rows each for n <= 8192)
 constexpr unsigned kNone = 0xFFFFu;
-constexpr int kNoPos = INT_MAX;
+constexpr int kSegRows = 64;   // rows per column segment (one 64-bit mask)
+constexpr int kSegMax = 128;   // segments per column (n <= 8192)
+constexpr int kSegPerWarp = kSegMax / 32;
+constexpr unsigned kLastNone = 0xFFFFFFFFu;   // packed (-1, -1): no pixel of either class
+constexpr unsigned kFirstNone = 0x7FFF7FFFu;  // packed (32767, 32767), beyond any row
 
-// Column pass. Thread (column x, segment sg) holds its segment's mask bits in one
-// 64-bit word; the nearest pixel of each class above the segment is the prefix
-// maximum of the segments' last positions, the nearest below the suffix minimum of
-// their first positions (Hillis-Steele scans over the block's segments). Every row
-// of the segment then finds its nearest pixel of each class on either side with one
-// leading/trailing-bit count, and g is written once.
-__global__ void __launch_bounds__(kCX * kSegs)
+// Column pass. Lane x of warp w holds, for column x of the block's 32 and each segment
+// s = w, w + 32, .. of 64 rows, the segment's mask bits in one 64-bit word (loaded one row
+// at a time: a warp reads 32 consecutive bytes of a row, its stores write 128). The
+// nearest pixel of each class above a segment is the prefix maximum of the segments' last
+// positions, the nearest below the suffix minimum of their first positions: per column
+// one sequential scan over the segments in shared memory, both classes at once as signed
+// 16-bit halves (positions < 8192). The rows of a segment then take their distances from
+// the runs of equal rows (below), and g is written once.
+__global__ void __launch_bounds__(1024)
 k_edt_cols(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g) {
-    __shared__ int sc[2][4][kSegs][kCX];  // [buffer][last0, last1, first0, first1][segment][column]
+    __shared__ unsigned sL[kSegMax][32], sF[kSegMax][32];  // packed (class 0 | class 1 << 16)
     pdl_trigger();
     pdl_wait();
     mask += (size_t)blockIdx.y * n * n;  // clip blockIdx.y of a batch
     g += (size_t)blockIdx.y * n * n;
-    const int cx = threadIdx.x, sg = threadIdx.y;
-    const int x = blockIdx.x * kCX + cx;
-    const int L = (n + kSegs - 1) / kSegs;
-    const int ys = min(n, sg * L), len = min(n, ys + L) - ys;
-    unsigned long long bits = 0ull;
-    if (x < n) {
-        for (int i = 0; i < len; ++i)
-            if (mask[(size_t)(ys + i) * n + x]) bits |= 1ull << i;
-    }
-    const unsigned long long valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
-    const unsigned long long b1 = bits, b0 = ~bits & valid;
-    sc[0][0][sg][cx] = b0 ? ys + 63 - __clzll((long long)b0) : -1;
-    sc[0][1][sg][cx] = b1 ? ys + 63 - __clzll((long long)b1) : -1;
-    sc[0][2][sg][cx] = b0 ? ys + __ffsll((long long)b0) - 1 : kNoPos;
-    sc[0][3][sg][cx] = b1 ? ys + __ffsll((long long)b1) - 1 : kNoPos;
-    int cur = 0;
-    for (int off = 1; off < kSegs; off <<= 1) {
-        __syncthreads();
-        int l0 = sc[cur][0][sg][cx], l1 = sc[cur][1][sg][cx];
-        int f0 = sc[cur][2][sg][cx], f1 = sc[cur][3][sg][cx];
-        if (sg >= off) {
-            l0 = max(l0, sc[cur][0][sg - off][cx]);
-            l1 = max(l1, sc[cur][1][sg - off][cx]);
+    const int lane = threadIdx.x, w = threadIdx.y, nw = blockDim.y;
+    const int x = blockIdx.x * 32 + lane;
+    const int S = (n + kSegRows - 1) / kSegRows;
+    unsigned long long bits[kSegPerWarp];
+#pragma unroll
+    for (int j = 0; j < kSegPerWarp; ++j) {
+        const int sg = w + j * nw, ys = sg * kSegRows, len = min(kSegRows, n - ys);
+        bits[j] = 0ull;
+        if (sg < S && x < n) {
+            const unsigned char* p = mask + (size_t)ys * n + x;
+#pragma unroll 16
+            for (int i = 0; i < len; ++i)
+                if (p[(size_t)i * n]) bits[j] |= 1ull << i;
         }
-        if (sg + off < kSegs) {
-            f0 = min(f0, sc[cur][2][sg + off][cx]);
-            f1 = min(f1, sc[cur][3][sg + off][cx]);
+        if (sg < S) {
+            const unsigned long long valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
+            const unsigned long long b1 = bits[j], b0 = ~b1 & valid;
+            const int l0 = b0 ? ys + 63 - __clzll((long long)b0) : -1;
+            const int l1 = b1 ? ys + 63 - __clzll((long long)b1) : -1;
+            const int f0 = b0 ? ys + __ffsll((long long)b0) - 1 : 0x7FFF;
+            const int f1 = b1 ? ys + __ffsll((long long)b1) - 1 : 0x7FFF;
+            sL[sg][lane] = ((unsigned)l0 & 0xFFFFu) | ((unsigned)l1 << 16);
+            sF[sg][lane] = (unsigned)f0 | ((unsigned)f1 << 16);
         }
-        sc[cur ^ 1][0][sg][cx] = l0;
-        sc[cur ^ 1][1][sg][cx] = l1;
-        sc[cur ^ 1][2][sg][cx] = f0;
-        sc[cur ^ 1][3][sg][cx] = f1;
-        cur ^= 1;
     }
     __syncthreads();
-    if (x >= n || len == 0) return;
-    const int up0 = sg > 0 ? sc[cur][0][sg - 1][cx] : -1;
-    const int up1 = sg > 0 ? sc[cur][1][sg - 1][cx] : -1;
-    const int dn0 = sg + 1 < kSegs ? sc[cur][2][sg + 1][cx] : kNoPos;
-    const int dn1 = sg + 1 < kSegs ? sc[cur][3][sg + 1][cx] : kNoPos;
-    for (int i = 0; i < len; ++i) {
-        const int y = ys + i;
-        const unsigned long long le = (2ull << i) - 1ull, ge = ~0ull << i;
-        const unsigned long long a0 = b0 & le, a1 = b1 & le, c0 = b0 & ge, c1 = b1 & ge;
-        const int pa0 = a0 ? ys + 63 - __clzll((long long)a0) : up0;
-        const int pa1 = a1 ? ys + 63 - __clzll((long long)a1) : up1;
-        const int pb0 = c0 ? ys + __ffsll((long long)c0) - 1 : dn0;
-        const int pb1 = c1 ? ys + __ffsll((long long)c1) - 1 : dn1;
-        unsigned d0 = pa0 >= 0 ? (unsigned)(y - pa0) : kNone;
-        unsigned d1 = pa1 >= 0 ? (unsigned)(y - pa1) : kNone;
-        if (pb0 != kNoPos) d0 = min(d0, (unsigned)(pb0 - y));
-        if (pb1 != kNoPos) d1 = min(d1, (unsigned)(pb1 - y));
-        g[(size_t)y * n + x] = d0 | (d1 << 16);
+    if (w == 0) {  // inclusive prefix maxima of the last positions, top down
+        unsigned acc = kLastNone;
+#pragma unroll 8
+        for (int sg = 0; sg < S; ++sg) {
+            acc = __vmaxs2(acc, sL[sg][lane]);
+            sL[sg][lane] = acc;
+        }
+    }
+    if (w == (nw > 1 ? 1 : 0)) {  // inclusive suffix minima of the first positions, bottom up
+        unsigned acc = kFirstNone;
+#pragma unroll 8
+        for (int sg = S - 1; sg >= 0; --sg) {
+            acc = __vmins2(acc, sF[sg][lane]);
+            sF[sg][lane] = acc;
+        }
+    }
+    __syncthreads();
+    if (x >= n) return;
+#pragma unroll
+    for (int j = 0; j < kSegPerWarp; ++j) {
+        const int sg = w + j * nw;
+        if (sg >= S) break;
+        const int ys = sg * kSegRows, len = min(kSegRows, n - ys);
+        const unsigned up = sg > 0 ? sL[sg - 1][lane] : kLastNone;
+        const unsigned dn = sg + 1 < S ? sF[sg + 1][lane] : kFirstNone;
+        const int up0 = (int)(short)(up & 0xFFFFu), up1 = (int)(short)(up >> 16);
+        const int dn0 = (int)(dn & 0xFFFFu), dn1 = (int)(dn >> 16);
+        const unsigned long long valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
+        const unsigned long long b1 = bits[j];
+        // A pixel's own class is at distance 0; the other class is nearest just outside the
+        // pixel's run of equal rows. Bit i of t: rows i and i + 1 differ. At a run's first
+        // row the run's end (the next set bit of t) and the nearest other-class rows above
+        // and below are found once; every row of the run then needs a few operations.
+        const unsigned long long t = (b1 ^ (b1 >> 1)) & (valid >> 1);
+        int re = -1, above = -1, below = 0x7FFF;
+        unsigned cls = 0u;
+        unsigned* gp = g + (size_t)ys * n + x;
+        for (int i = 0; i < len; ++i) {
+            const int y = ys + i;
+            if (i > re) {  // a run starts at row i
+                cls = (unsigned)(b1 >> i) & 1u;
+                const unsigned long long nt = t >> i;
+                re = nt ? i + __ffsll((long long)nt) - 1 : len - 1;
+                above = i > 0 ? y - 1 : (cls ? up0 : up1);
+                below = re < len - 1 ? ys + re + 1 : (cls ? dn0 : dn1);
+            }
+            unsigned d = above >= 0 ? (unsigned)(y - above) : kNone;
+            if (below != 0x7FFF) d = min(d, (unsigned)(below - y));
+            gp[(size_t)i * n] = cls ? d : (d << 16);  // (class 0 | class 1 << 16), own class 0
+        }
     }
 }
 
@@ -240,7 +267,8 @@ int reinit_init_attrs() {
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
                   cudaStream_t s, int B) {
     prof_begin(PK_EDT_COLS, s);
-    cudaError_t e = launch_pdl(k_edt_cols, dim3((n + kCX - 1) / kCX, B), dim3(kCX, kSegs), 0, s, mask, n,
+    const int segs = (n + kSegRows - 1) / kSegRows;
+    cudaError_t e = launch_pdl(k_edt_cols, dim3((n + 31) / 32, B), dim3(32, std::min(32, segs)), 0, s, mask, n,
                                reinterpret_cast<unsigned*>(d2));
     prof_end(PK_EDT_COLS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_edt_cols");
