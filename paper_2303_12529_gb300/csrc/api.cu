@@ -214,7 +214,7 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
     float* phi_alt = w.phi2;
     int rc;
     if (!cl.phi_given) {
-        rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s);
+        rc = launch_reinit(n, cl.target, phi, w.d2, p->d_lo, p->d_hi, s, 1, false);
         if (rc) return rc;
     }
     const bool tcp = o->precision == DEVEL_PREC_BF16X3;
@@ -279,7 +279,7 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
         phi = phi_alt;
         phi_alt = tmp;
         if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
-            rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s);
+            rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s, 1, false);
             if (rc) return rc;
         }
     }

@@ -178,7 +178,7 @@ int enqueue_batch(const devel_ilt_params* p, devel_batch* b, int B, const BatchA
     float* phi_alt = w.phi2;
     int rc;
     if (!a.phi_given) {
-        rc = launch_reinit(n, a.target, phi, w.d2, p->d_lo, p->d_hi, s, B);
+        rc = launch_reinit(n, a.target, phi, w.d2, p->d_lo, p->d_hi, s, B, false);
         if (rc) return rc;
     }
     rc = launch_mask_from_phi(n, phi, w.M, s, B);
@@ -203,7 +203,7 @@ int enqueue_batch(const devel_ilt_params* p, devel_batch* b, int B, const BatchA
         std::swap(phi, phi_alt);
         const int gi = p->start_iter + t;
         if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
-            rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s, B);
+            rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s, B, false);
             if (rc) return rc;
         }
     }

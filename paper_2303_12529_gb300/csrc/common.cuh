@@ -349,9 +349,10 @@ int litho_init_attrs();
 int reinit_init_attrs();
 
 // reinit.cu
-// B > 1: a batch of B clips, each array's clip c at c n^2
+// B > 1: a batch of B clips, each array's clip c at c n^2. want_d2 false: d2 is scratch
+// only (it then holds the packed column distances, and the row pass skips its store)
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
-                  cudaStream_t s, int B = 1);
+                  cudaStream_t s, int B = 1, bool want_d2 = true);
 
 // forward / adjoint bodies shared by the ABI and the solver (api.cu)
 int forward_from_mhat(const devel_optics* o, float* I, cudaStream_t s);

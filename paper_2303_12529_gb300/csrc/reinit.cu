@@ -160,7 +160,7 @@ __device__ __forceinline__ int scan_block(const int* f, int x, int k, int best) 
 
 __global__ void __launch_bounds__(256)
 k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__ g,
-           float* __restrict__ phi, float d_lo, float d_hi) {
+           float* __restrict__ phi, float d_lo, float d_hi, int store_d2) {
     extern __shared__ int sfx[];
     pdl_trigger();
     pdl_wait();
@@ -173,13 +173,35 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     int* const BM = sfx + 2 * npad;
     int* const EL = BM + 2 * nb;
     int* const ER = BM + 4 * nb;
+    unsigned char* const SM = reinterpret_cast<unsigned char*>(BM + 6 * nb);  // the row's mask bytes
     const int y = blockIdx.x;
     const size_t base = (size_t)y * n;
-    for (int x = threadIdx.x; x < npad; x += blockDim.x) {
-        const unsigned w = x < n ? g[base + x] : (kNone | (kNone << 16));
-        const unsigned a = w & 0xFFFFu, b = w >> 16;
-        F[x] = a == kNone ? kFar : (int)(a * a);
-        F[npad + x] = b == kNone ? kFar : (int)(b * b);
+    // the row's packed column distances and mask bytes, eight columns per thread with all
+    // their loads issued before the first use
+    constexpr int kFill = 8;
+    for (int x0 = threadIdx.x; x0 < npad; x0 += kFill * blockDim.x) {
+        unsigned w[kFill];
+        unsigned char mk[kFill];
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int x = x0 + u * blockDim.x;
+            w[u] = kNone | (kNone << 16);
+            mk[u] = 0;
+            if (x < n) {
+                w[u] = g[base + x];
+                mk[u] = mask[base + x];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int x = x0 + u * blockDim.x;
+            if (x < npad) {
+                const unsigned a = w[u] & 0xFFFFu, b = w[u] >> 16;
+                F[x] = a == kNone ? kFar : (int)(a * a);
+                F[npad + x] = b == kNone ? kFar : (int)(b * b);
+                SM[x] = mk[u];
+            }
+        }
     }
     __syncthreads();
     bool any0 = false, any1 = false;
@@ -206,7 +228,7 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
     for (int x0 = warp * 32; x0 < n; x0 += nwarps * 32) {
         const int x = x0 + lane;
         const bool valid = x < n;
-        const bool inside = valid && mask[base + x] != 0;
+        const bool inside = valid && SM[x] != 0;
         const int c = inside ? 0 : 1;
         const int* f = F + c * npad;
         const int* bm = BM + c * nb;
@@ -248,7 +270,7 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
                 v = inside ? -dist : dist;
                 v = fminf(fmaxf(v, d_lo), d_hi);
             }
-            g[base + x] = (unsigned)d2;
+            if (store_d2) g[base + x] = (unsigned)d2;
             phi[base + x] = v;
         }
     }
@@ -256,7 +278,7 @@ k_edt_rows(const unsigned char* __restrict__ mask, int n, unsigned* __restrict__
 
 }  // namespace
 
-static size_t edt_rows_smem(int n) { return sizeof(int) * (2 * edt_nb(n) * kBlk + 6 * edt_nb(n)); }
+static size_t edt_rows_smem(int n) { return sizeof(int) * (2 * edt_nb(n) * kBlk + 6 * edt_nb(n)) + edt_nb(n) * kBlk; }
 
 int reinit_init_attrs() {
     DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -265,7 +287,7 @@ int reinit_init_attrs() {
 }
 
 int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
-                  cudaStream_t s, int B) {
+                  cudaStream_t s, int B, bool want_d2) {
     prof_begin(PK_EDT_COLS, s);
     const int segs = (n + kSegRows - 1) / kSegRows;
     cudaError_t e = launch_pdl(k_edt_cols, dim3((n + 31) / 32, B), dim3(32, std::min(32, segs)), 0, s, mask, n,
@@ -274,7 +296,7 @@ int launch_reinit(int n, const unsigned char* mask, float* phi, int* d2, float d
     if (e != cudaSuccess) return cuda_error(e, "k_edt_cols");
     prof_begin(PK_EDT_ROWS, s);
     e = launch_pdl(k_edt_rows, dim3(n, B), dim3(256), edt_rows_smem(n), s, mask, n, reinterpret_cast<unsigned*>(d2), phi,
-                   d_lo, d_hi);
+                   d_lo, d_hi, want_d2 ? 1 : 0);
     prof_end(PK_EDT_ROWS, s);
     if (e != cudaSuccess) return cuda_error(e, "k_edt_rows");
     return DEVEL_OK;
@@ -329,5 +351,5 @@ extern "C" int devel_reinit_sdf_static(int n, const unsigned char* mask, float* 
     }
     // every scratch word the kernels read is written earlier in the same call,
     // so the previous call's contents need no clearing
-    return launch_reinit(n, mask, phi, static_cast<int*>(scratch), d_lo, d_hi, s);
+    return launch_reinit(n, mask, phi, static_cast<int*>(scratch), d_lo, d_hi, s, 1, false);
 }
