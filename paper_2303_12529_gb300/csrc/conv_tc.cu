@@ -53,25 +53,34 @@ constexpr uint32_t kStgRow = 8 * kStgBox;           // the 64 channels of one ra
 constexpr uint32_t kSmemMax = 232448;               // 227 KiB of dynamic shared memory per CTA
 
 // Per output-channel count N: TR output rows per tile, HR = TR + 2 halo rows, RS raw-row
-// slots, and as many weight "tap rows" (the three boxes of one (channel block, dy), at most
-// 9) as fit beside them in one CTA per SM.
+// slots, and as many weight granules (GT taps' boxes each, at most 9 granules) as fit beside
+// them in one CTA per SM.
+//   N = 32, 64, 128: M = 128 pixels of one row (PX = 128), N = Cout; a granule is a tap
+//                    row (the three boxes of one (channel block, dy));
+//   N = 256 (SW):    planes of side 64, operands swapped: A = the weights (M = 128 output
+//                    channels, two halves), B = the halo rows (N = PX = 64 pixels); a
+//                    granule is one tap's box of all 256 output channels.
 template <int N>
 struct CfgC {
+    static constexpr bool SW = N == 256;
     static constexpr int TR = 2;
     static constexpr int HR = TR + 2;
-    static constexpr int RS = N == 128 ? 3 : 4;
+    static constexpr int RS = SW ? 2 : N == 128 ? 3 : 4;
+    static constexpr int GT = SW ? 1 : 3;             // taps per weight granule
+    static constexpr int GPU = 9 / GT;                // granules per unit
+    static constexpr int PX = SW ? 64 : 128;          // pixels of a tile row
     static constexpr uint32_t kA = HR * kHaloBytes;
     static constexpr uint32_t kStg = RS * kStgRow;
     static constexpr uint32_t kB = N * 128;           // one (channel block, tap) weight box
     static constexpr uint32_t kFixed = 1024 + kA + kStg + 1024;  // alignment, halo, raw rows, barriers
-    static constexpr int kFit = (int)((kSmemMax - kFixed) / (3 * kB));
-    static constexpr int kRows = kFit > 9 ? 9 : kFit;  // weight tap-row slots
+    static constexpr int kFit = (int)((kSmemMax - kFixed) / (GT * kB));
+    static constexpr int kRows = kFit > 9 ? 9 : kFit;  // weight granule slots
     static_assert(kFit >= 2, "weight ring too small");
-    static constexpr int kAcc = TR * N;               // TMEM columns of one accumulator
+    static constexpr int kAcc = SW ? TR * (N / 128) * PX : TR * N;  // TMEM columns of one accumulator
     static_assert(2 * kAcc <= 512, "two accumulators in TMEM");
     static constexpr uint32_t kCols = 2 * kAcc <= 32 ? 32 : 2 * kAcc <= 64 ? 64 : 2 * kAcc <= 128 ? 128
                                     : 2 * kAcc <= 256 ? 256 : 512;
-    static constexpr size_t kSmem = kFixed + (size_t)kRows * 3 * kB;
+    static constexpr size_t kSmem = kFixed + (size_t)kRows * GT * kB;
     static_assert(kSmem <= kSmemMax, "shared memory");
 };
 
@@ -147,23 +156,78 @@ __device__ __forceinline__ bool conv_tap_row(uint32_t acc, uint32_t halo, uint32
     return true;
 }
 
+// Tap row DY with swapped operands (N = 256 on planes of side 64): per tap, a wait for its
+// weight box (a granule of one tap), then TR output rows x two 128-channel halves x KS
+// steps: A = rows 128 h .. of the box, B = the halo view (64 pixel rows from dx), D =
+// columns (r * 2 + h) * 64 of the accumulator (TMEM lane = output channel, column = pixel).
+template <int N, int KS, bool RES, int DY>
+__device__ __forceinline__ bool conv_tap_row_sw(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb,
+                                                uint32_t accf, const ConvBars& b, volatile int* abort) {
+    using CF = CfgC<N>;
+    constexpr int TR = CF::TR, HR = CF::HR, R = CF::kRows, NH = N / 128, PX = CF::PX;
+    constexpr int r0 = DY == 0 ? 0 : TR + DY - 1, r1 = TR + DY;
+#pragma unroll
+    for (int hr = r0; hr < r1; ++hr)
+        if (!mbar_wait_ab(&b.h_full[hr], (uint32_t)u & 1u, nullptr, abort)) return false;
+    constexpr uint32_t idesc = idesc_bf16(128, PX);
+    const uint64_t h0 = smem_desc_sw128(halo);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+        const int tap = DY * 3 + dx;
+        int slot;
+        if constexpr (RES) {
+            slot = cb * 9 + tap;
+        } else {
+            const int g = u * 9 + tap;
+            slot = g % R;
+            if (!mbar_wait_ab(&b.w_full[slot], (uint32_t)(g / R) & 1u, nullptr, abort)) return false;
+        }
+        fence_after_sync();
+        const uint64_t w0 = smem_desc_sw128(wsm + (uint32_t)slot * CF::kB);
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int h = 0; h < NH; ++h)
+#pragma unroll
+                for (int kk = 0; kk < KS; ++kk) {
+                    const uint64_t ad = w0 + (uint64_t)(((h * 128 * 128) >> 4) + kk * 2);
+                    const uint64_t bd = h0 + (uint64_t)((((r + DY) * kHaloBytes + dx * 128) >> 4) + kk * 2);
+                    mma_bf16(acc + (uint32_t)((r * NH + h) * PX), ad, bd, idesc,
+                             (DY == 0 && dx == 0 && kk == 0) ? accf : 1u);
+                }
+        if constexpr (!RES) mma_commit(&b.w_empty[slot]);
+    }
+    if constexpr (DY < 2) {
+        mma_commit(&b.h_empty[DY]);
+    } else {
+#pragma unroll
+        for (int hr = 2; hr < HR; ++hr) mma_commit(&b.h_empty[hr]);
+    }
+    return true;
+}
+
 template <int N, int KS, bool RES>
 __device__ __forceinline__ bool conv_unit(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb, uint32_t accf,
                                           const ConvBars& b, volatile int* abort) {
-    return conv_tap_row<N, KS, RES, 0>(acc, halo, wsm, u, cb, accf, b, abort) &&
-           conv_tap_row<N, KS, RES, 1>(acc, halo, wsm, u, cb, accf, b, abort) &&
-           conv_tap_row<N, KS, RES, 2>(acc, halo, wsm, u, cb, accf, b, abort);
+    if constexpr (CfgC<N>::SW)
+        return conv_tap_row_sw<N, KS, RES, 0>(acc, halo, wsm, u, cb, accf, b, abort) &&
+               conv_tap_row_sw<N, KS, RES, 1>(acc, halo, wsm, u, cb, accf, b, abort) &&
+               conv_tap_row_sw<N, KS, RES, 2>(acc, halo, wsm, u, cb, accf, b, abort);
+    else
+        return conv_tap_row<N, KS, RES, 0>(acc, halo, wsm, u, cb, accf, b, abort) &&
+               conv_tap_row<N, KS, RES, 1>(acc, halo, wsm, u, cb, accf, b, abort) &&
+               conv_tap_row<N, KS, RES, 2>(acc, halo, wsm, u, cb, accf, b, abort);
 }
 
 // The MMA issuer (one thread): tile i into TMEM accumulator i & 1, its channel blocks in
 // order (the first overwrites the accumulator), then a commit to t_full. With resident
-// weights every tap row's boxes are waited for once, before the first tile.
+// weights every granule is waited for once, before the first tile.
 template <int N, bool RES>
 __device__ __forceinline__ void conv_mma_role(int T, int ncb, int Cin, uint32_t tmem, uint32_t halo, uint32_t wsm,
                                               const ConvBars& b, volatile int* abort) {
     bool ok = true;
     if constexpr (RES)
-        for (int g = 0; g < 3 * ncb && ok; ++g) ok = mbar_wait_ab(&b.w_full[g], 0u, nullptr, abort);
+        for (int g = 0; g < CfgC<N>::GPU * ncb && ok; ++g) ok = mbar_wait_ab(&b.w_full[g], 0u, nullptr, abort);
     for (int i = 0; i < T && ok; ++i) {
         const int buf = i & 1;
         if (i >= 2 && !mbar_wait_ab(&b.t_empty[buf], (uint32_t)((i >> 1) - 1) & 1u, nullptr, abort)) {
@@ -216,7 +280,7 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
     uint8_t* sA = smem;                    // [HR][kHaloRows][128 B] halo rows
     uint8_t* sS = sA + CF::kA;             // [RS][8 channel groups][8 planes][152 px] raw rows
     uint8_t* misc = sS + CF::kStg;         // barriers, TMEM address, abort flag, dummy rows
-    uint8_t* sB = misc + 1024;             // [R][3 taps][N][128 B] weight boxes
+    uint8_t* sB = misc + 1024;             // [R][GT taps][N][128 B] weight boxes
     uint64_t* st_full = reinterpret_cast<uint64_t*>(misc);  // [RS]
     uint64_t* st_empty = st_full + 4;      // [RS]
     uint64_t* h_full = st_full + 8;        // [HR]
@@ -233,14 +297,14 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Cin = CA + CB, ncb = (Cin + 63) / 64;
-    const bool resident = 3 * ncb <= R;    // every weight box of the layer stays in shared memory
-    const int segs = (Wd + 127) / 128, rgroups = (H + TR - 1) / TR;
+    const bool resident = CF::GPU * ncb <= R;  // every weight box of the layer stays in shared memory
+    const int segs = (Wd + CF::PX - 1) / CF::PX, rgroups = (H + TR - 1) / TR;
     const long long tiles = (long long)nb * rgroups * segs;
     const int t0 = (int)(tiles * blockIdx.x / gridDim.x), t1 = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
     const int T = t1 - t0, U = T * ncb;
     const size_t plane = (size_t)H * Wd;
     auto tile_of = [&](int t, int& n, int& y0, int& x0) {
-        x0 = (t % segs) * 128;
+        x0 = (t % segs) * CF::PX;
         const int r = t / segs;
         y0 = (r % rgroups) * TR;
         n = r / rgroups;
@@ -276,7 +340,7 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
     if (warp == 8) {
         // ---------------- TMA: raw rows and weight boxes
         if (lane == 0 && U > 0) {
-            const int rows = U * HR, wtot = resident ? 3 * ncb : 3 * U;
+            const int rows = U * HR, wtot = resident ? CF::GPU * ncb : CF::GPU * U;
             int k = 0, ws = 0;
             bool idle = false;
             unsigned long long t_idle = 0;
@@ -297,13 +361,13 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
                     prog = true;
                 }
                 if (ws < wtot && (resident || ws < R || mbar_test_wait(&w_empty[ws % R], (uint32_t)((ws / R) - 1) & 1u))) {
-                    // tap row ws: (channel block, dy) = (ws / 3, ws % 3) resident, else
-                    // (unit ws / 3, dy ws % 3); its boxes are 9 cb + 3 dy + dx
+                    // granule ws: (channel block ws / GPU, granule ws % GPU) resident, else
+                    // (unit ws / GPU, granule ws % GPU); its boxes are 9 cb + GT granule + j
                     const int sl = resident ? ws : ws % R;
-                    const int box = resident ? 3 * ws : ((ws / 3) % ncb) * 9 + (ws % 3) * 3;
-                    mbar_arrive_expect_tx(&w_full[sl], 3 * CF::kB);
-                    for (int dx = 0; dx < 3; ++dx)
-                        tma_load_2d(&tmW, &w_full[sl], sB + (sl * 3 + dx) * CF::kB, 0, (box + dx) * N);
+                    const int box = resident ? CF::GT * ws : ((ws / CF::GPU) % ncb) * 9 + (ws % CF::GPU) * CF::GT;
+                    mbar_arrive_expect_tx(&w_full[sl], CF::GT * CF::kB);
+                    for (int j = 0; j < CF::GT; ++j)
+                        tma_load_2d(&tmW, &w_full[sl], sB + (sl * CF::GT + j) * CF::kB, 0, (box + j) * N);
                     ++ws;
                     prog = true;
                 }
@@ -367,6 +431,61 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
             const ConvBars bars{st_full, st_empty, h_full, h_empty, t_full, t_empty, mma_done, w_full, w_empty};
             if (resident) conv_mma_role<N, true>(T, ncb, Cin, tmem, smem_u32(sA), smem_u32(sB), bars, abort);
             else conv_mma_role<N, false>(T, ncb, Cin, tmem, smem_u32(sA), smem_u32(sB), bars, abort);
+        }
+    } else if constexpr (CF::SW) {
+        // ---------------- epilogue, swapped operands: TMEM lanes 32 w .. (output channels of
+        // half h), columns (r * 2 + h) * 64 .. (pixels): each thread writes its channel's
+        // 64-pixel row (128 bytes) of output row y0 + r
+        constexpr int NH = N / 128, PX = CF::PX;
+        bool good = true;
+        for (int i = 0; i < T; ++i) {
+            const int buf = i & 1;
+            if (good) {
+                const bool w = mbar_wait_ab(&t_full[buf], (uint32_t)(i >> 1) & 1u, nullptr, abort);
+                good = __all_sync(0xffffffffu, w);
+            }
+            fence_after_sync();
+            int n, y0, x0;
+            tile_of(t0 + i, n, y0, x0);
+            for (int r = 0; r < TR; ++r) {
+                const int y = y0 + r;
+                for (int h = 0; h < NH; ++h) {
+                    const int co = h * 128 + warp * 32 + lane;
+                    static_assert(PX == 64, "two 32-column loads per row");
+                    uint32_t v0[32], v1[32];  // pixels 0-31 and 32-63
+                    if (good) {
+                        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * CF::kAcc + (r * NH + h) * PX);
+                        tmem_ld32(ta, v0);
+                        tmem_ld32(ta + 32u, v1);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v0[j] = v1[j] = 0x7fc00000u;  // NaN: the result is unusable
+                    }
+                    if (y < H) {
+                        const float bv = bias[co];
+                        uint4* dst = reinterpret_cast<uint4*>(Y + (((size_t)n * N + co) * H + y) * Wd + x0);
+#pragma unroll
+                        for (int q = 0; q < PX / 8; ++q) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = 8 * q + 2 * e;
+                                const float a0 = __uint_as_float(j < 32 ? v0[j] : v1[j - 32]);
+                                const float a1 = __uint_as_float(j < 32 ? v0[j + 1] : v1[j - 31]);
+                                const __nv_bfloat162 hb = __floats2bfloat162_rn(good ? fmaxf(a0 + bv, 0.f) : a0,
+                                                                                 good ? fmaxf(a1 + bv, 0.f) : a1);
+                                pk[e] = *reinterpret_cast<const uint32_t*>(&hb);
+                            }
+                            dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        }
+                    }
+                }
+            }
+            if (good) {
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[buf]);
+            }
         }
     } else {
         // ---------------- epilogue: TMEM lanes 32 w .. (pixels), columns r N + co of accumulator i & 1
@@ -445,7 +564,9 @@ int make_map_rows(CUtensorMap* tm, const bf16* X, int C, int nb, int side, int p
 }  // namespace
 
 bool conv3_tc_supported(int Cin, int Cout, int side) {
-    return (Cout == 32 || Cout == 64 || Cout == 128) && Cin % 16 == 0 && Cin >= 16 && side >= 128 && side % 8 == 0;
+    const bool rows = (Cout == 32 || Cout == 64 || Cout == 128) && side >= 128 && side % 8 == 0;
+    const bool swapped = Cout == 256 && side == CfgC<256>::PX;
+    return (rows || swapped) && Cin % 16 == 0 && Cin >= 16;
 }
 
 size_t conv3_tc_weight_elems(int Cin, int Cout) { return (size_t)((Cin + 63) / 64) * 9 * Cout * 64; }
@@ -454,6 +575,7 @@ int conv3_tc_init_attrs() {
     cudaError_t e = set_attr_conv<32>();
     if (e == cudaSuccess) e = set_attr_conv<64>();
     if (e == cudaSuccess) e = set_attr_conv<128>();
+    if (e == cudaSuccess) e = set_attr_conv<256>();
     if (e != cudaSuccess) return cuda_error(e, "conv3_tc_init_attrs");
     return DEVEL_OK;
 }
@@ -488,7 +610,8 @@ int launch_conv3_tc(const bf16* XA, int CA, const bf16* XB, int CB, const CUtens
     int rc = make_map_rows(&mA, XA, CA, nb, side, pb);
     if (rc == DEVEL_OK) rc = make_map_rows(&mB, CB > 0 ? XB : XA, CB > 0 ? CB : CA, nb, side, pb);
     if (rc != DEVEL_OK) return rc;
-    const long long tiles = (long long)nb * ((side + 1) / 2) * ((side + 127) / 128);  // TR = 2 rows per tile
+    const int px = Cout == 256 ? CfgC<256>::PX : CfgC<32>::PX;
+    const long long tiles = (long long)nb * ((side + 1) / 2) * ((side + px - 1) / px);  // TR = 2 rows per tile
     const unsigned grid = (unsigned)std::min<long long>(tiles, sms);
     switch (Cout) {
         case 32:
@@ -497,8 +620,11 @@ int launch_conv3_tc(const bf16* XA, int CA, const bf16* XB, int CB, const CUtens
         case 64:
             k_conv3_tc<64><<<grid, 320, CfgC<64>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
             break;
-        default:
+        case 128:
             k_conv3_tc<128><<<grid, 320, CfgC<128>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
+            break;
+        default:
+            k_conv3_tc<256><<<grid, 320, CfgC<256>::kSmem, s>>>(mA, mB, CA, CB, tmW, bias, Y, side, side, nb, pb);
             break;
     }
     DEVEL_LAUNCH_CHECK("k_conv3_tc");

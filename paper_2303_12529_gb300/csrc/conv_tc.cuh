@@ -8,8 +8,10 @@
 
 namespace devel {
 
-// Layers the tensor-core kernel takes: Cout in {32, 64, 128}, Cin a multiple of 16,
-// planes of side >= 128 (one 128-pixel row segment per MMA tile).
+// Layers the tensor-core kernel takes: Cin a multiple of 16, and either Cout in
+// {32, 64, 128} on planes of side >= 128 (a multiple of 8; one 128-pixel row segment per
+// MMA tile) or Cout = 256 on planes of side 64 (operands swapped: one 64-pixel row per
+// MMA tile, 128 output channels per MMA).
 bool conv3_tc_supported(int Cin, int Cout, int side);
 // bf16 elements of the prepared weights Wtc[ceil(Cin / 64)][9][Cout][64]
 size_t conv3_tc_weight_elems(int Cin, int Cout);

@@ -232,14 +232,16 @@ def test_network_on_the_full_clip_grid():
     assert np.all(np.isfinite(host(out)))
 
 
-@pytest.mark.parametrize("S,nb,width", [(256, 2, 32), (512, 1, 16)])
+@pytest.mark.parametrize("S,nb,width", [(256, 2, 32), (512, 1, 16), (512, 1, 32)])
 def test_tensor_core_convolutions_match_oracle(S, nb, width):
     """At side 256 and width 32 the layers with 32, 64 or 128 output channels on planes of
     side >= 128 run on the tcgen05 implicit-GEMM kernel (the layers of levels 0 and 1 and
     of the decoder's levels 1 and 0); at side 512 and width 16 so do those of levels 1 and 2
     and of the decoder's levels 2 and 1, among them 16 -> 32 (one 16-channel step per
     channel block, raw rows copied 8 planes per box) and 96 -> 32 (a 64- and a 32-channel
-    block). The forward pass matches the oracle storing in BF16
+    block); at side 512 and width 32 (the network of the full-size learned start) every 3x3
+    layer does, level 3's 128 -> 256 and 256 -> 256 on the 64^2 plane with the operands
+    swapped (weights as A, 64-pixel halo rows as B). The forward pass matches the oracle storing in BF16
     where the GPU does, and the same network computed entirely with the warp-level MMA
     kernel (DEVEL_DSN_NO_TC=1 at creation). At this width the 15 layers store about 10^7
     BF16 activations, and FP32 sums (either kernel) against the oracle's FP64 sums flip some
