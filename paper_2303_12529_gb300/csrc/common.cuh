@@ -86,6 +86,10 @@ struct ResistArgs {
     float I_th, d2in, d2out;
     float a_nom, a_in, a_out, b;
     float k_nom, k_in, k_out;
+    float pad_;
+    // the same values broadcast to pairs, for the packed FP32 path (kernel-parameter
+    // operands: no registers held for them)
+    float2 a_nom2, a_in2, a_out2, b2, d2in2, d2out2, k_nom2, k_in2, k_out2;
 };
 
 // N tile of the tensor-core GEMM T = E Z (a multiple of 16): narrow, so that the

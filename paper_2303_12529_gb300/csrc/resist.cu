@@ -138,8 +138,10 @@ __device__ __forceinline__ Px4<kDef> load4(const float* In, const float* Id, con
 __device__ __forceinline__ void split_store4(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t q, const float (&r)[4]) {
     const __nv_bfloat162 h01 = __floats2bfloat162_rn(r[0], r[1]), h23 = __floats2bfloat162_rn(r[2], r[3]);
     const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-    const __nv_bfloat162 l01 = __floats2bfloat162_rn(r[0] - f01.x, r[1] - f01.y);
-    const __nv_bfloat162 l23 = __floats2bfloat162_rn(r[2] - f23.x, r[3] - f23.y);
+    const float2 d01 = __fadd2_rn(make_float2(r[0], r[1]), make_float2(-f01.x, -f01.y));
+    const float2 d23 = __fadd2_rn(make_float2(r[2], r[3]), make_float2(-f23.x, -f23.y));
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(d01.x, d01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(d23.x, d23.y);
     *reinterpret_cast<uint2*>(hi + q) =
         make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
     *reinterpret_cast<uint2*>(lo + q) =
@@ -179,6 +181,7 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
         if (out.pvb_hist) out.pvb_hist += c * out.hist_stride;
     }
     LossAcc acc;
+    float2 s2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     const long long npix = (long long)n * n;
     // logical block lb of nlb, thread tid of its 256
     const int nlb = gridDim.x * LB, lb = blockIdx.x * LB + threadIdx.x / kThreads, tid = threadIdx.x % kThreads;
@@ -209,8 +212,12 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
 #pragma unroll
                         for (int j = 0; j < 4; ++j) rn[j] = resist_px2(iv[j], dv[j], zv[j] != 0, p, acc, rd[j]);
                     } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) rn[j] = resist_px(iv[j], zv[j] != 0, p, acc);
+                        const float2 r01 = resist_pair(make_float2(iv[0], iv[1]), zv[0] != 0, zv[1] != 0, p, acc, s2);
+                        const float2 r23 = resist_pair(make_float2(iv[2], iv[3]), zv[2] != 0, zv[3] != 0, p, acc, s2);
+                        rn[0] = r01.x;
+                        rn[1] = r01.y;
+                        rn[2] = r23.x;
+                        rn[3] = r23.y;
                     }
                     if (Rn) {
                         reinterpret_cast<float4*>(Rn)[gk] = make_float4(rn[0], rn[1], rn[2], rn[3]);
@@ -260,6 +267,9 @@ k_resist(const float* In, const float* Id, const unsigned char* __restrict__ Zt,
             }
         }
     }
+    acc.s0 += s2[0].x + s2[0].y;  // the paired lanes of the four-pixel path (zero elsewhere)
+    acc.s1 += s2[1].x + s2[1].y;
+    acc.s2 += s2[2].x + s2[2].y;
     block_store_loss(acc, blockIdx.x * LB, qpart, lpart, sf, si);
     // the last block to finish sums all partials (fixed order) and resets the counter
     __shared__ bool last;

@@ -20,6 +20,16 @@ inline ResistArgs make_resist_args(const devel_resist_params& p) {
     a.k_nom = (float)(2.0 * sz * p.alpha);
     a.k_in = (float)(2.0 * sz * p.beta * d2i);
     a.k_out = (float)(2.0 * sz * p.beta * d2o);
+    a.pad_ = 0.f;
+    a.a_nom2 = make_float2(a.a_nom, a.a_nom);
+    a.a_in2 = make_float2(a.a_in, a.a_in);
+    a.a_out2 = make_float2(a.a_out, a.a_out);
+    a.b2 = make_float2(a.b, a.b);
+    a.d2in2 = make_float2(a.d2in, a.d2in);
+    a.d2out2 = make_float2(a.d2out, a.d2out);
+    a.k_nom2 = make_float2(a.k_nom, a.k_nom);
+    a.k_in2 = make_float2(a.k_in, a.k_in);
+    a.k_out2 = make_float2(a.k_out, a.k_out);
     return a;
 }
 
@@ -89,6 +99,40 @@ __device__ __forceinline__ float resist_px(float I, bool zt_on, const ResistArgs
     float g = (p.k_nom * en) * cn.ez2;
     g = fmaf(p.k_in * ei, ci.ez2, g);
     return fmaf(p.k_out * eo, co.ez2, g);
+}
+
+// Two pixels at once on the packed FP32 pipe (f32x2 add / mul / fma: the same IEEE
+// round-to-nearest operations, so each pixel's dL/dI is bit-identical to resist_px): the
+// parameters pre-broadcast in ResistArgs, the exponentials and the reciprocal per pixel. The squared
+// errors accumulate per lane of s (pixel pairs (0, 2), (1, 3) of a group of four), folded
+// into the thread's sums once at the end (a fixed order).
+__device__ __forceinline__ float2 sfu_exp2_capped2(float2 u) {
+    return make_float2(sfu_exp2(min_nan(u.x, 40.f)), sfu_exp2(min_nan(u.y, 40.f)));
+}
+__device__ __forceinline__ float2 resist_pair(float2 I, bool zt0, bool zt1, const ResistArgs& p, LossAcc& a,
+                                              float2 (&s)[3]) {
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 e1 = sfu_exp2_capped2(__ffma2_rn(p.a_nom2, I, p.b2));
+    const float2 e2 = sfu_exp2_capped2(__ffma2_rn(p.a_in2, I, p.b2));
+    const float2 e3 = sfu_exp2_capped2(__ffma2_rn(p.a_out2, I, p.b2));
+    const float2 q1 = __fadd2_rn(one, e1), q2 = __fadd2_rn(one, e2), q3 = __fadd2_rn(one, e3);
+    const float2 q23 = __fmul2_rn(q2, q3);
+    const float2 pr = __fmul2_rn(q1, q23);
+    const float2 r = make_float2(sfu_rcp(pr.x), sfu_rcp(pr.y));
+    const float2 z1 = __fmul2_rn(q23, r), z2 = __fmul2_rn(__fmul2_rn(q1, q3), r), z3 = __fmul2_rn(__fmul2_rn(q1, q2), r);
+    const float2 g1 = __fmul2_rn(__fmul2_rn(e1, z1), z1), g2 = __fmul2_rn(__fmul2_rn(e2, z2), z2),
+                 g3 = __fmul2_rn(__fmul2_rn(e3, z3), z3);
+    const float2 nzt = make_float2(zt0 ? -1.f : -0.f, zt1 ? -1.f : -0.f);  // z - zt as z + (-zt)
+    const float2 en = __fadd2_rn(z1, nzt), ei = __fadd2_rn(z2, nzt), eo = __fadd2_rn(z3, nzt);
+    s[0] = __ffma2_rn(en, en, s[0]);
+    s[1] = __ffma2_rn(ei, ei, s[1]);
+    s[2] = __ffma2_rn(eo, eo, s[2]);
+    a.l2 += ((I.x >= p.I_th) != zt0) + ((I.y >= p.I_th) != zt1);
+    const float2 di = __fmul2_rn(p.d2in2, I), dd = __fmul2_rn(p.d2out2, I);
+    a.pvb += ((di.x >= p.I_th) != (dd.x >= p.I_th)) + ((di.y >= p.I_th) != (dd.y >= p.I_th));
+    float2 g = __fmul2_rn(__fmul2_rn(p.k_nom2, en), g1);
+    g = __ffma2_rn(__fmul2_rn(p.k_in2, ei), g2, g);
+    return __ffma2_rn(__fmul2_rn(p.k_out2, eo), g3, g);
 }
 
 // Defocused process corner (Sec. II-C): the inner corner images through the defocused
