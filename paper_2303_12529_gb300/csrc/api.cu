@@ -272,13 +272,17 @@ static int enqueue_clip(const devel_ilt_params* p, const devel_clip& cl, int* st
             vel = w.cgD;
             velmax = w.cg_vmax;
         }
-        rc = launch_levelset_step(n, phi, vel, velmax, cl.m, p->dt, p->lambda, phi_alt, w.M,
-                                  tcp ? o->Xhi : nullptr, o->ldn, s, p->upwind);
+        // the tensor-core forward reads the bf16 mask; the u8 mask then only feeds a
+        // re-initialisation (which also overwrites phi) and the final mask output
+        const bool reinit = p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0;
+        const bool keep_mask = !tcp || reinit || (t + 1 == p->iters && cl.mask_out);
+        rc = launch_levelset_step(n, phi, vel, velmax, cl.m, p->dt, p->lambda, reinit ? nullptr : phi_alt,
+                                  keep_mask ? w.M : nullptr, tcp ? o->Xhi : nullptr, o->ldn, s, p->upwind);
         if (rc) return rc;
         float* tmp = phi;
         phi = phi_alt;
         phi_alt = tmp;
-        if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
+        if (reinit) {
             rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s, 1, false);
             if (rc) return rc;
         }

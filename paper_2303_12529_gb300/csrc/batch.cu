@@ -196,13 +196,17 @@ int enqueue_batch(const devel_ilt_params* p, devel_batch* b, int B, const BatchA
         if (t == p->iters) break;  // the final masks are imaged for their metrics only
         rc = launch_spectrum_resident(&v, v.W2, w.rhat, s);
         if (!rc) rc = adjoint_from_rhat(&v, w.bufV, w.vmax, a.status, s);
+        // the next forward reads the bf16 mask; the u8 mask only feeds a re-initialisation
+        // (which also overwrites phi) and the final mask output
+        const int gi = p->start_iter + t;
+        const bool reinit = p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0;
+        const bool keep_mask = reinit || (t + 1 == p->iters && a.mask_out);
         if (!rc)
-            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, a.m, p->dt, p->lambda, phi_alt, w.M, v.Xhi, v.ldn, s,
-                                      p->upwind, B);
+            rc = launch_levelset_step(n, phi, w.bufV, w.vmax, a.m, p->dt, p->lambda, reinit ? nullptr : phi_alt,
+                                      keep_mask ? w.M : nullptr, v.Xhi, v.ldn, s, p->upwind, B);
         if (rc) return rc;
         std::swap(phi, phi_alt);
-        const int gi = p->start_iter + t;
-        if (p->reinit_every > 0 && (gi + 1) % p->reinit_every == 0) {
+        if (reinit) {
             rc = launch_reinit(n, w.M, phi, w.d2, p->d_lo, p->d_hi, s, B, false);
             if (rc) return rc;
         }

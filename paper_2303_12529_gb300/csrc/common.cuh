@@ -338,7 +338,7 @@ int launch_cg_direction(int n, const float* V, float* Vp, float* D, bool restart
                         float* beta_f, double* beta_out, unsigned* counters, double* vmax, int* status,
                         cudaStream_t s);
 // B > 1: a batch of B clips, each array's clip c at c n^2 (mask_bf: c n ldb, vmax: c; m: c n^2
-// or NULL)
+// or NULL). phi_out, mask_out or mask_bf NULL: that output is not written.
 int launch_levelset_step(int n, const float* phi, const float* V, const double* vmax,
                          const float* m, float dt, float lambda, float* phi_out,
                          unsigned char* mask_out, __nv_bfloat16* mask_bf, int ldb, cudaStream_t s,

@@ -785,14 +785,6 @@ int conv_fwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     }
     const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
     dim3 grid(mtiles, cv.coutp / kMCo, nb);
-    static bool attr = false;
-    if (!attr) {
-        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<__nv_bfloat16, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMSmem));
-        DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kMSmem));
-        attr = true;
-    }
     prof_begin(PK_DSN_CONV, s);
     k_conv3_mma<__nv_bfloat16, true><<<grid, 256, kMSmem, s>>>(XA, CA, XB, CB, cv.Wm, cv.coutp, d->P + cv.b_off, 1, Y,
                                                                cv.cout, nullptr, 0, side, side, cv.cout);
@@ -817,13 +809,24 @@ int conv_bwd(devel_dsn* d, int ci, int nb, const __nv_bfloat16* XA, int CA, cons
     k_wgrad_reduce<<<(unsigned)((wc + 255) / 256), 256, 0, s>>>(d->part, tiles, wc, d->G + cv.w_off);
     k_wgrad_reduce<<<(unsigned)((cv.cout + 255) / 256), 256, 0, s>>>(bpart, tiles, (size_t)cv.cout,
                                                                      d->G + cv.b_off);
-    if (dXA) {  // the forward kernel sets the shared-memory attribute of both instances first
+    if (dXA) {  // shared-memory attributes of both instances set at creation (mma_init_attrs)
         const int mtiles = ((side + kMCols - 1) / kMCols) * ((side + kMRows - 1) / kMRows);
         dim3 gd(mtiles, cv.cinp / kMCo, nb);
         k_conv3_mma<float, false><<<gd, 256, kMSmem, s>>>(dY, cv.cout, (const float*)nullptr, 0, cv.Wtm, cv.cinp,
                                                           nullptr, 0, dXA, CA, dXB, accumulate, side, side, cv.cin);
     }
     DEVEL_LAUNCH_CHECK("dsn conv backward");
+    return DEVEL_OK;
+}
+
+// shared-memory opt-in of the warp-level MMA convolution (forward and input-gradient
+// instances), once per device, at network creation: the input gradients need it even when
+// every forward layer runs on the tensor-core kernel
+int mma_init_attrs() {
+    DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kMSmem));
+    DEVEL_CUDA_TRY(cudaFuncSetAttribute(k_conv3_mma<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kMSmem));
     return DEVEL_OK;
 }
 
@@ -995,6 +998,7 @@ int devel_dsn_create(int S, int batch, int width, devel_dsn** out) {
     // (DEVEL_DSN_NO_TC=1 in the environment keeps every layer on the warp-level kernel)
     const char* no_tc = std::getenv("DEVEL_DSN_NO_TC");
     const bool use_tc = !(no_tc && no_tc[0] && no_tc[0] != '0');
+    if (e == cudaSuccess && mma_init_attrs() != DEVEL_OK) e = cudaErrorUnknown;
     if (use_tc && e == cudaSuccess && conv3_tc_init_attrs() != DEVEL_OK) e = cudaErrorUnknown;
     for (size_t i = 0; i < d->convs.size() && e == cudaSuccess; ++i) {
         auto& cv = d->convs[i];

@@ -79,7 +79,7 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
         V += c * np;
         vmax += c;
         if (m) m += c * np;
-        phi_out += c * np;
+        if (phi_out) phi_out += c * np;
         if (mask_out) mask_out += c * np;
         if (mask_bf) mask_bf += c * (size_t)n * ldb;
     }
@@ -134,7 +134,7 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
                            vv[r][j], inv, dt, lam, mv[r][j]);
         }
         if (vec) {
-            *reinterpret_cast<float4*>(phi_out + prow + x0) = make_float4(o[0], o[1], o[2], o[3]);
+            if (phi_out) *reinterpret_cast<float4*>(phi_out + prow + x0) = make_float4(o[0], o[1], o[2], o[3]);
             if (mask_out)
                 *reinterpret_cast<uchar4*>(mask_out + prow + x0) =
                     make_uchar4(o[0] <= 0.f, o[1] <= 0.f, o[2] <= 0.f, o[3] <= 0.f);
@@ -148,7 +148,7 @@ k_levelset_step(const float* __restrict__ phi, const float* __restrict__ V,
 #pragma unroll
             for (int j = 0; j < kPX; ++j) {
                 if (x0 + j < n) {
-                    phi_out[prow + x0 + j] = o[j];
+                    if (phi_out) phi_out[prow + x0 + j] = o[j];
                     if (mask_out) mask_out[prow + x0 + j] = o[j] <= 0.f ? 1 : 0;
                     if (mask_bf) mask_bf[(size_t)y * ldb + x0 + j] = __float2bfloat16_rn(o[j] <= 0.f ? 1.f : 0.f);
                 }
@@ -250,7 +250,7 @@ k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
         V += c * np;
         vmax += c;
         if (m) m += c * np;
-        phi_out += c * np;
+        if (phi_out) phi_out += c * np;
         if (mask_out) mask_out += c * np;
         if (mask_bf) mask_bf += c * (size_t)n * ldb;
     }
@@ -276,7 +276,7 @@ k_levelset_step_weno(const float* __restrict__ phi, const float* __restrict__ V,
         const size_t p = (size_t)y * n + x;
         const float F = -dt * (V[p] * inv);
         const float out = weno_px(t, ly + kWH, threadIdx.x + kWH, F, dt, lam, m ? m[p] : 1.f);
-        phi_out[p] = out;
+        if (phi_out) phi_out[p] = out;
         if (mask_out) mask_out[p] = out <= 0.f ? 1 : 0;
         if (mask_bf) mask_bf[(size_t)y * ldb + x] = __float2bfloat16_rn(out <= 0.f ? 1.f : 0.f);
     }

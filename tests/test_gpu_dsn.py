@@ -232,6 +232,32 @@ def test_network_on_the_full_clip_grid():
     assert np.all(np.isfinite(host(out)))
 
 
+def test_training_step_in_a_fresh_process():
+    """A process whose first and only network is the full-clip one (512^2, width 32), whose
+    every forward layer runs on the tensor-core kernel: its training step launches the
+    warp-level input-gradient kernel without any earlier forward use of that kernel (which
+    once set its shared-memory limit as a side effect), so it is run in a new interpreter."""
+    import os
+    import subprocess
+    import sys
+    need_gpu()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, torch\n"
+        "import paper_2303_12529_gb300 as dv\n"
+        "S, nb = 512, 1\n"
+        "net = dv.Dsn(S, nb, 32, seed=7)\n"
+        "yy, xx = np.mgrid[0:S, 0:S]\n"
+        "x = torch.from_numpy((np.hypot(yy - 200.0, xx - 260.0) - 90.0).astype(np.float32)).cuda()\n"
+        "loss = torch.zeros(1, dtype=torch.float64, device='cuda')\n"
+        "net.train_step(nb, x, x + 3.0, 1e-3, loss, 16.0)\n"
+        "torch.cuda.synchronize()\n"
+        "assert np.isfinite(loss.item()) and loss.item() > 0\n"
+        "print('ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]
+
+
 @pytest.mark.parametrize("S,nb,width", [(256, 2, 32), (512, 1, 16), (512, 1, 32)])
 def test_tensor_core_convolutions_match_oracle(S, nb, width):
     """At side 256 and width 32 the layers with 32, 64 or 128 output channels on planes of
