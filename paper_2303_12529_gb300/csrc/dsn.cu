@@ -658,41 +658,56 @@ __global__ void k_scale(const float* __restrict__ y, size_t count, float s, floa
 }
 
 // coarse[b][I][J] = (sum of the f x f block of fine) * inv, inv = 1 / f^3; the block's
-// rows in order, each left to right
-__global__ void k_phi_down(const float* __restrict__ fine, int n, int f, size_t count, float inv,
+// rows in order, each left to right. Grid (coarse column blocks, coarse row I, images b in
+// steps of gridDim.z): no index divisions.
+__global__ void k_phi_down(const float* __restrict__ fine, int n, int f, int nb, float inv,
                            float* __restrict__ coarse) {
     const int m = n / f;
-    const size_t mm = (size_t)m * m, nn = (size_t)n * n;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / mm;
-        const int r = (int)(i - b * mm), I = r / m, J = r - (r / m) * m;
-        const float* src = fine + b * nn + (size_t)I * f * n + (size_t)J * f;
+    const int J = blockIdx.x * blockDim.x + threadIdx.x, I = blockIdx.y;
+    if (J >= m) return;
+    for (int b = blockIdx.z; b < nb; b += gridDim.z) {
+        const float* src = fine + (size_t)b * n * n + (size_t)I * f * n + (size_t)J * f;
         float s = 0.f;
         for (int u = 0; u < f; ++u)
             for (int v = 0; v < f; ++v) s += src[(size_t)u * n + v];
-        coarse[i] = s * inv;
+        coarse[((size_t)b * m + I) * m + J] = s * inv;
     }
 }
 
 // fine[b][p][q] = f * bilinear interpolation of coarse[b] at ((p + 1/2) / f - 1/2,
-// (q + 1/2) / f - 1/2), coarse indices clamped to [0, m - 1]
-__global__ void k_phi_up(const float* __restrict__ coarse, int n, int f, size_t count, float* __restrict__ fine) {
+// (q + 1/2) / f - 1/2), coarse indices clamped to [0, m - 1]. Grid (blocks of 4 x 256
+// fine columns, fine row p, images b in steps of gridDim.z); a thread writes four
+// consecutive columns (one 16-byte store when n % 4 == 0).
+__global__ void k_phi_up(const float* __restrict__ coarse, int n, int f, int nb, float* __restrict__ fine) {
     const int m = n / f;
-    const size_t mm = (size_t)m * m, nn = (size_t)n * n;
     const float two_f = 2.f * (float)f, ff = (float)f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / nn;
-        const int r = (int)(i - b * nn), p = r / n, q = r - (r / n) * n;
-        const float yc = (float)(2 * p + 1 - f) / two_f, xc = (float)(2 * q + 1 - f) / two_f;
-        const float fy = floorf(yc), fx = floorf(xc);
-        const float ty = yc - fy, tx = xc - fx;
-        const int i0 = (int)fy, j0 = (int)fx;
-        const int ia = min(max(i0, 0), m - 1), ib = min(max(i0 + 1, 0), m - 1);
-        const int ja = min(max(j0, 0), m - 1), jb = min(max(j0 + 1, 0), m - 1);
-        const float* c = coarse + b * mm;
-        const float top = (1.f - tx) * c[(size_t)ia * m + ja] + tx * c[(size_t)ia * m + jb];
-        const float bot = (1.f - tx) * c[(size_t)ib * m + ja] + tx * c[(size_t)ib * m + jb];
-        fine[i] = ff * ((1.f - ty) * top + ty * bot);
+    const int p = blockIdx.y, q0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (q0 >= n) return;
+    const float yc = (float)(2 * p + 1 - f) / two_f;
+    const float fy = floorf(yc), ty = yc - fy;
+    const int i0 = (int)fy;
+    const int ia = min(max(i0, 0), m - 1), ib = min(max(i0 + 1, 0), m - 1);
+    for (int b = blockIdx.z; b < nb; b += gridDim.z) {
+        const float* ca = coarse + ((size_t)b * m + ia) * m;
+        const float* cb = coarse + ((size_t)b * m + ib) * m;
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = min(q0 + j, n - 1);
+            const float xc = (float)(2 * q + 1 - f) / two_f;
+            const float fx = floorf(xc), tx = xc - fx;
+            const int j0 = (int)fx;
+            const int ja = min(max(j0, 0), m - 1), jb = min(max(j0 + 1, 0), m - 1);
+            const float top = (1.f - tx) * ca[ja] + tx * ca[jb];
+            const float bot = (1.f - tx) * cb[ja] + tx * cb[jb];
+            o[j] = ff * ((1.f - ty) * top + ty * bot);
+        }
+        float* out = fine + ((size_t)b * n + p) * n + q0;
+        if ((n & 3) == 0) {
+            *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int j = 0; j < 4 && q0 + j < n; ++j) out[j] = o[j];
+        }
     }
 }
 
@@ -1236,9 +1251,10 @@ extern "C" {
 int devel_phi_downsample(int n, int f, int nb, const float* fine, float* coarse, cudaStream_t s) {
     const int rc = resample_args("devel_phi_downsample", n, f, nb, fine, coarse);
     if (rc || nb == 0) return rc;
-    const size_t count = (size_t)nb * (n / f) * (n / f);
+    const int m = n / f;
     prof_begin(PK_RESAMPLE, s);
-    k_phi_down<<<grid1(count), 256, 0, s>>>(fine, n, f, count, (float)(1.0 / ((double)f * f * f)), coarse);
+    k_phi_down<<<dim3((m + 255) / 256, m, std::min(nb, 65535)), 256, 0, s>>>(fine, n, f, nb,
+                                                                             (float)(1.0 / ((double)f * f * f)), coarse);
     prof_end(PK_RESAMPLE, s);
     DEVEL_LAUNCH_CHECK("devel_phi_downsample");
     return DEVEL_OK;
@@ -1247,9 +1263,8 @@ int devel_phi_downsample(int n, int f, int nb, const float* fine, float* coarse,
 int devel_phi_upsample(int n, int f, int nb, const float* coarse, float* fine, cudaStream_t s) {
     const int rc = resample_args("devel_phi_upsample", n, f, nb, coarse, fine);
     if (rc || nb == 0) return rc;
-    const size_t count = (size_t)nb * n * n;
     prof_begin(PK_RESAMPLE, s);
-    k_phi_up<<<grid1(count), 256, 0, s>>>(coarse, n, f, count, fine);
+    k_phi_up<<<dim3((n + 1023) / 1024, n, std::min(nb, 65535)), 256, 0, s>>>(coarse, n, f, nb, fine);
     prof_end(PK_RESAMPLE, s);
     DEVEL_LAUNCH_CHECK("devel_phi_upsample");
     return DEVEL_OK;
