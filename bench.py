@@ -78,8 +78,9 @@ TRAFFIC = {
     # DRAM bytes per launch from ncu captures of the current kernels (dram__bytes_read.sum +
     # dram__bytes_write.sum), keyed (class, precision[, clips per launch]); a kernel that
     # changes after its capture loses its entry until it is captured again.
-    # profiles/kernels_batched2048_levelset.md: 536.9 MB read + 427.3 MB written
-    ("levelset_step", "bf16x3", 16): 964.2e6,
+    # profiles/kernels_batched2048_levelset.md: five consecutive launches (one of them before a
+    # re-initialisation), 536.9 MB read and 325.4 MB written on average
+    ("levelset_step", "bf16x3", 16): 862.4e6,
 }
 
 
@@ -110,7 +111,10 @@ def kernel_bytes(name, n, K, k, tc, defocus=False):
     ldn = -(-n // 64) * 64
     slices = -(-n // 128) * -(-ldn // 256)
     if name == "levelset_step":
-        return (15 if tc else 13) * px            # phi, V in; phi, mask (+ bf16 mask) out
+        # the method's bytes (phi, V in; phi, the mask out): 4 + 4 + 4 + 1 = 13 B/px, on either
+        # path (the bf16 copy of the mask the tensor-core forward reads, and the u8 mask and
+        # phi stores the solve skips where nothing reads them, are the implementation's)
+        return 13 * px
     if name == "resist":
         # I, Z_t in; dL/dI (fp32, or bf16 hi + lo) out; with the defocused corner also
         # I_def in and dL/dI_def out
@@ -118,7 +122,7 @@ def kernel_bytes(name, n, K, k, tc, defocus=False):
     if name == "edt_cols":
         return 5 * px                             # mask in, packed column distances out
     if name == "edt_rows":
-        return 13 * px                            # distances and mask in, d^2 and phi out
+        return 9 * px                             # distances and mask in, phi out (the solve keeps no d^2)
     if name in ("tc_expand", "expand_gemm"):
         # output image + the two operands; launches alternate between W2 and W
         ops = lambda l: 2 * n * l * (4 if tc else 4)

@@ -915,10 +915,18 @@ __global__ void k_mask_bf16(const unsigned char* __restrict__ M, int n, int ldo,
     const unsigned char* mr = M + (size_t)blockIdx.z * n * n + (size_t)r * n;
     __nv_bfloat16* hr = hi + (size_t)blockIdx.z * n * ldo + (size_t)r * ldo;
     const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    const bool vec = (n & 3) == 0 && (ldo & 3) == 0;  // 4-byte mask loads, 8-byte bf16 stores
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < ldo; c += gridDim.x * blockDim.x * 4) {
+        if (vec && c + 4 <= n) {
+            const uchar4 m4 = *reinterpret_cast<const uchar4*>(mr + c);
+            const unsigned short h1 = 0x3F80u;  // bf16 1.0
+            const uint2 o = make_uint2((m4.x ? h1 : 0u) | ((m4.y ? h1 : 0u) << 16), (m4.z ? h1 : 0u) | ((m4.w ? h1 : 0u) << 16));
+            *reinterpret_cast<uint2*>(hr + c) = o;
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (c + j < ldo) hr[c + j] = (c + j < n && mr[c + j]) ? one : zero;
+            for (int j = 0; j < 4; ++j)
+                if (c + j < ldo) hr[c + j] = (c + j < n && mr[c + j]) ? one : zero;
+        }
     }
 }
 
