@@ -48,7 +48,10 @@ def test_flop_and_byte_accounting():
     assert abs(bench.algorithmic_flops_per_iter(2048, 24, 35) / 1e9 - 58.5) < 0.05
     px = 2048 * 2048
     assert bench.kernel_bytes("resist", 2048, 24, 35, True) == 9 * px
+    # the level-set step's method bytes (phi, V in; phi, mask out) on either path
     assert bench.kernel_bytes("levelset_step", 2048, 24, 35, False) == 13 * px
-    assert bench.kernel_bytes("edt_rows", 2048, 24, 35, True) == 13 * px
+    assert bench.kernel_bytes("levelset_step", 2048, 24, 35, True) == 13 * px
+    # the EDT row pass in the solve: column distances and mask in, phi out (no d^2 kept)
+    assert bench.kernel_bytes("edt_rows", 2048, 24, 35, True) == 9 * px
     # the difference window removes the K dependence of the n^2-sized work
     assert bench.window_flops_per_iter(2048, 24, 35) < bench.algorithmic_flops_per_iter(2048, 24, 35) / 10
