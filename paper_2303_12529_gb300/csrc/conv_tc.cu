@@ -53,30 +53,39 @@ constexpr uint32_t kStgRow = 8 * kStgBox;           // the 64 channels of one ra
 constexpr uint32_t kSmemMax = 232448;               // 227 KiB of dynamic shared memory per CTA
 
 // Per output-channel count N: TR output rows per tile, HR = TR + 2 halo rows, RS raw-row
-// slots, and as many weight granules (GT taps' boxes each, at most 9 granules) as fit beside
-// them in one CTA per SM.
-//   N = 32, 64, 128: M = 128 pixels of one row (PX = 128), N = Cout; a granule is a tap
+// slots, and as many weight granules (GT boxes each, at most 9 granules) as fit beside them
+// in one CTA per SM.
+//   N = 64, 128:     M = 128 pixels of one row (PX = 128), N = Cout; a granule is a tap
 //                    row (the three boxes of one (channel block, dy));
+//   N = 32 (ST):     the three vertical taps stacked along N: per halo row and dx one
+//                    product of N = 96 (B = [W(dy 2); W(dy 1); W(dy 0)] of that dx) into
+//                    TMEM columns 32 hr .. 32 hr + 95, so that every contribution to output
+//                    row r lands at columns 32 (r + 2); TR = 4, accumulators zeroed by the
+//                    epilogue; a granule is one (channel block, dx) box of 96 rows;
 //   N = 256 (SW):    planes of side 64, operands swapped: A = the weights (M = 128 output
 //                    channels, two halves), B = the halo rows (N = PX = 64 pixels); a
 //                    granule is one tap's box of all 256 output channels.
 template <int N>
 struct CfgC {
     static constexpr bool SW = N == 256;
-    static constexpr int TR = 2;
+    static constexpr bool ST = N == 32;
+    static constexpr int TR = ST ? 4 : 2;
     static constexpr int HR = TR + 2;
-    static constexpr int RS = SW ? 2 : N == 128 ? 3 : 4;
-    static constexpr int GT = SW ? 1 : 3;             // taps per weight granule
-    static constexpr int GPU = 9 / GT;                // granules per unit
+    static constexpr int RS = SW ? 2 : N == 64 ? 4 : 3;
+    static constexpr int GT = SW || ST ? 1 : 3;       // boxes per weight granule
+    static constexpr int GPU = ST ? 3 : 9 / GT;       // granules per unit
+    static constexpr int kBoxPerCb = ST ? 3 : 9;      // weight boxes per channel block
+    static constexpr int kBoxRows = ST ? 3 * N : N;   // rows of one weight box
     static constexpr int PX = SW ? 64 : 128;          // pixels of a tile row
     static constexpr uint32_t kA = HR * kHaloBytes;
     static constexpr uint32_t kStg = RS * kStgRow;
-    static constexpr uint32_t kB = N * 128;           // one (channel block, tap) weight box
+    static constexpr uint32_t kB = kBoxRows * 128;    // one weight box
     static constexpr uint32_t kFixed = 1024 + kA + kStg + 1024;  // alignment, halo, raw rows, barriers
     static constexpr int kFit = (int)((kSmemMax - kFixed) / (GT * kB));
     static constexpr int kRows = kFit > 9 ? 9 : kFit;  // weight granule slots
     static_assert(kFit >= 2, "weight ring too small");
-    static constexpr int kAcc = SW ? TR * (N / 128) * PX : TR * N;  // TMEM columns of one accumulator
+    // TMEM columns of one accumulator
+    static constexpr int kAcc = SW ? TR * (N / 128) * PX : ST ? N * (HR + 2) : TR * N;
     static_assert(2 * kAcc <= 512, "two accumulators in TMEM");
     static constexpr uint32_t kCols = 2 * kAcc <= 32 ? 32 : 2 * kAcc <= 64 ? 64 : 2 * kAcc <= 128 ? 128
                                     : 2 * kAcc <= 256 ? 256 : 512;
@@ -206,10 +215,57 @@ __device__ __forceinline__ bool conv_tap_row_sw(uint32_t acc, uint32_t halo, uin
     return true;
 }
 
+// One unit with the vertical taps stacked (N = 32): its three (channel block, dx) weight
+// boxes first (resident: waited once before the first tile), then per halo row hr, once it
+// is in, 3 dx x KS products of N = 96 into TMEM columns 32 hr .. (accumulating onto the
+// zeroed accumulator), and the release of that halo row; the boxes are released at the end.
+template <int N, int KS, bool RES>
+__device__ __forceinline__ bool conv_unit_st(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb,
+                                             const ConvBars& b, volatile int* abort) {
+    using CF = CfgC<N>;
+    constexpr int HR = CF::HR, R = CF::kRows;
+    // the unit's boxes are consecutive granules: slots s0, s0 + 1, s0 + 2 (mod R)
+    const int g0 = RES ? cb * 3 : u * 3;
+    const int s0 = RES ? g0 : g0 % R, s1 = RES ? g0 + 1 : (g0 + 1) % R, s2 = RES ? g0 + 2 : (g0 + 2) % R;
+    if constexpr (!RES) {
+        if (!mbar_wait_ab(&b.w_full[s0], (uint32_t)(g0 / R) & 1u, nullptr, abort) ||
+            !mbar_wait_ab(&b.w_full[s1], (uint32_t)((g0 + 1) / R) & 1u, nullptr, abort) ||
+            !mbar_wait_ab(&b.w_full[s2], (uint32_t)((g0 + 2) / R) & 1u, nullptr, abort))
+            return false;
+    }
+    constexpr uint32_t idesc = idesc_bf16(128, 3 * N);
+    const uint64_t a0 = smem_desc_sw128(halo);
+    const uint64_t wd0 = smem_desc_sw128(wsm + (uint32_t)s0 * CF::kB), wd1 = smem_desc_sw128(wsm + (uint32_t)s1 * CF::kB),
+                   wd2 = smem_desc_sw128(wsm + (uint32_t)s2 * CF::kB);
+    // a runtime loop over the halo rows (each starts with a wait, a branch anyway); the 3 x KS
+    // products of one row are one unrolled run
+#pragma unroll 1
+    for (int hr = 0; hr < HR; ++hr) {
+        if (!mbar_wait_ab(&b.h_full[hr], (uint32_t)u & 1u, nullptr, abort)) return false;
+        fence_after_sync();
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const uint64_t ad = a0 + (uint64_t)(((hr * kHaloBytes + dx * 128) >> 4) + kk * 2);
+                mma_bf16(acc + (uint32_t)(hr * N), ad, (dx == 0 ? wd0 : dx == 1 ? wd1 : wd2) + (uint64_t)(kk * 2), idesc, 1u);
+            }
+        mma_commit(&b.h_empty[hr]);
+    }
+    if constexpr (!RES) {
+        mma_commit(&b.w_empty[s0]);
+        mma_commit(&b.w_empty[s1]);
+        mma_commit(&b.w_empty[s2]);
+    }
+    return true;
+}
+
 template <int N, int KS, bool RES>
 __device__ __forceinline__ bool conv_unit(uint32_t acc, uint32_t halo, uint32_t wsm, int u, int cb, uint32_t accf,
                                           const ConvBars& b, volatile int* abort) {
-    if constexpr (CfgC<N>::SW)
+    if constexpr (CfgC<N>::ST)
+        return conv_unit_st<N, KS, RES>(acc, halo, wsm, u, cb, b, abort);
+    else if constexpr (CfgC<N>::SW)
         return conv_tap_row_sw<N, KS, RES, 0>(acc, halo, wsm, u, cb, accf, b, abort) &&
                conv_tap_row_sw<N, KS, RES, 1>(acc, halo, wsm, u, cb, accf, b, abort) &&
                conv_tap_row_sw<N, KS, RES, 2>(acc, halo, wsm, u, cb, accf, b, abort);
@@ -230,7 +286,11 @@ __device__ __forceinline__ void conv_mma_role(int T, int ncb, int Cin, uint32_t 
         for (int g = 0; g < CfgC<N>::GPU * ncb && ok; ++g) ok = mbar_wait_ab(&b.w_full[g], 0u, nullptr, abort);
     for (int i = 0; i < T && ok; ++i) {
         const int buf = i & 1;
-        if (i >= 2 && !mbar_wait_ab(&b.t_empty[buf], (uint32_t)((i >> 1) - 1) & 1u, nullptr, abort)) {
+        // the accumulator free: drained by the epilogue (and, stacked, zeroed: every tile waits,
+        // the first two on the initial zeroing)
+        const bool wait_acc = CfgC<N>::ST || i >= 2;
+        const uint32_t par = CfgC<N>::ST ? (uint32_t)(i >> 1) & 1u : (uint32_t)((i >> 1) - 1) & 1u;
+        if (wait_acc && !mbar_wait_ab(&b.t_empty[buf], par, nullptr, abort)) {
             ok = false;
             break;
         }
@@ -284,16 +344,16 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
     uint64_t* st_full = reinterpret_cast<uint64_t*>(misc);  // [RS]
     uint64_t* st_empty = st_full + 4;      // [RS]
     uint64_t* h_full = st_full + 8;        // [HR]
-    uint64_t* h_empty = st_full + 12;      // [HR]
-    uint64_t* t_full = st_full + 16;       // [2]
-    uint64_t* t_empty = st_full + 18;      // [2]
-    uint64_t* mma_done = st_full + 20;
-    uint64_t* w_full = st_full + 21;       // [R]
+    uint64_t* h_empty = st_full + 16;      // [HR]
+    uint64_t* t_full = st_full + 24;       // [2]
+    uint64_t* t_empty = st_full + 26;      // [2]
+    uint64_t* mma_done = st_full + 28;
+    uint64_t* w_full = st_full + 29;       // [R]
     uint64_t* w_empty = w_full + R;        // [R]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(w_empty + R);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     uint8_t* dummy = misc + 896;           // 8 x 16 B: stored matrix rows that fall outside a halo block
-    static_assert(HR <= 4 && RS <= 4 && (21 + 2 * R) * 8 + 8 <= 896, "barrier block");
+    static_assert(HR <= 8 && RS <= 4 && (29 + 2 * R) * 8 + 8 <= 896, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Cin = CA + CB, ncb = (Cin + 63) / 64;
@@ -362,12 +422,13 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
                 }
                 if (ws < wtot && (resident || ws < R || mbar_test_wait(&w_empty[ws % R], (uint32_t)((ws / R) - 1) & 1u))) {
                     // granule ws: (channel block ws / GPU, granule ws % GPU) resident, else
-                    // (unit ws / GPU, granule ws % GPU); its boxes are 9 cb + GT granule + j
+                    // (unit ws / GPU, granule ws % GPU); its boxes are kBoxPerCb cb + GT granule + j
                     const int sl = resident ? ws : ws % R;
-                    const int box = resident ? CF::GT * ws : ((ws / CF::GPU) % ncb) * 9 + (ws % CF::GPU) * CF::GT;
+                    const int box =
+                        resident ? CF::GT * ws : ((ws / CF::GPU) % ncb) * CF::kBoxPerCb + (ws % CF::GPU) * CF::GT;
                     mbar_arrive_expect_tx(&w_full[sl], CF::GT * CF::kB);
                     for (int j = 0; j < CF::GT; ++j)
-                        tma_load_2d(&tmW, &w_full[sl], sB + (sl * CF::GT + j) * CF::kB, 0, (box + j) * N);
+                        tma_load_2d(&tmW, &w_full[sl], sB + (sl * CF::GT + j) * CF::kB, 0, (box + j) * CF::kBoxRows);
                     ++ws;
                     prog = true;
                 }
@@ -488,7 +549,20 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
             }
         }
     } else {
-        // ---------------- epilogue: TMEM lanes 32 w .. (pixels), columns r N + co of accumulator i & 1
+        // ---------------- epilogue: TMEM lanes 32 w .. (pixels), columns r N + co of accumulator
+        // i & 1 (stacked: (r + 2) N + co, and the accumulator zeroed after the drain; both
+        // zeroed before the first tile)
+        const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+        if constexpr (CF::ST) {
+            for (int c = 0; c < 2 * CF::kAcc; c += 32) tmem_st32_zero(tlane + (uint32_t)c);
+            tmem_wait_st();
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&t_empty[0]);
+                mbar_arrive(&t_empty[1]);
+            }
+        }
         bool good = true;
         for (int i = 0; i < T; ++i) {
             const int buf = i & 1;
@@ -505,7 +579,7 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
                 for (int c = 0; c < N; c += 32) {
                     uint32_t v[32];
                     if (good) {
-                        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * CF::kAcc + r * N + c), v);
+                        tmem_ld32(tlane + (uint32_t)(buf * CF::kAcc + (CF::ST ? r + 2 : r) * N + c), v);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = 0x7fc00000u;  // NaN: the result is unusable
@@ -521,6 +595,10 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
                 }
             }
             if (good) {
+                if constexpr (CF::ST) {
+                    for (int c = 0; c < CF::kAcc; c += 32) tmem_st32_zero(tlane + (uint32_t)(buf * CF::kAcc + c));
+                    tmem_wait_st();
+                }
                 fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&t_empty[buf]);
@@ -536,14 +614,17 @@ k_conv3_tc(const __grid_constant__ CUtensorMap tmXA, const __grid_constant__ CUt
     }
 }
 
-// Wtc[cb][tap][co][64] = bf16(W[co][ci = 64 cb + j][tap]), zero for ci >= Cin
-__global__ void k_prep_wtc(const float* __restrict__ W, int Cout, int Cin, bf16* __restrict__ Wt) {
+// Wtc[cb][tap][co][64] = bf16(W[co][ci = 64 cb + j][tap]), zero for ci >= Cin; stacked
+// (Cout = 32): Wtc[cb][dx][s][co][64] with the tap (dy = 2 - s, dx), so that the three
+// vertical taps of one dx form one 96-row box
+__global__ void k_prep_wtc(const float* __restrict__ W, int Cout, int Cin, int stacked, bf16* __restrict__ Wt) {
     const int ncb = (Cin + 63) / 64;
     const size_t count = (size_t)ncb * 9 * Cout * 64;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(i % 64);
         const size_t r = i / 64;
-        const int co = (int)(r % Cout), tap = (int)((r / Cout) % 9), cb = (int)(r / ((size_t)Cout * 9));
+        const int co = (int)(r % Cout), q = (int)((r / Cout) % 9), cb = (int)(r / ((size_t)Cout * 9));
+        const int tap = stacked ? (2 - q % 3) * 3 + q / 3 : q;  // stacked: q = 3 dx + s
         const int ci = cb * 64 + j;
         Wt[i] = __float2bfloat16_rn(ci < Cin ? W[((size_t)co * Cin + ci) * 9 + tap] : 0.f);
     }
@@ -582,12 +663,13 @@ int conv3_tc_init_attrs() {
 
 int conv3_tc_make_map(CUtensorMap* tm, const bf16* Wt, int Cin, int Cout) {
     const int rows = (Cin + 63) / 64 * 9 * Cout;
-    return tc::make_map(tm, Wt, rows, 64, 64, Cout);
+    return tc::make_map(tm, Wt, rows, 64, 64, Cout == 32 ? CfgC<32>::kBoxRows : Cout);
 }
 
 int launch_prep_wtc(const float* W, int Cout, int Cin, bf16* Wt, cudaStream_t s) {
     const size_t count = conv3_tc_weight_elems(Cin, Cout);
-    k_prep_wtc<<<(unsigned)std::min<size_t>((count + 255) / 256, 152 * 16), 256, 0, s>>>(W, Cout, Cin, Wt);
+    k_prep_wtc<<<(unsigned)std::min<size_t>((count + 255) / 256, 152 * 16), 256, 0, s>>>(W, Cout, Cin,
+                                                                                          Cout == 32 ? 1 : 0, Wt);
     DEVEL_LAUNCH_CHECK("k_prep_wtc");
     return DEVEL_OK;
 }
@@ -610,8 +692,9 @@ int launch_conv3_tc(const bf16* XA, int CA, const bf16* XB, int CB, const CUtens
     int rc = make_map_rows(&mA, XA, CA, nb, side, pb);
     if (rc == DEVEL_OK) rc = make_map_rows(&mB, CB > 0 ? XB : XA, CB > 0 ? CB : CA, nb, side, pb);
     if (rc != DEVEL_OK) return rc;
-    const int px = Cout == 256 ? CfgC<256>::PX : CfgC<32>::PX;
-    const long long tiles = (long long)nb * ((side + 1) / 2) * ((side + px - 1) / px);  // TR = 2 rows per tile
+    const int px = Cout == 256 ? CfgC<256>::PX : CfgC<64>::PX;
+    const int tr = Cout == 32 ? CfgC<32>::TR : CfgC<64>::TR;
+    const long long tiles = (long long)nb * ((side + tr - 1) / tr) * ((side + px - 1) / px);
     const unsigned grid = (unsigned)std::min<long long>(tiles, sms);
     switch (Cout) {
         case 32:
