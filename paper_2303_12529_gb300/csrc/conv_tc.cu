@@ -3,9 +3,12 @@
 //
 //   D[p][co] = sum_{tap, ci} X[ci][y + dy - 1][x + dx - 1] W[co][ci][tap]      (zero padding)
 //
-// with M = 128 output pixels of one image row (x0 .. x0 + 127), N = Cout (32, 64 or 128),
-// and K = 9 taps x Cin channels, 16 channels per MMA. A tile is TR = 2 consecutive output
-// rows of one 128-pixel segment; a unit is one tile's 64-channel block.
+// with M = 128 output pixels of one image row (x0 .. x0 + 127), N = Cout (64 or 128), and
+// K = 9 taps x Cin channels, 16 channels per MMA. A tile is TR consecutive output rows of
+// one 128-pixel segment; a unit is one tile's 64-channel block. Two other forms share the
+// kernel (CfgC): Cout = 32 stacks the three vertical taps of one dx along N (one N = 96
+// product per halo row and dx, TR = 4), and Cout = 256 on 64^2 planes swaps the operands
+// (weights as A, the 64 pixels of a row as N).
 //
 // Operands:
 //   A  the input rows y0 - 1 .. y0 + TR of a unit as "halo rows": per input row a
@@ -17,12 +20,13 @@
 //      this part: views starting 1, 2 or 7 rows into a 1024-byte pattern read exactly, with
 //      the descriptor's base offset field left 0), so the shifted views need no copy.
 //   B  the weights, prepared as Wtc[cb][tap][co][64] (bf16, channels of block cb, zero past
-//      Cin), one [Cout x 64] box per (channel block, tap), by TMA: resident for the whole
-//      kernel when all of a layer's boxes fit, else through a ring.
+//      Cin; for Cout = 32 as [cb][dx][2 - dy][co][64]), by TMA in boxes of one (channel
+//      block, tap) (96 rows for the stacked form): resident for the whole kernel when all
+//      of a layer's boxes fit, else through a ring.
 //
-// The halo rows are built on chip: TMA copies the raw NCHW row segments (8 channel planes
-// x 152 pixels from x0 - 8 per box; outside the image the copy fills zeros, which is the
-// padding) into a ring of raw rows, and four warps transpose them with ldmatrix /
+// The halo rows are built on chip: TMA copies the raw NCHW row segments (32 or 8 channel
+// planes x 152 pixels from x0 - 8 per box; outside the image the copy fills zeros, which
+// is the padding) into a ring of raw rows, and four warps transpose them with ldmatrix /
 // stmatrix.trans. The kernel is persistent (one CTA per SM over a contiguous range of
 // tiles), warp-specialised, with one mbarrier pair per halo row and per raw-row slot, so
 // that the transposes of a unit's first halo rows overlap the MMAs still reading its

@@ -13,7 +13,8 @@ namespace devel {
 // MMA tile) or Cout = 256 on planes of side 64 (operands swapped: one 64-pixel row per
 // MMA tile, 128 output channels per MMA).
 bool conv3_tc_supported(int Cin, int Cout, int side);
-// bf16 elements of the prepared weights Wtc[ceil(Cin / 64)][9][Cout][64]
+// bf16 elements of the prepared weights Wtc[ceil(Cin / 64)][9][Cout][64] (for Cout = 32 in
+// the order [cb][dx][2 - dy], the same count)
 size_t conv3_tc_weight_elems(int Cin, int Cout);
 // shared-memory opt-in of the kernel instances (once per device, outside any capture)
 int conv3_tc_init_attrs();

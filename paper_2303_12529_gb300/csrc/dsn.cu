@@ -731,7 +731,7 @@ struct devel_dsn {
         int coutp = 0, cinp = 0;
         int side = 0;                  // plane side of the layer's output
         // tcgen05 forward path (conv_tc.cu), when the layer's shape allows it
-        __nv_bfloat16* Wtc = nullptr;  // weights [ceil(Cin / 64)][9][Cout][64]
+        __nv_bfloat16* Wtc = nullptr;  // weights [ceil(Cin / 64)][9][Cout][64] (Cout = 32: [cb][dx][2 - dy])
         CUtensorMap mWtc;
     };
     std::vector<Conv> convs;
