@@ -1348,6 +1348,7 @@ def run_headline(args, wl):
     te_host = te.cpu().pin_memory()
     tg = torch.empty(G, N, dtype=torch.uint8, device=dev)     # the step's targets
     tmp = torch.empty(G, N, dtype=torch.float32, device=dev)
+    d2g = torch.empty(G, N, dtype=torch.int32, device=dev)    # scratch of the batched TSDF
     xc = torch.empty(G, Nc, dtype=torch.float32, device=dev)
     pc = torch.empty(G, Nc, dtype=torch.float32, device=dev)
     arms = {}
@@ -1367,9 +1368,9 @@ def run_headline(args, wl):
         arms[name] = a
 
     def learned_start(phi):
-        """TSDF of each target, block mean to the network's grid, DSN inference, back."""
-        for j in range(G):
-            dv.devel_reinit_sdf(n, tg[j], tmp[j], d2, stream=stream)
+        """TSDF of the targets (one batched call), block mean to the network's grid, DSN
+        inference, back."""
+        dv.devel_reinit_sdf_batch(n, G, tg, tmp, d2g, stream=stream)
         dv.devel_phi_downsample(n, f, tmp, xc, stream)
         net.forward(G, xc, pc, band, stream)
         dv.devel_phi_upsample(n, f, pc, phi, stream)

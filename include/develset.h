@@ -6,6 +6,7 @@
  * Optimization" (Chen et al., arXiv 2303.12529) as CUDA kernels for sm_103a:
  *
  *   devel_reinit_sdf      Eqs. (sdf), (tsdf), Alg. 1 CUDA_TSDF     TSDF of a mask
+ *   devel_reinit_sdf_batch  the same for a batch of masks in one launch
  *   devel_litho_forward   Sec. II-B SOCS imaging                   I = sum_j w_j |M (*) h_j|^2
  *   devel_resist_loss     Sec. III-A sigmoid resist, L_ilt, L_pvb; Sec. II-C L2, PVBand
  *   devel_litho_adjoint   Eqs. (ilt_gradient), (pvb_gradient), (vel)  dL/dM from dL/dI
@@ -241,6 +242,18 @@ int devel_levelset_step_weno5(int n, const float* phi, const float* V, const dou
  */
 int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, float d_lo,
                      float d_hi, cudaStream_t stream);
+
+/*
+ * devel_reinit_sdf of nb masks at once (Eqs. (sdf), (tsdf)): clip c's mask, phi and d2
+ * at offset c*n*n of each array; one launch of each pass over the whole batch, and
+ * per clip the same arithmetic in the same order, so every clip's phi and d2 are
+ * bit-identical to devel_reinit_sdf on it alone.
+ *   mask   device uint8[nb][n*n];  phi  device float[nb][n*n], written
+ *   d2     device int[nb][n*n], scratch and output as in devel_reinit_sdf
+ * Requires 1 <= n <= 8192, 1 <= nb <= 65535, d_lo <= d_hi; 16-byte-aligned arrays.
+ */
+int devel_reinit_sdf_batch(int n, int nb, const unsigned char* mask, float* phi, int* d2,
+                           float d_lo, float d_hi, cudaStream_t stream);
 
 /*
  * Allocation-free re-initialisation (the paper has no counterpart).

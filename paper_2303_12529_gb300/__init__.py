@@ -86,6 +86,7 @@ _sig("devel_resist_loss", [_P, _P, _P, ctypes.POINTER(devel_resist_params), _P, 
 _sig("devel_litho_adjoint", [_P, _P, _P, _P, _P, _P])
 _sig("devel_levelset_step", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_reinit_sdf", [_I, _P, _P, _P, _F, _F, _P])
+_sig("devel_reinit_sdf_batch", [_I, _I, _P, _P, _P, _F, _F, _P])
 _sig("devel_levelset_step_weno5", [_I, _P, _P, _P, _P, _F, _F, _P, _P, _P])
 _sig("devel_cg_direction", [_P, _P, _P, _P, _I, _P, _P, _P, _P])
 _sig("devel_modulation_candidates", [_I, _P, _I, _P, _P, _P])
@@ -135,7 +136,7 @@ EXPORTED = ("devel_last_error", "devel_version", "devel_optics_create", "devel_o
             "devel_dsn_param_count", "devel_dsn_init", "devel_dsn_set_params", "devel_dsn_get_params",
             "devel_dsn_grads", "devel_dsn_forward", "devel_dsn_train_step", "devel_dsn_forward_ahf",
             "devel_dsn_train_step_ahf", "devel_phi_downsample", "devel_phi_upsample", "devel_modulation_search",
-            "devel_batch_create", "devel_batch_destroy", "devel_ilt_solve_batch")
+            "devel_batch_create", "devel_batch_destroy", "devel_ilt_solve_batch", "devel_reinit_sdf_batch")
 REINIT_STATIC_MAX_N = 2048
 
 
@@ -428,6 +429,15 @@ def devel_reinit_sdf(n: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 
     N = n * n
     _check(_lib.devel_reinit_sdf(n, _ptr(mask, torch.uint8, N, "mask"), _ptr(phi, torch.float32, N, "phi"),
                                  _ptr(d2, torch.int32, N, "d2"), d_lo, d_hi, _stream(stream)))
+
+
+def devel_reinit_sdf_batch(n: int, nb: int, mask, phi, d2, d_lo: float = -100.0, d_hi: float = 900.0,
+                           stream=None):
+    """devel_reinit_sdf of nb masks stored back to back (arrays of nb * n * n elements)."""
+    import torch
+    N = nb * n * n
+    _check(_lib.devel_reinit_sdf_batch(n, nb, _ptr(mask, torch.uint8, N, "mask"), _ptr(phi, torch.float32, N, "phi"),
+                                       _ptr(d2, torch.int32, N, "d2"), d_lo, d_hi, _stream(stream)))
 
 
 def devel_reinit_sdf_static(n: int, mask, phi, d_lo: float = -100.0, d_hi: float = 900.0, stream=None):

@@ -922,6 +922,19 @@ int devel_reinit_sdf(int n, const unsigned char* mask, float* phi, int* d2, floa
     return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s);
 }
 
+int devel_reinit_sdf_batch(int n, int nb, const unsigned char* mask, float* phi, int* d2, float d_lo, float d_hi,
+                           cudaStream_t s) {
+    if (n < 1 || n > 8192) return set_error(DEVEL_EINVAL, "devel_reinit_sdf_batch: n=%d outside [1, 8192]", n);
+    if (nb < 1 || nb > 65535) return set_error(DEVEL_EINVAL, "devel_reinit_sdf_batch: nb=%d outside [1, 65535]", nb);
+    CHECK_PTR(mask, "mask");
+    CHECK_PTR(phi, "phi");
+    CHECK_PTR(d2, "d2");
+    if (!(d_lo <= d_hi)) return set_error(DEVEL_EINVAL, "devel_reinit_sdf_batch: d_lo > d_hi");
+    int rc = init_device_attrs();
+    if (rc) return rc;
+    return launch_reinit(n, mask, phi, d2, d_lo, d_hi, s, nb);
+}
+
 int devel_modulation_candidates(int n, const float* phi_gt, int ncand, const float* dh_host, float* m_out,
                                 cudaStream_t s) {
     if (n < 1 || n > 8192) return set_error(DEVEL_EINVAL, "devel_modulation_candidates: n=%d outside [1, 8192]", n);

@@ -91,6 +91,12 @@ def test_argument_checks_need_no_device(lib):
     assert lib.devel_reinit_sdf(16, 17, 32, 48, 0.0, 1.0, None) == dv.DEVEL_EINVAL
     assert lib.devel_reinit_sdf(16, 16, 32, 48, 2.0, 1.0, None) == dv.DEVEL_EINVAL
     assert "d_lo" in dv.devel_last_error()
+    lib.devel_reinit_sdf_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_void_p]
+    assert lib.devel_reinit_sdf_batch(16, 0, 16, 32, 48, 0.0, 1.0, None) == dv.DEVEL_EINVAL      # no clips
+    assert lib.devel_reinit_sdf_batch(16, 65536, 16, 32, 48, 0.0, 1.0, None) == dv.DEVEL_EINVAL  # grid limit
+    assert lib.devel_reinit_sdf_batch(16, 2, 17, 32, 48, 0.0, 1.0, None) == dv.DEVEL_EINVAL      # misaligned
+    assert lib.devel_reinit_sdf_batch(16, 2, 16, 32, 48, 2.0, 1.0, None) == dv.DEVEL_EINVAL      # inverted clamp
     # the CG direction refuses a missing handle and aliased arrays before any launch
     lib.devel_cg_direction.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 4
     assert lib.devel_cg_direction(None, 16, 32, 48, 0, None, 64, None, None) == dv.DEVEL_EINVAL

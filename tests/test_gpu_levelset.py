@@ -82,6 +82,38 @@ def test_reinit_bit_exact_distances(name):
     assert np.array_equal((phi <= 0).astype(np.uint8), (M != 0).astype(np.uint8))
 
 
+@pytest.mark.parametrize("n,kinds", [(200, ("random200", "rects", "empty", "full")), (65, ("single65", "full", "empty"))])
+def test_reinit_batch_matches_the_oracle_and_single_calls(n, kinds):
+    """devel_reinit_sdf_batch on masks stored back to back (a ragged side, the degenerate
+    empty and full masks among them): every clip's d2 equals the oracle's exact squared
+    distances, and its phi and d2 are bit-identical to devel_reinit_sdf on that mask alone."""
+    dv = need_gpu()
+    masks = []
+    for i, k in enumerate(kinds):
+        if k == "random200":
+            masks.append(synth.random_mask(3, n, 0.3))
+        elif k == "rects":
+            masks.append(synth.rect_clip(7, n=n, border=8))
+        elif k == "empty":
+            masks.append(np.zeros((n, n), np.uint8))
+        elif k == "full":
+            masks.append(np.ones((n, n), np.uint8))
+        else:
+            masks.append(REINIT_MASKS[k]())
+    nb = len(masks)
+    M = np.stack([m.astype(np.uint8) for m in masks])
+    phi = torch.empty(nb * n * n, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(nb * n * n, dtype=torch.int32, device="cuda")
+    dv.devel_reinit_sdf_batch(n, nb, dev(M), phi, d2, -100.0, 900.0)
+    torch.cuda.synchronize()
+    phi_b = host(phi).reshape(nb, n, n)
+    d2_b = host(d2).reshape(nb, n, n)
+    for c in range(nb):
+        assert np.array_equal(d2_b[c], sdf.opposite_class_d2(M[c])), c
+        phi1, d21 = _reinit(dv, M[c])
+        assert np.array_equal(phi_b[c], phi1) and np.array_equal(d2_b[c], d21), c
+
+
 def test_reinit_full_size_sampled_rows():
     dv = need_gpu()
     M = synth.manhattan_clip(1003)
