@@ -225,11 +225,6 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def simt_fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak of the CUDA cores: 152 SMs x 128 lanes x 2 flops x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
 # --------------------------------------------------------------------------
 # the reference arm: the FP64 CPU oracle on a bounded sample
 # --------------------------------------------------------------------------
